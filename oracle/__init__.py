@@ -1,0 +1,229 @@
+"""FP64 CPU oracle of the butterfly-filtering hot path (arXiv:1802.01685,
+Sect. 2.1-2.2): chirp templates, bank grid, normalised sliding correlation,
+per-template max/argmax/sigma, max-histogram, time-frequency map and the
+time-randomised control.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It shares no code with the CUDA library and never imports it.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, OpenMP over templates);
+this module only compiles it with gcc and marshals numpy arrays through ctypes.
+Every definition is a reading of the paper's prose; ``oracle.c`` states each
+one next to the code.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+LINEAR, POWERLAW = 0, 1
+ASC, DESC = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, -O2, OpenMP)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+        d, l, i, p = C.c_double, C.c_long, C.c_int, C.c_void_p
+        lib.oracle_powerlaw_tc.restype = d
+        lib.oracle_powerlaw_tc.argtypes = [d, d, d]
+        lib.oracle_cycles.restype = d
+        lib.oracle_cycles.argtypes = [i, d, d, d, d]
+        lib.oracle_freq.restype = d
+        lib.oracle_freq.argtypes = [i, d, d, d, d]
+        lib.oracle_support_len.restype = l
+        lib.oracle_support_len.argtypes = [d, d]
+        lib.oracle_support_first.restype = l
+        lib.oracle_support_first.argtypes = [i, l, l]
+        lib.oracle_check_chirp.restype = i
+        lib.oracle_check_chirp.argtypes = [i, i, d, d, d, d, l]
+        lib.oracle_template.restype = i
+        lib.oracle_template.argtypes = [i, i, d, d, d, d, l, p]
+        lib.oracle_grid.restype = l
+        lib.oracle_grid.argtypes = [p, l, p, l, p, l, d, d, l, l, p, p, p, p, p]
+        lib.oracle_correlate_raw.restype = None
+        lib.oracle_correlate_raw.argtypes = [p, l, p, l, p, p]
+        lib.oracle_search.restype = i
+        lib.oracle_search.argtypes = [p, l, d, p, p, p, p, p, l, l, d, d, d, l, l,
+                                      p, p, p, p, p]
+        lib.oracle_histogram.restype = None
+        lib.oracle_histogram.argtypes = [p, l, l, p]
+        lib.oracle_splitmix64.restype = C.c_uint64
+        lib.oracle_splitmix64.argtypes = [C.c_uint64]
+        lib.oracle_permutation.restype = i
+        lib.oracle_permutation.argtypes = [l, C.c_uint64, p]
+        lib.oracle_permute.restype = i
+        lib.oracle_permute.argtypes = [p, l, C.c_uint64, p]
+        lib.oracle_num_threads.restype = i
+        lib.oracle_num_threads.argtypes = []
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+# ---------------------------------------------------------------- chirps
+
+def powerlaw_tc(f_lo, f_hi, D):
+    return _load().oracle_powerlaw_tc(f_lo, f_hi, D)
+
+
+def cycles(track, f_lo, f_hi, D, t):
+    return _load().oracle_cycles(track, f_lo, f_hi, D, t)
+
+
+def freq(track, f_lo, f_hi, D, t):
+    return _load().oracle_freq(track, f_lo, f_hi, D, t)
+
+
+def support_len(D, fs):
+    return _load().oracle_support_len(D, fs)
+
+
+def support_first(sense, M, MD):
+    return _load().oracle_support_first(sense, M, MD)
+
+
+def check_chirp(track, sense, f_lo, f_hi, D, fs, M) -> bool:
+    return _load().oracle_check_chirp(track, sense, f_lo, f_hi, D, fs, M) == 0
+
+
+def template(track, sense, f_lo, f_hi, D, fs, M) -> np.ndarray:
+    h = np.zeros(M, np.float64)
+    if _load().oracle_template(track, sense, f_lo, f_hi, D, fs, M, _ptr(h)):
+        raise ValueError("invalid chirp parameters")
+    return h
+
+
+def grid(tracks, senses, durations, f_min, f_max, I, J) -> dict:
+    tr = np.ascontiguousarray(tracks, np.int32)
+    se = np.ascontiguousarray(senses, np.int32)
+    du = np.ascontiguousarray(durations, np.float64)
+    K = len(tr) * len(se) * len(du) * I * J
+    out = dict(track=np.zeros(K, np.int32), sense=np.zeros(K, np.int32),
+               f_lo=np.zeros(K), f_hi=np.zeros(K), D=np.zeros(K))
+    n = _load().oracle_grid(_ptr(tr), len(tr), _ptr(se), len(se), _ptr(du), len(du),
+                            f_min, f_max, I, J, _ptr(out["track"]), _ptr(out["sense"]),
+                            _ptr(out["f_lo"]), _ptr(out["f_hi"]), _ptr(out["D"]))
+    assert n == K
+    return out
+
+
+def bank(params: dict, fs: float, M: int) -> np.ndarray:
+    """[K, M] FP64 templates in bank order."""
+    K = len(params["track"])
+    H = np.zeros((K, M), np.float64)
+    for k in range(K):
+        H[k] = template(int(params["track"][k]), int(params["sense"][k]),
+                        float(params["f_lo"][k]), float(params["f_hi"][k]),
+                        float(params["D"][k]), fs, M)
+    return H
+
+
+# ---------------------------------------------------------------- correlation
+
+def correlate_raw(x: np.ndarray, h: np.ndarray):
+    x = np.ascontiguousarray(x, np.float32)
+    h = np.ascontiguousarray(h, np.float64)
+    L = len(x) - len(h) + 1
+    num = np.zeros(L)
+    en = np.zeros(L)
+    _load().oracle_correlate_raw(_ptr(x), len(x), _ptr(h), len(h), _ptr(num), _ptr(en))
+    return num, en
+
+
+def map_shape(N: int, fs: float, dt: float, df: float):
+    """Time bins cover the series, frequency bins cover [0, fs/2)."""
+    nt = int(np.ceil(N / (fs * dt)))
+    nf = int(np.ceil((fs / 2.0) / df))
+    return nt, nf
+
+
+def search(x: np.ndarray, fs: float, params: dict, M: int, *, kappa: float = 5.0,
+           thr: float | None = None, dt: float = 1e-3, df: float = 4.0,
+           want_rho: bool = False, want_map: bool = False) -> dict:
+    """Full oracle search of one series against the bank given by ``params``."""
+    x = np.ascontiguousarray(x, np.float32)
+    N = len(x)
+    K = len(params["track"])
+    L = N - M + 1
+    if thr is None:
+        thr = kappa / np.sqrt(M)
+    tr = np.ascontiguousarray(params["track"], np.int32)
+    se = np.ascontiguousarray(params["sense"], np.int32)
+    fl = np.ascontiguousarray(params["f_lo"], np.float64)
+    fh = np.ascontiguousarray(params["f_hi"], np.float64)
+    Dd = np.ascontiguousarray(params["D"], np.float64)
+    nt, nf = map_shape(N, fs, dt, df)
+    rho = np.zeros((K, L)) if want_rho else None
+    vmax = np.zeros(K)
+    arg = np.zeros(K, np.int64)
+    sig = np.zeros(K)
+    mp = np.zeros((nt, nf)) if want_map else None
+    rc = _load().oracle_search(_ptr(x), N, fs, _ptr(tr), _ptr(se), _ptr(fl), _ptr(fh),
+                               _ptr(Dd), K, M, float(thr), dt, df, nt, nf, _ptr(rho),
+                               _ptr(vmax), _ptr(arg), _ptr(sig), _ptr(mp))
+    if rc:
+        raise ValueError("oracle_search: invalid input")
+    return dict(rho=rho, max=vmax, argmax=arg, sigma=sig, map=mp, thr=float(thr),
+                nt=nt, nf=nf)
+
+
+def histogram(v: np.ndarray, nbins: int = 1024) -> np.ndarray:
+    v = np.ascontiguousarray(v, np.float64)
+    c = np.zeros(nbins, np.uint32)
+    _load().oracle_histogram(_ptr(v), len(v), nbins, _ptr(c))
+    return c
+
+
+# ---------------------------------------------------------------- control
+
+def splitmix64(z: int) -> int:
+    return int(_load().oracle_splitmix64(z & 0xFFFFFFFFFFFFFFFF))
+
+
+def permutation(n: int, seed: int) -> np.ndarray:
+    pi = np.zeros(max(n, 1), np.int64)
+    if _load().oracle_permutation(n, seed & 0xFFFFFFFFFFFFFFFF, _ptr(pi)):
+        raise MemoryError
+    return pi[:n]
+
+
+def permute(x: np.ndarray, seed: int) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.zeros(max(len(x), 1), np.float32)
+    if _load().oracle_permute(_ptr(x), len(x), seed & 0xFFFFFFFFFFFFFFFF, _ptr(y)):
+        raise MemoryError
+    return y[:len(x)]
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
