@@ -1,0 +1,277 @@
+/*
+ * bf.h -- C ABI of the GB300 (sm_103a) butterfly-filtering library.
+ *
+ * Butterfly filtering (van Putten, arXiv:1802.01685, Sect. 2.1) is matched
+ * filtering of a time series -- a gravitational-wave strain channel or a
+ * binned gamma-ray light curve -- against a large bank of ~1 s ascending and
+ * descending chirp templates at every time offset.  Sect. 2.2 adds the
+ * time-randomised control and the reduction of the filter output rho to its
+ * tails rho > kappa * sigma.  This library computes, on one GPU:
+ *
+ *   rho_k(tau) = sum_m x[tau+m] h_k[m] / sqrt(sum_m x[tau+m]^2),
+ *                tau = 0 .. N-M,  rho := 0 where the window is all zero,
+ *
+ * for every template k of a bank and every lag tau, without materialising
+ * rho, and reduces it to per-template max |rho|, its first argmax and
+ * sigma_k = sqrt(mean_tau rho^2), a histogram of the per-template maxima and
+ * a time-frequency scatter-max map painted by the tracks f(t) of all (k, tau)
+ * with |rho| >= kappa / sqrt(M).
+ *
+ * Conventions for every call:
+ *   - Every call returns a bf_status; none aborts the process.  On failure
+ *     bf_last_error() gives a message (thread-local, valid until the next call
+ *     on the same thread).
+ *   - "device pointer" means memory of the context's CUDA device (cudaMalloc,
+ *     torch CUDA tensors, ...); "host pointer" means ordinary or pinned host
+ *     memory.  Where a call accepts either, it detects which with
+ *     cudaPointerGetAttributes.
+ *   - Objects returned through an out-parameter are owned by the library until
+ *     the matching *_destroy call.  Input arrays are copied; the caller keeps
+ *     ownership and may free them when the call returns.
+ *   - Series are float32, finite, uniformly sampled at the rate fs given.
+ */
+#ifndef BF_H
+#define BF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BF_ABI_VERSION 1
+
+typedef enum {
+    BF_OK = 0,
+    BF_EINVAL = 1,      /* invalid argument                                   */
+    BF_ENOMEM = 2,      /* device memory or HBM budget exhausted              */
+    BF_ECUDA = 3,       /* a CUDA runtime call failed                          */
+    BF_ETIMEDOUT = 4,   /* a wait ran out of time                              */
+    BF_EPENDING = 5,    /* serving: the request is still in progress           */
+    BF_EAGAIN = 6,      /* serving: the queue is full, retry later             */
+    BF_ECANCELED = 7,   /* serving: the request was cancelled                  */
+    BF_EDEVICE = 8,     /* a kernel reported an error through its status word  */
+    BF_ENOTSUP = 9      /* the requested mode is not available on this device */
+} bf_status;
+
+/* chirp track and sense (Sect. 2.1: ascending and descending chirps) */
+typedef enum { BF_LINEAR = 0, BF_POWERLAW = 1 } bf_track;
+typedef enum { BF_ASC = 0, BF_DESC = 1 } bf_sense;
+
+/* arithmetic of the correlation (FP32 accumulate in every mode) */
+typedef enum {
+    BF_FP32 = 0,        /* FP32 operands, FP32 FMA (SIMT)                      */
+    BF_BF16 = 1,        /* BF16 operands on tcgen05 tensor cores               */
+    BF_SPLIT_BF16 = 2   /* x = hi + lo, h = hi + lo in BF16; three tcgen05 MMAs
+                           hi*hi + hi*lo + lo*hi into one FP32 accumulator     */
+} bf_precision;
+
+/* which sample layouts a bank keeps in device memory (bit flags) */
+enum {
+    BF_BANK_FP32 = 1,          /* needed by BF_FP32                            */
+    BF_BANK_SPLIT_BF16 = 2     /* needed by BF_BF16 and BF_SPLIT_BF16          */
+};
+
+/*
+ * One chirp template (Sect. 2.1).  The template is T seconds long
+ * (M = round(T * fs) samples); the sweep occupies D = sweep_s seconds
+ * (M_D = round(D * fs) samples, 0 < M_D <= M) centred in the window, starting
+ * at m_s = floor((M - M_D) / 2), with local time t = (m - m_s) / fs:
+ *   linear:    f(t) = f_lo + (f_hi - f_lo) t / D
+ *   power law: f(t) = f_lo (1 - t/t_c)^(-3/8), t_c = D / (1 - (f_lo/f_hi)^(8/3))
+ *   g[m] = sin^2(pi (m - m_s + 1/2) / M_D) cos(2 pi integral_0^t f),
+ *   descending templates are the time reverse h[M-1-m] of the ascending one,
+ *   h = g / |g|_2.
+ * Requires 0 < f_lo < f_hi < fs / 2.
+ */
+typedef struct {
+    int32_t track;      /* bf_track  */
+    int32_t sense;      /* bf_sense  */
+    double f_lo;        /* Hz */
+    double f_hi;        /* Hz */
+    double sweep_s;     /* D, seconds, 0 < D <= T */
+} bf_chirp;
+
+/*
+ * Rectangular grid of chirps (bank sizes of Sect. 2.1-2.2: 0.5 M to 8.64 M):
+ *   f_lo_i  = f_min + (f_max - f_min) i / I,          i = 0..I-1
+ *   f_hi_ij = f_lo_i + (f_max - f_lo_i) (j + 1) / J,  j = 0..J-1
+ * template index k = ((((a * n_senses + b) * n_durations + d) * I + i) * J + j)
+ * for tracks[a], senses[b], durations[d].
+ */
+typedef struct {
+    const int32_t* tracks;   size_t n_tracks;
+    const int32_t* senses;   size_t n_senses;
+    const double* durations; size_t n_durations;
+    double f_min, f_max;     /* Hz */
+    size_t I, J;
+} bf_chirp_grid;
+
+typedef struct {
+    int32_t device;          /* CUDA device ordinal                             */
+    size_t hbm_budget;       /* bytes the context may hold; 0 = 90 % of free    */
+    size_t max_candidates;   /* capacity of the tail list per call; 0 = 2^22    */
+    int32_t serve_slots;     /* requests served concurrently; 0 = 8             */
+    int32_t serve_queue;     /* requests waiting for a slot; 0 = 1024           */
+    int32_t log_level;       /* 0 silent .. 3 verbose                           */
+} bf_config;
+
+typedef struct bf_ctx bf_ctx;
+typedef struct bf_bank bf_bank;
+typedef struct bf_result bf_result;
+
+/* Fills *cfg with the defaults above. */
+void bf_config_default(bf_config* cfg);
+
+/* Creates a context on cfg->device (cfg may be NULL for defaults).  The
+ * context owns a stream, a caching device allocator bounded by hbm_budget and,
+ * once serving is used, a scheduler thread.  BF_ENOTSUP if the device is not
+ * compute capability 10.3. */
+bf_status bf_init(const bf_config* cfg, bf_ctx** out);
+void bf_destroy(bf_ctx* ctx);
+
+/*
+ * Template bank (Sect. 2.1).  Synthesises K templates of T seconds at rate fs
+ * on the device: phase in FP64 cycles reduced mod 1, cosine in FP32, taper,
+ * FP64 unit norm.  `storage` is a mask of BF_BANK_* layouts to keep.
+ * params: host array of K chirps, copied.  BF_EINVAL on a chirp violating the
+ * rules of bf_chirp or K == 0; BF_ENOMEM when the layouts exceed the budget.
+ */
+bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double fs,
+                         double T, unsigned storage, bf_bank** out);
+bf_status bf_bank_create_grid(bf_ctx* ctx, const bf_chirp_grid* grid, double fs,
+                              double T, unsigned storage, bf_bank** out);
+void bf_bank_destroy(bf_bank* bank);
+size_t bf_bank_size(const bf_bank* bank);           /* K */
+size_t bf_bank_template_len(const bf_bank* bank);   /* M */
+/* Copies templates [k0, k0+n) as float32 (row-major [n][M]) to host memory.
+ * Reads the FP32 layout if kept, else hi + lo of the split layout. */
+bf_status bf_bank_read(const bf_bank* bank, size_t k0, size_t n, float* host_out);
+/* Copies the chirp parameters of templates [k0, k0+n) to host memory. */
+bf_status bf_bank_params(const bf_bank* bank, size_t k0, size_t n, bf_chirp* host_out);
+
+typedef struct {
+    int32_t precision;       /* bf_precision                                    */
+    size_t bank_begin;       /* templates [bank_begin, bank_end); end 0 = all   */
+    size_t bank_end;
+    double kappa;            /* tails |rho| >= kappa / sqrt(M) paint the map;
+                                <= 0 means 5                                    */
+    double map_dt_s;         /* map cell: seconds (0 = 1e-3)                    */
+    double map_df_hz;        /* map cell: Hz (0 = 4)                            */
+    int32_t want_map;        /* paint the time-frequency map                    */
+    int32_t want_hist;       /* histogram of per-template maxima                */
+    uint32_t hist_bins;      /* 0 = 1024, uniform on [0, 1]                     */
+    void* stream;            /* cudaStream_t; NULL = synchronous on the context
+                                stream.  Otherwise the call returns once the
+                                work is enqueued and the result is valid after
+                                the stream has reached that point.             */
+    float* rho_out;          /* optional device pointer; with one series, the
+                                full filter output rho[k - bank_begin][tau]
+                                (n_templates x L floats, row-major) is written
+                                here as well.  For inspection of small cases. */
+} bf_opts;
+
+void bf_opts_default(bf_opts* opts);
+
+/*
+ * Searches n_series series against templates [bank_begin, bank_end) of bank
+ * in one batched launch (Sect. 2.1-2.2).  series[s] (host or device pointer)
+ * holds lengths[s] >= M samples at rate fs == the bank's rate.  The result
+ * holds, per series, per template: max |rho| (float), its first argmax
+ * (int32, smallest lag on ties), sigma; the histogram and map when asked;
+ * and over all series the per-template mean of the maxima.
+ * BF_EINVAL on a bad length, rate, range or a precision whose layout the bank
+ * lacks; BF_EDEVICE if a kernel reported an internal timeout.
+ */
+bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* series,
+                       const size_t* lengths, size_t n_series, double fs,
+                       const bf_opts* opts, bf_result** out);
+
+typedef struct {
+    size_t n_series;
+    size_t n_templates;            /* bank_end - bank_begin                     */
+    size_t template_len;           /* M                                         */
+    double correlations;           /* sum over series of lags x templates       */
+    double useful_flops;           /* 2 M x correlations                        */
+    uint64_t n_candidates;         /* (k, tau) with |rho| >= threshold          */
+    int32_t candidates_overflow;   /* 1 if more than max_candidates: map partial */
+    float threshold;               /* kappa / sqrt(M)                           */
+    uint32_t hist_bins;
+    double kernel_ms;              /* correlation kernel time (synchronous calls) */
+} bf_result_info;
+
+bf_status bf_result_info_get(const bf_result* r, bf_result_info* info);
+/* Map of series s: nt = ceil(N_s / (fs dt)) time cells (rows) by
+ * nf = ceil((fs / 2) / df) frequency cells, row-major; cell (b, c) covers
+ * times [b dt, (b+1) dt) and frequencies [c df, (c+1) df). */
+bf_status bf_result_map_shape(const bf_result* r, size_t s, size_t* nt, size_t* nf);
+/* Device pointers into the result for series s (valid until destroy). */
+bf_status bf_result_get_max(const bf_result* r, size_t s, const float** vmax,
+                            const int32_t** argmax, const float** sigma);
+bf_status bf_result_get_hist(const bf_result* r, size_t s, const uint32_t** hist);
+bf_status bf_result_get_map(const bf_result* r, size_t s, const float** map);
+bf_status bf_result_get_mean_max(const bf_result* r, const float** mean_max);
+/* Copies series s's outputs to host arrays; NULL arrays are skipped.
+ * Sizes: n_templates for vmax/argmax/sigma, hist_bins, map_nt * map_nf. */
+bf_status bf_result_copy_to_host(const bf_result* r, size_t s, float* vmax,
+                                 int32_t* argmax, float* sigma, uint32_t* hist,
+                                 float* map);
+bf_status bf_result_copy_mean_max(const bf_result* r, float* host_mean_max);
+void bf_result_destroy(bf_result* r);
+
+/*
+ * Time-randomised control (Sect. 2.2 and Fig. 2: maximal-entropy data with
+ * the same sample histogram).  out[j] = in[pi(j)] with pi the argsort of the
+ * pairs (splitmix64(seed XOR i), i), i = 0..n-1; splitmix64 is the published
+ * generator (one step from state z: z += 0x9E3779B97F4A7C15, two
+ * xor-shift-multiply rounds, final xor-shift).  `in` and `out` are host or
+ * device pointers of n floats and must not overlap.  Deterministic for
+ * (n, seed).  Synchronous.
+ */
+bf_status bf_control_randomize(bf_ctx* ctx, const float* in, size_t n, uint64_t seed,
+                               float* out);
+
+/*
+ * Serving with continuous batching.  submit copies the series and returns a
+ * ticket without waiting for GPU work; a scheduler thread admits requests
+ * while slots and HBM budget allow, and each launch of the batched kernel
+ * mixes template tiles of every admitted request, so a request that arrives
+ * while others run joins the next launch.  BF_EAGAIN: queue full.
+ * BF_ENOMEM: the request alone exceeds the budget.  BF_EINVAL: bad request.
+ */
+typedef struct {
+    const float* series;     /* host or device, n samples                        */
+    size_t n;
+    double fs;
+    const bf_bank* bank;     /* must stay alive until the request completes      */
+    bf_opts opts;            /* opts.stream is ignored                           */
+} bf_request;
+
+bf_status bf_serve_submit(bf_ctx* ctx, const bf_request* req, uint64_t* ticket);
+/* Waits up to timeout_us (< 0: forever, 0: no wait).  BF_OK hands over the
+ * result (caller destroys it); BF_EPENDING / BF_ETIMEDOUT if not done;
+ * BF_ECANCELED if cancelled; BF_EINVAL for an unknown ticket. */
+bf_status bf_serve_poll(bf_ctx* ctx, uint64_t ticket, int64_t timeout_us,
+                        bf_result** out);
+bf_status bf_serve_cancel(bf_ctx* ctx, uint64_t ticket);
+
+typedef struct {
+    uint64_t submitted, completed, cancelled, rejected;
+    uint64_t queued, active;
+    double p50_ms, p99_ms;         /* submit -> completion latency              */
+    double correlations_per_s;     /* completed lag-correlations / busy time    */
+    uint64_t launches;             /* batched kernel launches so far            */
+    size_t hbm_in_use;
+} bf_serve_stats;
+
+bf_status bf_serve_stats_get(bf_ctx* ctx, bf_serve_stats* out);
+
+const char* bf_last_error(void);
+const char* bf_status_string(bf_status s);
+int bf_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BF_H */

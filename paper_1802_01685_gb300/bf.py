@@ -1,0 +1,375 @@
+"""ctypes binding of the C ABI in include/bf.h (argument marshalling only).
+
+Every function of the header is exposed under the same name and raises
+``BFError`` when the call returns a status other than BF_OK (or one of the
+statuses the caller asked to receive).  Arrays may be numpy arrays (host
+memory) or torch tensors (their ``data_ptr()``; host or CUDA).  All arithmetic
+runs in the CUDA library: if ``libbf.so`` is missing this module raises on
+load -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libbf.so")
+
+# ---------------------------------------------------------------- constants
+BF_OK, BF_EINVAL, BF_ENOMEM, BF_ECUDA, BF_ETIMEDOUT, BF_EPENDING, BF_EAGAIN, \
+    BF_ECANCELED, BF_EDEVICE, BF_ENOTSUP = range(10)
+BF_LINEAR, BF_POWERLAW = 0, 1
+BF_ASC, BF_DESC = 0, 1
+BF_FP32, BF_BF16, BF_SPLIT_BF16 = 0, 1, 2
+BF_BANK_FP32, BF_BANK_SPLIT_BF16 = 1, 2
+
+PRECISIONS = {"fp32": BF_FP32, "bf16": BF_BF16, "split_bf16": BF_SPLIT_BF16}
+
+
+class BFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"bf status {status}: {msg}")
+        self.status = status
+
+
+# ---------------------------------------------------------------- structs
+class bf_config(C.Structure):
+    _fields_ = [("device", C.c_int32), ("hbm_budget", C.c_size_t),
+                ("max_candidates", C.c_size_t), ("serve_slots", C.c_int32),
+                ("serve_queue", C.c_int32), ("log_level", C.c_int32)]
+
+
+class bf_chirp(C.Structure):
+    _fields_ = [("track", C.c_int32), ("sense", C.c_int32), ("f_lo", C.c_double),
+                ("f_hi", C.c_double), ("sweep_s", C.c_double)]
+
+
+class bf_chirp_grid(C.Structure):
+    _fields_ = [("tracks", C.POINTER(C.c_int32)), ("n_tracks", C.c_size_t),
+                ("senses", C.POINTER(C.c_int32)), ("n_senses", C.c_size_t),
+                ("durations", C.POINTER(C.c_double)), ("n_durations", C.c_size_t),
+                ("f_min", C.c_double), ("f_max", C.c_double), ("I", C.c_size_t),
+                ("J", C.c_size_t)]
+
+
+class bf_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("bank_begin", C.c_size_t),
+                ("bank_end", C.c_size_t), ("kappa", C.c_double), ("map_dt_s", C.c_double),
+                ("map_df_hz", C.c_double), ("want_map", C.c_int32), ("want_hist", C.c_int32),
+                ("hist_bins", C.c_uint32), ("stream", C.c_void_p), ("rho_out", C.c_void_p)]
+
+
+class bf_result_info(C.Structure):
+    _fields_ = [("n_series", C.c_size_t), ("n_templates", C.c_size_t),
+                ("template_len", C.c_size_t), ("correlations", C.c_double),
+                ("useful_flops", C.c_double), ("n_candidates", C.c_uint64),
+                ("candidates_overflow", C.c_int32), ("threshold", C.c_float),
+                ("hist_bins", C.c_uint32), ("kernel_ms", C.c_double)]
+
+
+class bf_request(C.Structure):
+    _fields_ = [("series", C.c_void_p), ("n", C.c_size_t), ("fs", C.c_double),
+                ("bank", C.c_void_p), ("opts", bf_opts)]
+
+
+class bf_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64),
+                ("cancelled", C.c_uint64), ("rejected", C.c_uint64), ("queued", C.c_uint64),
+                ("active", C.c_uint64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("correlations_per_s", C.c_double), ("launches", C.c_uint64),
+                ("hbm_in_use", C.c_size_t)]
+
+
+# ---------------------------------------------------------------- loading
+_lock = threading.Lock()
+_lib = None
+
+
+def load() -> C.CDLL:
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is not built; run "
+                               "__graft_entry__.build() (no CPU fallback exists)")
+        lib = C.CDLL(LIB_PATH)
+        p, s, i, d, u64 = C.c_void_p, C.c_size_t, C.c_int, C.c_double, C.c_uint64
+        P = C.POINTER
+        sig = {
+            "bf_config_default": (None, [P(bf_config)]),
+            "bf_init": (i, [P(bf_config), P(p)]),
+            "bf_destroy": (None, [p]),
+            "bf_bank_create": (i, [p, P(bf_chirp), s, d, d, C.c_uint, P(p)]),
+            "bf_bank_create_grid": (i, [p, P(bf_chirp_grid), d, d, C.c_uint, P(p)]),
+            "bf_bank_destroy": (None, [p]),
+            "bf_bank_size": (s, [p]),
+            "bf_bank_template_len": (s, [p]),
+            "bf_bank_read": (i, [p, s, s, p]),
+            "bf_bank_params": (i, [p, s, s, P(bf_chirp)]),
+            "bf_opts_default": (None, [P(bf_opts)]),
+            "bf_correlate": (i, [p, p, P(p), P(s), s, d, P(bf_opts), P(p)]),
+            "bf_result_info_get": (i, [p, P(bf_result_info)]),
+            "bf_result_map_shape": (i, [p, s, P(s), P(s)]),
+            "bf_result_get_max": (i, [p, s, P(p), P(p), P(p)]),
+            "bf_result_get_hist": (i, [p, s, P(p)]),
+            "bf_result_get_map": (i, [p, s, P(p)]),
+            "bf_result_get_mean_max": (i, [p, P(p)]),
+            "bf_result_copy_to_host": (i, [p, s, p, p, p, p, p]),
+            "bf_result_copy_mean_max": (i, [p, p]),
+            "bf_result_destroy": (None, [p]),
+            "bf_control_randomize": (i, [p, p, s, u64, p]),
+            "bf_serve_submit": (i, [p, P(bf_request), P(u64)]),
+            "bf_serve_poll": (i, [p, u64, C.c_int64, P(p)]),
+            "bf_serve_cancel": (i, [p, u64]),
+            "bf_serve_stats_get": (i, [p, P(bf_serve_stats)]),
+            "bf_last_error": (C.c_char_p, []),
+            "bf_status_string": (C.c_char_p, [i]),
+            "bf_abi_version": (i, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(st: int, ok=(BF_OK,)) -> int:
+    if st not in ok:
+        raise BFError(st, load().bf_last_error().decode())
+    return st
+
+
+def _addr(a) -> int:
+    """Address of a numpy array or torch tensor (host or device)."""
+    if hasattr(a, "data_ptr"):
+        return int(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        return int(a.ctypes.data)
+    if isinstance(a, int):
+        return a
+    raise TypeError(type(a))
+
+
+# ---------------------------------------------------------------- context
+def bf_config_default() -> bf_config:
+    c = bf_config()
+    load().bf_config_default(C.byref(c))
+    return c
+
+
+def bf_init(cfg: bf_config | None = None) -> int:
+    h = C.c_void_p()
+    _check(load().bf_init(C.byref(cfg) if cfg is not None else None, C.byref(h)))
+    return h.value
+
+
+def bf_destroy(ctx: int) -> None:
+    load().bf_destroy(ctx)
+
+
+# ---------------------------------------------------------------- banks
+def bf_bank_create(ctx: int, chirps, fs: float, T: float,
+                   storage: int = BF_BANK_FP32 | BF_BANK_SPLIT_BF16) -> int:
+    """chirps: sequence of (track, sense, f_lo, f_hi, sweep_s)."""
+    arr = (bf_chirp * len(chirps))(*[bf_chirp(int(a), int(b), float(c), float(d), float(e))
+                                     for a, b, c, d, e in chirps])
+    h = C.c_void_p()
+    _check(load().bf_bank_create(ctx, arr, len(chirps), fs, T, storage, C.byref(h)))
+    return h.value
+
+
+def bf_bank_create_grid(ctx: int, spec: dict, fs: float, T: float,
+                        storage: int = BF_BANK_FP32 | BF_BANK_SPLIT_BF16) -> int:
+    tr = (C.c_int32 * len(spec["tracks"]))(*spec["tracks"])
+    se = (C.c_int32 * len(spec["senses"]))(*spec["senses"])
+    du = (C.c_double * len(spec["durations"]))(*spec["durations"])
+    g = bf_chirp_grid(tr, len(spec["tracks"]), se, len(spec["senses"]), du,
+                      len(spec["durations"]), spec["f_min"], spec["f_max"], spec["I"], spec["J"])
+    h = C.c_void_p()
+    _check(load().bf_bank_create_grid(ctx, C.byref(g), fs, T, storage, C.byref(h)))
+    return h.value
+
+
+def bf_bank_destroy(bank: int) -> None:
+    load().bf_bank_destroy(bank)
+
+
+def bf_bank_size(bank: int) -> int:
+    return int(load().bf_bank_size(bank))
+
+
+def bf_bank_template_len(bank: int) -> int:
+    return int(load().bf_bank_template_len(bank))
+
+
+def bf_bank_read(bank: int, k0: int, n: int) -> np.ndarray:
+    M = bf_bank_template_len(bank)
+    out = np.zeros((n, M), np.float32)
+    _check(load().bf_bank_read(bank, k0, n, out.ctypes.data))
+    return out
+
+
+def bf_bank_params(bank: int, k0: int, n: int) -> list:
+    arr = (bf_chirp * n)()
+    _check(load().bf_bank_params(bank, k0, n, arr))
+    return [(c.track, c.sense, c.f_lo, c.f_hi, c.sweep_s) for c in arr]
+
+
+# ---------------------------------------------------------------- correlate
+def bf_opts_default() -> bf_opts:
+    o = bf_opts()
+    load().bf_opts_default(C.byref(o))
+    return o
+
+
+def make_opts(precision=BF_SPLIT_BF16, bank_begin=0, bank_end=0, kappa=5.0, map_dt_s=1e-3,
+              map_df_hz=4.0, want_map=False, want_hist=True, hist_bins=1024,
+              stream=None, rho_out=None) -> bf_opts:
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    o = bf_opts_default()
+    o.precision = precision
+    o.bank_begin = bank_begin
+    o.bank_end = bank_end
+    o.kappa = kappa
+    o.map_dt_s = map_dt_s
+    o.map_df_hz = map_df_hz
+    o.want_map = int(bool(want_map))
+    o.want_hist = int(bool(want_hist))
+    o.hist_bins = hist_bins
+    o.stream = stream
+    o.rho_out = _addr(rho_out) if rho_out is not None else None
+    return o
+
+
+def bf_correlate(ctx: int, bank: int, series, fs: float, opts: bf_opts | None = None,
+                 lengths=None) -> int:
+    """series: list of float32 arrays (numpy host arrays or torch tensors)."""
+    n = len(series)
+    ptrs = (C.c_void_p * n)(*[_addr(x) for x in series])
+    if lengths is None:
+        lengths = [x.numel() if hasattr(x, "numel") else len(x) for x in series]
+    lens = (C.c_size_t * n)(*lengths)
+    h = C.c_void_p()
+    _check(load().bf_correlate(ctx, bank, ptrs, lens, n, fs,
+                               C.byref(opts) if opts is not None else None, C.byref(h)))
+    return h.value
+
+
+def bf_result_info_get(res: int) -> bf_result_info:
+    info = bf_result_info()
+    _check(load().bf_result_info_get(res, C.byref(info)))
+    return info
+
+
+def bf_result_map_shape(res: int, s: int):
+    nt, nf = C.c_size_t(), C.c_size_t()
+    _check(load().bf_result_map_shape(res, s, C.byref(nt), C.byref(nf)))
+    return nt.value, nf.value
+
+
+def bf_result_get_max(res: int, s: int):
+    a, b, c = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    _check(load().bf_result_get_max(res, s, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def bf_result_get_hist(res: int, s: int) -> int:
+    a = C.c_void_p()
+    _check(load().bf_result_get_hist(res, s, C.byref(a)))
+    return a.value
+
+
+def bf_result_get_map(res: int, s: int) -> int:
+    a = C.c_void_p()
+    _check(load().bf_result_get_map(res, s, C.byref(a)))
+    return a.value
+
+
+def bf_result_get_mean_max(res: int) -> int:
+    a = C.c_void_p()
+    _check(load().bf_result_get_mean_max(res, C.byref(a)))
+    return a.value
+
+
+def bf_result_copy_to_host(res: int, s: int, want_hist=True, want_map=False) -> dict:
+    info = bf_result_info_get(res)
+    K = info.n_templates
+    vmax = np.zeros(K, np.float32)
+    arg = np.zeros(K, np.int32)
+    sig = np.zeros(K, np.float32)
+    hist = np.zeros(info.hist_bins, np.uint32) if want_hist else None
+    mp = None
+    if want_map:
+        nt, nf = bf_result_map_shape(res, s)
+        mp = np.zeros((nt, nf), np.float32)
+    _check(load().bf_result_copy_to_host(
+        res, s, vmax.ctypes.data, arg.ctypes.data, sig.ctypes.data,
+        hist.ctypes.data if hist is not None else None, mp.ctypes.data if mp is not None else None))
+    return dict(max=vmax, argmax=arg, sigma=sig, hist=hist, map=mp)
+
+
+def bf_result_copy_mean_max(res: int) -> np.ndarray:
+    K = bf_result_info_get(res).n_templates
+    out = np.zeros(K, np.float32)
+    _check(load().bf_result_copy_mean_max(res, out.ctypes.data))
+    return out
+
+
+def bf_result_destroy(res: int) -> None:
+    load().bf_result_destroy(res)
+
+
+# ---------------------------------------------------------------- control
+def bf_control_randomize(ctx: int, x, seed: int, out=None):
+    """Returns out (a new float32 numpy array when out is None)."""
+    n = x.numel() if hasattr(x, "numel") else len(x)
+    if out is None:
+        out = np.zeros(n, np.float32)
+    _check(load().bf_control_randomize(ctx, _addr(x), n, seed & 0xFFFFFFFFFFFFFFFF, _addr(out)))
+    return out
+
+
+# ---------------------------------------------------------------- serving
+def bf_serve_submit(ctx: int, bank: int, series, fs: float, opts: bf_opts | None = None) -> int:
+    n = series.numel() if hasattr(series, "numel") else len(series)
+    req = bf_request(_addr(series), n, fs, bank, opts if opts is not None else bf_opts_default())
+    t = C.c_uint64()
+    _check(load().bf_serve_submit(ctx, C.byref(req), C.byref(t)))
+    return t.value
+
+
+def bf_serve_poll(ctx: int, ticket: int, timeout_us: int = -1):
+    """Returns (status, result handle or None); BF_EPENDING / BF_ETIMEDOUT are
+    returned, not raised."""
+    h = C.c_void_p()
+    st = _check(load().bf_serve_poll(ctx, ticket, timeout_us, C.byref(h)),
+                ok=(BF_OK, BF_EPENDING, BF_ETIMEDOUT, BF_ECANCELED))
+    return st, h.value
+
+
+def bf_serve_cancel(ctx: int, ticket: int) -> None:
+    _check(load().bf_serve_cancel(ctx, ticket))
+
+
+def bf_serve_stats_get(ctx: int) -> bf_serve_stats:
+    s = bf_serve_stats()
+    _check(load().bf_serve_stats_get(ctx, C.byref(s)))
+    return s
+
+
+def bf_last_error() -> str:
+    return load().bf_last_error().decode()
+
+
+def bf_status_string(st: int) -> str:
+    return load().bf_status_string(st).decode()
+
+
+def bf_abi_version() -> int:
+    return int(load().bf_abi_version())

@@ -1,0 +1,952 @@
+// C ABI of the butterfly-filtering library: context, caching device allocator,
+// template banks, the batched correlation call, results and the control.
+// The serving loop lives in serve.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "bf_internal.h"
+#include "runtime.h"
+
+namespace bfi {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+bf_status cuda_fail(cudaError_t e, const char* what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return BF_ECUDA;
+}
+
+// ---------------------------------------------------------------- allocator
+static size_t round_alloc(size_t b)
+{
+    const size_t small = 512, big = 2u << 20;
+    if (b <= big) return (b + small - 1) / small * small;
+    return (b + big - 1) / big * big;
+}
+
+Allocator::~Allocator()
+{
+    trim();
+    for (auto& kv : size_of_) cudaFree(kv.first);
+}
+
+void* Allocator::alloc(size_t bytes)
+{
+    if (bytes == 0) bytes = 1;
+    const size_t b = round_alloc(bytes);
+    std::lock_guard<std::mutex> g(mu_);
+    auto it = cache_.lower_bound(b);
+    if (it != cache_.end() && it->first <= b + b / 4 + 4096) {
+        void* p = it->second;
+        cache_.erase(it);
+        live_ += size_of_[p];
+        return p;
+    }
+    if (held_ + b > budget_) {
+        for (auto& kv : cache_) {                      // give back cached blocks
+            cudaFree(kv.second);
+            held_ -= size_of_[kv.second];
+            size_of_.erase(kv.second);
+        }
+        cache_.clear();
+        if (held_ + b > budget_) return nullptr;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, b) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    held_ += b;
+    live_ += b;
+    size_of_[p] = b;
+    return p;
+}
+
+void Allocator::release(void* p)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> g(mu_);
+    auto it = size_of_.find(p);
+    if (it == size_of_.end()) return;
+    live_ -= it->second;
+    cache_.emplace(it->second, p);
+}
+
+void Allocator::trim()
+{
+    std::lock_guard<std::mutex> g(mu_);
+    for (auto& kv : cache_) {
+        cudaFree(kv.second);
+        held_ -= size_of_[kv.second];
+        size_of_.erase(kv.second);
+    }
+    cache_.clear();
+}
+
+size_t Allocator::in_use() const
+{
+    std::lock_guard<std::mutex> g(mu_);
+    return live_;
+}
+
+bool Allocator::fits(size_t bytes) const
+{
+    std::lock_guard<std::mutex> g(mu_);
+    return live_ + round_alloc(bytes) <= budget_;
+}
+
+// ---------------------------------------------------------------- helpers
+static bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+uint32_t template_len(double T, double fs) { return (uint32_t)std::floor(T * fs + 0.5); }
+
+static bool chirp_ok(const bf_chirp& c, double fs, uint32_t M, char* why, size_t n)
+{
+    if (c.track != BF_LINEAR && c.track != BF_POWERLAW) { snprintf(why, n, "bad track %d", c.track); return false; }
+    if (c.sense != BF_ASC && c.sense != BF_DESC) { snprintf(why, n, "bad sense %d", c.sense); return false; }
+    if (!(c.f_lo > 0.0) || !(c.f_hi > c.f_lo) || !(c.f_hi < 0.5 * fs)) {
+        snprintf(why, n, "need 0 < f_lo < f_hi < fs/2 (f_lo=%g f_hi=%g fs=%g)", c.f_lo, c.f_hi, fs);
+        return false;
+    }
+    if (!(c.sweep_s > 0.0)) { snprintf(why, n, "sweep time must be positive"); return false; }
+    const long MD = (long)std::floor(c.sweep_s * fs + 0.5);
+    if (MD < 2 || MD > (long)M) { snprintf(why, n, "sweep of %ld samples outside [2, M=%u]", MD, M); return false; }
+    return true;
+}
+
+static ChirpDev to_dev(const bf_chirp& c, double fs, uint32_t M)
+{
+    ChirpDev d{};
+    d.track = c.track;
+    d.sense = c.sense;
+    d.f_lo = c.f_lo;
+    d.f_hi = c.f_hi;
+    d.D = c.sweep_s;
+    d.tc = c.track == BF_POWERLAW ? c.sweep_s / (1.0 - std::pow(c.f_lo / c.f_hi, 8.0 / 3.0)) : 0.0;
+    d.MD = (int32_t)std::floor(c.sweep_s * fs + 0.5);
+    d.first = (int32_t)((M - (uint32_t)d.MD) / 2);
+    return d;
+}
+
+// ---------------------------------------------------------------- series prep
+void PreparedSeries::release(Allocator& mem)
+{
+    for (void* p : owned) mem.release(p);
+    owned.clear();
+}
+
+bf_status prepare_series(bf_ctx* ctx, const float* src, size_t N, uint32_t M, uint32_t M_pad,
+                         int precision, cudaStream_t st, PreparedSeries* out)
+{
+    PreparedSeries& ps = *out;
+    ps.N = N;
+    ps.L = (uint32_t)(N - M + 1);
+    Allocator& mem = *ctx->mem;
+    auto grab = [&](size_t bytes) -> void* {
+        void* p = mem.alloc(bytes);
+        if (p) ps.owned.push_back(p);
+        return p;
+    };
+    const uint64_t n_lt_simt = ceil_div(ps.L, SIMT_TILE_L);
+    const uint64_t xcap = n_lt_simt * SIMT_TILE_L + M_pad + 1024;
+    ps.x = static_cast<float*>(grab(xcap * sizeof(float)));
+    ps.inv = static_cast<float*>(grab((size_t)ps.L * sizeof(float)));
+    const uint64_t nb = inv_norm_scratch_blocks(N);
+    double* prefix = static_cast<double*>(grab((N + 1) * sizeof(double)));
+    double* bsum = static_cast<double*>(grab(nb * sizeof(double)));
+    if (!ps.x || !ps.inv || !prefix || !bsum) {
+        ps.release(mem);
+        set_error("out of device memory preparing a series of %zu samples", N);
+        return BF_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpyAsync(ps.x, src, N * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ps.x + N, 0, (xcap - N) * sizeof(float), st);
+    if (e == cudaSuccess) e = launch_inv_norm(ps.x, N, M, prefix, bsum, nb, ps.inv, st);
+    if (e == cudaSuccess && precision != BF_FP32) {
+        const uint64_t n_lt = ceil_div(ps.L, TC_TILE_L);
+        const uint64_t rows = n_lt * TC_TILE_L + M_pad + 64;
+        ps.yhi = static_cast<uint4*>(grab(rows * 16));
+        ps.ylo = static_cast<uint4*>(grab(rows * 16));
+        if (!ps.yhi || !ps.ylo) {
+            ps.release(mem);
+            set_error("out of device memory for split rows");
+            return BF_ENOMEM;
+        }
+        e = launch_split_rows(ps.x, N, rows, ps.yhi, ps.ylo, st);
+    }
+    if (e != cudaSuccess) {
+        ps.release(mem);
+        return cuda_fail(e, "series preparation");
+    }
+    return BF_OK;
+}
+
+size_t prepared_series_bytes(size_t N, uint32_t M, uint32_t M_pad, int precision)
+{
+    const uint64_t L = N - M + 1;
+    size_t b = (ceil_div(L, SIMT_TILE_L) * SIMT_TILE_L + M_pad + 1024) * 4 + L * 4 + (N + 1) * 8 +
+               inv_norm_scratch_blocks(N) * 8;
+    if (precision != BF_FP32) b += 2 * (ceil_div(L, TC_TILE_L) * TC_TILE_L + M_pad + 64) * 16;
+    return b + 8 * 4096;
+}
+
+Seg make_segment(const PreparedSeries& ps, uint32_t series_id, const bf_bank* bank, size_t k_begin,
+                 size_t k_end, uint32_t tt_first, uint32_t tt_count, int precision,
+                 unsigned long long* packed_s, double* sumsq_s, float* rho)
+{
+    Seg g{};
+    g.rho = rho;
+    g.x = ps.x;
+    g.yhi = ps.yhi;
+    g.ylo = ps.ylo;
+    g.inv_norm = ps.inv;
+    g.bank_f32 = bank->f32;
+    g.bank_hi = bank->hi;
+    g.bank_lo = bank->lo;
+    g.vmax = packed_s;
+    g.sumsq = sumsq_s;
+    g.L = ps.L;
+    g.n_lag_tiles = (uint32_t)ceil_div(ps.L, tile_lags(precision));
+    g.tt0 = tt_first;
+    g.n_tt = tt_count;
+    g.k_begin = (uint32_t)k_begin;
+    g.k_end = (uint32_t)k_end;
+    g.M_pad = bank->M_pad;
+    g.series_id = series_id;
+    return g;
+}
+
+// One segment per series over the whole template range.
+static void build_segments(const std::vector<PreparedSeries*>& ser, const std::vector<uint32_t>& ids,
+                           const bf_bank* bank, size_t k_begin, size_t k_end, int precision,
+                           unsigned long long* packed, double* sumsq, size_t K,
+                           std::vector<Seg>& segs)
+{
+    const uint32_t tile_t = tile_templates(precision);
+    const uint32_t tt0 = (uint32_t)(k_begin / tile_t);
+    const uint32_t ntt = (uint32_t)(ceil_div(k_end, tile_t) - tt0);
+    for (size_t i = 0; i < ser.size(); ++i)
+        segs.push_back(make_segment(*ser[i], ids[i], bank, k_begin, k_end, tt0, ntt, precision,
+                                    packed + (size_t)ids[i] * K, sumsq + (size_t)ids[i] * K));
+}
+
+cudaError_t launch_segments(bf_ctx* ctx, const std::vector<Seg>& segs, int precision, float thr,
+                            Candidate* cand, unsigned int* cand_count, unsigned int cand_cap,
+                            cudaStream_t st, uint64_t* tiles_out)
+{
+    uint64_t tiles = 0;
+    for (size_t b = 0; b < segs.size(); b += MAX_SEG) {
+        CorrParams p{};
+        p.n_seg = (int)std::min(segs.size() - b, (size_t)MAX_SEG);
+        uint64_t t = 0;
+        for (int i = 0; i < p.n_seg; ++i) {
+            p.seg[i] = segs[b + i];
+            p.seg[i].tile_begin = t;
+            t += (uint64_t)p.seg[i].n_lag_tiles * p.seg[i].n_tt;
+        }
+        p.total_tiles = t;
+        p.thr = thr;
+        p.cand = cand;
+        p.cand_count = cand_count;
+        p.cand_cap = cand_cap;
+        p.err = ctx->d_err;
+        cudaError_t e = precision == BF_FP32 ? launch_corr_simt(p, st)
+                                             : launch_corr_tc(p, precision == BF_SPLIT_BF16 ? 3 : 1,
+                                                              ctx->n_sm, st);
+        if (e != cudaSuccess) return e;
+        tiles += t;
+    }
+    if (tiles_out) *tiles_out = tiles;
+    return cudaSuccess;
+}
+
+static void free_result_buffers(bf_result* r)
+{
+    Allocator& mem = *r->ctx->mem;
+    for (void* p : {(void*)r->packed, (void*)r->sumsq, (void*)r->vmax, (void*)r->argmax,
+                    (void*)r->sigma, (void*)r->hist, (void*)r->map, (void*)r->mean_max,
+                    (void*)r->cand, (void*)r->cand_count})
+        mem.release(p);
+    for (void* p : r->scratch) mem.release(p);
+    r->scratch.clear();
+    r->packed = nullptr;
+    r->sumsq = nullptr;
+    r->vmax = nullptr;
+    r->argmax = nullptr;
+    r->sigma = nullptr;
+    r->hist = nullptr;
+    r->map = nullptr;
+    r->mean_max = nullptr;
+    r->cand = nullptr;
+    r->cand_count = nullptr;
+}
+
+void map_shape(size_t N, double fs, double dt, double df, uint32_t* nt, uint32_t* nf)
+{
+    *nt = (uint32_t)std::ceil((double)N / (fs * dt));
+    *nf = (uint32_t)std::ceil((fs / 2.0) / df);
+}
+
+bf_status resolve_opts(const bf_bank* bank, const bf_opts* in, bf_opts* o)
+{
+    if (in) *o = *in;
+    else bf_opts_default(o);
+    if (o->bank_end == 0) o->bank_end = bank->K;
+    if (o->bank_begin >= o->bank_end || o->bank_end > bank->K) {
+        set_error("bank range [%zu, %zu) outside [0, %zu)", o->bank_begin, o->bank_end, bank->K);
+        return BF_EINVAL;
+    }
+    if (o->precision != BF_FP32 && o->precision != BF_BF16 && o->precision != BF_SPLIT_BF16) {
+        set_error("unknown precision %d", o->precision);
+        return BF_EINVAL;
+    }
+    if (o->precision == BF_FP32 && !bank->f32) {
+        set_error("bank keeps no FP32 layout (create it with BF_BANK_FP32)");
+        return BF_EINVAL;
+    }
+    if (o->precision != BF_FP32 && !bank->hi) {
+        set_error("bank keeps no split-BF16 layout (create it with BF_BANK_SPLIT_BF16)");
+        return BF_EINVAL;
+    }
+    if (!(o->kappa > 0.0)) o->kappa = 5.0;
+    if (!(o->map_dt_s > 0.0)) o->map_dt_s = 1e-3;
+    if (!(o->map_df_hz > 0.0)) o->map_df_hz = 4.0;
+    if (o->hist_bins == 0) o->hist_bins = 1024;
+    return BF_OK;
+}
+
+// Allocates and zeroes the outputs of a result for series of the given lengths.
+bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
+                       const std::vector<size_t>& lengths, double fs, cudaStream_t st,
+                       bf_result** out)
+{
+    std::unique_ptr<bf_result> r(new bf_result());
+    r->ctx = ctx;
+    r->n_series = lengths.size();
+    r->K = o.bank_end - o.bank_begin;
+    r->k_begin = o.bank_begin;
+    r->M = bank->M;
+    r->fs = fs;
+    r->dt = o.map_dt_s;
+    r->df = o.map_df_hz;
+    r->nbins = o.hist_bins;
+    r->want_map = o.want_map != 0;
+    r->want_hist = o.want_hist != 0;
+    r->lengths = lengths;
+    r->thr = (float)(o.kappa / std::sqrt((double)bank->M));
+    Allocator& mem = *ctx->mem;
+    const size_t S = r->n_series, K = r->K;
+    r->packed = static_cast<unsigned long long*>(mem.alloc(S * K * 8));
+    r->sumsq = static_cast<double*>(mem.alloc(S * K * 8));
+    r->vmax = static_cast<float*>(mem.alloc(S * K * 4));
+    r->argmax = static_cast<int32_t*>(mem.alloc(S * K * 4));
+    r->sigma = static_cast<float*>(mem.alloc(S * K * 4));
+    r->mean_max = static_cast<float*>(mem.alloc(K * 4));
+    r->cand_cap = (unsigned int)std::min<size_t>(ctx->cfg.max_candidates, 0xFFFFFFF0u);
+    if (!r->want_map) r->cand_cap = 0;
+    r->cand = static_cast<Candidate*>(mem.alloc(std::max<size_t>(r->cand_cap, 1) * sizeof(Candidate)));
+    r->cand_count = static_cast<unsigned int*>(mem.alloc(sizeof(unsigned int)));
+    bool ok = r->packed && r->sumsq && r->vmax && r->argmax && r->sigma && r->mean_max && r->cand &&
+              r->cand_count;
+    if (ok && r->want_hist) {
+        r->hist = static_cast<uint32_t*>(mem.alloc(S * r->nbins * 4));
+        ok = r->hist != nullptr;
+    }
+    size_t map_total = 0;
+    r->map_nt.resize(S);
+    for (size_t s = 0; s < S; ++s) {
+        uint32_t nt, nf;
+        map_shape(lengths[s], fs, r->dt, r->df, &nt, &nf);
+        r->map_nt[s] = nt;
+        r->map_nf = nf;
+        r->map_off.push_back(map_total);
+        map_total += (size_t)nt * nf;
+    }
+    if (ok && r->want_map) {
+        r->map = static_cast<float*>(mem.alloc(map_total * 4));
+        ok = r->map != nullptr;
+    }
+    if (!ok) {
+        free_result_buffers(r.get());
+        set_error("out of device memory for the result buffers");
+        return BF_ENOMEM;
+    }
+    cudaError_t e = cudaMemsetAsync(r->packed, 0, S * K * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->sumsq, 0, S * K * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->cand_count, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess && r->hist) e = cudaMemsetAsync(r->hist, 0, S * r->nbins * 4, st);
+    if (e == cudaSuccess && r->map) e = cudaMemsetAsync(r->map, 0, map_total * 4, st);
+    if (e != cudaSuccess) {
+        free_result_buffers(r.get());
+        return cuda_fail(e, "clearing result buffers");
+    }
+    *out = r.release();
+    return BF_OK;
+}
+
+size_t result_bytes(const bf_bank* bank, const bf_opts& o, size_t N, double fs, size_t max_cand)
+{
+    const size_t K = o.bank_end - o.bank_begin;
+    size_t b = K * (8 + 8 + 4 + 4 + 4 + 4) + 16 * 512;
+    if (o.want_hist) b += (size_t)o.hist_bins * 4;
+    if (o.want_map) {
+        uint32_t nt, nf;
+        map_shape(N, fs, o.map_dt_s, o.map_df_hz, &nt, &nf);
+        b += (size_t)nt * nf * 4 + max_cand * sizeof(Candidate);
+    }
+    (void)bank;
+    return b;
+}
+
+// Finalize kernels for a result whose correlation launches are enqueued.
+bf_status finalize_result(bf_ctx* ctx, const bf_bank* bank, bf_result* r, cudaStream_t st)
+{
+    const size_t S = r->n_series, K = r->K;
+    cudaError_t e = cudaSuccess;
+    for (size_t s0 = 0; s0 < S && e == cudaSuccess; s0 += MAX_FIN) {
+        FinalizeParams fp{};
+        fp.s0 = (uint32_t)s0;
+        fp.n = (uint32_t)std::min(S - s0, (size_t)MAX_FIN);
+        for (uint32_t i = 0; i < fp.n; ++i) {
+            const size_t s = s0 + i;
+            FinalizeSeries& f = fp.ser[i];
+            f.packed = r->packed + s * K;
+            f.sumsq = r->sumsq + s * K;
+            f.vmax = r->vmax + s * K;
+            f.argmax = r->argmax + s * K;
+            f.sigma = r->sigma + s * K;
+            f.hist = r->hist ? r->hist + s * r->nbins : nullptr;
+            f.map = r->map ? r->map + r->map_off[s] : nullptr;
+            f.L = (uint32_t)(r->lengths[s] - bank->M + 1);
+            f.nt = r->map_nt[s];
+        }
+        e = launch_finalize(fp, (uint32_t)K, r->nbins, st);
+        if (e == cudaSuccess && r->map)
+            e = launch_paint(r->cand, r->cand_count, r->cand_cap, bank->d_params, fp, bank->M,
+                             r->fs, r->dt, r->df, r->map_nf, (unsigned)ctx->n_sm, st);
+    }
+    if (e == cudaSuccess) e = launch_mean_max(r->vmax, (uint32_t)S, (uint32_t)K, r->mean_max, st);
+    if (e != cudaSuccess) return cuda_fail(e, "finalize");
+    return BF_OK;
+}
+
+bf_status check_device_status(bf_ctx* ctx)
+{
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading kernel status");
+    if (h != DEV_OK) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        set_error("kernel reported internal timeout (code %d)", h);
+        return BF_EDEVICE;
+    }
+    return BF_OK;
+}
+
+}  // namespace bfi
+
+using namespace bfi;
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* bf_last_error(void) { return g_err.c_str(); }
+int bf_abi_version(void) { return BF_ABI_VERSION; }
+
+const char* bf_status_string(bf_status s)
+{
+    switch (s) {
+    case BF_OK: return "ok";
+    case BF_EINVAL: return "invalid argument";
+    case BF_ENOMEM: return "out of memory";
+    case BF_ECUDA: return "CUDA error";
+    case BF_ETIMEDOUT: return "timed out";
+    case BF_EPENDING: return "pending";
+    case BF_EAGAIN: return "queue full";
+    case BF_ECANCELED: return "cancelled";
+    case BF_EDEVICE: return "device-side error";
+    case BF_ENOTSUP: return "not supported";
+    }
+    return "unknown status";
+}
+
+void bf_config_default(bf_config* c)
+{
+    if (!c) return;
+    memset(c, 0, sizeof *c);
+    c->device = 0;
+    c->hbm_budget = 0;
+    c->max_candidates = 1u << 22;
+    c->serve_slots = 8;
+    c->serve_queue = 1024;
+    c->log_level = 0;
+}
+
+void bf_opts_default(bf_opts* o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->precision = BF_SPLIT_BF16;
+    o->kappa = 5.0;
+    o->map_dt_s = 1e-3;
+    o->map_df_hz = 4.0;
+    o->want_hist = 1;
+    o->hist_bins = 1024;
+}
+
+bf_status bf_init(const bf_config* cfg, bf_ctx** out)
+{
+    if (!out) { set_error("out is NULL"); return BF_EINVAL; }
+    *out = nullptr;
+    bf_config c;
+    if (cfg) c = *cfg;
+    else bf_config_default(&c);
+    if (c.max_candidates == 0) c.max_candidates = 1u << 22;
+    if (c.serve_slots <= 0) c.serve_slots = 8;
+    if (c.serve_queue <= 0) c.serve_queue = 1024;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (c.device < 0 || c.device >= n) { set_error("device %d of %d", c.device, n); return BF_EINVAL; }
+    e = cudaSetDevice(c.device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaDeviceProp prop{};
+    e = cudaGetDeviceProperties(&prop, c.device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    if (!(prop.major == 10 && prop.minor == 3)) {
+        set_error("device %d is sm_%d%d; this library is built for sm_103a", c.device, prop.major,
+                  prop.minor);
+        return BF_ENOTSUP;
+    }
+    size_t fr = 0, tot = 0;
+    e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+    if (c.hbm_budget == 0) c.hbm_budget = (size_t)(0.9 * (double)fr);
+    std::unique_ptr<bf_ctx> ctx(new bf_ctx());
+    ctx->device = c.device;
+    ctx->n_sm = prop.multiProcessorCount;
+    ctx->cfg = c;
+    ctx->mem.reset(new Allocator(c.hbm_budget));
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+    e = cudaMalloc(&ctx->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(ctx->stream);
+        return cuda_fail(e, "status word");
+    }
+    *out = ctx.release();
+    return BF_OK;
+}
+
+void bf_destroy(bf_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    serve_shutdown(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->mem.reset();
+    cudaFree(ctx->d_err);
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double fs, double T,
+                         unsigned storage, bf_bank** out)
+{
+    if (!ctx || !params || !out) { set_error("NULL argument"); return BF_EINVAL; }
+    *out = nullptr;
+    if (K == 0 || K > 0x7FFFFF00u) { set_error("bank size %zu outside [1, 2^31)", K); return BF_EINVAL; }
+    if (!(fs > 0.0) || !(T > 0.0)) { set_error("need fs > 0 and T > 0"); return BF_EINVAL; }
+    if ((storage & (BF_BANK_FP32 | BF_BANK_SPLIT_BF16)) == 0 || (storage & ~3u)) {
+        set_error("storage mask %u must select BF_BANK_FP32 and/or BF_BANK_SPLIT_BF16", storage);
+        return BF_EINVAL;
+    }
+    const uint32_t M = template_len(T, fs);
+    if (M < 2 || M > (1u << 20)) { set_error("template length %u outside [2, 2^20]", M); return BF_EINVAL; }
+    char why[256];
+    for (size_t k = 0; k < K; ++k)
+        if (!chirp_ok(params[k], fs, M, why, sizeof why)) {
+            set_error("template %zu: %s", k, why);
+            return BF_EINVAL;
+        }
+    cudaSetDevice(ctx->device);
+    std::unique_ptr<bf_bank> b(new bf_bank());
+    b->ctx = ctx;
+    b->K = K;
+    b->K_pad = ceil_div(K, K_ALIGN) * K_ALIGN;
+    b->M = M;
+    b->M_pad = (uint32_t)(ceil_div(M, M_ALIGN) * M_ALIGN);
+    b->fs = fs;
+    b->T = T;
+    b->storage = storage;
+    b->params.assign(params, params + K);
+    std::vector<ChirpDev> dev(K);
+    for (size_t k = 0; k < K; ++k) dev[k] = to_dev(params[k], fs, M);
+    Allocator& mem = *ctx->mem;
+    b->d_params = static_cast<ChirpDev*>(mem.alloc(K * sizeof(ChirpDev)));
+    const size_t elems = b->K_pad * (size_t)b->M_pad;
+    if (storage & BF_BANK_FP32) b->f32 = static_cast<float*>(mem.alloc(elems * 4));
+    if (storage & BF_BANK_SPLIT_BF16) {
+        b->hi = static_cast<uint8_t*>(mem.alloc(elems * 2));
+        b->lo = static_cast<uint8_t*>(mem.alloc(elems * 2));
+    }
+    if (!b->d_params || ((storage & BF_BANK_FP32) && !b->f32) ||
+        ((storage & BF_BANK_SPLIT_BF16) && (!b->hi || !b->lo))) {
+        bf_bank_destroy(b.release());
+        set_error("bank of %zu x %u samples exceeds the device memory budget", K, M);
+        return BF_ENOMEM;
+    }
+    std::lock_guard<std::mutex> g(ctx->launch_mu);
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaMemcpyAsync(b->d_params, dev.data(), K * sizeof(ChirpDev),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_bank_synth(b->d_params, (uint32_t)K, (uint32_t)b->K_pad, M, b->M_pad, fs, b->f32,
+                              b->hi, b->lo, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        bf_bank_destroy(b.release());
+        return cuda_fail(e, "bank synthesis");
+    }
+    *out = b.release();
+    return BF_OK;
+}
+
+bf_status bf_bank_create_grid(bf_ctx* ctx, const bf_chirp_grid* g, double fs, double T,
+                              unsigned storage, bf_bank** out)
+{
+    if (!g || !g->tracks || !g->senses || !g->durations) { set_error("NULL grid"); return BF_EINVAL; }
+    const size_t K = g->n_tracks * g->n_senses * g->n_durations * g->I * g->J;
+    if (K == 0) { set_error("empty grid"); return BF_EINVAL; }
+    if (!(g->f_max > g->f_min)) { set_error("need f_min < f_max"); return BF_EINVAL; }
+    std::vector<bf_chirp> p;
+    p.reserve(K);
+    for (size_t a = 0; a < g->n_tracks; ++a)
+        for (size_t s = 0; s < g->n_senses; ++s)
+            for (size_t d = 0; d < g->n_durations; ++d)
+                for (size_t i = 0; i < g->I; ++i) {
+                    const double lo = g->f_min + (g->f_max - g->f_min) * (double)i / (double)g->I;
+                    for (size_t j = 0; j < g->J; ++j) {
+                        bf_chirp c;
+                        c.track = g->tracks[a];
+                        c.sense = g->senses[s];
+                        c.f_lo = lo;
+                        c.f_hi = lo + (g->f_max - lo) * (double)(j + 1) / (double)g->J;
+                        c.sweep_s = g->durations[d];
+                        p.push_back(c);
+                    }
+                }
+    return bf_bank_create(ctx, p.data(), K, fs, T, storage, out);
+}
+
+void bf_bank_destroy(bf_bank* b)
+{
+    if (!b) return;
+    Allocator& mem = *b->ctx->mem;
+    cudaStreamSynchronize(b->ctx->stream);
+    mem.release(b->d_params);
+    mem.release(b->f32);
+    mem.release(b->hi);
+    mem.release(b->lo);
+    delete b;
+}
+
+size_t bf_bank_size(const bf_bank* b) { return b ? b->K : 0; }
+size_t bf_bank_template_len(const bf_bank* b) { return b ? b->M : 0; }
+
+bf_status bf_bank_params(const bf_bank* b, size_t k0, size_t n, bf_chirp* out)
+{
+    if (!b || !out || k0 + n > b->K) { set_error("bad bank range"); return BF_EINVAL; }
+    memcpy(out, b->params.data() + k0, n * sizeof(bf_chirp));
+    return BF_OK;
+}
+
+bf_status bf_bank_read(const bf_bank* b, size_t k0, size_t n, float* out)
+{
+    if (!b || !out || k0 + n > b->K) { set_error("bad bank range"); return BF_EINVAL; }
+    cudaSetDevice(b->ctx->device);
+    if (b->f32) {
+        cudaError_t e = cudaMemcpy2D(out, b->M * sizeof(float), b->f32 + k0 * b->M_pad,
+                                     b->M_pad * sizeof(float), b->M * sizeof(float), n,
+                                     cudaMemcpyDeviceToHost);
+        return e == cudaSuccess ? BF_OK : cuda_fail(e, "bank read");
+    }
+    // split layout: copy whole 128-template tiles and decode hi + lo
+    const uint32_t n_kb = b->M_pad / TC_BK;
+    const size_t tile_bytes = (size_t)n_kb * TILE_BYTES_A;
+    std::vector<uint16_t> hi(tile_bytes / 2), lo(tile_bytes / 2);
+    for (size_t tt = k0 / TC_TILE_T; tt * TC_TILE_T < k0 + n; ++tt) {
+        cudaError_t e = cudaMemcpy(hi.data(), b->hi + tt * tile_bytes, tile_bytes, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(lo.data(), b->lo + tt * tile_bytes, tile_bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "bank read");
+        for (uint32_t r = 0; r < TC_TILE_T; ++r) {
+            const size_t k = tt * TC_TILE_T + r;
+            if (k < k0 || k >= k0 + n) continue;
+            for (uint32_t m = 0; m < b->M; ++m) {
+                const uint32_t kb = m / TC_BK, c = m % TC_BK;
+                const size_t off = ((size_t)kb * TILE_BYTES_A + (r / 8) * 1024 + (c / 8) * 128 +
+                                    (r % 8) * 16 + (c % 8) * 2) / 2;
+                uint32_t hb = (uint32_t)hi[off] << 16, lb = (uint32_t)lo[off] << 16;
+                float hf, lf;
+                memcpy(&hf, &hb, 4);
+                memcpy(&lf, &lb, 4);
+                out[(k - k0) * b->M + m] = hf + lf;
+            }
+        }
+    }
+    return BF_OK;
+}
+
+bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* series,
+                       const size_t* lengths, size_t n_series, double fs, const bf_opts* opts,
+                       bf_result** out)
+{
+    if (!ctx || !bank || !series || !lengths || !out || n_series == 0) {
+        set_error("NULL argument or no series");
+        return BF_EINVAL;
+    }
+    *out = nullptr;
+    if (bank->ctx != ctx) { set_error("bank belongs to another context"); return BF_EINVAL; }
+    if (std::fabs(fs - bank->fs) > 1e-9 * bank->fs) {
+        set_error("series rate %g differs from the bank's %g", fs, bank->fs);
+        return BF_EINVAL;
+    }
+    bf_opts o;
+    bf_status st = resolve_opts(bank, opts, &o);
+    if (st) return st;
+    if (o.rho_out && n_series != 1) { set_error("rho_out needs exactly one series"); return BF_EINVAL; }
+    if (o.rho_out && !is_device_ptr(o.rho_out)) { set_error("rho_out must be device memory"); return BF_EINVAL; }
+    for (size_t s = 0; s < n_series; ++s) {
+        if (!series[s]) { set_error("series %zu is NULL", s); return BF_EINVAL; }
+        if (lengths[s] < bank->M || lengths[s] > 0xFFFFFFF0ull) {
+            set_error("series %zu has %zu samples; need M=%u <= N < 2^32", s, lengths[s], bank->M);
+            return BF_EINVAL;
+        }
+    }
+    cudaSetDevice(ctx->device);
+    const bool sync = o.stream == nullptr;
+    cudaStream_t strm = sync ? ctx->stream : static_cast<cudaStream_t>(o.stream);
+    std::lock_guard<std::mutex> g(ctx->launch_mu);
+
+    std::vector<size_t> lens(lengths, lengths + n_series);
+    bf_result* r = nullptr;
+    st = alloc_result(ctx, bank, o, lens, fs, strm, &r);
+    if (st) return st;
+    std::unique_ptr<bf_result, void (*)(bf_result*)> guard(r, bf_result_destroy);
+
+    std::vector<PreparedSeries> prep(n_series);
+    std::vector<PreparedSeries*> pptr;
+    std::vector<uint32_t> ids;
+    for (size_t s = 0; s < n_series; ++s) {
+        st = prepare_series(ctx, series[s], lengths[s], bank->M, bank->M_pad, o.precision, strm, &prep[s]);
+        if (st) {
+            for (auto& p : prep) p.release(*ctx->mem);
+            return st;
+        }
+        for (void* p : prep[s].owned) r->scratch.push_back(p);
+        prep[s].owned.clear();
+        pptr.push_back(&prep[s]);
+        ids.push_back((uint32_t)s);
+        r->correlations += (double)prep[s].L * (double)r->K;
+    }
+    std::vector<Seg> segs;
+    build_segments(pptr, ids, bank, o.bank_begin, o.bank_end, o.precision, r->packed, r->sumsq, r->K, segs);
+    if (o.rho_out) segs[0].rho = o.rho_out;
+
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (sync) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, strm);
+    }
+    cudaError_t e = launch_segments(ctx, segs, o.precision, r->thr, r->cand, r->cand_count,
+                                    r->cand_cap, strm, nullptr);
+    if (sync) cudaEventRecord(e1, strm);
+    if (e != cudaSuccess) {
+        if (e0) { cudaEventDestroy(e0); cudaEventDestroy(e1); }
+        return cuda_fail(e, "correlation launch");
+    }
+    st = finalize_result(ctx, bank, r, strm);
+    if (st) {
+        if (e0) { cudaEventDestroy(e0); cudaEventDestroy(e1); }
+        return st;
+    }
+    if (sync) {
+        e = cudaStreamSynchronize(strm);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        r->kernel_ms = ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e != cudaSuccess) return cuda_fail(e, "correlation");
+        st = check_device_status(ctx);
+        if (st) return st;
+        unsigned int cnt = 0;
+        cudaMemcpy(&cnt, r->cand_count, sizeof cnt, cudaMemcpyDeviceToHost);
+        r->n_candidates = cnt;
+        for (void* p : r->scratch) ctx->mem->release(p);
+        r->scratch.clear();
+    }
+    *out = guard.release();
+    return BF_OK;
+}
+
+bf_status bf_result_info_get(const bf_result* r, bf_result_info* info)
+{
+    if (!r || !info) { set_error("NULL argument"); return BF_EINVAL; }
+    memset(info, 0, sizeof *info);
+    info->n_series = r->n_series;
+    info->n_templates = r->K;
+    info->template_len = r->M;
+    info->correlations = r->correlations;
+    info->useful_flops = 2.0 * r->M * r->correlations;
+    uint64_t n = r->n_candidates;
+    if (r->cand_count && n == 0) {
+        unsigned int c = 0;
+        if (cudaMemcpy(&c, r->cand_count, sizeof c, cudaMemcpyDeviceToHost) == cudaSuccess) n = c;
+    }
+    info->n_candidates = n;
+    info->candidates_overflow = n > r->cand_cap ? 1 : 0;
+    info->threshold = r->thr;
+    info->hist_bins = r->nbins;
+    info->kernel_ms = r->kernel_ms;
+    return BF_OK;
+}
+
+bf_status bf_result_map_shape(const bf_result* r, size_t s, size_t* nt, size_t* nf)
+{
+    if (!r || s >= r->n_series) { set_error("bad series index"); return BF_EINVAL; }
+    if (nt) *nt = r->map_nt[s];
+    if (nf) *nf = r->map_nf;
+    return BF_OK;
+}
+
+bf_status bf_result_get_max(const bf_result* r, size_t s, const float** vmax, const int32_t** argmax,
+                            const float** sigma)
+{
+    if (!r || s >= r->n_series) { set_error("bad series index"); return BF_EINVAL; }
+    if (vmax) *vmax = r->vmax + s * r->K;
+    if (argmax) *argmax = r->argmax + s * r->K;
+    if (sigma) *sigma = r->sigma + s * r->K;
+    return BF_OK;
+}
+
+bf_status bf_result_get_hist(const bf_result* r, size_t s, const uint32_t** hist)
+{
+    if (!r || s >= r->n_series || !r->hist) { set_error("no histogram for this series"); return BF_EINVAL; }
+    *hist = r->hist + s * r->nbins;
+    return BF_OK;
+}
+
+bf_status bf_result_get_map(const bf_result* r, size_t s, const float** map)
+{
+    if (!r || s >= r->n_series || !r->map) { set_error("no map for this series"); return BF_EINVAL; }
+    *map = r->map + r->map_off[s];
+    return BF_OK;
+}
+
+bf_status bf_result_get_mean_max(const bf_result* r, const float** mean_max)
+{
+    if (!r || !mean_max) { set_error("NULL argument"); return BF_EINVAL; }
+    *mean_max = r->mean_max;
+    return BF_OK;
+}
+
+bf_status bf_result_copy_to_host(const bf_result* r, size_t s, float* vmax, int32_t* argmax,
+                                 float* sigma, uint32_t* hist, float* map)
+{
+    if (!r || s >= r->n_series) { set_error("bad series index"); return BF_EINVAL; }
+    cudaSetDevice(r->ctx->device);
+    const size_t K = r->K;
+    cudaError_t e = cudaSuccess;
+    if (vmax) e = cudaMemcpy(vmax, r->vmax + s * K, K * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && argmax) e = cudaMemcpy(argmax, r->argmax + s * K, K * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && sigma) e = cudaMemcpy(sigma, r->sigma + s * K, K * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && hist) {
+        if (!r->hist) { set_error("no histogram was requested"); return BF_EINVAL; }
+        e = cudaMemcpy(hist, r->hist + s * r->nbins, r->nbins * 4, cudaMemcpyDeviceToHost);
+    }
+    if (e == cudaSuccess && map) {
+        if (!r->map) { set_error("no map was requested"); return BF_EINVAL; }
+        e = cudaMemcpy(map, r->map + r->map_off[s], (size_t)r->map_nt[s] * r->map_nf * 4,
+                       cudaMemcpyDeviceToHost);
+    }
+    return e == cudaSuccess ? BF_OK : cuda_fail(e, "result copy");
+}
+
+bf_status bf_result_copy_mean_max(const bf_result* r, float* out)
+{
+    if (!r || !out) { set_error("NULL argument"); return BF_EINVAL; }
+    cudaSetDevice(r->ctx->device);
+    cudaError_t e = cudaMemcpy(out, r->mean_max, r->K * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? BF_OK : cuda_fail(e, "result copy");
+}
+
+void bf_result_destroy(bf_result* r)
+{
+    if (!r) return;
+    free_result_buffers(r);
+    delete r;
+}
+
+bf_status bf_control_randomize(bf_ctx* ctx, const float* in, size_t n, uint64_t seed, float* out)
+{
+    if (!ctx || !in || !out) { set_error("NULL argument"); return BF_EINVAL; }
+    if (n == 0) return BF_OK;
+    if (n >= 0xFFFFFFFFull) { set_error("series of %zu samples too long", n); return BF_EINVAL; }
+    const char* a = reinterpret_cast<const char*>(in);
+    const char* b = reinterpret_cast<const char*>(out);
+    if (a < b + n * 4 && b < a + n * 4) { set_error("in and out overlap"); return BF_EINVAL; }
+    cudaSetDevice(ctx->device);
+    std::lock_guard<std::mutex> g(ctx->launch_mu);
+    Allocator& mem = *ctx->mem;
+    const bool din = is_device_ptr(in), dout = is_device_ptr(out);
+    void* scratch = mem.alloc(permute_scratch_bytes(n));
+    float* dx = din ? const_cast<float*>(in) : static_cast<float*>(mem.alloc(n * 4));
+    float* dy = dout ? out : static_cast<float*>(mem.alloc(n * 4));
+    auto cleanup = [&]() {
+        mem.release(scratch);
+        if (!din) mem.release(dx);
+        if (!dout) mem.release(dy);
+    };
+    if (!scratch || !dx || !dy) {
+        cleanup();
+        set_error("out of device memory for the control of %zu samples", n);
+        return BF_ENOMEM;
+    }
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    if (!din) e = cudaMemcpyAsync(dx, in, n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_permute(dx, n, seed, dy, scratch, st);
+    if (e == cudaSuccess && !dout) e = cudaMemcpyAsync(out, dy, n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    return e == cudaSuccess ? BF_OK : cuda_fail(e, "control randomisation");
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Template synthesis on the device (arXiv:1802.01685 Sect. 2.1: banks of up to
+// 8.64 million ascending and descending chirps of ~1 s).
+//
+// One CTA builds one template: the phase in cycles is evaluated in FP64 and
+// reduced to [-1/2, 1/2) before the cosine, which then runs in FP32 (the
+// reduction is where FP64 is needed; after it FP32 holds the phase to ~1e-7
+// of a cycle).  The taper is sin^2(pi (j + 1/2) / M_D); the unit norm is an FP64
+// sum over the template.  Outputs, as requested:
+//   f32: row-major [K_pad][M_pad] float (SIMT path),
+//   hi/lo: the tensor-core operand layout (below), hi = bf16(h), lo = bf16(h - hi).
+//
+// Tensor-core operand layout ("A" operand of tcgen05.mma, K-major, no swizzle):
+// templates are grouped in tiles of 128 (tt = k / 128, r = k % 128) and samples
+// in blocks of 64 (kb = m / 64, c = m % 64).  Each (tt, kb) block is 16 KiB,
+// stored contiguously at ((tt * n_kb + kb) * 16384) so one bulk copy stages it;
+// inside, the 8x8 core matrix (r / 8, c / 8) is 128 contiguous bytes at
+// (r / 8) * 1024 + (c / 8) * 128, row r % 8 at +16 * (r % 8), element c % 8 at +2.
+// Hence LBO (next 8 samples) = 128 B and SBO (next 8 templates) = 1024 B.
+#include "bf_internal.h"
+
+namespace bfi {
+
+__device__ __forceinline__ double d_cycles(const ChirpDev& p, double t)
+{
+    if (p.track == BF_LINEAR) return p.f_lo * t + (p.f_hi - p.f_lo) * t * t / (2.0 * p.D);
+    return 1.6 * p.f_lo * p.tc * (1.0 - pow(1.0 - t / p.tc, 0.625));
+}
+
+__device__ __forceinline__ size_t tc_offset(uint32_t k, uint32_t m, uint32_t n_kb)
+{
+    uint32_t tt = k >> 7, r = k & 127, kb = m >> 6, c = m & 63;
+    return ((size_t)tt * n_kb + kb) * TILE_BYTES_A + (r >> 3) * 1024 + (c >> 3) * 128 +
+           (r & 7) * 16 + (c & 7) * 2;
+}
+
+__global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__ params,
+                                                    uint32_t K, uint32_t M, uint32_t M_pad,
+                                                    double fs, float* __restrict__ f32,
+                                                    uint8_t* __restrict__ hi,
+                                                    uint8_t* __restrict__ lo)
+{
+    extern __shared__ float g[];        // M_pad samples of the ascending template
+    __shared__ double red[8];
+    const uint32_t k = blockIdx.x;
+    const uint32_t n_kb = M_pad / TC_BK;
+    const bool valid = k < K;
+    ChirpDev p{};
+    if (valid) p = params[k];
+
+    double part = 0.0;
+    for (uint32_t m = threadIdx.x; m < M_pad; m += blockDim.x) {
+        float v = 0.f;
+        if (valid) {
+            int j = (int)m - p.first;          // ascending-template sample index
+            if (p.sense == BF_DESC) j = (int)(M - 1 - m) - p.first;
+            if (m < M && j >= 0 && j < p.MD) {
+                double c = d_cycles(p, (double)j / fs);
+                double fr = c - rint(c);                   // [-1/2, 1/2]
+                float cs = cospif((float)(2.0 * fr));
+                float s = sinpif((float)(((double)j + 0.5) / (double)p.MD));
+                v = s * s * cs;
+            }
+        }
+        g[m] = v;
+        part += (double)v * (double)v;
+    }
+    // block sum of g^2 in FP64
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
+
+    for (uint32_t m = threadIdx.x; m < M_pad; m += blockDim.x) {
+        double h = (double)g[m] * inv;
+        if (f32) f32[(size_t)k * M_pad + m] = (float)h;
+        if (hi) {
+            __nv_bfloat16 bh = __double2bfloat16(h);
+            __nv_bfloat16 bl = __double2bfloat16(h - (double)__bfloat162float(bh));
+            size_t off = tc_offset(k, m, n_kb);
+            *reinterpret_cast<__nv_bfloat16*>(hi + off) = bh;
+            *reinterpret_cast<__nv_bfloat16*>(lo + off) = bl;
+        }
+    }
+}
+
+cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t K, uint32_t K_pad, uint32_t M,
+                              uint32_t M_pad, double fs, float* f32, uint8_t* hi, uint8_t* lo,
+                              cudaStream_t s)
+{
+    size_t smem = (size_t)M_pad * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_bank_synth,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_bank_synth<<<K_pad, 256, smem, s>>>(params, K, M, M_pad, fs, f32, hi, lo);
+    return cudaGetLastError();
+}
+
+}  // namespace bfi

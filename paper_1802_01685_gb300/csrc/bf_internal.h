@@ -1,0 +1,219 @@
+// Internal declarations of the butterfly-filtering library (not part of the
+// C ABI).  Geometry of the kernels, the launch record passed by value to the
+// correlation kernels, and the host-side objects behind the opaque handles.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "bf.h"
+
+namespace bfi {
+
+// ---------------------------------------------------------------- geometry
+// Tensor-core path: one CTA tile is 128 templates (MMA M) x 512 lags (two MMAs
+// with N = 256) and runs over the template length in stages of 64 samples.
+constexpr int TC_TILE_T = 128;
+constexpr int TC_TILE_L = 512;
+constexpr int TC_BK = 64;
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 192;           // producer, MMA, 4 epilogue warps
+// SIMT FP32 path: one block tile is 64 templates x 256 lags, 32-sample chunks.
+constexpr int SIMT_TILE_T = 64;
+constexpr int SIMT_TILE_L = 256;
+constexpr int SIMT_BK = 32;
+constexpr int SIMT_THREADS = 256;
+
+constexpr int M_ALIGN = 64;               // template length padded to this
+constexpr int K_ALIGN = 128;              // bank size padded to this
+constexpr int MAX_SEG = 64;               // series (segments) per launch
+constexpr uint32_t TILE_BYTES_A = TC_TILE_T * TC_BK * 2;   // 16 KiB per k-block
+
+// device error codes written to the context's status word
+enum : int { DEV_OK = 0, DEV_TIMEOUT_FULL = 1, DEV_TIMEOUT_EMPTY = 2,
+             DEV_TIMEOUT_TMEM = 3, DEV_TMEM_ALLOC = 4 };
+
+struct Candidate {
+    uint32_t series;
+    uint32_t k;        // absolute bank index
+    uint32_t tau;
+    float rho;
+};
+
+// One series searched against a contiguous range of template tiles.
+struct Seg {
+    const float* x;                 // FP32 samples, zero padded (SIMT path)
+    const uint4* yhi;               // row w = bf16 hi parts of x[w .. w+7]
+    const uint4* ylo;               // row w = bf16 lo parts of x[w .. w+7]
+    const float* inv_norm;          // [L] 1 / |window|, 0 for empty windows
+    const float* bank_f32;          // [K_pad][M_pad]
+    const uint8_t* bank_hi;         // core-matrix tiles, see bank.cu
+    const uint8_t* bank_lo;
+    unsigned long long* vmax;       // packed max per template, index k - k_begin
+    double* sumsq;                  // sum of rho^2 per template
+    float* rho;                     // optional dense output [k - k_begin][tau]
+    uint64_t tile_begin;            // first global tile index of this segment
+    uint32_t L;                     // lags
+    uint32_t n_lag_tiles;
+    uint32_t tt0, n_tt;             // template tiles [tt0, tt0 + n_tt)
+    uint32_t k_begin, k_end;        // templates whose outputs are kept
+    uint32_t M_pad;
+    uint32_t series_id;
+};
+
+struct CorrParams {
+    int n_seg;
+    int pad0;
+    uint64_t total_tiles;
+    float thr;                      // candidate threshold on |rho|
+    unsigned int cand_cap;
+    Candidate* cand;
+    unsigned int* cand_count;
+    int* err;                       // device status word
+    Seg seg[MAX_SEG];
+};
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_corr_simt(const CorrParams& p, cudaStream_t s);
+cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int n_sm, cudaStream_t s);
+
+struct ChirpDev {                   // device copy of a template's parameters
+    int32_t track, sense;
+    double f_lo, f_hi, D;
+    double tc;                      // power-law t_c (0 for linear)
+    int32_t MD;                     // support length M_D
+    int32_t first;                  // m_s, first support sample of the
+                                    // ascending template
+};
+
+cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t K, uint32_t K_pad,
+                              uint32_t M, uint32_t M_pad, double fs, float* f32,
+                              uint8_t* hi, uint8_t* lo, cudaStream_t s);
+
+// series preparation: padded FP32 copy, split rows, FP64 prefix, inverse norms
+cudaError_t launch_split_rows(const float* x, uint64_t N, uint64_t rows, uint4* yhi,
+                              uint4* ylo, cudaStream_t s);
+cudaError_t launch_inv_norm(const float* x, uint64_t N, uint32_t M, double* prefix,
+                            double* block_scratch, uint64_t n_blocks_cap, float* inv,
+                            cudaStream_t s);
+uint64_t inv_norm_scratch_blocks(uint64_t N);
+
+struct FinalizeSeries {
+    const unsigned long long* packed;
+    const double* sumsq;
+    float* vmax;
+    int32_t* argmax;
+    float* sigma;
+    uint32_t* hist;
+    float* map;
+    uint32_t L;
+    uint32_t nt;
+};
+constexpr int MAX_FIN = 128;        // series per finalize / paint launch
+struct FinalizeParams {
+    uint32_t s0, n;                 // series [s0, s0 + n) of the result
+    FinalizeSeries ser[MAX_FIN];
+};
+cudaError_t launch_finalize(const FinalizeParams& p, uint32_t K, uint32_t nbins, cudaStream_t s);
+cudaError_t launch_mean_max(const float* vmax, uint32_t n_series, uint32_t K, float* mean,
+                            cudaStream_t s);
+cudaError_t launch_paint(const Candidate* cand, const unsigned int* count,
+                         unsigned int cap, const ChirpDev* params,
+                         const FinalizeParams& p, uint32_t M, double fs, double dt,
+                         double df, uint32_t nf, unsigned int n_sm, cudaStream_t s);
+
+// control randomisation
+size_t permute_scratch_bytes(uint64_t n);
+cudaError_t launch_permute(const float* in, uint64_t n, uint64_t seed, float* out,
+                           void* scratch, cudaStream_t s);
+
+// ---------------------------------------------------------------- host side
+void set_error(const char* fmt, ...);
+
+struct Allocator {
+    explicit Allocator(size_t budget) : budget_(budget) {}
+    ~Allocator();
+    void* alloc(size_t bytes);          // nullptr when over budget / OOM
+    void release(void* p);
+    void trim();
+    size_t in_use() const;
+    size_t budget() const { return budget_; }
+    bool fits(size_t bytes) const;
+
+  private:
+    size_t budget_;
+    size_t held_ = 0;                   // bytes obtained from cudaMalloc
+    size_t live_ = 0;                   // bytes handed out
+    std::multimap<size_t, void*> cache_;
+    std::unordered_map<void*, size_t> size_of_;
+    mutable std::mutex mu_;
+};
+
+struct ServeState;
+
+}  // namespace bfi
+
+struct bf_ctx {
+    int device = 0;
+    int n_sm = 0;
+    bf_config cfg{};
+    cudaStream_t stream = nullptr;
+    std::unique_ptr<bfi::Allocator> mem;
+    int* d_err = nullptr;               // kernel status word
+    std::mutex launch_mu;               // serialises use of d_err / stream
+    bfi::ServeState* serve = nullptr;   // owned; freed by serve_shutdown
+};
+
+struct bf_bank {
+    bf_ctx* ctx = nullptr;
+    size_t K = 0, K_pad = 0;
+    uint32_t M = 0, M_pad = 0;
+    double fs = 0, T = 0;
+    unsigned storage = 0;
+    std::vector<bf_chirp> params;
+    bfi::ChirpDev* d_params = nullptr;
+    float* f32 = nullptr;
+    uint8_t* hi = nullptr;
+    uint8_t* lo = nullptr;
+};
+
+struct bf_result {
+    bf_ctx* ctx = nullptr;
+    size_t n_series = 0, K = 0, k_begin = 0;
+    uint32_t M = 0, nbins = 0;
+    double fs = 0, dt = 0, df = 0;
+    bool want_map = false, want_hist = false;
+    std::vector<size_t> lengths;
+    std::vector<uint32_t> map_nt;
+    uint32_t map_nf = 0;
+    // device buffers (owned)
+    unsigned long long* packed = nullptr;   // [S][K]
+    double* sumsq = nullptr;                // [S][K]
+    float* vmax = nullptr;                  // [S][K]
+    int32_t* argmax = nullptr;              // [S][K]
+    float* sigma = nullptr;                 // [S][K]
+    uint32_t* hist = nullptr;               // [S][nbins]
+    float* map = nullptr;                   // concatenated per-series maps
+    std::vector<size_t> map_off;            // element offsets into map
+    float* mean_max = nullptr;              // [K]
+    bfi::Candidate* cand = nullptr;
+    unsigned int* cand_count = nullptr;
+    unsigned int cand_cap = 0;
+    uint64_t n_candidates = 0;
+    float thr = 0;
+    double correlations = 0;
+    double kernel_ms = 0;
+    std::vector<void*> scratch;             // released at destroy
+};

@@ -1,0 +1,426 @@
+// Tensor-core correlation (tcgen05, TMEM accumulators, bulk-async copies) with
+// the fused epilogue.  The sliding correlation of Sect. 2.1 is a dense
+// contraction C[k, tau] = sum_m h_k[m] x[tau + m]; here it runs as an implicit
+// GEMM with templates as the MMA M dimension (A operand, 128 per tile), lags
+// as N (B operand, two MMAs of N = 256 per tile) and template samples as K.
+//
+// The lag operand is a Hankel matrix, B[n][m] = x[lag0 + n + m].  It is never
+// materialised: the series is kept as overlapping "split rows" (row w = the
+// eight samples x[w .. w+7]; see prep.cu), so the 8x8 core matrix of lags
+// n0..n0+7 and samples m0..m0+7 is row block (lag0 + n0 + m0) .. +7, i.e. 128
+// contiguous bytes, and both descriptor strides (next 8 lags, next 8 samples)
+// are 128 B.  One bulk copy of 568 rows stages a whole 512-lag x 64-sample
+// block; the core matrices overlap in shared memory, which the MMA only reads.
+//
+// Precision: BF_BF16 issues one MMA (x_hi * h_hi); BF_SPLIT_BF16 issues three
+// into the same FP32 accumulator (x_hi h_hi + x_hi h_lo + x_lo h_hi), dropping
+// only x_lo h_lo (relative size 2^-16 or less).
+//
+// Warp roles (192 threads, one CTA per SM, persistent over tiles):
+//   warp 0  producer: bulk copies of template and series blocks per stage
+//   warp 1  allocates TMEM, one lane issues tcgen05.mma and commits
+//   warps 2-5 epilogue: tcgen05.ld of the 128 x 512 FP32 accumulator, each
+//            thread owning one template row: rho = C * inv_norm, running
+//            max/argmax (ties to the smallest lag), sum of rho^2, tails.
+// Every mbarrier wait is bounded in time; on expiry the kernel records an
+// error code in the status word, drains its own copies and MMAs, frees TMEM
+// and returns.
+#include "corr_common.cuh"
+
+namespace bfi {
+
+namespace {
+
+constexpr uint32_t B_ROWS = TC_TILE_L + TC_BK - 8;          // 568 rows per stage
+constexpr uint32_t B_BYTES = B_ROWS * 16;                    // 9088 B
+constexpr uint32_t A_BYTES = TILE_BYTES_A;                   // 16384 B
+constexpr uint32_t OFF_AHI = 0;
+constexpr uint32_t OFF_ALO = A_BYTES;
+constexpr uint32_t OFF_BHI = 2 * A_BYTES;
+constexpr uint32_t OFF_BLO = 2 * A_BYTES + B_BYTES;
+constexpr uint32_t STAGE_BYTES = 51200;                      // 50 KiB, 1 KiB aligned
+static_assert(OFF_BLO + B_BYTES <= STAGE_BYTES, "stage layout");
+constexpr uint32_t OFF_INV = TC_STAGES * STAGE_BYTES;        // 512 floats
+constexpr uint32_t OFF_BAR = OFF_INV + TC_TILE_L * 4;
+constexpr uint32_t N_BARS = 2 * TC_STAGES + 3;
+constexpr uint32_t SMEM_BYTES = OFF_BAR + N_BARS * 8 + 16 + 1024;   // + alignment slack
+constexpr uint64_t TIMEOUT_NS = 10ull * 1000 * 1000 * 1000;
+constexpr uint32_t TMEM_COLS = 512;
+
+// instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major,
+// N = 256, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
+                           ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait.  Returns false on timeout or when another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          volatile int* abort_flag, bool honour_abort = true)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (honour_abort && *abort_flag) return false;
+            if (globaltimer() - t0 > TIMEOUT_NS) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// shared-memory matrix descriptor, no swizzle, K-major
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;                     // descriptor version (tcgen05)
+    return d;                                   // base offset 0, no swizzle
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(IDESC), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// OR of a predicate over the 128 epilogue threads (named barrier 1)
+__device__ __forceinline__ bool epilogue_any(bool pred)
+{
+    uint32_t res;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(res)
+        : "r"((uint32_t)pred)
+        : "memory");
+    return res != 0;
+}
+
+__device__ __forceinline__ void record_error(int* err, int code)
+{
+    atomicCAS(err, 0, code);
+}
+
+struct TileCoord {
+    const Seg* s;
+    uint32_t tt, lag0;
+};
+
+__device__ __forceinline__ TileCoord tile_coord(const CorrParams& p, uint64_t t)
+{
+    const Seg* s = &p.seg[find_seg(p, t)];
+    const uint64_t local = t - s->tile_begin;
+    TileCoord c;
+    c.s = s;
+    c.tt = s->tt0 + (uint32_t)(local / s->n_lag_tiles);
+    c.lag0 = (uint32_t)(local % s->n_lag_tiles) * TC_TILE_L;
+    return c;
+}
+
+}  // namespace
+
+template <int NPROD>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant__ CorrParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    float* sh_inv = reinterpret_cast<float*>(sm + OFF_INV);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + N_BARS * 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + OFF_BAR + N_BARS * 8 + 4);
+
+    const uint32_t base = smem_u32(sm);
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_bar = [&](uint32_t st) { return bar0 + 8 * st; };
+    auto empty_bar = [&](uint32_t st) { return bar0 + 8 * (TC_STAGES + st); };
+    const uint32_t tfull_bar = bar0 + 8 * (2 * TC_STAGES);
+    const uint32_t tempty_bar = bar0 + 8 * (2 * TC_STAGES + 1);
+    const uint32_t drain_bar = bar0 + 8 * (2 * TC_STAGES + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (uint32_t st = 0; st < TC_STAGES; ++st) {
+            mbar_init(full_bar(st), 1);
+            mbar_init(empty_bar(st), 1);
+        }
+        mbar_init(tfull_bar, 1);
+        mbar_init(tempty_bar, 128);
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            uint32_t st = 0, ph = 0;
+            uint64_t issued = 0;
+            bool ok = true;
+            for (uint64_t t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
+                const TileCoord c = tile_coord(p, t);
+                const uint32_t n_kb = c.s->M_pad / TC_BK;
+                const uint8_t* a_hi = c.s->bank_hi + (size_t)c.tt * n_kb * A_BYTES;
+                const uint8_t* a_lo = c.s->bank_lo + (size_t)c.tt * n_kb * A_BYTES;
+                for (uint32_t kb = 0; kb < n_kb; ++kb) {
+                    if (!mbar_wait(empty_bar(st), ph ^ 1, abort_flag)) {
+                        if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_EMPTY);
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sbase = base + st * STAGE_BYTES;
+                    const uint32_t bytes = NPROD == 3 ? 2 * (A_BYTES + B_BYTES) : A_BYTES + B_BYTES;
+                    mbar_expect_tx(full_bar(st), bytes);
+                    const uint64_t w0 = (uint64_t)c.lag0 + (uint64_t)kb * TC_BK;
+                    bulk_g2s(sbase + OFF_AHI, a_hi + (size_t)kb * A_BYTES, A_BYTES, full_bar(st));
+                    bulk_g2s(sbase + OFF_BHI, c.s->yhi + w0, B_BYTES, full_bar(st));
+                    if (NPROD == 3) {
+                        bulk_g2s(sbase + OFF_ALO, a_lo + (size_t)kb * A_BYTES, A_BYTES, full_bar(st));
+                        bulk_g2s(sbase + OFF_BLO, c.s->ylo + w0, B_BYTES, full_bar(st));
+                    }
+                    ++issued;
+                    if (++st == TC_STAGES) { st = 0; ph ^= 1; }
+                }
+            }
+            if (!ok) {
+                // let copies already in flight land before shared memory is released
+                uint64_t first = issued > TC_STAGES ? issued - TC_STAGES : 0;
+                for (uint64_t i = first; i < issued; ++i)
+                    mbar_wait(full_bar((uint32_t)(i % TC_STAGES)), (uint32_t)((i / TC_STAGES) & 1),
+                              abort_flag, false);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t st = 0, ph = 0, tph = 0;
+            bool ok = true;
+            for (uint64_t t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
+                const TileCoord c = tile_coord(p, t);
+                const uint32_t n_kb = c.s->M_pad / TC_BK;
+                if (!mbar_wait(tempty_bar, tph ^ 1, abort_flag)) {
+                    if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_TMEM);
+                    *abort_flag = 1;
+                    break;
+                }
+                fence_after();
+                for (uint32_t kb = 0; kb < n_kb; ++kb) {
+                    if (!mbar_wait(full_bar(st), ph, abort_flag)) {
+                        if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_FULL);
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t sbase = base + st * STAGE_BYTES;
+#pragma unroll
+                    for (uint32_t kk = 0; kk < TC_BK / 16; ++kk) {
+                        const uint64_t ahi = make_desc(sbase + OFF_AHI + kk * 256, 128, 1024);
+                        const uint64_t alo = make_desc(sbase + OFF_ALO + kk * 256, 128, 1024);
+#pragma unroll
+                        for (uint32_t h = 0; h < 2; ++h) {
+                            const uint32_t boff = h * 256 * 16 + kk * 256;
+                            const uint64_t bhi = make_desc(sbase + OFF_BHI + boff, 128, 128);
+                            const uint64_t blo = make_desc(sbase + OFF_BLO + boff, 128, 128);
+                            const uint32_t d = tmem + h * 256;
+                            mma_f16(d, ahi, bhi, (kb | kk) != 0);
+                            if (NPROD == 3) {
+                                mma_f16(d, ahi, blo, 1);
+                                mma_f16(d, alo, bhi, 1);
+                            }
+                        }
+                    }
+                    mma_commit(empty_bar(st));
+                    if (++st == TC_STAGES) { st = 0; ph ^= 1; }
+                }
+                if (!ok) break;
+                mma_commit(tfull_bar);
+                tph ^= 1;
+            }
+            // drain: every MMA issued by this thread completes before TMEM is freed
+            mma_commit(drain_bar);
+            mbar_wait(drain_bar, 0, abort_flag, false);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const uint32_t q = warp & 3;                       // TMEM lane quadrant
+        const uint32_t row = q * 32 + lane;                // template row of the tile
+        const uint32_t e = threadIdx.x - 64;               // 0..127
+        uint32_t tph = 0;
+        for (uint64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
+            const TileCoord c = tile_coord(p, t);
+            const Seg& s = *c.s;
+            const uint32_t nvalid = min((uint32_t)TC_TILE_L, s.L - c.lag0);
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+#pragma unroll
+            for (uint32_t i = 0; i < 4; ++i) {
+                uint32_t j = 4 * e + i;
+                sh_inv[j] = j < nvalid ? s.inv_norm[c.lag0 + j] : 0.f;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const bool ok = mbar_wait(tfull_bar, tph, abort_flag);
+            if (epilogue_any(!ok)) {       // all epilogue threads leave together
+                if (!ok && !*abort_flag) record_error(p.err, DEV_TIMEOUT_TMEM);
+                *abort_flag = 1;
+                break;
+            }
+            fence_after();
+            const uint32_t k = c.tt * TC_TILE_T + row;
+            const bool keep = k >= s.k_begin && k < s.k_end;
+            unsigned long long best = 0ull;
+            float ss = 0.f;
+            const uint32_t taddr = tmem + ((q * 32) << 16);
+#pragma unroll 1
+            for (uint32_t c0 = 0; c0 < TC_TILE_L; c0 += 32) {
+                uint32_t r[32];
+                __syncwarp();
+                tmem_ld32(taddr + c0, r);
+                if (c0 < nvalid) {
+#pragma unroll
+                    for (uint32_t j = 0; j < 32; ++j) {
+                        if (c0 + j < nvalid) {
+                            const float v = __uint_as_float(r[j]) * sh_inv[c0 + j];
+                            const float av = fabsf(v);
+                            if (s.rho && keep) s.rho[(size_t)(k - s.k_begin) * s.L + c.lag0 + c0 + j] = v;
+                            const unsigned long long key = pack_max(av, c.lag0 + c0 + j);
+                            best = key > best ? key : best;
+                            ss = fmaf(v, v, ss);
+                            if (keep && av >= p.thr)
+                                push_candidate(p, s.series_id, k, c.lag0 + c0 + j, v);
+                        }
+                    }
+                }
+            }
+            fence_before();
+            mbar_arrive(tempty_bar);
+            tph ^= 1;
+            if (keep) {
+                atomicMax(s.vmax + (k - s.k_begin), best);
+                atomicAdd(s.sumsq + (k - s.k_begin), (double)ss);
+            }
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int n_sm, cudaStream_t st)
+{
+    if (p.total_tiles == 0) return cudaSuccess;
+    static bool attr_done[2] = {false, false};
+    const int which = nprod == 3 ? 1 : 0;
+    auto kern = nprod == 3 ? k_corr_tc<3> : k_corr_tc<1>;
+    if (!attr_done[which]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_done[which] = true;
+    }
+    uint64_t grid = p.total_tiles < (uint64_t)n_sm ? p.total_tiles : (uint64_t)n_sm;
+    kern<<<(unsigned)grid, TC_THREADS, SMEM_BYTES, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace bfi

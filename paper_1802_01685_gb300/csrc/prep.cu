@@ -1,0 +1,167 @@
+// Series preparation on the device.
+//
+// (1) Split rows for the tensor-core path.  Row w holds the eight samples
+//     x[w .. w+7] rounded to bf16 (hi) and the bf16 rounding of the remainder
+//     x - hi (lo; x - hi is exact in FP32).  Consecutive rows overlap by seven
+//     samples, so the 8-row x 8-sample core matrix that starts at row w is the
+//     Hankel block x[w + i + c] (i, c < 8) stored as 128 contiguous bytes: the
+//     correlation kernel feeds it to tcgen05.mma as the lag operand with 16-byte
+//     row pitch and no gather.  Rows past the series read zeros.
+// (2) Inverse window norms.  S[n] = sum_{i<n} x[i]^2 in FP64 (every x^2 of an
+//     FP32 sample is exact in FP64), nu(tau) = S[tau+M] - S[tau], and
+//     inv(tau) = 1 / sqrt(nu) rounded to FP32, 0 where nu == 0 (an all-zero
+//     window: the prefix is then constant, so the difference is exactly 0).
+#include "bf_internal.h"
+
+namespace bfi {
+
+__global__ void k_split_rows(const float* __restrict__ x, uint64_t N, uint64_t rows,
+                             uint4* __restrict__ yhi, uint4* __restrict__ ylo)
+{
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < rows;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int c = 0; c < 8; c += 2) {
+            float v0 = (w + c < N) ? x[w + c] : 0.f;
+            float v1 = (w + c + 1 < N) ? x[w + c + 1] : 0.f;
+            __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+            __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+            __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+            h[c / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            l[c / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        yhi[w] = make_uint4(h[0], h[1], h[2], h[3]);
+        ylo[w] = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+cudaError_t launch_split_rows(const float* x, uint64_t N, uint64_t rows, uint4* yhi, uint4* ylo,
+                              cudaStream_t s)
+{
+    uint64_t blocks = (rows + 255) / 256;
+    if (blocks > 65535ull * 16) blocks = 65535ull * 16;
+    if (blocks == 0) blocks = 1;
+    k_split_rows<<<(unsigned)blocks, 256, 0, s>>>(x, N, rows, yhi, ylo);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- FP64 scan
+constexpr int SCAN_T = 512;              // threads per scan block
+constexpr int SCAN_E = 4;                // elements per thread
+constexpr int SCAN_B = SCAN_T * SCAN_E;  // elements per block
+
+uint64_t inv_norm_scratch_blocks(uint64_t N) { return (N + SCAN_B - 1) / SCAN_B + 1; }
+
+__device__ __forceinline__ double block_excl_scan(double v, double* sh, double* total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        double t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) sh[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        double s = lane < (SCAN_T / 32) ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            double t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane < SCAN_T / 32) sh[lane] = s;
+    }
+    __syncthreads();
+    double base = wid > 0 ? sh[wid - 1] : 0.0;
+    if (total) *total = sh[SCAN_T / 32 - 1];
+    return base + inc - v;
+}
+
+// per-block sums of x^2
+__global__ void __launch_bounds__(SCAN_T) k_block_sq(const float* __restrict__ x, uint64_t N,
+                                                     double* __restrict__ bsum)
+{
+    __shared__ double sh[SCAN_T / 32];
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_B + (uint64_t)threadIdx.x * SCAN_E;
+    double v = 0.0;
+#pragma unroll
+    for (int e = 0; e < SCAN_E; ++e)
+        if (base + e < N) {
+            double d = x[base + e];
+            v += d * d;
+        }
+    double tot;
+    block_excl_scan(v, sh, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// exclusive scan of the block sums by one block (loops over chunks)
+__global__ void __launch_bounds__(SCAN_T) k_scan_sums(double* __restrict__ bsum, uint64_t n)
+{
+    __shared__ double sh[SCAN_T / 32];
+    double carry = 0.0;
+    for (uint64_t c = 0; c < n; c += SCAN_T) {
+        uint64_t i = c + threadIdx.x;
+        double v = i < n ? bsum[i] : 0.0;
+        double tot;
+        double ex = block_excl_scan(v, sh, &tot);
+        __syncthreads();
+        if (i < n) bsum[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+// S[n] for n = 0..N (inclusive prefix shifted by one)
+__global__ void __launch_bounds__(SCAN_T) k_prefix(const float* __restrict__ x, uint64_t N,
+                                                   const double* __restrict__ boff,
+                                                   double* __restrict__ S)
+{
+    __shared__ double sh[SCAN_T / 32];
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_B + (uint64_t)threadIdx.x * SCAN_E;
+    double v[SCAN_E];
+    double t = 0.0;
+#pragma unroll
+    for (int e = 0; e < SCAN_E; ++e) {
+        double d = base + e < N ? (double)x[base + e] : 0.0;
+        v[e] = d * d;
+        t += v[e];
+    }
+    double ex = block_excl_scan(t, sh, nullptr) + boff[blockIdx.x];
+    if (blockIdx.x == 0 && threadIdx.x == 0) S[0] = 0.0;
+#pragma unroll
+    for (int e = 0; e < SCAN_E; ++e) {
+        ex += v[e];
+        if (base + e < N) S[base + e + 1] = ex;
+    }
+}
+
+__global__ void k_inv_norm(const double* __restrict__ S, uint64_t L, uint32_t M,
+                           float* __restrict__ inv)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < L;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        double nu = S[t + M] - S[t];
+        inv[t] = nu > 0.0 ? (float)(1.0 / sqrt(nu)) : 0.f;
+    }
+}
+
+cudaError_t launch_inv_norm(const float* x, uint64_t N, uint32_t M, double* prefix,
+                            double* block_scratch, uint64_t n_blocks_cap, float* inv,
+                            cudaStream_t s)
+{
+    uint64_t nb = (N + SCAN_B - 1) / SCAN_B;
+    if (nb == 0 || nb + 1 > n_blocks_cap || N < M) return cudaErrorInvalidValue;
+    k_block_sq<<<(unsigned)nb, SCAN_T, 0, s>>>(x, N, block_scratch);
+    k_scan_sums<<<1, SCAN_T, 0, s>>>(block_scratch, nb);
+    k_prefix<<<(unsigned)nb, SCAN_T, 0, s>>>(x, N, block_scratch, prefix);
+    uint64_t L = N - M + 1;
+    uint64_t blocks = (L + 255) / 256;
+    if (blocks > 65535ull * 16) blocks = 65535ull * 16;
+    k_inv_norm<<<(unsigned)blocks, 256, 0, s>>>(prefix, L, M, inv);
+    return cudaGetLastError();
+}
+
+}  // namespace bfi

@@ -1,0 +1,52 @@
+// Host runtime pieces shared by the C ABI (api.cu) and the serving scheduler
+// (serve.cu): series preparation, segment building, launches, results.
+#pragma once
+#include "bf_internal.h"
+
+namespace bfi {
+
+bf_status cuda_fail(cudaError_t e, const char* what);
+uint32_t template_len(double T, double fs);
+void map_shape(size_t N, double fs, double dt, double df, uint32_t* nt, uint32_t* nf);
+
+// A series resident on the device in the layouts the kernels read.
+struct PreparedSeries {
+    size_t N = 0;
+    uint32_t L = 0;
+    float* x = nullptr;             // padded FP32 samples
+    float* inv = nullptr;           // [L] inverse window norms
+    uint4* yhi = nullptr;           // split rows (tensor-core path)
+    uint4* ylo = nullptr;
+    std::vector<void*> owned;       // every buffer, prefix scratch included
+    void release(Allocator& mem);
+};
+
+bf_status prepare_series(bf_ctx* ctx, const float* src, size_t N, uint32_t M, uint32_t M_pad,
+                         int precision, cudaStream_t st, PreparedSeries* out);
+size_t prepared_series_bytes(size_t N, uint32_t M, uint32_t M_pad, int precision);
+
+// Template-tile geometry of a precision's kernel.
+inline uint32_t tile_templates(int precision) { return precision == BF_FP32 ? SIMT_TILE_T : TC_TILE_T; }
+inline uint32_t tile_lags(int precision) { return precision == BF_FP32 ? SIMT_TILE_L : TC_TILE_L; }
+
+// One segment: series `ps` (result slot series_id) against template tiles
+// [tt_first, tt_first + tt_count), keeping outputs of templates [k_begin, k_end).
+Seg make_segment(const PreparedSeries& ps, uint32_t series_id, const bf_bank* bank, size_t k_begin,
+                 size_t k_end, uint32_t tt_first, uint32_t tt_count, int precision,
+                 unsigned long long* packed_s, double* sumsq_s, float* rho = nullptr);
+
+cudaError_t launch_segments(bf_ctx* ctx, const std::vector<Seg>& segs, int precision, float thr,
+                            Candidate* cand, unsigned int* cand_count, unsigned int cand_cap,
+                            cudaStream_t st, uint64_t* tiles_out);
+
+bf_status resolve_opts(const bf_bank* bank, const bf_opts* in, bf_opts* o);
+bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
+                       const std::vector<size_t>& lengths, double fs, cudaStream_t st,
+                       bf_result** out);
+size_t result_bytes(const bf_bank* bank, const bf_opts& o, size_t N, double fs, size_t max_cand);
+bf_status finalize_result(bf_ctx* ctx, const bf_bank* bank, bf_result* r, cudaStream_t st);
+bf_status check_device_status(bf_ctx* ctx);
+
+void serve_shutdown(bf_ctx* ctx);
+
+}  // namespace bfi

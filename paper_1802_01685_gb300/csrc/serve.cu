@@ -1,0 +1,463 @@
+// Serving with continuous batching.
+//
+// Requests (one series against a slice of a bank) are submitted from any
+// thread.  One scheduler thread per context admits queued requests while a
+// slot is free and the HBM budget holds their series and result buffers,
+// uploads and prepares each admitted series once, and then drives the device
+// in iterations: every iteration launches the batched correlation kernel over
+// a chunk of template tiles from EVERY admitted request (one segment per
+// request), so a request arriving while others run joins the next iteration
+// instead of waiting for them to finish.  When a request's last chunk has been
+// launched its finalize kernels follow on the same stream; its completion
+// event then releases the slot and its memory.  Requests of different
+// precisions go to separate launches of the matching kernel.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "runtime.h"
+
+namespace bfi {
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+double now_s()
+{
+    return std::chrono::duration<double>(clk::now().time_since_epoch()).count();
+}
+
+enum RState { R_QUEUED, R_ACTIVE, R_DONE, R_CANCELED, R_FAILED };
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<float> host;        // copy of the series
+    double fs = 0;
+    const bf_bank* bank = nullptr;
+    bf_opts opts{};
+    RState state = R_QUEUED;
+    bf_status status = BF_OK;
+    std::string error;
+    bool cancel = false;
+    bf_result* result = nullptr;
+    PreparedSeries prep;
+    uint32_t tt_next = 0, tt_end = 0;   // template-tile cursor
+    uint32_t n_lag_tiles = 0;
+    bool finalized = false;
+    cudaEvent_t done = nullptr;
+    size_t bytes = 0;
+    double t_submit = 0, t_done = 0;
+    double correlations = 0;
+};
+
+// tiles per SM per iteration: large enough to amortise the launch, small
+// enough that new arrivals join within a few milliseconds
+constexpr uint64_t TILES_PER_SM = 8;
+
+}  // namespace
+
+struct ServeState {
+    bf_ctx* ctx = nullptr;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> queue;
+    std::vector<Request*> active;
+    std::unordered_map<uint64_t, Request*> all;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    bool started = false;
+    cudaStream_t stream = nullptr;
+    // statistics
+    uint64_t submitted = 0, completed = 0, cancelled = 0, rejected = 0, launches = 0;
+    std::vector<double> latency_ms;
+    double corr_done = 0, busy_s = 0, busy_since = -1;
+
+    ~ServeState() = default;
+};
+
+static void release_request_device(bf_ctx* ctx, Request* r)
+{
+    r->prep.release(*ctx->mem);
+    if (r->done) {
+        cudaEventDestroy(r->done);
+        r->done = nullptr;
+    }
+}
+
+// Admission: allocate the result, upload and prepare the series.
+static bool admit(ServeState* S, Request* r)
+{
+    bf_ctx* ctx = S->ctx;
+    const bf_bank* bank = r->bank;
+    std::vector<size_t> len{r->host.size()};
+    bf_result* res = nullptr;
+    bf_status st = alloc_result(ctx, bank, r->opts, len, r->fs, S->stream, &res);
+    if (st == BF_OK) {
+        st = prepare_series(ctx, r->host.data(), r->host.size(), bank->M, bank->M_pad,
+                            r->opts.precision, S->stream, &r->prep);
+        if (st != BF_OK) bf_result_destroy(res);
+    }
+    if (st != BF_OK) {
+        r->status = st;
+        r->error = bf_last_error();
+        return false;
+    }
+    r->result = res;
+    const uint32_t tile_t = tile_templates(r->opts.precision);
+    r->tt_next = (uint32_t)(r->opts.bank_begin / tile_t);
+    r->tt_end = (uint32_t)((r->opts.bank_end + tile_t - 1) / tile_t);
+    r->n_lag_tiles = (r->prep.L + tile_lags(r->opts.precision) - 1) / tile_lags(r->opts.precision);
+    r->correlations = (double)r->prep.L * (double)(r->opts.bank_end - r->opts.bank_begin);
+    res->correlations = r->correlations;
+    cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
+    r->state = R_ACTIVE;
+    return true;
+}
+
+static void scheduler(ServeState* S)
+{
+    bf_ctx* ctx = S->ctx;
+    cudaSetDevice(ctx->device);
+    cudaEvent_t prev = nullptr, cur = nullptr;
+    cudaEventCreateWithFlags(&prev, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&cur, cudaEventDisableTiming);
+    bool prev_valid = false;
+
+    for (;;) {
+        std::vector<Request*> act;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->active.empty(); });
+            if (S->stop) break;
+            // admission, in arrival order, while a slot and the budget allow
+            while (!S->queue.empty() && (int)S->active.size() < ctx->cfg.serve_slots) {
+                Request* r = S->queue.front();
+                if (r->cancel) {
+                    S->queue.pop_front();
+                    r->state = R_CANCELED;
+                    ++S->cancelled;
+                    S->cv_done.notify_all();
+                    continue;
+                }
+                if (!ctx->mem->fits(r->bytes) && !S->active.empty()) break;
+                S->queue.pop_front();
+                lk.unlock();
+                const bool ok = admit(S, r);
+                lk.lock();
+                if (!ok) {
+                    r->state = R_FAILED;
+                    ++S->rejected;
+                    S->cv_done.notify_all();
+                    continue;
+                }
+                if (S->busy_since < 0) S->busy_since = now_s();
+                S->active.push_back(r);
+            }
+            act = S->active;
+        }
+
+        // one iteration: a chunk of template tiles of every admitted request
+        std::vector<std::pair<Request*, Seg>> segs[3];
+        std::vector<Request*> finishing;
+        uint64_t n_work = 0;
+        for (Request* r : act)
+            if (!r->cancel && r->tt_next < r->tt_end) ++n_work;
+        const uint64_t budget = (uint64_t)ctx->n_sm * TILES_PER_SM;
+        for (Request* r : act) {
+            if (r->cancel || r->tt_next >= r->tt_end) continue;
+            uint64_t per = std::max<uint64_t>(1, budget / std::max<uint64_t>(1, n_work));
+            uint64_t ntt = std::max<uint64_t>(1, per / std::max<uint32_t>(1, r->n_lag_tiles));
+            ntt = std::min<uint64_t>(ntt, r->tt_end - r->tt_next);
+            bf_result* res = r->result;
+            segs[r->opts.precision].emplace_back(
+                r, make_segment(r->prep, 0, r->bank, r->opts.bank_begin, r->opts.bank_end,
+                                r->tt_next, (uint32_t)ntt, r->opts.precision, res->packed,
+                                res->sumsq));
+            r->tt_next += (uint32_t)ntt;
+            if (r->tt_next >= r->tt_end) finishing.push_back(r);
+        }
+        // Requests without a map share one launch per precision (tails are not
+        // collected); a request with a map owns the candidate buffer its
+        // segment writes, so it gets a launch of its own in the same iteration.
+        bool any = false;
+        for (int prec = 0; prec < 3; ++prec) {
+            if (segs[prec].empty()) continue;
+            std::vector<Seg> shared;
+            std::vector<Request*> shared_owner;
+            for (auto& rs : segs[prec]) {
+                Request* r = rs.first;
+                if (r->result->want_map) {
+                    std::vector<Seg> one{rs.second};
+                    cudaError_t e = launch_segments(ctx, one, prec, r->result->thr, r->result->cand,
+                                                    r->result->cand_count, r->result->cand_cap,
+                                                    S->stream, nullptr);
+                    if (e != cudaSuccess) { r->status = cuda_fail(e, "serve launch"); r->cancel = true; }
+                } else {
+                    shared.push_back(rs.second);
+                    shared_owner.push_back(r);
+                }
+            }
+            if (!shared.empty()) {
+                bf_result* r0 = shared_owner[0]->result;
+                cudaError_t e = launch_segments(ctx, shared, prec, INFINITY, r0->cand, r0->cand_count,
+                                                0, S->stream, nullptr);
+                if (e != cudaSuccess)
+                    for (Request* r : shared_owner) { r->status = cuda_fail(e, "serve launch"); r->cancel = true; }
+            }
+            any = true;
+        }
+        for (Request* r : finishing) {
+            if (r->status == BF_OK && finalize_result(ctx, r->bank, r->result, S->stream) != BF_OK)
+                r->status = BF_ECUDA;
+            cudaEventRecord(r->done, S->stream);
+            r->finalized = true;
+        }
+        if (any) {
+            cudaEventRecord(cur, S->stream);
+            std::swap(prev, cur);
+            // keep at most two iterations in flight: wait for the one before
+            if (prev_valid) cudaEventSynchronize(cur);
+            prev_valid = true;
+            std::lock_guard<std::mutex> g(S->mu);
+            ++S->launches;
+        }
+
+        // completions and cancellations
+        {
+            std::vector<Request*> done_now;
+            for (Request* r : act) {
+                if (r->finalized && cudaEventQuery(r->done) == cudaSuccess) done_now.push_back(r);
+                else if (r->cancel && !r->finalized) {
+                    cudaStreamSynchronize(S->stream);
+                    done_now.push_back(r);
+                }
+            }
+            if (!any && done_now.empty() && !act.empty()) {
+                // nothing launched: wait for outstanding work rather than spin
+                cudaStreamSynchronize(S->stream);
+                continue;
+            }
+            if (!done_now.empty()) {
+                // a kernel that gave up on a wait marks every request it served
+                const bf_status dev = check_device_status(ctx);
+                std::lock_guard<std::mutex> g(S->mu);
+                const double t = now_s();
+                for (Request* r : done_now) {
+                    S->active.erase(std::find(S->active.begin(), S->active.end(), r));
+                    release_request_device(ctx, r);
+                    if (r->cancel && r->status == BF_OK) {
+                        bf_result_destroy(r->result);
+                        r->result = nullptr;
+                        r->state = R_CANCELED;
+                        ++S->cancelled;
+                    } else if (r->status != BF_OK || dev != BF_OK) {
+                        bf_result_destroy(r->result);
+                        r->result = nullptr;
+                        r->state = R_FAILED;
+                    } else {
+                        unsigned int c = 0;
+                        cudaMemcpy(&c, r->result->cand_count, sizeof c, cudaMemcpyDeviceToHost);
+                        r->result->n_candidates = c;
+                        r->state = R_DONE;
+                        r->t_done = t;
+                        ++S->completed;
+                        S->latency_ms.push_back(1e3 * (t - r->t_submit));
+                        S->corr_done += r->correlations;
+                    }
+                }
+                if (S->active.empty() && S->busy_since >= 0) {
+                    S->busy_s += t - S->busy_since;
+                    S->busy_since = S->queue.empty() ? -1 : t;
+                }
+                S->cv_done.notify_all();
+            }
+        }
+    }
+    cudaStreamSynchronize(S->stream);
+    cudaEventDestroy(prev);
+    cudaEventDestroy(cur);
+}
+
+static bf_status ensure_started(bf_ctx* ctx)
+{
+    if (!ctx->serve) {
+        ctx->serve = new ServeState();
+        ctx->serve->ctx = ctx;
+    }
+    ServeState* S = ctx->serve;
+    if (!S->started) {
+        cudaSetDevice(ctx->device);
+        cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "serve stream");
+        S->th = std::thread(scheduler, S);
+        S->started = true;
+    }
+    return BF_OK;
+}
+
+void serve_shutdown(bf_ctx* ctx)
+{
+    if (!ctx->serve) return;
+    ServeState* S = ctx->serve;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->th.joinable()) S->th.join();
+    for (auto& kv : S->all) {
+        Request* r = kv.second;
+        release_request_device(ctx, r);
+        if (r->result) bf_result_destroy(r->result);
+        delete r;
+    }
+    S->all.clear();
+    if (S->stream) cudaStreamDestroy(S->stream);
+    delete S;
+    ctx->serve = nullptr;
+}
+
+}  // namespace bfi
+
+using namespace bfi;
+
+extern "C" {
+
+bf_status bf_serve_submit(bf_ctx* ctx, const bf_request* req, uint64_t* ticket)
+{
+    if (!ctx || !req || !ticket || !req->series || !req->bank) {
+        set_error("NULL argument");
+        return BF_EINVAL;
+    }
+    const bf_bank* bank = req->bank;
+    if (bank->ctx != ctx) { set_error("bank belongs to another context"); return BF_EINVAL; }
+    if (std::fabs(req->fs - bank->fs) > 1e-9 * bank->fs) {
+        set_error("request rate %g differs from the bank's %g", req->fs, bank->fs);
+        return BF_EINVAL;
+    }
+    if (req->n < bank->M || req->n > 0xFFFFFFF0ull) {
+        set_error("request series of %zu samples; need M=%u <= N", req->n, bank->M);
+        return BF_EINVAL;
+    }
+    bf_opts o;
+    bf_status st = resolve_opts(bank, &req->opts, &o);
+    if (st) return st;
+    o.stream = nullptr;
+    std::unique_ptr<Request> r(new Request());
+    r->host.resize(req->n);
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMemcpy(r->host.data(), req->series, req->n * 4, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "copying the request series");
+    r->fs = req->fs;
+    r->bank = bank;
+    r->opts = o;
+    r->bytes = prepared_series_bytes(req->n, bank->M, bank->M_pad, o.precision) +
+               result_bytes(bank, o, req->n, req->fs, ctx->cfg.max_candidates);
+    if (r->bytes > ctx->mem->budget()) {
+        set_error("request needs %zu bytes, over the budget of %zu", r->bytes, ctx->mem->budget());
+        return BF_ENOMEM;
+    }
+    {
+        std::lock_guard<std::mutex> g(ctx->launch_mu);
+        st = ensure_started(ctx);
+        if (st) return st;
+    }
+    ServeState* S = ctx->serve;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if ((int)S->queue.size() >= ctx->cfg.serve_queue) {
+            set_error("serving queue full (%d)", ctx->cfg.serve_queue);
+            return BF_EAGAIN;
+        }
+        r->ticket = S->next_ticket++;
+        r->t_submit = now_s();
+        *ticket = r->ticket;
+        S->all[r->ticket] = r.get();
+        S->queue.push_back(r.release());
+        ++S->submitted;
+    }
+    S->cv_work.notify_all();
+    return BF_OK;
+}
+
+bf_status bf_serve_poll(bf_ctx* ctx, uint64_t ticket, int64_t timeout_us, bf_result** out)
+{
+    if (!ctx || !out) { set_error("NULL argument"); return BF_EINVAL; }
+    *out = nullptr;
+    if (!ctx->serve) { set_error("unknown ticket %llu", (unsigned long long)ticket); return BF_EINVAL; }
+    ServeState* S = ctx->serve;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) { set_error("unknown ticket %llu", (unsigned long long)ticket); return BF_EINVAL; }
+    Request* r = it->second;
+    auto finished = [&] { return r->state == R_DONE || r->state == R_CANCELED || r->state == R_FAILED; };
+    if (!finished()) {
+        if (timeout_us == 0) return BF_EPENDING;
+        if (timeout_us < 0) S->cv_done.wait(lk, finished);
+        else if (!S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), finished)) {
+            set_error("request %llu still running", (unsigned long long)ticket);
+            return BF_ETIMEDOUT;
+        }
+    }
+    S->all.erase(it);
+    bf_status st = BF_OK;
+    if (r->state == R_DONE) {
+        *out = r->result;
+    } else if (r->state == R_CANCELED) {
+        st = BF_ECANCELED;
+        set_error("request %llu was cancelled", (unsigned long long)ticket);
+    } else {
+        st = r->status != BF_OK ? r->status : BF_ECUDA;
+        set_error("%s", r->error.empty() ? "request failed" : r->error.c_str());
+    }
+    delete r;
+    return st;
+}
+
+bf_status bf_serve_cancel(bf_ctx* ctx, uint64_t ticket)
+{
+    if (!ctx || !ctx->serve) { set_error("unknown ticket"); return BF_EINVAL; }
+    ServeState* S = ctx->serve;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) { set_error("unknown ticket"); return BF_EINVAL; }
+    Request* r = it->second;
+    if (r->state == R_QUEUED || r->state == R_ACTIVE) r->cancel = true;
+    S->cv_work.notify_all();
+    return BF_OK;
+}
+
+bf_status bf_serve_stats_get(bf_ctx* ctx, bf_serve_stats* out)
+{
+    if (!ctx || !out) { set_error("NULL argument"); return BF_EINVAL; }
+    memset(out, 0, sizeof *out);
+    out->hbm_in_use = ctx->mem->in_use();
+    if (!ctx->serve) return BF_OK;
+    ServeState* S = ctx->serve;
+    std::lock_guard<std::mutex> g(S->mu);
+    out->submitted = S->submitted;
+    out->completed = S->completed;
+    out->cancelled = S->cancelled;
+    out->rejected = S->rejected;
+    out->queued = S->queue.size();
+    out->active = S->active.size();
+    out->launches = S->launches;
+    if (!S->latency_ms.empty()) {
+        std::vector<double> v = S->latency_ms;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) {
+            size_t i = (size_t)std::ceil(q * (double)v.size()) - 1;
+            return v[std::min(i, v.size() - 1)];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+    }
+    double busy = S->busy_s + (S->busy_since >= 0 ? now_s() - S->busy_since : 0.0);
+    out->correlations_per_s = busy > 0 ? S->corr_done / busy : 0.0;
+    return BF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs, element by element."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_01685_gb300 import bf, synth
+
+from parity import (TOL, check_hist, check_map, check_maxima, check_sigma, oracle_params, run,
+                    subset)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    h = bf.bf_init()
+    yield h
+    bf.bf_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def tiny(ctx):
+    w = synth.tiny(seed=1)
+    fs, M = w["fs"], w["M"]
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, M / fs)
+    p = oracle_params(w["grid"])
+    ref = oracle.search(w["series"][0], fs, p, M, want_rho=True)
+    yield w, bank, p, ref
+    bf.bf_bank_destroy(bank)
+
+
+# ------------------------------------------------------------------ bank
+
+def test_bank_templates_match_oracle(ctx):
+    chirps = [(bf.BF_LINEAR, bf.BF_ASC, 50.0, 1000.0, 1.0), (bf.BF_LINEAR, bf.BF_DESC, 600.0, 700.0, 0.2),
+              (bf.BF_POWERLAW, bf.BF_ASC, 20.0, 1000.0, 0.2), (bf.BF_POWERLAW, bf.BF_DESC, 40.0, 400.0, 1.0),
+              (bf.BF_POWERLAW, bf.BF_ASC, 999.0, 1000.0, 0.55), (bf.BF_LINEAR, bf.BF_ASC, 1.0, 2.0, 0.37)]
+    fs, T = 2048.0, 1.0
+    for storage in (bf.BF_BANK_FP32, bf.BF_BANK_SPLIT_BF16):
+        bank = bf.bf_bank_create(ctx, chirps, fs, T, storage)
+        got = bf.bf_bank_read(bank, 0, len(chirps))
+        for k, c in enumerate(chirps):
+            ref = oracle.template(c[0], c[1], c[2], c[3], c[4], fs, 2048)
+            err = np.abs(got[k] - ref).max()
+            assert err < 1e-6, (storage, k, err)
+        assert bf.bf_bank_params(bank, 1, 1)[0] == chirps[1]
+        bf.bf_bank_destroy(bank)
+
+
+def test_bank_grid_matches_oracle_grid(ctx):
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC],
+                           [0.2, 0.6, 1.0], 20.0, 1000.0, 3, 5)
+    bank = bf.bf_bank_create_grid(ctx, spec, 2048.0, 1.0, bf.BF_BANK_FP32)
+    p = oracle_params(spec)
+    K = bf.bf_bank_size(bank)
+    assert K == len(p["track"]) == synth.grid_size(spec)
+    got = bf.bf_bank_params(bank, 0, K)
+    for k in range(K):
+        assert got[k] == (p["track"][k], p["sense"][k], p["f_lo"][k], p["f_hi"][k], p["D"][k])
+    bf.bf_bank_destroy(bank)
+
+
+def test_bank_rejects_invalid_chirps(ctx):
+    for bad in [(bf.BF_LINEAR, bf.BF_ASC, 50.0, 1024.0, 1.0),
+                (bf.BF_LINEAR, bf.BF_ASC, 0.0, 100.0, 1.0),
+                (bf.BF_LINEAR, bf.BF_ASC, 50.0, 100.0, 1.5),
+                (3, bf.BF_ASC, 50.0, 100.0, 1.0)]:
+        with pytest.raises(bf.BFError) as e:
+            bf.bf_bank_create(ctx, [bad], 2048.0, 1.0)
+        assert e.value.status == bf.BF_EINVAL
+
+
+# ------------------------------------------------------------------ control
+
+@pytest.mark.parametrize("n", [1, 2, 3, 1000, 2047, 2048, 2049, 65537, 262144])
+def test_control_bit_exact(ctx, n):
+    x = np.random.default_rng(n).standard_normal(n).astype(np.float32)
+    ref = oracle.permute(x, 4)
+    got = bf.bf_control_randomize(ctx, x, 4)                   # host -> host
+    np.testing.assert_array_equal(got, ref)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    bf.bf_control_randomize(ctx, xd, 4, yd)                    # device -> device
+    np.testing.assert_array_equal(yd.cpu().numpy(), ref)
+
+
+def test_control_seed_edge_values(ctx):
+    x = np.arange(5000, dtype=np.float32)
+    for seed in (0, 2 ** 64 - 1, 0x9E3779B97F4A7C15):
+        np.testing.assert_array_equal(bf.bf_control_randomize(ctx, x, seed), oracle.permute(x, seed))
+
+
+# ------------------------------------------------------------------ tiny config, full parity
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16"])
+def test_tiny_dense_rho(ctx, tiny, prec):
+    w, bank, p, ref = tiny
+    x, fs = w["series"][0], w["fs"]
+    K, L = ref["rho"].shape
+    rho = torch.zeros((K, L), dtype=torch.float32, device="cuda")
+    outs, _, info = run(ctx, bank, [x], fs, prec, rho_out=rho)
+    err = np.abs(rho.cpu().numpy().astype(np.float64) - ref["rho"])
+    assert err.max() <= TOL[prec], f"{prec}: max |rho - oracle| = {err.max():.3e}"
+    assert info.correlations == K * L
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16"])
+def test_tiny_maxima_sigma_hist(ctx, tiny, prec):
+    w, bank, p, ref = tiny
+    x, fs = w["series"][0], w["fs"]
+    outs, mean, _ = run(ctx, bank, [x], fs, prec)
+    g = outs[0]
+    frac = check_maxima(g, ref, ref["rho"], TOL[prec], prec)
+    # the margin rule leaves fewer templates to compare at the looser BF16 bound
+    assert frac > (0.3 if prec == "bf16" else 0.5)
+    check_sigma(g, ref, TOL[prec], prec)
+    check_hist(g["hist"], ref["max"], TOL[prec])
+    np.testing.assert_array_equal(mean, g["max"])             # one series
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+def test_tiny_tf_map(ctx, tiny, prec):
+    w, bank, p, ref = tiny
+    x, fs, M = w["series"][0], w["fs"], w["M"]
+    kappa = 3.5                                               # enough tails to paint
+    outs, _, info = run(ctx, bank, [x], fs, prec, want_map=True, kappa=kappa)
+    assert info.candidates_overflow == 0 and info.n_candidates > 0
+    n_ref, n_gpu = check_map(outs[0]["map"], x, fs, p, M, kappa, TOL[prec])
+    assert n_gpu > 0
+
+
+def test_injection_recovered(ctx):
+    """A bank template injected into noise is found at its offset."""
+    fs, M = 2048.0, 2048
+    spec = synth.grid_spec([synth.LINEAR], [synth.ASC, synth.DESC], [1.0], 50.0, 1000.0, 4, 4)
+    p = oracle_params(spec)
+    k, n0 = 21, 3000
+    h = oracle.template(int(p["track"][k]), int(p["sense"][k]), p["f_lo"][k], p["f_hi"][k], 1.0, fs, M)
+    x = np.random.default_rng(3).standard_normal(8192)
+    x[n0:n0 + M] += 30.0 * h
+    x = x.astype(np.float32)
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
+    for prec in ("split_bf16", "fp32", "bf16"):
+        g = run(ctx, bank, [x], fs, prec)[0][0]
+        assert g["argmax"][k] == n0 and g["max"][k] == g["max"].max()
+    bf.bf_bank_destroy(bank)
+
+
+# ------------------------------------------------------------------ ragged batch and edges
+
+def test_ragged_batch_and_bank_slice(ctx):
+    """Several series of uneven length in one launch (one exactly M long, one
+    M + 1, ragged lag tiles), a bank whose size is not a multiple of the tile
+    and a sub-range of it, zero windows inside a series."""
+    fs, M = 1024.0, 1024
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0, 0.45],
+                           20.0, 500.0, 5, 5)                    # 200 templates
+    p = oracle_params(spec)
+    rng = np.random.default_rng(5)
+    lens = [M, M + 1, 1537, 2 * M + 700, 5000]
+    xs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+    xs[3][100:1700] = 0.0                                        # windows of zeros
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
+    b0, b1 = 37, 181
+    for prec in ("split_bf16", "fp32", "bf16"):
+        outs, mean, info = run(ctx, bank, xs, fs, prec, bank_begin=b0, bank_end=b1)
+        assert info.n_templates == b1 - b0
+        ps = subset(p, np.arange(b0, b1))
+        acc = np.zeros(b1 - b0)
+        for s, x in enumerate(xs):
+            ref = oracle.search(x, fs, ps, M, want_rho=True)
+            check_maxima(outs[s], ref, ref["rho"], TOL[prec], f"{prec} series {s}")
+            check_sigma(outs[s], ref, TOL[prec])
+            acc += ref["max"]
+        np.testing.assert_allclose(mean, acc / len(xs), atol=TOL[prec])
+    bf.bf_bank_destroy(bank)
+
+
+def test_zero_series_gives_zero(ctx):
+    fs, M = 1024.0, 1024
+    spec = synth.grid_spec([synth.LINEAR], [synth.ASC], [1.0], 20.0, 500.0, 2, 2)
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
+    x = np.zeros(3000, np.float32)
+    for prec in ("split_bf16", "fp32"):
+        g = run(ctx, bank, [x], fs, prec)[0][0]
+        assert np.all(g["max"] == 0) and np.all(g["argmax"] == 0) and np.all(g["sigma"] == 0)
+    bf.bf_bank_destroy(bank)
+
+
+def test_invalid_calls(ctx, tiny):
+    w, bank, _, _ = tiny
+    x = w["series"][0]
+    with pytest.raises(bf.BFError) as e:
+        bf.bf_correlate(ctx, bank, [x[:2047]], w["fs"])          # shorter than M
+    assert e.value.status == bf.BF_EINVAL
+    with pytest.raises(bf.BFError):
+        bf.bf_correlate(ctx, bank, [x], 4096.0)                  # wrong rate
+    with pytest.raises(bf.BFError):
+        bf.bf_correlate(ctx, bank, [x], w["fs"], bf.make_opts(bank_begin=10, bank_end=5))
+    with pytest.raises(bf.BFError):
+        bf.bf_correlate(ctx, bank, [], w["fs"])
+    b32 = bf.bf_bank_create_grid(ctx, w["grid"], w["fs"], 1.0, bf.BF_BANK_FP32)
+    with pytest.raises(bf.BFError):                              # no split layout
+        bf.bf_correlate(ctx, b32, [x], w["fs"], bf.make_opts(precision="split_bf16"))
+    bf.bf_bank_destroy(b32)
+
+
+def test_async_stream_matches_sync(ctx, tiny):
+    w, bank, _, ref = tiny
+    x = torch.from_numpy(w["series"][0]).cuda()
+    s = torch.cuda.Stream()
+    res = bf.bf_correlate(ctx, bank, [x], w["fs"], bf.make_opts(stream=s.cuda_stream))
+    s.synchronize()
+    g = bf.bf_result_copy_to_host(res, 0)
+    bf.bf_result_destroy(res)
+    sync = run(ctx, bank, [w["series"][0]], w["fs"], "split_bf16")[0][0]
+    np.testing.assert_array_equal(g["max"], sync["max"])
+    np.testing.assert_array_equal(g["argmax"], sync["argmax"])
