@@ -1,0 +1,485 @@
+#!/usr/bin/env python
+"""Benchmark of the butterfly-filtering hot path on GB300.
+
+Workload (one step): the GW-like pair -- two 64 s series at 4096 Hz
+(262,144 samples each) of coloured Gaussian noise with a common power-law
+chirp -- plus their two time-randomised controls, searched against a bank of
+65,536 ascending power-law templates of 4096 samples (1 s).  A step runs every
+stage of the path: template synthesis, the two controls, series preparation
+(split rows, FP64 prefix norms), the batched split-BF16 tensor-core correlation
+of all four series in one launch, the fused epilogue (max/argmax, sigma,
+tails), finalize (histogram of maxima, time-frequency map painting) -- all
+through the C ABI.
+
+metric: lag-correlations per second (one normalised length-M inner product of
+one template at one lag), whole job.  Printed as one JSON line by rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this project
+has) on a bounded sample of the same workload.  Under torchrun every rank runs
+an independent replica (the search of one batch is not sharded across GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "correlations/s (lag-correlations, split-BF16 tcgen05 path, |err| <= 2e-5 vs FP64)"
+UNIT = "correlations/s"
+
+# DRAM traffic of the tensor-core correlation kernel measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, one launch of the
+# --kernel-case capture), per 128-template tile: every CTA works on the same
+# template tile at once, so each template block is read from DRAM once and the
+# traffic grows with the number of template tiles, not with the lag tiles.
+# Keyed by the hash of the kernel source the counters were taken on; a changed
+# kernel reports null until it is captured again.
+TRAFFIC_BYTES_PER_TEMPLATE_TILE = {}
+
+
+def kernel_source_hash() -> str:
+    with open(os.path.join(ROOT, "paper_1802_01685_gb300", "csrc", "corr_tc.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------------ helpers
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"bf16_burst": d["bf16_tflops"], "bf16_sustained": d["bf16_tflops_sustained"],
+                "hbm": d["hbm_gbs"], "source": "measured"}
+    return {"bf16_burst": 1900.0, "bf16_sustained": 1700.0, "hbm": 6800.0, "source": "fallback"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_1802_01685_gb300 import bf, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = synth.gw_pair()
+    fs, M = w["fs"], w["M"]
+    seeds = w["control_seeds"]
+    cfg = bf.bf_config_default()
+    cfg.device = local
+    ctx = bf.bf_init(cfg)
+    xs_host = [torch.from_numpy(x).pin_memory() for x in w["series"]]
+    xs = [x.cuda() for x in xs_host]
+    ctrl = [torch.empty_like(x) for x in xs]
+    N = xs[0].numel()
+    K = synth.grid_size(w["grid"])
+    L = N - M + 1
+    corr_per_step = 4 * L * K
+    opts = bf.make_opts(precision="split_bf16", want_map=True, want_hist=True)
+    kernel_ms = []
+    stage_ms = {}
+
+    def step(record=False):
+        t0 = time.perf_counter()
+        bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16)
+        t1 = time.perf_counter()
+        for x, c, sd in zip(xs, ctrl, seeds):
+            bf.bf_control_randomize(ctx, x, sd, c)
+        t2 = time.perf_counter()
+        res = bf.bf_correlate(ctx, bank, xs + ctrl, fs, opts)
+        t3 = time.perf_counter()
+        info = bf.bf_result_info_get(res)
+        if record:
+            kernel_ms.append(info.kernel_ms)
+            for k, v in (("bank_synthesis", t1 - t0), ("controls", t2 - t1), ("correlate", t3 - t2)):
+                stage_ms.setdefault(k, []).append(1e3 * v)
+        bf.bf_result_destroy(res)
+        bf.bf_bank_destroy(bank)
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = bf.bf_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        info = step(record=True)
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = bf.bf_kernel_launches() - launches0
+    barrier()
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    ms_per_step = elapsed_ms / args.steps
+    value = world * corr_per_step * args.steps / (elapsed_ms / 1e3)
+
+    # roofline of the dominant kernel (the split-BF16 tcgen05 correlation)
+    peaks = measured_peaks()
+    k_ms = float(np.mean(kernel_ms))
+    issued_flops = 3 * 2 * M * corr_per_step          # three BF16 MMAs per sample pair
+    achieved = issued_flops / (k_ms / 1e3) / 1e12
+    th = kernel_source_hash()
+    traffic = None
+    if th in TRAFFIC_BYTES_PER_TEMPLATE_TILE:
+        traffic = round(TRAFFIC_BYTES_PER_TEMPLATE_TILE[th] * (K // 128))
+    roofline = {"bound": "tensor", "achieved": round(achieved, 1),
+                "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
+                "frac": round(achieved / peaks["bf16_sustained"], 4), "traffic": traffic,
+                "kernel": "k_corr_tc<3> (split-BF16)", "kernel_ms": round(k_ms, 2),
+                "peak_source": f"{peaks['source']} bf16_tflops_sustained",
+                "algorithmic_flops_per_launch": issued_flops,
+                "useful_tflops": round(2 * M * corr_per_step / (k_ms / 1e3) / 1e12, 1)}
+
+    # end to end through the public API with pinned host buffers
+    e2e = run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step)
+
+    # plain FP32 SIMT path on the same workload (one step)
+    fp32 = None
+    if not args.no_fp32:
+        fp32 = run_fp32(ctx, bf, torch, w, xs, ctrl, corr_per_step)
+
+    # oracle on a bounded sample, and accuracy of the timed path on that sample
+    cpu = None
+    accuracy = None
+    if rank == 0 and not args.no_cpu:
+        cpu, accuracy = run_cpu_sample(ctx, bf, w, xs_host, args.cpu_templates)
+
+    serve = None
+    if rank == 0 and not args.no_serve:
+        serve = run_serve(ctx, bf, synth, args)
+
+    bf.bf_destroy(ctx)
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 (split) -> f32",
+        "data": "synthetic (seeded numpy PCG64; coloured Gaussian noise + power-law chirp)",
+        "config": {"workload": "gw_pair: 2 x 262144 samples at 4096 Hz + 2 time-randomised "
+                               "controls, 65536 power-law templates x 4096 samples",
+                   "series": 4, "samples_per_series": N, "templates": K, "template_len": M,
+                   "lags_per_series": L, "correlations_per_step": corr_per_step,
+                   "precision": "split_bf16", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (split bank 1.07 GB re-synthesised every step)",
+                   "stages_in_step": ["bank_synthesis", "controls", "series_prep",
+                                      "correlation+epilogue", "finalize+hist+map"]},
+        "stage_ms": {k: round(float(np.mean(v)), 2) for k, v in stage_ms.items()},
+        "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
+        "fp32_path": fp32, "accuracy_vs_oracle": accuracy, "cpu_baseline": cpu, "serve": serve,
+    }
+
+
+def run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step):
+    fs = w["fs"]
+    seeds = w["control_seeds"]
+    N = xs_host[0].numel()
+    ctrl_host = [torch.empty_like(x).pin_memory() for x in xs_host]
+    out = {}
+
+    def step():
+        bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16)
+        for x, c, sd in zip(xs_host, ctrl_host, seeds):
+            bf.bf_control_randomize(ctx, x, sd, c)
+        res = bf.bf_correlate(ctx, bank, xs_host + ctrl_host, fs, opts)
+        d2h = 0
+        for s in range(4):
+            r = bf.bf_result_copy_to_host(res, s, want_hist=True, want_map=True)
+            d2h += sum(a.nbytes for a in r.values() if a is not None)
+        bf.bf_result_destroy(res)
+        bf.bf_bank_destroy(bank)
+        return d2h
+
+    step()
+    n = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(n):
+        d2h = step()
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / n
+    h2d = 2 * N * 4 + 4 * N * 4                     # control inputs + the four searched series
+    out = {"value": corr_per_step / (ms / 1e3), "unit": UNIT, "ms_per_step": round(ms, 2),
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h + 2 * N * 4,
+           "steps": n, "inputs": "pinned host float32; results copied to host each step"}
+    return out
+
+
+def run_fp32(ctx, bf, torch, w, xs, ctrl, corr_per_step):
+    fs = w["fs"]
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_FP32)
+    warm = bf.make_opts(precision="fp32", bank_end=1024, want_map=True)
+    bf.bf_result_destroy(bf.bf_correlate(ctx, bank, xs + ctrl, fs, warm))
+    opts = bf.make_opts(precision="fp32", want_map=True, want_hist=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = bf.bf_correlate(ctx, bank, xs + ctrl, fs, opts)
+    wall = time.perf_counter() - t0
+    info = bf.bf_result_info_get(res)
+    bf.bf_result_destroy(res)
+    bf.bf_bank_destroy(bank)
+    return {"value": corr_per_step / wall, "unit": UNIT, "ms_per_step": round(1e3 * wall, 1),
+            "kernel_ms": round(info.kernel_ms, 1),
+            "kernel_tflops": round(2 * w["M"] * corr_per_step / (info.kernel_ms / 1e3) / 1e12, 1),
+            "note": "bank synthesis excluded; same series, bank and outputs, FP32 SIMT kernel"}
+
+
+def run_cpu_sample(ctx, bf, w, xs_host, n_templates):
+    import oracle
+    fs, M = w["fs"], w["M"]
+    g = w["grid"]
+    p = oracle.grid(g["tracks"], g["senses"], g["durations"], g["f_min"], g["f_max"], g["I"], g["J"])
+    K = len(p["track"])
+    idx = np.linspace(0, K - 1, n_templates).astype(np.int64)
+    sub = {k: np.ascontiguousarray(v[idx]) for k, v in p.items()}
+    x = xs_host[0].numpy()
+    t0 = time.perf_counter()
+    ref = oracle.search(x, fs, sub, M)
+    dt = time.perf_counter() - t0
+    L = len(x) - M + 1
+    cpu = {"value": n_templates * L / dt, "unit": UNIT, "cores": oracle.num_threads(),
+           "kind": "oracle", "seconds": round(dt, 2),
+           "sample": f"{n_templates} templates spread over the 65536-template bank x all "
+                     f"{L} lags of series 0 (FP64 direct correlation, OpenMP over templates)"}
+    # accuracy of the timed GPU path on the same sample
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16)
+    acc = {}
+    for prec in ("split_bf16", "bf16"):
+        res = bf.bf_correlate(ctx, bank, [xs_host[0]], fs, bf.make_opts(precision=prec))
+        got = bf.bf_result_copy_to_host(res, 0)
+        bf.bf_result_destroy(res)
+        err = np.abs(got["max"][idx].astype(np.float64) - ref["max"])
+        acc[prec] = {"max_abs_err_of_max_rho": float(err.max()),
+                     "argmax_equal": int((got["argmax"][idx] == ref["argmax"]).sum()),
+                     "templates": int(n_templates)}
+    bf.bf_bank_destroy(bank)
+    return cpu, acc
+
+
+def run_serve(ctx, bf, synth, args):
+    """Finite seeded stream of mixed requests (lengths 4-64 s, 2048/4096 Hz,
+    Gaussian or Poisson-count, bank slices of 2^12..2^16 templates) arriving
+    as a Poisson process; continuous batching; p50/p99 from submission."""
+    reqs = synth.serving_stream(seed=8, n_requests=args.serve_requests, rate_hz=args.serve_rate,
+                                t_min=4.0, t_max=64.0, k_min_log2=12, k_max_log2=16)
+    banks = {}
+    for fs in (2048.0, 4096.0):
+        spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0],
+                               20.0, min(1000.0, fs / 2 - 24), 128, 128)
+        banks[fs] = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_SPLIT_BF16)
+    series = [synth.request_series(r) for r in reqs]
+    t0 = time.perf_counter()
+    tickets = []
+    corr = 0.0
+    for r, x in zip(reqs, series):
+        while time.perf_counter() - t0 < r["arrival_s"]:
+            time.sleep(0.0005)
+        opts = bf.make_opts(precision="split_bf16", bank_end=r["n_templates"])
+        tickets.append(bf.bf_serve_submit(ctx, banks[r["fs"]], x, r["fs"], opts))
+        corr += (len(x) - int(r["fs"]) + 1) * r["n_templates"]
+    for t in tickets:
+        st, res = bf.bf_serve_poll(ctx, t, -1)
+        if res:
+            bf.bf_result_destroy(res)
+    wall = time.perf_counter() - t0
+    s = bf.bf_serve_stats_get(ctx)
+    for b in banks.values():
+        bf.bf_bank_destroy(b)
+    return {"requests": len(reqs), "rate_hz": args.serve_rate, "p50_ms": round(s.p50_ms, 2),
+            "p99_ms": round(s.p99_ms, 2), "sustained_correlations_per_s": corr / wall,
+            "busy_correlations_per_s": s.correlations_per_s, "launches": int(s.launches),
+            "precision": "split_bf16",
+            "stream": "seeded Poisson arrivals; 4-64 s series; 2048/4096 Hz; 2^12-2^16 templates"}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, rank, world, local):
+    """The FP64 CPU oracle timed as it stands on the host cores, each step a
+    bounded sample of the same workload: the four series (two data, two
+    controls) against a fixed slice of the bank."""
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1802_01685_gb300 import synth
+    oracle.build()
+    w = synth.gw_pair()
+    fs, M = w["fs"], w["M"]
+    g = w["grid"]
+    p = oracle.grid(g["tracks"], g["senses"], g["durations"], g["f_min"], g["f_max"], g["I"], g["J"])
+    K = len(p["track"])
+    idx = np.linspace(0, K - 1, args.ref_templates).astype(np.int64)
+    sub = {k: np.ascontiguousarray(v[idx]) for k, v in p.items()}
+    series = list(w["series"]) + [oracle.permute(x, sd) for x, sd in zip(w["series"], w["control_seeds"])]
+    L = len(series[0]) - M + 1
+
+    def step():
+        for x in series:
+            oracle.search(x, fs, sub, M)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    corr = 4 * L * args.ref_templates
+    v = corr / dt
+    sample = (f"{args.ref_templates} of 65536 templates x 4 series x {L} lags per step "
+              f"(FP64 direct correlation)")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded numpy PCG64)",
+            "config": {"workload": "gw_pair (bounded sample)", "templates_per_step": args.ref_templates},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_kernel_case():
+    """Moderate case of the split-BF16 kernel for profiler captures: one 16 s
+    series at 4096 Hz against 16,384 power-law templates (split bank 268 MB,
+    larger than L2); two launches, each printed with its CUDA-event time."""
+    from paper_1802_01685_gb300 import bf, synth
+    import __graft_entry__
+    __graft_entry__.build()
+    w = synth.gw_pair(n=65536, I=128, J=128)
+    ctx = bf.bf_init()
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], w["fs"], 1.0, bf.BF_BANK_SPLIT_BF16)
+    for _ in range(2):
+        res = bf.bf_correlate(ctx, bank, [w["series"][0]], w["fs"],
+                              bf.make_opts(precision="split_bf16"))
+        info = bf.bf_result_info_get(res)
+        print(json.dumps({"kernel_case": "gw_pair 16 s x 16384 templates", "kernel_ms": info.kernel_ms,
+                          "correlations": info.correlations}), flush=True)
+        bf.bf_result_destroy(res)
+    bf.bf_bank_destroy(bank)
+    bf.bf_destroy(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="run only the moderate profiling case of the tensor-core kernel")
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--cpu-templates", type=int, default=128)
+    ap.add_argument("--ref-templates", type=int, default=8)
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=8.0)
+    args = ap.parse_args()
+    if args.kernel_case:
+        run_kernel_case()
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_env()
+    out = run_reference(args, rank, world, local) if args.impl == "reference" else \
+        run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

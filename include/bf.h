@@ -270,6 +270,9 @@ bf_status bf_serve_stats_get(bf_ctx* ctx, bf_serve_stats* out);
 const char* bf_last_error(void);
 const char* bf_status_string(bf_status s);
 int bf_abi_version(void);
+/* Number of kernels this library has launched in the process so far (all
+ * contexts); a diagnostic for benchmarks.  The paper has no counterpart. */
+uint64_t bf_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -242,9 +242,10 @@ int oracle_search(const float *x, long N, double fs, const int *track,
             return -1;
     long L = N - M + 1;
 
-    /* window energies, shared by all templates */
+    /* window energies, shared by all templates (lags are independent) */
     double *energy = (double *)malloc(sizeof(double) * (size_t)L);
     if (!energy) return -1;
+#pragma omp parallel for schedule(static)
     for (long tau = 0; tau < L; ++tau) {
         double e = 0.0;
         for (long m = 0; m < M; ++m) e += (double)x[tau + m] * (double)x[tau + m];

@@ -129,6 +129,7 @@ def load() -> C.CDLL:
             "bf_last_error": (C.c_char_p, []),
             "bf_status_string": (C.c_char_p, [i]),
             "bf_abi_version": (i, []),
+            "bf_kernel_launches": (u64, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -373,3 +374,7 @@ def bf_status_string(st: int) -> str:
 
 def bf_abi_version() -> int:
     return int(load().bf_abi_version())
+
+
+def bf_kernel_launches() -> int:
+    return int(load().bf_kernel_launches())

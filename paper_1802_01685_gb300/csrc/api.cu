@@ -11,6 +11,8 @@
 
 namespace bfi {
 
+std::atomic<uint64_t> g_launches{0};
+
 // ---------------------------------------------------------------- errors
 static thread_local std::string g_err;
 
@@ -476,6 +478,7 @@ extern "C" {
 
 const char* bf_last_error(void) { return g_err.c_str(); }
 int bf_abi_version(void) { return BF_ABI_VERSION; }
+uint64_t bf_kernel_launches(void) { return g_launches.load(); }
 
 const char* bf_status_string(bf_status s)
 {

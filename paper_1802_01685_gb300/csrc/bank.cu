@@ -96,6 +96,7 @@ cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t K, uint32_t K_pad
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
+    count_launches(1);
     k_bank_synth<<<K_pad, 256, smem, s>>>(params, K, M, M_pad, fs, f32, hi, lo);
     return cudaGetLastError();
 }

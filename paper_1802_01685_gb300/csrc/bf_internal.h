@@ -86,6 +86,10 @@ struct CorrParams {
 };
 
 // ---------------------------------------------------------------- launchers
+// Process-wide count of kernel launches made by this library.
+extern std::atomic<uint64_t> g_launches;
+inline void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 cudaError_t launch_corr_simt(const CorrParams& p, cudaStream_t s);
 cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int n_sm, cudaStream_t s);
 

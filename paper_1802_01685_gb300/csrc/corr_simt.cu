@@ -116,6 +116,7 @@ cudaError_t launch_corr_simt(const CorrParams& p, cudaStream_t st)
     if (p.total_tiles == 0) return cudaSuccess;
     uint64_t grid = p.total_tiles;
     if (grid > (1ull << 30)) grid = 1ull << 30;
+    count_launches(1);
     k_corr_simt<<<(unsigned)grid, SIMT_THREADS, 0, st>>>(p);
     return cudaGetLastError();
 }

@@ -419,6 +419,7 @@ cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int n_sm, cudaStream_
         attr_done[which] = true;
     }
     uint64_t grid = p.total_tiles < (uint64_t)n_sm ? p.total_tiles : (uint64_t)n_sm;
+    count_launches(1);
     kern<<<(unsigned)grid, TC_THREADS, SMEM_BYTES, st>>>(p);
     return cudaGetLastError();
 }

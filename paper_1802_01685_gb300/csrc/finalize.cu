@@ -54,6 +54,7 @@ cudaError_t launch_finalize(const FinalizeParams& p, uint32_t K, uint32_t nbins,
     uint64_t blocks = (total + 255) / 256;
     if (blocks > 65535ull * 32) blocks = 65535ull * 32;
     if (blocks == 0) return cudaSuccess;
+    count_launches(1);
     k_finalize<<<(unsigned)blocks, 256, 0, s>>>(p, K, nbins);
     return cudaGetLastError();
 }
@@ -63,6 +64,7 @@ cudaError_t launch_mean_max(const float* vmax, uint32_t n_series, uint32_t K, fl
 {
     unsigned b = (K + 255) / 256;
     if (b == 0) return cudaSuccess;
+    count_launches(1);
     k_mean_max<<<b, 256, 0, s>>>(vmax, n_series, K, mean);
     return cudaGetLastError();
 }
@@ -112,6 +114,7 @@ cudaError_t launch_paint(const Candidate* cand, const unsigned int* count, unsig
                          const ChirpDev* params, const FinalizeParams& fp, uint32_t M, double fs,
                          double dt, double df, uint32_t nf, unsigned int n_sm, cudaStream_t s)
 {
+    count_launches(1);
     k_paint<<<n_sm * 8, 256, 0, s>>>(cand, count, cap, params, fp, M, fs, dt, df, nf);
     return cudaGetLastError();
 }

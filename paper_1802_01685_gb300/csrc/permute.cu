@@ -124,15 +124,21 @@ cudaError_t launch_permute(const float* in, uint64_t n, uint64_t seed, float* ou
     const uint64_t P = pow2_at_least(n);
     uint64_t* keys = reinterpret_cast<uint64_t*>(scratch);
     uint32_t* idx = reinterpret_cast<uint32_t*>(keys + P);
+    count_launches(1);
     k_perm_keys<<<grid_for(P), 256, 0, s>>>(keys, idx, n, P, seed);
     const uint64_t chunk = P < (uint64_t)SORT_CHUNK ? P : (uint64_t)SORT_CHUNK;
     const unsigned nchunks = (unsigned)(P / chunk);
+    count_launches(1);
     k_bitonic_shared<<<nchunks, SORT_THREADS, 0, s>>>(keys, idx, chunk, 2, chunk, 1);
     for (uint64_t k = chunk << 1; k <= P; k <<= 1) {
-        for (uint64_t j = k >> 1; j >= chunk; j >>= 1)
+        for (uint64_t j = k >> 1; j >= chunk; j >>= 1) {
+            count_launches(1);
             k_bitonic_global<<<grid_for(P / 2), 256, 0, s>>>(keys, idx, P, j, k);
+        }
+        count_launches(1);
         k_bitonic_shared<<<nchunks, SORT_THREADS, 0, s>>>(keys, idx, chunk, k, k, chunk >> 1);
     }
+    count_launches(1);
     k_gather<<<grid_for(n), 256, 0, s>>>(in, idx, n, out);
     return cudaGetLastError();
 }

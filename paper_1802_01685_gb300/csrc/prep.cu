@@ -42,6 +42,7 @@ cudaError_t launch_split_rows(const float* x, uint64_t N, uint64_t rows, uint4* 
     uint64_t blocks = (rows + 255) / 256;
     if (blocks > 65535ull * 16) blocks = 65535ull * 16;
     if (blocks == 0) blocks = 1;
+    count_launches(1);
     k_split_rows<<<(unsigned)blocks, 256, 0, s>>>(x, N, rows, yhi, ylo);
     return cudaGetLastError();
 }
@@ -154,6 +155,7 @@ cudaError_t launch_inv_norm(const float* x, uint64_t N, uint32_t M, double* pref
 {
     uint64_t nb = (N + SCAN_B - 1) / SCAN_B;
     if (nb == 0 || nb + 1 > n_blocks_cap || N < M) return cudaErrorInvalidValue;
+    count_launches(4);
     k_block_sq<<<(unsigned)nb, SCAN_T, 0, s>>>(x, N, block_scratch);
     k_scan_sums<<<1, SCAN_T, 0, s>>>(block_scratch, nb);
     k_prefix<<<(unsigned)nb, SCAN_T, 0, s>>>(x, N, block_scratch, prefix);
