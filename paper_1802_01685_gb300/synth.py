@@ -158,12 +158,14 @@ def grb_batch(seed: int = 6, n_series: int = 42, fs: float = 2000.0,
               J: int = 1024):
     """n_series mean-subtracted Poisson light curves at 0.5 ms bins, lengths
     uniform in [t_min, t_max] s; bank of 2 x I x J linear 1 s templates over
-    [20, 1000] Hz, both senses (1,048,576 for I=512, J=1024)."""
+    [20, 999] Hz, both senses (1,048,576 for I=512, J=1024).  The band stops
+    1 Hz short of 1000 Hz, the Nyquist frequency of 0.5 ms bins, which no
+    template may reach."""
     rng = np.random.default_rng(seed)
     M = int(fs)
     lens = rng.uniform(t_min, t_max, n_series)
     xs = [grb_lightcurve(int(round(T * fs)), fs, rng).astype(np.float32) for T in lens]
-    spec = grid_spec([LINEAR], [ASC, DESC], [1.0], 20.0, 1000.0, I, J)
+    spec = grid_spec([LINEAR], [ASC, DESC], [1.0], 20.0, 999.0, I, J)
     return dict(name="grb_batch", series=xs, fs=fs, M=M, grid=spec)
 
 
