@@ -233,6 +233,30 @@ bf_status bf_control_randomize(bf_ctx* ctx, const float* in, size_t n, uint64_t 
                                float* out);
 
 /*
+ * Time-randomised control that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory where they need the control -- code inside a framework whose
+ * allocator owns all device memory, pipelines with a device-memory plan fixed
+ * up front (cudaMalloc can also stall them on an implicit synchronisation),
+ * callers under a hard memory cap.  It needs no context.
+ *   in, out  device pointers (current device) of n floats, not overlapping;
+ *   n        1 .. BF_STATIC_CONTROL_MAX (larger n: BF_EINVAL);
+ *   stream   cudaStream_t to enqueue on, NULL for the default stream.  The call
+ *            returns once the work is enqueued; out is valid when the stream
+ *            reaches it.
+ * Output equals bf_control_randomize(ctx, in, n, seed, out).  The sort scratch
+ * is a fixed array in the library's device code (6 MiB, held on every GPU
+ * that loads the library until the process exits); it is shared by every
+ * call and keeps the last call's contents (nothing in it needs clearing), so
+ * calls whose work overlaps on the GPU, e.g. on two streams, race.  The first
+ * call on a device looks the array's address up (cudaGetSymbolAddress); make
+ * that first call outside any stream capture.
+ */
+#define BF_STATIC_CONTROL_MAX 524288
+bf_status bf_control_randomize_static(const float* in, size_t n, uint64_t seed, float* out,
+                                      void* stream);
+
+/*
  * Serving with continuous batching.  submit copies the series and returns a
  * ticket without waiting for GPU work; a scheduler thread admits requests
  * while slots and HBM budget allow, and each launch of the batched kernel

@@ -122,6 +122,7 @@ def load() -> C.CDLL:
             "bf_result_copy_mean_max": (i, [p, p]),
             "bf_result_destroy": (None, [p]),
             "bf_control_randomize": (i, [p, p, s, u64, p]),
+            "bf_control_randomize_static": (i, [p, s, u64, p, p]),
             "bf_serve_submit": (i, [p, P(bf_request), P(u64)]),
             "bf_serve_poll": (i, [p, u64, C.c_int64, P(p)]),
             "bf_serve_cancel": (i, [p, u64]),
@@ -334,6 +335,17 @@ def bf_control_randomize(ctx: int, x, seed: int, out=None):
         out = np.zeros(n, np.float32)
     _check(load().bf_control_randomize(ctx, _addr(x), n, seed & 0xFFFFFFFFFFFFFFFF, _addr(out)))
     return out
+
+
+BF_STATIC_CONTROL_MAX = 524288
+
+
+def bf_control_randomize_static(x, seed: int, out, stream=None) -> None:
+    """Control without device allocation: x and out are CUDA tensors (or device
+    addresses); enqueued on `stream` (a cudaStream_t handle, None = default)."""
+    n = x.numel() if hasattr(x, "numel") else len(x)
+    _check(load().bf_control_randomize_static(_addr(x), n, seed & 0xFFFFFFFFFFFFFFFF, _addr(out),
+                                              stream))
 
 
 # ---------------------------------------------------------------- serving
