@@ -47,7 +47,7 @@ UNIT = "correlations/s"
 # Keyed by the hash of the kernel source the counters were taken on; a changed
 # kernel reports null until it is captured again.
 TRAFFIC_BYTES_PER_TEMPLATE_TILE = {
-    "8465809a8bdb5b15": (273.64e6 + 4.10e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
+    "b6460b139d9129d2": (271.58e6 + 4.07e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
 }
 
 

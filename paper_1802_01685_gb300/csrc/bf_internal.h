@@ -29,7 +29,7 @@ constexpr int TC_TILE_T = 128;
 constexpr int TC_TILE_L = 512;
 constexpr int TC_BK = 64;
 constexpr int TC_STAGES = 4;
-constexpr int TC_THREADS = 192;           // producer, MMA, 4 epilogue warps
+constexpr int TC_THREADS = 320;           // producer, MMA, 8 epilogue warps
 // SIMT FP32 path: one block tile is 64 templates x 256 lags, 32-sample chunks.
 constexpr int SIMT_TILE_T = 64;
 constexpr int SIMT_TILE_L = 256;

@@ -16,12 +16,16 @@
 // into the same FP32 accumulator (x_hi h_hi + x_hi h_lo + x_lo h_hi), dropping
 // only x_lo h_lo (relative size 2^-16 or less).
 //
-// Warp roles (192 threads, one CTA per SM, persistent over tiles):
+// Warp roles (320 threads, one CTA per SM, persistent over tiles):
 //   warp 0  producer: bulk copies of template and series blocks per stage
 //   warp 1  allocates TMEM, one lane issues tcgen05.mma and commits
-//   warps 2-5 epilogue: tcgen05.ld of the 128 x 512 FP32 accumulator, each
-//            thread owning one template row: rho = C * inv_norm, running
-//            max/argmax (ties to the smallest lag), sum of rho^2, tails.
+//   warps 2-9 epilogue: tcgen05.ld of the 128 x 512 FP32 accumulator; two
+//            warps per TMEM lane quadrant, each thread owning one template
+//            row and half of the lags: rho = C * inv_norm, running max/argmax
+//            (ties to the smallest lag), sum of rho^2, tails.  Four
+//            independent accumulator chains per thread keep the ALU busy:
+//            the accumulator fills TMEM, so the next tile's MMAs wait for the
+//            epilogue and its speed is tensor-pipe time.
 // Every mbarrier wait is bounded in time; on expiry the kernel records an
 // error code in the status word, drains its own copies and MMAs, frees TMEM
 // and returns.
@@ -163,19 +167,61 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// OR of a predicate over the 128 epilogue threads (named barrier 1)
+constexpr uint32_t EPI_THREADS = TC_THREADS - 64;            // 256
+
+// OR of a predicate over the epilogue threads (named barrier 1)
 __device__ __forceinline__ bool epilogue_any(bool pred)
 {
     uint32_t res;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "barrier.red.or.pred q, 1, 128, p;\n\t"
+        "barrier.red.or.pred q, 1, %2, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(res)
-        : "r"((uint32_t)pred)
+        : "r"((uint32_t)pred), "n"(EPI_THREADS)
         : "memory");
     return res != 0;
+}
+
+__device__ __forceinline__ void epilogue_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+}
+
+// running reductions of one template row over its lags, in 4 chains
+struct EpiState {
+    float bv[4];          // max |rho| per chain (-1: nothing seen)
+    uint32_t bi[4];       // its column (first on ties within the chain)
+    float ss[4];          // sum of rho^2
+};
+
+// 32 accumulator columns c0 .. c0+31 of one template row
+template <bool FULL, bool DENSE>
+__device__ __forceinline__ void epi_chunk(const uint32_t (&r)[32], const float* __restrict__ inv,
+                                          uint32_t c0, uint32_t nvalid, EpiState& st,
+                                          const CorrParams& p, const Seg& s, uint32_t k,
+                                          bool keep, uint32_t lag0)
+{
+#pragma unroll
+    for (uint32_t j4 = 0; j4 < 32; j4 += 4) {
+        const float4 iv = *reinterpret_cast<const float4*>(inv + c0 + j4);
+        const float ivs[4] = {iv.x, iv.y, iv.z, iv.w};
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+            const uint32_t j = j4 + u;
+            if (!FULL && c0 + j >= nvalid) continue;
+            const float v = __uint_as_float(r[j]) * ivs[u];
+            const float a = fabsf(v);
+            if (a > st.bv[u]) {
+                st.bv[u] = a;
+                st.bi[u] = c0 + j;
+            }
+            st.ss[u] = fmaf(v, v, st.ss[u]);
+            if (DENSE && keep) s.rho[(size_t)(k - s.k_begin) * s.L + lag0 + c0 + j] = v;
+            if (keep && a >= p.thr) push_candidate(p, s.series_id, k, lag0 + c0 + j, v);
+        }
+    }
 }
 
 __device__ __forceinline__ void record_error(int* err, int code)
@@ -227,7 +273,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             mbar_init(empty_bar(st), 1);
         }
         mbar_init(tfull_bar, 1);
-        mbar_init(tempty_bar, 128);
+        mbar_init(tempty_bar, EPI_THREADS);
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -338,20 +384,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
     } else {
         // ------------------------------------------------------------ epilogue
         const uint32_t q = warp & 3;                       // TMEM lane quadrant
+        const uint32_t half = (warp - 2) >> 2;             // lags [256 half, 256 half + 256)
         const uint32_t row = q * 32 + lane;                // template row of the tile
-        const uint32_t e = threadIdx.x - 64;               // 0..127
+        const uint32_t e = threadIdx.x - 64;               // 0 .. EPI_THREADS-1
         uint32_t tph = 0;
         for (uint64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
             const TileCoord c = tile_coord(p, t);
             const Seg& s = *c.s;
             const uint32_t nvalid = min((uint32_t)TC_TILE_L, s.L - c.lag0);
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-#pragma unroll
-            for (uint32_t i = 0; i < 4; ++i) {
-                uint32_t j = 4 * e + i;
+            epilogue_sync();
+            for (uint32_t j = e; j < TC_TILE_L; j += EPI_THREADS)
                 sh_inv[j] = j < nvalid ? s.inv_norm[c.lag0 + j] : 0.f;
-            }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            epilogue_sync();
             const bool ok = mbar_wait(tfull_bar, tph, abort_flag);
             if (epilogue_any(!ok)) {       // all epilogue threads leave together
                 if (!ok && !*abort_flag) record_error(p.err, DEV_TIMEOUT_TMEM);
@@ -361,36 +405,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             fence_after();
             const uint32_t k = c.tt * TC_TILE_T + row;
             const bool keep = k >= s.k_begin && k < s.k_end;
-            unsigned long long best = 0ull;
-            float ss = 0.f;
+            const bool full = nvalid == TC_TILE_L;
+            const bool dense = s.rho != nullptr;
+            EpiState st;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                st.bv[u] = -1.f;
+                st.bi[u] = 0;
+                st.ss[u] = 0.f;
+            }
             const uint32_t taddr = tmem + ((q * 32) << 16);
 #pragma unroll 1
-            for (uint32_t c0 = 0; c0 < TC_TILE_L; c0 += 32) {
+            for (uint32_t c0 = half * (TC_TILE_L / 2); c0 < (half + 1) * (TC_TILE_L / 2); c0 += 32) {
                 uint32_t r[32];
                 __syncwarp();
                 tmem_ld32(taddr + c0, r);
                 if (c0 < nvalid) {
-#pragma unroll
-                    for (uint32_t j = 0; j < 32; ++j) {
-                        if (c0 + j < nvalid) {
-                            const float v = __uint_as_float(r[j]) * sh_inv[c0 + j];
-                            const float av = fabsf(v);
-                            if (s.rho && keep) s.rho[(size_t)(k - s.k_begin) * s.L + c.lag0 + c0 + j] = v;
-                            const unsigned long long key = pack_max(av, c.lag0 + c0 + j);
-                            best = key > best ? key : best;
-                            ss = fmaf(v, v, ss);
-                            if (keep && av >= p.thr)
-                                push_candidate(p, s.series_id, k, c.lag0 + c0 + j, v);
-                        }
-                    }
+                    if (dense) epi_chunk<false, true>(r, sh_inv, c0, nvalid, st, p, s, k, keep, c.lag0);
+                    else if (full) epi_chunk<true, false>(r, sh_inv, c0, nvalid, st, p, s, k, keep, c.lag0);
+                    else epi_chunk<false, false>(r, sh_inv, c0, nvalid, st, p, s, k, keep, c.lag0);
                 }
             }
             fence_before();
             mbar_arrive(tempty_bar);
             tph ^= 1;
-            if (keep) {
-                atomicMax(s.vmax + (k - s.k_begin), best);
-                atomicAdd(s.sumsq + (k - s.k_begin), (double)ss);
+            // merge the chains: largest |rho|, smallest column on ties
+            float bv = st.bv[0];
+            uint32_t bi = st.bi[0];
+#pragma unroll
+            for (int u = 1; u < 4; ++u)
+                if (st.bv[u] > bv || (st.bv[u] == bv && st.bi[u] < bi)) {
+                    bv = st.bv[u];
+                    bi = st.bi[u];
+                }
+            if (keep && bv >= 0.f) {
+                atomicMax(s.vmax + (k - s.k_begin), pack_max(bv, c.lag0 + bi));
+                atomicAdd(s.sumsq + (k - s.k_begin),
+                          (double)((st.ss[0] + st.ss[1]) + (st.ss[2] + st.ss[3])));
             }
         }
     }
