@@ -151,7 +151,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+// Issues a 32-lane x 32-column TMEM load; the registers are valid only after
+// tmem_wait(r) (the load completes asynchronously).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32])
 {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -164,7 +166,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
           "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Waits for this thread's outstanding TMEM loads.  The registers of the load
+// in flight are passed as read-write operands so that no use of them can be
+// scheduled before the wait.
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                   "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                   "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 
 constexpr uint32_t EPI_THREADS = TC_THREADS - 64;            // 256
@@ -196,13 +213,15 @@ struct EpiState {
     float ss[4];          // sum of rho^2
 };
 
-// 32 accumulator columns c0 .. c0+31 of one template row
+// 32 accumulator columns c0 .. c0+31 of one template row: running max/argmax
+// and sum of squares; returns the largest |rho| of the chunk so that the tail
+// test costs one branch per chunk.  DENSE also stores every rho.
 template <bool FULL, bool DENSE>
-__device__ __forceinline__ void epi_chunk(const uint32_t (&r)[32], const float* __restrict__ inv,
-                                          uint32_t c0, uint32_t nvalid, EpiState& st,
-                                          const CorrParams& p, const Seg& s, uint32_t k,
-                                          bool keep, uint32_t lag0)
+__device__ __forceinline__ float epi_chunk(const uint32_t (&r)[32], const float* __restrict__ inv,
+                                           uint32_t c0, uint32_t nvalid, EpiState& st,
+                                           float* __restrict__ rho_row)
 {
+    float cmax = 0.f;
 #pragma unroll
     for (uint32_t j4 = 0; j4 < 32; j4 += 4) {
         const float4 iv = *reinterpret_cast<const float4*>(inv + c0 + j4);
@@ -218,9 +237,23 @@ __device__ __forceinline__ void epi_chunk(const uint32_t (&r)[32], const float* 
                 st.bi[u] = c0 + j;
             }
             st.ss[u] = fmaf(v, v, st.ss[u]);
-            if (DENSE && keep) s.rho[(size_t)(k - s.k_begin) * s.L + lag0 + c0 + j] = v;
-            if (keep && a >= p.thr) push_candidate(p, s.series_id, k, lag0 + c0 + j, v);
+            cmax = fmaxf(cmax, a);
+            if (DENSE) rho_row[c0 + j] = v;
         }
+    }
+    return cmax;
+}
+
+// rare path: push every tail of a chunk whose largest |rho| reached thr
+__device__ __forceinline__ void epi_tails(const uint32_t (&r)[32], const float* __restrict__ inv,
+                                          uint32_t c0, uint32_t nvalid, float thr,
+                                          const CorrParams& p, uint32_t series, uint32_t k,
+                                          uint32_t lag0)
+{
+#pragma unroll
+    for (uint32_t j = 0; j < 32; ++j) {     // unrolled: r stays in registers
+        const float v = __uint_as_float(r[j]) * inv[c0 + j];
+        if (c0 + j < nvalid && fabsf(v) >= thr) push_candidate(p, series, k, lag0 + c0 + j, v);
     }
 }
 
@@ -406,7 +439,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             const uint32_t k = c.tt * TC_TILE_T + row;
             const bool keep = k >= s.k_begin && k < s.k_end;
             const bool full = nvalid == TC_TILE_L;
-            const bool dense = s.rho != nullptr;
+            float* const rho_row = (s.rho != nullptr && keep) ? s.rho + (size_t)(k - s.k_begin) * s.L + c.lag0
+                                                              : nullptr;
+            const bool dense = rho_row != nullptr;
+            const float thr = keep ? p.thr : INFINITY;
+            const uint32_t series = s.series_id, lag0 = c.lag0;
             EpiState st;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -415,19 +452,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
                 st.ss[u] = 0.f;
             }
             const uint32_t taddr = tmem + ((q * 32) << 16);
+            // software pipeline over the 8 chunks of 32 columns: the load of
+            // chunk i+1 is in flight while chunk i is reduced; TMEM is handed
+            // back to the MMA warp as soon as the last load has landed
+            const uint32_t cbeg = half * (TC_TILE_L / 2), cend = cbeg + TC_TILE_L / 2;
+            uint32_t ra[32], rb[32];
+            auto reduce = [&](const uint32_t (&r)[32], uint32_t cc) {
+                if (cc >= nvalid) return;
+                float cmax;
+                if (dense) cmax = epi_chunk<false, true>(r, sh_inv, cc, nvalid, st, rho_row);
+                else if (full) cmax = epi_chunk<true, false>(r, sh_inv, cc, nvalid, st, nullptr);
+                else cmax = epi_chunk<false, false>(r, sh_inv, cc, nvalid, st, nullptr);
+                if (cmax >= thr) epi_tails(r, sh_inv, cc, nvalid, thr, p, series, k, lag0);
+            };
+            __syncwarp();
+            tmem_ld32_async(taddr + cbeg, ra);
+            tmem_wait(ra);
 #pragma unroll 1
-            for (uint32_t c0 = half * (TC_TILE_L / 2); c0 < (half + 1) * (TC_TILE_L / 2); c0 += 32) {
-                uint32_t r[32];
+            for (uint32_t c0 = cbeg; c0 < cend; c0 += 64) {
                 __syncwarp();
-                tmem_ld32(taddr + c0, r);
-                if (c0 < nvalid) {
-                    if (dense) epi_chunk<false, true>(r, sh_inv, c0, nvalid, st, p, s, k, keep, c.lag0);
-                    else if (full) epi_chunk<true, false>(r, sh_inv, c0, nvalid, st, p, s, k, keep, c.lag0);
-                    else epi_chunk<false, false>(r, sh_inv, c0, nvalid, st, p, s, k, keep, c.lag0);
+                tmem_ld32_async(taddr + c0 + 32, rb);
+                reduce(ra, c0);
+                tmem_wait(rb);
+                const bool more = c0 + 64 < cend;
+                if (more) {
+                    __syncwarp();
+                    tmem_ld32_async(taddr + c0 + 64, ra);
+                } else {
+                    fence_before();
+                    mbar_arrive(tempty_bar);          // every column of this thread is read
                 }
+                reduce(rb, c0 + 32);
+                if (more) tmem_wait(ra);
             }
-            fence_before();
-            mbar_arrive(tempty_bar);
             tph ^= 1;
             // merge the chains: largest |rho|, smallest column on ties
             float bv = st.bv[0];
