@@ -70,7 +70,13 @@ typedef enum {
 /* which sample layouts a bank keeps in device memory (bit flags) */
 enum {
     BF_BANK_FP32 = 1,          /* needed by BF_FP32                            */
-    BF_BANK_SPLIT_BF16 = 2     /* needed by BF_BF16 and BF_SPLIT_BF16          */
+    BF_BANK_SPLIT_BF16 = 2,    /* needed by BF_BF16 and BF_SPLIT_BF16          */
+    BF_BANK_GENERATED = 4      /* keep only the chirp parameters: every
+                                  bf_correlate synthesises the templates it
+                                  needs on the fly, chunk by chunk, into a
+                                  small ring that stays in L2 while the
+                                  correlation consumes it.  Exclusive of the
+                                  other flags; serves every precision.        */
 };
 
 /*

@@ -24,7 +24,7 @@ BF_OK, BF_EINVAL, BF_ENOMEM, BF_ECUDA, BF_ETIMEDOUT, BF_EPENDING, BF_EAGAIN, \
 BF_LINEAR, BF_POWERLAW = 0, 1
 BF_ASC, BF_DESC = 0, 1
 BF_FP32, BF_BF16, BF_SPLIT_BF16 = 0, 1, 2
-BF_BANK_FP32, BF_BANK_SPLIT_BF16 = 1, 2
+BF_BANK_FP32, BF_BANK_SPLIT_BF16, BF_BANK_GENERATED = 1, 2, 4
 
 PRECISIONS = {"fp32": BF_FP32, "bf16": BF_BF16, "split_bf16": BF_SPLIT_BF16}
 

@@ -326,11 +326,13 @@ bf_status resolve_opts(const bf_bank* bank, const bf_opts* in, bf_opts* o)
         set_error("unknown precision %d", o->precision);
         return BF_EINVAL;
     }
-    if (o->precision == BF_FP32 && !bank->f32) {
+    if (bank->generated) {
+        // synthesised per call in whichever layout the precision needs
+    } else if (o->precision == BF_FP32 && !bank->f32) {
         set_error("bank keeps no FP32 layout (create it with BF_BANK_FP32)");
         return BF_EINVAL;
     }
-    if (o->precision != BF_FP32 && !bank->hi) {
+    if (!bank->generated && o->precision != BF_FP32 && !bank->hi) {
         set_error("bank keeps no split-BF16 layout (create it with BF_BANK_SPLIT_BF16)");
         return BF_EINVAL;
     }
@@ -456,6 +458,86 @@ bf_status finalize_result(bf_ctx* ctx, const bf_bank* bank, bf_result* r, cudaSt
     return BF_OK;
 }
 
+// Generated bank: templates are synthesised in chunks of template tiles into a
+// two-slot ring (~24 MiB per slot, so the ring stays in L2) on the auxiliary
+// stream, and each chunk is correlated on the main stream as soon as it is
+// ready; chunk c+1 is synthesised while chunk c is correlated.  Events order
+// the reuse of a slot after the correlation that read it.  The segments in
+// `segs` describe the whole call; each chunk restricts them to its tiles.
+constexpr size_t GEN_SLOT_BYTES = 24u << 20;
+
+cudaError_t correlate_generated(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
+                                const std::vector<Seg>& segs, bf_result* r, cudaStream_t strm)
+{
+    const bool tc = o.precision != BF_FP32;
+    const size_t tile_bytes = (size_t)TC_TILE_T * bank->M_pad * 4;     // hi+lo, or FP32
+    const size_t chunk_tiles = std::max<size_t>(1, GEN_SLOT_BYTES / tile_bytes);
+    const size_t t_begin = o.bank_begin / TC_TILE_T;
+    const size_t t_end = ceil_div(o.bank_end, TC_TILE_T);
+    const size_t n_chunks = ceil_div(t_end - t_begin, chunk_tiles);
+    const size_t slot_elems = std::min(chunk_tiles, t_end - t_begin) * TC_TILE_T * bank->M_pad;
+    Allocator& mem = *ctx->mem;
+    void* slot[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    for (int i = 0; i < 2 && i < (int)n_chunks; ++i)
+        for (int j = 0; j < (tc ? 2 : 1); ++j) {
+            slot[i][j] = mem.alloc(slot_elems * (tc ? 2 : 4));
+            if (!slot[i][j]) {
+                set_error("out of device memory for the synthesis ring");
+                return cudaErrorMemoryAllocation;
+            }
+            r->scratch.push_back(slot[i][j]);
+        }
+    cudaEvent_t ev_start, synth_done[2], corr_done[2];
+    cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+    for (int i = 0; i < 2; ++i) {
+        cudaEventCreateWithFlags(&synth_done[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&corr_done[i], cudaEventDisableTiming);
+    }
+    // the synthesis stream starts after everything already queued on the main one
+    cudaError_t e = cudaEventRecord(ev_start, strm);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, ev_start, 0);
+    for (size_t c = 0; c < n_chunks && e == cudaSuccess; ++c) {
+        const int sl = (int)(c & 1);
+        const size_t t0 = t_begin + c * chunk_tiles;
+        const size_t t1 = std::min(t0 + chunk_tiles, t_end);
+        const size_t k0 = t0 * TC_TILE_T;
+        const size_t kc = std::min(t1 * TC_TILE_T, bank->K) - k0;
+        if (c >= 2) e = cudaStreamWaitEvent(ctx->aux, corr_done[sl], 0);
+        if (e == cudaSuccess)
+            e = launch_bank_synth(bank->d_params + k0, (uint32_t)kc, (uint32_t)((t1 - t0) * TC_TILE_T),
+                                  bank->M, bank->M_pad, bank->fs,
+                                  tc ? nullptr : static_cast<float*>(slot[sl][0]),
+                                  tc ? static_cast<uint8_t*>(slot[sl][0]) : nullptr,
+                                  tc ? static_cast<uint8_t*>(slot[sl][1]) : nullptr, ctx->aux);
+        if (e == cudaSuccess) e = cudaEventRecord(synth_done[sl], ctx->aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(strm, synth_done[sl], 0);
+        if (e != cudaSuccess) break;
+        // the call's segments restricted to this chunk's template tiles
+        const uint32_t tile_t = tile_templates(o.precision);
+        const size_t q0 = std::max(k0, (size_t)o.bank_begin) / tile_t;
+        const size_t q1 = ceil_div(std::min(t1 * TC_TILE_T, (size_t)o.bank_end), tile_t);
+        std::vector<Seg> cs = segs;
+        for (Seg& g : cs) {
+            g.tt0 = (uint32_t)q0;
+            g.n_tt = (uint32_t)(q1 - q0);
+            g.bank_k0 = (uint32_t)k0;
+            g.bank_f32 = tc ? nullptr : static_cast<const float*>(slot[sl][0]);
+            g.bank_hi = tc ? static_cast<const uint8_t*>(slot[sl][0]) : nullptr;
+            g.bank_lo = tc ? static_cast<const uint8_t*>(slot[sl][1]) : nullptr;
+        }
+        e = launch_segments(ctx, cs, o.precision, r->thr, r->cand, r->cand_count, r->cand_cap, strm,
+                            nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(corr_done[sl], strm);
+    }
+    // events may be destroyed while pending work still references them
+    cudaEventDestroy(ev_start);
+    for (int i = 0; i < 2; ++i) {
+        cudaEventDestroy(synth_done[i]);
+        cudaEventDestroy(corr_done[i]);
+    }
+    return e;
+}
+
 bf_status check_device_status(bf_ctx* ctx)
 {
     int h = 0;
@@ -555,6 +637,7 @@ bf_status bf_init(const bf_config* cfg, bf_ctx** out)
     ctx->cfg = c;
     ctx->mem.reset(new Allocator(c.hbm_budget));
     e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
     e = cudaMalloc(&ctx->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
@@ -575,6 +658,7 @@ void bf_destroy(bf_ctx* ctx)
     ctx->mem.reset();
     cudaFree(ctx->d_err);
     cudaStreamDestroy(ctx->stream);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
     delete ctx;
 }
 
@@ -585,8 +669,10 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
     *out = nullptr;
     if (K == 0 || K > 0x7FFFFF00u) { set_error("bank size %zu outside [1, 2^31)", K); return BF_EINVAL; }
     if (!(fs > 0.0) || !(T > 0.0)) { set_error("need fs > 0 and T > 0"); return BF_EINVAL; }
-    if ((storage & (BF_BANK_FP32 | BF_BANK_SPLIT_BF16)) == 0 || (storage & ~3u)) {
-        set_error("storage mask %u must select BF_BANK_FP32 and/or BF_BANK_SPLIT_BF16", storage);
+    const bool generated = storage == BF_BANK_GENERATED;
+    if (!generated && ((storage & (BF_BANK_FP32 | BF_BANK_SPLIT_BF16)) == 0 || (storage & ~3u))) {
+        set_error("storage mask %u must be BF_BANK_GENERATED alone, or select BF_BANK_FP32 "
+                  "and/or BF_BANK_SPLIT_BF16", storage);
         return BF_EINVAL;
     }
     const uint32_t M = template_len(T, fs);
@@ -607,6 +693,7 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
     b->fs = fs;
     b->T = T;
     b->storage = storage;
+    b->generated = generated;
     b->params.assign(params, params + K);
     std::vector<ChirpDev> dev(K);
     for (size_t k = 0; k < K; ++k) dev[k] = to_dev(params[k], fs, M);
@@ -628,7 +715,7 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
     cudaStream_t st = ctx->stream;
     cudaError_t e = cudaMemcpyAsync(b->d_params, dev.data(), K * sizeof(ChirpDev),
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !generated)
         e = launch_bank_synth(b->d_params, (uint32_t)K, (uint32_t)b->K_pad, M, b->M_pad, fs, b->f32,
                               b->hi, b->lo, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -693,6 +780,21 @@ bf_status bf_bank_read(const bf_bank* b, size_t k0, size_t n, float* out)
 {
     if (!b || !out || k0 + n > b->K) { set_error("bad bank range"); return BF_EINVAL; }
     cudaSetDevice(b->ctx->device);
+    if (b->generated) {
+        // synthesise the range into a scratch FP32 block and copy it out
+        const size_t n_pad = ceil_div(n, K_ALIGN) * K_ALIGN;
+        float* tmp = static_cast<float*>(b->ctx->mem->alloc(n_pad * b->M_pad * sizeof(float)));
+        if (!tmp) { set_error("out of device memory reading a generated bank"); return BF_ENOMEM; }
+        std::lock_guard<std::mutex> g(b->ctx->launch_mu);
+        cudaError_t e = launch_bank_synth(b->d_params + k0, (uint32_t)n, (uint32_t)n_pad, b->M, b->M_pad,
+                                          b->fs, tmp, nullptr, nullptr, b->ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2D(out, b->M * sizeof(float), tmp, b->M_pad * sizeof(float),
+                             b->M * sizeof(float), n, cudaMemcpyDeviceToHost);
+        b->ctx->mem->release(tmp);
+        return e == cudaSuccess ? BF_OK : cuda_fail(e, "generated bank read");
+    }
     if (b->f32) {
         cudaError_t e = cudaMemcpy2D(out, b->M * sizeof(float), b->f32 + k0 * b->M_pad,
                                      b->M_pad * sizeof(float), b->M * sizeof(float), n,
@@ -787,8 +889,10 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
         cudaEventCreate(&e1);
         cudaEventRecord(e0, strm);
     }
-    cudaError_t e = launch_segments(ctx, segs, o.precision, r->thr, r->cand, r->cand_count,
-                                    r->cand_cap, strm, nullptr);
+    cudaError_t e = bank->generated
+                        ? correlate_generated(ctx, bank, o, segs, r, strm)
+                        : launch_segments(ctx, segs, o.precision, r->thr, r->cand, r->cand_count,
+                                          r->cand_cap, strm, nullptr);
     if (sync) cudaEventRecord(e1, strm);
     if (e != cudaSuccess) {
         if (e0) { cudaEventDestroy(e0); cudaEventDestroy(e1); }

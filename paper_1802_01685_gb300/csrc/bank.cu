@@ -4,8 +4,13 @@
 // One CTA builds one template: the phase in cycles is evaluated in FP64 and
 // reduced to [-1/2, 1/2) before the cosine, which then runs in FP32 (the
 // reduction is where FP64 is needed; after it FP32 holds the phase to ~1e-7
-// of a cycle).  The taper is sin^2(pi (j + 1/2) / M_D); the unit norm is an FP64
-// sum over the template.  Outputs, as requested:
+// of a cycle).  The taper is sin^2(pi (j + 1/2) / M_D) in FP32; the unit norm is
+// an FP64 sum over the template.
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, so the power-law phase
+// avoids a full FP64 pow: (1 - t/t_c)^(5/8) starts from the FP32 powf value and
+// takes one Newton step on y^8 = u^5 in FP64 (relative error ~1e-7 squared),
+// whose reciprocal comes from an FP32 seed and one Newton-Raphson step.  Outputs, as requested:
 //   f32: row-major [K_pad][M_pad] float (SIMT path),
 //   hi/lo: the tensor-core operand layout (below), hi = bf16(h), lo = bf16(h - hi).
 //
@@ -20,10 +25,27 @@
 
 namespace bfi {
 
-__device__ __forceinline__ double d_cycles(const ChirpDev& p, double t)
+// u^(5/8) for u in (0, 1]; very small u (a sweep over more than ~30x in
+// frequency) would underflow y^8 in FP32 and takes the FP64 pow instead
+__device__ __forceinline__ double pow_5_8(double u)
 {
-    if (p.track == BF_LINEAR) return p.f_lo * t + (p.f_hi - p.f_lo) * t * t / (2.0 * p.D);
-    return 1.6 * p.f_lo * p.tc * (1.0 - pow(1.0 - t / p.tc, 0.625));
+    if (u < 1e-4) return pow(u, 0.625);
+    const double y = (double)powf((float)u, 0.625f);
+    const double u2 = u * u, u5 = u2 * u2 * u;
+    const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
+    double r = (double)(1.0f / (float)y8);              // 1/y^8, then one refinement
+    r = r * fma(-y8, r, 2.0);
+    const double qv = u5 * r;                           // u^5 / y^8, close to 1
+    return y * fma(qv - 1.0, 0.125, 1.0);               // y - (y^8 - u^5) / (8 y^7)
+}
+
+// cycles elapsed at local time t of the ascending track; k1, k2 are
+// per-template constants (linear: f_lo and (f_hi - f_lo)/(2D); power law:
+// 1.6 f_lo t_c and 1/t_c)
+__device__ __forceinline__ double d_cycles(int track, double k1, double k2, double t)
+{
+    if (track == BF_LINEAR) return t * fma(k2, t, k1);
+    return k1 * (1.0 - pow_5_8(fma(-t, k2, 1.0)));
 }
 
 __device__ __forceinline__ size_t tc_offset(uint32_t k, uint32_t m, uint32_t n_kb)
@@ -47,6 +69,19 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
     ChirpDev p{};
     if (valid) p = params[k];
 
+    const double inv_fs = 1.0 / fs;
+    double k1 = 0.0, k2 = 0.0;
+    float inv_md = 0.f;
+    if (valid) {
+        if (p.track == BF_LINEAR) {
+            k1 = p.f_lo;
+            k2 = (p.f_hi - p.f_lo) / (2.0 * p.D);
+        } else {
+            k1 = 1.6 * p.f_lo * p.tc;
+            k2 = 1.0 / p.tc;
+        }
+        inv_md = 1.0f / (float)p.MD;
+    }
     double part = 0.0;
     for (uint32_t m = threadIdx.x; m < M_pad; m += blockDim.x) {
         float v = 0.f;
@@ -54,11 +89,11 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
             int j = (int)m - p.first;          // ascending-template sample index
             if (p.sense == BF_DESC) j = (int)(M - 1 - m) - p.first;
             if (m < M && j >= 0 && j < p.MD) {
-                double c = d_cycles(p, (double)j / fs);
-                double fr = c - rint(c);                   // [-1/2, 1/2]
-                float cs = cospif((float)(2.0 * fr));
-                float s = sinpif((float)(((double)j + 0.5) / (double)p.MD));
-                v = s * s * cs;
+                const double c = d_cycles(p.track, k1, k2, (double)j * inv_fs);
+                const double fr = c - rint(c);             // [-1/2, 1/2]
+                const float cs = cospif((float)(2.0 * fr));
+                const float sn = sinpif(((float)j + 0.5f) * inv_md);
+                v = sn * sn * cs;
             }
         }
         g[m] = v;

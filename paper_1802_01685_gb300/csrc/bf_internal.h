@@ -64,6 +64,10 @@ struct Seg {
     unsigned long long* vmax;       // packed max per template, index k - k_begin
     double* sumsq;                  // sum of rho^2 per template
     float* rho;                     // optional dense output [k - k_begin][tau]
+    uint32_t bank_k0;               // template index held at the bank pointers
+                                    // (0 for a stored bank, the chunk start
+                                    // for a generated one)
+    uint32_t pad1;
     uint64_t tile_begin;            // first global tile index of this segment
     uint32_t L;                     // lags
     uint32_t n_lag_tiles;
@@ -174,6 +178,7 @@ struct bf_ctx {
     int n_sm = 0;
     bf_config cfg{};
     cudaStream_t stream = nullptr;
+    cudaStream_t aux = nullptr;         // template synthesis of generated banks
     std::unique_ptr<bfi::Allocator> mem;
     int* d_err = nullptr;               // kernel status word
     std::mutex launch_mu;               // serialises use of d_err / stream
@@ -182,6 +187,7 @@ struct bf_ctx {
 
 struct bf_bank {
     bf_ctx* ctx = nullptr;
+    bool generated = false;             // parameters only; synthesised per call
     size_t K = 0, K_pad = 0;
     uint32_t M = 0, M_pad = 0;
     double fs = 0, T = 0;

@@ -332,8 +332,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             for (uint64_t t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
                 const TileCoord c = tile_coord(p, t);
                 const uint32_t n_kb = c.s->M_pad / TC_BK;
-                const uint8_t* a_hi = c.s->bank_hi + (size_t)c.tt * n_kb * A_BYTES;
-                const uint8_t* a_lo = c.s->bank_lo + (size_t)c.tt * n_kb * A_BYTES;
+                const size_t tt_rel = c.tt - c.s->bank_k0 / TC_TILE_T;
+                const uint8_t* a_hi = c.s->bank_hi + tt_rel * n_kb * A_BYTES;
+                const uint8_t* a_lo = c.s->bank_lo + tt_rel * n_kb * A_BYTES;
                 for (uint32_t kb = 0; kb < n_kb; ++kb) {
                     if (!mbar_wait(empty_bar(st), ph ^ 1, abort_flag)) {
                         if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_EMPTY);

@@ -334,6 +334,10 @@ bf_status bf_serve_submit(bf_ctx* ctx, const bf_request* req, uint64_t* ticket)
     }
     const bf_bank* bank = req->bank;
     if (bank->ctx != ctx) { set_error("bank belongs to another context"); return BF_EINVAL; }
+    if (bank->generated) {
+        set_error("serving needs a stored bank (BF_BANK_FP32 and/or BF_BANK_SPLIT_BF16)");
+        return BF_ENOTSUP;
+    }
     if (std::fabs(req->fs - bank->fs) > 1e-9 * bank->fs) {
         set_error("request rate %g differs from the bank's %g", req->fs, bank->fs);
         return BF_EINVAL;
