@@ -47,7 +47,7 @@ UNIT = "correlations/s"
 # Keyed by the hash of the kernel source the counters were taken on; a changed
 # kernel reports null until it is captured again.
 TRAFFIC_BYTES_PER_TEMPLATE_TILE = {
-    "b6460b139d9129d2": (271.58e6 + 4.07e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
+    "1692752bfa8732a6": (272.05e6 + 4.32e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
 }
 
 
@@ -125,19 +125,17 @@ def dist_env():
     return rank, world, local
 
 
-# ------------------------------------------------------------------ our arm
-
-def run_ours(args, rank, world, local):
+def make_dist(world: int, backend: str, device=None):
+    """Barrier and max-over-ranks for N independent replicas (each rank runs
+    the whole workload on its own GPU; nothing is exchanged but timings)."""
     import torch
     import torch.distributed as dist
 
-    import __graft_entry__
-    from paper_1802_01685_gb300 import bf, synth
-
-    __graft_entry__.build()
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if world > 1 and not dist.is_initialized():
+        if device is not None:
+            dist.init_process_group(backend, device_id=device)
+        else:
+            dist.init_process_group(backend)
 
     def barrier():
         if world > 1:
@@ -146,9 +144,30 @@ def run_ours(args, rank, world, local):
     def max_over_ranks(v: float) -> float:
         if world == 1:
             return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        t = torch.tensor([v], dtype=torch.float64,
+                         device=device if device is not None else "cpu")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
+
+    return barrier, max_over_ranks
+
+
+def whole_job_value(units_per_step: float, steps: int, world: int, max_elapsed_ms: float) -> float:
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return world * units_per_step * steps / (max_elapsed_ms / 1e3)
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import __graft_entry__
+    from paper_1802_01685_gb300 import bf, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    barrier, max_over_ranks = make_dist(world, "nccl", torch.device("cuda", local))
 
     w = synth.gw_pair()
     fs, M = w["fs"], w["M"]
@@ -205,7 +224,7 @@ def run_ours(args, rank, world, local):
     barrier()
     elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1))
     ms_per_step = elapsed_ms / args.steps
-    value = world * corr_per_step * args.steps / (elapsed_ms / 1e3)
+    value = whole_job_value(corr_per_step, args.steps, world, elapsed_ms)
 
     # roofline of the dominant kernel (the split-BF16 tcgen05 correlation)
     peaks = measured_peaks()
@@ -382,11 +401,42 @@ def run_serve(ctx, bf, synth, args):
     s = bf.bf_serve_stats_get(ctx)
     for b in banks.values():
         bf.bf_bank_destroy(b)
-    return {"requests": len(reqs), "rate_hz": args.serve_rate, "p50_ms": round(s.p50_ms, 2),
-            "p99_ms": round(s.p99_ms, 2), "sustained_correlations_per_s": corr / wall,
-            "busy_correlations_per_s": s.correlations_per_s, "launches": int(s.launches),
-            "precision": "split_bf16",
-            "stream": "seeded Poisson arrivals; 4-64 s series; 2048/4096 Hz; 2^12-2^16 templates"}
+    out = {"requests": len(reqs), "rate_hz": args.serve_rate, "p50_ms": round(s.p50_ms, 2),
+           "p99_ms": round(s.p99_ms, 2), "sustained_correlations_per_s": corr / wall,
+           "busy_correlations_per_s": s.correlations_per_s, "launches": int(s.launches),
+           "precision": "split_bf16",
+           "stream": "seeded Poisson arrivals; 4-64 s series; 2048/4096 Hz; 2^12-2^16 templates"}
+    if not args.no_fp32:
+        out["fp32_one_at_a_time"] = run_serve_fp32_baseline(ctx, bf, synth, reqs, series)
+    return out
+
+
+def run_serve_fp32_baseline(ctx, bf, synth, reqs, series):
+    """The same stream, replayed in real time through the plain FP32 path one
+    request at a time (each waits for the previous one); latency from arrival."""
+    banks = {}
+    for fs in (2048.0, 4096.0):
+        spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0],
+                               20.0, min(1000.0, fs / 2 - 24), 128, 128)
+        banks[fs] = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_FP32)
+    lat, corr = [], 0.0
+    t0 = time.perf_counter()
+    for r, x in zip(reqs, series):
+        while time.perf_counter() - t0 < r["arrival_s"]:
+            time.sleep(0.0005)
+        res = bf.bf_correlate(ctx, banks[r["fs"]], [x], r["fs"],
+                              bf.make_opts(precision="fp32", bank_end=r["n_templates"]))
+        bf.bf_result_copy_to_host(res, 0)
+        bf.bf_result_destroy(res)
+        lat.append(1e3 * (time.perf_counter() - t0 - r["arrival_s"]))
+        corr += (len(x) - int(r["fs"]) + 1) * r["n_templates"]
+    wall = time.perf_counter() - t0
+    for b in banks.values():
+        bf.bf_bank_destroy(b)
+    lat = np.sort(np.array(lat))
+    pct = lambda q: float(lat[min(len(lat) - 1, int(np.ceil(q * len(lat))) - 1)])
+    return {"p50_ms": round(pct(0.5), 2), "p99_ms": round(pct(0.99), 2),
+            "sustained_correlations_per_s": corr / wall}
 
 
 # ------------------------------------------------------------------ reference arm

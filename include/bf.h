@@ -176,6 +176,7 @@ typedef struct {
                                 full filter output rho[k - bank_begin][tau]
                                 (n_templates x L floats, row-major) is written
                                 here as well.  For inspection of small cases. */
+    int32_t want_tails;      /* keep the list of tails (see bf_result_tails)   */
 } bf_opts;
 
 void bf_opts_default(bf_opts* opts);
@@ -224,6 +225,24 @@ bf_status bf_result_copy_to_host(const bf_result* r, size_t s, float* vmax,
                                  int32_t* argmax, float* sigma, uint32_t* hist,
                                  float* map);
 bf_status bf_result_copy_mean_max(const bf_result* r, float* host_mean_max);
+
+/*
+ * Tails of the filter output (Sect. 2.2: only the tails rho > kappa sigma are
+ * handed on from the GPU): every (series, k, tau) with |rho| >= the call's
+ * threshold kappa / sqrt(M), with its signed rho.  Kept when opts.want_tails
+ * or opts.want_map is set, up to bf_config.max_candidates entries per call
+ * (bf_result_info.candidates_overflow tells when more were found); the order
+ * is unspecified.  bf_result_tails gives the device array; copy_tails copies
+ * at most cap entries to host memory and reports the count kept.
+ */
+typedef struct {
+    uint32_t series;   /* index into the call's series                       */
+    uint32_t k;        /* absolute template index in the bank                */
+    uint32_t tau;      /* lag                                                */
+    float rho;         /* normalised correlation                             */
+} bf_tail;
+bf_status bf_result_tails(const bf_result* r, const bf_tail** tails, size_t* count);
+bf_status bf_result_copy_tails(const bf_result* r, bf_tail* host, size_t cap, size_t* count);
 void bf_result_destroy(bf_result* r);
 
 /*

@@ -59,7 +59,12 @@ class bf_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("bank_begin", C.c_size_t),
                 ("bank_end", C.c_size_t), ("kappa", C.c_double), ("map_dt_s", C.c_double),
                 ("map_df_hz", C.c_double), ("want_map", C.c_int32), ("want_hist", C.c_int32),
-                ("hist_bins", C.c_uint32), ("stream", C.c_void_p), ("rho_out", C.c_void_p)]
+                ("hist_bins", C.c_uint32), ("stream", C.c_void_p), ("rho_out", C.c_void_p),
+                ("want_tails", C.c_int32)]
+
+
+class bf_tail(C.Structure):
+    _fields_ = [("series", C.c_uint32), ("k", C.c_uint32), ("tau", C.c_uint32), ("rho", C.c_float)]
 
 
 class bf_result_info(C.Structure):
@@ -120,6 +125,8 @@ def load() -> C.CDLL:
             "bf_result_get_mean_max": (i, [p, P(p)]),
             "bf_result_copy_to_host": (i, [p, s, p, p, p, p, p]),
             "bf_result_copy_mean_max": (i, [p, p]),
+            "bf_result_tails": (i, [p, P(p), P(s)]),
+            "bf_result_copy_tails": (i, [p, p, s, P(s)]),
             "bf_result_destroy": (None, [p]),
             "bf_control_randomize": (i, [p, p, s, u64, p]),
             "bf_control_randomize_static": (i, [p, s, u64, p, p]),
@@ -231,7 +238,7 @@ def bf_opts_default() -> bf_opts:
 
 def make_opts(precision=BF_SPLIT_BF16, bank_begin=0, bank_end=0, kappa=5.0, map_dt_s=1e-3,
               map_df_hz=4.0, want_map=False, want_hist=True, hist_bins=1024,
-              stream=None, rho_out=None) -> bf_opts:
+              stream=None, rho_out=None, want_tails=False) -> bf_opts:
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     o = bf_opts_default()
@@ -246,6 +253,7 @@ def make_opts(precision=BF_SPLIT_BF16, bank_begin=0, bank_end=0, kappa=5.0, map_
     o.hist_bins = hist_bins
     o.stream = stream
     o.rho_out = _addr(rho_out) if rho_out is not None else None
+    o.want_tails = int(bool(want_tails))
     return o
 
 
@@ -320,6 +328,26 @@ def bf_result_copy_mean_max(res: int) -> np.ndarray:
     K = bf_result_info_get(res).n_templates
     out = np.zeros(K, np.float32)
     _check(load().bf_result_copy_mean_max(res, out.ctypes.data))
+    return out
+
+
+TAIL_DTYPE = np.dtype([("series", np.uint32), ("k", np.uint32), ("tau", np.uint32),
+                       ("rho", np.float32)])
+
+
+def bf_result_tails(res: int):
+    """(device address, count) of the kept tails."""
+    a, n = C.c_void_p(), C.c_size_t()
+    _check(load().bf_result_tails(res, C.byref(a), C.byref(n)))
+    return a.value, n.value
+
+
+def bf_result_copy_tails(res: int) -> np.ndarray:
+    n = C.c_size_t()
+    _check(load().bf_result_copy_tails(res, None, 0, C.byref(n)))
+    out = np.zeros(n.value, TAIL_DTYPE)
+    if n.value:
+        _check(load().bf_result_copy_tails(res, out.ctypes.data, n.value, C.byref(n)))
     return out
 
 

@@ -360,6 +360,7 @@ bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
     r->nbins = o.hist_bins;
     r->want_map = o.want_map != 0;
     r->want_hist = o.want_hist != 0;
+    r->want_tails = o.want_tails != 0;
     r->lengths = lengths;
     r->thr = (float)(o.kappa / std::sqrt((double)bank->M));
     Allocator& mem = *ctx->mem;
@@ -371,7 +372,7 @@ bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
     r->sigma = static_cast<float*>(mem.alloc(S * K * 4));
     r->mean_max = static_cast<float*>(mem.alloc(K * 4));
     r->cand_cap = (unsigned int)std::min<size_t>(ctx->cfg.max_candidates, 0xFFFFFFF0u);
-    if (!r->want_map) r->cand_cap = 0;
+    if (!r->want_map && !r->want_tails) r->cand_cap = 0;
     r->cand = static_cast<Candidate*>(mem.alloc(std::max<size_t>(r->cand_cap, 1) * sizeof(Candidate)));
     r->cand_count = static_cast<unsigned int*>(mem.alloc(sizeof(unsigned int)));
     bool ok = r->packed && r->sumsq && r->vmax && r->argmax && r->sigma && r->mean_max && r->cand &&
@@ -420,8 +421,9 @@ size_t result_bytes(const bf_bank* bank, const bf_opts& o, size_t N, double fs, 
     if (o.want_map) {
         uint32_t nt, nf;
         map_shape(N, fs, o.map_dt_s, o.map_df_hz, &nt, &nf);
-        b += (size_t)nt * nf * 4 + max_cand * sizeof(Candidate);
+        b += (size_t)nt * nf * 4;
     }
+    if (o.want_map || o.want_tails) b += max_cand * sizeof(Candidate);
     (void)bank;
     return b;
 }
@@ -1012,6 +1014,39 @@ bf_status bf_result_copy_mean_max(const bf_result* r, float* out)
     cudaSetDevice(r->ctx->device);
     cudaError_t e = cudaMemcpy(out, r->mean_max, r->K * 4, cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? BF_OK : cuda_fail(e, "result copy");
+}
+
+static size_t kept_tails(const bf_result* r)
+{
+    uint64_t n = r->n_candidates;
+    if (r->cand_count) {
+        unsigned int c = 0;
+        if (cudaMemcpy(&c, r->cand_count, sizeof c, cudaMemcpyDeviceToHost) == cudaSuccess) n = c;
+    }
+    return (size_t)std::min<uint64_t>(n, r->cand_cap);
+}
+
+bf_status bf_result_tails(const bf_result* r, const bf_tail** tails, size_t* count)
+{
+    if (!r || !tails || !count) { set_error("NULL argument"); return BF_EINVAL; }
+    if (r->cand_cap == 0) { set_error("tails were not requested (opts.want_tails)"); return BF_EINVAL; }
+    static_assert(sizeof(bf_tail) == sizeof(Candidate), "tail record layout");
+    cudaSetDevice(r->ctx->device);
+    *tails = reinterpret_cast<const bf_tail*>(r->cand);
+    *count = kept_tails(r);
+    return BF_OK;
+}
+
+bf_status bf_result_copy_tails(const bf_result* r, bf_tail* host, size_t cap, size_t* count)
+{
+    const bf_tail* dev = nullptr;
+    size_t n = 0;
+    bf_status st = bf_result_tails(r, &dev, &n);
+    if (st) return st;
+    if (count) *count = n;
+    if (!host || cap == 0 || n == 0) return BF_OK;
+    cudaError_t e = cudaMemcpy(host, dev, std::min(n, cap) * sizeof(bf_tail), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? BF_OK : cuda_fail(e, "tail copy");
 }
 
 void bf_result_destroy(bf_result* r)

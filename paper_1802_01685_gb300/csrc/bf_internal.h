@@ -204,7 +204,7 @@ struct bf_result {
     size_t n_series = 0, K = 0, k_begin = 0;
     uint32_t M = 0, nbins = 0;
     double fs = 0, dt = 0, df = 0;
-    bool want_map = false, want_hist = false;
+    bool want_map = false, want_hist = false, want_tails = false;
     std::vector<size_t> lengths;
     std::vector<uint32_t> map_nt;
     uint32_t map_nf = 0;

@@ -39,7 +39,8 @@ def tiny(ctx):
 def test_bank_templates_match_oracle(ctx):
     chirps = [(bf.BF_LINEAR, bf.BF_ASC, 50.0, 1000.0, 1.0), (bf.BF_LINEAR, bf.BF_DESC, 600.0, 700.0, 0.2),
               (bf.BF_POWERLAW, bf.BF_ASC, 20.0, 1000.0, 0.2), (bf.BF_POWERLAW, bf.BF_DESC, 40.0, 400.0, 1.0),
-              (bf.BF_POWERLAW, bf.BF_ASC, 999.0, 1000.0, 0.55), (bf.BF_LINEAR, bf.BF_ASC, 1.0, 2.0, 0.37)]
+              (bf.BF_POWERLAW, bf.BF_ASC, 999.0, 1000.0, 0.55), (bf.BF_LINEAR, bf.BF_ASC, 1.0, 2.0, 0.37),
+              (bf.BF_POWERLAW, bf.BF_ASC, 2.0, 1000.0, 1.0), (bf.BF_POWERLAW, bf.BF_DESC, 30.0, 1000.0, 0.3)]
     fs, T = 2048.0, 1.0
     for storage in (bf.BF_BANK_FP32, bf.BF_BANK_SPLIT_BF16):
         bank = bf.bf_bank_create(ctx, chirps, fs, T, storage)
@@ -132,6 +133,35 @@ def test_tiny_tf_map(ctx, tiny, prec):
     assert info.candidates_overflow == 0 and info.n_candidates > 0
     n_ref, n_gpu = check_map(outs[0]["map"], x, fs, p, M, kappa, TOL[prec])
     assert n_gpu > 0
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16"])
+def test_tiny_tails(ctx, tiny, prec):
+    """The tail list holds every (k, tau) with |rho| >= thr + tol, nothing
+    below thr - tol, each with its rho within tol."""
+    w, bank, p, ref = tiny
+    x, fs, M = w["series"][0], w["fs"], w["M"]
+    kappa, tol = 3.5, TOL[prec]
+    thr = kappa / np.sqrt(M)
+    res = bf.bf_correlate(ctx, bank, [x], fs, bf.make_opts(precision=prec, want_tails=True,
+                                                           kappa=kappa))
+    info = bf.bf_result_info_get(res)
+    tails = bf.bf_result_copy_tails(res)
+    bf.bf_result_destroy(res)
+    assert info.candidates_overflow == 0 and len(tails) == info.n_candidates
+    a = np.abs(ref["rho"])
+    got = {(int(t["k"]), int(t["tau"])): float(t["rho"]) for t in tails}
+    assert len(got) == len(tails)                                 # no duplicates
+    must = set(zip(*[v.tolist() for v in np.nonzero(a >= thr + tol)]))
+    may = set(zip(*[v.tolist() for v in np.nonzero(a >= thr - tol)]))
+    assert must <= set(got) <= may
+    for (k, tau), r in got.items():
+        assert abs(r - ref["rho"][k, tau]) <= tol
+    assert np.all(tails["series"] == 0)
+    res = bf.bf_correlate(ctx, bank, [x], fs, bf.make_opts(precision=prec))
+    with pytest.raises(bf.BFError):
+        bf.bf_result_tails(res)                                   # not requested
+    bf.bf_result_destroy(res)
 
 
 def test_injection_recovered(ctx):
