@@ -246,6 +246,27 @@ bf_status bf_result_copy_tails(const bf_result* r, bf_tail* host, size_t cap, si
 void bf_result_destroy(bf_result* r);
 
 /*
+ * Search plans: a fixed search shape replayed as one CUDA graph.
+ * bf_plan_create fixes the bank, the template range, the number and lengths of
+ * the series, the rate and the options (opts.stream and opts.rho_out are
+ * ignored), allocates every buffer once and captures the device work of one
+ * search -- clearing the outputs, series preparation, the batched correlation,
+ * finalize, histogram and map -- into a CUDA graph.  bf_plan_run copies new
+ * series (host or device pointers, the lengths given at creation) into the
+ * plan and launches the graph on `stream` (NULL: synchronously on the
+ * context stream).  *out points at the plan's result: valid until the next run
+ * or bf_plan_destroy, read with the bf_result_* calls, never destroyed by the
+ * caller.  Stored banks only (BF_ENOTSUP for a generated bank).  Runs of one
+ * plan must not overlap on the GPU.
+ */
+typedef struct bf_plan bf_plan;
+bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths,
+                         size_t n_series, double fs, const bf_opts* opts, bf_plan** out);
+bf_status bf_plan_run(bf_plan* plan, const float* const* series, void* stream,
+                      const bf_result** out);
+void bf_plan_destroy(bf_plan* plan);
+
+/*
  * Time-randomised control (Sect. 2.2 and Fig. 2: maximal-entropy data with
  * the same sample histogram).  out[j] = in[pi(j)] with pi the argsort of the
  * pairs (splitmix64(seed XOR i), i), i = 0..n-1; splitmix64 is the published

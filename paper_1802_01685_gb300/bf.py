@@ -128,6 +128,9 @@ def load() -> C.CDLL:
             "bf_result_tails": (i, [p, P(p), P(s)]),
             "bf_result_copy_tails": (i, [p, p, s, P(s)]),
             "bf_result_destroy": (None, [p]),
+            "bf_plan_create": (i, [p, p, P(s), s, d, P(bf_opts), P(p)]),
+            "bf_plan_run": (i, [p, P(p), p, P(p)]),
+            "bf_plan_destroy": (None, [p]),
             "bf_control_randomize": (i, [p, p, s, u64, p]),
             "bf_control_randomize_static": (i, [p, s, u64, p, p]),
             "bf_serve_submit": (i, [p, P(bf_request), P(u64)]),
@@ -353,6 +356,29 @@ def bf_result_copy_tails(res: int) -> np.ndarray:
 
 def bf_result_destroy(res: int) -> None:
     load().bf_result_destroy(res)
+
+
+# ---------------------------------------------------------------- plans
+def bf_plan_create(ctx: int, bank: int, lengths, fs: float, opts: bf_opts | None = None) -> int:
+    n = len(lengths)
+    lens = (C.c_size_t * n)(*lengths)
+    h = C.c_void_p()
+    _check(load().bf_plan_create(ctx, bank, lens, n, fs,
+                                 C.byref(opts) if opts is not None else None, C.byref(h)))
+    return h.value
+
+
+def bf_plan_run(plan: int, series, stream=None) -> int:
+    """Returns the plan's result handle (owned by the plan; do not destroy)."""
+    n = len(series)
+    ptrs = (C.c_void_p * n)(*[_addr(x) for x in series])
+    h = C.c_void_p()
+    _check(load().bf_plan_run(plan, ptrs, stream, C.byref(h)))
+    return h.value
+
+
+def bf_plan_destroy(plan: int) -> None:
+    load().bf_plan_destroy(plan)
 
 
 # ---------------------------------------------------------------- control

@@ -112,7 +112,7 @@ bool Allocator::fits(size_t bytes) const
 }
 
 // ---------------------------------------------------------------- helpers
-static bool is_device_ptr(const void* p)
+bool is_device_ptr(const void* p)
 {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -122,7 +122,7 @@ static bool is_device_ptr(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
 uint32_t template_len(double T, double fs) { return (uint32_t)std::floor(T * fs + 0.5); }
 
@@ -161,8 +161,8 @@ void PreparedSeries::release(Allocator& mem)
     owned.clear();
 }
 
-bf_status prepare_series(bf_ctx* ctx, const float* src, size_t N, uint32_t M, uint32_t M_pad,
-                         int precision, cudaStream_t st, PreparedSeries* out)
+bf_status prepare_series_alloc(bf_ctx* ctx, size_t N, uint32_t M, uint32_t M_pad, int precision,
+                               PreparedSeries* out)
 {
     PreparedSeries& ps = *out;
     ps.N = N;
@@ -173,35 +173,46 @@ bf_status prepare_series(bf_ctx* ctx, const float* src, size_t N, uint32_t M, ui
         if (p) ps.owned.push_back(p);
         return p;
     };
-    const uint64_t n_lt_simt = ceil_div(ps.L, SIMT_TILE_L);
-    const uint64_t xcap = n_lt_simt * SIMT_TILE_L + M_pad + 1024;
-    ps.x = static_cast<float*>(grab(xcap * sizeof(float)));
+    ps.xcap = ceil_div(ps.L, SIMT_TILE_L) * SIMT_TILE_L + M_pad + 1024;
+    ps.x = static_cast<float*>(grab(ps.xcap * sizeof(float)));
     ps.inv = static_cast<float*>(grab((size_t)ps.L * sizeof(float)));
-    const uint64_t nb = inv_norm_scratch_blocks(N);
-    double* prefix = static_cast<double*>(grab((N + 1) * sizeof(double)));
-    double* bsum = static_cast<double*>(grab(nb * sizeof(double)));
-    if (!ps.x || !ps.inv || !prefix || !bsum) {
+    ps.nb = inv_norm_scratch_blocks(N);
+    ps.prefix = static_cast<double*>(grab((N + 1) * sizeof(double)));
+    ps.bsum = static_cast<double*>(grab(ps.nb * sizeof(double)));
+    bool ok = ps.x && ps.inv && ps.prefix && ps.bsum;
+    if (ok && precision != BF_FP32) {
+        ps.rows = ceil_div(ps.L, TC_TILE_L) * TC_TILE_L + M_pad + 64;
+        ps.yhi = static_cast<uint4*>(grab(ps.rows * 16));
+        ps.ylo = static_cast<uint4*>(grab(ps.rows * 16));
+        ok = ps.yhi && ps.ylo;
+    }
+    if (!ok) {
         ps.release(mem);
         set_error("out of device memory preparing a series of %zu samples", N);
         return BF_ENOMEM;
     }
-    cudaError_t e = cudaMemcpyAsync(ps.x, src, N * sizeof(float), cudaMemcpyDefault, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ps.x + N, 0, (xcap - N) * sizeof(float), st);
-    if (e == cudaSuccess) e = launch_inv_norm(ps.x, N, M, prefix, bsum, nb, ps.inv, st);
-    if (e == cudaSuccess && precision != BF_FP32) {
-        const uint64_t n_lt = ceil_div(ps.L, TC_TILE_L);
-        const uint64_t rows = n_lt * TC_TILE_L + M_pad + 64;
-        ps.yhi = static_cast<uint4*>(grab(rows * 16));
-        ps.ylo = static_cast<uint4*>(grab(rows * 16));
-        if (!ps.yhi || !ps.ylo) {
-            ps.release(mem);
-            set_error("out of device memory for split rows");
-            return BF_ENOMEM;
-        }
-        e = launch_split_rows(ps.x, N, rows, ps.yhi, ps.ylo, st);
-    }
+    return BF_OK;
+}
+
+cudaError_t prepare_series_kernels(const PreparedSeries& ps, uint32_t M, int precision,
+                                   cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(ps.x + ps.N, 0, (ps.xcap - ps.N) * sizeof(float), st);
+    if (e == cudaSuccess) e = launch_inv_norm(ps.x, ps.N, M, ps.prefix, ps.bsum, ps.nb, ps.inv, st);
+    if (e == cudaSuccess && precision != BF_FP32)
+        e = launch_split_rows(ps.x, ps.N, ps.rows, ps.yhi, ps.ylo, st);
+    return e;
+}
+
+bf_status prepare_series(bf_ctx* ctx, const float* src, size_t N, uint32_t M, uint32_t M_pad,
+                         int precision, cudaStream_t st, PreparedSeries* out)
+{
+    bf_status s = prepare_series_alloc(ctx, N, M, M_pad, precision, out);
+    if (s) return s;
+    cudaError_t e = cudaMemcpyAsync(out->x, src, N * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = prepare_series_kernels(*out, M, precision, st);
     if (e != cudaSuccess) {
-        ps.release(mem);
+        out->release(*ctx->mem);
         return cuda_fail(e, "series preparation");
     }
     return BF_OK;
@@ -243,7 +254,7 @@ Seg make_segment(const PreparedSeries& ps, uint32_t series_id, const bf_bank* ba
 }
 
 // One segment per series over the whole template range.
-static void build_segments(const std::vector<PreparedSeries*>& ser, const std::vector<uint32_t>& ids,
+void build_segments(const std::vector<PreparedSeries*>& ser, const std::vector<uint32_t>& ids,
                            const bf_bank* bank, size_t k_begin, size_t k_end, int precision,
                            unsigned long long* packed, double* sumsq, size_t K,
                            std::vector<Seg>& segs)
@@ -400,11 +411,8 @@ bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
         set_error("out of device memory for the result buffers");
         return BF_ENOMEM;
     }
-    cudaError_t e = cudaMemsetAsync(r->packed, 0, S * K * 8, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(r->sumsq, 0, S * K * 8, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(r->cand_count, 0, sizeof(unsigned int), st);
-    if (e == cudaSuccess && r->hist) e = cudaMemsetAsync(r->hist, 0, S * r->nbins * 4, st);
-    if (e == cudaSuccess && r->map) e = cudaMemsetAsync(r->map, 0, map_total * 4, st);
+    r->map_total = map_total;
+    cudaError_t e = clear_result(r.get(), st);
     if (e != cudaSuccess) {
         free_result_buffers(r.get());
         return cuda_fail(e, "clearing result buffers");
@@ -426,6 +434,18 @@ size_t result_bytes(const bf_bank* bank, const bf_opts& o, size_t N, double fs, 
     if (o.want_map || o.want_tails) b += max_cand * sizeof(Candidate);
     (void)bank;
     return b;
+}
+
+// Zeroes what the kernels accumulate into.
+cudaError_t clear_result(bf_result* r, cudaStream_t st)
+{
+    const size_t S = r->n_series, K = r->K;
+    cudaError_t e = cudaMemsetAsync(r->packed, 0, S * K * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->sumsq, 0, S * K * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->cand_count, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess && r->hist) e = cudaMemsetAsync(r->hist, 0, S * r->nbins * 4, st);
+    if (e == cudaSuccess && r->map) e = cudaMemsetAsync(r->map, 0, r->map_total * 4, st);
+    return e;
 }
 
 // Finalize kernels for a result whose correlation launches are enqueued.

@@ -92,10 +92,13 @@ struct CorrParams {
 // ---------------------------------------------------------------- launchers
 // Process-wide count of kernel launches made by this library.
 extern std::atomic<uint64_t> g_launches;
+bf_status cuda_fail(cudaError_t e, const char* what);
 inline void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 cudaError_t launch_corr_simt(const CorrParams& p, cudaStream_t s);
 cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int n_sm, cudaStream_t s);
+// sets the tensor-core kernels' shared-memory attribute (outside graph capture)
+cudaError_t corr_tc_set_attributes();
 
 struct ChirpDev {                   // device copy of a template's parameters
     int32_t track, sense;
@@ -217,6 +220,7 @@ struct bf_result {
     uint32_t* hist = nullptr;               // [S][nbins]
     float* map = nullptr;                   // concatenated per-series maps
     std::vector<size_t> map_off;            // element offsets into map
+    size_t map_total = 0;
     float* mean_max = nullptr;              // [K]
     bfi::Candidate* cand = nullptr;
     unsigned int* cand_count = nullptr;

@@ -515,18 +515,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
     }
 }
 
-cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int n_sm, cudaStream_t st)
+static bool g_attr_done[2] = {false, false};
+
+cudaError_t corr_tc_set_attributes()
 {
-    if (p.total_tiles == 0) return cudaSuccess;
-    static bool attr_done[2] = {false, false};
-    const int which = nprod == 3 ? 1 : 0;
-    auto kern = nprod == 3 ? k_corr_tc<3> : k_corr_tc<1>;
-    if (!attr_done[which]) {
+    for (int which = 0; which < 2; ++which) {
+        if (g_attr_done[which]) continue;
+        auto kern = which == 1 ? k_corr_tc<3> : k_corr_tc<1>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        attr_done[which] = true;
+        g_attr_done[which] = true;
     }
+    return cudaSuccess;
+}
+
+cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int n_sm, cudaStream_t st)
+{
+    if (p.total_tiles == 0) return cudaSuccess;
+    auto kern = nprod == 3 ? k_corr_tc<3> : k_corr_tc<1>;
+    cudaError_t ea = corr_tc_set_attributes();
+    if (ea != cudaSuccess) return ea;
     uint64_t grid = p.total_tiles < (uint64_t)n_sm ? p.total_tiles : (uint64_t)n_sm;
     count_launches(1);
     kern<<<(unsigned)grid, TC_THREADS, SMEM_BYTES, st>>>(p);

@@ -17,12 +17,27 @@ struct PreparedSeries {
     float* inv = nullptr;           // [L] inverse window norms
     uint4* yhi = nullptr;           // split rows (tensor-core path)
     uint4* ylo = nullptr;
+    double* prefix = nullptr;       // FP64 prefix of x^2 (scratch)
+    double* bsum = nullptr;         // scan block sums (scratch)
+    uint64_t xcap = 0, nb = 0, rows = 0;
     std::vector<void*> owned;       // every buffer, prefix scratch included
     void release(Allocator& mem);
 };
 
 bf_status prepare_series(bf_ctx* ctx, const float* src, size_t N, uint32_t M, uint32_t M_pad,
                          int precision, cudaStream_t st, PreparedSeries* out);
+// the two halves of prepare_series: buffers, then the kernels that fill them
+// from ps.x[0..N)
+bf_status prepare_series_alloc(bf_ctx* ctx, size_t N, uint32_t M, uint32_t M_pad, int precision,
+                               PreparedSeries* out);
+cudaError_t prepare_series_kernels(const PreparedSeries& ps, uint32_t M, int precision,
+                                   cudaStream_t st);
+void build_segments(const std::vector<PreparedSeries*>& ser, const std::vector<uint32_t>& ids,
+                    const bf_bank* bank, size_t k_begin, size_t k_end, int precision,
+                    unsigned long long* packed, double* sumsq, size_t K, std::vector<Seg>& segs);
+bool is_device_ptr(const void* p);
+uint64_t ceil_div(uint64_t a, uint64_t b);
+cudaError_t clear_result(bf_result* r, cudaStream_t st);
 size_t prepared_series_bytes(size_t N, uint32_t M, uint32_t M_pad, int precision);
 
 // Template-tile geometry of a precision's kernel.

@@ -1,0 +1,92 @@
+"""Search plans: one search shape captured as a CUDA graph and replayed on new
+series must give what bf_correlate gives for the same inputs."""
+import numpy as np
+import pytest
+
+from paper_1802_01685_gb300 import bf, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import __graft_entry__
+    __graft_entry__.build()
+    ctx = bf.bf_init()
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0, 0.5],
+                           20.0, 1000.0, 8, 12)                  # 768 templates
+    bank = bf.bf_bank_create_grid(ctx, spec, 2048.0, 1.0)
+    yield ctx, bank, spec
+    bf.bf_bank_destroy(bank)
+    bf.bf_destroy(ctx)
+
+
+def outputs(res, n, want_map):
+    return [bf.bf_result_copy_to_host(res, s, want_hist=True, want_map=want_map) for s in range(n)]
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16"])
+def test_plan_replays_equal_correlate(setup, prec):
+    ctx, bank, spec = setup
+    lens = [2048, 5000, 9000, 2049]
+    opts = bf.make_opts(precision=prec, bank_begin=10, bank_end=700, want_map=True, kappa=4.0,
+                        want_tails=True)
+    plan = bf.bf_plan_create(ctx, bank, lens, 2048.0, opts)
+    try:
+        for run in range(3):
+            rng = np.random.default_rng(100 + run)
+            xs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+            res = bf.bf_plan_run(plan, xs)
+            got = outputs(res, len(lens), True)
+            got_mean = bf.bf_result_copy_mean_max(res)
+            got_tails = np.sort(bf.bf_result_copy_tails(res), order=["series", "k", "tau"])
+            ref_h = bf.bf_correlate(ctx, bank, xs, 2048.0, opts)
+            ref = outputs(ref_h, len(lens), True)
+            ref_mean = bf.bf_result_copy_mean_max(ref_h)
+            ref_tails = np.sort(bf.bf_result_copy_tails(ref_h), order=["series", "k", "tau"])
+            bf.bf_result_destroy(ref_h)
+            for g, r in zip(got, ref):
+                np.testing.assert_array_equal(g["max"], r["max"])
+                np.testing.assert_array_equal(g["argmax"], r["argmax"])
+                np.testing.assert_allclose(g["sigma"], r["sigma"], rtol=1e-6)
+                np.testing.assert_array_equal(g["hist"], r["hist"])
+                np.testing.assert_array_equal(g["map"], r["map"])
+            np.testing.assert_array_equal(got_mean, ref_mean)
+            np.testing.assert_array_equal(got_tails, ref_tails)
+    finally:
+        bf.bf_plan_destroy(plan)
+
+
+def test_plan_on_a_stream_and_launch_count(setup):
+    ctx, bank, spec = setup
+    lens = [4096, 3000]
+    plan = bf.bf_plan_create(ctx, bank, lens, 2048.0, bf.make_opts())
+    rng = np.random.default_rng(7)
+    xs = [torch.from_numpy(rng.standard_normal(n).astype(np.float32)).cuda() for n in lens]
+    s = torch.cuda.Stream()
+    n0 = bf.bf_kernel_launches()
+    res = bf.bf_plan_run(plan, xs, s.cuda_stream)
+    s.synchronize()
+    assert bf.bf_kernel_launches() - n0 >= 2 * 5 + 3            # prep per series, correlation, finalize
+    got = outputs(res, 2, False)
+    ref_h = bf.bf_correlate(ctx, bank, xs, 2048.0, bf.make_opts())
+    ref = outputs(ref_h, 2, False)
+    bf.bf_result_destroy(ref_h)
+    for g, r in zip(got, ref):
+        np.testing.assert_array_equal(g["max"], r["max"])
+        np.testing.assert_array_equal(g["argmax"], r["argmax"])
+    bf.bf_plan_destroy(plan)
+
+
+def test_plan_rejects_generated_bank_and_bad_lengths(setup):
+    ctx, bank, spec = setup
+    gen = bf.bf_bank_create_grid(ctx, spec, 2048.0, 1.0, bf.BF_BANK_GENERATED)
+    with pytest.raises(bf.BFError) as e:
+        bf.bf_plan_create(ctx, gen, [4096], 2048.0)
+    assert e.value.status == bf.BF_ENOTSUP
+    bf.bf_bank_destroy(gen)
+    with pytest.raises(bf.BFError) as e:
+        bf.bf_plan_create(ctx, bank, [100], 2048.0)
+    assert e.value.status == bf.BF_EINVAL
