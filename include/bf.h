@@ -177,6 +177,12 @@ typedef struct {
                                 (n_templates x L floats, row-major) is written
                                 here as well.  For inspection of small cases. */
     int32_t want_tails;      /* keep the list of tails (see bf_result_tails)   */
+    int32_t tile_lags;       /* lags per tensor-core tile: 512 (one TMEM
+                                accumulator) or 256 (two, so the epilogue of
+                                one tile overlaps the MMAs of the next); 0 =
+                                chosen by the library's autotuner, which times
+                                both once per precision and template length
+                                per context.  Ignored by BF_FP32.            */
 } bf_opts;
 
 void bf_opts_default(bf_opts* opts);
@@ -206,6 +212,7 @@ typedef struct {
     float threshold;               /* kappa / sqrt(M)                           */
     uint32_t hist_bins;
     double kernel_ms;              /* correlation kernel time (synchronous calls) */
+    int32_t tile_lags;             /* lags per tile of the kernel that ran      */
 } bf_result_info;
 
 bf_status bf_result_info_get(const bf_result* r, bf_result_info* info);

@@ -60,7 +60,7 @@ class bf_opts(C.Structure):
                 ("bank_end", C.c_size_t), ("kappa", C.c_double), ("map_dt_s", C.c_double),
                 ("map_df_hz", C.c_double), ("want_map", C.c_int32), ("want_hist", C.c_int32),
                 ("hist_bins", C.c_uint32), ("stream", C.c_void_p), ("rho_out", C.c_void_p),
-                ("want_tails", C.c_int32)]
+                ("want_tails", C.c_int32), ("tile_lags", C.c_int32)]
 
 
 class bf_tail(C.Structure):
@@ -72,7 +72,7 @@ class bf_result_info(C.Structure):
                 ("template_len", C.c_size_t), ("correlations", C.c_double),
                 ("useful_flops", C.c_double), ("n_candidates", C.c_uint64),
                 ("candidates_overflow", C.c_int32), ("threshold", C.c_float),
-                ("hist_bins", C.c_uint32), ("kernel_ms", C.c_double)]
+                ("hist_bins", C.c_uint32), ("kernel_ms", C.c_double), ("tile_lags", C.c_int32)]
 
 
 class bf_request(C.Structure):
@@ -241,7 +241,7 @@ def bf_opts_default() -> bf_opts:
 
 def make_opts(precision=BF_SPLIT_BF16, bank_begin=0, bank_end=0, kappa=5.0, map_dt_s=1e-3,
               map_df_hz=4.0, want_map=False, want_hist=True, hist_bins=1024,
-              stream=None, rho_out=None, want_tails=False) -> bf_opts:
+              stream=None, rho_out=None, want_tails=False, tile_lags=0) -> bf_opts:
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     o = bf_opts_default()
@@ -257,6 +257,7 @@ def make_opts(precision=BF_SPLIT_BF16, bank_begin=0, bank_end=0, kappa=5.0, map_
     o.stream = stream
     o.rho_out = _addr(rho_out) if rho_out is not None else None
     o.want_tails = int(bool(want_tails))
+    o.tile_lags = int(tile_lags)
     return o
 
 

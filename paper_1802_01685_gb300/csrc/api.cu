@@ -267,10 +267,79 @@ void build_segments(const std::vector<PreparedSeries*>& ser, const std::vector<u
                                     packed + (size_t)ids[i] * K, sumsq + (size_t)ids[i] * K));
 }
 
+// Times both tile shapes of the tensor-core kernel on a zero series (its cost
+// does not depend on the data) against up to 4 of the segment's template
+// tiles, two waves of tiles each, and keeps the faster one per context.
+int choose_lag_tile(bf_ctx* ctx, const Seg& g, int precision, cudaStream_t st)
+{
+    const std::pair<int, uint32_t> key(precision, g.M_pad);
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        auto it = ctx->tuned.find(key);
+        if (it != ctx->tuned.end()) return it->second;
+    }
+    const uint32_t ntt = std::min<uint32_t>(g.n_tt, 4);
+    const uint64_t L = (uint64_t)ctx->n_sm * TC_TILE_L * 2 / ntt + 1;
+    const uint64_t rows = ceil_div(L, TC_TILE_L) * TC_TILE_L + g.M_pad + 64;
+    Allocator& mem = *ctx->mem;
+    void* yh = mem.alloc(rows * 16);
+    void* yl = mem.alloc(rows * 16);
+    void* inv = mem.alloc(L * 4);
+    int best = TC_TILE_L;
+    if (yh && yl && inv) {
+        Seg t = g;
+        t.yhi = static_cast<const uint4*>(yh);
+        t.ylo = static_cast<const uint4*>(yl);
+        t.inv_norm = static_cast<const float*>(inv);
+        t.L = (uint32_t)L;
+        t.n_tt = ntt;
+        t.k_begin = t.k_end = 0;                  // no output is kept
+        t.rho = nullptr;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaError_t e = cudaMemsetAsync(yh, 0, rows * 16, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(yl, 0, rows * 16, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(inv, 0, L * 4, st);
+        float ms_best = 0.f;
+        for (int lt : {TC_TILE_L, TC_TILE_L / 2}) {
+            std::vector<Seg> one{t};
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                cudaEventRecord(e0, st);
+                e = launch_segments(ctx, one, precision, INFINITY, nullptr, nullptr, 0, st, nullptr, lt);
+                cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ms_min = std::min(ms_min, ms);      // first run warms up
+            }
+            if (e == cudaSuccess && (lt == TC_TILE_L || ms_min < ms_best)) {
+                if (lt != TC_TILE_L) best = lt;
+                ms_best = ms_min;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e != cudaSuccess) cudaGetLastError();
+        if (ctx->cfg.log_level > 0)
+            fprintf(stderr, "bf: autotune precision %d M_pad %u -> %d lags per tile\n", precision,
+                    g.M_pad, best);
+    }
+    mem.release(yh);
+    mem.release(yl);
+    mem.release(inv);
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    ctx->tuned[key] = best;
+    return best;
+}
+
 cudaError_t launch_segments(bf_ctx* ctx, const std::vector<Seg>& segs, int precision, float thr,
                             Candidate* cand, unsigned int* cand_count, unsigned int cand_cap,
-                            cudaStream_t st, uint64_t* tiles_out)
+                            cudaStream_t st, uint64_t* tiles_out, int lt)
 {
+    if (precision != BF_FP32 && lt == 0 && !segs.empty()) lt = choose_lag_tile(ctx, segs[0], precision, st);
+    if (precision == BF_FP32) lt = SIMT_TILE_L;
     uint64_t tiles = 0;
     for (size_t b = 0; b < segs.size(); b += MAX_SEG) {
         CorrParams p{};
@@ -278,6 +347,7 @@ cudaError_t launch_segments(bf_ctx* ctx, const std::vector<Seg>& segs, int preci
         uint64_t t = 0;
         for (int i = 0; i < p.n_seg; ++i) {
             p.seg[i] = segs[b + i];
+            p.seg[i].n_lag_tiles = (uint32_t)ceil_div(p.seg[i].L, (uint64_t)lt);
             p.seg[i].tile_begin = t;
             t += (uint64_t)p.seg[i].n_lag_tiles * p.seg[i].n_tt;
         }
@@ -289,7 +359,7 @@ cudaError_t launch_segments(bf_ctx* ctx, const std::vector<Seg>& segs, int preci
         p.err = ctx->d_err;
         cudaError_t e = precision == BF_FP32 ? launch_corr_simt(p, st)
                                              : launch_corr_tc(p, precision == BF_SPLIT_BF16 ? 3 : 1,
-                                                              ctx->n_sm, st);
+                                                              lt, ctx->n_sm, st);
         if (e != cudaSuccess) return e;
         tiles += t;
     }
@@ -345,6 +415,10 @@ bf_status resolve_opts(const bf_bank* bank, const bf_opts* in, bf_opts* o)
     }
     if (!bank->generated && o->precision != BF_FP32 && !bank->hi) {
         set_error("bank keeps no split-BF16 layout (create it with BF_BANK_SPLIT_BF16)");
+        return BF_EINVAL;
+    }
+    if (o->tile_lags != 0 && o->tile_lags != TC_TILE_L && o->tile_lags != TC_TILE_L / 2) {
+        set_error("tile_lags %d: use 0 (autotuned), 256 or 512", o->tile_lags);
         return BF_EINVAL;
     }
     if (!(o->kappa > 0.0)) o->kappa = 5.0;
@@ -489,7 +563,7 @@ bf_status finalize_result(bf_ctx* ctx, const bf_bank* bank, bf_result* r, cudaSt
 constexpr size_t GEN_SLOT_BYTES = 24u << 20;
 
 cudaError_t correlate_generated(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
-                                const std::vector<Seg>& segs, bf_result* r, cudaStream_t strm)
+                                const std::vector<Seg>& segs, bf_result* r, cudaStream_t strm, int lt)
 {
     const bool tc = o.precision != BF_FP32;
     const size_t tile_bytes = (size_t)TC_TILE_T * bank->M_pad * 4;     // hi+lo, or FP32
@@ -547,8 +621,12 @@ cudaError_t correlate_generated(bf_ctx* ctx, const bf_bank* bank, const bf_opts&
             g.bank_hi = tc ? static_cast<const uint8_t*>(slot[sl][0]) : nullptr;
             g.bank_lo = tc ? static_cast<const uint8_t*>(slot[sl][1]) : nullptr;
         }
+        if (lt == 0) {
+            lt = choose_lag_tile(ctx, cs[0], o.precision, strm);
+            r->tile_lags = lt;
+        }
         e = launch_segments(ctx, cs, o.precision, r->thr, r->cand, r->cand_count, r->cand_cap, strm,
-                            nullptr);
+                            nullptr, lt);
         if (e == cudaSuccess) e = cudaEventRecord(corr_done[sl], strm);
     }
     // events may be destroyed while pending work still references them
@@ -911,10 +989,15 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
         cudaEventCreate(&e1);
         cudaEventRecord(e0, strm);
     }
+    // lags per tile: fixed by the caller, else the autotuner's choice (for a
+    // generated bank it is made on the first synthesised chunk)
+    int lt = o.precision == BF_FP32 ? SIMT_TILE_L : o.tile_lags;
+    if (lt == 0 && !bank->generated) lt = choose_lag_tile(ctx, segs[0], o.precision, strm);
+    r->tile_lags = lt;
     cudaError_t e = bank->generated
-                        ? correlate_generated(ctx, bank, o, segs, r, strm)
+                        ? correlate_generated(ctx, bank, o, segs, r, strm, lt)
                         : launch_segments(ctx, segs, o.precision, r->thr, r->cand, r->cand_count,
-                                          r->cand_cap, strm, nullptr);
+                                          r->cand_cap, strm, nullptr, lt);
     if (sync) cudaEventRecord(e1, strm);
     if (e != cudaSuccess) {
         if (e0) { cudaEventDestroy(e0); cudaEventDestroy(e1); }
@@ -964,6 +1047,7 @@ bf_status bf_result_info_get(const bf_result* r, bf_result_info* info)
     info->threshold = r->thr;
     info->hist_bins = r->nbins;
     info->kernel_ms = r->kernel_ms;
+    info->tile_lags = r->tile_lags;
     return BF_OK;
 }
 

@@ -96,7 +96,7 @@ bf_status cuda_fail(cudaError_t e, const char* what);
 inline void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 cudaError_t launch_corr_simt(const CorrParams& p, cudaStream_t s);
-cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int n_sm, cudaStream_t s);
+cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int lt, int n_sm, cudaStream_t s);
 // sets the tensor-core kernels' shared-memory attribute (outside graph capture)
 cudaError_t corr_tc_set_attributes();
 
@@ -186,6 +186,8 @@ struct bf_ctx {
     int* d_err = nullptr;               // kernel status word
     std::mutex launch_mu;               // serialises use of d_err / stream
     bfi::ServeState* serve = nullptr;   // owned; freed by serve_shutdown
+    std::map<std::pair<int, uint32_t>, int> tuned;   // (precision, M_pad) -> lags per tile
+    std::mutex tune_mu;
 };
 
 struct bf_bank {
@@ -227,6 +229,7 @@ struct bf_result {
     unsigned int cand_cap = 0;
     uint64_t n_candidates = 0;
     float thr = 0;
+    int tile_lags = 0;
     double correlations = 0;
     double kernel_ms = 0;
     std::vector<void*> scratch;             // released at destroy

@@ -2,7 +2,8 @@
 // the fused epilogue.  The sliding correlation of Sect. 2.1 is a dense
 // contraction C[k, tau] = sum_m h_k[m] x[tau + m]; here it runs as an implicit
 // GEMM with templates as the MMA M dimension (A operand, 128 per tile), lags
-// as N (B operand, two MMAs of N = 256 per tile) and template samples as K.
+// as N (B operand, MMAs of N = 256; 512 or 256 lags per tile, see Geo) and
+// template samples as K.
 //
 // The lag operand is a Hankel matrix, B[n][m] = x[lag0 + n + m].  It is never
 // materialised: the series is kept as overlapping "split rows" (row w = the
@@ -35,19 +36,33 @@ namespace bfi {
 
 namespace {
 
-constexpr uint32_t B_ROWS = TC_TILE_L + TC_BK - 8;          // 568 rows per stage
-constexpr uint32_t B_BYTES = B_ROWS * 16;                    // 9088 B
-constexpr uint32_t A_BYTES = TILE_BYTES_A;                   // 16384 B
-constexpr uint32_t OFF_AHI = 0;
-constexpr uint32_t OFF_ALO = A_BYTES;
-constexpr uint32_t OFF_BHI = 2 * A_BYTES;
-constexpr uint32_t OFF_BLO = 2 * A_BYTES + B_BYTES;
-constexpr uint32_t STAGE_BYTES = 51200;                      // 50 KiB, 1 KiB aligned
-static_assert(OFF_BLO + B_BYTES <= STAGE_BYTES, "stage layout");
-constexpr uint32_t OFF_INV = TC_STAGES * STAGE_BYTES;        // 512 floats
-constexpr uint32_t OFF_BAR = OFF_INV + TC_TILE_L * 4;
-constexpr uint32_t N_BARS = 2 * TC_STAGES + 3;
-constexpr uint32_t SMEM_BYTES = OFF_BAR + N_BARS * 8 + 16 + 1024;   // + alignment slack
+constexpr uint32_t A_BYTES = TILE_BYTES_A;                   // 16384 B per k-block
+constexpr uint32_t round1k(uint32_t b) { return (b + 1023u) & ~1023u; }
+
+// Shared-memory and TMEM geometry of a tile of LT lags.  LT = 512: one
+// accumulator of 512 columns (two N = 256 MMAs per step) fills TMEM, and the
+// next tile's MMAs wait for the epilogue.  LT = 256: two accumulators of 256
+// columns used alternately, so the epilogue of one tile overlaps the MMAs of
+// the next, at twice the template-operand traffic per lag.
+template <int LT>
+struct Geo {
+    static constexpr uint32_t NSUB = LT / 256;                 // N = 256 MMAs per step
+    static constexpr uint32_t NBUF = 512 / LT;                 // accumulators in TMEM
+    static constexpr uint32_t B_ROWS = LT + TC_BK - 8;         // split rows per stage
+    static constexpr uint32_t B_BYTES = B_ROWS * 16;
+    static constexpr uint32_t OFF_AHI = 0;
+    static constexpr uint32_t OFF_ALO = A_BYTES;
+    static constexpr uint32_t OFF_BHI = 2 * A_BYTES;
+    static constexpr uint32_t OFF_BLO = 2 * A_BYTES + B_BYTES;
+    static constexpr uint32_t STAGE_BYTES = round1k(2 * A_BYTES + 2 * B_BYTES);
+    static constexpr uint32_t STAGES = LT == 512 ? 4 : 5;
+    static constexpr uint32_t OFF_INV = STAGES * STAGE_BYTES;  // LT floats
+    static constexpr uint32_t OFF_BAR = OFF_INV + LT * 4;
+    static constexpr uint32_t N_BARS = 2 * STAGES + 2 * NBUF + 1;
+    static constexpr uint32_t SMEM = OFF_BAR + N_BARS * 8 + 16 + 1024;   // + alignment slack
+};
+static_assert(Geo<512>::STAGE_BYTES == 51200, "stage layout");
+static_assert(Geo<512>::SMEM <= 232448 && Geo<256>::SMEM <= 232448, "shared memory per CTA");
 constexpr uint64_t TIMEOUT_NS = 10ull * 1000 * 1000 * 1000;
 constexpr uint32_t TMEM_COLS = 512;
 
@@ -267,6 +282,7 @@ struct TileCoord {
     uint32_t tt, lag0;
 };
 
+template <int LT>
 __device__ __forceinline__ TileCoord tile_coord(const CorrParams& p, uint64_t t)
 {
     const Seg* s = &p.seg[find_seg(p, t)];
@@ -274,39 +290,42 @@ __device__ __forceinline__ TileCoord tile_coord(const CorrParams& p, uint64_t t)
     TileCoord c;
     c.s = s;
     c.tt = s->tt0 + (uint32_t)(local / s->n_lag_tiles);
-    c.lag0 = (uint32_t)(local % s->n_lag_tiles) * TC_TILE_L;
+    c.lag0 = (uint32_t)(local % s->n_lag_tiles) * LT;
     return c;
 }
 
 }  // namespace
 
-template <int NPROD>
+template <int NPROD, int LT>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant__ CorrParams p)
 {
+    using G = Geo<LT>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    float* sh_inv = reinterpret_cast<float*>(sm + OFF_INV);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + N_BARS * 8);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + OFF_BAR + N_BARS * 8 + 4);
+    float* sh_inv = reinterpret_cast<float*>(sm + G::OFF_INV);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + G::OFF_BAR);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + G::OFF_BAR + G::N_BARS * 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + G::OFF_BAR + G::N_BARS * 8 + 4);
 
     const uint32_t base = smem_u32(sm);
     const uint32_t bar0 = smem_u32(bars);
     auto full_bar = [&](uint32_t st) { return bar0 + 8 * st; };
-    auto empty_bar = [&](uint32_t st) { return bar0 + 8 * (TC_STAGES + st); };
-    const uint32_t tfull_bar = bar0 + 8 * (2 * TC_STAGES);
-    const uint32_t tempty_bar = bar0 + 8 * (2 * TC_STAGES + 1);
-    const uint32_t drain_bar = bar0 + 8 * (2 * TC_STAGES + 2);
+    auto empty_bar = [&](uint32_t st) { return bar0 + 8 * (G::STAGES + st); };
+    auto tfull_bar = [&](uint32_t b) { return bar0 + 8 * (2 * G::STAGES + b); };
+    auto tempty_bar = [&](uint32_t b) { return bar0 + 8 * (2 * G::STAGES + G::NBUF + b); };
+    const uint32_t drain_bar = bar0 + 8 * (2 * G::STAGES + 2 * G::NBUF);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (uint32_t st = 0; st < TC_STAGES; ++st) {
+        for (uint32_t st = 0; st < G::STAGES; ++st) {
             mbar_init(full_bar(st), 1);
             mbar_init(empty_bar(st), 1);
         }
-        mbar_init(tfull_bar, 1);
-        mbar_init(tempty_bar, EPI_THREADS);
+        for (uint32_t b = 0; b < G::NBUF; ++b) {
+            mbar_init(tfull_bar(b), 1);
+            mbar_init(tempty_bar(b), EPI_THREADS);
+        }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -330,7 +349,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             uint64_t issued = 0;
             bool ok = true;
             for (uint64_t t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
-                const TileCoord c = tile_coord(p, t);
+                const TileCoord c = tile_coord<LT>(p, t);
                 const uint32_t n_kb = c.s->M_pad / TC_BK;
                 const size_t tt_rel = c.tt - c.s->bank_k0 / TC_TILE_T;
                 const uint8_t* a_hi = c.s->bank_hi + tt_rel * n_kb * A_BYTES;
@@ -342,37 +361,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
                         ok = false;
                         break;
                     }
-                    const uint32_t sbase = base + st * STAGE_BYTES;
-                    const uint32_t bytes = NPROD == 3 ? 2 * (A_BYTES + B_BYTES) : A_BYTES + B_BYTES;
+                    const uint32_t sbase = base + st * G::STAGE_BYTES;
+                    const uint32_t bytes = NPROD == 3 ? 2 * (A_BYTES + G::B_BYTES) : A_BYTES + G::B_BYTES;
                     mbar_expect_tx(full_bar(st), bytes);
                     const uint64_t w0 = (uint64_t)c.lag0 + (uint64_t)kb * TC_BK;
-                    bulk_g2s(sbase + OFF_AHI, a_hi + (size_t)kb * A_BYTES, A_BYTES, full_bar(st));
-                    bulk_g2s(sbase + OFF_BHI, c.s->yhi + w0, B_BYTES, full_bar(st));
+                    bulk_g2s(sbase + G::OFF_AHI, a_hi + (size_t)kb * A_BYTES, A_BYTES, full_bar(st));
+                    bulk_g2s(sbase + G::OFF_BHI, c.s->yhi + w0, G::B_BYTES, full_bar(st));
                     if (NPROD == 3) {
-                        bulk_g2s(sbase + OFF_ALO, a_lo + (size_t)kb * A_BYTES, A_BYTES, full_bar(st));
-                        bulk_g2s(sbase + OFF_BLO, c.s->ylo + w0, B_BYTES, full_bar(st));
+                        bulk_g2s(sbase + G::OFF_ALO, a_lo + (size_t)kb * A_BYTES, A_BYTES, full_bar(st));
+                        bulk_g2s(sbase + G::OFF_BLO, c.s->ylo + w0, G::B_BYTES, full_bar(st));
                     }
                     ++issued;
-                    if (++st == TC_STAGES) { st = 0; ph ^= 1; }
+                    if (++st == G::STAGES) { st = 0; ph ^= 1; }
                 }
             }
             if (!ok) {
                 // let copies already in flight land before shared memory is released
-                uint64_t first = issued > TC_STAGES ? issued - TC_STAGES : 0;
+                uint64_t first = issued > G::STAGES ? issued - G::STAGES : 0;
                 for (uint64_t i = first; i < issued; ++i)
-                    mbar_wait(full_bar((uint32_t)(i % TC_STAGES)), (uint32_t)((i / TC_STAGES) & 1),
+                    mbar_wait(full_bar((uint32_t)(i % G::STAGES)), (uint32_t)((i / G::STAGES) & 1),
                               abort_flag, false);
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            uint32_t st = 0, ph = 0, tph = 0;
+            uint32_t st = 0, ph = 0, buf = 0, tph = 0;     // tph bit b: phase of accumulator b
             bool ok = true;
             for (uint64_t t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
-                const TileCoord c = tile_coord(p, t);
+                const TileCoord c = tile_coord<LT>(p, t);
                 const uint32_t n_kb = c.s->M_pad / TC_BK;
-                if (!mbar_wait(tempty_bar, tph ^ 1, abort_flag)) {
+                if (!mbar_wait(tempty_bar(buf), ((tph >> buf) & 1) ^ 1, abort_flag)) {
                     if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_TMEM);
                     *abort_flag = 1;
                     break;
@@ -386,17 +405,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
                         break;
                     }
                     fence_after();
-                    const uint32_t sbase = base + st * STAGE_BYTES;
+                    const uint32_t sbase = base + st * G::STAGE_BYTES;
 #pragma unroll
                     for (uint32_t kk = 0; kk < TC_BK / 16; ++kk) {
-                        const uint64_t ahi = make_desc(sbase + OFF_AHI + kk * 256, 128, 1024);
-                        const uint64_t alo = make_desc(sbase + OFF_ALO + kk * 256, 128, 1024);
+                        const uint64_t ahi = make_desc(sbase + G::OFF_AHI + kk * 256, 128, 1024);
+                        const uint64_t alo = make_desc(sbase + G::OFF_ALO + kk * 256, 128, 1024);
 #pragma unroll
-                        for (uint32_t h = 0; h < 2; ++h) {
+                        for (uint32_t h = 0; h < G::NSUB; ++h) {
                             const uint32_t boff = h * 256 * 16 + kk * 256;
-                            const uint64_t bhi = make_desc(sbase + OFF_BHI + boff, 128, 128);
-                            const uint64_t blo = make_desc(sbase + OFF_BLO + boff, 128, 128);
-                            const uint32_t d = tmem + h * 256;
+                            const uint64_t bhi = make_desc(sbase + G::OFF_BHI + boff, 128, 128);
+                            const uint64_t blo = make_desc(sbase + G::OFF_BLO + boff, 128, 128);
+                            const uint32_t d = tmem + buf * 256 + h * 256;
                             mma_f16(d, ahi, bhi, (kb | kk) != 0);
                             if (NPROD == 3) {
                                 mma_f16(d, ahi, blo, 1);
@@ -405,11 +424,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
                         }
                     }
                     mma_commit(empty_bar(st));
-                    if (++st == TC_STAGES) { st = 0; ph ^= 1; }
+                    if (++st == G::STAGES) { st = 0; ph ^= 1; }
                 }
                 if (!ok) break;
-                mma_commit(tfull_bar);
-                tph ^= 1;
+                mma_commit(tfull_bar(buf));
+                tph ^= 1u << buf;
+                buf = buf + 1 == G::NBUF ? 0 : buf + 1;
             }
             // drain: every MMA issued by this thread completes before TMEM is freed
             mma_commit(drain_bar);
@@ -418,19 +438,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
     } else {
         // ------------------------------------------------------------ epilogue
         const uint32_t q = warp & 3;                       // TMEM lane quadrant
-        const uint32_t half = (warp - 2) >> 2;             // lags [256 half, 256 half + 256)
+        const uint32_t half = (warp - 2) >> 2;             // columns [half LT/2, (half+1) LT/2)
         const uint32_t row = q * 32 + lane;                // template row of the tile
         const uint32_t e = threadIdx.x - 64;               // 0 .. EPI_THREADS-1
-        uint32_t tph = 0;
+        uint32_t buf = 0, tph = 0;
         for (uint64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
-            const TileCoord c = tile_coord(p, t);
+            const TileCoord c = tile_coord<LT>(p, t);
             const Seg& s = *c.s;
-            const uint32_t nvalid = min((uint32_t)TC_TILE_L, s.L - c.lag0);
+            const uint32_t nvalid = min((uint32_t)LT, s.L - c.lag0);
             epilogue_sync();
-            for (uint32_t j = e; j < TC_TILE_L; j += EPI_THREADS)
+            for (uint32_t j = e; j < (uint32_t)LT; j += EPI_THREADS)
                 sh_inv[j] = j < nvalid ? s.inv_norm[c.lag0 + j] : 0.f;
             epilogue_sync();
-            const bool ok = mbar_wait(tfull_bar, tph, abort_flag);
+            const bool ok = mbar_wait(tfull_bar(buf), (tph >> buf) & 1, abort_flag);
             if (epilogue_any(!ok)) {       // all epilogue threads leave together
                 if (!ok && !*abort_flag) record_error(p.err, DEV_TIMEOUT_TMEM);
                 *abort_flag = 1;
@@ -439,7 +459,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             fence_after();
             const uint32_t k = c.tt * TC_TILE_T + row;
             const bool keep = k >= s.k_begin && k < s.k_end;
-            const bool full = nvalid == TC_TILE_L;
+            const bool full = nvalid == (uint32_t)LT;
             float* const rho_row = (s.rho != nullptr && keep) ? s.rho + (size_t)(k - s.k_begin) * s.L + c.lag0
                                                               : nullptr;
             const bool dense = rho_row != nullptr;
@@ -452,11 +472,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
                 st.bi[u] = 0;
                 st.ss[u] = 0.f;
             }
-            const uint32_t taddr = tmem + ((q * 32) << 16);
-            // software pipeline over the 8 chunks of 32 columns: the load of
-            // chunk i+1 is in flight while chunk i is reduced; TMEM is handed
-            // back to the MMA warp as soon as the last load has landed
-            const uint32_t cbeg = half * (TC_TILE_L / 2), cend = cbeg + TC_TILE_L / 2;
+            const uint32_t taddr = tmem + ((q * 32) << 16) + buf * 256;
+            // software pipeline over the chunks of 32 columns: the load of
+            // chunk i+1 is in flight while chunk i is reduced; the accumulator
+            // is handed back to the MMA warp as soon as the last load has landed
+            static_assert((LT / 2) % 64 == 0, "chunk pairs per warp");
+            const uint32_t cbeg = half * (LT / 2), cend = cbeg + LT / 2;
             uint32_t ra[32], rb[32];
             auto reduce = [&](const uint32_t (&r)[32], uint32_t cc) {
                 if (cc >= nvalid) return;
@@ -481,12 +502,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
                     tmem_ld32_async(taddr + c0 + 64, ra);
                 } else {
                     fence_before();
-                    mbar_arrive(tempty_bar);          // every column of this thread is read
+                    mbar_arrive(tempty_bar(buf));     // every column of this thread is read
                 }
                 reduce(rb, c0 + 32);
                 if (more) tmem_wait(ra);
             }
-            tph ^= 1;
+            tph ^= 1u << buf;
+            buf = buf + 1 == G::NBUF ? 0 : buf + 1;
             // merge the chains: largest |rho|, smallest column on ties
             float bv = st.bv[0];
             uint32_t bi = st.bi[0];
@@ -515,30 +537,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
     }
 }
 
-static bool g_attr_done[2] = {false, false};
+template <int NPROD, int LT>
+static cudaError_t set_attr()
+{
+    return cudaFuncSetAttribute(k_corr_tc<NPROD, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Geo<LT>::SMEM);
+}
+
+static bool g_attr_done = false;
 
 cudaError_t corr_tc_set_attributes()
 {
-    for (int which = 0; which < 2; ++which) {
-        if (g_attr_done[which]) continue;
-        auto kern = which == 1 ? k_corr_tc<3> : k_corr_tc<1>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        g_attr_done[which] = true;
-    }
-    return cudaSuccess;
+    if (g_attr_done) return cudaSuccess;
+    cudaError_t e = set_attr<1, 512>();
+    if (e == cudaSuccess) e = set_attr<3, 512>();
+    if (e == cudaSuccess) e = set_attr<1, 256>();
+    if (e == cudaSuccess) e = set_attr<3, 256>();
+    if (e == cudaSuccess) g_attr_done = true;
+    return e;
 }
 
-cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int n_sm, cudaStream_t st)
+cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int lt, int n_sm, cudaStream_t st)
 {
     if (p.total_tiles == 0) return cudaSuccess;
-    auto kern = nprod == 3 ? k_corr_tc<3> : k_corr_tc<1>;
     cudaError_t ea = corr_tc_set_attributes();
     if (ea != cudaSuccess) return ea;
-    uint64_t grid = p.total_tiles < (uint64_t)n_sm ? p.total_tiles : (uint64_t)n_sm;
+    const unsigned grid = (unsigned)(p.total_tiles < (uint64_t)n_sm ? p.total_tiles : (uint64_t)n_sm);
     count_launches(1);
-    kern<<<(unsigned)grid, TC_THREADS, SMEM_BYTES, st>>>(p);
+    if (lt == 256) {
+        if (nprod == 3) k_corr_tc<3, 256><<<grid, TC_THREADS, Geo<256>::SMEM, st>>>(p);
+        else k_corr_tc<1, 256><<<grid, TC_THREADS, Geo<256>::SMEM, st>>>(p);
+    } else {
+        if (nprod == 3) k_corr_tc<3, 512><<<grid, TC_THREADS, Geo<512>::SMEM, st>>>(p);
+        else k_corr_tc<1, 512><<<grid, TC_THREADS, Geo<512>::SMEM, st>>>(p);
+    }
     return cudaGetLastError();
 }
 

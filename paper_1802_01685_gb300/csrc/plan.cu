@@ -93,6 +93,10 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
     cudaError_t e = cudaStreamSynchronize(strm);
     if (e == cudaSuccess) e = corr_tc_set_attributes();
     if (e != cudaSuccess) return cuda_fail(e, "plan set-up");
+    // the tile shape is fixed before capture (the autotuner times launches)
+    int lt = o.precision == BF_FP32 ? SIMT_TILE_L
+                                    : (o.tile_lags ? o.tile_lags : choose_lag_tile(ctx, segs[0], o.precision, strm));
+    p->r->tile_lags = lt;
 
     // capture one search
     const uint64_t l0 = g_launches.load();
@@ -103,7 +107,7 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
         ec = prepare_series_kernels(p->prep[s], bank->M, o.precision, strm);
     if (ec == cudaSuccess)
         ec = launch_segments(ctx, segs, o.precision, p->r->thr, p->r->cand, p->r->cand_count,
-                             p->r->cand_cap, strm, nullptr);
+                             p->r->cand_cap, strm, nullptr, lt);
     bf_status fst = BF_OK;
     if (ec == cudaSuccess) fst = finalize_result(ctx, bank, p->r, strm);
     cudaGraph_t graph = nullptr;

@@ -50,9 +50,13 @@ Seg make_segment(const PreparedSeries& ps, uint32_t series_id, const bf_bank* ba
                  size_t k_end, uint32_t tt_first, uint32_t tt_count, int precision,
                  unsigned long long* packed_s, double* sumsq_s, float* rho = nullptr);
 
+// lt: lags per tensor-core tile (256 or 512), 0 = autotuned; ignored by FP32
 cudaError_t launch_segments(bf_ctx* ctx, const std::vector<Seg>& segs, int precision, float thr,
                             Candidate* cand, unsigned int* cand_count, unsigned int cand_cap,
-                            cudaStream_t st, uint64_t* tiles_out);
+                            cudaStream_t st, uint64_t* tiles_out, int lt = 0);
+// The autotuner: lags per tile for this precision and template length, timed
+// once per context on a synthetic problem over the segment's template tiles.
+int choose_lag_tile(bf_ctx* ctx, const Seg& g, int precision, cudaStream_t st);
 
 bf_status resolve_opts(const bf_bank* bank, const bf_opts* in, bf_opts* o);
 bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,

@@ -98,13 +98,16 @@ def test_control_seed_edge_values(ctx):
 
 # ------------------------------------------------------------------ tiny config, full parity
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16"])
-def test_tiny_dense_rho(ctx, tiny, prec):
+@pytest.mark.parametrize("prec,lt", [("split_bf16", 512), ("split_bf16", 256), ("fp32", 0),
+                                     ("bf16", 512), ("bf16", 256)])
+def test_tiny_dense_rho(ctx, tiny, prec, lt):
     w, bank, p, ref = tiny
     x, fs = w["series"][0], w["fs"]
     K, L = ref["rho"].shape
     rho = torch.zeros((K, L), dtype=torch.float32, device="cuda")
-    outs, _, info = run(ctx, bank, [x], fs, prec, rho_out=rho)
+    outs, _, info = run(ctx, bank, [x], fs, prec, rho_out=rho, tile_lags=lt)
+    if lt:
+        assert info.tile_lags == lt
     err = np.abs(rho.cpu().numpy().astype(np.float64) - ref["rho"])
     assert err.max() <= TOL[prec], f"{prec}: max |rho - oracle| = {err.max():.3e}"
     assert info.correlations == K * L
@@ -238,6 +241,34 @@ def test_invalid_calls(ctx, tiny):
     with pytest.raises(bf.BFError):                              # no split layout
         bf.bf_correlate(ctx, b32, [x], w["fs"], bf.make_opts(precision="split_bf16"))
     bf.bf_bank_destroy(b32)
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "bf16"])
+def test_tile_shapes_agree(ctx, prec):
+    """Both tensor-core tile shapes compute every output by the same MMA
+    sequence, so maxima and argmaxes agree bit for bit; ragged lag tiles of
+    either width and the autotuner's choice are covered."""
+    fs = 2048.0
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0, 0.3],
+                           20.0, 1000.0, 6, 7)                   # 336 templates
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_SPLIT_BF16)
+    rng = np.random.default_rng(12)
+    xs = [rng.standard_normal(n).astype(np.float32) for n in (2048, 2048 + 255, 2048 + 700, 20000)]
+    res = {}
+    for lt in (256, 512, 0):
+        outs, mean, info = run(ctx, bank, xs, fs, prec, tile_lags=lt, want_tails=True)
+        assert info.tile_lags in (256, 512) and (lt == 0 or info.tile_lags == lt)
+        res[lt] = (outs, mean)
+    for lt in (512, 0):
+        for a, b in zip(res[256][0], res[lt][0]):
+            np.testing.assert_array_equal(a["max"], b["max"])
+            np.testing.assert_array_equal(a["argmax"], b["argmax"])
+            np.testing.assert_allclose(a["sigma"], b["sigma"], rtol=1e-6)
+            np.testing.assert_array_equal(a["hist"], b["hist"])
+        np.testing.assert_array_equal(res[256][1], res[lt][1])
+    with pytest.raises(bf.BFError):
+        run(ctx, bank, xs, fs, prec, tile_lags=128)
+    bf.bf_bank_destroy(bank)
 
 
 def test_async_stream_matches_sync(ctx, tiny):
