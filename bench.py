@@ -44,10 +44,10 @@ UNIT = "correlations/s"
 # --kernel-case capture), per 128-template tile: every CTA works on the same
 # template tile at once, so each template block is read from DRAM once and the
 # traffic grows with the number of template tiles, not with the lag tiles.
-# Keyed by the hash of the kernel source the counters were taken on; a changed
-# kernel reports null until it is captured again.
+# Keyed by (hash of the kernel source the counters were taken on, lags per
+# tile); a changed kernel reports null until it is captured again.
 TRAFFIC_BYTES_PER_TEMPLATE_TILE = {
-    "1692752bfa8732a6": (272.05e6 + 4.32e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
+    ("bafca6b278e1181f", 256): (273.12e6 + 3.98e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
 }
 
 
@@ -185,6 +185,7 @@ def run_ours(args, rank, world, local):
     opts = bf.make_opts(precision="split_bf16", want_map=True, want_hist=True)
     kernel_ms = []
     stage_ms = {}
+    shapes = set()
 
     def step(record=False):
         t0 = time.perf_counter()
@@ -198,6 +199,7 @@ def run_ours(args, rank, world, local):
         info = bf.bf_result_info_get(res)
         if record:
             kernel_ms.append(info.kernel_ms)
+            shapes.add(info.tile_lags)
             for k, v in (("bank_synthesis", t1 - t0), ("controls", t2 - t1), ("correlate", t3 - t2)):
                 stage_ms.setdefault(k, []).append(1e3 * v)
         bf.bf_result_destroy(res)
@@ -232,13 +234,15 @@ def run_ours(args, rank, world, local):
     issued_flops = 3 * 2 * M * corr_per_step          # three BF16 MMAs per sample pair
     achieved = issued_flops / (k_ms / 1e3) / 1e12
     th = kernel_source_hash()
+    lt = sorted(shapes)[0] if len(shapes) == 1 else None
     traffic = None
-    if th in TRAFFIC_BYTES_PER_TEMPLATE_TILE:
-        traffic = round(TRAFFIC_BYTES_PER_TEMPLATE_TILE[th] * (K // 128))
+    if (th, lt) in TRAFFIC_BYTES_PER_TEMPLATE_TILE:
+        traffic = round(TRAFFIC_BYTES_PER_TEMPLATE_TILE[(th, lt)] * (K // 128))
     roofline = {"bound": "tensor", "achieved": round(achieved, 1),
                 "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
                 "frac": round(achieved / peaks["bf16_sustained"], 4), "traffic": traffic,
-                "kernel": "k_corr_tc<3> (split-BF16)", "kernel_ms": round(k_ms, 2),
+                "kernel": f"k_corr_tc<3,{lt}> (split-BF16, {lt} lags per tile, autotuned)",
+                "kernel_ms": round(k_ms, 2),
                 "peak_source": f"{peaks['source']} bf16_tflops_sustained",
                 "algorithmic_flops_per_launch": issued_flops,
                 "useful_tflops": round(2 * M * corr_per_step / (k_ms / 1e3) / 1e12, 1)}
@@ -484,10 +488,11 @@ def run_reference(args, rank, world, local):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_kernel_case():
+def run_kernel_case(tile_lags: int):
     """Moderate case of the split-BF16 kernel for profiler captures: one 16 s
     series at 4096 Hz against 16,384 power-law templates (split bank 268 MB,
-    larger than L2); two launches, each printed with its CUDA-event time."""
+    larger than L2); two launches of the given tile shape (no autotuner
+    launches), each printed with its CUDA-event time."""
     from paper_1802_01685_gb300 import bf, synth
     import __graft_entry__
     __graft_entry__.build()
@@ -496,10 +501,10 @@ def run_kernel_case():
     bank = bf.bf_bank_create_grid(ctx, w["grid"], w["fs"], 1.0, bf.BF_BANK_SPLIT_BF16)
     for _ in range(2):
         res = bf.bf_correlate(ctx, bank, [w["series"][0]], w["fs"],
-                              bf.make_opts(precision="split_bf16"))
+                              bf.make_opts(precision="split_bf16", tile_lags=tile_lags))
         info = bf.bf_result_info_get(res)
         print(json.dumps({"kernel_case": "gw_pair 16 s x 16384 templates", "kernel_ms": info.kernel_ms,
-                          "correlations": info.correlations}), flush=True)
+                          "tile_lags": info.tile_lags, "correlations": info.correlations}), flush=True)
         bf.bf_result_destroy(res)
     bf.bf_bank_destroy(bank)
     bf.bf_destroy(ctx)
@@ -565,6 +570,8 @@ def main():
     ap.add_argument("--check-templates", type=int, default=16)
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the moderate profiling case of the tensor-core kernel")
+    ap.add_argument("--tile-lags", type=int, default=256,
+                    help="tile shape of --kernel-case (the autotuner's choice on GB300)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -578,7 +585,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=8.0)
     args = ap.parse_args()
     if args.kernel_case:
-        run_kernel_case()
+        run_kernel_case(args.tile_lags)
         return
     if args.workload != "gw_pair":
         run_workload(args.workload, args.check_templates)
