@@ -144,6 +144,7 @@ void bf_destroy(bf_ctx* ctx);
  * params: host array of K chirps, copied.  BF_EINVAL on a chirp violating the
  * rules of bf_chirp or K == 0; BF_ENOMEM when the layouts exceed the budget.
  */
+#define BF_MAX_TEMPLATE_LEN 32768   /* M = round(T * fs) samples, at most */
 bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double fs,
                          double T, unsigned storage, bf_bank** out);
 bf_status bf_bank_create_grid(bf_ctx* ctx, const bf_chirp_grid* grid, double fs,

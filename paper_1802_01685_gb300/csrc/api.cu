@@ -776,7 +776,10 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
         return BF_EINVAL;
     }
     const uint32_t M = template_len(T, fs);
-    if (M < 2 || M > (1u << 20)) { set_error("template length %u outside [2, 2^20]", M); return BF_EINVAL; }
+    if (M < 2 || M > BF_MAX_TEMPLATE_LEN) {
+        set_error("template length %u outside [2, %d]", M, BF_MAX_TEMPLATE_LEN);
+        return BF_EINVAL;
+    }
     char why[256];
     for (size_t k = 0; k < K; ++k)
         if (!chirp_ok(params[k], fs, M, why, sizeof why)) {

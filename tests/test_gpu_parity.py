@@ -53,6 +53,12 @@ def test_bank_templates_match_oracle(ctx):
         bf.bf_bank_destroy(bank)
 
 
+def test_bank_rejects_templates_longer_than_the_limit(ctx):
+    with pytest.raises(bf.BFError) as e:
+        bf.bf_bank_create(ctx, [(bf.BF_LINEAR, bf.BF_ASC, 50.0, 100.0, 0.5)], 40000.0, 1.0)
+    assert e.value.status == bf.BF_EINVAL and "32768" in str(e.value)
+
+
 def test_bank_grid_matches_oracle_grid(ctx):
     spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC],
                            [0.2, 0.6, 1.0], 20.0, 1000.0, 3, 5)
