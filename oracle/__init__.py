@@ -70,7 +70,7 @@ def _load():
         lib.oracle_correlate_raw.restype = None
         lib.oracle_correlate_raw.argtypes = [p, l, p, l, p, p]
         lib.oracle_search.restype = i
-        lib.oracle_search.argtypes = [p, l, d, p, p, p, p, p, l, l, d, d, d, l, l,
+        lib.oracle_search.argtypes = [p, l, d, p, p, p, p, p, l, l, d, p, d, d, l, l,
                                       p, p, p, p, p]
         lib.oracle_histogram.restype = None
         lib.oracle_histogram.argtypes = [p, l, l, p]
@@ -168,9 +168,11 @@ def map_shape(N: int, fs: float, dt: float, df: float):
 
 
 def search(x: np.ndarray, fs: float, params: dict, M: int, *, kappa: float = 5.0,
-           thr: float | None = None, dt: float = 1e-3, df: float = 4.0,
-           want_rho: bool = False, want_map: bool = False) -> dict:
-    """Full oracle search of one series against the bank given by ``params``."""
+           thr: float | None = None, thr_k: np.ndarray | None = None, dt: float = 1e-3,
+           df: float = 4.0, want_rho: bool = False, want_map: bool = False) -> dict:
+    """Full oracle search of one series against the bank given by ``params``.
+    The map is painted by tails |rho| >= thr (default kappa / sqrt(M)), or
+    >= thr_k[k] per template when thr_k is given."""
     x = np.ascontiguousarray(x, np.float32)
     N = len(x)
     K = len(params["track"])
@@ -188,13 +190,53 @@ def search(x: np.ndarray, fs: float, params: dict, M: int, *, kappa: float = 5.0
     arg = np.zeros(K, np.int64)
     sig = np.zeros(K)
     mp = np.zeros((nt, nf)) if want_map else None
+    tk = np.ascontiguousarray(thr_k, np.float64) if thr_k is not None else None
     rc = _load().oracle_search(_ptr(x), N, fs, _ptr(tr), _ptr(se), _ptr(fl), _ptr(fh),
-                               _ptr(Dd), K, M, float(thr), dt, df, nt, nf, _ptr(rho),
+                               _ptr(Dd), K, M, float(thr), _ptr(tk), dt, df, nt, nf, _ptr(rho),
                                _ptr(vmax), _ptr(arg), _ptr(sig), _ptr(mp))
     if rc:
         raise ValueError("oracle_search: invalid input")
     return dict(rho=rho, max=vmax, argmax=arg, sigma=sig, map=mp, thr=float(thr),
                 nt=nt, nf=nf)
+
+
+def welch_power(x: np.ndarray, F: int) -> np.ndarray:
+    """Averaged periodogram of x over rectangular segments of F samples at hop
+    F/2, all F DFT bins: P(f) = mean_s |DFT_F(x_s)(f)|^2.  A series shorter than
+    F is one zero-padded segment scaled by F/N.  (Predictor step of Sect. 2.2
+    and Fig. 5: sigma of the filter output from Parseval's theorem.)"""
+    x = np.asarray(x, np.float64)
+    N = len(x)
+    if N >= F:
+        hop = F // 2
+        S = (N - F) // hop + 1
+        P = np.zeros(F)
+        for s in range(S):
+            P += np.abs(np.fft.fft(x[s * hop:s * hop + F])) ** 2
+        return P / S
+    return np.abs(np.fft.fft(x, F)) ** 2 * (F / N)
+
+
+def parseval_sigma(x: np.ndarray, H: np.ndarray) -> np.ndarray:
+    """Predicted standard deviation of rho for each template row of H ([K, M]),
+    before the search, from Parseval's theorem (Sect. 2.2, Fig. 5 caption):
+      E[C_k(tau)^2] = sum_f S_x(f) |H_k(f)|^2 / F   (S_x = P / F, F = 2M),
+      rho = C / |window|,  |window|^2 ~ M sigma_x^2,
+    so sigma_k^2 = sum_f P(f) |H_k(f)|^2 / (F^2 M sigma_x^2), sigma_x^2 the
+    mean of x^2; 0 for an all-zero series."""
+    H = np.atleast_2d(np.asarray(H, np.float64))
+    K, M = H.shape
+    F = 2 * M
+    x = np.asarray(x, np.float64)
+    sx2 = np.mean(x * x)
+    if sx2 == 0.0:
+        return np.zeros(K)
+    P = welch_power(x, F)
+    out = np.zeros(K)
+    for k in range(K):
+        Hf = np.abs(np.fft.fft(H[k], F)) ** 2
+        out[k] = np.sqrt(np.sum(P * Hf) / (F * F * M * sx2))
+    return out
 
 
 def histogram(v: np.ndarray, nbins: int = 1024) -> np.ndarray:

@@ -187,7 +187,8 @@ void oracle_correlate_raw(const float *x, long N, const double *h, long M,
 
 /*
  * Full search of one series against K templates given by their chirp
- * parameters.  Outputs (any pointer may be NULL):
+ * parameters.  The tail threshold is thr for every template, or thr_k[k]
+ * when thr_k is not NULL.  Outputs (any pointer may be NULL):
  *   rho[k*L + tau]   normalised correlation,
  *   vmax[k]          max over tau of |rho|           (Fig. 2: maxima of
  *                                                      butterfly output),
@@ -232,8 +233,8 @@ static void paint_track(double *map, long nt, long nf, double dt, double df,
 
 int oracle_search(const float *x, long N, double fs, const int *track,
                   const int *sense, const double *f_lo, const double *f_hi,
-                  const double *D, long K, long M, double thr, double dt,
-                  double df, long nt, long nf, double *rho, double *vmax,
+                  const double *D, long K, long M, double thr, const double *thr_k,
+                  double dt, double df, long nt, long nf, double *rho, double *vmax,
                   long *argmax, double *sigma, double *map)
 {
     if (N < M || M <= 0 || K < 0) return -1;
@@ -266,6 +267,7 @@ int oracle_search(const float *x, long N, double fs, const int *track,
             oracle_template(track[k], sense[k], f_lo[k], f_hi[k], D[k], fs, M, h);
             double best = -1.0, ss = 0.0;
             long best_tau = 0;
+            const double thr_here = thr_k ? thr_k[k] : thr;   /* per-template tails */
             for (long tau = 0; tau < L; ++tau) {
                 double s = 0.0;
                 for (long m = 0; m < M; ++m) s += (double)x[tau + m] * h[m];
@@ -277,7 +279,7 @@ int oracle_search(const float *x, long N, double fs, const int *track,
                     best_tau = tau;
                 }
                 ss += r * r;
-                if (map && a >= thr) {
+                if (map && a >= thr_here) {
 #pragma omp critical(oracle_map)
                     paint_track(map, nt, nf, dt, df, track[k], sense[k], f_lo[k],
                                 f_hi[k], D[k], fs, M, tau, a);

@@ -398,3 +398,67 @@ def test_tf_map_paints_injected_track():
         # nothing is painted outside the band swept by the track
         assert np.all(mp[:, : int(f0 // df) - 1] == 0)
         assert np.all(mp[:, int(f1 // df) + 2:] == 0)
+
+
+# ----------------------------------------------------------------- Parseval predictor
+
+def test_parseval_identity_for_circular_correlation():
+    """For one segment of exactly F samples, sum_f |X|^2 |H|^2 / F equals the
+    sum over all circular lags of the squared circular correlation."""
+    r = rng(20)
+    Mp = 64
+    F = 2 * Mp
+    x = r.standard_normal(F)
+    h = r.standard_normal(Mp)
+    P = oracle.welch_power(x, F)
+    Hf = np.abs(np.fft.fft(h, F)) ** 2
+    hpad = np.concatenate([h, np.zeros(F - Mp)])
+    circ = [np.dot(np.roll(x, -t), hpad) for t in range(F)]
+    assert abs(np.sum(P * Hf) / F - np.sum(np.square(circ))) < 1e-9 * np.sum(np.square(circ))
+
+
+def test_parseval_sigma_white_noise_is_one_over_sqrt_m():
+    Mw = 256
+    h = oracle.template(oracle.LINEAR, oracle.ASC, 40.0, 400.0, 0.25, 1024.0, Mw)
+    x = rng(21).standard_normal(Mw * 2000)
+    s = oracle.parseval_sigma(x, h[None, :])[0]
+    assert abs(s * np.sqrt(Mw) - 1.0) < 0.02
+    # scale invariance and the all-zero series
+    assert abs(oracle.parseval_sigma(3.0 * x, h[None, :])[0] - s) < 1e-12
+    assert oracle.parseval_sigma(np.zeros(4 * Mw), h[None, :])[0] == 0.0
+
+
+def test_parseval_sigma_predicts_measured_sigma_of_coloured_noise():
+    """On stationary coloured noise the prediction agrees with the rms of rho
+    measured by the search, template by template, to within the bias of a
+    predictor: rho divides by the local window norm, whose fluctuations on red
+    noise make E[C^2 / E_w] exceed E[C^2] / E[E_w] (here by ~5 %).  A
+    low-frequency template sees several times the noise of a high-frequency
+    one."""
+    fs, Mw = 1024.0, 256
+    p = oracle.grid([oracle.LINEAR], [oracle.ASC], [0.25], 10.0, 500.0, 2, 2)
+    r = rng(22)
+    w = r.standard_normal(Mw * 400)
+    X = np.fft.rfft(w)
+    f = np.fft.rfftfreq(len(w), 1 / fs)
+    X *= 1.0 / np.maximum(f / 30.0, 0.2)            # red spectrum below 30 Hz
+    x = np.fft.irfft(X, len(w)).astype(np.float32)
+    H = oracle.bank(p, fs, Mw)
+    pred = oracle.parseval_sigma(x, H)
+    meas = oracle.search(x, fs, p, Mw)["sigma"]
+    np.testing.assert_allclose(pred, meas, rtol=0.10)
+    assert np.all(pred <= meas)                     # the bias has this sign
+    assert pred.max() > 2 * pred.min()
+
+
+def test_per_template_thresholds_paint_only_their_tails():
+    fs, Mw = 1024.0, 256
+    p = oracle.grid([oracle.LINEAR], [oracle.ASC, oracle.DESC], [0.25], 40.0, 400.0, 1, 2)
+    x = rng(23).standard_normal(Mw * 8).astype(np.float32)
+    out = oracle.search(x, fs, p, Mw, want_rho=True)
+    K = len(p["track"])
+    thr_k = np.array([0.15, 10.0, 0.15, 10.0])[:K]
+    m1 = oracle.search(x, fs, p, Mw, thr_k=thr_k, want_map=True)["map"]
+    only = {k: v[[0, 2]] for k, v in p.items()} if K == 4 else p
+    m2 = oracle.search(x, fs, only, Mw, thr=0.15, want_map=True)["map"]
+    np.testing.assert_array_equal(m1, m2)
