@@ -59,6 +59,9 @@ typedef enum {
 typedef enum { BF_LINEAR = 0, BF_POWERLAW = 1 } bf_track;
 typedef enum { BF_ASC = 0, BF_DESC = 1 } bf_sense;
 
+/* threshold of the tails rho > kappa sigma (Sect. 2.2) */
+typedef enum { BF_SIGMA_WHITE = 0, BF_SIGMA_PARSEVAL = 1 } bf_tail_sigma;
+
 /* arithmetic of the correlation (FP32 accumulate in every mode) */
 typedef enum {
     BF_FP32 = 0,        /* FP32 operands, FP32 FMA (SIMT)                      */
@@ -178,6 +181,13 @@ typedef struct {
                                 (n_templates x L floats, row-major) is written
                                 here as well.  For inspection of small cases. */
     int32_t want_tails;      /* keep the list of tails (see bf_result_tails)   */
+    int32_t tail_sigma;      /* threshold of the tails (map, tail list):
+                                BF_SIGMA_WHITE: kappa / sqrt(M), the exact
+                                sigma of rho on white noise;
+                                BF_SIGMA_PARSEVAL: kappa * sigma_k, with
+                                sigma_k predicted per series and template from
+                                Parseval's theorem before the search (see
+                                bf_result_get_sigma_pred)                      */
     int32_t tile_lags;       /* lags per tensor-core tile: 512 (one TMEM
                                 accumulator) or 256 (two, so the epilogue of
                                 one tile overlaps the MMAs of the next); 0 =
@@ -233,6 +243,19 @@ bf_status bf_result_copy_to_host(const bf_result* r, size_t s, float* vmax,
                                  int32_t* argmax, float* sigma, uint32_t* hist,
                                  float* map);
 bf_status bf_result_copy_mean_max(const bf_result* r, float* host_mean_max);
+
+/*
+ * Predicted noise level of rho (Sect. 2.2 and Fig. 5 caption: sigma from
+ * Parseval's theorem in a predictor step, before the search), kept when
+ * opts.tail_sigma == BF_SIGMA_PARSEVAL:
+ *   sigma_k^2 = sum_f P_x(f) |H_k(f)|^2 / (F^2 M sigma_x^2),   F = 2M,
+ * P_x the periodogram of the series averaged over rectangular F-sample
+ * segments at hop F/2 (a series shorter than F: one zero-padded segment scaled
+ * by F/N), H_k the F-point DFT of template k, sigma_x^2 the mean of x^2.
+ * Exactly 1/sqrt(M) on white noise.  n_templates floats per series.
+ */
+bf_status bf_result_get_sigma_pred(const bf_result* r, size_t s, const float** sigma_pred);
+bf_status bf_result_copy_sigma_pred(const bf_result* r, size_t s, float* host);
 
 /*
  * Tails of the filter output (Sect. 2.2: only the tails rho > kappa sigma are

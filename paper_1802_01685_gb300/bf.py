@@ -25,6 +25,7 @@ BF_LINEAR, BF_POWERLAW = 0, 1
 BF_ASC, BF_DESC = 0, 1
 BF_FP32, BF_BF16, BF_SPLIT_BF16 = 0, 1, 2
 BF_BANK_FP32, BF_BANK_SPLIT_BF16, BF_BANK_GENERATED = 1, 2, 4
+BF_SIGMA_WHITE, BF_SIGMA_PARSEVAL = 0, 1
 
 PRECISIONS = {"fp32": BF_FP32, "bf16": BF_BF16, "split_bf16": BF_SPLIT_BF16}
 
@@ -60,7 +61,7 @@ class bf_opts(C.Structure):
                 ("bank_end", C.c_size_t), ("kappa", C.c_double), ("map_dt_s", C.c_double),
                 ("map_df_hz", C.c_double), ("want_map", C.c_int32), ("want_hist", C.c_int32),
                 ("hist_bins", C.c_uint32), ("stream", C.c_void_p), ("rho_out", C.c_void_p),
-                ("want_tails", C.c_int32), ("tile_lags", C.c_int32)]
+                ("want_tails", C.c_int32), ("tail_sigma", C.c_int32), ("tile_lags", C.c_int32)]
 
 
 class bf_tail(C.Structure):
@@ -126,6 +127,8 @@ def load() -> C.CDLL:
             "bf_result_copy_to_host": (i, [p, s, p, p, p, p, p]),
             "bf_result_copy_mean_max": (i, [p, p]),
             "bf_result_tails": (i, [p, P(p), P(s)]),
+            "bf_result_get_sigma_pred": (i, [p, s, P(p)]),
+            "bf_result_copy_sigma_pred": (i, [p, s, p]),
             "bf_result_copy_tails": (i, [p, p, s, P(s)]),
             "bf_result_destroy": (None, [p]),
             "bf_plan_create": (i, [p, p, P(s), s, d, P(bf_opts), P(p)]),
@@ -241,7 +244,8 @@ def bf_opts_default() -> bf_opts:
 
 def make_opts(precision=BF_SPLIT_BF16, bank_begin=0, bank_end=0, kappa=5.0, map_dt_s=1e-3,
               map_df_hz=4.0, want_map=False, want_hist=True, hist_bins=1024,
-              stream=None, rho_out=None, want_tails=False, tile_lags=0) -> bf_opts:
+              stream=None, rho_out=None, want_tails=False, tile_lags=0,
+              tail_sigma=BF_SIGMA_WHITE) -> bf_opts:
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     o = bf_opts_default()
@@ -258,6 +262,7 @@ def make_opts(precision=BF_SPLIT_BF16, bank_begin=0, bank_end=0, kappa=5.0, map_
     o.rho_out = _addr(rho_out) if rho_out is not None else None
     o.want_tails = int(bool(want_tails))
     o.tile_lags = int(tile_lags)
+    o.tail_sigma = int(tail_sigma)
     return o
 
 
@@ -352,6 +357,18 @@ def bf_result_copy_tails(res: int) -> np.ndarray:
     out = np.zeros(n.value, TAIL_DTYPE)
     if n.value:
         _check(load().bf_result_copy_tails(res, out.ctypes.data, n.value, C.byref(n)))
+    return out
+
+
+def bf_result_get_sigma_pred(res: int, s: int) -> int:
+    a = C.c_void_p()
+    _check(load().bf_result_get_sigma_pred(res, s, C.byref(a)))
+    return a.value
+
+
+def bf_result_copy_sigma_pred(res: int, s: int) -> np.ndarray:
+    out = np.zeros(bf_result_info_get(res).n_templates, np.float32)
+    _check(load().bf_result_copy_sigma_pred(res, s, out.ctypes.data))
     return out
 
 

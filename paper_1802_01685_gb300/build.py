@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbf.so")
 
 SOURCES = ["api.cu", "serve.cu", "bank.cu", "prep.cu", "corr_simt.cu", "corr_tc.cu",
-           "finalize.cu", "permute.cu", "noalloc.cu", "plan.cu"]
+           "finalize.cu", "permute.cu", "noalloc.cu", "plan.cu", "predict.cu"]
 HEADERS = ["bf_internal.h", "runtime.h", "corr_common.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -60,8 +60,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
+    cuda_lib = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64")
     cmd = [_nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + [
-        "-lpthread", "-ldl", "-lrt"]
+        "-L", cuda_lib, "-lcufft", "-Xlinker", "-rpath," + cuda_lib, "-lpthread", "-ldl", "-lrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

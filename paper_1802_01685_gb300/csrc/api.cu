@@ -372,8 +372,9 @@ static void free_result_buffers(bf_result* r)
     Allocator& mem = *r->ctx->mem;
     for (void* p : {(void*)r->packed, (void*)r->sumsq, (void*)r->vmax, (void*)r->argmax,
                     (void*)r->sigma, (void*)r->hist, (void*)r->map, (void*)r->mean_max,
-                    (void*)r->cand, (void*)r->cand_count})
+                    (void*)r->cand, (void*)r->cand_count, (void*)r->sigma_pred})
         mem.release(p);
+    r->sigma_pred = nullptr;
     for (void* p : r->scratch) mem.release(p);
     r->scratch.clear();
     r->packed = nullptr;
@@ -417,6 +418,10 @@ bf_status resolve_opts(const bf_bank* bank, const bf_opts* in, bf_opts* o)
         set_error("bank keeps no split-BF16 layout (create it with BF_BANK_SPLIT_BF16)");
         return BF_EINVAL;
     }
+    if (o->tail_sigma != BF_SIGMA_WHITE && o->tail_sigma != BF_SIGMA_PARSEVAL) {
+        set_error("unknown tail_sigma %d", o->tail_sigma);
+        return BF_EINVAL;
+    }
     if (o->tile_lags != 0 && o->tile_lags != TC_TILE_L && o->tile_lags != TC_TILE_L / 2) {
         set_error("tile_lags %d: use 0 (autotuned), 256 or 512", o->tile_lags);
         return BF_EINVAL;
@@ -446,6 +451,8 @@ bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
     r->want_map = o.want_map != 0;
     r->want_hist = o.want_hist != 0;
     r->want_tails = o.want_tails != 0;
+    r->parseval = o.tail_sigma == BF_SIGMA_PARSEVAL;
+    r->kappa = (float)o.kappa;
     r->lengths = lengths;
     r->thr = (float)(o.kappa / std::sqrt((double)bank->M));
     Allocator& mem = *ctx->mem;
@@ -459,9 +466,10 @@ bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
     r->cand_cap = (unsigned int)std::min<size_t>(ctx->cfg.max_candidates, 0xFFFFFFF0u);
     if (!r->want_map && !r->want_tails) r->cand_cap = 0;
     r->cand = static_cast<Candidate*>(mem.alloc(std::max<size_t>(r->cand_cap, 1) * sizeof(Candidate)));
+    if (r->parseval) r->sigma_pred = static_cast<float*>(mem.alloc(S * K * 4));
     r->cand_count = static_cast<unsigned int*>(mem.alloc(sizeof(unsigned int)));
     bool ok = r->packed && r->sumsq && r->vmax && r->argmax && r->sigma && r->mean_max && r->cand &&
-              r->cand_count;
+              r->cand_count && (!r->parseval || r->sigma_pred);
     if (ok && r->want_hist) {
         r->hist = static_cast<uint32_t*>(mem.alloc(S * r->nbins * 4));
         ok = r->hist != nullptr;
@@ -862,6 +870,7 @@ void bf_bank_destroy(bf_bank* b)
     if (!b) return;
     Allocator& mem = *b->ctx->mem;
     cudaStreamSynchronize(b->ctx->stream);
+    mem.release(b->ph);
     mem.release(b->d_params);
     mem.release(b->f32);
     mem.release(b->hi);
@@ -985,6 +994,18 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
     std::vector<Seg> segs;
     build_segments(pptr, ids, bank, o.bank_begin, o.bank_end, o.precision, r->packed, r->sumsq, r->K, segs);
     if (o.rho_out) segs[0].rho = o.rho_out;
+    if (r->parseval) {
+        // the predictor step: sigma_k per series before the search
+        st = bank_power_spectra(ctx, const_cast<bf_bank*>(bank), strm);
+        for (size_t s = 0; s < n_series && st == BF_OK; ++s)
+            st = predict_sigma(ctx, bank, prep[s], o.bank_begin, o.bank_end, r->sigma_pred + s * r->K,
+                               r->scratch, strm);
+        if (st) return st;
+        for (size_t s = 0; s < n_series; ++s) {
+            segs[s].sigma_pred = r->sigma_pred + s * r->K;
+            segs[s].kappa = r->kappa;
+        }
+    }
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (sync) {
@@ -1121,6 +1142,25 @@ bf_status bf_result_copy_mean_max(const bf_result* r, float* out)
     cudaSetDevice(r->ctx->device);
     cudaError_t e = cudaMemcpy(out, r->mean_max, r->K * 4, cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? BF_OK : cuda_fail(e, "result copy");
+}
+
+bf_status bf_result_get_sigma_pred(const bf_result* r, size_t s, const float** sigma_pred)
+{
+    if (!r || s >= r->n_series || !sigma_pred) { set_error("bad argument"); return BF_EINVAL; }
+    if (!r->sigma_pred) { set_error("no prediction (opts.tail_sigma = BF_SIGMA_PARSEVAL)"); return BF_EINVAL; }
+    *sigma_pred = r->sigma_pred + s * r->K;
+    return BF_OK;
+}
+
+bf_status bf_result_copy_sigma_pred(const bf_result* r, size_t s, float* host)
+{
+    const float* dev = nullptr;
+    bf_status st = bf_result_get_sigma_pred(r, s, &dev);
+    if (st) return st;
+    if (!host) { set_error("NULL host array"); return BF_EINVAL; }
+    cudaSetDevice(r->ctx->device);
+    cudaError_t e = cudaMemcpy(host, dev, r->K * sizeof(float), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? BF_OK : cuda_fail(e, "sigma copy");
 }
 
 static size_t kept_tails(const bf_result* r)

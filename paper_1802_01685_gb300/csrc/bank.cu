@@ -21,6 +21,8 @@
 // inside, the 8x8 core matrix (r / 8, c / 8) is 128 contiguous bytes at
 // (r / 8) * 1024 + (c / 8) * 128, row r % 8 at +16 * (r % 8), element c % 8 at +2.
 // Hence LBO (next 8 samples) = 128 B and SBO (next 8 templates) = 1024 B.
+#include <algorithm>
+
 #include "bf_internal.h"
 
 namespace bfi {
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
                                                     uint8_t* __restrict__ hi,
                                                     uint8_t* __restrict__ lo)
 {
-    extern __shared__ float g[];        // M_pad samples of the ascending template
+    extern __shared__ float g[];        // the first M_s = round64(M) samples of the row
     __shared__ double red[8];
     const uint32_t k = blockIdx.x;
     const uint32_t n_kb = M_pad / TC_BK;
@@ -82,8 +84,9 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
         }
         inv_md = 1.0f / (float)p.MD;
     }
+    const uint32_t M_s = min(M_pad, (M + 63u) & ~63u);
     double part = 0.0;
-    for (uint32_t m = threadIdx.x; m < M_pad; m += blockDim.x) {
+    for (uint32_t m = threadIdx.x; m < M_s; m += blockDim.x) {
         float v = 0.f;
         if (valid) {
             int j = (int)m - p.first;          // ascending-template sample index
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
     const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
 
     for (uint32_t m = threadIdx.x; m < M_pad; m += blockDim.x) {
-        double h = (double)g[m] * inv;
+        double h = m < M_s ? (double)g[m] * inv : 0.0;
         if (f32) f32[(size_t)k * M_pad + m] = (float)h;
         if (hi) {
             __nv_bfloat16 bh = __double2bfloat16(h);
@@ -124,7 +127,7 @@ cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t K, uint32_t K_pad
                               uint32_t M_pad, double fs, float* f32, uint8_t* hi, uint8_t* lo,
                               cudaStream_t s)
 {
-    size_t smem = (size_t)M_pad * sizeof(float);
+    size_t smem = (size_t)std::min(M_pad, (M + 63u) & ~63u) * sizeof(float);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_bank_synth,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -64,6 +64,11 @@ struct Seg {
     unsigned long long* vmax;       // packed max per template, index k - k_begin
     double* sumsq;                  // sum of rho^2 per template
     float* rho;                     // optional dense output [k - k_begin][tau]
+    const float* sigma_pred;        // optional predicted sigma per template
+                                    // (index k - k_begin): tails are then
+                                    // |rho| >= kappa * sigma_pred[k]
+    float kappa;
+    float pad2;
     uint32_t bank_k0;               // template index held at the bank pointers
                                     // (0 for a stored bank, the chunk start
                                     // for a generated one)
@@ -202,6 +207,7 @@ struct bf_bank {
     float* f32 = nullptr;
     uint8_t* hi = nullptr;
     uint8_t* lo = nullptr;
+    float* ph = nullptr;                // template power spectra [K_pad][M+1] (lazy)
 };
 
 struct bf_result {
@@ -209,7 +215,9 @@ struct bf_result {
     size_t n_series = 0, K = 0, k_begin = 0;
     uint32_t M = 0, nbins = 0;
     double fs = 0, dt = 0, df = 0;
-    bool want_map = false, want_hist = false, want_tails = false;
+    bool want_map = false, want_hist = false, want_tails = false, parseval = false;
+    float kappa = 5.f;
+    float* sigma_pred = nullptr;            // [S][K] predicted sigma (Parseval)
     std::vector<size_t> lengths;
     std::vector<uint32_t> map_nt;
     uint32_t map_nf = 0;

@@ -82,6 +82,8 @@ __global__ void __launch_bounds__(SIMT_THREADS, 2) k_corr_simt(const __grid_cons
         for (int a = 0; a < 8; ++a) {
             const uint32_t k = k0 + 8 * warp + a;
             const bool keep = k >= s.k_begin && k < s.k_end;
+            const float thr = !keep ? INFINITY
+                                    : (s.sigma_pred ? s.kappa * s.sigma_pred[k - s.k_begin] : p.thr);
             unsigned long long best = 0ull;
             float ss = 0.f;
 #pragma unroll
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, 2) k_corr_simt(const __grid_cons
                     unsigned long long key = pack_max(ar, tau);
                     best = key > best ? key : best;
                     ss = fmaf(r, r, ss);
-                    if (keep && ar >= p.thr) push_candidate(p, s.series_id, k, tau, r);
+                    if (ar >= thr) push_candidate(p, s.series_id, k, tau, r);
                 }
             }
 #pragma unroll

@@ -463,7 +463,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             float* const rho_row = (s.rho != nullptr && keep) ? s.rho + (size_t)(k - s.k_begin) * s.L + c.lag0
                                                               : nullptr;
             const bool dense = rho_row != nullptr;
-            const float thr = keep ? p.thr : INFINITY;
+            const float thr = !keep ? INFINITY
+                                    : (s.sigma_pred ? s.kappa * s.sigma_pred[k - s.k_begin] : p.thr);
             const uint32_t series = s.series_id, lag0 = c.lag0;
             EpiState st;
 #pragma unroll

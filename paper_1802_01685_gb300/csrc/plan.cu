@@ -59,6 +59,10 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
     bf_opts o;
     bf_status st = resolve_opts(bank, opts, &o);
     if (st) return st;
+    if (o.tail_sigma == BF_SIGMA_PARSEVAL) {
+        set_error("plans take BF_SIGMA_WHITE tails (the Parseval predictor runs cuFFT outside the graph)");
+        return BF_ENOTSUP;
+    }
     o.stream = nullptr;
     o.rho_out = nullptr;
     for (size_t s = 0; s < n_series; ++s)

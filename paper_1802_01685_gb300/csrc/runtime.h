@@ -68,4 +68,9 @@ bf_status check_device_status(bf_ctx* ctx);
 
 void serve_shutdown(bf_ctx* ctx);
 
+// Parseval predictor of the noise level of rho (predict.cu)
+bf_status bank_power_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st);
+bf_status predict_sigma(bf_ctx* ctx, const bf_bank* bank, const PreparedSeries& ps, size_t k_begin,
+                        size_t k_end, float* out, std::vector<void*>& scratch, cudaStream_t st);
+
 }  // namespace bfi

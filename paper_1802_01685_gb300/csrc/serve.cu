@@ -105,6 +105,20 @@ static bool admit(ServeState* S, Request* r)
         r->error = bf_last_error();
         return false;
     }
+    if (res->parseval) {
+        std::lock_guard<std::mutex> g(ctx->launch_mu);    // the bank's spectra cache
+        st = bank_power_spectra(ctx, const_cast<bf_bank*>(bank), S->stream);
+        if (st == BF_OK)
+            st = predict_sigma(ctx, bank, r->prep, r->opts.bank_begin, r->opts.bank_end,
+                               res->sigma_pred, res->scratch, S->stream);
+        if (st != BF_OK) {
+            r->status = st;
+            r->error = bf_last_error();
+            r->prep.release(*ctx->mem);
+            bf_result_destroy(res);
+            return false;
+        }
+    }
     r->result = res;
     const uint32_t tile_t = tile_templates(r->opts.precision);
     r->tt_next = (uint32_t)(r->opts.bank_begin / tile_t);
@@ -172,10 +186,14 @@ static void scheduler(ServeState* S)
             uint64_t ntt = std::max<uint64_t>(1, per / std::max<uint32_t>(1, r->n_lag_tiles));
             ntt = std::min<uint64_t>(ntt, r->tt_end - r->tt_next);
             bf_result* res = r->result;
-            segs[r->opts.precision].emplace_back(
-                r, make_segment(r->prep, 0, r->bank, r->opts.bank_begin, r->opts.bank_end,
-                                r->tt_next, (uint32_t)ntt, r->opts.precision, res->packed,
-                                res->sumsq));
+            Seg g = make_segment(r->prep, 0, r->bank, r->opts.bank_begin, r->opts.bank_end,
+                                 r->tt_next, (uint32_t)ntt, r->opts.precision, res->packed,
+                                 res->sumsq);
+            if (res->parseval) {
+                g.sigma_pred = res->sigma_pred;
+                g.kappa = res->kappa;
+            }
+            segs[r->opts.precision].emplace_back(r, g);
             r->tt_next += (uint32_t)ntt;
             if (r->tt_next >= r->tt_end) finishing.push_back(r);
         }

@@ -173,6 +173,71 @@ def test_tiny_tails(ctx, tiny, prec):
     bf.bf_result_destroy(res)
 
 
+def test_parseval_predictor_matches_oracle(ctx):
+    """sigma_k predicted before the search (Parseval) against the FP64
+    oracle: white noise, coloured GW-like noise, a Poisson light curve, and a
+    series shorter than the 2M-sample FFT (one zero-padded segment)."""
+    rng = np.random.default_rng(41)
+    fs, M = 2048.0, 2048
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0, 0.35],
+                           20.0, 1000.0, 4, 5)                    # 160 templates
+    p = oracle_params(spec)
+    H = oracle.bank(p, fs, M)
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
+    xs = [synth.white(20000, rng).astype(np.float32),
+          synth.gw_coloured(30000, fs, rng).astype(np.float32),
+          synth.grb_lightcurve(25000, fs, rng).astype(np.float32),
+          synth.white(3000, rng).astype(np.float32)]
+    for prec in ("split_bf16", "fp32"):
+        res = bf.bf_correlate(ctx, bank, xs, fs, bf.make_opts(precision=prec, bank_begin=7,
+                                                               bank_end=150,
+                                                               tail_sigma=bf.BF_SIGMA_PARSEVAL))
+        for s, x in enumerate(xs):
+            got = bf.bf_result_copy_sigma_pred(res, s)
+            ref = oracle.parseval_sigma(x, H[7:150])
+            np.testing.assert_allclose(got, ref, rtol=2e-5, atol=1e-9)
+        bf.bf_result_destroy(res)
+    res = bf.bf_correlate(ctx, bank, xs[:1], fs)
+    with pytest.raises(bf.BFError):
+        bf.bf_result_copy_sigma_pred(res, 0)                      # not requested
+    bf.bf_result_destroy(res)
+    bf.bf_bank_destroy(bank)
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+def test_parseval_tails_and_map(ctx, prec):
+    """Tails |rho| >= kappa sigma_k with sigma_k predicted per template: the
+    list and the map against the oracle with per-template thresholds."""
+    w = synth.gw_pair(n=16384, I=8, J=8)
+    fs, M = w["fs"], w["M"]
+    x = w["series"][0]
+    p = oracle_params(w["grid"])
+    H = oracle.bank(p, fs, M)
+    kappa, tol = 3.0, TOL[prec]
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0)
+    res = bf.bf_correlate(ctx, bank, [x], fs, bf.make_opts(
+        precision=prec, kappa=kappa, want_tails=True, want_map=True,
+        tail_sigma=bf.BF_SIGMA_PARSEVAL))
+    sig = bf.bf_result_copy_sigma_pred(res, 0).astype(np.float64)
+    tails = bf.bf_result_copy_tails(res)
+    mp = bf.bf_result_copy_to_host(res, 0, want_map=True)["map"]
+    bf.bf_result_destroy(res)
+    ref_sig = oracle.parseval_sigma(x, H)
+    np.testing.assert_allclose(sig, ref_sig, rtol=2e-5)
+    thr = kappa * ref_sig
+    ref = oracle.search(x, fs, p, M, want_rho=True)
+    a = np.abs(ref["rho"])
+    slack = tol + kappa * 2e-5 * thr                              # rho and threshold rounding
+    got = {(int(t["k"]), int(t["tau"])) for t in tails}
+    must = set(zip(*[v.tolist() for v in np.nonzero(a >= (thr + slack)[:, None])]))
+    may = set(zip(*[v.tolist() for v in np.nonzero(a >= (thr - slack)[:, None])]))
+    assert len(must) > 0 and must <= got <= may
+    hi = oracle.search(x, fs, p, M, thr_k=thr + slack, want_map=True)["map"]
+    lo = oracle.search(x, fs, p, M, thr_k=thr - slack, want_map=True)["map"]
+    assert np.all(mp >= hi - tol) and np.all(mp <= lo + tol)
+    bf.bf_bank_destroy(bank)
+
+
 def test_injection_recovered(ctx):
     """A bank template injected into noise is found at its offset."""
     fs, M = 2048.0, 2048
