@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-METRIC = "correlations/s (lag-correlations, split-BF16 tcgen05 path, |err| <= 2e-5 vs FP64)"
+METRIC = "correlations/s on 1 GB300, split-BF16 vs FP32 at |err|<=2e-5; serve p50/p99 ms"
 UNIT = "correlations/s"
 
 # DRAM traffic of the tensor-core correlation kernel measured by ncu
@@ -271,7 +271,10 @@ def run_ours(args, rank, world, local):
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 (split) -> f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (split hi/lo operands, f32 accumulate)",
+        "metric_unit_note": "one correlation = one template at one lag (a length-M normalised "
+                            "inner product); the FP32 path and serving p50/p99 are in fp32_path "
+                            "and serve",
         "data": "synthetic (seeded numpy PCG64; coloured Gaussian noise + power-law chirp)",
         "config": {"workload": "gw_pair: 2 x 262144 samples at 4096 Hz + 2 time-randomised "
                                "controls, 65536 power-law templates x 4096 samples",
