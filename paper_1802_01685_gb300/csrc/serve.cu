@@ -197,9 +197,10 @@ static void scheduler(ServeState* S)
             r->tt_next += (uint32_t)ntt;
             if (r->tt_next >= r->tt_end) finishing.push_back(r);
         }
-        // Requests without a map share one launch per precision (tails are not
-        // collected); a request with a map owns the candidate buffer its
-        // segment writes, so it gets a launch of its own in the same iteration.
+        // Requests that keep no tails share one launch per precision (no tail is
+        // collected there); a request with a map or a tail list owns the
+        // candidate buffer its segment writes, so it gets a launch of its own
+        // in the same iteration.
         bool any = false;
         for (int prec = 0; prec < 3; ++prec) {
             if (segs[prec].empty()) continue;
@@ -207,14 +208,16 @@ static void scheduler(ServeState* S)
             std::vector<Request*> shared_owner;
             for (auto& rs : segs[prec]) {
                 Request* r = rs.first;
-                if (r->result->want_map) {
+                if (r->result->cand_cap > 0) {
                     std::vector<Seg> one{rs.second};
                     cudaError_t e = launch_segments(ctx, one, prec, r->result->thr, r->result->cand,
                                                     r->result->cand_count, r->result->cand_cap,
                                                     S->stream, nullptr);
                     if (e != cudaSuccess) { r->status = cuda_fail(e, "serve launch"); r->cancel = true; }
                 } else {
-                    shared.push_back(rs.second);
+                    Seg g = rs.second;
+                    g.sigma_pred = nullptr;           // no tails in a shared launch
+                    shared.push_back(g);
                     shared_owner.push_back(r);
                 }
             }

@@ -35,20 +35,22 @@ def requests():
             (3.0, 0, 2048, "split_bf16", False), (7.5, 100, 1900, "split_bf16", True),
             (2.0, 0, 512, "bf16", False), (12.25, 640, 2048, "split_bf16", False),
             (4.0, 0, 1024, "fp32", True), (1.0 + 1 / 2048, 5, 133, "split_bf16", False),
-            (5.0, 64, 1500, "split_bf16", True)]):
+            (5.0, 64, 1500, "split_bf16", True), (3.5, 0, 2048, "split_bf16", False)]):
         n = int(secs * FS)
         x = synth.white(n, rng).astype(np.float32) if i % 2 == 0 else \
             synth.grb_lightcurve(n, FS, rng).astype(np.float32)
         out.append((x, bf.make_opts(precision=prec, bank_begin=k0, bank_end=k1, want_map=mp,
-                                    kappa=4.0, want_tails=mp,
+                                    kappa=4.0, want_tails=mp or i == 7,
                                     tail_sigma=bf.BF_SIGMA_PARSEVAL if i == 6 else bf.BF_SIGMA_WHITE)))
     return out
 
 
-def fetch(res, want_map, parseval=False):
+def fetch(res, want_map, parseval=False, tails=False):
     r = bf.bf_result_copy_to_host(res, 0, want_hist=True, want_map=want_map)
     if parseval:
         r["sigma_pred"] = bf.bf_result_copy_sigma_pred(res, 0)
+    if tails:
+        r["tails"] = np.sort(bf.bf_result_copy_tails(res), order=["k", "tau"])
     bf.bf_result_destroy(res)
     return r
 
@@ -56,14 +58,14 @@ def fetch(res, want_map, parseval=False):
 def test_each_result_is_the_same_alone_and_in_the_mix(served):
     ctx, bank = served
     reqs = requests()
-    alone = [fetch(bf.bf_correlate(ctx, bank, [x], FS, o), o.want_map, o.tail_sigma == 1)
-             for x, o in reqs]
+    alone = [fetch(bf.bf_correlate(ctx, bank, [x], FS, o), o.want_map, o.tail_sigma == 1,
+                   o.want_tails == 1) for x, o in reqs]
     tickets = [bf.bf_serve_submit(ctx, bank, x, FS, o) for x, o in reqs]
     mixed = []
     for t, (x, o) in zip(tickets, reqs):
         st, res = bf.bf_serve_poll(ctx, t, 60_000_000)
         assert st == bf.BF_OK
-        mixed.append(fetch(res, o.want_map, o.tail_sigma == 1))
+        mixed.append(fetch(res, o.want_map, o.tail_sigma == 1, o.want_tails == 1))
     for a, m in zip(alone, mixed):
         np.testing.assert_array_equal(m["max"], a["max"])
         np.testing.assert_array_equal(m["argmax"], a["argmax"])
@@ -73,6 +75,9 @@ def test_each_result_is_the_same_alone_and_in_the_mix(served):
             np.testing.assert_array_equal(m["map"], a["map"])
         if "sigma_pred" in a:
             np.testing.assert_array_equal(m["sigma_pred"], a["sigma_pred"])
+        if "tails" in a:
+            assert len(a["tails"]) > 0
+            np.testing.assert_array_equal(m["tails"], a["tails"])
     s = bf.bf_serve_stats_get(ctx)
     assert s.completed >= len(reqs) and s.p99_ms >= s.p50_ms > 0
 
