@@ -28,7 +28,7 @@ _lock = threading.Lock()
 _lib = None
 
 LINEAR, POWERLAW = 0, 1
-ASC, DESC = 0, 1
+ASC, DESC, BOTH = 0, 1, 2
 
 
 def build(force: bool = False) -> str:

@@ -28,7 +28,7 @@
 #define O_PI 3.14159265358979323846
 
 enum { O_LINEAR = 0, O_POWERLAW = 1 };
-enum { O_ASC = 0, O_DESC = 1 };
+enum { O_ASC = 0, O_DESC = 1, O_BOTH = 2 };
 
 /* ------------------------------------------------------------------------ */
 /* Chirp tracks (Sect. 2.1: trajectories f(t) of finite slope; ascending and  */
@@ -83,7 +83,7 @@ int oracle_check_chirp(int track, int sense, double f_lo, double f_hi, double D,
                        double fs, long M)
 {
     if (track != O_LINEAR && track != O_POWERLAW) return -1;
-    if (sense != O_ASC && sense != O_DESC) return -1;
+    if (sense != O_ASC && sense != O_DESC && sense != O_BOTH) return -1;
     if (!(fs > 0.0) || M <= 0) return -1;
     if (!(f_lo > 0.0) || !(f_hi > f_lo) || !(f_hi < 0.5 * fs)) return -1;
     if (!(D > 0.0)) return -1;
@@ -93,12 +93,13 @@ int oracle_check_chirp(int track, int sense, double f_lo, double f_hi, double D,
 }
 
 /*
- * One template h[0..M-1] (Sect. 2.1, "templates ... ascending and descending
- * chirps of intermediate duration").  Reading:
+ * One template h[0..M-1] (Sect. 2.1, "templates ... superpositions of
+ * ascending and descending chirps of intermediate duration").  Reading:
  *   j = m - m_s in [0, M_D), t = j / fs,
  *   g[m] = sin^2(pi (j + 1/2) / M_D) * cos(2 pi c(t)),  zero off the support,
- *   descending: h_desc[m] = h_asc[M - 1 - m],
- *   h = g / sqrt(sum g^2)   (unit L2 norm).
+ *   descending: g[M - 1 - m] (the time reverse),
+ *   both ("butterfly"): g[m] + g[M - 1 - m], the superposition of the two,
+ *   h = the chosen g / sqrt(sum g^2)   (unit L2 norm).
  */
 int oracle_template(int track, int sense, double f_lo, double f_hi, double D,
                     double fs, long M, double *h)
@@ -113,11 +114,18 @@ int oracle_template(int track, int sense, double f_lo, double f_hi, double D,
         double c = oracle_cycles(track, f_lo, f_hi, D, t);
         h[ms + j] = s * s * cos(2.0 * O_PI * c);
     }
+    if (sense == O_BOTH) {
+        for (long a = 0, b = M - 1; a <= b; ++a, --b) {
+            double s = h[a] + h[b];
+            h[a] = s;
+            h[b] = s;
+        }
+    }
     double e = 0.0;
     for (long m = 0; m < M; ++m) e += h[m] * h[m];
     double inv = 1.0 / sqrt(e);
     for (long m = 0; m < M; ++m) h[m] *= inv;
-    if (sense == O_DESC) {
+    if (sense == O_DESC) {       /* reversal keeps the norm: reverse last */
         for (long a = 0, b = M - 1; a < b; ++a, --b) {
             double tmp = h[a];
             h[a] = h[b];
@@ -203,9 +211,9 @@ void oracle_correlate_raw(const float *x, long N, const double *h, long M,
  *                    spectrogram, Sect. 2.1).  Must be zeroed by the caller.
  * Returns 0, or -1 for invalid input.
  */
-static void paint_track(double *map, long nt, long nf, double dt, double df,
-                        int track, int sense, double f_lo, double f_hi, double D,
-                        double fs, long M, long tau, double a)
+static void paint_one(double *map, long nt, long nf, double dt, double df,
+                      int track, int sense, double f_lo, double f_hi, double D,
+                      double fs, long M, long tau, double a)
 {
     long MD = oracle_support_len(D, fs);
     long first = oracle_support_first(sense, M, MD);
@@ -228,6 +236,19 @@ static void paint_track(double *map, long nt, long nf, double dt, double df,
         if (fb < 0 || fb >= nf) continue;
         double *cell = map + b * nf + fb;
         if (a > *cell) *cell = a;
+    }
+}
+
+/* a superposed ("butterfly") template paints both of its tracks */
+static void paint_track(double *map, long nt, long nf, double dt, double df,
+                        int track, int sense, double f_lo, double f_hi, double D,
+                        double fs, long M, long tau, double a)
+{
+    if (sense == O_BOTH) {
+        paint_one(map, nt, nf, dt, df, track, O_ASC, f_lo, f_hi, D, fs, M, tau, a);
+        paint_one(map, nt, nf, dt, df, track, O_DESC, f_lo, f_hi, D, fs, M, tau, a);
+    } else {
+        paint_one(map, nt, nf, dt, df, track, sense, f_lo, f_hi, D, fs, M, tau, a);
     }
 }
 

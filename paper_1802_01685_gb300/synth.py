@@ -18,9 +18,10 @@ from __future__ import annotations
 
 import numpy as np
 
-# chirp-parameter codes shared with the C-ABI (plain enumerations)
+# chirp-parameter codes shared with the C-ABI (plain enumerations; BOTH is
+# the superposition of an ascending chirp and its time reverse)
 LINEAR, POWERLAW = 0, 1
-ASC, DESC = 0, 1
+ASC, DESC, BOTH = 0, 1, 2
 
 
 # ------------------------------------------------------------- test signals

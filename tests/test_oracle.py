@@ -220,6 +220,35 @@ def test_template_unit_norm_support_and_reversal():
             assert oracle.support_first(oracle.DESC, Mt, MD) == Mt - ms - MD
 
 
+def test_butterfly_template_is_the_superposition_of_both_senses():
+    """BOTH = (ascending + its time reverse), unit norm: it is symmetric in
+    time and equals (h_asc + h_desc) / |h_asc + h_desc| because both have unit
+    norm; its track paints both senses on the map."""
+    for track in (oracle.LINEAR, oracle.POWERLAW):
+        args = (track, 80.0, 700.0, 0.6, 2048.0, 2048)
+        a = oracle.template(args[0], oracle.ASC, *args[1:])
+        d = oracle.template(args[0], oracle.DESC, *args[1:])
+        b = oracle.template(args[0], oracle.BOTH, *args[1:])
+        ref = (a + d) / np.linalg.norm(a + d)
+        np.testing.assert_allclose(b, ref, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(b, b[::-1], rtol=0, atol=1e-15)
+        assert abs(np.sum(b * b) - 1.0) < 1e-13
+    fs, Mt = 2048.0, 2048
+    h = oracle.template(oracle.LINEAR, oracle.BOTH, 200.0, 600.0, 1.0, fs, Mt)
+    x = np.zeros(3 * Mt, np.float32)
+    x[500:500 + Mt] = h
+    p = dict(track=np.array([0], np.int32), sense=np.array([oracle.BOTH], np.int32),
+             f_lo=np.array([200.0]), f_hi=np.array([600.0]), D=np.array([1.0]))
+    mp = oracle.search(x, fs, p, Mt, want_map=True)["map"]
+    pa = dict(p, sense=np.array([oracle.ASC], np.int32))
+    pd = dict(p, sense=np.array([oracle.DESC], np.int32))
+    ha = oracle.template(oracle.LINEAR, oracle.ASC, 200.0, 600.0, 1.0, fs, Mt)
+    # the map of the superposition holds an X: a rising and a falling track
+    b = 500 + Mt // 4
+    row = mp[int((b / fs) / 1e-3)]
+    assert np.count_nonzero(row > 0.9) >= 2
+
+
 def test_linear_template_phase_matches_scipy_chirp():
     fs, Mt, D, f0, f1 = 2048.0, 2048, 0.75, 120.0, 640.0
     h = oracle.template(oracle.LINEAR, oracle.ASC, f0, f1, D, fs, Mt)
