@@ -57,7 +57,12 @@ typedef enum {
 
 /* chirp track and sense (Sect. 2.1: ascending and descending chirps) */
 typedef enum { BF_LINEAR = 0, BF_POWERLAW = 1 } bf_track;
-typedef enum { BF_ASC = 0, BF_DESC = 1 } bf_sense;
+typedef enum {
+    BF_ASC = 0,
+    BF_DESC = 1,
+    BF_BOTH = 2     /* superposition of the ascending chirp and its time reverse
+                       (the "butterfly": both tracks at once), unit norm       */
+} bf_sense;
 
 /* threshold of the tails rho > kappa sigma (Sect. 2.2) */
 typedef enum { BF_SIGMA_WHITE = 0, BF_SIGMA_PARSEVAL = 1 } bf_tail_sigma;
@@ -90,7 +95,8 @@ enum {
  *   linear:    f(t) = f_lo + (f_hi - f_lo) t / D
  *   power law: f(t) = f_lo (1 - t/t_c)^(-3/8), t_c = D / (1 - (f_lo/f_hi)^(8/3))
  *   g[m] = sin^2(pi (m - m_s + 1/2) / M_D) cos(2 pi integral_0^t f),
- *   descending templates are the time reverse h[M-1-m] of the ascending one,
+ *   descending templates are the time reverse g[M-1-m] of the ascending one,
+ *   BF_BOTH templates are g[m] + g[M-1-m],
  *   h = g / |g|_2.
  * Requires 0 < f_lo < f_hi < fs / 2.
  */

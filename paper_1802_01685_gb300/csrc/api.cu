@@ -129,7 +129,10 @@ uint32_t template_len(double T, double fs) { return (uint32_t)std::floor(T * fs 
 static bool chirp_ok(const bf_chirp& c, double fs, uint32_t M, char* why, size_t n)
 {
     if (c.track != BF_LINEAR && c.track != BF_POWERLAW) { snprintf(why, n, "bad track %d", c.track); return false; }
-    if (c.sense != BF_ASC && c.sense != BF_DESC) { snprintf(why, n, "bad sense %d", c.sense); return false; }
+    if (c.sense != BF_ASC && c.sense != BF_DESC && c.sense != BF_BOTH) {
+        snprintf(why, n, "bad sense %d", c.sense);
+        return false;
+    }
     if (!(c.f_lo > 0.0) || !(c.f_hi > c.f_lo) || !(c.f_hi < 0.5 * fs)) {
         snprintf(why, n, "need 0 < f_lo < f_hi < fs/2 (f_lo=%g f_hi=%g fs=%g)", c.f_lo, c.f_hi, fs);
         return false;

@@ -88,16 +88,20 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
     double part = 0.0;
     for (uint32_t m = threadIdx.x; m < M_s; m += blockDim.x) {
         float v = 0.f;
-        if (valid) {
-            int j = (int)m - p.first;          // ascending-template sample index
-            if (p.sense == BF_DESC) j = (int)(M - 1 - m) - p.first;
-            if (m < M && j >= 0 && j < p.MD) {
+        if (valid && m < M) {
+            // ascending-template sample index of m, and of its mirror M-1-m
+            const int ja = (int)m - p.first, jd = (int)(M - 1 - m) - p.first;
+            auto sample = [&](int j) -> float {
+                if (j < 0 || j >= p.MD) return 0.f;
                 const double c = d_cycles(p.track, k1, k2, (double)j * inv_fs);
                 const double fr = c - rint(c);             // [-1/2, 1/2]
                 const float cs = cospif((float)(2.0 * fr));
                 const float sn = sinpif(((float)j + 0.5f) * inv_md);
-                v = sn * sn * cs;
-            }
+                return sn * sn * cs;
+            };
+            if (p.sense == BF_ASC) v = sample(ja);
+            else if (p.sense == BF_DESC) v = sample(jd);
+            else v = sample(ja) + sample(jd);          // superposition of both senses
         }
         g[m] = v;
         part += (double)v * (double)v;

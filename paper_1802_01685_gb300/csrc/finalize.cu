@@ -89,23 +89,27 @@ __global__ void k_paint(const Candidate* __restrict__ cand, const unsigned int* 
         if (cd.series < fp.s0 || cd.series >= fp.s0 + fp.n) continue;
         const ChirpDev p = params[cd.k];
         const FinalizeSeries& f = fp.ser[cd.series - fp.s0];
-        const int64_t first = p.sense == BF_ASC ? p.first : (int64_t)M - p.first - p.MD;
+        const float a = fabsf(cd.rho);
+        // a superposed template paints both of its tracks
+        for (int pass = 0; pass < (p.sense == BF_BOTH ? 2 : 1); ++pass) {
+        const int sense = p.sense == BF_BOTH ? (pass == 0 ? BF_ASC : BF_DESC) : p.sense;
+        const int64_t first = sense == BF_ASC ? p.first : (int64_t)M - p.first - p.MD;
         const double t0 = (double)((int64_t)cd.tau + first) / fs;
         const double t1 = (double)((int64_t)cd.tau + first + p.MD) / fs;
         int64_t b_lo = (int64_t)floor(t0 / dt - 0.5);
         const int64_t b_hi = (int64_t)ceil(t1 / dt);
         if (b_lo < 0) b_lo = 0;
-        const float a = fabsf(cd.rho);
         for (int64_t b = b_lo + lane; b <= b_hi && b < (int64_t)f.nt; b += 32) {
             const double tb = ((double)b + 0.5) * dt;
             if (!(tb >= t0 && tb < t1)) continue;
             const double t = tb - t0;
-            double u = p.sense == BF_ASC ? t : p.D - t;
+            double u = sense == BF_ASC ? t : p.D - t;
             if (u < 0.0) u = 0.0;
             if (u > p.D) u = p.D;
             const int64_t fb = (int64_t)floor(track_freq(p, u) / df);
             if (fb < 0 || fb >= (int64_t)nf) continue;
             atomicMax(reinterpret_cast<int*>(f.map + (size_t)b * nf + fb), __float_as_int(a));
+        }
         }
     }
 }

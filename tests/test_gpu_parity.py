@@ -40,7 +40,8 @@ def test_bank_templates_match_oracle(ctx):
     chirps = [(bf.BF_LINEAR, bf.BF_ASC, 50.0, 1000.0, 1.0), (bf.BF_LINEAR, bf.BF_DESC, 600.0, 700.0, 0.2),
               (bf.BF_POWERLAW, bf.BF_ASC, 20.0, 1000.0, 0.2), (bf.BF_POWERLAW, bf.BF_DESC, 40.0, 400.0, 1.0),
               (bf.BF_POWERLAW, bf.BF_ASC, 999.0, 1000.0, 0.55), (bf.BF_LINEAR, bf.BF_ASC, 1.0, 2.0, 0.37),
-              (bf.BF_POWERLAW, bf.BF_ASC, 2.0, 1000.0, 1.0), (bf.BF_POWERLAW, bf.BF_DESC, 30.0, 1000.0, 0.3)]
+              (bf.BF_POWERLAW, bf.BF_ASC, 2.0, 1000.0, 1.0), (bf.BF_POWERLAW, bf.BF_DESC, 30.0, 1000.0, 0.3),
+              (bf.BF_LINEAR, bf.BF_BOTH, 120.0, 800.0, 1.0), (bf.BF_POWERLAW, bf.BF_BOTH, 40.0, 400.0, 0.45)]
     fs, T = 2048.0, 1.0
     for storage in (bf.BF_BANK_FP32, bf.BF_BANK_SPLIT_BF16):
         bank = bf.bf_bank_create(ctx, chirps, fs, T, storage)
@@ -235,6 +236,32 @@ def test_parseval_tails_and_map(ctx, prec):
     hi = oracle.search(x, fs, p, M, thr_k=thr + slack, want_map=True)["map"]
     lo = oracle.search(x, fs, p, M, thr_k=thr - slack, want_map=True)["map"]
     assert np.all(mp >= hi - tol) and np.all(mp <= lo + tol)
+    bf.bf_bank_destroy(bank)
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+def test_butterfly_templates(ctx, prec):
+    """Superposed templates (ascending + descending, both senses at once):
+    dense rho, maxima and the map of their two tracks against the oracle."""
+    fs, M = 2048.0, 2048
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.BOTH], [1.0, 0.5],
+                           50.0, 1000.0, 4, 4)                   # 64 templates
+    p = oracle_params(spec)
+    rng = np.random.default_rng(52)
+    x = rng.standard_normal(9000)
+    h = oracle.template(int(p["track"][5]), synth.BOTH, p["f_lo"][5], p["f_hi"][5], 1.0, fs, M)
+    x[2000:2000 + M] += 20.0 * h
+    x = x.astype(np.float32)
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
+    ref = oracle.search(x, fs, p, M, want_rho=True)
+    K, L = ref["rho"].shape
+    rho = torch.zeros((K, L), dtype=torch.float32, device="cuda")
+    outs, _, _ = run(ctx, bank, [x], fs, prec, rho_out=rho)
+    assert np.abs(rho.cpu().numpy() - ref["rho"]).max() <= TOL[prec]
+    check_maxima(outs[0], ref, ref["rho"], TOL[prec], prec)
+    assert outs[0]["argmax"][5] == 2000
+    outs, _, _ = run(ctx, bank, [x], fs, prec, want_map=True, kappa=4.0)
+    check_map(outs[0]["map"], x, fs, p, M, 4.0, TOL[prec])
     bf.bf_bank_destroy(bank)
 
 
