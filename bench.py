@@ -8,8 +8,8 @@ chirp -- plus their two time-randomised controls, searched against a bank of
 stage of the path: template synthesis, the two controls, series preparation
 (split rows, FP64 prefix norms), the batched split-BF16 tensor-core correlation
 of all four series in one launch, the fused epilogue (max/argmax, sigma,
-tails), finalize (histogram of maxima, time-frequency map painting) -- all
-through the C ABI.
+tails), finalize (histogram of maxima, time-frequency map painting) and the
+skew-normal fits of the maxima of data and controls -- all through the C ABI.
 
 metric: lag-correlations per second (one normalised length-M inner product of
 one template at one lag), whole job.  Printed as one JSON line by rank 0.
@@ -186,6 +186,7 @@ def run_ours(args, rank, world, local):
     kernel_ms = []
     stage_ms = {}
     shapes = set()
+    fits = {}
 
     def step(record=False):
         t0 = time.perf_counter()
@@ -195,9 +196,13 @@ def run_ours(args, rank, world, local):
             bf.bf_control_randomize(ctx, x, sd, c)
         t2 = time.perf_counter()
         res = bf.bf_correlate(ctx, bank, xs + ctrl, fs, opts)
+        # skew-normal fits of the maxima: data (series 0, 1) vs controls (2, 3)
+        fit = [bf.bf_result_fit_max(res, s) for s in range(4)]
         t3 = time.perf_counter()
         info = bf.bf_result_info_get(res)
         if record:
+            fits.update({name: {k: round(fit[i][k], 6) for k in ("xi", "omega", "alpha")}
+                         for i, name in enumerate(("data_0", "data_1", "control_0", "control_1"))})
             kernel_ms.append(info.kernel_ms)
             shapes.add(info.tile_lags)
             for k, v in (("bank_synthesis", t1 - t0), ("controls", t2 - t1), ("correlate", t3 - t2)):
@@ -283,10 +288,12 @@ def run_ours(args, rank, world, local):
                    "precision": "split_bf16", "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (split bank 1.07 GB re-synthesised every step)",
                    "stages_in_step": ["bank_synthesis", "controls", "series_prep",
-                                      "correlation+epilogue", "finalize+hist+map"]},
+                                      "correlation+epilogue", "finalize+hist+map",
+                                      "skew-normal fit of maxima"]},
         "stage_ms": {k: round(float(np.mean(v)), 2) for k, v in stage_ms.items()},
         "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
         "fp32_path": fp32, "accuracy_vs_oracle": accuracy, "cpu_baseline": cpu, "serve": serve,
+        "maxima_fit": fits,
     }
 
 

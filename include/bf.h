@@ -250,6 +250,29 @@ bf_status bf_result_copy_to_host(const bf_result* r, size_t s, float* vmax,
                                  float* map);
 bf_status bf_result_copy_mean_max(const bf_result* r, float* host_mean_max);
 
+/* Skew-normal fit of the per-template maxima (Sect. 1, Fig. 2: the
+ * distributions of maxima of the filter output, for the data and for the
+ * time-randomised control, are left-truncated skewed Gaussians whose
+ * difference is the statistic).  The fit is the method of moments of
+ * Azzalini (1985) on the population (1/n) moments, computed in FP64 on the
+ * device; the skewness is clipped to the skew-normal's range |g| < 0.99527
+ * and the truncation is not modelled.  Density of the fit:
+ *   f(v) = 2/omega phi((v - xi)/omega) Phi(alpha (v - xi)/omega). */
+typedef struct bf_skewnorm {
+    double n;                /* number of maxima fitted                          */
+    double mean, sd;         /* sample mean and standard deviation (1/n)         */
+    double skewness;         /* sample skewness, after clipping                  */
+    double xi, omega, alpha; /* location, scale, shape                           */
+} bf_skewnorm;
+
+#define BF_FIT_MEAN ((size_t)-1)
+
+/* Fits the maxima of series s, or with s = BF_FIT_MEAN the mean over series
+ * (bf_result_get_mean_max).  Runs on `stream` (NULL: the context stream),
+ * after whatever the caller enqueued there, and synchronises it before
+ * writing *out.  BF_EINVAL for a bad index or a NULL argument. */
+bf_status bf_result_fit_max(const bf_result* r, size_t s, void* stream, bf_skewnorm* out);
+
 /*
  * Predicted noise level of rho (Sect. 2.2 and Fig. 5 caption: sigma from
  * Parseval's theorem in a predictor step, before the search), kept when

@@ -239,6 +239,33 @@ def parseval_sigma(x: np.ndarray, H: np.ndarray) -> np.ndarray:
     return out
 
 
+def skewnorm_fit(v: np.ndarray) -> dict:
+    """Skew-normal fit of the per-template maxima (Fig. 2: the distributions of
+    maxima are left-truncated skewed Gaussians) by the method of moments of
+    Azzalini (1985): from the sample mean m, standard deviation s and skewness
+    g (clipped to the skew-normal's range |g| < 0.99527),
+      |delta| = sqrt(pi/2 * |g|^(2/3) / (|g|^(2/3) + ((4 - pi)/2)^(2/3))),
+      alpha = delta / sqrt(1 - delta^2),
+      omega = s / sqrt(1 - 2 delta^2 / pi),  xi = m - omega delta sqrt(2/pi).
+    Moments use the population (1/n) normalisation; the truncation is not
+    modelled."""
+    v = np.asarray(v, np.float64)
+    n = len(v)
+    m = v.mean()
+    d = v - m
+    var = np.mean(d * d)
+    sd = np.sqrt(var)
+    g = np.mean(d ** 3) / var ** 1.5 if var > 0 else 0.0
+    gmax = 0.99527
+    g = float(np.clip(g, -gmax, gmax))
+    a = abs(g) ** (2.0 / 3.0)
+    delta = np.sign(g) * np.sqrt(np.pi / 2.0 * a / (a + ((4.0 - np.pi) / 2.0) ** (2.0 / 3.0)))
+    alpha = delta / np.sqrt(1.0 - delta * delta)
+    omega = sd / np.sqrt(1.0 - 2.0 * delta * delta / np.pi)
+    xi = m - omega * delta * np.sqrt(2.0 / np.pi)
+    return dict(n=n, mean=m, sd=sd, skewness=g, xi=xi, omega=omega, alpha=alpha)
+
+
 def histogram(v: np.ndarray, nbins: int = 1024) -> np.ndarray:
     v = np.ascontiguousarray(v, np.float64)
     c = np.zeros(nbins, np.uint32)

@@ -76,6 +76,15 @@ class bf_result_info(C.Structure):
                 ("hist_bins", C.c_uint32), ("kernel_ms", C.c_double), ("tile_lags", C.c_int32)]
 
 
+class bf_skewnorm(C.Structure):
+    _fields_ = [("n", C.c_double), ("mean", C.c_double), ("sd", C.c_double),
+                ("skewness", C.c_double), ("xi", C.c_double), ("omega", C.c_double),
+                ("alpha", C.c_double)]
+
+
+BF_FIT_MEAN = (1 << 64) - 1
+
+
 class bf_request(C.Structure):
     _fields_ = [("series", C.c_void_p), ("n", C.c_size_t), ("fs", C.c_double),
                 ("bank", C.c_void_p), ("opts", bf_opts)]
@@ -126,6 +135,7 @@ def load() -> C.CDLL:
             "bf_result_get_mean_max": (i, [p, P(p)]),
             "bf_result_copy_to_host": (i, [p, s, p, p, p, p, p]),
             "bf_result_copy_mean_max": (i, [p, p]),
+            "bf_result_fit_max": (i, [p, s, p, P(bf_skewnorm)]),
             "bf_result_tails": (i, [p, P(p), P(s)]),
             "bf_result_get_sigma_pred": (i, [p, s, P(p)]),
             "bf_result_copy_sigma_pred": (i, [p, s, p]),
@@ -338,6 +348,14 @@ def bf_result_copy_mean_max(res: int) -> np.ndarray:
     out = np.zeros(K, np.float32)
     _check(load().bf_result_copy_mean_max(res, out.ctypes.data))
     return out
+
+
+def bf_result_fit_max(res: int, s: int = BF_FIT_MEAN, stream=None) -> dict:
+    """Skew-normal fit of the maxima of series s (default: of their mean over
+    series); returns the fields of bf_skewnorm as a dict."""
+    out = bf_skewnorm()
+    _check(load().bf_result_fit_max(res, s, stream, C.byref(out)))
+    return {name: getattr(out, name) for name, _ in bf_skewnorm._fields_}
 
 
 TAIL_DTYPE = np.dtype([("series", np.uint32), ("k", np.uint32), ("tau", np.uint32),

@@ -1147,6 +1147,33 @@ bf_status bf_result_copy_mean_max(const bf_result* r, float* out)
     return e == cudaSuccess ? BF_OK : cuda_fail(e, "result copy");
 }
 
+bf_status bf_result_fit_max(const bf_result* r, size_t s, void* stream, bf_skewnorm* out)
+{
+    if (!r || !out) { set_error("NULL argument"); return BF_EINVAL; }
+    if (s != BF_FIT_MEAN && s >= r->n_series) { set_error("bad series index"); return BF_EINVAL; }
+    if (r->K == 0) { set_error("no templates to fit"); return BF_EINVAL; }
+    bf_ctx* ctx = r->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    const float* v = s == BF_FIT_MEAN ? r->mean_max : r->vmax + s * r->K;
+    double* acc = static_cast<double*>(ctx->mem->alloc(16 * sizeof(double)));
+    if (!acc) { set_error("out of device memory (fit)"); return BF_ENOMEM; }
+    double host[7];
+    cudaError_t e = launch_skewnorm_fit(v, r->K, acc, acc + 8, ctx->n_sm, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, acc + 8, sizeof host, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    ctx->mem->release(acc);
+    if (e != cudaSuccess) return cuda_fail(e, "skew-normal fit");
+    out->n = host[0];
+    out->mean = host[1];
+    out->sd = host[2];
+    out->skewness = host[3];
+    out->xi = host[4];
+    out->omega = host[5];
+    out->alpha = host[6];
+    return BF_OK;
+}
+
 bf_status bf_result_get_sigma_pred(const bf_result* r, size_t s, const float** sigma_pred)
 {
     if (!r || s >= r->n_series || !sigma_pred) { set_error("bad argument"); return BF_EINVAL; }

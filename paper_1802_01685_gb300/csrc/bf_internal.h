@@ -143,6 +143,8 @@ struct FinalizeParams {
     FinalizeSeries ser[MAX_FIN];
 };
 cudaError_t launch_finalize(const FinalizeParams& p, uint32_t K, uint32_t nbins, cudaStream_t s);
+cudaError_t launch_skewnorm_fit(const float* v, uint64_t n, double* acc, double* out, int n_sm,
+                                cudaStream_t s);
 cudaError_t launch_mean_max(const float* vmax, uint32_t n_series, uint32_t K, float* mean,
                             cudaStream_t s);
 cudaError_t launch_paint(const Candidate* cand, const unsigned int* count,

@@ -69,6 +69,92 @@ cudaError_t launch_mean_max(const float* vmax, uint32_t n_series, uint32_t K, fl
     return cudaGetLastError();
 }
 
+// Moments of the maxima for the skew-normal fit (Fig. 2: the distributions
+// of maxima of the filter output are left-truncated skewed Gaussians).  Two
+// FP64 passes over v[0, n): pass 0 sums v into acc[0]; pass 1 sums the
+// squared and cubed deviations from mean = acc[0] / n into acc[1], acc[2].
+__global__ void k_moments(const float* __restrict__ v, uint64_t n, int pass, double* __restrict__ acc)
+{
+    const double mean = pass ? acc[0] / (double)n : 0.0;
+    double a = 0.0, b = 0.0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const double x = (double)v[i];
+        if (pass == 0) {
+            a += x;
+        } else {
+            const double d = x - mean, d2 = d * d;
+            a += d2;
+            b += d2 * d;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    __shared__ double sa[32], sb[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { sa[w] = a; sb[w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        a = lane < nw ? sa[lane] : 0.0;
+        b = lane < nw ? sb[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
+            atomicAdd(acc + (pass ? 1 : 0), a);
+            if (pass) atomicAdd(acc + 2, b);
+        }
+    }
+}
+
+// Method-of-moments skew-normal parameters (Azzalini 1985) from the sums of
+// k_moments: sample skewness g, clipped to the family's range, gives
+// |delta| = sqrt(pi/2 |g|^(2/3) / (|g|^(2/3) + ((4 - pi)/2)^(2/3))) with the
+// sign of g, then alpha = delta / sqrt(1 - delta^2), omega = sd /
+// sqrt(1 - 2 delta^2 / pi) and xi = mean - omega delta sqrt(2 / pi).
+// out = {n, mean, sd, skewness, xi, omega, alpha}.
+__global__ void k_skewnorm_close(const double* __restrict__ acc, uint64_t n, double* __restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double pi = 3.14159265358979323846;
+    const double dn = (double)n;
+    const double mean = acc[0] / dn, var = acc[1] / dn, m3 = acc[2] / dn;
+    const double sd = sqrt(var);
+    double g = var > 0.0 ? m3 / (var * sd) : 0.0;
+    const double gmax = 0.99527;
+    g = fmin(fmax(g, -gmax), gmax);
+    const double a = pow(fabs(g), 2.0 / 3.0);
+    const double c = pow((4.0 - pi) / 2.0, 2.0 / 3.0);
+    const double delta = copysign(sqrt(pi / 2.0 * a / (a + c)), g);
+    out[0] = dn;
+    out[1] = mean;
+    out[2] = sd;
+    out[3] = g;
+    const double omega = sd / sqrt(1.0 - 2.0 * delta * delta / pi);
+    out[4] = mean - omega * delta * sqrt(2.0 / pi);
+    out[5] = omega;
+    out[6] = delta / sqrt(1.0 - delta * delta);
+}
+
+// acc: 3 doubles (zeroed here); out: 7 doubles, both device memory
+cudaError_t launch_skewnorm_fit(const float* v, uint64_t n, double* acc, double* out, int n_sm,
+                                cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(acc, 0, 3 * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    const uint64_t want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, 4ull * n_sm));
+    count_launches(3);
+    k_moments<<<blocks, 256, 0, s>>>(v, n, 0, acc);
+    k_moments<<<blocks, 256, 0, s>>>(v, n, 1, acc);
+    k_skewnorm_close<<<1, 32, 0, s>>>(acc, n, out);
+    return cudaGetLastError();
+}
+
 __device__ __forceinline__ double track_freq(const ChirpDev& p, double u)
 {
     if (p.track == BF_LINEAR) return p.f_lo + (p.f_hi - p.f_lo) * u / p.D;

@@ -85,7 +85,8 @@ def test_struct_layouts_match_the_header(lib, tmp_path):
     structs = {"bf_config": bf.bf_config, "bf_chirp": bf.bf_chirp,
                "bf_chirp_grid": bf.bf_chirp_grid, "bf_opts": bf.bf_opts,
                "bf_result_info": bf.bf_result_info, "bf_request": bf.bf_request,
-               "bf_serve_stats": bf.bf_serve_stats, "bf_tail": bf.bf_tail}
+               "bf_serve_stats": bf.bf_serve_stats, "bf_tail": bf.bf_tail,
+               "bf_skewnorm": bf.bf_skewnorm}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bf.h"', "int main(void){"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')

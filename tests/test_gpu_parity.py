@@ -380,3 +380,36 @@ def test_async_stream_matches_sync(ctx, tiny):
     sync = run(ctx, bank, [w["series"][0]], w["fs"], "split_bf16")[0][0]
     np.testing.assert_array_equal(g["max"], sync["max"])
     np.testing.assert_array_equal(g["argmax"], sync["argmax"])
+
+
+def test_skewnorm_fit_of_maxima(ctx):
+    """The device fit of the maxima equals the oracle's fit of the same
+    values, and the oracle's fit of its own maxima within the maxima's
+    tolerance; data and the time-randomised control differ."""
+    w = synth.gw_pair(n=16384, I=16, J=16)
+    fs, M = w["fs"], w["M"]
+    x = w["series"][0]
+    c = bf.bf_control_randomize(ctx, x, w["control_seeds"][0])
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0)
+    opts = bf.make_opts(precision="split_bf16")
+    res = bf.bf_correlate(ctx, bank, [x, c], fs, opts)
+    try:
+        vm = [bf.bf_result_copy_to_host(res, s, want_hist=False)["max"] for s in range(2)]
+        mean = bf.bf_result_copy_mean_max(res)
+        for s, v in ((0, vm[0]), (1, vm[1]), (bf.BF_FIT_MEAN, mean)):
+            g = bf.bf_result_fit_max(res, s)
+            o = oracle.skewnorm_fit(v)
+            assert g["n"] == len(v)
+            for key in ("mean", "sd", "skewness"):
+                assert abs(g[key] - o[key]) <= 1e-9 * max(1.0, abs(o[key])), (s, key, g[key], o[key])
+            for key in ("xi", "omega", "alpha"):
+                assert abs(g[key] - o[key]) <= 1e-6 * max(1.0, abs(o[key])), (s, key, g[key], o[key])
+        ref = oracle.search(x, fs, oracle_params(w["grid"]), M)
+        g0 = bf.bf_result_fit_max(res, 0)
+        o0 = oracle.skewnorm_fit(ref["max"])
+        assert abs(g0["mean"] - o0["mean"]) <= TOL["split_bf16"]
+        assert abs(g0["sd"] - o0["sd"]) <= 2 * TOL["split_bf16"]
+        assert g0["mean"] > bf.bf_result_fit_max(res, 1)["mean"]
+    finally:
+        bf.bf_result_destroy(res)
+        bf.bf_bank_destroy(bank)

@@ -491,3 +491,37 @@ def test_per_template_thresholds_paint_only_their_tails():
     only = {k: v[[0, 2]] for k, v in p.items()} if K == 4 else p
     m2 = oracle.search(x, fs, only, Mw, thr=0.15, want_map=True)["map"]
     np.testing.assert_array_equal(m1, m2)
+
+
+# ----------------------------------------------------------------- skew-normal fit
+
+def test_skewnorm_fit_recovers_known_parameters():
+    """Samples of scipy's skew-normal with known (xi, omega, alpha) give back
+    those parameters within their sampling error."""
+    for alpha, xi, omega in ((4.0, 0.10, 0.02), (-3.0, 0.5, 0.1), (1.5, -1.0, 2.0)):
+        v = scipy.stats.skewnorm.rvs(alpha, loc=xi, scale=omega, size=400_000,
+                                     random_state=np.random.default_rng(int(abs(alpha) * 10)))
+        f = oracle.skewnorm_fit(v)
+        assert abs(f["xi"] - xi) < 0.02 * omega
+        assert abs(f["omega"] / omega - 1.0) < 0.02
+        assert abs(f["alpha"] / alpha - 1.0) < 0.1
+        ref_skew = scipy.stats.skew(v)
+        assert abs(f["skewness"] - ref_skew) < 1e-9
+
+
+def test_skewnorm_fit_of_a_symmetric_sample_is_the_normal():
+    """A sample symmetric about its mean has zero skewness, so the fit is the
+    normal distribution: alpha = 0, xi = mean, omega = standard deviation."""
+    u = np.random.default_rng(3).normal(0.0, 0.5, 100_000)
+    v = np.concatenate([2.0 + u, 2.0 - u])
+    f = oracle.skewnorm_fit(v)
+    assert abs(f["skewness"]) < 1e-12 and abs(f["alpha"]) < 1e-3
+    assert abs(f["xi"] - 2.0) < 1e-3 * 0.5 and abs(f["omega"] - np.std(v)) < 1e-9
+
+
+def test_skewnorm_fit_clips_at_the_maximum_skewness():
+    """An exponential sample (skewness 2) lies beyond the skew-normal's range;
+    the fit saturates at |delta| -> 1 with a large positive alpha."""
+    v = np.random.default_rng(4).exponential(1.0, 100_000)
+    f = oracle.skewnorm_fit(v)
+    assert f["skewness"] == pytest.approx(0.99527) and f["alpha"] > 20
