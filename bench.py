@@ -47,7 +47,7 @@ UNIT = "correlations/s"
 # Keyed by (hash of the kernel source the counters were taken on, lags per
 # tile); a changed kernel reports null until it is captured again.
 TRAFFIC_BYTES_PER_TEMPLATE_TILE = {
-    ("bafca6b278e1181f", 256): (273.12e6 + 3.98e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
+    ("e553d827bd7a05cc", 256): (272.14e6 + 3.99e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
 }
 
 
@@ -589,7 +589,7 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--cpu-templates", type=int, default=128)
+    ap.add_argument("--cpu-templates", type=int, default=384)
     ap.add_argument("--ref-templates", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-rate", type=float, default=8.0)
