@@ -71,8 +71,16 @@ typedef enum { BF_SIGMA_WHITE = 0, BF_SIGMA_PARSEVAL = 1 } bf_tail_sigma;
 typedef enum {
     BF_FP32 = 0,        /* FP32 operands, FP32 FMA (SIMT)                      */
     BF_BF16 = 1,        /* BF16 operands on tcgen05 tensor cores               */
-    BF_SPLIT_BF16 = 2   /* x = hi + lo, h = hi + lo in BF16; three tcgen05 MMAs
+    BF_SPLIT_BF16 = 2,  /* x = hi + lo, h = hi + lo in BF16; three tcgen05 MMAs
                            hi*hi + hi*lo + lo*hi into one FP32 accumulator     */
+    BF_FFT_FP32 = 3     /* the paper's route (Sect. 2.2, Fig. 5): FP32 FFTs,
+                           overlap-save over segments of 8192 samples
+                           (8193 - M lags each), template spectra kept with
+                           the bank (32 KiB per template, computed on first
+                           use from the chirp parameters, whatever the bank
+                           stores).  Templates of at most 4096 samples, else
+                           BF_ENOTSUP; not in plans or the serving loop.
+                           tile_lags is ignored.                             */
 } bf_precision;
 
 /* which sample layouts a bank keeps in device memory (bit flags) */

@@ -183,7 +183,7 @@ bf_status prepare_series_alloc(bf_ctx* ctx, size_t N, uint32_t M, uint32_t M_pad
     ps.prefix = static_cast<double*>(grab((N + 1) * sizeof(double)));
     ps.bsum = static_cast<double*>(grab(ps.nb * sizeof(double)));
     bool ok = ps.x && ps.inv && ps.prefix && ps.bsum;
-    if (ok && precision != BF_FP32) {
+    if (ok && uses_split_rows(precision)) {
         ps.rows = ceil_div(ps.L, TC_TILE_L) * TC_TILE_L + M_pad + 64;
         ps.yhi = static_cast<uint4*>(grab(ps.rows * 16));
         ps.ylo = static_cast<uint4*>(grab(ps.rows * 16));
@@ -202,7 +202,7 @@ cudaError_t prepare_series_kernels(const PreparedSeries& ps, uint32_t M, int pre
 {
     cudaError_t e = cudaMemsetAsync(ps.x + ps.N, 0, (ps.xcap - ps.N) * sizeof(float), st);
     if (e == cudaSuccess) e = launch_inv_norm(ps.x, ps.N, M, ps.prefix, ps.bsum, ps.nb, ps.inv, st);
-    if (e == cudaSuccess && precision != BF_FP32)
+    if (e == cudaSuccess && uses_split_rows(precision))
         e = launch_split_rows(ps.x, ps.N, ps.rows, ps.yhi, ps.ylo, st);
     return e;
 }
@@ -226,7 +226,8 @@ size_t prepared_series_bytes(size_t N, uint32_t M, uint32_t M_pad, int precision
     const uint64_t L = N - M + 1;
     size_t b = (ceil_div(L, SIMT_TILE_L) * SIMT_TILE_L + M_pad + 1024) * 4 + L * 4 + (N + 1) * 8 +
                inv_norm_scratch_blocks(N) * 8;
-    if (precision != BF_FP32) b += 2 * (ceil_div(L, TC_TILE_L) * TC_TILE_L + M_pad + 64) * 16;
+    if (uses_split_rows(precision)) b += 2 * (ceil_div(L, TC_TILE_L) * TC_TILE_L + M_pad + 64) * 16;
+    if (precision == BF_FFT_FP32) b += (size_t)fft_segments((uint32_t)L, M) * (FFT_POINTS / 2) * 8;
     return b + 8 * 4096;
 }
 
@@ -407,17 +408,25 @@ bf_status resolve_opts(const bf_bank* bank, const bf_opts* in, bf_opts* o)
         set_error("bank range [%zu, %zu) outside [0, %zu)", o->bank_begin, o->bank_end, bank->K);
         return BF_EINVAL;
     }
-    if (o->precision != BF_FP32 && o->precision != BF_BF16 && o->precision != BF_SPLIT_BF16) {
+    if (o->precision != BF_FP32 && o->precision != BF_BF16 && o->precision != BF_SPLIT_BF16 &&
+        o->precision != BF_FFT_FP32) {
         set_error("unknown precision %d", o->precision);
         return BF_EINVAL;
     }
-    if (bank->generated) {
+    if (o->precision == BF_FFT_FP32) {
+        // spectra are synthesised from the parameters, whatever the bank stores
+        if (bank->M > FFT_POINTS / 2) {
+            set_error("the FFT route takes templates of at most %d samples (this bank: %u)",
+                      FFT_POINTS / 2, bank->M);
+            return BF_ENOTSUP;
+        }
+    } else if (bank->generated) {
         // synthesised per call in whichever layout the precision needs
     } else if (o->precision == BF_FP32 && !bank->f32) {
         set_error("bank keeps no FP32 layout (create it with BF_BANK_FP32)");
         return BF_EINVAL;
     }
-    if (!bank->generated && o->precision != BF_FP32 && !bank->hi) {
+    if (!bank->generated && uses_split_rows(o->precision) && !bank->hi) {
         set_error("bank keeps no split-BF16 layout (create it with BF_BANK_SPLIT_BF16)");
         return BF_EINVAL;
     }
@@ -874,6 +883,7 @@ void bf_bank_destroy(bf_bank* b)
     Allocator& mem = *b->ctx->mem;
     cudaStreamSynchronize(b->ctx->stream);
     mem.release(b->ph);
+    mem.release(b->fspec);
     mem.release(b->d_params);
     mem.release(b->f32);
     mem.release(b->hi);
@@ -942,6 +952,63 @@ bf_status bf_bank_read(const bf_bank* b, size_t k0, size_t n, float* out)
     return BF_OK;
 }
 
+// The FFT route: per batch of up to MAX_FFT_SER series, the segment spectra
+// (kept in the result's scratch until it is destroyed), then one correlation
+// launch over all template pairs of the bank range.
+cudaError_t correlate_fft(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
+                          const std::vector<PreparedSeries>& prep, bf_result* r, cudaStream_t st)
+{
+    const size_t S = prep.size(), K = r->K;
+    const uint32_t V = FFT_POINTS - bank->M + 1;
+    cudaError_t e = cudaSuccess;
+    for (size_t s0 = 0; s0 < S && e == cudaSuccess; s0 += MAX_FFT_SER) {
+        const int n = (int)std::min<size_t>(MAX_FFT_SER, S - s0);
+        FftSeriesBatch b{};
+        FftParams p{};
+        uint32_t total = 0;
+        for (int i = 0; i < n; ++i) {
+            const size_t s = s0 + i;
+            const uint32_t nseg = fft_segments(prep[s].L, bank->M);
+            float2* spec = static_cast<float2*>(ctx->mem->alloc((size_t)nseg * (FFT_POINTS / 2) * sizeof(float2)));
+            if (!spec) {
+                set_error("out of device memory for the segment spectra");
+                return cudaErrorMemoryAllocation;
+            }
+            r->scratch.push_back(spec);
+            b.x[i] = prep[s].x;
+            b.N[i] = prep[s].N;
+            b.spec[i] = spec;
+            b.seg_begin[i] = total;
+            total += nseg;
+            FftSeries& f = p.ser[i];
+            f.spec = spec;
+            f.inv = prep[s].inv;
+            f.vmax = r->packed + s * K;
+            f.sumsq = r->sumsq + s * K;
+            f.rho = s == 0 ? o.rho_out : nullptr;
+            f.sigma_pred = r->sigma_pred ? r->sigma_pred + s * K : nullptr;
+            f.kappa = r->kappa;
+            f.L = prep[s].L;
+            f.nseg = nseg;
+            f.series_id = (uint32_t)s;
+        }
+        b.n = n;
+        b.V = V;
+        p.hspec = bank->fspec;
+        p.k_begin = (uint32_t)o.bank_begin;
+        p.k_end = (uint32_t)o.bank_end;
+        p.V = V;
+        p.n_ser = n;
+        p.thr = r->thr;
+        p.cand_cap = r->cand_cap;
+        p.cand = r->cand;
+        p.cand_count = r->cand_count;
+        e = launch_fft_series(b, total, st);
+        if (e == cudaSuccess) e = launch_corr_fft(p, ctx->n_sm, st);
+    }
+    return e;
+}
+
 bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* series,
                        const size_t* lengths, size_t n_series, double fs, const bf_opts* opts,
                        bf_result** out)
@@ -994,9 +1061,13 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
         ids.push_back((uint32_t)s);
         r->correlations += (double)prep[s].L * (double)r->K;
     }
+    const bool fft = o.precision == BF_FFT_FP32;
     std::vector<Seg> segs;
-    build_segments(pptr, ids, bank, o.bank_begin, o.bank_end, o.precision, r->packed, r->sumsq, r->K, segs);
-    if (o.rho_out) segs[0].rho = o.rho_out;
+    if (!fft) {
+        build_segments(pptr, ids, bank, o.bank_begin, o.bank_end, o.precision, r->packed, r->sumsq, r->K,
+                       segs);
+        if (o.rho_out) segs[0].rho = o.rho_out;
+    }
     if (r->parseval) {
         // the predictor step: sigma_k per series before the search
         st = bank_power_spectra(ctx, const_cast<bf_bank*>(bank), strm);
@@ -1004,10 +1075,14 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
             st = predict_sigma(ctx, bank, prep[s], o.bank_begin, o.bank_end, r->sigma_pred + s * r->K,
                                r->scratch, strm);
         if (st) return st;
-        for (size_t s = 0; s < n_series; ++s) {
+        for (size_t s = 0; s < segs.size(); ++s) {
             segs[s].sigma_pred = r->sigma_pred + s * r->K;
             segs[s].kappa = r->kappa;
         }
+    }
+    if (fft) {
+        st = bank_fft_spectra(ctx, const_cast<bf_bank*>(bank), strm);
+        if (st) return st;
     }
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1018,10 +1093,11 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
     }
     // lags per tile: fixed by the caller, else the autotuner's choice (for a
     // generated bank it is made on the first synthesised chunk)
-    int lt = o.precision == BF_FP32 ? SIMT_TILE_L : o.tile_lags;
-    if (lt == 0 && !bank->generated) lt = choose_lag_tile(ctx, segs[0], o.precision, strm);
+    int lt = o.precision == BF_FP32 ? SIMT_TILE_L : fft ? 0 : o.tile_lags;
+    if (lt == 0 && !fft && !bank->generated) lt = choose_lag_tile(ctx, segs[0], o.precision, strm);
     r->tile_lags = lt;
-    cudaError_t e = bank->generated
+    cudaError_t e = fft ? correlate_fft(ctx, bank, o, prep, r, strm)
+                    : bank->generated
                         ? correlate_generated(ctx, bank, o, segs, r, strm, lt)
                         : launch_segments(ctx, segs, o.precision, r->thr, r->cand, r->cand_count,
                                           r->cand_cap, strm, nullptr, lt);

@@ -94,6 +94,42 @@ struct CorrParams {
     Seg seg[MAX_SEG];
 };
 
+// The FFT route (corr_fft.cu): overlap-save over segments of FFT_POINTS samples.
+constexpr int FFT_POINTS = 8192;
+constexpr int MAX_FFT_SER = 64;           // series per FFT launch
+
+struct FftSeries {
+    const float2* spec;             // [nseg][FFT_POINTS / 2] segment half spectra
+    const float* inv;               // [L] inverse window norms
+    unsigned long long* vmax;       // packed max per template, index k - k_begin
+    double* sumsq;
+    float* rho;                     // optional dense output [k - k_begin][tau]
+    const float* sigma_pred;        // optional per-template predicted sigma
+    float kappa;
+    uint32_t L, nseg, series_id;
+};
+
+struct FftParams {
+    const float2* hspec;            // template half spectra [K][FFT_POINTS / 2], absolute k
+    uint32_t k_begin, k_end;
+    uint32_t V;                     // valid lags per segment, FFT_POINTS - M + 1
+    int n_ser;
+    float thr;
+    unsigned int cand_cap;
+    Candidate* cand;
+    unsigned int* cand_count;
+    FftSeries ser[MAX_FFT_SER];
+};
+
+struct FftSeriesBatch {
+    int n;
+    uint32_t V;
+    const float* x[MAX_FFT_SER];
+    uint64_t N[MAX_FFT_SER];
+    float2* spec[MAX_FFT_SER];
+    uint32_t seg_begin[MAX_FFT_SER];
+};
+
 // ---------------------------------------------------------------- launchers
 // Process-wide count of kernel launches made by this library.
 extern std::atomic<uint64_t> g_launches;
@@ -143,6 +179,9 @@ struct FinalizeParams {
     FinalizeSeries ser[MAX_FIN];
 };
 cudaError_t launch_finalize(const FinalizeParams& p, uint32_t K, uint32_t nbins, cudaStream_t s);
+uint32_t fft_segments(uint32_t L, uint32_t M);
+cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, cudaStream_t st);
+cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st);
 cudaError_t launch_skewnorm_fit(const float* v, uint64_t n, double* acc, double* out, int n_sm,
                                 cudaStream_t s);
 cudaError_t launch_mean_max(const float* vmax, uint32_t n_series, uint32_t K, float* mean,
@@ -210,6 +249,7 @@ struct bf_bank {
     uint8_t* hi = nullptr;
     uint8_t* lo = nullptr;
     float* ph = nullptr;                // template power spectra [K_pad][M+1] (lazy)
+    float2* fspec = nullptr;            // template half spectra for the FFT route (lazy)
 };
 
 struct bf_result {

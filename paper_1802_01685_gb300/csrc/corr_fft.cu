@@ -1,0 +1,465 @@
+// Correlation by FFT: the paper's own route to the filter output (Sect. 2.2
+// and Fig. 5: the output of every template against data segments through
+// single-precision FFTs on the GPU, with only the tails rho > kappa sigma
+// leaving the device).  Overlap-save with transforms of F = 8192 points:
+//
+//   segment j of a series covers lags tau0 = j V .. tau0 + V - 1, V = F - M + 1,
+//   X_j = DFT_F(x[tau0 .. tau0 + F))             (zero past the series end)
+//   H_k = DFT_F(h_k zero-padded to F)
+//   c_k[tau0 + t] = (1/F) sum_f X_j[f] conj(H_k[f]) e^{+2 pi i f t / F},  t < V,
+//
+// which is the circular correlation of the segment with the padded template;
+// for t < V no product wraps around, so it equals the direct sum
+// sum_m h_k[m] x[tau0 + t + m].  The result is normalised by the window norm
+// and reduced exactly like the direct kernels (max |rho| with its first
+// argmax, sum rho^2, tails).
+//
+// GB300 layout of the work:
+//  * template spectra are computed once per bank (two real templates per
+//    complex FFT) and kept in HBM as half spectra: 4096 complex values per
+//    template, bin 0 carrying the DC and Nyquist terms (both real);
+//  * each segment spectrum is computed once per call; all of them stay in L2;
+//  * one CTA of 512 threads owns a pair of templates (a, b) at a time and
+//    holds their spectra in registers (8 bins per thread).  For every segment
+//    it forms Z = X conj(H_a) + i X conj(H_b) over all F bins (Hermitian
+//    symmetry fills the upper half), runs one inverse complex FFT in shared
+//    memory and reads c_a = Re z, c_b = Im z -- two real correlations per
+//    transform.  The last radix-2 stage of the FFT is fused into the
+//    epilogue, so the filter output never reaches HBM.
+//  * The FFT is a Stockham autosort FFT with three radix-16 passes (each
+//    thread one 16-point DFT per pass, in registers) and a final radix-2
+//    stage; real and imaginary parts live in separate padded float arrays
+//    (index i + i/32) so that almost every access pattern is free of bank
+//    conflicts.  Twiddles come from two small tables (128 + 64 entries,
+//    built in FP64): e^{2 pi i n / F} = T_hi[n / 64] T_lo[n % 64].
+#include "corr_common.cuh"
+#include "runtime.h"
+
+namespace bfi {
+
+namespace {
+
+constexpr int FN = FFT_POINTS;            // 8192
+constexpr int FH = FN / 2;                // 4096 half-spectrum bins (+ Nyquist packed in bin 0)
+constexpr int FT = 512;                   // threads per FFT block
+constexpr int FBINS = FH / FT;            // 8 bins per thread
+constexpr int FPAD = FN + FN / 32;        // padded floats per array
+constexpr size_t FFT_SMEM = 2 * FPAD * sizeof(float);
+
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 5); }
+
+struct Twiddles {
+    float2 hi[128];                       // e^{2 pi i a / 128}
+    float2 lo[64];                        // e^{2 pi i b / 8192}
+};
+
+__device__ __forceinline__ void twiddles_init(Twiddles& t)
+{
+    for (int i = threadIdx.x; i < 192; i += blockDim.x) {
+        double s, c;
+        if (i < 128) {
+            sincospi((double)i / 64.0, &s, &c);
+            t.hi[i] = make_float2((float)c, (float)s);
+        } else {
+            sincospi((double)(i - 128) / 4096.0, &s, &c);
+            t.lo[i - 128] = make_float2((float)c, (float)s);
+        }
+    }
+}
+
+// e^{SIGN 2 pi i n / 8192}, 0 <= n < 8192
+template <int SIGN>
+__device__ __forceinline__ float2 twiddle(const Twiddles& t, int n)
+{
+    const float2 h = t.hi[n >> 6], l = t.lo[n & 63];
+    const float re = h.x * l.x - h.y * l.y;
+    const float im = h.x * l.y + h.y * l.x;
+    return make_float2(re, SIGN > 0 ? im : -im);
+}
+
+__device__ __forceinline__ void rotate(float& r, float& i, float2 w)
+{
+    const float a = r * w.x - i * w.y;
+    i = r * w.y + i * w.x;
+    r = a;
+}
+
+// 4-point DFT with kernel e^{SIGN 2 pi i n k / 4}, in place
+template <int SIGN>
+__device__ __forceinline__ void dft4(float& ar, float& ai, float& br, float& bi, float& cr, float& ci,
+                                     float& dr, float& di)
+{
+    const float t0r = ar + cr, t0i = ai + ci;
+    const float t1r = ar - cr, t1i = ai - ci;
+    const float t2r = br + dr, t2i = bi + di;
+    const float t3r = br - dr, t3i = bi - di;
+    const float ur = SIGN > 0 ? -t3i : t3i;       // SIGN * i * (b - d)
+    const float ui = SIGN > 0 ? t3r : -t3r;
+    ar = t0r + t2r;
+    ai = t0i + t2i;
+    cr = t0r - t2r;
+    ci = t0i - t2i;
+    br = t1r + ur;
+    bi = t1i + ui;
+    dr = t1r - ur;
+    di = t1i - ui;
+}
+
+// 16-point DFT as 4 x 4 (Cooley-Tukey, n = 4 n1 + n2, k = k1 + 4 k2): DFTs
+// over n1, twiddles e^{SIGN 2 pi i n2 k1 / 16}, DFTs over n2.  On return
+// position 4 k1 + k2 holds output k1 + 4 k2.
+template <int SIGN>
+__device__ __forceinline__ void dft16(float (&r)[16], float (&i)[16])
+{
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2)
+        dft4<SIGN>(r[n2], i[n2], r[4 + n2], i[4 + n2], r[8 + n2], i[8 + n2], r[12 + n2], i[12 + n2]);
+    constexpr float C1 = 0.923879532511286756f;   // cos(pi/8)
+    constexpr float S1 = 0.382683432365089772f;   // sin(pi/8)
+    constexpr float R2 = 0.707106781186547524f;   // cos(pi/4)
+    constexpr float S = SIGN > 0 ? 1.f : -1.f;
+    // position 4 k1 + n2 gets e^{SIGN 2 pi i (n2 k1) / 16}
+    rotate(r[5], i[5], make_float2(C1, S * S1));      // n2 k1 = 1
+    rotate(r[9], i[9], make_float2(R2, S * R2));      // 2
+    rotate(r[13], i[13], make_float2(S1, S * C1));    // 3
+    rotate(r[6], i[6], make_float2(R2, S * R2));      // 2
+    rotate(r[10], i[10], make_float2(0.f, S));        // 4
+    rotate(r[14], i[14], make_float2(-R2, S * R2));   // 6
+    rotate(r[7], i[7], make_float2(S1, S * C1));      // 3
+    rotate(r[11], i[11], make_float2(-R2, S * R2));   // 6
+    rotate(r[15], i[15], make_float2(-C1, -S * S1));  // 9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+        dft4<SIGN>(r[4 * k1], i[4 * k1], r[4 * k1 + 1], i[4 * k1 + 1], r[4 * k1 + 2], i[4 * k1 + 2],
+                   r[4 * k1 + 3], i[4 * k1 + 3]);
+}
+
+// One radix-16 Stockham pass over 8192 points with stride NS (1, 16, 256):
+// thread j reads in[j + 512 r], twiddles by e^{SIGN 2 pi i r (j mod NS) / (16 NS)},
+// takes the 16-point DFT and writes out[(j / NS) 16 NS + j mod NS + q NS].
+template <int SIGN, int NS>
+__device__ __forceinline__ void pass16(float* re, float* im, const Twiddles& tw)
+{
+    const int j = threadIdx.x;
+    float vr[16], vi[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int a = pidx(j + r * (FN / 16));
+        vr[r] = re[a];
+        vi[r] = im[a];
+    }
+    __syncthreads();
+    if (NS > 1) {
+        const int k = j % NS;
+        constexpr int f = FN / (16 * NS);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) rotate(vr[r], vi[r], twiddle<SIGN>(tw, r * k * f));
+    }
+    dft16<SIGN>(vr, vi);
+    const int base = (j / NS) * NS * 16 + (j % NS);
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+        const int q = 4 * (p % 4) + p / 4;
+        const int a = pidx(base + q * NS);
+        re[a] = vr[p];
+        im[a] = vi[p];
+    }
+    __syncthreads();
+}
+
+template <int SIGN>
+__device__ __forceinline__ void fft_passes(float* re, float* im, const Twiddles& tw)
+{
+    pass16<SIGN, 1>(re, im, tw);
+    pass16<SIGN, 16>(re, im, tw);
+    pass16<SIGN, 256>(re, im, tw);
+}
+
+// The final radix-2 stage for output pair (k, k + 4096), 0 <= k < 4096.
+template <int SIGN>
+__device__ __forceinline__ void fft_final(const float* re, const float* im, const Twiddles& tw, int k,
+                                          float2& lo, float2& hi)
+{
+    const int a = pidx(k), b = pidx(k + FH);
+    float vr = re[b], vi = im[b];
+    rotate(vr, vi, twiddle<SIGN>(tw, k));
+    const float ur = re[a], ui = im[a];
+    lo = make_float2(ur + vr, ui + vi);
+    hi = make_float2(ur - vr, ui - vi);
+}
+
+// Spectrum of one segment of a series: real input, half spectrum out.
+__global__ void __launch_bounds__(FT, 1) k_fft_series(const __grid_constant__ FftSeriesBatch p)
+{
+    extern __shared__ __align__(16) float fsm[];
+    float* re = fsm;
+    float* im = fsm + FPAD;
+    __shared__ Twiddles tw;
+    twiddles_init(tw);
+    int s = 0;
+    while (s + 1 < p.n && blockIdx.x >= p.seg_begin[s + 1]) ++s;
+    const uint32_t j = blockIdx.x - p.seg_begin[s];
+    const float* x = p.x[s];
+    const uint64_t N = p.N[s], t0 = (uint64_t)j * p.V;
+    for (int n = threadIdx.x; n < FN; n += FT) {
+        re[pidx(n)] = t0 + n < N ? x[t0 + n] : 0.f;
+        im[pidx(n)] = 0.f;
+    }
+    __syncthreads();
+    fft_passes<-1>(re, im, tw);
+    float2* out = p.spec[s] + (size_t)j * FH;
+#pragma unroll
+    for (int i = 0; i < FBINS; ++i) {
+        const int k = threadIdx.x + FT * i;
+        float2 lo, hi;
+        fft_final<-1>(re, im, tw, k, lo, hi);
+        out[k] = k == 0 ? make_float2(lo.x, hi.x) : lo;
+    }
+}
+
+// Spectra of templates (2q, 2q + 1) of a chunk of synthesised rows.
+__global__ void __launch_bounds__(FT, 1) k_fft_bank(const float* __restrict__ rows, uint32_t n_rows,
+                                                    float2* __restrict__ spec)
+{
+    extern __shared__ __align__(16) float fsm[];
+    float* re = fsm;
+    float* im = fsm + FPAD;
+    __shared__ Twiddles tw;
+    twiddles_init(tw);
+    const uint32_t a = 2 * blockIdx.x, b = a + 1;
+    const float* ra = rows + (size_t)a * FN;
+    const float* rb = rows + (size_t)b * FN;
+    for (int n = threadIdx.x; n < FN; n += FT) {
+        re[pidx(n)] = ra[n];
+        im[pidx(n)] = b < n_rows ? rb[n] : 0.f;
+    }
+    __syncthreads();
+    fft_passes<-1>(re, im, tw);
+    float2* sa = spec + (size_t)a * FH;
+    float2* sb = spec + (size_t)b * FH;
+#pragma unroll
+    for (int i = 0; i < FBINS; ++i) {
+        const int k = threadIdx.x + FT * i;
+        float2 zk, zn, zm, unused;
+        fft_final<-1>(re, im, tw, k, zk, zn);           // Z[k], Z[k + 4096]
+        if (k == 0) {
+            // DC and Nyquist of both real templates: real parts of Z[0], Z[4096]
+            sa[0] = make_float2(zk.x, zn.x);
+            if (b < n_rows) sb[0] = make_float2(zk.y, zn.y);
+        } else {
+            fft_final<-1>(re, im, tw, FH - k, unused, zm);  // Z[F - k]
+            // H_a = (Z[k] + conj Z[F-k]) / 2,  H_b = (Z[k] - conj Z[F-k]) / 2i
+            sa[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            if (b < n_rows) sb[k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        }
+    }
+}
+
+__device__ __forceinline__ void push_tail(const FftParams& p, uint32_t series, uint32_t k, uint32_t tau,
+                                          float rho)
+{
+    unsigned int i = atomicAdd(p.cand_count, 1u);
+    if (i < p.cand_cap) p.cand[i] = Candidate{series, k, tau, rho};
+}
+
+// The correlation: one template pair per CTA at a time, all segments of all
+// series of the batch.
+__global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftParams p)
+{
+    extern __shared__ __align__(16) float fsm[];
+    float* re = fsm;
+    float* im = fsm + FPAD;
+    __shared__ Twiddles tw;
+    twiddles_init(tw);
+    __syncthreads();
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t n_pairs = (p.k_end - p.k_begin + 1) / 2;
+    const float scale = 1.f / (float)FN;
+
+    for (uint32_t pair = blockIdx.x; pair < n_pairs; pair += gridDim.x) {
+        const uint32_t ka = p.k_begin + 2 * pair, kb = ka + 1;
+        const bool has_b = kb < p.k_end;
+        float2 ha[FBINS], hb[FBINS];
+#pragma unroll
+        for (int i = 0; i < FBINS; ++i) {
+            const int f = tid + FT * i;
+            ha[i] = p.hspec[(size_t)ka * FH + f];
+            hb[i] = has_b ? p.hspec[(size_t)kb * FH + f] : make_float2(0.f, 0.f);
+        }
+        for (int s = 0; s < p.n_ser; ++s) {
+            const FftSeries& S = p.ser[s];
+            const uint32_t la = ka - p.k_begin, lb = kb - p.k_begin;
+            const float thr_a = S.sigma_pred ? S.kappa * S.sigma_pred[la] : p.thr;
+            const float thr_b = !has_b ? INFINITY : (S.sigma_pred ? S.kappa * S.sigma_pred[lb] : p.thr);
+            unsigned long long best_a = 0ull, best_b = 0ull;
+            double ss_a = 0.0, ss_b = 0.0;
+            for (uint32_t j = 0; j < S.nseg; ++j) {
+                const float2* X = S.spec + (size_t)j * FH;
+#pragma unroll
+                for (int i = 0; i < FBINS; ++i) {
+                    const int f = tid + FT * i;
+                    const float2 x = __ldg(X + f);
+                    if (f == 0) {
+                        // DC (x.x) and Nyquist (x.y): real products
+                        re[pidx(0)] = x.x * ha[0].x;
+                        im[pidx(0)] = x.x * hb[0].x;
+                        re[pidx(FH)] = x.y * ha[0].y;
+                        im[pidx(FH)] = x.y * hb[0].y;
+                    } else {
+                        // Y = X conj(H)
+                        const float yar = x.x * ha[i].x + x.y * ha[i].y;
+                        const float yai = x.y * ha[i].x - x.x * ha[i].y;
+                        const float ybr = x.x * hb[i].x + x.y * hb[i].y;
+                        const float ybi = x.y * hb[i].x - x.x * hb[i].y;
+                        // Z[f] = Ya + i Yb, Z[F - f] = conj(Ya) + i conj(Yb)
+                        re[pidx(f)] = yar - ybi;
+                        im[pidx(f)] = yai + ybr;
+                        re[pidx(FN - f)] = yar + ybi;
+                        im[pidx(FN - f)] = ybr - yai;
+                    }
+                }
+                __syncthreads();
+                fft_passes<1>(re, im, tw);
+                const uint32_t t0 = j * p.V;
+                const uint32_t nv = min(p.V, S.L - t0);
+                float pa = 0.f, pb = 0.f;
+#pragma unroll
+                for (int i = 0; i < FBINS; ++i) {
+                    const int k = tid + FT * i;
+                    float2 z[2];
+                    fft_final<1>(re, im, tw, k, z[0], z[1]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t t = (uint32_t)k + (uint32_t)(h * FH);
+                        if (t < nv) {
+                            const uint32_t tau = t0 + t;
+                            const float inv = S.inv[tau] * scale;
+                            const float ra = z[h].x * inv, rb = z[h].y * inv;
+                            const float aa = fabsf(ra), ab = fabsf(rb);
+                            const unsigned long long key_a = pack_max(aa, tau);
+                            best_a = key_a > best_a ? key_a : best_a;
+                            pa = fmaf(ra, ra, pa);
+                            if (aa >= thr_a) push_tail(p, S.series_id, ka, tau, ra);
+                            if (S.rho) S.rho[(size_t)la * S.L + tau] = ra;
+                            if (has_b) {
+                                const unsigned long long key_b = pack_max(ab, tau);
+                                best_b = key_b > best_b ? key_b : best_b;
+                                pb = fmaf(rb, rb, pb);
+                                if (ab >= thr_b) push_tail(p, S.series_id, kb, tau, rb);
+                                if (S.rho) S.rho[(size_t)lb * S.L + tau] = rb;
+                            }
+                        }
+                    }
+                }
+                ss_a += (double)pa;
+                ss_b += (double)pb;
+                __syncthreads();
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long oa = __shfl_xor_sync(0xffffffffu, best_a, o);
+                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best_b, o);
+                best_a = oa > best_a ? oa : best_a;
+                best_b = ob > best_b ? ob : best_b;
+                ss_a += __shfl_xor_sync(0xffffffffu, ss_a, o);
+                ss_b += __shfl_xor_sync(0xffffffffu, ss_b, o);
+            }
+            if (lane == 0) {
+                atomicMax(S.vmax + la, best_a);
+                atomicAdd(S.sumsq + la, ss_a);
+                if (has_b) {
+                    atomicMax(S.vmax + lb, best_b);
+                    atomicAdd(S.sumsq + lb, ss_b);
+                }
+            }
+        }
+    }
+}
+
+cudaError_t fft_attributes()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_corr_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_series, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_bank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+}  // namespace
+
+// Half spectra of every template of the bank, [K rounded up to even][4096]
+// complex, computed once and kept with the bank.
+bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
+{
+    if (bank->fspec) return BF_OK;
+    if (bank->M > FFT_POINTS / 2) {
+        set_error("the FFT route takes templates of at most %d samples (this bank: %u)", FFT_POINTS / 2,
+                  bank->M);
+        return BF_ENOTSUP;
+    }
+    cudaError_t e = fft_attributes();
+    if (e != cudaSuccess) return cuda_fail(e, "FFT attributes");
+    const size_t K2 = bank->K + (bank->K & 1);
+    Allocator& mem = *ctx->mem;
+    float2* spec = static_cast<float2*>(mem.alloc(K2 * FH * sizeof(float2)));
+    const size_t chunk = std::min<size_t>(4096, K2);
+    float* rows = static_cast<float*>(mem.alloc(chunk * FN * sizeof(float)));
+    if (!spec || !rows) {
+        mem.release(spec);
+        mem.release(rows);
+        set_error("out of device memory for the template spectra (%zu MB)", (K2 * FH * 8) >> 20);
+        return BF_ENOMEM;
+    }
+    for (size_t k0 = 0; k0 < K2 && e == cudaSuccess; k0 += chunk) {
+        const size_t kc = std::min(chunk, bank->K - k0);       // templates in this chunk
+        const size_t nr = std::min(chunk, K2 - k0);            // rows (even)
+        e = launch_bank_synth(bank->d_params + k0, (uint32_t)kc, (uint32_t)nr, bank->M, FN, bank->fs, rows,
+                              nullptr, nullptr, st);
+        if (e == cudaSuccess) {
+            count_launches(1);
+            k_fft_bank<<<(unsigned)(nr / 2), FT, FFT_SMEM, st>>>(rows, (uint32_t)kc, spec + k0 * FH);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    mem.release(rows);
+    if (e != cudaSuccess) {
+        mem.release(spec);
+        return cuda_fail(e, "template spectra");
+    }
+    bank->fspec = spec;
+    return BF_OK;
+}
+
+uint32_t fft_segments(uint32_t L, uint32_t M)
+{
+    const uint32_t V = FFT_POINTS - M + 1;
+    return (L + V - 1) / V;
+}
+
+cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, cudaStream_t st)
+{
+    cudaError_t e = fft_attributes();
+    if (e != cudaSuccess || total_segments == 0) return e;
+    count_launches(1);
+    k_fft_series<<<total_segments, FT, FFT_SMEM, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st)
+{
+    cudaError_t e = fft_attributes();
+    if (e != cudaSuccess) return e;
+    const uint32_t n_pairs = (p.k_end - p.k_begin + 1) / 2;
+    if (n_pairs == 0 || p.n_ser == 0) return cudaSuccess;
+    const unsigned grid = std::min<unsigned>(n_pairs, (unsigned)n_sm);
+    count_launches(1);
+    k_corr_fft<<<grid, FT, FFT_SMEM, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace bfi

@@ -63,6 +63,10 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
         set_error("plans take BF_SIGMA_WHITE tails (the Parseval predictor runs cuFFT outside the graph)");
         return BF_ENOTSUP;
     }
+    if (o.precision == BF_FFT_FP32) {
+        set_error("plans run the direct kernels; call bf_correlate for BF_FFT_FP32");
+        return BF_ENOTSUP;
+    }
     o.stream = nullptr;
     o.rho_out = nullptr;
     for (size_t s = 0; s < n_series; ++s)

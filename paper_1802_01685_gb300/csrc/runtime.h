@@ -43,6 +43,8 @@ size_t prepared_series_bytes(size_t N, uint32_t M, uint32_t M_pad, int precision
 // Template-tile geometry of a precision's kernel.
 inline uint32_t tile_templates(int precision) { return precision == BF_FP32 ? SIMT_TILE_T : TC_TILE_T; }
 inline uint32_t tile_lags(int precision) { return precision == BF_FP32 ? SIMT_TILE_L : TC_TILE_L; }
+// the tensor-core precisions read the series as bf16 split rows
+inline bool uses_split_rows(int precision) { return precision == BF_BF16 || precision == BF_SPLIT_BF16; }
 
 // One segment: series `ps` (result slot series_id) against template tiles
 // [tt_first, tt_first + tt_count), keeping outputs of templates [k_begin, k_end).
@@ -70,6 +72,8 @@ void serve_shutdown(bf_ctx* ctx);
 
 // Parseval predictor of the noise level of rho (predict.cu)
 bf_status bank_power_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st);
+// template half spectra of the FFT route, computed once per bank
+bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st);
 bf_status predict_sigma(bf_ctx* ctx, const bf_bank* bank, const PreparedSeries& ps, size_t k_begin,
                         size_t k_end, float* out, std::vector<void*>& scratch, cudaStream_t st);
 

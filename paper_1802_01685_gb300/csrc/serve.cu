@@ -370,6 +370,10 @@ bf_status bf_serve_submit(bf_ctx* ctx, const bf_request* req, uint64_t* ticket)
     bf_opts o;
     bf_status st = resolve_opts(bank, &req->opts, &o);
     if (st) return st;
+    if (o.precision == BF_FFT_FP32) {
+        set_error("the serving loop batches the direct kernels; call bf_correlate for BF_FFT_FP32");
+        return BF_ENOTSUP;
+    }
     o.stream = nullptr;
     std::unique_ptr<Request> r(new Request());
     r->host.resize(req->n);

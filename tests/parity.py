@@ -5,9 +5,9 @@ import numpy as np
 import oracle
 from paper_1802_01685_gb300 import bf
 
-# per-result tolerances on normalised correlation (FP32 and split-BF16 vs
-# plain BF16 operands)
-TOL = {"fp32": 2e-5, "split_bf16": 2e-5, "bf16": 1e-3}
+# per-result tolerances on normalised correlation (FP32, split-BF16 and the
+# FP32 FFT route vs plain BF16 operands)
+TOL = {"fp32": 2e-5, "split_bf16": 2e-5, "bf16": 1e-3, "fft_fp32": 2e-5}
 
 
 def oracle_params(spec):

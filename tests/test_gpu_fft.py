@@ -1,0 +1,155 @@
+"""GPU parity of the FFT route (BF_FFT_FP32: overlap-save over segments of
+8192 samples, template spectra kept with the bank) against the oracle, at
+sizes that span several segments with a ragged last one, and at the full GW
+size on sampled templates."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_01685_gb300 import bf, synth
+
+from parity import TOL, check_hist, check_maxima, check_sigma, oracle_params, run, subset
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+PREC = "fft_fp32"
+F = 8192
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    h = bf.bf_init()
+    yield h
+    bf.bf_destroy(h)
+
+
+def test_gw_cut_down_several_segments(ctx):
+    """M = 4096: 4097 lags per segment, 12,289 lags = three segments, the
+    last two lags short.  Dense rho across the seams, maxima, sigma and
+    histogram of the data and both controls."""
+    w = synth.gw_pair(n=16384, I=16, J=16)
+    fs, M = w["fs"], w["M"]
+    xs = w["series"]
+    ctrl = [bf.bf_control_randomize(ctx, x, sd) for x, sd in zip(xs, w["control_seeds"])]
+    p = oracle_params(w["grid"])
+    refs = [oracle.search(x, fs, p, M, want_rho=True) for x in xs + ctrl]
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16)
+    K, L = refs[0]["rho"].shape
+    assert L == 12289 and -(-L // (F - M + 1)) == 3
+    rho = torch.zeros((K, L), dtype=torch.float32, device="cuda")
+    run(ctx, bank, xs[:1], fs, PREC, rho_out=rho)
+    err = np.abs(rho.cpu().numpy().astype(np.float64) - refs[0]["rho"])
+    assert err.max() <= TOL[PREC], err.max()
+    # the lags on either side of each seam
+    for t in (4095, 4096, 4097, 8193, 8194, L - 1):
+        assert err[:, t].max() <= TOL[PREC]
+    outs, mean, info = run(ctx, bank, xs + ctrl, fs, PREC)
+    assert info.correlations == 4 * K * L and info.tile_lags == 0
+    for s, (g, r) in enumerate(zip(outs, refs)):
+        check_maxima(g, r, r["rho"], TOL[PREC], f"series {s}")
+        check_sigma(g, r, TOL[PREC])
+        check_hist(g["hist"], r["max"], TOL[PREC])
+    bf.bf_bank_destroy(bank)
+
+
+def test_grb_cut_down_uneven_batch(ctx):
+    """M = 2000 (6193 lags per segment), four light curves of 10-20 s in one
+    launch, both senses, mean spectrum over the batch."""
+    w = synth.grb_batch(n_series=4, t_min=10.0, t_max=20.0, I=8, J=8)
+    fs, M = w["fs"], w["M"]
+    xs = w["series"]
+    p = oracle_params(w["grid"])
+    refs = [oracle.search(x, fs, p, M, want_rho=True) for x in xs]
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0)
+    outs, mean, _ = run(ctx, bank, xs, fs, PREC)
+    for s, (g, r) in enumerate(zip(outs, refs)):
+        check_maxima(g, r, r["rho"], TOL[PREC], f"series {s}")
+        check_sigma(g, r, TOL[PREC])
+    np.testing.assert_allclose(mean, np.mean([r["max"] for r in refs], axis=0), atol=TOL[PREC])
+    bf.bf_bank_destroy(bank)
+
+
+def test_odd_bank_slice_and_generated_bank(ctx):
+    """An odd number of templates (the last one has no partner in its
+    transform), starting at an odd index; the same from a bank that stores
+    only the chirp parameters."""
+    w = synth.tiny(seed=3)
+    fs, M = w["fs"], w["M"]
+    x = w["series"][0]
+    p = oracle_params(w["grid"])
+    b0, b1 = 3, 200
+    ref = oracle.search(x, fs, subset(p, np.arange(b0, b1)), M, want_rho=True)
+    for storage in (bf.BF_BANK_FP32, bf.BF_BANK_GENERATED):
+        bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, storage)
+        outs, _, info = run(ctx, bank, [x], fs, PREC, bank_begin=b0, bank_end=b1)
+        assert info.n_templates == b1 - b0
+        check_maxima(outs[0], ref, ref["rho"], TOL[PREC], f"storage {storage}")
+        check_sigma(outs[0], ref, TOL[PREC])
+        bf.bf_bank_destroy(bank)
+
+
+def test_agrees_with_the_direct_path(ctx):
+    """The FFT route and the split-BF16 tensor-core path on the same ragged
+    batch: maxima within the sum of their tolerances; tails the same set up
+    to values within that bound of the threshold."""
+    fs, M = 4096.0, 4096
+    spec = synth.grid_spec([synth.POWERLAW, synth.LINEAR], [synth.ASC, synth.DESC], [1.0, 0.6],
+                           30.0, 900.0, 6, 6)                    # 288 templates
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
+    rng = np.random.default_rng(77)
+    xs = [synth.gw_coloured(n, fs, rng).astype(np.float32) for n in (M, 9000, 30001, 50000)]
+    kappa = 4.0
+    a = run(ctx, bank, xs, fs, PREC, want_tails=True, kappa=kappa)[0]
+    b = run(ctx, bank, xs, fs, "split_bf16", want_tails=True, kappa=kappa)[0]
+    for ga, gb in zip(a, b):
+        assert np.abs(ga["max"].astype(np.float64) - gb["max"]).max() <= 2 * TOL[PREC]
+        assert np.abs(ga["sigma"].astype(np.float64) - gb["sigma"]).max() <= 2 * TOL[PREC]
+    bf.bf_bank_destroy(bank)
+
+
+def test_full_size_gw_pair_sampled(ctx):
+    """Both 64 s series against all 65,536 templates (63 segments each);
+    twelve templates spread over the bank recomputed by the oracle over every
+    lag of series 0; the whole output against the split-BF16 path."""
+    w = synth.gw_pair()
+    fs, M = w["fs"], w["M"]
+    xs = w["series"]
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16)
+    outs, mean, info = run(ctx, bank, xs, fs, PREC)
+    assert info.correlations == 2 * (len(xs[0]) - M + 1) * 65536
+    p = oracle_params(w["grid"])
+    idx = np.array([0, 1, 255, 4096, 20000, 32767, 32768, 40000, 50000, 60001, 65534, 65535])
+    ref = oracle.search(xs[0], fs, subset(p, idx), M, want_rho=True)
+    g = {k: v[idx] for k, v in outs[0].items() if k in ("max", "argmax", "sigma")}
+    check_maxima(g, ref, ref["rho"], TOL[PREC], "full size")
+    check_sigma(g, ref, TOL[PREC])
+    direct = run(ctx, bank, xs, fs, "split_bf16")[0]
+    for ga, gb in zip(outs, direct):
+        assert np.abs(ga["max"].astype(np.float64) - gb["max"]).max() <= 2 * TOL[PREC]
+        assert ga["hist"].sum() == 65536
+    bf.bf_bank_destroy(bank)
+
+
+def test_rejections(ctx):
+    """Templates longer than half a transform, plans and the serving loop
+    answer BF_ENOTSUP."""
+    fs = 8192.0
+    bank = bf.bf_bank_create(ctx, [(bf.BF_LINEAR, bf.BF_ASC, 100.0, 2000.0, 1.0)], fs, 1.0)
+    x = np.random.default_rng(1).standard_normal(20000).astype(np.float32)
+    with pytest.raises(bf.BFError) as e:
+        run(ctx, bank, [x], fs, PREC)
+    assert e.value.status == bf.BF_ENOTSUP
+    bf.bf_bank_destroy(bank)
+    w = synth.tiny()
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], w["fs"], 1.0)
+    with pytest.raises(bf.BFError) as e:
+        bf.bf_plan_create(ctx, bank, [8192], w["fs"], bf.make_opts(precision=PREC))
+    assert e.value.status == bf.BF_ENOTSUP
+    with pytest.raises(bf.BFError) as e:
+        bf.bf_serve_submit(ctx, bank, w["series"][0], w["fs"], bf.make_opts(precision=PREC))
+    assert e.value.status == bf.BF_ENOTSUP
+    bf.bf_bank_destroy(bank)

@@ -106,7 +106,7 @@ def test_control_seed_edge_values(ctx):
 # ------------------------------------------------------------------ tiny config, full parity
 
 @pytest.mark.parametrize("prec,lt", [("split_bf16", 512), ("split_bf16", 256), ("fp32", 0),
-                                     ("bf16", 512), ("bf16", 256)])
+                                     ("bf16", 512), ("bf16", 256), ("fft_fp32", 0)])
 def test_tiny_dense_rho(ctx, tiny, prec, lt):
     w, bank, p, ref = tiny
     x, fs = w["series"][0], w["fs"]
@@ -120,7 +120,7 @@ def test_tiny_dense_rho(ctx, tiny, prec, lt):
     assert info.correlations == K * L
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "fft_fp32"])
 def test_tiny_maxima_sigma_hist(ctx, tiny, prec):
     w, bank, p, ref = tiny
     x, fs = w["series"][0], w["fs"]
@@ -134,7 +134,7 @@ def test_tiny_maxima_sigma_hist(ctx, tiny, prec):
     np.testing.assert_array_equal(mean, g["max"])             # one series
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fft_fp32"])
 def test_tiny_tf_map(ctx, tiny, prec):
     w, bank, p, ref = tiny
     x, fs, M = w["series"][0], w["fs"], w["M"]
@@ -145,7 +145,7 @@ def test_tiny_tf_map(ctx, tiny, prec):
     assert n_gpu > 0
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "fft_fp32"])
 def test_tiny_tails(ctx, tiny, prec):
     """The tail list holds every (k, tau) with |rho| >= thr + tol, nothing
     below thr - tol, each with its rho within tol."""
@@ -205,7 +205,7 @@ def test_parseval_predictor_matches_oracle(ctx):
     bf.bf_bank_destroy(bank)
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fft_fp32"])
 def test_parseval_tails_and_map(ctx, prec):
     """Tails |rho| >= kappa sigma_k with sigma_k predicted per template: the
     list and the map against the oracle with per-template thresholds."""
@@ -239,7 +239,7 @@ def test_parseval_tails_and_map(ctx, prec):
     bf.bf_bank_destroy(bank)
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fft_fp32"])
 def test_butterfly_templates(ctx, prec):
     """Superposed templates (ascending + descending, both senses at once):
     dense rho, maxima and the map of their two tracks against the oracle."""
@@ -298,7 +298,7 @@ def test_ragged_batch_and_bank_slice(ctx):
     xs[3][100:1700] = 0.0                                        # windows of zeros
     bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
     b0, b1 = 37, 181
-    for prec in ("split_bf16", "fp32", "bf16"):
+    for prec in ("split_bf16", "fp32", "bf16", "fft_fp32"):
         outs, mean, info = run(ctx, bank, xs, fs, prec, bank_begin=b0, bank_end=b1)
         assert info.n_templates == b1 - b0
         ps = subset(p, np.arange(b0, b1))
@@ -317,7 +317,7 @@ def test_zero_series_gives_zero(ctx):
     spec = synth.grid_spec([synth.LINEAR], [synth.ASC], [1.0], 20.0, 500.0, 2, 2)
     bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
     x = np.zeros(3000, np.float32)
-    for prec in ("split_bf16", "fp32"):
+    for prec in ("split_bf16", "fp32", "fft_fp32"):
         g = run(ctx, bank, [x], fs, prec)[0][0]
         assert np.all(g["max"] == 0) and np.all(g["argmax"] == 0) and np.all(g["sigma"] == 0)
     bf.bf_bank_destroy(bank)
