@@ -545,11 +545,12 @@ def run_reference(args, rank, world, local):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_kernel_case(tile_lags: int):
-    """Moderate case of the split-BF16 kernel for profiler captures: one 16 s
-    series at 4096 Hz against 16,384 power-law templates (split bank 268 MB,
-    larger than L2); two launches of the given tile shape (no autotuner
-    launches), each printed with its CUDA-event time."""
+def run_kernel_case(tile_lags: int, precision: str = "split_bf16"):
+    """Moderate case of the correlation kernels for profiler captures: one
+    16 s series at 4096 Hz against 16,384 power-law templates (split bank
+    268 MB, template spectra 537 MB, both larger than L2); two launches of
+    the given tile shape (no autotuner launches) or of the FFT route, each
+    printed with its CUDA-event time."""
     from paper_1802_01685_gb300 import bf, synth
     import __graft_entry__
     __graft_entry__.build()
@@ -558,9 +559,10 @@ def run_kernel_case(tile_lags: int):
     bank = bf.bf_bank_create_grid(ctx, w["grid"], w["fs"], 1.0, bf.BF_BANK_SPLIT_BF16)
     for _ in range(2):
         res = bf.bf_correlate(ctx, bank, [w["series"][0]], w["fs"],
-                              bf.make_opts(precision="split_bf16", tile_lags=tile_lags))
+                              bf.make_opts(precision=precision, tile_lags=tile_lags))
         info = bf.bf_result_info_get(res)
-        print(json.dumps({"kernel_case": "gw_pair 16 s x 16384 templates", "kernel_ms": info.kernel_ms,
+        print(json.dumps({"kernel_case": "gw_pair 16 s x 16384 templates", "precision": precision,
+                          "kernel_ms": info.kernel_ms,
                           "tile_lags": info.tile_lags, "correlations": info.correlations}), flush=True)
         bf.bf_result_destroy(res)
     bf.bf_bank_destroy(bank)
@@ -635,6 +637,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-fft", action="store_true")
+    ap.add_argument("--fft", action="store_true", help="--kernel-case: the FFT route")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--cpu-templates", type=int, default=384)
@@ -643,7 +646,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=8.0)
     args = ap.parse_args()
     if args.kernel_case:
-        run_kernel_case(args.tile_lags)
+        run_kernel_case(args.tile_lags, "fft_fp32" if args.fft else "split_bf16")
         return
     if args.workload != "gw_pair":
         run_workload(args.workload, args.check_templates)

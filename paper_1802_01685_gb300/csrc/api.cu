@@ -777,6 +777,7 @@ void bf_destroy(bf_ctx* ctx)
     cudaStreamSynchronize(ctx->stream);
     ctx->mem.reset();
     cudaFree(ctx->d_err);
+    if (ctx->fft_tw) cudaFree(ctx->fft_tw);
     cudaStreamDestroy(ctx->stream);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     delete ctx;
@@ -960,7 +961,8 @@ cudaError_t correlate_fft(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
 {
     const size_t S = prep.size(), K = r->K;
     const uint32_t V = FFT_POINTS - bank->M + 1;
-    cudaError_t e = cudaSuccess;
+    const float2* tw = nullptr;
+    cudaError_t e = fft_tables(ctx, st, &tw);
     for (size_t s0 = 0; s0 < S && e == cudaSuccess; s0 += MAX_FFT_SER) {
         const int n = (int)std::min<size_t>(MAX_FFT_SER, S - s0);
         FftSeriesBatch b{};
@@ -994,7 +996,9 @@ cudaError_t correlate_fft(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
         }
         b.n = n;
         b.V = V;
+        b.tw = tw;
         p.hspec = bank->fspec;
+        p.tw = tw;
         p.k_begin = (uint32_t)o.bank_begin;
         p.k_end = (uint32_t)o.bank_end;
         p.V = V;
@@ -1003,7 +1007,7 @@ cudaError_t correlate_fft(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
         p.cand_cap = r->cand_cap;
         p.cand = r->cand;
         p.cand_count = r->cand_count;
-        e = launch_fft_series(b, total, st);
+        e = launch_fft_series(b, total, ctx->n_sm, st);
         if (e == cudaSuccess) e = launch_corr_fft(p, ctx->n_sm, st);
     }
     return e;

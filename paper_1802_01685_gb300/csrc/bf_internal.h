@@ -111,6 +111,7 @@ struct FftSeries {
 
 struct FftParams {
     const float2* hspec;            // template half spectra [K][FFT_POINTS / 2], absolute k
+    const float2* tw;               // twiddle tables (corr_fft.cu)
     uint32_t k_begin, k_end;
     uint32_t V;                     // valid lags per segment, FFT_POINTS - M + 1
     int n_ser;
@@ -124,6 +125,7 @@ struct FftParams {
 struct FftSeriesBatch {
     int n;
     uint32_t V;
+    const float2* tw;
     const float* x[MAX_FFT_SER];
     uint64_t N[MAX_FFT_SER];
     float2* spec[MAX_FFT_SER];
@@ -180,7 +182,7 @@ struct FinalizeParams {
 };
 cudaError_t launch_finalize(const FinalizeParams& p, uint32_t K, uint32_t nbins, cudaStream_t s);
 uint32_t fft_segments(uint32_t L, uint32_t M);
-cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, cudaStream_t st);
+cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, int n_sm, cudaStream_t st);
 cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st);
 cudaError_t launch_skewnorm_fit(const float* v, uint64_t n, double* acc, double* out, int n_sm,
                                 cudaStream_t s);
@@ -233,6 +235,7 @@ struct bf_ctx {
     std::mutex launch_mu;               // serialises use of d_err / stream
     bfi::ServeState* serve = nullptr;   // owned; freed by serve_shutdown
     std::map<std::pair<int, uint32_t>, int> tuned;   // (precision, M_pad) -> lags per tile
+    float2* fft_tw = nullptr;           // twiddle tables of the FFT route (lazy, cudaMalloc)
     std::mutex tune_mu;
 };
 

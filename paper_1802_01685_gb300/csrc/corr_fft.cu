@@ -30,8 +30,12 @@
 //    thread one 16-point DFT per pass, in registers) and a final radix-2
 //    stage; real and imaginary parts live in separate padded float arrays
 //    (index i + i/32) so that almost every access pattern is free of bank
-//    conflicts.  Twiddles come from two small tables (128 + 64 entries,
-//    built in FP64): e^{2 pi i n / F} = T_hi[n / 64] T_lo[n % 64].
+//    conflicts, and every thread addresses them at fixed offsets from one
+//    base.  The twiddles of each pass sit in their own table, laid out
+//    [r][k] so that a warp reads consecutive entries: 15 x 16 and 15 x 256
+//    entries for the second and third passes and 4096 for the last stage,
+//    rounded from FP64 once per context and copied into shared memory by
+//    every CTA.
 #include "corr_common.cuh"
 #include "runtime.h"
 
@@ -44,37 +48,46 @@ constexpr int FH = FN / 2;                // 4096 half-spectrum bins (+ Nyquist 
 constexpr int FT = 512;                   // threads per FFT block
 constexpr int FBINS = FH / FT;            // 8 bins per thread
 constexpr int FPAD = FN + FN / 32;        // padded floats per array
-constexpr size_t FFT_SMEM = 2 * FPAD * sizeof(float);
+constexpr int ROW = FT + FT / 32;         // padded distance of rows 512 apart (528)
+// twiddle tables e^{+2 pi i n / 8192}: pass 2 [15][16], pass 3 [15][256], last stage [4096]
+constexpr int TW2 = 0, TW3 = 15 * 16, TWF = TW3 + 15 * 256, TW_N = TWF + FH;   // 8176 entries
+constexpr size_t FFT_SMEM = 2 * FPAD * sizeof(float) + TW_N * sizeof(float2);
 
-__device__ __forceinline__ int pidx(int i) { return i + (i >> 5); }
-
-struct Twiddles {
-    float2 hi[128];                       // e^{2 pi i a / 128}
-    float2 lo[64];                        // e^{2 pi i b / 8192}
-};
-
-__device__ __forceinline__ void twiddles_init(Twiddles& t)
+__global__ void k_fft_tables(float2* __restrict__ tw)
 {
-    for (int i = threadIdx.x; i < 192; i += blockDim.x) {
-        double s, c;
-        if (i < 128) {
-            sincospi((double)i / 64.0, &s, &c);
-            t.hi[i] = make_float2((float)c, (float)s);
-        } else {
-            sincospi((double)(i - 128) / 4096.0, &s, &c);
-            t.lo[i - 128] = make_float2((float)c, (float)s);
-        }
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < TW_N; e += gridDim.x * blockDim.x) {
+        int n;                                    // exponent in units of 2 pi / 8192
+        if (e < TW3) n = ((e - TW2) / 16 + 1) * ((e - TW2) % 16) * 32;
+        else if (e < TWF) n = ((e - TW3) / 256 + 1) * ((e - TW3) % 256) * 2;
+        else n = e - TWF;
+        double sn, cs;
+        sincospi((double)n / 4096.0, &sn, &cs);
+        tw[e] = make_float2((float)cs, (float)sn);
     }
 }
 
-// e^{SIGN 2 pi i n / 8192}, 0 <= n < 8192
-template <int SIGN>
-__device__ __forceinline__ float2 twiddle(const Twiddles& t, int n)
+struct Smem {
+    float* re;
+    float* im;
+    const float2* tw;
+};
+
+__device__ __forceinline__ Smem smem_setup(const float2* __restrict__ tw_global)
 {
-    const float2 h = t.hi[n >> 6], l = t.lo[n & 63];
-    const float re = h.x * l.x - h.y * l.y;
-    const float im = h.x * l.y + h.y * l.x;
-    return make_float2(re, SIGN > 0 ? im : -im);
+    extern __shared__ __align__(16) float fsm[];
+    Smem m{fsm, fsm + FPAD, reinterpret_cast<const float2*>(fsm + 2 * FPAD)};
+    float4* dst = reinterpret_cast<float4*>(fsm + 2 * FPAD);
+    const float4* src = reinterpret_cast<const float4*>(tw_global);
+    for (int i = threadIdx.x; i < TW_N / 2; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    return m;
+}
+
+template <int SIGN>
+__device__ __forceinline__ float2 tw_get(const float2* t, int e)
+{
+    const float2 w = t[e];
+    return make_float2(w.x, SIGN > 0 ? w.y : -w.y);
 }
 
 __device__ __forceinline__ void rotate(float& r, float& i, float2 w)
@@ -137,121 +150,141 @@ __device__ __forceinline__ void dft16(float (&r)[16], float (&i)[16])
 // One radix-16 Stockham pass over 8192 points with stride NS (1, 16, 256):
 // thread j reads in[j + 512 r], twiddles by e^{SIGN 2 pi i r (j mod NS) / (16 NS)},
 // takes the 16-point DFT and writes out[(j / NS) 16 NS + j mod NS + q NS].
+// Padded addresses (i + i/32) are written as a per-thread base plus
+// constant offsets.
 template <int SIGN, int NS>
-__device__ __forceinline__ void pass16(float* re, float* im, const Twiddles& tw)
+__device__ __forceinline__ void pass16(const Smem& m)
 {
     const int j = threadIdx.x;
+    const int rd = j + (j >> 5);
     float vr[16], vi[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-        const int a = pidx(j + r * (FN / 16));
-        vr[r] = re[a];
-        vi[r] = im[a];
+        vr[r] = m.re[rd + ROW * r];
+        vi[r] = m.im[rd + ROW * r];
     }
     __syncthreads();
     if (NS > 1) {
         const int k = j % NS;
-        constexpr int f = FN / (16 * NS);
+        const float2* t = m.tw + (NS == 16 ? TW2 : TW3) + k;
 #pragma unroll
-        for (int r = 1; r < 16; ++r) rotate(vr[r], vi[r], twiddle<SIGN>(tw, r * k * f));
+        for (int r = 1; r < 16; ++r) rotate(vr[r], vi[r], tw_get<SIGN>(t, (r - 1) * NS));
     }
     dft16<SIGN>(vr, vi);
-    const int base = (j / NS) * NS * 16 + (j % NS);
+    int wb;                                       // padded address of output q = 0
+    if (NS == 1) wb = 16 * j + (j >> 1);
+    else if (NS == 16) wb = (j / 16) * 264 + (j % 16);
+    else wb = (j / 256) * 4224 + (j % 256) + ((j % 256) >> 5);
 #pragma unroll
     for (int p = 0; p < 16; ++p) {
         const int q = 4 * (p % 4) + p / 4;
-        const int a = pidx(base + q * NS);
-        re[a] = vr[p];
-        im[a] = vi[p];
+        const int off = NS == 1 ? q : NS == 16 ? 16 * q + (q >> 1) : 264 * q;
+        m.re[wb + off] = vr[p];
+        m.im[wb + off] = vi[p];
     }
     __syncthreads();
 }
 
 template <int SIGN>
-__device__ __forceinline__ void fft_passes(float* re, float* im, const Twiddles& tw)
+__device__ __forceinline__ void fft_passes(const Smem& m)
 {
-    pass16<SIGN, 1>(re, im, tw);
-    pass16<SIGN, 16>(re, im, tw);
-    pass16<SIGN, 256>(re, im, tw);
+    pass16<SIGN, 1>(m);
+    pass16<SIGN, 16>(m);
+    pass16<SIGN, 256>(m);
 }
 
-// The final radix-2 stage for output pair (k, k + 4096), 0 <= k < 4096.
+// The final radix-2 stage for output pair (k, k + 4096), k = tid + 512 i.
 template <int SIGN>
-__device__ __forceinline__ void fft_final(const float* re, const float* im, const Twiddles& tw, int k,
-                                          float2& lo, float2& hi)
+__device__ __forceinline__ void fft_final(const Smem& m, int i, float2& lo, float2& hi)
 {
-    const int a = pidx(k), b = pidx(k + FH);
-    float vr = re[b], vi = im[b];
-    rotate(vr, vi, twiddle<SIGN>(tw, k));
-    const float ur = re[a], ui = im[a];
+    const int k = threadIdx.x + FT * i;
+    const int a = threadIdx.x + (threadIdx.x >> 5) + ROW * i;
+    float vr = m.re[a + FH + FH / 32], vi = m.im[a + FH + FH / 32];
+    rotate(vr, vi, tw_get<SIGN>(m.tw + TWF, k));
+    const float ur = m.re[a], ui = m.im[a];
     lo = make_float2(ur + vr, ui + vi);
     hi = make_float2(ur - vr, ui - vi);
 }
 
-// Spectrum of one segment of a series: real input, half spectrum out.
-__global__ void __launch_bounds__(FT, 1) k_fft_series(const __grid_constant__ FftSeriesBatch p)
+// Z[F - k] = the upper output of the final stage at 4096 - k, 1 <= k < 4096
+template <int SIGN>
+__device__ __forceinline__ float2 fft_final_mirror(const Smem& m, int k)
 {
-    extern __shared__ __align__(16) float fsm[];
-    float* re = fsm;
-    float* im = fsm + FPAD;
-    __shared__ Twiddles tw;
-    twiddles_init(tw);
-    int s = 0;
-    while (s + 1 < p.n && blockIdx.x >= p.seg_begin[s + 1]) ++s;
-    const uint32_t j = blockIdx.x - p.seg_begin[s];
-    const float* x = p.x[s];
-    const uint64_t N = p.N[s], t0 = (uint64_t)j * p.V;
-    for (int n = threadIdx.x; n < FN; n += FT) {
-        re[pidx(n)] = t0 + n < N ? x[t0 + n] : 0.f;
-        im[pidx(n)] = 0.f;
-    }
-    __syncthreads();
-    fft_passes<-1>(re, im, tw);
-    float2* out = p.spec[s] + (size_t)j * FH;
+    const int kk = FH - k;
+    const int a = kk + (kk >> 5);
+    float vr = m.re[a + FH + FH / 32], vi = m.im[a + FH + FH / 32];
+    rotate(vr, vi, tw_get<SIGN>(m.tw + TWF, kk));
+    return make_float2(m.re[a] - vr, m.im[a] - vi);
+}
+
+// Spectra of segments of a batch of series: real input, half spectrum out.
+__global__ void __launch_bounds__(FT, 1) k_fft_series(const __grid_constant__ FftSeriesBatch p,
+                                                      uint32_t total)
+{
+    const Smem m = smem_setup(p.tw);
+    const int tid = threadIdx.x;
+    for (uint32_t g = blockIdx.x; g < total; g += gridDim.x) {
+        int s = 0;
+        while (s + 1 < p.n && g >= p.seg_begin[s + 1]) ++s;
+        const uint32_t j = g - p.seg_begin[s];
+        const float* x = p.x[s];
+        const uint64_t N = p.N[s], t0 = (uint64_t)j * p.V;
+        for (int n = tid; n < FN; n += FT) {
+            const int a = n + (n >> 5);
+            m.re[a] = t0 + n < N ? x[t0 + n] : 0.f;
+            m.im[a] = 0.f;
+        }
+        __syncthreads();
+        fft_passes<-1>(m);
+        float2* out = p.spec[s] + (size_t)j * FH;
 #pragma unroll
-    for (int i = 0; i < FBINS; ++i) {
-        const int k = threadIdx.x + FT * i;
-        float2 lo, hi;
-        fft_final<-1>(re, im, tw, k, lo, hi);
-        out[k] = k == 0 ? make_float2(lo.x, hi.x) : lo;
+        for (int i = 0; i < FBINS; ++i) {
+            float2 lo, hi;
+            fft_final<-1>(m, i, lo, hi);
+            out[tid + FT * i] = (tid == 0 && i == 0) ? make_float2(lo.x, hi.x) : lo;
+        }
+        __syncthreads();
     }
 }
 
-// Spectra of templates (2q, 2q + 1) of a chunk of synthesised rows.
+// Spectra of templates (2q, 2q + 1) of a chunk of synthesised rows: one
+// complex transform of h_a + i h_b, separated by Hermitian symmetry.
 __global__ void __launch_bounds__(FT, 1) k_fft_bank(const float* __restrict__ rows, uint32_t n_rows,
+                                                    uint32_t n_pairs, const float2* __restrict__ tw,
                                                     float2* __restrict__ spec)
 {
-    extern __shared__ __align__(16) float fsm[];
-    float* re = fsm;
-    float* im = fsm + FPAD;
-    __shared__ Twiddles tw;
-    twiddles_init(tw);
-    const uint32_t a = 2 * blockIdx.x, b = a + 1;
-    const float* ra = rows + (size_t)a * FN;
-    const float* rb = rows + (size_t)b * FN;
-    for (int n = threadIdx.x; n < FN; n += FT) {
-        re[pidx(n)] = ra[n];
-        im[pidx(n)] = b < n_rows ? rb[n] : 0.f;
-    }
-    __syncthreads();
-    fft_passes<-1>(re, im, tw);
-    float2* sa = spec + (size_t)a * FH;
-    float2* sb = spec + (size_t)b * FH;
-#pragma unroll
-    for (int i = 0; i < FBINS; ++i) {
-        const int k = threadIdx.x + FT * i;
-        float2 zk, zn, zm, unused;
-        fft_final<-1>(re, im, tw, k, zk, zn);           // Z[k], Z[k + 4096]
-        if (k == 0) {
-            // DC and Nyquist of both real templates: real parts of Z[0], Z[4096]
-            sa[0] = make_float2(zk.x, zn.x);
-            if (b < n_rows) sb[0] = make_float2(zk.y, zn.y);
-        } else {
-            fft_final<-1>(re, im, tw, FH - k, unused, zm);  // Z[F - k]
-            // H_a = (Z[k] + conj Z[F-k]) / 2,  H_b = (Z[k] - conj Z[F-k]) / 2i
-            sa[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-            if (b < n_rows) sb[k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    const Smem m = smem_setup(tw);
+    const int tid = threadIdx.x;
+    for (uint32_t q = blockIdx.x; q < n_pairs; q += gridDim.x) {
+        const uint32_t a = 2 * q, b = a + 1;
+        const float* ra = rows + (size_t)a * FN;
+        const float* rb = rows + (size_t)b * FN;
+        for (int n = tid; n < FN; n += FT) {
+            const int ad = n + (n >> 5);
+            m.re[ad] = ra[n];
+            m.im[ad] = b < n_rows ? rb[n] : 0.f;
         }
+        __syncthreads();
+        fft_passes<-1>(m);
+        float2* sa = spec + (size_t)a * FH;
+        float2* sb = spec + (size_t)b * FH;
+#pragma unroll
+        for (int i = 0; i < FBINS; ++i) {
+            const int k = tid + FT * i;
+            float2 zk, zn;
+            fft_final<-1>(m, i, zk, zn);           // Z[k], Z[k + 4096]
+            if (k == 0) {
+                // DC and Nyquist of both real templates: real parts of Z[0], Z[4096]
+                sa[0] = make_float2(zk.x, zn.x);
+                if (b < n_rows) sb[0] = make_float2(zk.y, zn.y);
+            } else {
+                const float2 zm = fft_final_mirror<-1>(m, k);      // Z[F - k]
+                // H_a = (Z[k] + conj Z[F-k]) / 2,  H_b = (Z[k] - conj Z[F-k]) / 2i
+                sa[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+                if (b < n_rows) sb[k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -262,17 +295,23 @@ __device__ __forceinline__ void push_tail(const FftParams& p, uint32_t series, u
     if (i < p.cand_cap) p.cand[i] = Candidate{series, k, tau, rho};
 }
 
+// running max |rho| with its first lag (lags arrive out of order within a thread)
+__device__ __forceinline__ void track_max(float a, uint32_t tau, float& best, uint32_t& arg)
+{
+    if (a > best || (a == best && tau < arg)) {
+        best = a;
+        arg = tau;
+    }
+}
+
 // The correlation: one template pair per CTA at a time, all segments of all
 // series of the batch.
 __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftParams p)
 {
-    extern __shared__ __align__(16) float fsm[];
-    float* re = fsm;
-    float* im = fsm + FPAD;
-    __shared__ Twiddles tw;
-    twiddles_init(tw);
-    __syncthreads();
+    const Smem m = smem_setup(p.tw);
     const int tid = threadIdx.x, lane = tid & 31;
+    const int rd = tid + (tid >> 5);
+    const int rv = (FN - tid) + ((FN - tid) >> 5);        // padded address of Z[F - tid]
     const uint32_t n_pairs = (p.k_end - p.k_begin + 1) / 2;
     const float scale = 1.f / (float)FN;
 
@@ -291,62 +330,60 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
             const uint32_t la = ka - p.k_begin, lb = kb - p.k_begin;
             const float thr_a = S.sigma_pred ? S.kappa * S.sigma_pred[la] : p.thr;
             const float thr_b = !has_b ? INFINITY : (S.sigma_pred ? S.kappa * S.sigma_pred[lb] : p.thr);
-            unsigned long long best_a = 0ull, best_b = 0ull;
+            float best_a = -1.f, best_b = -1.f;
+            uint32_t arg_a = 0xFFFFFFFFu, arg_b = 0xFFFFFFFFu;
             double ss_a = 0.0, ss_b = 0.0;
             for (uint32_t j = 0; j < S.nseg; ++j) {
                 const float2* X = S.spec + (size_t)j * FH;
 #pragma unroll
                 for (int i = 0; i < FBINS; ++i) {
-                    const int f = tid + FT * i;
-                    const float2 x = __ldg(X + f);
-                    if (f == 0) {
+                    const float2 x = __ldg(X + tid + FT * i);
+                    if (tid == 0 && i == 0) {
                         // DC (x.x) and Nyquist (x.y): real products
-                        re[pidx(0)] = x.x * ha[0].x;
-                        im[pidx(0)] = x.x * hb[0].x;
-                        re[pidx(FH)] = x.y * ha[0].y;
-                        im[pidx(FH)] = x.y * hb[0].y;
+                        m.re[0] = x.x * ha[0].x;
+                        m.im[0] = x.x * hb[0].x;
+                        m.re[FH + FH / 32] = x.y * ha[0].y;
+                        m.im[FH + FH / 32] = x.y * hb[0].y;
                     } else {
-                        // Y = X conj(H)
+                        // Y = X conj(H); Z[f] = Ya + i Yb, Z[F - f] = conj(Ya) + i conj(Yb)
                         const float yar = x.x * ha[i].x + x.y * ha[i].y;
                         const float yai = x.y * ha[i].x - x.x * ha[i].y;
                         const float ybr = x.x * hb[i].x + x.y * hb[i].y;
                         const float ybi = x.y * hb[i].x - x.x * hb[i].y;
-                        // Z[f] = Ya + i Yb, Z[F - f] = conj(Ya) + i conj(Yb)
-                        re[pidx(f)] = yar - ybi;
-                        im[pidx(f)] = yai + ybr;
-                        re[pidx(FN - f)] = yar + ybi;
-                        im[pidx(FN - f)] = ybr - yai;
+                        m.re[rd + ROW * i] = yar - ybi;
+                        m.im[rd + ROW * i] = yai + ybr;
+                        m.re[rv - ROW * i] = yar + ybi;
+                        m.im[rv - ROW * i] = ybr - yai;
                     }
                 }
                 __syncthreads();
-                fft_passes<1>(re, im, tw);
+                fft_passes<1>(m);
                 const uint32_t t0 = j * p.V;
                 const uint32_t nv = min(p.V, S.L - t0);
                 float pa = 0.f, pb = 0.f;
 #pragma unroll
                 for (int i = 0; i < FBINS; ++i) {
-                    const int k = tid + FT * i;
                     float2 z[2];
-                    fft_final<1>(re, im, tw, k, z[0], z[1]);
+                    fft_final<1>(m, i, z[0], z[1]);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const uint32_t t = (uint32_t)k + (uint32_t)(h * FH);
+                        const uint32_t t = (uint32_t)(tid + FT * i + FH * h);
                         if (t < nv) {
                             const uint32_t tau = t0 + t;
-                            const float inv = S.inv[tau] * scale;
+                            const float inv = __ldg(S.inv + tau) * scale;
                             const float ra = z[h].x * inv, rb = z[h].y * inv;
                             const float aa = fabsf(ra), ab = fabsf(rb);
-                            const unsigned long long key_a = pack_max(aa, tau);
-                            best_a = key_a > best_a ? key_a : best_a;
+                            track_max(aa, tau, best_a, arg_a);
+                            track_max(ab, tau, best_b, arg_b);
                             pa = fmaf(ra, ra, pa);
-                            if (aa >= thr_a) push_tail(p, S.series_id, ka, tau, ra);
-                            if (S.rho) S.rho[(size_t)la * S.L + tau] = ra;
-                            if (has_b) {
-                                const unsigned long long key_b = pack_max(ab, tau);
-                                best_b = key_b > best_b ? key_b : best_b;
-                                pb = fmaf(rb, rb, pb);
+                            pb = fmaf(rb, rb, pb);
+                            if (aa >= thr_a || ab >= thr_b) {
+                                if (aa >= thr_a) push_tail(p, S.series_id, ka, tau, ra);
                                 if (ab >= thr_b) push_tail(p, S.series_id, kb, tau, rb);
-                                if (S.rho) S.rho[(size_t)lb * S.L + tau] = rb;
+                            }
+                            if (S.rho) {
+                                S.rho[(size_t)la * S.L + tau] = ra;
+                                if (has_b) S.rho[(size_t)lb * S.L + tau] = rb;
                             }
                         }
                     }
@@ -355,20 +392,22 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
                 ss_b += (double)pb;
                 __syncthreads();
             }
+            unsigned long long key_a = best_a >= 0.f ? pack_max(best_a, arg_a) : 0ull;
+            unsigned long long key_b = best_b >= 0.f ? pack_max(best_b, arg_b) : 0ull;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long oa = __shfl_xor_sync(0xffffffffu, best_a, o);
-                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best_b, o);
-                best_a = oa > best_a ? oa : best_a;
-                best_b = ob > best_b ? ob : best_b;
+                const unsigned long long oa = __shfl_xor_sync(0xffffffffu, key_a, o);
+                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, key_b, o);
+                key_a = oa > key_a ? oa : key_a;
+                key_b = ob > key_b ? ob : key_b;
                 ss_a += __shfl_xor_sync(0xffffffffu, ss_a, o);
                 ss_b += __shfl_xor_sync(0xffffffffu, ss_b, o);
             }
             if (lane == 0) {
-                atomicMax(S.vmax + la, best_a);
+                atomicMax(S.vmax + la, key_a);
                 atomicAdd(S.sumsq + la, ss_a);
                 if (has_b) {
-                    atomicMax(S.vmax + lb, best_b);
+                    atomicMax(S.vmax + lb, key_b);
                     atomicAdd(S.sumsq + lb, ss_b);
                 }
             }
@@ -391,6 +430,27 @@ cudaError_t fft_attributes()
 
 }  // namespace
 
+// The context's twiddle tables, built on first use.
+cudaError_t fft_tables(bf_ctx* ctx, cudaStream_t st, const float2** out)
+{
+    if (!ctx->fft_tw) {
+        float2* t = nullptr;
+        cudaError_t e = cudaMalloc(&t, TW_N * sizeof(float2));
+        if (e != cudaSuccess) return e;
+        count_launches(1);
+        k_fft_tables<<<(TW_N + 255) / 256, 256, 0, st>>>(t);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaFree(t);
+            return e;
+        }
+        ctx->fft_tw = t;
+    }
+    *out = ctx->fft_tw;
+    return fft_attributes();
+}
+
 // Half spectra of every template of the bank, [K rounded up to even][4096]
 // complex, computed once and kept with the bank.
 bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
@@ -401,8 +461,9 @@ bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
                   bank->M);
         return BF_ENOTSUP;
     }
-    cudaError_t e = fft_attributes();
-    if (e != cudaSuccess) return cuda_fail(e, "FFT attributes");
+    const float2* tw = nullptr;
+    cudaError_t e = fft_tables(ctx, st, &tw);
+    if (e != cudaSuccess) return cuda_fail(e, "FFT tables");
     const size_t K2 = bank->K + (bank->K & 1);
     Allocator& mem = *ctx->mem;
     float2* spec = static_cast<float2*>(mem.alloc(K2 * FH * sizeof(float2)));
@@ -420,8 +481,10 @@ bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
         e = launch_bank_synth(bank->d_params + k0, (uint32_t)kc, (uint32_t)nr, bank->M, FN, bank->fs, rows,
                               nullptr, nullptr, st);
         if (e == cudaSuccess) {
+            const uint32_t pairs = (uint32_t)(nr / 2);
             count_launches(1);
-            k_fft_bank<<<(unsigned)(nr / 2), FT, FFT_SMEM, st>>>(rows, (uint32_t)kc, spec + k0 * FH);
+            k_fft_bank<<<std::min<uint32_t>(pairs, (uint32_t)ctx->n_sm), FT, FFT_SMEM, st>>>(
+                rows, (uint32_t)kc, pairs, tw, spec + k0 * FH);
             e = cudaGetLastError();
         }
     }
@@ -441,19 +504,16 @@ uint32_t fft_segments(uint32_t L, uint32_t M)
     return (L + V - 1) / V;
 }
 
-cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, cudaStream_t st)
+cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, int n_sm, cudaStream_t st)
 {
-    cudaError_t e = fft_attributes();
-    if (e != cudaSuccess || total_segments == 0) return e;
+    if (total_segments == 0) return cudaSuccess;
     count_launches(1);
-    k_fft_series<<<total_segments, FT, FFT_SMEM, st>>>(b);
+    k_fft_series<<<std::min<uint32_t>(total_segments, (uint32_t)n_sm), FT, FFT_SMEM, st>>>(b, total_segments);
     return cudaGetLastError();
 }
 
 cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st)
 {
-    cudaError_t e = fft_attributes();
-    if (e != cudaSuccess) return e;
     const uint32_t n_pairs = (p.k_end - p.k_begin + 1) / 2;
     if (n_pairs == 0 || p.n_ser == 0) return cudaSuccess;
     const unsigned grid = std::min<unsigned>(n_pairs, (unsigned)n_sm);

@@ -74,6 +74,8 @@ void serve_shutdown(bf_ctx* ctx);
 bf_status bank_power_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st);
 // template half spectra of the FFT route, computed once per bank
 bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st);
+// the context's twiddle tables of the FFT route (built on first use)
+cudaError_t fft_tables(bf_ctx* ctx, cudaStream_t st, const float2** out);
 bf_status predict_sigma(bf_ctx* ctx, const bf_bank* bank, const PreparedSeries& ps, size_t k_begin,
                         size_t k_end, float* out, std::vector<void*>& scratch, cudaStream_t st);
 
