@@ -18,7 +18,9 @@
 //  * template spectra are computed once per bank (two real templates per
 //    complex FFT) and kept in HBM as half spectra: 4096 complex values per
 //    template, bin 0 carrying the DC and Nyquist terms (both real);
-//  * each segment spectrum is computed once per call; all of them stay in L2;
+//  * each segment spectrum is computed once per call; all of them stay in L2
+//    and reach shared memory by asynchronous copies (cp.async) issued one
+//    segment ahead, together with the segment's window norms;
 //  * one CTA of 512 threads owns a pair of templates (a, b) at a time and
 //    holds their spectra in registers (8 bins per thread).  For every segment
 //    it forms Z = X conj(H_a) + i X conj(H_b) over all F bins (Hermitian
@@ -28,10 +30,10 @@
 //    epilogue, so the filter output never reaches HBM.
 //  * The FFT is a Stockham autosort FFT with three radix-16 passes (each
 //    thread one 16-point DFT per pass, in registers) and a final radix-2
-//    stage; real and imaginary parts live in separate padded float arrays
-//    (index i + i/32) so that almost every access pattern is free of bank
-//    conflicts, and every thread addresses them at fixed offsets from one
-//    base.  The twiddles of each pass sit in their own table, laid out
+//    stage; the work array holds complex values with index i stored at
+//    i + i/16, so that every pass moves a warp's 64-bit values in the
+//    minimum two wavefronts, and every thread addresses it at fixed offsets
+//    from one base.  The twiddles of each pass sit in their own table, laid out
 //    [r][k] so that a warp reads consecutive entries: 15 x 16 and 15 x 256
 //    entries for the second and third passes and 4096 for the last stage,
 //    rounded from FP64 once per context and copied into shared memory by
@@ -47,11 +49,16 @@ constexpr int FN = FFT_POINTS;            // 8192
 constexpr int FH = FN / 2;                // 4096 half-spectrum bins (+ Nyquist packed in bin 0)
 constexpr int FT = 512;                   // threads per FFT block
 constexpr int FBINS = FH / FT;            // 8 bins per thread
-constexpr int FPAD = FN + FN / 32;        // padded floats per array
-constexpr int ROW = FT + FT / 32;         // padded distance of rows 512 apart (528)
+constexpr int ZPAD = FN + FN / 16;        // padded complex values of the work array
+constexpr int ROW = FT + FT / 16;         // padded distance of elements 512 apart (544)
+constexpr int UPPER = FH + FH / 16;       // padded distance of elements 4096 apart (4352)
 // twiddle tables e^{+2 pi i n / 8192}: pass 2 [15][16], pass 3 [15][256], last stage [4096]
 constexpr int TW2 = 0, TW3 = 15 * 16, TWF = TW3 + 15 * 256, TW_N = TWF + FH;   // 8176 entries
-constexpr size_t FFT_SMEM = 2 * FPAD * sizeof(float) + TW_N * sizeof(float2);
+constexpr int INV_MAX = FN;               // window norms staged per segment (V <= 8192)
+// shared memory: work array, twiddles, then (correlation only) the staged
+// segment spectrum and window norms
+constexpr size_t FFT_SMEM = (ZPAD + TW_N) * sizeof(float2);
+constexpr size_t CORR_SMEM = FFT_SMEM + FH * sizeof(float2) + INV_MAX * sizeof(float);
 
 __global__ void k_fft_tables(float2* __restrict__ tw)
 {
@@ -66,22 +73,43 @@ __global__ void k_fft_tables(float2* __restrict__ tw)
     }
 }
 
+// Work array z (complex, index i stored at i + i/16), twiddle tables, and the
+// staging buffers of the correlation kernel.
 struct Smem {
-    float* re;
-    float* im;
+    float2* z;
     const float2* tw;
+    float2* x;
+    float* inv;
 };
 
 __device__ __forceinline__ Smem smem_setup(const float2* __restrict__ tw_global)
 {
-    extern __shared__ __align__(16) float fsm[];
-    Smem m{fsm, fsm + FPAD, reinterpret_cast<const float2*>(fsm + 2 * FPAD)};
-    float4* dst = reinterpret_cast<float4*>(fsm + 2 * FPAD);
+    extern __shared__ __align__(16) float2 fsm[];
+    Smem m{fsm, fsm + ZPAD, fsm + ZPAD + TW_N, reinterpret_cast<float*>(fsm + ZPAD + TW_N + FH)};
+    float4* dst = reinterpret_cast<float4*>(fsm + ZPAD);
     const float4* src = reinterpret_cast<const float4*>(tw_global);
     for (int i = threadIdx.x; i < TW_N / 2; i += blockDim.x) dst[i] = __ldg(src + i);
     __syncthreads();
     return m;
 }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// waits until at most N of this thread's most recent groups are in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <int SIGN>
 __device__ __forceinline__ float2 tw_get(const float2* t, int e)
@@ -150,18 +178,18 @@ __device__ __forceinline__ void dft16(float (&r)[16], float (&i)[16])
 // One radix-16 Stockham pass over 8192 points with stride NS (1, 16, 256):
 // thread j reads in[j + 512 r], twiddles by e^{SIGN 2 pi i r (j mod NS) / (16 NS)},
 // takes the 16-point DFT and writes out[(j / NS) 16 NS + j mod NS + q NS].
-// Padded addresses (i + i/32) are written as a per-thread base plus
-// constant offsets.
+// Padded addresses (i + i/16) are a per-thread base plus constant offsets.
 template <int SIGN, int NS>
 __device__ __forceinline__ void pass16(const Smem& m)
 {
     const int j = threadIdx.x;
-    const int rd = j + (j >> 5);
+    const int rd = j + (j >> 4);
     float vr[16], vi[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-        vr[r] = m.re[rd + ROW * r];
-        vi[r] = m.im[rd + ROW * r];
+        const float2 v = m.z[rd + ROW * r];
+        vr[r] = v.x;
+        vi[r] = v.y;
     }
     __syncthreads();
     if (NS > 1) {
@@ -172,15 +200,14 @@ __device__ __forceinline__ void pass16(const Smem& m)
     }
     dft16<SIGN>(vr, vi);
     int wb;                                       // padded address of output q = 0
-    if (NS == 1) wb = 16 * j + (j >> 1);
-    else if (NS == 16) wb = (j / 16) * 264 + (j % 16);
-    else wb = (j / 256) * 4224 + (j % 256) + ((j % 256) >> 5);
+    if (NS == 1) wb = 17 * j;
+    else if (NS == 16) wb = (j / 16) * 272 + (j % 16);
+    else wb = (j / 256) * 4352 + (j % 256) + ((j % 256) >> 4);
 #pragma unroll
     for (int p = 0; p < 16; ++p) {
         const int q = 4 * (p % 4) + p / 4;
-        const int off = NS == 1 ? q : NS == 16 ? 16 * q + (q >> 1) : 264 * q;
-        m.re[wb + off] = vr[p];
-        m.im[wb + off] = vi[p];
+        const int off = NS == 1 ? q : NS == 16 ? 17 * q : 272 * q;
+        m.z[wb + off] = make_float2(vr[p], vi[p]);
     }
     __syncthreads();
 }
@@ -198,12 +225,13 @@ template <int SIGN>
 __device__ __forceinline__ void fft_final(const Smem& m, int i, float2& lo, float2& hi)
 {
     const int k = threadIdx.x + FT * i;
-    const int a = threadIdx.x + (threadIdx.x >> 5) + ROW * i;
-    float vr = m.re[a + FH + FH / 32], vi = m.im[a + FH + FH / 32];
+    const int a = threadIdx.x + (threadIdx.x >> 4) + ROW * i;
+    const float2 v = m.z[a + UPPER];
+    float vr = v.x, vi = v.y;
     rotate(vr, vi, tw_get<SIGN>(m.tw + TWF, k));
-    const float ur = m.re[a], ui = m.im[a];
-    lo = make_float2(ur + vr, ui + vi);
-    hi = make_float2(ur - vr, ui - vi);
+    const float2 u = m.z[a];
+    lo = make_float2(u.x + vr, u.y + vi);
+    hi = make_float2(u.x - vr, u.y - vi);
 }
 
 // Z[F - k] = the upper output of the final stage at 4096 - k, 1 <= k < 4096
@@ -211,10 +239,12 @@ template <int SIGN>
 __device__ __forceinline__ float2 fft_final_mirror(const Smem& m, int k)
 {
     const int kk = FH - k;
-    const int a = kk + (kk >> 5);
-    float vr = m.re[a + FH + FH / 32], vi = m.im[a + FH + FH / 32];
+    const int a = kk + (kk >> 4);
+    const float2 v = m.z[a + UPPER];
+    float vr = v.x, vi = v.y;
     rotate(vr, vi, tw_get<SIGN>(m.tw + TWF, kk));
-    return make_float2(m.re[a] - vr, m.im[a] - vi);
+    const float2 u = m.z[a];
+    return make_float2(u.x - vr, u.y - vi);
 }
 
 // Spectra of segments of a batch of series: real input, half spectrum out.
@@ -229,11 +259,7 @@ __global__ void __launch_bounds__(FT, 1) k_fft_series(const __grid_constant__ Ff
         const uint32_t j = g - p.seg_begin[s];
         const float* x = p.x[s];
         const uint64_t N = p.N[s], t0 = (uint64_t)j * p.V;
-        for (int n = tid; n < FN; n += FT) {
-            const int a = n + (n >> 5);
-            m.re[a] = t0 + n < N ? x[t0 + n] : 0.f;
-            m.im[a] = 0.f;
-        }
+        for (int n = tid; n < FN; n += FT) m.z[n + (n >> 4)] = make_float2(t0 + n < N ? x[t0 + n] : 0.f, 0.f);
         __syncthreads();
         fft_passes<-1>(m);
         float2* out = p.spec[s] + (size_t)j * FH;
@@ -259,11 +285,7 @@ __global__ void __launch_bounds__(FT, 1) k_fft_bank(const float* __restrict__ ro
         const uint32_t a = 2 * q, b = a + 1;
         const float* ra = rows + (size_t)a * FN;
         const float* rb = rows + (size_t)b * FN;
-        for (int n = tid; n < FN; n += FT) {
-            const int ad = n + (n >> 5);
-            m.re[ad] = ra[n];
-            m.im[ad] = b < n_rows ? rb[n] : 0.f;
-        }
+        for (int n = tid; n < FN; n += FT) m.z[n + (n >> 4)] = make_float2(ra[n], b < n_rows ? rb[n] : 0.f);
         __syncthreads();
         fft_passes<-1>(m);
         float2* sa = spec + (size_t)a * FH;
@@ -304,94 +326,131 @@ __device__ __forceinline__ void track_max(float a, uint32_t tau, float& best, ui
     }
 }
 
-// The correlation: one template pair per CTA at a time, all segments of all
-// series of the batch.
+// segment spectrum j of a series into shared memory (16-byte asynchronous copies)
+__device__ __forceinline__ void stage_spectrum(const Smem& m, const float2* src)
+{
+    for (int c = threadIdx.x; c < FH / 2; c += FT) cp_async16(m.x + 2 * c, src + 2 * c);
+}
+
+// The correlation.  Each CTA walks its items (template pair, series, segment)
+// in order; while the FFT of one segment runs, the spectrum of the next one
+// and the window norms of this one arrive in shared memory.
 __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftParams p)
 {
     const Smem m = smem_setup(p.tw);
     const int tid = threadIdx.x, lane = tid & 31;
-    const int rd = tid + (tid >> 5);
-    const int rv = (FN - tid) + ((FN - tid) >> 5);        // padded address of Z[F - tid]
+    const int rd = tid + (tid >> 4);
+    const int rv = (FN - tid) + ((FN - tid) >> 4);        // padded address of Z[F - tid]
     const uint32_t n_pairs = (p.k_end - p.k_begin + 1) / 2;
     const float scale = 1.f / (float)FN;
+    uint32_t pair = blockIdx.x;
+    if (pair >= n_pairs || p.n_ser == 0) return;
+    int s = 0;
+    uint32_t j = 0;
+    stage_spectrum(m, p.ser[0].spec);
+    cp_async_commit();
 
-    for (uint32_t pair = blockIdx.x; pair < n_pairs; pair += gridDim.x) {
-        const uint32_t ka = p.k_begin + 2 * pair, kb = ka + 1;
-        const bool has_b = kb < p.k_end;
-        float2 ha[FBINS], hb[FBINS];
+    float2 ha[FBINS], hb[FBINS];
+    uint32_t ka = 0, kb = 0;
+    bool has_b = false;
+    float thr_a = 0.f, thr_b = 0.f;
+    float best_a = -1.f, best_b = -1.f;
+    uint32_t arg_a = 0xFFFFFFFFu, arg_b = 0xFFFFFFFFu;
+    double ss_a = 0.0, ss_b = 0.0;
+    bool new_pair = true, new_series = true;
+
+    for (;;) {
+        const FftSeries& S = p.ser[s];
+        if (new_pair) {
+            ka = p.k_begin + 2 * pair;
+            kb = ka + 1;
+            has_b = kb < p.k_end;
+#pragma unroll
+            for (int i = 0; i < FBINS; ++i) {
+                const int f = tid + FT * i;
+                ha[i] = p.hspec[(size_t)ka * FH + f];
+                hb[i] = has_b ? p.hspec[(size_t)kb * FH + f] : make_float2(0.f, 0.f);
+            }
+        }
+        const uint32_t la = ka - p.k_begin, lb = kb - p.k_begin;
+        if (new_series) {
+            thr_a = S.sigma_pred ? S.kappa * S.sigma_pred[la] : p.thr;
+            thr_b = !has_b ? INFINITY : (S.sigma_pred ? S.kappa * S.sigma_pred[lb] : p.thr);
+            best_a = best_b = -1.f;
+            arg_a = arg_b = 0xFFFFFFFFu;
+            ss_a = ss_b = 0.0;
+        }
+        const uint32_t t0 = j * p.V;
+        const uint32_t nv = min(p.V, S.L - t0);
+        for (uint32_t e = tid; e < nv; e += FT) cp_async4(m.inv + e, S.inv + t0 + e);
+        cp_async_commit();
+        // the item after this one
+        uint32_t np = pair, nj = j + 1;
+        int ns = s;
+        if (nj >= S.nseg) {
+            nj = 0;
+            if (++ns >= p.n_ser) {
+                ns = 0;
+                np = pair + gridDim.x;
+            }
+        }
+        cp_async_wait<1>();                         // this segment's spectrum
+        __syncthreads();
 #pragma unroll
         for (int i = 0; i < FBINS; ++i) {
-            const int f = tid + FT * i;
-            ha[i] = p.hspec[(size_t)ka * FH + f];
-            hb[i] = has_b ? p.hspec[(size_t)kb * FH + f] : make_float2(0.f, 0.f);
-        }
-        for (int s = 0; s < p.n_ser; ++s) {
-            const FftSeries& S = p.ser[s];
-            const uint32_t la = ka - p.k_begin, lb = kb - p.k_begin;
-            const float thr_a = S.sigma_pred ? S.kappa * S.sigma_pred[la] : p.thr;
-            const float thr_b = !has_b ? INFINITY : (S.sigma_pred ? S.kappa * S.sigma_pred[lb] : p.thr);
-            float best_a = -1.f, best_b = -1.f;
-            uint32_t arg_a = 0xFFFFFFFFu, arg_b = 0xFFFFFFFFu;
-            double ss_a = 0.0, ss_b = 0.0;
-            for (uint32_t j = 0; j < S.nseg; ++j) {
-                const float2* X = S.spec + (size_t)j * FH;
-#pragma unroll
-                for (int i = 0; i < FBINS; ++i) {
-                    const float2 x = __ldg(X + tid + FT * i);
-                    if (tid == 0 && i == 0) {
-                        // DC (x.x) and Nyquist (x.y): real products
-                        m.re[0] = x.x * ha[0].x;
-                        m.im[0] = x.x * hb[0].x;
-                        m.re[FH + FH / 32] = x.y * ha[0].y;
-                        m.im[FH + FH / 32] = x.y * hb[0].y;
-                    } else {
-                        // Y = X conj(H); Z[f] = Ya + i Yb, Z[F - f] = conj(Ya) + i conj(Yb)
-                        const float yar = x.x * ha[i].x + x.y * ha[i].y;
-                        const float yai = x.y * ha[i].x - x.x * ha[i].y;
-                        const float ybr = x.x * hb[i].x + x.y * hb[i].y;
-                        const float ybi = x.y * hb[i].x - x.x * hb[i].y;
-                        m.re[rd + ROW * i] = yar - ybi;
-                        m.im[rd + ROW * i] = yai + ybr;
-                        m.re[rv - ROW * i] = yar + ybi;
-                        m.im[rv - ROW * i] = ybr - yai;
-                    }
-                }
-                __syncthreads();
-                fft_passes<1>(m);
-                const uint32_t t0 = j * p.V;
-                const uint32_t nv = min(p.V, S.L - t0);
-                float pa = 0.f, pb = 0.f;
-#pragma unroll
-                for (int i = 0; i < FBINS; ++i) {
-                    float2 z[2];
-                    fft_final<1>(m, i, z[0], z[1]);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const uint32_t t = (uint32_t)(tid + FT * i + FH * h);
-                        if (t < nv) {
-                            const uint32_t tau = t0 + t;
-                            const float inv = __ldg(S.inv + tau) * scale;
-                            const float ra = z[h].x * inv, rb = z[h].y * inv;
-                            const float aa = fabsf(ra), ab = fabsf(rb);
-                            track_max(aa, tau, best_a, arg_a);
-                            track_max(ab, tau, best_b, arg_b);
-                            pa = fmaf(ra, ra, pa);
-                            pb = fmaf(rb, rb, pb);
-                            if (aa >= thr_a || ab >= thr_b) {
-                                if (aa >= thr_a) push_tail(p, S.series_id, ka, tau, ra);
-                                if (ab >= thr_b) push_tail(p, S.series_id, kb, tau, rb);
-                            }
-                            if (S.rho) {
-                                S.rho[(size_t)la * S.L + tau] = ra;
-                                if (has_b) S.rho[(size_t)lb * S.L + tau] = rb;
-                            }
-                        }
-                    }
-                }
-                ss_a += (double)pa;
-                ss_b += (double)pb;
-                __syncthreads();
+            const float2 x = m.x[tid + FT * i];
+            if (tid == 0 && i == 0) {
+                // DC (x.x) and Nyquist (x.y): real products
+                m.z[0] = make_float2(x.x * ha[0].x, x.x * hb[0].x);
+                m.z[UPPER] = make_float2(x.y * ha[0].y, x.y * hb[0].y);
+            } else {
+                // Y = X conj(H); Z[f] = Ya + i Yb, Z[F - f] = conj(Ya) + i conj(Yb)
+                const float yar = x.x * ha[i].x + x.y * ha[i].y;
+                const float yai = x.y * ha[i].x - x.x * ha[i].y;
+                const float ybr = x.x * hb[i].x + x.y * hb[i].y;
+                const float ybi = x.y * hb[i].x - x.x * hb[i].y;
+                m.z[rd + ROW * i] = make_float2(yar - ybi, yai + ybr);
+                m.z[rv - ROW * i] = make_float2(yar + ybi, ybr - yai);
             }
+        }
+        __syncthreads();
+        if (np < n_pairs) stage_spectrum(m, p.ser[ns].spec + (size_t)nj * FH);
+        cp_async_commit();
+        fft_passes<1>(m);
+        cp_async_wait<1>();                         // this segment's window norms
+        __syncthreads();
+        float pa = 0.f, pb = 0.f;
+#pragma unroll
+        for (int i = 0; i < FBINS; ++i) {
+            float2 z[2];
+            fft_final<1>(m, i, z[0], z[1]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t t = (uint32_t)(tid + FT * i + FH * h);
+                if (t < nv) {
+                    const uint32_t tau = t0 + t;
+                    const float inv = m.inv[t] * scale;
+                    const float ra = z[h].x * inv, rb = z[h].y * inv;
+                    const float aa = fabsf(ra), ab = fabsf(rb);
+                    track_max(aa, tau, best_a, arg_a);
+                    track_max(ab, tau, best_b, arg_b);
+                    pa = fmaf(ra, ra, pa);
+                    pb = fmaf(rb, rb, pb);
+                    if (aa >= thr_a || ab >= thr_b) {
+                        if (aa >= thr_a) push_tail(p, S.series_id, ka, tau, ra);
+                        if (ab >= thr_b) push_tail(p, S.series_id, kb, tau, rb);
+                    }
+                    if (S.rho) {
+                        S.rho[(size_t)la * S.L + tau] = ra;
+                        if (has_b) S.rho[(size_t)lb * S.L + tau] = rb;
+                    }
+                }
+            }
+        }
+        ss_a += (double)pa;
+        ss_b += (double)pb;
+        if (nj == 0) {
+            // last segment of this series: reduce and publish
             unsigned long long key_a = best_a >= 0.f ? pack_max(best_a, arg_a) : 0ull;
             unsigned long long key_b = best_b >= 0.f ? pack_max(best_b, arg_b) : 0ull;
 #pragma unroll
@@ -412,14 +471,22 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
                 }
             }
         }
+        __syncthreads();
+        if (np >= n_pairs) break;
+        new_pair = np != pair;
+        new_series = nj == 0;
+        pair = np;
+        s = ns;
+        j = nj;
     }
+    cp_async_wait<0>();
 }
 
 cudaError_t fft_attributes()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_corr_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_corr_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CORR_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fft_series, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
     if (e == cudaSuccess)
@@ -518,7 +585,7 @@ cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st)
     if (n_pairs == 0 || p.n_ser == 0) return cudaSuccess;
     const unsigned grid = std::min<unsigned>(n_pairs, (unsigned)n_sm);
     count_launches(1);
-    k_corr_fft<<<grid, FT, FFT_SMEM, st>>>(p);
+    k_corr_fft<<<grid, FT, CORR_SMEM, st>>>(p);
     return cudaGetLastError();
 }
 
