@@ -421,7 +421,7 @@ def run_cpu_sample(ctx, bf, w, xs_host, n_templates):
     # accuracy of the timed GPU path on the same sample
     bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16)
     acc = {}
-    for prec in ("split_bf16", "bf16"):
+    for prec in ("split_bf16", "bf16", "fft_fp32"):
         res = bf.bf_correlate(ctx, bank, [xs_host[0]], fs, bf.make_opts(precision=prec))
         got = bf.bf_result_copy_to_host(res, 0)
         bf.bf_result_destroy(res)
