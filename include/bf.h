@@ -281,6 +281,25 @@ typedef struct bf_skewnorm {
  * writing *out.  BF_EINVAL for a bad index or a NULL argument. */
 bf_status bf_result_fit_max(const bf_result* r, size_t s, void* stream, bf_skewnorm* out);
 
+/* Pseudo-spectra of tails of two detectors (Fig. 6: counts of rho > kappa
+ * sigma against frequency, for H1 and L1 independently and simultaneously,
+ * with frequency pairs within delta f = 50 Hz).  Series a and b of a result
+ * made with want_map are the two detectors over the same time block.  A map
+ * cell (t, c) is occupied when a tail of that series painted it (the tail
+ * threshold of opts.kappa and opts.tail_sigma).  For each frequency cell
+ * c = 0 .. map_nf - 1 (frequencies [c df, (c+1) df)):
+ *   indep_a[c] = number of time cells t with (t, c) occupied in a;
+ *   coinc_a[c] = number of those with an occupied cell (t', c') of b,
+ *                |t' - t| <= dt_cells and |c' - c| <= floor(delta_f_hz / df);
+ * and indep_b, coinc_b with a and b exchanged.  The maps are compared over
+ * their common time cells.  Averages over blocks are sums over calls divided
+ * by their number.  Host arrays of map_nf entries each (NULL to skip); runs
+ * on `stream` (NULL: the context stream) and synchronises it.  BF_EINVAL
+ * without maps, for a bad index or delta_f_hz < 0. */
+bf_status bf_result_coincidence(const bf_result* r, size_t a, size_t b, double delta_f_hz,
+                                uint32_t dt_cells, void* stream, uint32_t* indep_a,
+                                uint32_t* indep_b, uint32_t* coinc_a, uint32_t* coinc_b);
+
 /*
  * Predicted noise level of rho (Sect. 2.2 and Fig. 5 caption: sigma from
  * Parseval's theorem in a predictor step, before the search), kept when

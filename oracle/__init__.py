@@ -266,6 +266,36 @@ def skewnorm_fit(v: np.ndarray) -> dict:
     return dict(n=n, mean=m, sd=sd, skewness=g, xi=xi, omega=omega, alpha=alpha)
 
 
+def coincidence(map_a: np.ndarray, map_b: np.ndarray, df: float, delta_f_hz: float,
+                dt_cells: int = 0) -> dict:
+    """Pseudo-spectra of tails of two detectors (Fig. 6): per frequency cell
+    c of two time-frequency maps, the independent counts of time cells that
+    a tail painted, and the simultaneous counts of those that have a painted
+    cell of the other detector within dt_cells time cells and within
+    delta_f_hz (|c - c'| df <= delta_f_hz, i.e. floor(delta_f_hz / df)
+    cells).  The maps are cut to their common number of time cells.  Plain
+    loops over the painted cells."""
+    nt = min(map_a.shape[0], map_b.shape[0])
+    nf = map_a.shape[1]
+    oa = np.asarray(map_a[:nt]) > 0
+    ob = np.asarray(map_b[:nt]) > 0
+    w = int(np.floor(delta_f_hz / df + 1e-9))
+    out = {k: np.zeros(nf, np.int64) for k in ("indep_a", "indep_b", "coinc_a", "coinc_b")}
+
+    def any_in_window(o, t, c):
+        t0, t1 = max(t - dt_cells, 0), min(t + dt_cells, nt - 1)
+        c0, c1 = max(c - w, 0), min(c + w, nf - 1)
+        return bool(o[t0:t1 + 1, c0:c1 + 1].any())
+
+    for t, c in zip(*np.nonzero(oa)):
+        out["indep_a"][c] += 1
+        out["coinc_a"][c] += any_in_window(ob, t, c)
+    for t, c in zip(*np.nonzero(ob)):
+        out["indep_b"][c] += 1
+        out["coinc_b"][c] += any_in_window(oa, t, c)
+    return out
+
+
 def histogram(v: np.ndarray, nbins: int = 1024) -> np.ndarray:
     v = np.ascontiguousarray(v, np.float64)
     c = np.zeros(nbins, np.uint32)

@@ -136,6 +136,7 @@ def load() -> C.CDLL:
             "bf_result_copy_to_host": (i, [p, s, p, p, p, p, p]),
             "bf_result_copy_mean_max": (i, [p, p]),
             "bf_result_fit_max": (i, [p, s, p, P(bf_skewnorm)]),
+            "bf_result_coincidence": (i, [p, s, s, d, C.c_uint32, p, p, p, p, p]),
             "bf_result_tails": (i, [p, P(p), P(s)]),
             "bf_result_get_sigma_pred": (i, [p, s, P(p)]),
             "bf_result_copy_sigma_pred": (i, [p, s, p]),
@@ -356,6 +357,18 @@ def bf_result_fit_max(res: int, s: int = BF_FIT_MEAN, stream=None) -> dict:
     out = bf_skewnorm()
     _check(load().bf_result_fit_max(res, s, stream, C.byref(out)))
     return {name: getattr(out, name) for name, _ in bf_skewnorm._fields_}
+
+
+def bf_result_coincidence(res: int, a: int, b: int, delta_f_hz: float = 50.0, dt_cells: int = 0,
+                          stream=None) -> dict:
+    """Pseudo-spectra of tails of series a and b (independent and
+    simultaneous counts per frequency cell of the map)."""
+    nf = bf_result_map_shape(res, a)[1]
+    out = {k: np.zeros(nf, np.uint32) for k in ("indep_a", "indep_b", "coinc_a", "coinc_b")}
+    _check(load().bf_result_coincidence(res, a, b, float(delta_f_hz), int(dt_cells), stream,
+                                        *[out[k].ctypes.data for k in ("indep_a", "indep_b",
+                                                                        "coinc_a", "coinc_b")]))
+    return out
 
 
 TAIL_DTYPE = np.dtype([("series", np.uint32), ("k", np.uint32), ("tau", np.uint32),

@@ -1254,6 +1254,36 @@ bf_status bf_result_fit_max(const bf_result* r, size_t s, void* stream, bf_skewn
     return BF_OK;
 }
 
+bf_status bf_result_coincidence(const bf_result* r, size_t a, size_t b, double delta_f_hz,
+                                uint32_t dt_cells, void* stream, uint32_t* indep_a, uint32_t* indep_b,
+                                uint32_t* coinc_a, uint32_t* coinc_b)
+{
+    if (!r || a >= r->n_series || b >= r->n_series) { set_error("bad series index"); return BF_EINVAL; }
+    if (!r->map) { set_error("no maps (opts.want_map)"); return BF_EINVAL; }
+    if (!(delta_f_hz >= 0.0)) { set_error("delta_f_hz must be >= 0"); return BF_EINVAL; }
+    bf_ctx* ctx = r->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    const uint32_t nf = r->map_nf;
+    const uint32_t nt = std::min(r->map_nt[a], r->map_nt[b]);
+    const double wc = std::floor(delta_f_hz / r->df + 1e-9);
+    const uint32_t w = (uint32_t)std::min<double>(wc, (double)nf);
+    const uint32_t dt = std::min(dt_cells, nt);
+    unsigned int* d = static_cast<unsigned int*>(ctx->mem->alloc(4 * (size_t)nf * sizeof(unsigned int)));
+    if (!d) { set_error("out of device memory (coincidence)"); return BF_ENOMEM; }
+    std::vector<unsigned int> h(4 * (size_t)nf);
+    cudaError_t e = launch_coincidence(r->map + r->map_off[a], r->map + r->map_off[b], nt, nf, w, dt, d,
+                                       ctx->n_sm, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, h.size() * sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    ctx->mem->release(d);
+    if (e != cudaSuccess) return cuda_fail(e, "coincidence");
+    uint32_t* outs[4] = {indep_a, indep_b, coinc_a, coinc_b};
+    for (int q = 0; q < 4; ++q)
+        if (outs[q]) std::copy(h.begin() + (size_t)q * nf, h.begin() + (size_t)(q + 1) * nf, outs[q]);
+    return BF_OK;
+}
+
 bf_status bf_result_get_sigma_pred(const bf_result* r, size_t s, const float** sigma_pred)
 {
     if (!r || s >= r->n_series || !sigma_pred) { set_error("bad argument"); return BF_EINVAL; }

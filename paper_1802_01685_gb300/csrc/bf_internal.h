@@ -184,6 +184,8 @@ cudaError_t launch_finalize(const FinalizeParams& p, uint32_t K, uint32_t nbins,
 uint32_t fft_segments(uint32_t L, uint32_t M);
 cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, int n_sm, cudaStream_t st);
 cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st);
+cudaError_t launch_coincidence(const float* A, const float* B, uint32_t nt, uint32_t nf, uint32_t w,
+                               uint32_t dt, unsigned int* out, int n_sm, cudaStream_t s);
 cudaError_t launch_skewnorm_fit(const float* v, uint64_t n, double* acc, double* out, int n_sm,
                                 cudaStream_t s);
 cudaError_t launch_mean_max(const float* vmax, uint32_t n_series, uint32_t K, float* mean,

@@ -140,6 +140,57 @@ __global__ void k_skewnorm_close(const double* __restrict__ acc, uint64_t n, dou
     out[6] = delta / sqrt(1.0 - delta * delta);
 }
 
+// Pseudo-spectra of tails of two detectors (Fig. 6: counts of rho > kappa
+// sigma against frequency, independently and simultaneously in both
+// detectors with frequency pairs within delta f).  A cell (t, c) of a map is
+// occupied when a tail painted it (value > 0).  out = [4][nf]: independent
+// counts of a and b, then the counts of occupied cells of a (of b) that have
+// an occupied cell of the other map within dt time cells and w frequency
+// cells.  Tails are sparse, so the window is searched only at occupied cells.
+__device__ __forceinline__ bool any_occupied(const float* __restrict__ m, uint32_t nf, uint32_t t0,
+                                             uint32_t t1, uint32_t c0, uint32_t c1)
+{
+    for (uint32_t t = t0; t <= t1; ++t)
+        for (uint32_t c = c0; c <= c1; ++c)
+            if (m[(size_t)t * nf + c] > 0.f) return true;
+    return false;
+}
+
+__global__ void k_coincidence(const float* __restrict__ A, const float* __restrict__ B, uint32_t nt,
+                              uint32_t nf, uint32_t w, uint32_t dt, unsigned int* __restrict__ out)
+{
+    const uint64_t total = (uint64_t)nt * nf;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const bool oa = A[i] > 0.f, ob = B[i] > 0.f;
+        if (!oa && !ob) continue;
+        const uint32_t t = (uint32_t)(i / nf), c = (uint32_t)(i % nf);
+        const uint32_t t0 = t > dt ? t - dt : 0, t1 = min(t + dt, nt - 1);
+        const uint32_t c0 = c > w ? c - w : 0, c1 = min(c + w, nf - 1);
+        if (oa) {
+            atomicAdd(out + c, 1u);
+            if (any_occupied(B, nf, t0, t1, c0, c1)) atomicAdd(out + 2 * nf + c, 1u);
+        }
+        if (ob) {
+            atomicAdd(out + nf + c, 1u);
+            if (any_occupied(A, nf, t0, t1, c0, c1)) atomicAdd(out + 3 * nf + c, 1u);
+        }
+    }
+}
+
+// out: 4 nf counters, zeroed here
+cudaError_t launch_coincidence(const float* A, const float* B, uint32_t nt, uint32_t nf, uint32_t w,
+                               uint32_t dt, unsigned int* out, int n_sm, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, 4 * (size_t)nf * sizeof(unsigned int), s);
+    const uint64_t total = (uint64_t)nt * nf;
+    if (e != cudaSuccess || total == 0) return e;
+    const unsigned blocks = (unsigned)std::min<uint64_t>((total + 255) / 256, 8ull * n_sm);
+    count_launches(1);
+    k_coincidence<<<blocks, 256, 0, s>>>(A, B, nt, nf, w, dt, out);
+    return cudaGetLastError();
+}
+
 // acc: 3 doubles (zeroed here); out: 7 doubles, both device memory
 cudaError_t launch_skewnorm_fit(const float* v, uint64_t n, double* acc, double* out, int n_sm,
                                 cudaStream_t s)

@@ -525,3 +525,64 @@ def test_skewnorm_fit_clips_at_the_maximum_skewness():
     v = np.random.default_rng(4).exponential(1.0, 100_000)
     f = oracle.skewnorm_fit(v)
     assert f["skewness"] == pytest.approx(0.99527) and f["alpha"] > 20
+
+
+# ----------------------------------------------------------------- coincidence pseudo-spectra
+
+def _cells(nt, nf, cells):
+    m = np.zeros((nt, nf), np.float32)
+    for t, c in cells:
+        m[t, c] = 0.5
+    return m
+
+
+def test_coincidence_hand_worked_example():
+    """Counts worked out by hand: df = 4 Hz and delta_f = 8 Hz give a window
+    of two cells; with dt = 0 only equal time cells pair, with dt = 1 the
+    neighbouring rows too."""
+    a = _cells(6, 10, [(1, 2), (3, 5), (5, 9)])
+    b = _cells(6, 10, [(1, 4), (4, 7), (5, 6)])
+    r = oracle.coincidence(a, b, 4.0, 8.0, 0)
+    # a(1,2)-b(1,4): |2-4| = 2 <= 2 yes; a(3,5): row 3 of b empty; a(5,9)-b(5,6): 3 > 2 no
+    assert r["indep_a"].tolist() == [0, 0, 1, 0, 0, 1, 0, 0, 0, 1]
+    assert r["coinc_a"].tolist() == [0, 0, 1, 0, 0, 0, 0, 0, 0, 0]
+    assert r["coinc_b"].tolist() == [0, 0, 0, 0, 1, 0, 0, 0, 0, 0]
+    r = oracle.coincidence(a, b, 4.0, 8.0, 1)
+    # now a(3,5)-b(4,7): |5-7| = 2 yes; a(5,9)-b(4,7): |9-7| = 2 yes; b(5,6) pairs
+    # with neither a(5,9) (3 cells) nor a(3,5) (two rows away)
+    assert r["coinc_a"].tolist() == [0, 0, 1, 0, 0, 1, 0, 0, 0, 1]
+    assert r["coinc_b"].tolist() == [0, 0, 0, 0, 1, 0, 0, 1, 0, 0]
+    r = oracle.coincidence(a, b, 4.0, 7.99, 1)          # one cell of window
+    assert r["coinc_a"].sum() == 0 and r["coinc_b"].sum() == 0
+
+
+def test_coincidence_special_cases():
+    rng = np.random.default_rng(21)
+    a = (rng.random((200, 64)) < 0.03) * rng.random((200, 64))
+    b = (rng.random((200, 64)) < 0.03) * rng.random((200, 64))
+    # a map against itself: every painted cell is simultaneous with itself
+    r = oracle.coincidence(a, a, 4.0, 0.0, 0)
+    np.testing.assert_array_equal(r["coinc_a"], r["indep_a"])
+    np.testing.assert_array_equal(r["indep_a"], (a > 0).sum(axis=0))
+    # exchanging the detectors exchanges the outputs
+    r1, r2 = oracle.coincidence(a, b, 4.0, 50.0, 2), oracle.coincidence(b, a, 4.0, 50.0, 2)
+    for x, y in (("indep_a", "indep_b"), ("coinc_a", "coinc_b")):
+        np.testing.assert_array_equal(r1[x], r2[y])
+    # disjoint in time: no coincidences
+    a2, b2 = a.copy(), b.copy()
+    a2[100:] = 0
+    b2[:103] = 0
+    r = oracle.coincidence(a2, b2, 4.0, 1000.0, 2)
+    assert r["coinc_a"].sum() == 0 and r["coinc_b"].sum() == 0
+    # counts grow with the windows and are bounded by the independent counts
+    prev = None
+    for w in (0.0, 8.0, 40.0, 400.0):
+        r = oracle.coincidence(a, b, 4.0, w, 1)
+        assert np.all(r["coinc_a"] <= r["indep_a"])
+        if prev is not None:
+            assert np.all(r["coinc_a"] >= prev)
+        prev = r["coinc_a"]
+    # an infinite window pairs every painted cell of a with any painted cell of b in reach in time
+    r = oracle.coincidence(a, b, 4.0, 1e9, 0)
+    rows_b = (b > 0).any(axis=1)
+    np.testing.assert_array_equal(r["coinc_a"], ((a > 0) & rows_b[:, None]).sum(axis=0))
