@@ -9,7 +9,8 @@ stage of the path: template synthesis, the two controls, series preparation
 (split rows, FP64 prefix norms), the batched split-BF16 tensor-core correlation
 of all four series in one launch, the fused epilogue (max/argmax, sigma,
 tails), finalize (histogram of maxima, time-frequency map painting) and the
-skew-normal fits of the maxima of data and controls -- all through the C ABI.
+skew-normal fits of the maxima and the two-detector coincidence pseudo-spectra
+of data and controls -- all through the C ABI.
 
 metric: lag-correlations per second (one normalised length-M inner product of
 one template at one lag), whole job.  Printed as one JSON line by rank 0.
@@ -187,6 +188,7 @@ def run_ours(args, rank, world, local):
     stage_ms = {}
     shapes = set()
     fits = {}
+    coincidences = {}
 
     def step(record=False):
         t0 = time.perf_counter()
@@ -198,11 +200,15 @@ def run_ours(args, rank, world, local):
         res = bf.bf_correlate(ctx, bank, xs + ctrl, fs, opts)
         # skew-normal fits of the maxima: data (series 0, 1) vs controls (2, 3)
         fit = [bf.bf_result_fit_max(res, s) for s in range(4)]
+        # two-detector pseudo-spectra: data pair (0, 1) and control pair (2, 3)
+        coinc = [bf.bf_result_coincidence(res, a, b, 50.0, 0) for a, b in ((0, 1), (2, 3))]
         t3 = time.perf_counter()
         info = bf.bf_result_info_get(res)
         if record:
             fits.update({name: {k: round(fit[i][k], 6) for k in ("xi", "omega", "alpha")}
                          for i, name in enumerate(("data_0", "data_1", "control_0", "control_1"))})
+            coincidences.update({name: {k: int(v.sum()) for k, v in c.items()}
+                                 for name, c in zip(("data", "control"), coinc)})
             kernel_ms.append(info.kernel_ms)
             shapes.add(info.tile_lags)
             for k, v in (("bank_synthesis", t1 - t0), ("controls", t2 - t1), ("correlate", t3 - t2)):
@@ -294,11 +300,13 @@ def run_ours(args, rank, world, local):
                    "l2": "inputs larger than L2 (split bank 1.07 GB re-synthesised every step)",
                    "stages_in_step": ["bank_synthesis", "controls", "series_prep",
                                       "correlation+epilogue", "finalize+hist+map",
-                                      "skew-normal fit of maxima"]},
+                                      "skew-normal fit of maxima",
+                                      "coincidence pseudo-spectra (delta f 50 Hz)"]},
         "stage_ms": {k: round(float(np.mean(v)), 2) for k, v in stage_ms.items()},
         "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
         "fp32_path": fp32, "fft_path": fft, "accuracy_vs_oracle": accuracy, "cpu_baseline": cpu, "serve": serve,
         "maxima_fit": fits,
+        "coincidence_counts": coincidences,
     }
 
 
