@@ -65,12 +65,14 @@ def _load():
         lib.oracle_check_chirp.argtypes = [i, i, d, d, d, d, l]
         lib.oracle_template.restype = i
         lib.oracle_template.argtypes = [i, i, d, d, d, d, l, p]
+        lib.oracle_template_phase.restype = i
+        lib.oracle_template_phase.argtypes = [i, i, d, d, d, d, l, i, p]
         lib.oracle_grid.restype = l
         lib.oracle_grid.argtypes = [p, l, p, l, p, l, d, d, l, l, p, p, p, p, p]
         lib.oracle_correlate_raw.restype = None
         lib.oracle_correlate_raw.argtypes = [p, l, p, l, p, p]
         lib.oracle_search.restype = i
-        lib.oracle_search.argtypes = [p, l, d, p, p, p, p, p, l, l, d, p, d, d, l, l,
+        lib.oracle_search.argtypes = [p, l, d, p, p, p, p, p, l, l, i, d, p, d, d, l, l,
                                       p, p, p, p, p]
         lib.oracle_histogram.restype = None
         lib.oracle_histogram.argtypes = [p, l, l, p]
@@ -116,9 +118,10 @@ def check_chirp(track, sense, f_lo, f_hi, D, fs, M) -> bool:
     return _load().oracle_check_chirp(track, sense, f_lo, f_hi, D, fs, M) == 0
 
 
-def template(track, sense, f_lo, f_hi, D, fs, M) -> np.ndarray:
+def template(track, sense, f_lo, f_hi, D, fs, M, phase: int = 0) -> np.ndarray:
+    """Unit-norm template; phase 1 is the quadrature (sine-phase) partner."""
     h = np.zeros(M, np.float64)
-    if _load().oracle_template(track, sense, f_lo, f_hi, D, fs, M, _ptr(h)):
+    if _load().oracle_template_phase(track, sense, f_lo, f_hi, D, fs, M, int(phase), _ptr(h)):
         raise ValueError("invalid chirp parameters")
     return h
 
@@ -137,14 +140,14 @@ def grid(tracks, senses, durations, f_min, f_max, I, J) -> dict:
     return out
 
 
-def bank(params: dict, fs: float, M: int) -> np.ndarray:
-    """[K, M] FP64 templates in bank order."""
+def bank(params: dict, fs: float, M: int, phase: int = 0) -> np.ndarray:
+    """[K, M] FP64 templates in bank order (phase 1: their quadrature partners)."""
     K = len(params["track"])
     H = np.zeros((K, M), np.float64)
     for k in range(K):
         H[k] = template(int(params["track"][k]), int(params["sense"][k]),
                         float(params["f_lo"][k]), float(params["f_hi"][k]),
-                        float(params["D"][k]), fs, M)
+                        float(params["D"][k]), fs, M, phase)
     return H
 
 
@@ -169,16 +172,19 @@ def map_shape(N: int, fs: float, dt: float, df: float):
 
 def search(x: np.ndarray, fs: float, params: dict, M: int, *, kappa: float = 5.0,
            thr: float | None = None, thr_k: np.ndarray | None = None, dt: float = 1e-3,
-           df: float = 4.0, want_rho: bool = False, want_map: bool = False) -> dict:
+           df: float = 4.0, want_rho: bool = False, want_map: bool = False,
+           quadrature: bool = False) -> dict:
     """Full oracle search of one series against the bank given by ``params``.
-    The map is painted by tails |rho| >= thr (default kappa / sqrt(M)), or
-    >= thr_k[k] per template when thr_k is given."""
+    The map is painted by tails |rho| >= thr (default kappa / sqrt(M), or
+    kappa sqrt(2 / M) for quadrature output), or >= thr_k[k] per template
+    when thr_k is given.  With ``quadrature`` the output of template k is
+    sqrt(rho_cos^2 + rho_sin^2), rho_sin from its sine-phase partner."""
     x = np.ascontiguousarray(x, np.float32)
     N = len(x)
     K = len(params["track"])
     L = N - M + 1
     if thr is None:
-        thr = kappa / np.sqrt(M)
+        thr = kappa * np.sqrt((2.0 if quadrature else 1.0) / M)
     tr = np.ascontiguousarray(params["track"], np.int32)
     se = np.ascontiguousarray(params["sense"], np.int32)
     fl = np.ascontiguousarray(params["f_lo"], np.float64)
@@ -192,7 +198,8 @@ def search(x: np.ndarray, fs: float, params: dict, M: int, *, kappa: float = 5.0
     mp = np.zeros((nt, nf)) if want_map else None
     tk = np.ascontiguousarray(thr_k, np.float64) if thr_k is not None else None
     rc = _load().oracle_search(_ptr(x), N, fs, _ptr(tr), _ptr(se), _ptr(fl), _ptr(fh),
-                               _ptr(Dd), K, M, float(thr), _ptr(tk), dt, df, nt, nf, _ptr(rho),
+                               _ptr(Dd), K, M, int(bool(quadrature)), float(thr), _ptr(tk), dt, df,
+                               nt, nf, _ptr(rho),
                                _ptr(vmax), _ptr(arg), _ptr(sig), _ptr(mp))
     if rc:
         raise ValueError("oracle_search: invalid input")

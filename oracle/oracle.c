@@ -100,9 +100,16 @@ int oracle_check_chirp(int track, int sense, double f_lo, double f_hi, double D,
  *   descending: g[M - 1 - m] (the time reverse),
  *   both ("butterfly"): g[m] + g[M - 1 - m], the superposition of the two,
  *   h = the chosen g / sqrt(sum g^2)   (unit L2 norm).
+ * The quadrature partner (phase = 1) is the Hilbert transform of the
+ * template, for the phase-insensitive output sqrt(rho_cos^2 + rho_sin^2):
+ * g_s takes sin(2 pi c(t)) in place of the cosine, and a time-reversed part
+ * enters with a minus sign (reversal negates the Hilbert transform), so
+ *   ascending g_s[m], descending -g_s[M - 1 - m],
+ *   both g_s[m] - g_s[M - 1 - m],
+ * each at unit norm.
  */
-int oracle_template(int track, int sense, double f_lo, double f_hi, double D,
-                    double fs, long M, double *h)
+int oracle_template_phase(int track, int sense, double f_lo, double f_hi, double D,
+                          double fs, long M, int phase, double *h)
 {
     if (oracle_check_chirp(track, sense, f_lo, f_hi, D, fs, M)) return -1;
     long MD = oracle_support_len(D, fs);
@@ -112,13 +119,19 @@ int oracle_template(int track, int sense, double f_lo, double f_hi, double D,
         double t = (double)j / fs;
         double s = sin(O_PI * ((double)j + 0.5) / (double)MD);
         double c = oracle_cycles(track, f_lo, f_hi, D, t);
-        h[ms + j] = s * s * cos(2.0 * O_PI * c);
+        h[ms + j] = s * s * (phase ? sin(2.0 * O_PI * c) : cos(2.0 * O_PI * c));
     }
     if (sense == O_BOTH) {
         for (long a = 0, b = M - 1; a <= b; ++a, --b) {
-            double s = h[a] + h[b];
-            h[a] = s;
-            h[b] = s;
+            if (phase) {
+                double d = h[a] - h[b];
+                h[a] = d;
+                h[b] = -d;
+            } else {
+                double s = h[a] + h[b];
+                h[a] = s;
+                h[b] = s;
+            }
         }
     }
     double e = 0.0;
@@ -131,8 +144,16 @@ int oracle_template(int track, int sense, double f_lo, double f_hi, double D,
             h[a] = h[b];
             h[b] = tmp;
         }
+        if (phase)
+            for (long m = 0; m < M; ++m) h[m] = -h[m];
     }
     return 0;
+}
+
+int oracle_template(int track, int sense, double f_lo, double f_hi, double D,
+                    double fs, long M, double *h)
+{
+    return oracle_template_phase(track, sense, f_lo, f_hi, D, fs, M, 0, h);
 }
 
 /*
@@ -254,7 +275,7 @@ static void paint_track(double *map, long nt, long nf, double dt, double df,
 
 int oracle_search(const float *x, long N, double fs, const int *track,
                   const int *sense, const double *f_lo, const double *f_hi,
-                  const double *D, long K, long M, double thr, const double *thr_k,
+                  const double *D, long K, long M, int quad, double thr, const double *thr_k,
                   double dt, double df, long nt, long nf, double *rho, double *vmax,
                   long *argmax, double *sigma, double *map)
 {
@@ -278,14 +299,17 @@ int oracle_search(const float *x, long N, double fs, const int *track,
 #pragma omp parallel
     {
         double *h = (double *)malloc(sizeof(double) * (size_t)M);
-        if (!h) {
+        double *hs = (double *)malloc(sizeof(double) * (size_t)M);
+        if (!h || !hs) {
 #pragma omp atomic write
             failed = 1;
         }
 #pragma omp for schedule(dynamic, 1)
         for (long k = 0; k < K; ++k) {
-            if (!h) continue;
-            oracle_template(track[k], sense[k], f_lo[k], f_hi[k], D[k], fs, M, h);
+            if (!h || !hs) continue;
+            oracle_template_phase(track[k], sense[k], f_lo[k], f_hi[k], D[k], fs, M, 0, h);
+            if (quad)
+                oracle_template_phase(track[k], sense[k], f_lo[k], f_hi[k], D[k], fs, M, 1, hs);
             double best = -1.0, ss = 0.0;
             long best_tau = 0;
             const double thr_here = thr_k ? thr_k[k] : thr;   /* per-template tails */
@@ -293,6 +317,13 @@ int oracle_search(const float *x, long N, double fs, const int *track,
                 double s = 0.0;
                 for (long m = 0; m < M; ++m) s += (double)x[tau + m] * h[m];
                 double r = energy[tau] > 0.0 ? s / sqrt(energy[tau]) : 0.0;
+                if (quad) {
+                    /* quadrature: the magnitude of (rho_cos, rho_sin) */
+                    double q = 0.0;
+                    for (long m = 0; m < M; ++m) q += (double)x[tau + m] * hs[m];
+                    double rs = energy[tau] > 0.0 ? q / sqrt(energy[tau]) : 0.0;
+                    r = sqrt(r * r + rs * rs);
+                }
                 if (rho) rho[k * L + tau] = r;
                 double a = fabs(r);
                 if (a > best) {   /* strict: the smallest lag wins ties */
@@ -311,6 +342,7 @@ int oracle_search(const float *x, long N, double fs, const int *track,
             if (sigma) sigma[k] = sqrt(ss / (double)L);
         }
         free(h);
+        free(hs);
     }
     free(energy);
     return failed ? -1 : 0;

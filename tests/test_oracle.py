@@ -586,3 +586,66 @@ def test_coincidence_special_cases():
     r = oracle.coincidence(a, b, 4.0, 1e9, 0)
     rows_b = (b > 0).any(axis=1)
     np.testing.assert_array_equal(r["coinc_a"], ((a > 0) & rows_b[:, None]).sum(axis=0))
+
+
+# ----------------------------------------------------------------- quadrature templates
+
+def test_quadrature_partner_is_the_hilbert_transform():
+    """The quadrature partner of a chirp well inside the band is the Hilbert
+    transform of the template (the imaginary part of its analytic signal),
+    up to the taper's edge effects, for either sense and for the
+    superposition of both."""
+    fs, M = 2048.0, 2048
+    for track, sense, f0, f1, D in ((0, 0, 100.0, 600.0, 1.0), (1, 1, 80.0, 500.0, 0.8),
+                                    (0, 2, 200.0, 300.0, 0.9)):
+        hc = oracle.template(track, sense, f0, f1, D, fs, M, 0)
+        hs = oracle.template(track, sense, f0, f1, D, fs, M, 1)
+        hh = scipy.signal.hilbert(hc).imag
+        c = np.dot(hh, hs) / np.linalg.norm(hh) / np.linalg.norm(hs)
+        assert c > 0.999, (track, sense, c)
+        assert abs(np.linalg.norm(hs) - 1.0) < 1e-12
+        assert abs(np.dot(hc, hs)) < 0.02                       # nearly orthogonal
+    # the superposition's pair is exactly orthogonal: symmetric against antisymmetric
+    hc = oracle.template(0, 2, 200.0, 300.0, 0.9, fs, M, 0)
+    hs = oracle.template(0, 2, 200.0, 300.0, 0.9, fs, M, 1)
+    np.testing.assert_allclose(hs, -hs[::-1], atol=1e-15)
+    assert abs(np.dot(hc, hs)) < 1e-12
+
+
+def test_quadrature_output_is_phase_blind():
+    """A noise-free signal cos(phi) h_c + sin(phi) h_s at a known offset gives
+    a quadrature output of 1 there for every phase, up to the overlap
+    eps = <h_c, h_s> of the pair; the cosine-only output follows cos(phi)."""
+    fs, M = 1024.0, 1024
+    p = dict(track=np.array([1], np.int32), sense=np.array([0], np.int32),
+             f_lo=np.array([60.0]), f_hi=np.array([300.0]), D=np.array([0.9]))
+    hc = oracle.template(1, 0, 60.0, 300.0, 0.9, fs, M, 0)
+    hs = oracle.template(1, 0, 60.0, 300.0, 0.9, fs, M, 1)
+    eps = abs(np.dot(hc, hs))
+    for phi in (0.0, 0.4, np.pi / 2, 2.5):
+        x = np.zeros(3000, np.float64)
+        x[700:700 + M] = np.cos(phi) * hc + np.sin(phi) * hs
+        x = x.astype(np.float32)
+        q = oracle.search(x, fs, p, M, want_rho=True, quadrature=True)
+        c = oracle.search(x, fs, p, M, want_rho=True)
+        assert abs(q["rho"][0, 700] - 1.0) <= 2 * eps + 1e-6, (phi, q["rho"][0, 700])
+        assert abs(c["rho"][0, 700] - np.cos(phi)) <= 2 * eps + 1e-6
+        assert np.all(q["rho"][0] >= np.abs(c["rho"][0]) - 1e-12)
+        assert q["argmax"][0] == 700
+
+
+def test_quadrature_white_noise_second_moment():
+    """For iid Gaussian windows E rho_cos^2 = E rho_sin^2 = 1/M exactly, so
+    the mean of the quadrature output squared is 2/M."""
+    rng = np.random.default_rng(17)
+    fs, M = 512.0, 512
+    spec = {"tracks": [0, 1], "senses": [0, 1], "durations": [0.9], "f_min": 20.0,
+            "f_max": 250.0, "I": 3, "J": 3}
+    p = oracle.grid(spec["tracks"], spec["senses"], spec["durations"], spec["f_min"],
+                    spec["f_max"], spec["I"], spec["J"])
+    x = rng.standard_normal(40000).astype(np.float32)
+    q = oracle.search(x, fs, p, M, quadrature=True)
+    m2 = np.mean(q["sigma"] ** 2)
+    # 36 templates x 39489 correlated lags: a few % statistical spread
+    assert abs(m2 * M / 2.0 - 1.0) < 0.05, m2 * M / 2
+    assert q["thr"] == pytest.approx(5.0 * np.sqrt(2.0 / M))
