@@ -87,12 +87,25 @@ typedef enum {
 enum {
     BF_BANK_FP32 = 1,          /* needed by BF_FP32                            */
     BF_BANK_SPLIT_BF16 = 2,    /* needed by BF_BF16 and BF_SPLIT_BF16          */
-    BF_BANK_GENERATED = 4      /* keep only the chirp parameters: every
+    BF_BANK_GENERATED = 4,     /* keep only the chirp parameters: every
                                   bf_correlate synthesises the templates it
                                   needs on the fly, chunk by chunk, into a
                                   small ring that stays in L2 while the
                                   correlation consumes it.  Exclusive of the
-                                  other flags; serves every precision.        */
+                                  other layout flags; serves every precision. */
+    BF_BANK_QUADRATURE = 8     /* with any of the above: every chirp also gets
+                                  its quadrature partner, the Hilbert
+                                  transform of the template (sin(2 pi c(t))
+                                  in place of the cosine, time-reversed parts
+                                  negated: descending -g_s[M-1-m], both
+                                  senses g_s[m] - g_s[M-1-m]), at unit norm.
+                                  The output of chirp k is then the phase-blind
+                                  sqrt(rho_cos^2 + rho_sin^2) >= 0 (max, argmax,
+                                  sigma = its rms, tails, maps), the white-
+                                  noise tail threshold kappa sqrt(2/M), and a
+                                  Parseval sigma the root of the pair's summed
+                                  squares.  Every precision.  A quadrature
+                                  output counts as two correlations.           */
 };
 
 /*
@@ -169,8 +182,11 @@ bf_status bf_bank_create_grid(bf_ctx* ctx, const bf_chirp_grid* grid, double fs,
 void bf_bank_destroy(bf_bank* bank);
 size_t bf_bank_size(const bf_bank* bank);           /* K */
 size_t bf_bank_template_len(const bf_bank* bank);   /* M */
-/* Copies templates [k0, k0+n) as float32 (row-major [n][M]) to host memory.
- * Reads the FP32 layout if kept, else hi + lo of the split layout. */
+size_t bf_bank_rows(const bf_bank* bank);   /* template rows: K, or 2K with BF_BANK_QUADRATURE */
+/* Copies templates [k0, k0+n) as float32 (row-major [n][M]) to host memory;
+ * for a quadrature bank each chirp gives two rows, template then partner
+ * ([2n][M]).  Reads the FP32 layout if kept, else hi + lo of the split
+ * layout, else synthesises the rows. */
 bf_status bf_bank_read(const bf_bank* bank, size_t k0, size_t n, float* host_out);
 /* Copies the chirp parameters of templates [k0, k0+n) to host memory. */
 bf_status bf_bank_params(const bf_bank* bank, size_t k0, size_t n, bf_chirp* host_out);

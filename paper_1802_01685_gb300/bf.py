@@ -24,7 +24,7 @@ BF_OK, BF_EINVAL, BF_ENOMEM, BF_ECUDA, BF_ETIMEDOUT, BF_EPENDING, BF_EAGAIN, \
 BF_LINEAR, BF_POWERLAW = 0, 1
 BF_ASC, BF_DESC, BF_BOTH = 0, 1, 2
 BF_FP32, BF_BF16, BF_SPLIT_BF16, BF_FFT_FP32 = 0, 1, 2, 3
-BF_BANK_FP32, BF_BANK_SPLIT_BF16, BF_BANK_GENERATED = 1, 2, 4
+BF_BANK_FP32, BF_BANK_SPLIT_BF16, BF_BANK_GENERATED, BF_BANK_QUADRATURE = 1, 2, 4, 8
 BF_SIGMA_WHITE, BF_SIGMA_PARSEVAL = 0, 1
 
 PRECISIONS = {"fp32": BF_FP32, "bf16": BF_BF16, "split_bf16": BF_SPLIT_BF16, "fft_fp32": BF_FFT_FP32}
@@ -123,6 +123,7 @@ def load() -> C.CDLL:
             "bf_bank_destroy": (None, [p]),
             "bf_bank_size": (s, [p]),
             "bf_bank_template_len": (s, [p]),
+            "bf_bank_rows": (s, [p]),
             "bf_bank_read": (i, [p, s, s, p]),
             "bf_bank_params": (i, [p, s, s, P(bf_chirp)]),
             "bf_opts_default": (None, [P(bf_opts)]),
@@ -233,9 +234,16 @@ def bf_bank_template_len(bank: int) -> int:
     return int(load().bf_bank_template_len(bank))
 
 
+def bf_bank_rows(bank: int) -> int:
+    return int(load().bf_bank_rows(bank))
+
+
 def bf_bank_read(bank: int, k0: int, n: int) -> np.ndarray:
+    """Templates [k0, k0+n); two rows per chirp (template, partner) for a
+    quadrature bank."""
     M = bf_bank_template_len(bank)
-    out = np.zeros((n, M), np.float32)
+    per = bf_bank_rows(bank) // bf_bank_size(bank)
+    out = np.zeros((per * n, M), np.float32)
     _check(load().bf_bank_read(bank, k0, n, out.ctypes.data))
     return out
 

@@ -250,8 +250,9 @@ Seg make_segment(const PreparedSeries& ps, uint32_t series_id, const bf_bank* ba
     g.n_lag_tiles = (uint32_t)ceil_div(ps.L, tile_lags(precision));
     g.tt0 = tt_first;
     g.n_tt = tt_count;
-    g.k_begin = (uint32_t)k_begin;
-    g.k_end = (uint32_t)k_end;
+    g.k_begin = (uint32_t)bank_row(bank, k_begin);
+    g.k_end = (uint32_t)bank_row(bank, k_end);
+    g.quad = bank->quad ? 1u : 0u;
     g.M_pad = bank->M_pad;
     g.series_id = series_id;
     return g;
@@ -264,8 +265,8 @@ void build_segments(const std::vector<PreparedSeries*>& ser, const std::vector<u
                            std::vector<Seg>& segs)
 {
     const uint32_t tile_t = tile_templates(precision);
-    const uint32_t tt0 = (uint32_t)(k_begin / tile_t);
-    const uint32_t ntt = (uint32_t)(ceil_div(k_end, tile_t) - tt0);
+    const uint32_t tt0 = (uint32_t)(bank_row(bank, k_begin) / tile_t);
+    const uint32_t ntt = (uint32_t)(ceil_div(bank_row(bank, k_end), tile_t) - tt0);
     for (size_t i = 0; i < ser.size(); ++i)
         segs.push_back(make_segment(*ser[i], ids[i], bank, k_begin, k_end, tt0, ntt, precision,
                                     packed + (size_t)ids[i] * K, sumsq + (size_t)ids[i] * K));
@@ -466,7 +467,8 @@ bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
     r->parseval = o.tail_sigma == BF_SIGMA_PARSEVAL;
     r->kappa = (float)o.kappa;
     r->lengths = lengths;
-    r->thr = (float)(o.kappa / std::sqrt((double)bank->M));
+    // the white-noise rms of the output: 1/sqrt(M), or sqrt(2/M) for quadrature pairs
+    r->thr = (float)(o.kappa * std::sqrt((bank->quad ? 2.0 : 1.0) / (double)bank->M));
     Allocator& mem = *ctx->mem;
     const size_t S = r->n_series, K = r->K;
     r->packed = static_cast<unsigned long long*>(mem.alloc(S * K * 8));
@@ -588,8 +590,8 @@ cudaError_t correlate_generated(bf_ctx* ctx, const bf_bank* bank, const bf_opts&
     const bool tc = o.precision != BF_FP32;
     const size_t tile_bytes = (size_t)TC_TILE_T * bank->M_pad * 4;     // hi+lo, or FP32
     const size_t chunk_tiles = std::max<size_t>(1, GEN_SLOT_BYTES / tile_bytes);
-    const size_t t_begin = o.bank_begin / TC_TILE_T;
-    const size_t t_end = ceil_div(o.bank_end, TC_TILE_T);
+    const size_t t_begin = bank_row(bank, o.bank_begin) / TC_TILE_T;
+    const size_t t_end = ceil_div(bank_row(bank, o.bank_end), TC_TILE_T);
     const size_t n_chunks = ceil_div(t_end - t_begin, chunk_tiles);
     const size_t slot_elems = std::min(chunk_tiles, t_end - t_begin) * TC_TILE_T * bank->M_pad;
     Allocator& mem = *ctx->mem;
@@ -617,10 +619,11 @@ cudaError_t correlate_generated(bf_ctx* ctx, const bf_bank* bank, const bf_opts&
         const size_t t0 = t_begin + c * chunk_tiles;
         const size_t t1 = std::min(t0 + chunk_tiles, t_end);
         const size_t k0 = t0 * TC_TILE_T;
-        const size_t kc = std::min(t1 * TC_TILE_T, bank->K) - k0;
+        const size_t kc = std::min(t1 * TC_TILE_T, bank->rows) - k0;
         if (c >= 2) e = cudaStreamWaitEvent(ctx->aux, corr_done[sl], 0);
         if (e == cudaSuccess)
-            e = launch_bank_synth(bank->d_params + k0, (uint32_t)kc, (uint32_t)((t1 - t0) * TC_TILE_T),
+            e = launch_bank_synth(bank->d_params, (uint32_t)k0, bank->quad, (uint32_t)kc,
+                                  (uint32_t)((t1 - t0) * TC_TILE_T),
                                   bank->M, bank->M_pad, bank->fs,
                                   tc ? nullptr : static_cast<float*>(slot[sl][0]),
                                   tc ? static_cast<uint8_t*>(slot[sl][0]) : nullptr,
@@ -630,8 +633,8 @@ cudaError_t correlate_generated(bf_ctx* ctx, const bf_bank* bank, const bf_opts&
         if (e != cudaSuccess) break;
         // the call's segments restricted to this chunk's template tiles
         const uint32_t tile_t = tile_templates(o.precision);
-        const size_t q0 = std::max(k0, (size_t)o.bank_begin) / tile_t;
-        const size_t q1 = ceil_div(std::min(t1 * TC_TILE_T, (size_t)o.bank_end), tile_t);
+        const size_t q0 = std::max(k0, bank_row(bank, o.bank_begin)) / tile_t;
+        const size_t q1 = ceil_div(std::min(t1 * TC_TILE_T, bank_row(bank, o.bank_end)), tile_t);
         std::vector<Seg> cs = segs;
         for (Seg& g : cs) {
             g.tt0 = (uint32_t)q0;
@@ -790,10 +793,13 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
     *out = nullptr;
     if (K == 0 || K > 0x7FFFFF00u) { set_error("bank size %zu outside [1, 2^31)", K); return BF_EINVAL; }
     if (!(fs > 0.0) || !(T > 0.0)) { set_error("need fs > 0 and T > 0"); return BF_EINVAL; }
-    const bool generated = storage == BF_BANK_GENERATED;
-    if (!generated && ((storage & (BF_BANK_FP32 | BF_BANK_SPLIT_BF16)) == 0 || (storage & ~3u))) {
+    const bool quad = (storage & BF_BANK_QUADRATURE) != 0;
+    const unsigned layout = storage & ~(unsigned)BF_BANK_QUADRATURE;
+    const bool generated = layout == BF_BANK_GENERATED;
+    if (!generated && ((layout & (BF_BANK_FP32 | BF_BANK_SPLIT_BF16)) == 0 || (layout & ~3u))) {
         set_error("storage mask %u must be BF_BANK_GENERATED alone, or select BF_BANK_FP32 "
-                  "and/or BF_BANK_SPLIT_BF16", storage);
+                  "and/or BF_BANK_SPLIT_BF16 (either way optionally with BF_BANK_QUADRATURE)",
+                  storage);
         return BF_EINVAL;
     }
     const uint32_t M = template_len(T, fs);
@@ -811,7 +817,9 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
     std::unique_ptr<bf_bank> b(new bf_bank());
     b->ctx = ctx;
     b->K = K;
-    b->K_pad = ceil_div(K, K_ALIGN) * K_ALIGN;
+    b->quad = quad;
+    b->rows = quad ? 2 * K : K;
+    b->K_pad = ceil_div(b->rows, K_ALIGN) * K_ALIGN;
     b->M = M;
     b->M_pad = (uint32_t)(ceil_div(M, M_ALIGN) * M_ALIGN);
     b->fs = fs;
@@ -840,8 +848,8 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
     cudaError_t e = cudaMemcpyAsync(b->d_params, dev.data(), K * sizeof(ChirpDev),
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !generated)
-        e = launch_bank_synth(b->d_params, (uint32_t)K, (uint32_t)b->K_pad, M, b->M_pad, fs, b->f32,
-                              b->hi, b->lo, st);
+        e = launch_bank_synth(b->d_params, 0, quad, (uint32_t)b->rows, (uint32_t)b->K_pad, M, b->M_pad, fs,
+                              b->f32, b->hi, b->lo, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         bf_bank_destroy(b.release());
@@ -893,6 +901,7 @@ void bf_bank_destroy(bf_bank* b)
 }
 
 size_t bf_bank_size(const bf_bank* b) { return b ? b->K : 0; }
+size_t bf_bank_rows(const bf_bank* b) { return b ? b->rows : 0; }
 size_t bf_bank_template_len(const bf_bank* b) { return b ? b->M : 0; }
 
 bf_status bf_bank_params(const bf_bank* b, size_t k0, size_t n, bf_chirp* out)
@@ -902,18 +911,19 @@ bf_status bf_bank_params(const bf_bank* b, size_t k0, size_t n, bf_chirp* out)
     return BF_OK;
 }
 
-bf_status bf_bank_read(const bf_bank* b, size_t k0, size_t n, float* out)
+bf_status bf_bank_read(const bf_bank* b, size_t c0, size_t nc, float* out)
 {
-    if (!b || !out || k0 + n > b->K) { set_error("bad bank range"); return BF_EINVAL; }
+    if (!b || !out || c0 + nc > b->K) { set_error("bad bank range"); return BF_EINVAL; }
     cudaSetDevice(b->ctx->device);
+    const size_t k0 = bank_row(b, c0), n = bank_row(b, c0 + nc) - k0;     // rows
     if (b->generated) {
         // synthesise the range into a scratch FP32 block and copy it out
         const size_t n_pad = ceil_div(n, K_ALIGN) * K_ALIGN;
         float* tmp = static_cast<float*>(b->ctx->mem->alloc(n_pad * b->M_pad * sizeof(float)));
         if (!tmp) { set_error("out of device memory reading a generated bank"); return BF_ENOMEM; }
         std::lock_guard<std::mutex> g(b->ctx->launch_mu);
-        cudaError_t e = launch_bank_synth(b->d_params + k0, (uint32_t)n, (uint32_t)n_pad, b->M, b->M_pad,
-                                          b->fs, tmp, nullptr, nullptr, b->ctx->stream);
+        cudaError_t e = launch_bank_synth(b->d_params, (uint32_t)k0, b->quad, (uint32_t)n, (uint32_t)n_pad,
+                                          b->M, b->M_pad, b->fs, tmp, nullptr, nullptr, b->ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->ctx->stream);
         if (e == cudaSuccess)
             e = cudaMemcpy2D(out, b->M * sizeof(float), tmp, b->M_pad * sizeof(float),
@@ -999,8 +1009,9 @@ cudaError_t correlate_fft(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
         b.tw = tw;
         p.hspec = bank->fspec;
         p.tw = tw;
-        p.k_begin = (uint32_t)o.bank_begin;
-        p.k_end = (uint32_t)o.bank_end;
+        p.k_begin = (uint32_t)bank_row(bank, o.bank_begin);
+        p.k_end = (uint32_t)bank_row(bank, o.bank_end);
+        p.quad = bank->quad ? 1 : 0;
         p.V = V;
         p.n_ser = n;
         p.thr = r->thr;
@@ -1063,7 +1074,7 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
         prep[s].owned.clear();
         pptr.push_back(&prep[s]);
         ids.push_back((uint32_t)s);
-        r->correlations += (double)prep[s].L * (double)r->K;
+        r->correlations += (double)prep[s].L * (double)r->K * (bank->quad ? 2.0 : 1.0);
     }
     const bool fft = o.precision == BF_FFT_FP32;
     std::vector<Seg> segs;

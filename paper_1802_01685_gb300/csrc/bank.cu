@@ -57,8 +57,14 @@ __device__ __forceinline__ size_t tc_offset(uint32_t k, uint32_t m, uint32_t n_k
            (r & 7) * 16 + (c & 7) * 2;
 }
 
+// Row k of the output is bank row row0 + k.  In a quadrature bank row r is
+// chirp r / 2, and odd rows hold the quadrature partner: the Hilbert
+// transform of the template, i.e. sin(2 pi c(t)) in place of the cosine with
+// time-reversed parts negated (ascending g_s[m], descending -g_s[M-1-m], both
+// g_s[m] - g_s[M-1-m]), at unit norm of its own.
 __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__ params,
-                                                    uint32_t K, uint32_t M, uint32_t M_pad,
+                                                    uint32_t row0, int quad, uint32_t K,
+                                                    uint32_t M, uint32_t M_pad,
                                                     double fs, float* __restrict__ f32,
                                                     uint8_t* __restrict__ hi,
                                                     uint8_t* __restrict__ lo)
@@ -68,8 +74,10 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
     const uint32_t k = blockIdx.x;
     const uint32_t n_kb = M_pad / TC_BK;
     const bool valid = k < K;
+    const uint32_t row = row0 + k;
+    const bool sine = quad && (row & 1u);
     ChirpDev p{};
-    if (valid) p = params[k];
+    if (valid) p = params[quad ? row >> 1 : row];
 
     const double inv_fs = 1.0 / fs;
     double k1 = 0.0, k2 = 0.0;
@@ -95,13 +103,14 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
                 if (j < 0 || j >= p.MD) return 0.f;
                 const double c = d_cycles(p.track, k1, k2, (double)j * inv_fs);
                 const double fr = c - rint(c);             // [-1/2, 1/2]
-                const float cs = cospif((float)(2.0 * fr));
+                const float cs = sine ? sinpif((float)(2.0 * fr)) : cospif((float)(2.0 * fr));
                 const float sn = sinpif(((float)j + 0.5f) * inv_md);
                 return sn * sn * cs;
             };
+            const float rev = sine ? -1.f : 1.f;       // the reversed part of a partner is negated
             if (p.sense == BF_ASC) v = sample(ja);
-            else if (p.sense == BF_DESC) v = sample(jd);
-            else v = sample(ja) + sample(jd);          // superposition of both senses
+            else if (p.sense == BF_DESC) v = rev * sample(jd);
+            else v = sample(ja) + rev * sample(jd);    // superposition of both senses
         }
         g[m] = v;
         part += (double)v * (double)v;
@@ -127,7 +136,7 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
     }
 }
 
-cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t K, uint32_t K_pad, uint32_t M,
+cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t row0, int quad, uint32_t K, uint32_t K_pad, uint32_t M,
                               uint32_t M_pad, double fs, float* f32, uint8_t* hi, uint8_t* lo,
                               cudaStream_t s)
 {
@@ -139,7 +148,7 @@ cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t K, uint32_t K_pad
         if (e != cudaSuccess) return e;
     }
     count_launches(1);
-    k_bank_synth<<<K_pad, 256, smem, s>>>(params, K, M, M_pad, fs, f32, hi, lo);
+    k_bank_synth<<<K_pad, 256, smem, s>>>(params, row0, quad, K, M, M_pad, fs, f32, hi, lo);
     return cudaGetLastError();
 }
 

@@ -69,15 +69,16 @@ struct Seg {
                                     // |rho| >= kappa * sigma_pred[k]
     float kappa;
     float pad2;
-    uint32_t bank_k0;               // template index held at the bank pointers
+    uint32_t bank_k0;               // template row held at the bank pointers
                                     // (0 for a stored bank, the chunk start
                                     // for a generated one)
-    uint32_t pad1;
+    uint32_t quad;                  // rows 2c, 2c+1 are the quadrature pair of
+                                    // chirp c: one output sqrt(rho_c^2 + rho_s^2)
     uint64_t tile_begin;            // first global tile index of this segment
     uint32_t L;                     // lags
     uint32_t n_lag_tiles;
     uint32_t tt0, n_tt;             // template tiles [tt0, tt0 + n_tt)
-    uint32_t k_begin, k_end;        // templates whose outputs are kept
+    uint32_t k_begin, k_end;        // template rows whose outputs are kept
     uint32_t M_pad;
     uint32_t series_id;
 };
@@ -110,9 +111,10 @@ struct FftSeries {
 };
 
 struct FftParams {
-    const float2* hspec;            // template half spectra [K][FFT_POINTS / 2], absolute k
+    const float2* hspec;            // template half spectra [rows][FFT_POINTS / 2], absolute row
     const float2* tw;               // twiddle tables (corr_fft.cu)
-    uint32_t k_begin, k_end;
+    uint32_t k_begin, k_end;        // template rows
+    int quad;                       // rows (2c, 2c+1) are a quadrature pair
     uint32_t V;                     // valid lags per segment, FFT_POINTS - M + 1
     int n_ser;
     float thr;
@@ -152,7 +154,9 @@ struct ChirpDev {                   // device copy of a template's parameters
                                     // ascending template
 };
 
-cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t K, uint32_t K_pad,
+// rows row0 .. row0 + K_pad - 1 of the bank into the output arrays (rows past
+// row0 + K - 1 are zero); quad: row r is chirp r / 2, sine phase when r is odd
+cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t row0, int quad, uint32_t K, uint32_t K_pad,
                               uint32_t M, uint32_t M_pad, double fs, float* f32,
                               uint8_t* hi, uint8_t* lo, cudaStream_t s);
 
@@ -244,7 +248,9 @@ struct bf_ctx {
 struct bf_bank {
     bf_ctx* ctx = nullptr;
     bool generated = false;             // parameters only; synthesised per call
-    size_t K = 0, K_pad = 0;
+    size_t K = 0, K_pad = 0;            // chirps; rows rounded up to the tile
+    size_t rows = 0;                    // template rows: K, or 2K for quadrature pairs
+    bool quad = false;
     uint32_t M = 0, M_pad = 0;
     double fs = 0, T = 0;
     unsigned storage = 0;

@@ -372,10 +372,11 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
                 hb[i] = has_b ? p.hspec[(size_t)kb * FH + f] : make_float2(0.f, 0.f);
             }
         }
-        const uint32_t la = ka - p.k_begin, lb = kb - p.k_begin;
+        // output indices: one per row, or one per quadrature pair (rows ka, kb)
+        const uint32_t la = p.quad ? (ka - p.k_begin) >> 1 : ka - p.k_begin, lb = kb - p.k_begin;
         if (new_series) {
             thr_a = S.sigma_pred ? S.kappa * S.sigma_pred[la] : p.thr;
-            thr_b = !has_b ? INFINITY : (S.sigma_pred ? S.kappa * S.sigma_pred[lb] : p.thr);
+            thr_b = (!has_b || p.quad) ? INFINITY : (S.sigma_pred ? S.kappa * S.sigma_pred[lb] : p.thr);
             best_a = best_b = -1.f;
             arg_a = arg_b = 0xFFFFFFFFu;
             ss_a = ss_b = 0.0;
@@ -427,7 +428,15 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t t = (uint32_t)(tid + FT * i + FH * h);
-                if (t < nv) {
+                if (t < nv && p.quad) {
+                    // quadrature pair: |c_cos + i c_sin| / |window|
+                    const uint32_t tau = t0 + t;
+                    const float r = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * (m.inv[t] * scale);
+                    track_max(r, tau, best_a, arg_a);
+                    pa = fmaf(r, r, pa);
+                    if (r >= thr_a) push_tail(p, S.series_id, ka >> 1, tau, r);
+                    if (S.rho) S.rho[(size_t)la * S.L + tau] = r;
+                } else if (t < nv) {
                     const uint32_t tau = t0 + t;
                     const float inv = m.inv[t] * scale;
                     const float ra = z[h].x * inv, rb = z[h].y * inv;
@@ -465,7 +474,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
             if (lane == 0) {
                 atomicMax(S.vmax + la, key_a);
                 atomicAdd(S.sumsq + la, ss_a);
-                if (has_b) {
+                if (has_b && !p.quad) {
                     atomicMax(S.vmax + lb, key_b);
                     atomicAdd(S.sumsq + lb, ss_b);
                 }
@@ -531,7 +540,7 @@ bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
     const float2* tw = nullptr;
     cudaError_t e = fft_tables(ctx, st, &tw);
     if (e != cudaSuccess) return cuda_fail(e, "FFT tables");
-    const size_t K2 = bank->K + (bank->K & 1);
+    const size_t K2 = bank->rows + (bank->rows & 1);
     Allocator& mem = *ctx->mem;
     float2* spec = static_cast<float2*>(mem.alloc(K2 * FH * sizeof(float2)));
     const size_t chunk = std::min<size_t>(4096, K2);
@@ -543,10 +552,10 @@ bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
         return BF_ENOMEM;
     }
     for (size_t k0 = 0; k0 < K2 && e == cudaSuccess; k0 += chunk) {
-        const size_t kc = std::min(chunk, bank->K - k0);       // templates in this chunk
+        const size_t kc = std::min(chunk, bank->rows - k0);    // template rows in this chunk
         const size_t nr = std::min(chunk, K2 - k0);            // rows (even)
-        e = launch_bank_synth(bank->d_params + k0, (uint32_t)kc, (uint32_t)nr, bank->M, FN, bank->fs, rows,
-                              nullptr, nullptr, st);
+        e = launch_bank_synth(bank->d_params, (uint32_t)k0, bank->quad, (uint32_t)kc, (uint32_t)nr, bank->M, FN,
+                              bank->fs, rows, nullptr, nullptr, st);
         if (e == cudaSuccess) {
             const uint32_t pairs = (uint32_t)(nr / 2);
             count_launches(1);

@@ -78,6 +78,41 @@ __global__ void __launch_bounds__(SIMT_THREADS, 2) k_corr_simt(const __grid_cons
             uint32_t tau = lag0 + 8 * lane + b;
             inv[b] = tau < s.L ? s.inv_norm[tau] : 0.f;
         }
+        if (s.quad) {
+            // rows (a, a + 1) are a quadrature pair: output sqrt(rho_cos^2 + rho_sin^2)
+#pragma unroll
+            for (int a = 0; a < 8; a += 2) {
+                const uint32_t k = k0 + 8 * warp + a;
+                const bool keep = k >= s.k_begin && k < s.k_end;
+                const uint32_t o = (k - s.k_begin) >> 1;
+                const float thr = !keep ? INFINITY : (s.sigma_pred ? s.kappa * s.sigma_pred[o] : p.thr);
+                unsigned long long best = 0ull;
+                float ss = 0.f;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    uint32_t tau = lag0 + 8 * lane + b;
+                    if (tau < s.L) {
+                        const float r = sqrtf(acc[a][b] * acc[a][b] + acc[a + 1][b] * acc[a + 1][b]) * inv[b];
+                        if (s.rho && keep) s.rho[(size_t)o * s.L + tau] = r;
+                        unsigned long long key = pack_max(r, tau);
+                        best = key > best ? key : best;
+                        ss = fmaf(r, r, ss);
+                        if (r >= thr) push_candidate(p, s.series_id, k >> 1, tau, r);
+                    }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, off);
+                    best = ob > best ? ob : best;
+                    ss += __shfl_xor_sync(0xffffffffu, ss, off);
+                }
+                if (lane == 0 && keep) {
+                    atomicMax(s.vmax + o, best);
+                    atomicAdd(s.sumsq + o, (double)ss);
+                }
+            }
+            continue;
+        }
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
             const uint32_t k = k0 + 8 * warp + a;

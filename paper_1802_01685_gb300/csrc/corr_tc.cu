@@ -272,6 +272,54 @@ __device__ __forceinline__ void epi_tails(const uint32_t (&r)[32], const float* 
     }
 }
 
+// Quadrature banks: the rows of a pair (cosine, sine) sit in lanes 2i, 2i+1
+// of a warp over the same 32 columns.  One exchange per column gives the even
+// lane columns 0..15 and the odd lane columns 16..31 of both rows; each lane
+// reduces the magnitude sqrt(c^2 + s^2) over its half.  q[] keeps the
+// unnormalised magnitudes for the rare tail path.
+template <bool FULL, bool DENSE>
+__device__ __forceinline__ float epi_chunk_quad(const uint32_t (&r)[32], const float* __restrict__ inv,
+                                                uint32_t c0, uint32_t nvalid, bool odd, EpiState& st,
+                                                float* __restrict__ rho_row, float (&q)[16])
+{
+    const uint32_t cb = c0 + (odd ? 16u : 0u);
+    float cmax = 0.f;
+#pragma unroll
+    for (uint32_t j = 0; j < 16; ++j) {
+        const uint32_t send = odd ? r[j] : r[16 + j];
+        const uint32_t recv = __shfl_xor_sync(0xffffffffu, send, 1);
+        const float c = __uint_as_float(odd ? recv : r[j]);
+        const float sn = __uint_as_float(odd ? r[16 + j] : recv);
+        q[j] = sqrtf(c * c + sn * sn);
+    }
+#pragma unroll
+    for (uint32_t j = 0; j < 16; ++j) {
+        const uint32_t u = j & 3;
+        if (!FULL && cb + j >= nvalid) continue;
+        const float v = q[j] * inv[cb + j];
+        if (v > st.bv[u]) {
+            st.bv[u] = v;
+            st.bi[u] = cb + j;
+        }
+        st.ss[u] = fmaf(v, v, st.ss[u]);
+        cmax = fmaxf(cmax, v);
+        if (DENSE) rho_row[cb + j] = v;
+    }
+    return cmax;
+}
+
+__device__ __forceinline__ void epi_tails_quad(const float (&q)[16], const float* __restrict__ inv,
+                                               uint32_t cb, uint32_t nvalid, float thr,
+                                               const CorrParams& p, uint32_t series, uint32_t chirp,
+                                               uint32_t lag0)
+{
+#pragma unroll
+    for (uint32_t j = 0; j < 16; ++j) {
+        const float v = q[j] * inv[cb + j];
+        if (cb + j < nvalid && v >= thr) push_candidate(p, series, chirp, lag0 + cb + j, v);
+    }
+}
+
 __device__ __forceinline__ void record_error(int* err, int code)
 {
     atomicCAS(err, 0, code);
@@ -460,11 +508,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             const uint32_t k = c.tt * TC_TILE_T + row;
             const bool keep = k >= s.k_begin && k < s.k_end;
             const bool full = nvalid == (uint32_t)LT;
-            float* const rho_row = (s.rho != nullptr && keep) ? s.rho + (size_t)(k - s.k_begin) * s.L + c.lag0
-                                                              : nullptr;
+            const bool quad = s.quad != 0, odd = (lane & 1) != 0;
+            // output index: the row, or the quadrature pair of the row
+            const uint32_t o = quad ? (k - s.k_begin) >> 1 : k - s.k_begin;
+            float* const rho_row = (s.rho != nullptr && keep) ? s.rho + (size_t)o * s.L + c.lag0 : nullptr;
             const bool dense = rho_row != nullptr;
-            const float thr = !keep ? INFINITY
-                                    : (s.sigma_pred ? s.kappa * s.sigma_pred[k - s.k_begin] : p.thr);
+            const float thr = !keep ? INFINITY : (s.sigma_pred ? s.kappa * s.sigma_pred[o] : p.thr);
             const uint32_t series = s.series_id, lag0 = c.lag0;
             EpiState st;
 #pragma unroll
@@ -483,6 +532,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             auto reduce = [&](const uint32_t (&r)[32], uint32_t cc) {
                 if (cc >= nvalid) return;
                 float cmax;
+                if (quad) {
+                    float q[16];
+                    if (dense) cmax = epi_chunk_quad<false, true>(r, sh_inv, cc, nvalid, odd, st, rho_row, q);
+                    else if (full) cmax = epi_chunk_quad<true, false>(r, sh_inv, cc, nvalid, odd, st, nullptr, q);
+                    else cmax = epi_chunk_quad<false, false>(r, sh_inv, cc, nvalid, odd, st, nullptr, q);
+                    if (cmax >= thr)
+                        epi_tails_quad(q, sh_inv, cc + (odd ? 16u : 0u), nvalid, thr, p, series, k >> 1, lag0);
+                    return;
+                }
                 if (dense) cmax = epi_chunk<false, true>(r, sh_inv, cc, nvalid, st, rho_row);
                 else if (full) cmax = epi_chunk<true, false>(r, sh_inv, cc, nvalid, st, nullptr);
                 else cmax = epi_chunk<false, false>(r, sh_inv, cc, nvalid, st, nullptr);
@@ -519,10 +577,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
                     bv = st.bv[u];
                     bi = st.bi[u];
                 }
-            if (keep && bv >= 0.f) {
-                atomicMax(s.vmax + (k - s.k_begin), pack_max(bv, c.lag0 + bi));
-                atomicAdd(s.sumsq + (k - s.k_begin),
-                          (double)((st.ss[0] + st.ss[1]) + (st.ss[2] + st.ss[3])));
+            float ssum = (st.ss[0] + st.ss[1]) + (st.ss[2] + st.ss[3]);
+            if (quad) {
+                // merge the two halves of the pair into the even lane
+                const float obv = __shfl_xor_sync(0xffffffffu, bv, 1);
+                const uint32_t obi = __shfl_xor_sync(0xffffffffu, bi, 1);
+                ssum += __shfl_xor_sync(0xffffffffu, ssum, 1);
+                if (obv > bv || (obv == bv && obi < bi)) {
+                    bv = obv;
+                    bi = obi;
+                }
+            }
+            if (keep && bv >= 0.f && !(quad && odd)) {
+                atomicMax(s.vmax + o, pack_max(bv, c.lag0 + bi));
+                atomicAdd(s.sumsq + o, (double)ssum);
             }
         }
     }

@@ -93,7 +93,7 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
         if (st) return st;
         pptr.push_back(&p->prep[s]);
         ids.push_back((uint32_t)s);
-        p->r->correlations += (double)p->prep[s].L * (double)p->r->K;
+        p->r->correlations += (double)p->prep[s].L * (double)p->r->K * (bank->quad ? 2.0 : 1.0);
     }
     std::vector<Seg> segs;
     build_segments(pptr, ids, bank, o.bank_begin, o.bank_end, o.precision, p->r->packed,

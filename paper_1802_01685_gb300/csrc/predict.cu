@@ -57,9 +57,10 @@ __global__ void k_welch_mean(const cufftComplex* __restrict__ X, uint32_t S, uin
     }
 }
 
-// sigma_k for k in [k_begin, k_end): one warp per template
+// sigma_k for k in [k_begin, k_end): one warp per template; the rows of a
+// quadrature pair add (E rho_q^2 = E rho_cos^2 + E rho_sin^2)
 __global__ void k_sigma_dot(const float* __restrict__ ph, uint32_t nf, const float* __restrict__ P,
-                            uint32_t k_begin, uint32_t k_end, const double* __restrict__ prefix,
+                            uint32_t k_begin, uint32_t k_end, int quad, const double* __restrict__ prefix,
                             uint64_t N, uint32_t M, float* __restrict__ sigma)
 {
     const uint32_t lane = threadIdx.x & 31;
@@ -67,9 +68,12 @@ __global__ void k_sigma_dot(const float* __restrict__ ph, uint32_t nf, const flo
     const double sx2 = prefix[N] / (double)N;
     const double F = 2.0 * M;
     for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k_begin + w < k_end; w += warps) {
-        const float* row = ph + (size_t)(k_begin + w) * nf;
+        const uint32_t k = k_begin + w;
         float acc = 0.f;
-        for (uint32_t f = lane; f < nf; f += 32) acc = fmaf(P[f], row[f], acc);
+        for (int q = 0; q <= quad; ++q) {
+            const float* row = ph + (size_t)(quad ? 2 * k + q : k) * nf;
+            for (uint32_t f = lane; f < nf; f += 32) acc = fmaf(P[f], row[f], acc);
+        }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0)
             sigma[w] = sx2 > 0.0 ? (float)sqrt((double)acc / (F * F * (double)M * sx2)) : 0.f;
@@ -110,10 +114,10 @@ bf_status bank_power_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
     cufftSetStream(plan, st);
     cudaError_t e = cudaSuccess;
     for (size_t k0 = 0; k0 < bank->K_pad && e == cudaSuccess && r == CUFFT_SUCCESS; k0 += chunk) {
-        const size_t kc = std::min(chunk, bank->K - std::min(k0, bank->K));
-        // rows of F samples: the template followed by zeros (rows past K are zero)
-        e = launch_bank_synth(bank->d_params + std::min(k0, bank->K), (uint32_t)kc, (uint32_t)chunk,
-                              M, F, bank->fs, rows, nullptr, nullptr, st);
+        const size_t kc = std::min(chunk, bank->rows - std::min(k0, bank->rows));
+        // rows of F samples: the template followed by zeros (rows past the bank are zero)
+        e = launch_bank_synth(bank->d_params, (uint32_t)std::min(k0, bank->rows), bank->quad, (uint32_t)kc,
+                              (uint32_t)chunk, M, F, bank->fs, rows, nullptr, nullptr, st);
         if (e == cudaSuccess) r = cufftExecR2C(plan, rows, spec);
         if (e == cudaSuccess && r == CUFFT_SUCCESS) {
             const uint32_t nrow = (uint32_t)std::min(chunk, bank->K_pad - k0);
@@ -185,7 +189,7 @@ bf_status predict_sigma(bf_ctx* ctx, const bf_bank* bank, const PreparedSeries& 
         const uint32_t K = (uint32_t)(k_end - k_begin);
         const unsigned blocks = std::max(1u, std::min((K + 7) / 8, 65535u * 8));
         k_sigma_dot<<<blocks, 256, 0, st>>>(bank->ph, nf, P, (uint32_t)k_begin, (uint32_t)k_end,
-                                            ps.prefix, N, M, out);
+                                            bank->quad ? 1 : 0, ps.prefix, N, M, out);
         e = cudaGetLastError();
     }
     // the plan's work area must outlive the transform; synchronising here keeps

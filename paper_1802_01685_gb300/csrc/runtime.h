@@ -43,6 +43,8 @@ size_t prepared_series_bytes(size_t N, uint32_t M, uint32_t M_pad, int precision
 // Template-tile geometry of a precision's kernel.
 inline uint32_t tile_templates(int precision) { return precision == BF_FP32 ? SIMT_TILE_T : TC_TILE_T; }
 inline uint32_t tile_lags(int precision) { return precision == BF_FP32 ? SIMT_TILE_L : TC_TILE_L; }
+// first template row of chirp k (quadrature banks hold two rows per chirp)
+inline size_t bank_row(const bf_bank* b, size_t k) { return b->quad ? 2 * k : k; }
 // the tensor-core precisions read the series as bf16 split rows
 inline bool uses_split_rows(int precision) { return precision == BF_BF16 || precision == BF_SPLIT_BF16; }
 

@@ -121,10 +121,11 @@ static bool admit(ServeState* S, Request* r)
     }
     r->result = res;
     const uint32_t tile_t = tile_templates(r->opts.precision);
-    r->tt_next = (uint32_t)(r->opts.bank_begin / tile_t);
-    r->tt_end = (uint32_t)((r->opts.bank_end + tile_t - 1) / tile_t);
+    r->tt_next = (uint32_t)(bank_row(r->bank, r->opts.bank_begin) / tile_t);
+    r->tt_end = (uint32_t)((bank_row(r->bank, r->opts.bank_end) + tile_t - 1) / tile_t);
     r->n_lag_tiles = (r->prep.L + tile_lags(r->opts.precision) - 1) / tile_lags(r->opts.precision);
-    r->correlations = (double)r->prep.L * (double)(r->opts.bank_end - r->opts.bank_begin);
+    r->correlations = (double)r->prep.L * (double)(r->opts.bank_end - r->opts.bank_begin) *
+                      (r->bank->quad ? 2.0 : 1.0);
     res->correlations = r->correlations;
     cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
     r->state = R_ACTIVE;
