@@ -180,7 +180,7 @@ bf_status prepare_series_alloc(bf_ctx* ctx, size_t N, uint32_t M, uint32_t M_pad
     ps.x = static_cast<float*>(grab(ps.xcap * sizeof(float)));
     ps.inv = static_cast<float*>(grab((size_t)ps.L * sizeof(float)));
     ps.nb = inv_norm_scratch_blocks(N);
-    ps.prefix = static_cast<double*>(grab((N + 1) * sizeof(double)));
+    ps.prefix = static_cast<double*>(grab(prefix_bytes(N)));
     ps.bsum = static_cast<double*>(grab(ps.nb * sizeof(double)));
     bool ok = ps.x && ps.inv && ps.prefix && ps.bsum;
     if (ok && uses_split_rows(precision)) {
@@ -224,7 +224,7 @@ bf_status prepare_series(bf_ctx* ctx, const float* src, size_t N, uint32_t M, ui
 size_t prepared_series_bytes(size_t N, uint32_t M, uint32_t M_pad, int precision)
 {
     const uint64_t L = N - M + 1;
-    size_t b = (ceil_div(L, SIMT_TILE_L) * SIMT_TILE_L + M_pad + 1024) * 4 + L * 4 + (N + 1) * 8 +
+    size_t b = (ceil_div(L, SIMT_TILE_L) * SIMT_TILE_L + M_pad + 1024) * 4 + L * 4 + prefix_bytes(N) +
                inv_norm_scratch_blocks(N) * 8;
     if (uses_split_rows(precision)) b += 2 * (ceil_div(L, TC_TILE_L) * TC_TILE_L + M_pad + 64) * 16;
     if (precision == BF_FFT_FP32) b += (size_t)fft_segments((uint32_t)L, M) * (FFT_POINTS / 2) * 8;

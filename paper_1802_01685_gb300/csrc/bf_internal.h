@@ -167,6 +167,8 @@ cudaError_t launch_inv_norm(const float* x, uint64_t N, uint32_t M, double* pref
                             double* block_scratch, uint64_t n_blocks_cap, float* inv,
                             cudaStream_t s);
 uint64_t inv_norm_scratch_blocks(uint64_t N);
+// bytes of the prefix scratch: FP64 energies S[0..N], then uint32 counts C[0..N]
+size_t prefix_bytes(uint64_t N);
 
 struct FinalizeSeries {
     const unsigned long long* packed;

@@ -9,8 +9,11 @@
 //     row pitch and no gather.  Rows past the series read zeros.
 // (2) Inverse window norms.  S[n] = sum_{i<n} x[i]^2 in FP64 (every x^2 of an
 //     FP32 sample is exact in FP64), nu(tau) = S[tau+M] - S[tau], and
-//     inv(tau) = 1 / sqrt(nu) rounded to FP32, 0 where nu == 0 (an all-zero
-//     window: the prefix is then constant, so the difference is exactly 0).
+//     inv(tau) = 1 / sqrt(nu) rounded to FP32.  A window without a nonzero
+//     sample gets exactly 0 (rho := 0 there): an exact count prefix C[n] of
+//     nonzero samples decides it, because the block-wise scan sums the energy
+//     prefix in different orders on either side of a block edge, so S may
+//     differ by rounding across an all-zero window.
 #include "bf_internal.h"
 
 namespace bfi {
@@ -52,7 +55,8 @@ constexpr int SCAN_T = 512;              // threads per scan block
 constexpr int SCAN_E = 4;                // elements per thread
 constexpr int SCAN_B = SCAN_T * SCAN_E;  // elements per block
 
-uint64_t inv_norm_scratch_blocks(uint64_t N) { return (N + SCAN_B - 1) / SCAN_B + 1; }
+// block-sum scratch (doubles): energies and nonzero counts of every scan block
+uint64_t inv_norm_scratch_blocks(uint64_t N) { return 2 * ((N + SCAN_B - 1) / SCAN_B + 1); }
 
 __device__ __forceinline__ double block_excl_scan(double v, double* sh, double* total)
 {
@@ -80,89 +84,115 @@ __device__ __forceinline__ double block_excl_scan(double v, double* sh, double* 
     return base + inc - v;
 }
 
-// per-block sums of x^2
-__global__ void __launch_bounds__(SCAN_T) k_block_sq(const float* __restrict__ x, uint64_t N,
+// Per-block sums of x^2 (FP64) and of the count of nonzero samples (an exact
+// integer in FP64): bsum[0, nb) and bsum[nb, 2 nb).
+__global__ void __launch_bounds__(SCAN_T) k_block_sq(const float* __restrict__ x, uint64_t N, uint64_t nb,
                                                      double* __restrict__ bsum)
 {
     __shared__ double sh[SCAN_T / 32];
     uint64_t base = (uint64_t)blockIdx.x * SCAN_B + (uint64_t)threadIdx.x * SCAN_E;
-    double v = 0.0;
+    double v = 0.0, c = 0.0;
 #pragma unroll
     for (int e = 0; e < SCAN_E; ++e)
         if (base + e < N) {
             double d = x[base + e];
             v += d * d;
+            c += d != 0.0 ? 1.0 : 0.0;
         }
-    double tot;
+    double tot, ctot;
     block_excl_scan(v, sh, &tot);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+    __syncthreads();
+    block_excl_scan(c, sh, &ctot);
+    if (threadIdx.x == 0) {
+        bsum[blockIdx.x] = tot;
+        bsum[nb + blockIdx.x] = ctot;
+    }
 }
 
-// exclusive scan of the block sums by one block (loops over chunks)
+// exclusive scan of the n block sums of one lane, in place (one block)
 __global__ void __launch_bounds__(SCAN_T) k_scan_sums(double* __restrict__ bsum, uint64_t n)
 {
     __shared__ double sh[SCAN_T / 32];
+    double* lane_sums = bsum + blockIdx.x * n;        // block 0: energies, block 1: counts
     double carry = 0.0;
     for (uint64_t c = 0; c < n; c += SCAN_T) {
         uint64_t i = c + threadIdx.x;
-        double v = i < n ? bsum[i] : 0.0;
+        double v = i < n ? lane_sums[i] : 0.0;
         double tot;
         double ex = block_excl_scan(v, sh, &tot);
         __syncthreads();
-        if (i < n) bsum[i] = carry + ex;
+        if (i < n) lane_sums[i] = carry + ex;
         carry += tot;
         __syncthreads();
     }
 }
 
-// S[n] for n = 0..N (inclusive prefix shifted by one)
-__global__ void __launch_bounds__(SCAN_T) k_prefix(const float* __restrict__ x, uint64_t N,
+// S[t] = sum_{i < t} x_i^2 and C[t] = #{i < t : x_i != 0}, t = 0..N
+__global__ void __launch_bounds__(SCAN_T) k_prefix(const float* __restrict__ x, uint64_t N, uint64_t nb,
                                                    const double* __restrict__ boff,
-                                                   double* __restrict__ S)
+                                                   double* __restrict__ S, uint32_t* __restrict__ C)
 {
     __shared__ double sh[SCAN_T / 32];
     uint64_t base = (uint64_t)blockIdx.x * SCAN_B + (uint64_t)threadIdx.x * SCAN_E;
     double v[SCAN_E];
-    double t = 0.0;
+    uint32_t nz[SCAN_E];
+    double t = 0.0, c = 0.0;
 #pragma unroll
     for (int e = 0; e < SCAN_E; ++e) {
         double d = base + e < N ? (double)x[base + e] : 0.0;
         v[e] = d * d;
+        nz[e] = d != 0.0 ? 1u : 0u;
         t += v[e];
+        c += (double)nz[e];
     }
     double ex = block_excl_scan(t, sh, nullptr) + boff[blockIdx.x];
-    if (blockIdx.x == 0 && threadIdx.x == 0) S[0] = 0.0;
+    __syncthreads();
+    uint32_t cx = (uint32_t)(block_excl_scan(c, sh, nullptr) + boff[nb + blockIdx.x]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S[0] = 0.0;
+        C[0] = 0u;
+    }
 #pragma unroll
     for (int e = 0; e < SCAN_E; ++e) {
         ex += v[e];
-        if (base + e < N) S[base + e + 1] = ex;
+        cx += nz[e];
+        if (base + e < N) {
+            S[base + e + 1] = ex;
+            C[base + e + 1] = cx;
+        }
     }
 }
 
-__global__ void k_inv_norm(const double* __restrict__ S, uint64_t L, uint32_t M,
-                           float* __restrict__ inv)
+// 1 / |window|, and exactly 0 for a window without a nonzero sample (rho := 0
+// there).  The count decides emptiness: a difference of FP64 prefix sums
+// formed in different orders need not vanish over an all-zero window.
+__global__ void k_inv_norm(const double* __restrict__ S, const uint32_t* __restrict__ C, uint64_t L,
+                           uint32_t M, float* __restrict__ inv)
 {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < L;
          t += (uint64_t)gridDim.x * blockDim.x) {
         double nu = S[t + M] - S[t];
-        inv[t] = nu > 0.0 ? (float)(1.0 / sqrt(nu)) : 0.f;
+        inv[t] = (C[t + M] != C[t] && nu > 0.0) ? (float)(1.0 / sqrt(nu)) : 0.f;
     }
 }
+
+size_t prefix_bytes(uint64_t N) { return (N + 1) * (sizeof(double) + sizeof(uint32_t)); }
 
 cudaError_t launch_inv_norm(const float* x, uint64_t N, uint32_t M, double* prefix,
                             double* block_scratch, uint64_t n_blocks_cap, float* inv,
                             cudaStream_t s)
 {
     uint64_t nb = (N + SCAN_B - 1) / SCAN_B;
-    if (nb == 0 || nb + 1 > n_blocks_cap || N < M) return cudaErrorInvalidValue;
+    if (nb == 0 || 2 * nb > n_blocks_cap || N < M) return cudaErrorInvalidValue;
+    uint32_t* counts = reinterpret_cast<uint32_t*>(prefix + N + 1);
     count_launches(4);
-    k_block_sq<<<(unsigned)nb, SCAN_T, 0, s>>>(x, N, block_scratch);
-    k_scan_sums<<<1, SCAN_T, 0, s>>>(block_scratch, nb);
-    k_prefix<<<(unsigned)nb, SCAN_T, 0, s>>>(x, N, block_scratch, prefix);
+    k_block_sq<<<(unsigned)nb, SCAN_T, 0, s>>>(x, N, nb, block_scratch);
+    k_scan_sums<<<2, SCAN_T, 0, s>>>(block_scratch, nb);
+    k_prefix<<<(unsigned)nb, SCAN_T, 0, s>>>(x, N, nb, block_scratch, prefix, counts);
     uint64_t L = N - M + 1;
     uint64_t blocks = (L + 255) / 256;
     if (blocks > 65535ull * 16) blocks = 65535ull * 16;
-    k_inv_norm<<<(unsigned)blocks, 256, 0, s>>>(prefix, L, M, inv);
+    k_inv_norm<<<(unsigned)blocks, 256, 0, s>>>(prefix, counts, L, M, inv);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ struct PreparedSeries {
     float* inv = nullptr;           // [L] inverse window norms
     uint4* yhi = nullptr;           // split rows (tensor-core path)
     uint4* ylo = nullptr;
-    double* prefix = nullptr;       // FP64 prefix of x^2 (scratch)
+    double* prefix = nullptr;       // FP64 prefix of x^2, then the uint32 nonzero counts (scratch)
     double* bsum = nullptr;         // scan block sums (scratch)
     uint64_t xcap = 0, nb = 0, rows = 0;
     std::vector<void*> owned;       // every buffer, prefix scratch included
