@@ -83,7 +83,9 @@ def test_dense_output_maxima_sigma(ctx, case, prec):
     assert err.max() <= TOL[prec], err.max()
     check_maxima(outs[0], ref, ref["rho"], TOL[prec], prec)
     check_sigma(outs[0], ref, TOL[prec])
-    assert outs[0]["argmax"][case["k_inj"]] == case["n0"]
+    # the phase-blind output follows the envelope, whose top is flat to a lag or two
+    assert abs(int(outs[0]["argmax"][case["k_inj"]]) - case["n0"]) <= 2
+    assert abs(int(ref["argmax"][case["k_inj"]]) - case["n0"]) <= 2
     # without the dense output (the fused path that the benchmark times)
     g = run(ctx, bank, [x], fs, prec)[0][0]
     check_maxima(g, ref, ref["rho"], TOL[prec], prec)
