@@ -335,6 +335,9 @@ __device__ __forceinline__ void stage_spectrum(const Smem& m, const float2* src)
 // The correlation.  Each CTA walks its items (template pair, series, segment)
 // in order; while the FFT of one segment runs, the spectrum of the next one
 // and the window norms of this one arrive in shared memory.
+// QUAD (a compile-time copy of p.quad, so that each epilogue gets its own
+// register allocation): the pair is a template and its quadrature partner.
+template <bool QUAD>
 __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftParams p)
 {
     const Smem m = smem_setup(p.tw);
@@ -356,7 +359,9 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
     float thr_a = 0.f, thr_b = 0.f;
     float best_a = -1.f, best_b = -1.f;
     uint32_t arg_a = 0xFFFFFFFFu, arg_b = 0xFFFFFFFFu;
-    double ss_a = 0.0, ss_b = 0.0;
+    // per-thread sums of rho^2 over a series (a few thousand terms of similar
+    // size: FP32 is ample); the sums over threads are FP64
+    float ss_a = 0.f, ss_b = 0.f;
     bool new_pair = true, new_series = true;
 
     for (;;) {
@@ -373,13 +378,13 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
             }
         }
         // output indices: one per row, or one per quadrature pair (rows ka, kb)
-        const uint32_t la = p.quad ? (ka - p.k_begin) >> 1 : ka - p.k_begin, lb = kb - p.k_begin;
+        const uint32_t la = QUAD ? (ka - p.k_begin) >> 1 : ka - p.k_begin, lb = kb - p.k_begin;
         if (new_series) {
             thr_a = S.sigma_pred ? S.kappa * S.sigma_pred[la] : p.thr;
-            thr_b = (!has_b || p.quad) ? INFINITY : (S.sigma_pred ? S.kappa * S.sigma_pred[lb] : p.thr);
+            thr_b = (!has_b || QUAD) ? INFINITY : (S.sigma_pred ? S.kappa * S.sigma_pred[lb] : p.thr);
             best_a = best_b = -1.f;
             arg_a = arg_b = 0xFFFFFFFFu;
-            ss_a = ss_b = 0.0;
+            ss_a = ss_b = 0.f;
         }
         const uint32_t t0 = j * p.V;
         const uint32_t nv = min(p.V, S.L - t0);
@@ -421,14 +426,14 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
         cp_async_wait<1>();                         // this segment's window norms
         __syncthreads();
         float pa = 0.f, pb = 0.f;
-#pragma unroll
+#pragma unroll 4          // a full unroll pushes the non-quadrature copy past 128 registers
         for (int i = 0; i < FBINS; ++i) {
             float2 z[2];
             fft_final<1>(m, i, z[0], z[1]);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t t = (uint32_t)(tid + FT * i + FH * h);
-                if (t < nv && p.quad) {
+                if (QUAD && t < nv) {
                     // quadrature pair: |c_cos + i c_sin| / |window|
                     const uint32_t tau = t0 + t;
                     const float r = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * (m.inv[t] * scale);
@@ -436,7 +441,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
                     pa = fmaf(r, r, pa);
                     if (r >= thr_a) push_tail(p, S.series_id, ka >> 1, tau, r);
                     if (S.rho) S.rho[(size_t)la * S.L + tau] = r;
-                } else if (t < nv) {
+                } else if (!QUAD && t < nv) {
                     const uint32_t tau = t0 + t;
                     const float inv = m.inv[t] * scale;
                     const float ra = z[h].x * inv, rb = z[h].y * inv;
@@ -456,27 +461,28 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
                 }
             }
         }
-        ss_a += (double)pa;
-        ss_b += (double)pb;
+        ss_a += pa;
+        ss_b += pb;
         if (nj == 0) {
             // last segment of this series: reduce and publish
             unsigned long long key_a = best_a >= 0.f ? pack_max(best_a, arg_a) : 0ull;
             unsigned long long key_b = best_b >= 0.f ? pack_max(best_b, arg_b) : 0ull;
+            double da = (double)ss_a, db = (double)ss_b;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const unsigned long long oa = __shfl_xor_sync(0xffffffffu, key_a, o);
                 const unsigned long long ob = __shfl_xor_sync(0xffffffffu, key_b, o);
                 key_a = oa > key_a ? oa : key_a;
                 key_b = ob > key_b ? ob : key_b;
-                ss_a += __shfl_xor_sync(0xffffffffu, ss_a, o);
-                ss_b += __shfl_xor_sync(0xffffffffu, ss_b, o);
+                da += __shfl_xor_sync(0xffffffffu, da, o);
+                db += __shfl_xor_sync(0xffffffffu, db, o);
             }
             if (lane == 0) {
                 atomicMax(S.vmax + la, key_a);
-                atomicAdd(S.sumsq + la, ss_a);
-                if (has_b && !p.quad) {
+                atomicAdd(S.sumsq + la, da);
+                if (has_b && !QUAD) {
                     atomicMax(S.vmax + lb, key_b);
-                    atomicAdd(S.sumsq + lb, ss_b);
+                    atomicAdd(S.sumsq + lb, db);
                 }
             }
         }
@@ -495,7 +501,9 @@ cudaError_t fft_attributes()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_corr_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CORR_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_corr_fft<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CORR_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_corr_fft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CORR_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fft_series, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
     if (e == cudaSuccess)
@@ -594,7 +602,8 @@ cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st)
     if (n_pairs == 0 || p.n_ser == 0) return cudaSuccess;
     const unsigned grid = std::min<unsigned>(n_pairs, (unsigned)n_sm);
     count_launches(1);
-    k_corr_fft<<<grid, FT, CORR_SMEM, st>>>(p);
+    if (p.quad) k_corr_fft<true><<<grid, FT, CORR_SMEM, st>>>(p);
+    else k_corr_fft<false><<<grid, FT, CORR_SMEM, st>>>(p);
     return cudaGetLastError();
 }
 
