@@ -48,7 +48,7 @@ UNIT = "correlations/s"
 # Keyed by (hash of the kernel source the counters were taken on, lags per
 # tile); a changed kernel reports null until it is captured again.
 TRAFFIC_BYTES_PER_TEMPLATE_TILE = {
-    ("e553d827bd7a05cc", 256): (272.14e6 + 3.99e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
+    ("4269de39282eb06d", 256): (272.01e6 + 3.93e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
 }
 
 
