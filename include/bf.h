@@ -75,10 +75,13 @@ typedef enum {
                            hi*hi + hi*lo + lo*hi into one FP32 accumulator     */
     BF_FFT_FP32 = 3     /* the paper's route (Sect. 2.2, Fig. 5): FP32 FFTs,
                            overlap-save over segments of 8192 samples
-                           (8193 - M lags each), template spectra kept with
-                           the bank (32 KiB per template, computed on first
-                           use from the chirp parameters, whatever the bank
-                           stores).  Templates of at most 4096 samples, else
+                           (8193 - M lags each).  Template spectra are made
+                           from the chirp parameters, whatever the bank
+                           stores: a stored bank keeps them (32 KiB per
+                           template, made on first use); a generated bank
+                           makes them per call, 16,384 rows at a time,
+                           overlapped with the correlation, so any bank size
+                           works.  Templates of at most 4096 samples, else
                            BF_ENOTSUP; not in plans or the serving loop.
                            tile_lags is ignored.                             */
 } bf_precision;

@@ -973,6 +973,7 @@ cudaError_t correlate_fft(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
     const uint32_t V = FFT_POINTS - bank->M + 1;
     const float2* tw = nullptr;
     cudaError_t e = fft_tables(ctx, st, &tw);
+    std::vector<FftParams> batches;
     for (size_t s0 = 0; s0 < S && e == cudaSuccess; s0 += MAX_FFT_SER) {
         const int n = (int)std::min<size_t>(MAX_FFT_SER, S - s0);
         FftSeriesBatch b{};
@@ -1007,7 +1008,6 @@ cudaError_t correlate_fft(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
         b.n = n;
         b.V = V;
         b.tw = tw;
-        p.hspec = bank->fspec;
         p.tw = tw;
         p.k_begin = (uint32_t)bank_row(bank, o.bank_begin);
         p.k_end = (uint32_t)bank_row(bank, o.bank_end);
@@ -1019,7 +1019,19 @@ cudaError_t correlate_fft(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
         p.cand = r->cand;
         p.cand_count = r->cand_count;
         e = launch_fft_series(b, total, ctx->n_sm, st);
-        if (e == cudaSuccess) e = launch_corr_fft(p, ctx->n_sm, st);
+        batches.push_back(p);
+    }
+    if (e != cudaSuccess) return e;
+    const uint32_t r0 = (uint32_t)bank_row(bank, o.bank_begin), r1 = (uint32_t)bank_row(bank, o.bank_end);
+    if (bank->generated) return fft_correlate_chunked(ctx, bank, batches, r0, r1, r->scratch, st);
+    // spectra kept with the bank
+    for (FftParams& p : batches) {
+        p.hspec = bank->fspec;
+        p.hrow0 = 0;
+        p.k_lo = r0;
+        p.k_hi = r1;
+        e = launch_corr_fft(p, ctx->n_sm, st);
+        if (e != cudaSuccess) break;
     }
     return e;
 }
@@ -1095,7 +1107,8 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
             segs[s].kappa = r->kappa;
         }
     }
-    if (fft) {
+    if (fft && !bank->generated) {
+        // kept with the bank; a generated bank makes them chunk by chunk per call
         st = bank_fft_spectra(ctx, const_cast<bf_bank*>(bank), strm);
         if (st) return st;
     }

@@ -111,9 +111,11 @@ struct FftSeries {
 };
 
 struct FftParams {
-    const float2* hspec;            // template half spectra [rows][FFT_POINTS / 2], absolute row
+    const float2* hspec;            // template half spectra [.][FFT_POINTS / 2]; row hrow0 first
     const float2* tw;               // twiddle tables (corr_fft.cu)
-    uint32_t k_begin, k_end;        // template rows
+    uint32_t k_begin, k_end;        // template rows of the call (outputs count from k_begin)
+    uint32_t k_lo, k_hi;            // template rows of this launch, within [k_begin, k_end)
+    uint32_t hrow0;                 // template row held at hspec[0]
     int quad;                       // rows (2c, 2c+1) are a quadrature pair
     uint32_t V;                     // valid lags per segment, FFT_POINTS - M + 1
     int n_ser;
@@ -190,6 +192,10 @@ cudaError_t launch_finalize(const FinalizeParams& p, uint32_t K, uint32_t nbins,
 uint32_t fft_segments(uint32_t L, uint32_t M);
 cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, int n_sm, cudaStream_t st);
 cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st);
+// FFT route: template spectra in chunks, for banks whose spectra are not kept (corr_fft.cu)
+cudaError_t fft_correlate_chunked(bf_ctx* ctx, const bf_bank* bank, std::vector<FftParams>& batches,
+                                  uint32_t row_begin, uint32_t row_end, std::vector<void*>& keep,
+                                  cudaStream_t st);
 cudaError_t launch_coincidence(const float* A, const float* B, uint32_t nt, uint32_t nf, uint32_t w,
                                uint32_t dt, unsigned int* out, int n_sm, cudaStream_t s);
 cudaError_t launch_skewnorm_fit(const float* v, uint64_t n, double* acc, double* out, int n_sm,

@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
     const int tid = threadIdx.x, lane = tid & 31;
     const int rd = tid + (tid >> 4);
     const int rv = (FN - tid) + ((FN - tid) >> 4);        // padded address of Z[F - tid]
-    const uint32_t n_pairs = (p.k_end - p.k_begin + 1) / 2;
+    const uint32_t n_pairs = (p.k_hi - p.k_lo + 1) / 2;
     const float scale = 1.f / (float)FN;
     uint32_t pair = blockIdx.x;
     if (pair >= n_pairs || p.n_ser == 0) return;
@@ -367,14 +367,14 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
     for (;;) {
         const FftSeries& S = p.ser[s];
         if (new_pair) {
-            ka = p.k_begin + 2 * pair;
+            ka = p.k_lo + 2 * pair;
             kb = ka + 1;
-            has_b = kb < p.k_end;
+            has_b = kb < p.k_hi;
 #pragma unroll
             for (int i = 0; i < FBINS; ++i) {
                 const int f = tid + FT * i;
-                ha[i] = p.hspec[(size_t)ka * FH + f];
-                hb[i] = has_b ? p.hspec[(size_t)kb * FH + f] : make_float2(0.f, 0.f);
+                ha[i] = p.hspec[(size_t)(ka - p.hrow0) * FH + f];
+                hb[i] = has_b ? p.hspec[(size_t)(kb - p.hrow0) * FH + f] : make_float2(0.f, 0.f);
             }
         }
         // output indices: one per row, or one per quadrature pair (rows ka, kb)
@@ -535,6 +535,31 @@ cudaError_t fft_tables(bf_ctx* ctx, cudaStream_t st, const float2** out)
     return fft_attributes();
 }
 
+// Half spectra of template rows [row0, row0 + nrows) into out[0 ..] (nrows
+// rounded up to even; an odd tail pairs with a zero row whose spectrum is not
+// written), through `scratch`, room for `scratch_rows` synthesised rows of F
+// samples.  Asynchronous on st.
+static cudaError_t template_spectra(const bf_bank* bank, size_t row0, size_t nrows, float* scratch,
+                                    size_t scratch_rows, const float2* tw, float2* out, int n_sm,
+                                    cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < nrows && e == cudaSuccess; k += scratch_rows) {
+        const size_t kc = std::min(scratch_rows, nrows - k);     // rows of this sub-chunk
+        const size_t nr = kc + (kc & 1);                          // scratch_rows is even
+        e = launch_bank_synth(bank->d_params, (uint32_t)(row0 + k), bank->quad, (uint32_t)kc, (uint32_t)nr,
+                              bank->M, FN, bank->fs, scratch, nullptr, nullptr, st);
+        if (e == cudaSuccess) {
+            const uint32_t pairs = (uint32_t)(nr / 2);
+            count_launches(1);
+            k_fft_bank<<<std::min<uint32_t>(pairs, (uint32_t)n_sm), FT, FFT_SMEM, st>>>(
+                scratch, (uint32_t)kc, pairs, tw, out + k * FH);
+            e = cudaGetLastError();
+        }
+    }
+    return e;
+}
+
 // Half spectra of every template of the bank, [K rounded up to even][4096]
 // complex, computed once and kept with the bank.
 bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
@@ -559,19 +584,7 @@ bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
         set_error("out of device memory for the template spectra (%zu MB)", (K2 * FH * 8) >> 20);
         return BF_ENOMEM;
     }
-    for (size_t k0 = 0; k0 < K2 && e == cudaSuccess; k0 += chunk) {
-        const size_t kc = std::min(chunk, bank->rows - k0);    // template rows in this chunk
-        const size_t nr = std::min(chunk, K2 - k0);            // rows (even)
-        e = launch_bank_synth(bank->d_params, (uint32_t)k0, bank->quad, (uint32_t)kc, (uint32_t)nr, bank->M, FN,
-                              bank->fs, rows, nullptr, nullptr, st);
-        if (e == cudaSuccess) {
-            const uint32_t pairs = (uint32_t)(nr / 2);
-            count_launches(1);
-            k_fft_bank<<<std::min<uint32_t>(pairs, (uint32_t)ctx->n_sm), FT, FFT_SMEM, st>>>(
-                rows, (uint32_t)kc, pairs, tw, spec + k0 * FH);
-            e = cudaGetLastError();
-        }
-    }
+    e = template_spectra(bank, 0, bank->rows, rows, chunk, tw, spec, ctx->n_sm, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     mem.release(rows);
     if (e != cudaSuccess) {
@@ -598,13 +611,78 @@ cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, 
 
 cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st)
 {
-    const uint32_t n_pairs = (p.k_end - p.k_begin + 1) / 2;
+    const uint32_t n_pairs = (p.k_hi - p.k_lo + 1) / 2;
     if (n_pairs == 0 || p.n_ser == 0) return cudaSuccess;
     const unsigned grid = std::min<unsigned>(n_pairs, (unsigned)n_sm);
     count_launches(1);
     if (p.quad) k_corr_fft<true><<<grid, FT, CORR_SMEM, st>>>(p);
     else k_corr_fft<false><<<grid, FT, CORR_SMEM, st>>>(p);
     return cudaGetLastError();
+}
+
+// A bank that keeps only its chirp parameters: the template spectra are made
+// chunk by chunk (FFT_CHUNK_ROWS rows, 512 MiB of spectra) into a two-slot
+// ring on the auxiliary stream, and chunk c is correlated against every
+// series batch on the main stream while chunk c+1 is made.  Events order the
+// reuse of a slot after the launches that read it.
+constexpr size_t FFT_CHUNK_ROWS = 16384;
+constexpr size_t FFT_SYNTH_ROWS = 4096;
+
+cudaError_t fft_correlate_chunked(bf_ctx* ctx, const bf_bank* bank, std::vector<FftParams>& batches,
+                                  uint32_t row_begin, uint32_t row_end, std::vector<void*>& keep,
+                                  cudaStream_t st)
+{
+    const size_t n_rows = row_end - row_begin;
+    const size_t chunk = std::min(FFT_CHUNK_ROWS, n_rows + (n_rows & 1));
+    const size_t n_chunks = (n_rows + chunk - 1) / chunk;
+    Allocator& mem = *ctx->mem;
+    float2* slot[2] = {nullptr, nullptr};
+    // the ring outlives this call's launches: the result releases it
+    float* scratch = static_cast<float*>(mem.alloc(FFT_SYNTH_ROWS * FN * sizeof(float)));
+    keep.push_back(scratch);
+    for (int i = 0; i < 2 && i < (int)n_chunks; ++i) {
+        slot[i] = static_cast<float2*>(mem.alloc(chunk * FH * sizeof(float2)));
+        keep.push_back(slot[i]);
+    }
+    if (!scratch || !slot[0] || (n_chunks > 1 && !slot[1])) {
+        set_error("out of device memory for the template-spectra ring");
+        return cudaErrorMemoryAllocation;
+    }
+    const float2* tw = batches.empty() ? nullptr : batches[0].tw;
+    cudaEvent_t ev_start, made[2], used[2];
+    cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+    for (int i = 0; i < 2; ++i) {
+        cudaEventCreateWithFlags(&made[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&used[i], cudaEventDisableTiming);
+    }
+    cudaError_t e = cudaEventRecord(ev_start, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, ev_start, 0);
+    for (size_t c = 0; c < n_chunks && e == cudaSuccess; ++c) {
+        const int sl = (int)(c & 1);
+        const uint32_t c0 = row_begin + (uint32_t)(c * chunk);
+        const uint32_t c1 = (uint32_t)std::min<size_t>(c0 + chunk, row_end);
+        if (c >= 2) e = cudaStreamWaitEvent(ctx->aux, used[sl], 0);
+        if (e == cudaSuccess)
+            e = template_spectra(bank, c0, c1 - c0, scratch, FFT_SYNTH_ROWS, tw, slot[sl], ctx->n_sm, ctx->aux);
+        if (e == cudaSuccess) e = cudaEventRecord(made[sl], ctx->aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, made[sl], 0);
+        for (FftParams& p : batches) {
+            if (e != cudaSuccess) break;
+            p.hspec = slot[sl];
+            p.hrow0 = c0;
+            p.k_lo = c0;
+            p.k_hi = c1;
+            e = launch_corr_fft(p, ctx->n_sm, st);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(used[sl], st);
+    }
+    // events may be destroyed while pending work still references them
+    cudaEventDestroy(ev_start);
+    for (int i = 0; i < 2; ++i) {
+        cudaEventDestroy(made[i]);
+        cudaEventDestroy(used[i]);
+    }
+    return e;
 }
 
 }  // namespace bfi

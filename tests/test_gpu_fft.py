@@ -153,3 +153,32 @@ def test_rejections(ctx):
         bf.bf_serve_submit(ctx, bank, w["series"][0], w["fs"], bf.make_opts(precision=PREC))
     assert e.value.status == bf.BF_ENOTSUP
     bf.bf_bank_destroy(bank)
+
+
+def test_generated_bank_in_chunks(ctx):
+    """A bank that keeps only chirp parameters makes its spectra 16,384 rows
+    at a time in a two-slot ring: a 20,000-template bank from an odd offset
+    spans two chunks.  Templates around the chunk edge against the oracle;
+    every template against the bank that keeps its spectra."""
+    fs, M = 2048.0, 2048
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0], 20.0,
+                           1000.0, 50, 100)                      # 20,000 templates
+    x = np.random.default_rng(23).standard_normal(12000).astype(np.float32)
+    b0 = 7
+    gen = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_GENERATED)
+    outs, _, info = run(ctx, gen, [x], fs, PREC, bank_begin=b0)
+    g = outs[0]
+    assert info.n_templates == 20000 - b0
+    p = oracle_params(spec)
+    idx = np.array([0, 1, 16382, 16383, 16384, 16385, 16386, 19991, 19992]) + 0
+    idx = idx[idx < 20000 - b0]
+    ref = oracle.search(x, fs, subset(p, idx + b0), M, want_rho=True)
+    gs = {k: v[idx] for k, v in g.items() if k in ("max", "argmax", "sigma")}
+    check_maxima(gs, ref, ref["rho"], TOL[PREC], "chunk edge")
+    check_sigma(gs, ref, TOL[PREC])
+    stored = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_FP32)
+    s = run(ctx, stored, [x], fs, PREC, bank_begin=b0)[0][0]
+    assert np.abs(s["max"].astype(np.float64) - g["max"]).max() <= 2 * TOL[PREC]
+    assert np.abs(s["sigma"].astype(np.float64) - g["sigma"]).max() <= 2 * TOL[PREC]
+    bf.bf_bank_destroy(stored)
+    bf.bf_bank_destroy(gen)
