@@ -583,7 +583,9 @@ def run_workload(name: str, n_check: int):
     at 2000 Hz, 1,048,576 linear templates, one batched launch, mean
     spectrum) or 'full_bank' (32 s at 2048 Hz, 8,640,000 templates over both
     tracks, both senses and nine sweep times, stored and generated banks,
-    histogram and map)."""
+    histogram and map).  Each also runs through the FFT route: the GRB bank
+    keeps its spectra (made in the untimed warm-up call), the full bank makes
+    them chunk by chunk inside the timed call."""
     import oracle
     import __graft_entry__
     from paper_1802_01685_gb300 import bf, synth
@@ -591,9 +593,12 @@ def run_workload(name: str, n_check: int):
     w = synth.grb_batch() if name == "grb_batch" else synth.full_bank()
     fs, M, xs = w["fs"], w["M"], w["series"]
     ctx = bf.bf_init()
-    modes = [("stored", bf.BF_BANK_SPLIT_BF16)]
+    modes = [("stored", bf.BF_BANK_SPLIT_BF16, "split_bf16")]
     if name == "full_bank":
-        modes.append(("generated", bf.BF_BANK_GENERATED))
+        modes.append(("generated", bf.BF_BANK_GENERATED, "split_bf16"))
+        modes.append(("fft_generated", bf.BF_BANK_GENERATED, "fft_fp32"))
+    else:
+        modes.append(("fft_stored", bf.BF_BANK_SPLIT_BF16, "fft_fp32"))
     g = w["grid"]
     p = oracle.grid(g["tracks"], g["senses"], g["durations"], g["f_min"], g["f_max"], g["I"], g["J"])
     K = len(p["track"])
@@ -601,12 +606,13 @@ def run_workload(name: str, n_check: int):
     sub = {k: np.ascontiguousarray(v[idx]) for k, v in p.items()}
     out = {"workload": name, "series": len(xs), "samples": int(sum(len(x) for x in xs)),
            "templates": K, "template_len": M}
-    for mode, storage in modes:
+    ref = oracle.search(xs[0], fs, sub, M)
+    for mode, storage, prec in modes:
         t0 = time.perf_counter()
         bank = bf.bf_bank_create_grid(ctx, g, fs, 1.0, storage)
         t1 = time.perf_counter()
-        opts = bf.make_opts(precision="split_bf16", want_map=(name == "full_bank"))
-        warm = bf.make_opts(precision="split_bf16", bank_end=4096)
+        opts = bf.make_opts(precision=prec, want_map=(name == "full_bank"))
+        warm = bf.make_opts(precision=prec, bank_end=4096)
         bf.bf_result_destroy(bf.bf_correlate(ctx, bank, xs, fs, warm))
         t2 = time.perf_counter()
         res = bf.bf_correlate(ctx, bank, xs, fs, opts)
@@ -616,16 +622,17 @@ def run_workload(name: str, n_check: int):
         mean = bf.bf_result_copy_mean_max(res)
         bf.bf_result_destroy(res)
         bf.bf_bank_destroy(bank)
-        out[mode] = {"bank_create_s": round(t1 - t0, 3), "search_s": round(t3 - t2, 3),
+        out[mode] = {"precision": prec, "bank_create_s": round(t1 - t0, 3),
+                     "warmup_s": round(t2 - t1, 3), "search_s": round(t3 - t2, 3),
                      "kernel_ms": round(info.kernel_ms, 1), "correlations": info.correlations,
                      "correlations_per_s": info.correlations / (t3 - t2),
-                     "issued_tflops": round(3 * 2 * M * info.correlations / (info.kernel_ms / 1e3) / 1e12, 1),
-                     "tails": int(info.n_candidates)}
-    ref = oracle.search(xs[0], fs, sub, M)
-    out["oracle_check"] = {"templates": n_check, "series": 0,
-                           "max_abs_err_of_max_rho": float(np.abs(got["max"][idx] - ref["max"]).max()),
-                           "argmax_equal": int((got["argmax"][idx] == ref["argmax"]).sum()),
-                           "mean_of_maxima_finite": bool(np.all(np.isfinite(mean)))}
+                     "tails": int(info.n_candidates),
+                     "oracle_check": {"templates": n_check, "series": 0,
+                                      "max_abs_err_of_max_rho": float(np.abs(got["max"][idx] - ref["max"]).max()),
+                                      "argmax_equal": int((got["argmax"][idx] == ref["argmax"]).sum()),
+                                      "mean_of_maxima_finite": bool(np.all(np.isfinite(mean)))}}
+        if prec != "fft_fp32":
+            out[mode]["issued_tflops"] = round(3 * 2 * M * info.correlations / (info.kernel_ms / 1e3) / 1e12, 1)
     bf.bf_destroy(ctx)
     print(json.dumps(out), flush=True)
 
