@@ -441,10 +441,12 @@ def run_cpu_sample(ctx, bf, w, xs_host, n_templates):
     return cpu, acc
 
 
-def run_serve(ctx, bf, synth, args):
+def run_serve(ctx, bf, synth, args, precision="split_bf16", baseline=True):
     """Finite seeded stream of mixed requests (lengths 4-64 s, 2048/4096 Hz,
     Gaussian or Poisson-count, bank slices of 2^12..2^16 templates) arriving
-    as a Poisson process; continuous batching; p50/p99 from submission."""
+    as a Poisson process; continuous batching; p50/p99 from submission.  The
+    statistics are the context's, so each precision runs in a context of its
+    own."""
     reqs = synth.serving_stream(seed=8, n_requests=args.serve_requests, rate_hz=args.serve_rate,
                                 t_min=4.0, t_max=64.0, k_min_log2=12, k_max_log2=16)
     banks = {}
@@ -459,7 +461,7 @@ def run_serve(ctx, bf, synth, args):
     for r, x in zip(reqs, series):
         while time.perf_counter() - t0 < r["arrival_s"]:
             time.sleep(0.0005)
-        opts = bf.make_opts(precision="split_bf16", bank_end=r["n_templates"])
+        opts = bf.make_opts(precision=precision, bank_end=r["n_templates"])
         tickets.append(bf.bf_serve_submit(ctx, banks[r["fs"]], x, r["fs"], opts))
         corr += (len(x) - int(r["fs"]) + 1) * r["n_templates"]
     for t in tickets:
@@ -473,10 +475,19 @@ def run_serve(ctx, bf, synth, args):
     out = {"requests": len(reqs), "rate_hz": args.serve_rate, "p50_ms": round(s.p50_ms, 2),
            "p99_ms": round(s.p99_ms, 2), "sustained_correlations_per_s": corr / wall,
            "busy_correlations_per_s": s.correlations_per_s, "launches": int(s.launches),
-           "precision": "split_bf16",
+           "precision": precision,
            "stream": "seeded Poisson arrivals; 4-64 s series; 2048/4096 Hz; 2^12-2^16 templates"}
-    if not args.no_fp32:
+    if baseline and not args.no_fp32:
         out["fp32_one_at_a_time"] = run_serve_fp32_baseline(ctx, bf, synth, reqs, series)
+    if baseline and not args.no_fft:
+        # the same stream through the FFT route, in a fresh context
+        ctx2 = bf.bf_init()
+        try:
+            f = run_serve(ctx2, bf, synth, args, precision="fft_fp32", baseline=False)
+        finally:
+            bf.bf_destroy(ctx2)
+        out["fft_route"] = {k: f[k] for k in ("p50_ms", "p99_ms", "sustained_correlations_per_s",
+                                               "busy_correlations_per_s", "launches")}
     return out
 
 

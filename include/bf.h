@@ -82,8 +82,9 @@ typedef enum {
                            makes them per call, 16,384 rows at a time,
                            overlapped with the correlation, so any bank size
                            works.  Templates of at most 4096 samples, else
-                           BF_ENOTSUP; not in plans or the serving loop.
-                           tile_lags is ignored.                             */
+                           BF_ENOTSUP.  Not in plans; the serving loop runs
+                           it per request with a stored bank.  tile_lags is
+                           ignored.                                          */
 } bf_precision;
 
 /* which sample layouts a bank keeps in device memory (bit flags) */

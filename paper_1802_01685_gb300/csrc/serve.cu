@@ -10,7 +10,10 @@
 // instead of waiting for them to finish.  When a request's last chunk has been
 // launched its finalize kernels follow on the same stream; its completion
 // event then releases the slot and its memory.  Requests of different
-// precisions go to separate launches of the matching kernel.
+// precisions go to separate launches of the matching kernel.  A request on
+// the FFT route makes its segment spectra at admission and then takes a
+// chunk of template pairs per iteration, in a launch of its own (the FFT
+// kernel walks one template range for all the series it is given).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -50,11 +53,18 @@ struct Request {
     size_t bytes = 0;
     double t_submit = 0, t_done = 0;
     double correlations = 0;
+    // the FFT route
+    bool fft = false;
+    FftParams fp{};                 // this request's series and outputs
+    float2* seg_spec = nullptr;     // its segment spectra
+    uint32_t k_next = 0, k_stop = 0;   // template-row cursor
 };
 
 // tiles per SM per iteration: large enough to amortise the launch, small
 // enough that new arrivals join within a few milliseconds
 constexpr uint64_t TILES_PER_SM = 8;
+// FFT-route transforms per SM per iteration (about as long as the tiles above)
+constexpr uint64_t TRANSFORMS_PER_SM = 100;
 
 }  // namespace
 
@@ -81,6 +91,10 @@ struct ServeState {
 static void release_request_device(bf_ctx* ctx, Request* r)
 {
     r->prep.release(*ctx->mem);
+    if (r->seg_spec) {
+        ctx->mem->release(r->seg_spec);
+        r->seg_spec = nullptr;
+    }
     if (r->done) {
         cudaEventDestroy(r->done);
         r->done = nullptr;
@@ -119,10 +133,70 @@ static bool admit(ServeState* S, Request* r)
             return false;
         }
     }
+    if (r->opts.precision == BF_FFT_FP32) {
+        // template spectra (kept with the bank), then this series' segment spectra
+        std::lock_guard<std::mutex> g(ctx->launch_mu);
+        const float2* tw = nullptr;
+        cudaError_t e = fft_tables(ctx, S->stream, &tw);
+        st = e == cudaSuccess ? bank_fft_spectra(ctx, const_cast<bf_bank*>(bank), S->stream)
+                              : cuda_fail(e, "FFT tables");
+        const uint32_t nseg = fft_segments(r->prep.L, bank->M);
+        if (st == BF_OK) {
+            r->seg_spec = static_cast<float2*>(ctx->mem->alloc((size_t)nseg * (FFT_POINTS / 2) * sizeof(float2)));
+            if (!r->seg_spec) {
+                set_error("out of device memory for the segment spectra");
+                st = BF_ENOMEM;
+            }
+        }
+        if (st == BF_OK) {
+            const uint32_t V = FFT_POINTS - bank->M + 1;
+            FftSeriesBatch b{};
+            b.n = 1;
+            b.V = V;
+            b.tw = tw;
+            b.x[0] = r->prep.x;
+            b.N[0] = r->prep.N;
+            b.spec[0] = r->seg_spec;
+            e = launch_fft_series(b, nseg, ctx->n_sm, S->stream);
+            if (e != cudaSuccess) st = cuda_fail(e, "segment spectra");
+            FftParams& p = r->fp;
+            p.hspec = bank->fspec;
+            p.tw = tw;
+            p.k_begin = (uint32_t)bank_row(bank, r->opts.bank_begin);
+            p.k_end = (uint32_t)bank_row(bank, r->opts.bank_end);
+            p.hrow0 = 0;
+            p.quad = bank->quad ? 1 : 0;
+            p.V = V;
+            p.n_ser = 1;
+            p.thr = res->thr;
+            p.cand_cap = res->cand_cap;
+            p.cand = res->cand;
+            p.cand_count = res->cand_count;
+            FftSeries& f = p.ser[0];
+            f.spec = r->seg_spec;
+            f.inv = r->prep.inv;
+            f.vmax = res->packed;
+            f.sumsq = res->sumsq;
+            f.sigma_pred = res->parseval ? res->sigma_pred : nullptr;
+            f.kappa = res->kappa;
+            f.L = r->prep.L;
+            f.nseg = nseg;
+            r->fft = true;
+            r->k_next = p.k_begin;
+            r->k_stop = p.k_end;
+        }
+        if (st != BF_OK) {
+            r->status = st;
+            r->error = bf_last_error();
+            release_request_device(ctx, r);
+            bf_result_destroy(res);
+            return false;
+        }
+    }
     r->result = res;
     const uint32_t tile_t = tile_templates(r->opts.precision);
     r->tt_next = (uint32_t)(bank_row(r->bank, r->opts.bank_begin) / tile_t);
-    r->tt_end = (uint32_t)((bank_row(r->bank, r->opts.bank_end) + tile_t - 1) / tile_t);
+    r->tt_end = r->fft ? r->tt_next : (uint32_t)((bank_row(r->bank, r->opts.bank_end) + tile_t - 1) / tile_t);
     r->n_lag_tiles = (r->prep.L + tile_lags(r->opts.precision) - 1) / tile_lags(r->opts.precision);
     r->correlations = (double)r->prep.L * (double)(r->opts.bank_end - r->opts.bank_begin) *
                       (r->bank->quad ? 2.0 : 1.0);
@@ -179,7 +253,7 @@ static void scheduler(ServeState* S)
         std::vector<Request*> finishing;
         uint64_t n_work = 0;
         for (Request* r : act)
-            if (!r->cancel && r->tt_next < r->tt_end) ++n_work;
+            if (!r->cancel && (r->tt_next < r->tt_end || r->k_next < r->k_stop)) ++n_work;
         const uint64_t budget = (uint64_t)ctx->n_sm * TILES_PER_SM;
         for (Request* r : act) {
             if (r->cancel || r->tt_next >= r->tt_end) continue;
@@ -229,6 +303,22 @@ static void scheduler(ServeState* S)
                 if (e != cudaSuccess)
                     for (Request* r : shared_owner) { r->status = cuda_fail(e, "serve launch"); r->cancel = true; }
             }
+            any = true;
+        }
+        // FFT-route requests: a chunk of template pairs each
+        for (Request* r : act) {
+            if (!r->fft || r->cancel || r->k_next >= r->k_stop) continue;
+            const uint64_t per = std::max<uint64_t>(1, (uint64_t)ctx->n_sm * TRANSFORMS_PER_SM /
+                                                           std::max<uint64_t>(1, n_work));
+            const uint64_t pairs = std::max<uint64_t>((uint64_t)ctx->n_sm, per / std::max<uint32_t>(1, r->fp.ser[0].nseg));
+            const uint32_t rows = (uint32_t)std::min<uint64_t>(2 * pairs, r->k_stop - r->k_next);
+            FftParams p = r->fp;
+            p.k_lo = r->k_next;
+            p.k_hi = r->k_next + rows;
+            cudaError_t e = launch_corr_fft(p, ctx->n_sm, S->stream);
+            if (e != cudaSuccess) { r->status = cuda_fail(e, "serve launch"); r->cancel = true; }
+            r->k_next += rows;
+            if (r->k_next >= r->k_stop) finishing.push_back(r);
             any = true;
         }
         for (Request* r : finishing) {
@@ -371,10 +461,6 @@ bf_status bf_serve_submit(bf_ctx* ctx, const bf_request* req, uint64_t* ticket)
     bf_opts o;
     bf_status st = resolve_opts(bank, &req->opts, &o);
     if (st) return st;
-    if (o.precision == BF_FFT_FP32) {
-        set_error("the serving loop batches the direct kernels; call bf_correlate for BF_FFT_FP32");
-        return BF_ENOTSUP;
-    }
     o.stream = nullptr;
     std::unique_ptr<Request> r(new Request());
     r->host.resize(req->n);

@@ -35,7 +35,8 @@ def requests():
             (3.0, 0, 2048, "split_bf16", False), (7.5, 100, 1900, "split_bf16", True),
             (2.0, 0, 512, "bf16", False), (12.25, 640, 2048, "split_bf16", False),
             (4.0, 0, 1024, "fp32", True), (1.0 + 1 / 2048, 5, 133, "split_bf16", False),
-            (5.0, 64, 1500, "split_bf16", True), (3.5, 0, 2048, "split_bf16", False)]):
+            (5.0, 64, 1500, "split_bf16", True), (3.5, 0, 2048, "split_bf16", False),
+            (6.0, 17, 2000, "fft_fp32", True), (9.0, 0, 2048, "fft_fp32", False)]):
         n = int(secs * FS)
         x = synth.white(n, rng).astype(np.float32) if i % 2 == 0 else \
             synth.grb_lightcurve(n, FS, rng).astype(np.float32)
