@@ -82,9 +82,8 @@ typedef enum {
                            makes them per call, 16,384 rows at a time,
                            overlapped with the correlation, so any bank size
                            works.  Templates of at most 4096 samples, else
-                           BF_ENOTSUP.  Not in plans; the serving loop runs
-                           it per request with a stored bank.  tile_lags is
-                           ignored.                                          */
+                           BF_ENOTSUP.  Plans and the serving loop run it
+                           with a stored bank.  tile_lags is ignored.        */
 } bf_precision;
 
 /* which sample layouts a bank keeps in device memory (bit flags) */

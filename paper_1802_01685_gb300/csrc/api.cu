@@ -674,6 +674,92 @@ bf_status check_device_status(bf_ctx* ctx)
     return BF_OK;
 }
 
+// The FFT route, in two halves so that a plan can capture the second:
+// fft_prepare makes the twiddle tables and allocates each batch's segment
+// spectra (kept in the result's scratch until it is destroyed) and fills the
+// launch records; fft_launch enqueues kernels only: the segment spectra of
+// every batch of up to MAX_FFT_SER series, then the correlation over all
+// template pairs of the bank range (spectra kept with a stored bank, made
+// chunk by chunk for a generated one).
+bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
+                      const std::vector<PreparedSeries>& prep, bf_result* r, cudaStream_t st, FftCall* c)
+{
+    const size_t S = prep.size(), K = r->K;
+    const uint32_t V = FFT_POINTS - bank->M + 1;
+    const float2* tw = nullptr;
+    cudaError_t e = fft_tables(ctx, st, &tw);
+    if (e != cudaSuccess) return cuda_fail(e, "FFT tables");
+    for (size_t s0 = 0; s0 < S; s0 += MAX_FFT_SER) {
+        const int n = (int)std::min<size_t>(MAX_FFT_SER, S - s0);
+        FftSeriesBatch b{};
+        FftParams p{};
+        uint32_t total = 0;
+        for (int i = 0; i < n; ++i) {
+            const size_t s = s0 + i;
+            const uint32_t nseg = fft_segments(prep[s].L, bank->M);
+            float2* spec = static_cast<float2*>(ctx->mem->alloc((size_t)nseg * (FFT_POINTS / 2) * sizeof(float2)));
+            if (!spec) {
+                set_error("out of device memory for the segment spectra");
+                return BF_ENOMEM;
+            }
+            r->scratch.push_back(spec);
+            b.x[i] = prep[s].x;
+            b.N[i] = prep[s].N;
+            b.spec[i] = spec;
+            b.seg_begin[i] = total;
+            total += nseg;
+            FftSeries& f = p.ser[i];
+            f.spec = spec;
+            f.inv = prep[s].inv;
+            f.vmax = r->packed + s * K;
+            f.sumsq = r->sumsq + s * K;
+            f.rho = s == 0 ? o.rho_out : nullptr;
+            f.sigma_pred = r->sigma_pred ? r->sigma_pred + s * K : nullptr;
+            f.kappa = r->kappa;
+            f.L = prep[s].L;
+            f.nseg = nseg;
+            f.series_id = (uint32_t)s;
+        }
+        b.n = n;
+        b.V = V;
+        b.tw = tw;
+        p.tw = tw;
+        p.k_begin = (uint32_t)bank_row(bank, o.bank_begin);
+        p.k_end = (uint32_t)bank_row(bank, o.bank_end);
+        p.quad = bank->quad ? 1 : 0;
+        p.V = V;
+        p.n_ser = n;
+        p.thr = r->thr;
+        p.cand_cap = r->cand_cap;
+        p.cand = r->cand;
+        p.cand_count = r->cand_count;
+        c->series.push_back(b);
+        c->totals.push_back(total);
+        c->batches.push_back(p);
+    }
+    return BF_OK;
+}
+
+cudaError_t fft_launch(bf_ctx* ctx, const bf_bank* bank, FftCall& c, bf_result* r, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < c.series.size() && e == cudaSuccess; ++i)
+        e = launch_fft_series(c.series[i], c.totals[i], ctx->n_sm, st);
+    if (e != cudaSuccess || c.batches.empty()) return e;
+    const uint32_t r0 = c.batches[0].k_begin, r1 = c.batches[0].k_end;
+    if (bank->generated) return fft_correlate_chunked(ctx, bank, c.batches, r0, r1, r->scratch, st);
+    // spectra kept with the bank
+    for (FftParams& p : c.batches) {
+        p.hspec = bank->fspec;
+        p.hrow0 = 0;
+        p.k_lo = r0;
+        p.k_hi = r1;
+        e = launch_corr_fft(p, ctx->n_sm, st);
+        if (e != cudaSuccess) break;
+    }
+    return e;
+}
+
 }  // namespace bfi
 
 using namespace bfi;
@@ -963,79 +1049,6 @@ bf_status bf_bank_read(const bf_bank* b, size_t c0, size_t nc, float* out)
     return BF_OK;
 }
 
-// The FFT route: per batch of up to MAX_FFT_SER series, the segment spectra
-// (kept in the result's scratch until it is destroyed), then one correlation
-// launch over all template pairs of the bank range.
-cudaError_t correlate_fft(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
-                          const std::vector<PreparedSeries>& prep, bf_result* r, cudaStream_t st)
-{
-    const size_t S = prep.size(), K = r->K;
-    const uint32_t V = FFT_POINTS - bank->M + 1;
-    const float2* tw = nullptr;
-    cudaError_t e = fft_tables(ctx, st, &tw);
-    std::vector<FftParams> batches;
-    for (size_t s0 = 0; s0 < S && e == cudaSuccess; s0 += MAX_FFT_SER) {
-        const int n = (int)std::min<size_t>(MAX_FFT_SER, S - s0);
-        FftSeriesBatch b{};
-        FftParams p{};
-        uint32_t total = 0;
-        for (int i = 0; i < n; ++i) {
-            const size_t s = s0 + i;
-            const uint32_t nseg = fft_segments(prep[s].L, bank->M);
-            float2* spec = static_cast<float2*>(ctx->mem->alloc((size_t)nseg * (FFT_POINTS / 2) * sizeof(float2)));
-            if (!spec) {
-                set_error("out of device memory for the segment spectra");
-                return cudaErrorMemoryAllocation;
-            }
-            r->scratch.push_back(spec);
-            b.x[i] = prep[s].x;
-            b.N[i] = prep[s].N;
-            b.spec[i] = spec;
-            b.seg_begin[i] = total;
-            total += nseg;
-            FftSeries& f = p.ser[i];
-            f.spec = spec;
-            f.inv = prep[s].inv;
-            f.vmax = r->packed + s * K;
-            f.sumsq = r->sumsq + s * K;
-            f.rho = s == 0 ? o.rho_out : nullptr;
-            f.sigma_pred = r->sigma_pred ? r->sigma_pred + s * K : nullptr;
-            f.kappa = r->kappa;
-            f.L = prep[s].L;
-            f.nseg = nseg;
-            f.series_id = (uint32_t)s;
-        }
-        b.n = n;
-        b.V = V;
-        b.tw = tw;
-        p.tw = tw;
-        p.k_begin = (uint32_t)bank_row(bank, o.bank_begin);
-        p.k_end = (uint32_t)bank_row(bank, o.bank_end);
-        p.quad = bank->quad ? 1 : 0;
-        p.V = V;
-        p.n_ser = n;
-        p.thr = r->thr;
-        p.cand_cap = r->cand_cap;
-        p.cand = r->cand;
-        p.cand_count = r->cand_count;
-        e = launch_fft_series(b, total, ctx->n_sm, st);
-        batches.push_back(p);
-    }
-    if (e != cudaSuccess) return e;
-    const uint32_t r0 = (uint32_t)bank_row(bank, o.bank_begin), r1 = (uint32_t)bank_row(bank, o.bank_end);
-    if (bank->generated) return fft_correlate_chunked(ctx, bank, batches, r0, r1, r->scratch, st);
-    // spectra kept with the bank
-    for (FftParams& p : batches) {
-        p.hspec = bank->fspec;
-        p.hrow0 = 0;
-        p.k_lo = r0;
-        p.k_hi = r1;
-        e = launch_corr_fft(p, ctx->n_sm, st);
-        if (e != cudaSuccess) break;
-    }
-    return e;
-}
-
 bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* series,
                        const size_t* lengths, size_t n_series, double fs, const bf_opts* opts,
                        bf_result** out)
@@ -1112,6 +1125,11 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
         st = bank_fft_spectra(ctx, const_cast<bf_bank*>(bank), strm);
         if (st) return st;
     }
+    FftCall fc;
+    if (fft) {
+        st = fft_prepare(ctx, bank, o, prep, r, strm, &fc);
+        if (st) return st;
+    }
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (sync) {
@@ -1124,7 +1142,7 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
     int lt = o.precision == BF_FP32 ? SIMT_TILE_L : fft ? 0 : o.tile_lags;
     if (lt == 0 && !fft && !bank->generated) lt = choose_lag_tile(ctx, segs[0], o.precision, strm);
     r->tile_lags = lt;
-    cudaError_t e = fft ? correlate_fft(ctx, bank, o, prep, r, strm)
+    cudaError_t e = fft ? fft_launch(ctx, bank, fc, r, strm)
                     : bank->generated
                         ? correlate_generated(ctx, bank, o, segs, r, strm, lt)
                         : launch_segments(ctx, segs, o.precision, r->thr, r->cand, r->cand_count,

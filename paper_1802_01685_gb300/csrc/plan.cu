@@ -63,10 +63,6 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
         set_error("plans take BF_SIGMA_WHITE tails (the Parseval predictor runs cuFFT outside the graph)");
         return BF_ENOTSUP;
     }
-    if (o.precision == BF_FFT_FP32) {
-        set_error("plans run the direct kernels; call bf_correlate for BF_FFT_FP32");
-        return BF_ENOTSUP;
-    }
     o.stream = nullptr;
     o.rho_out = nullptr;
     for (size_t s = 0; s < n_series; ++s)
@@ -95,27 +91,41 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
         ids.push_back((uint32_t)s);
         p->r->correlations += (double)p->prep[s].L * (double)p->r->K * (bank->quad ? 2.0 : 1.0);
     }
+    const bool fft = o.precision == BF_FFT_FP32;
     std::vector<Seg> segs;
-    build_segments(pptr, ids, bank, o.bank_begin, o.bank_end, o.precision, p->r->packed,
-                   p->r->sumsq, p->r->K, segs);
-    cudaError_t e = cudaStreamSynchronize(strm);
-    if (e == cudaSuccess) e = corr_tc_set_attributes();
-    if (e != cudaSuccess) return cuda_fail(e, "plan set-up");
-    // the tile shape is fixed before capture (the autotuner times launches)
-    int lt = o.precision == BF_FP32 ? SIMT_TILE_L
+    FftCall fc;
+    int lt = 0;
+    if (fft) {
+        // everything that allocates or synchronises happens before the capture:
+        // the bank's spectra, the twiddle tables, the segment-spectra buffers
+        st = bank_fft_spectra(ctx, const_cast<bf_bank*>(bank), strm);
+        if (st == BF_OK) st = fft_prepare(ctx, bank, o, p->prep, p->r, strm, &fc);
+        if (st) return st;
+        cudaError_t es = cudaStreamSynchronize(strm);
+        if (es != cudaSuccess) return cuda_fail(es, "plan set-up");
+    } else {
+        build_segments(pptr, ids, bank, o.bank_begin, o.bank_end, o.precision, p->r->packed,
+                       p->r->sumsq, p->r->K, segs);
+        cudaError_t es = cudaStreamSynchronize(strm);
+        if (es == cudaSuccess) es = corr_tc_set_attributes();
+        if (es != cudaSuccess) return cuda_fail(es, "plan set-up");
+        // the tile shape is fixed before capture (the autotuner times launches)
+        lt = o.precision == BF_FP32 ? SIMT_TILE_L
                                     : (o.tile_lags ? o.tile_lags : choose_lag_tile(ctx, segs[0], o.precision, strm));
+    }
     p->r->tile_lags = lt;
 
     // capture one search
     const uint64_t l0 = g_launches.load();
-    e = cudaStreamBeginCapture(strm, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(strm, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     cudaError_t ec = clear_result(p->r, strm);
     for (size_t s = 0; s < n_series && ec == cudaSuccess; ++s)
         ec = prepare_series_kernels(p->prep[s], bank->M, o.precision, strm);
     if (ec == cudaSuccess)
-        ec = launch_segments(ctx, segs, o.precision, p->r->thr, p->r->cand, p->r->cand_count,
-                             p->r->cand_cap, strm, nullptr, lt);
+        ec = fft ? fft_launch(ctx, bank, fc, p->r, strm)
+                 : launch_segments(ctx, segs, o.precision, p->r->thr, p->r->cand, p->r->cand_count,
+                                   p->r->cand_cap, strm, nullptr, lt);
     bf_status fst = BF_OK;
     if (ec == cudaSuccess) fst = finalize_result(ctx, bank, p->r, strm);
     cudaGraph_t graph = nullptr;

@@ -76,6 +76,16 @@ void serve_shutdown(bf_ctx* ctx);
 bf_status bank_power_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st);
 // template half spectra of the FFT route, computed once per bank
 bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st);
+// one call of the FFT route: per batch of series, the segment-spectra job and
+// the correlation record (api.cu)
+struct FftCall {
+    std::vector<FftSeriesBatch> series;
+    std::vector<uint32_t> totals;
+    std::vector<FftParams> batches;
+};
+bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
+                      const std::vector<PreparedSeries>& prep, bf_result* r, cudaStream_t st, FftCall* c);
+cudaError_t fft_launch(bf_ctx* ctx, const bf_bank* bank, FftCall& c, bf_result* r, cudaStream_t st);
 // the context's twiddle tables of the FFT route (built on first use)
 cudaError_t fft_tables(bf_ctx* ctx, cudaStream_t st, const float2** out);
 bf_status predict_sigma(bf_ctx* ctx, const bf_bank* bank, const PreparedSeries& ps, size_t k_begin,

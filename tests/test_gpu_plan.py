@@ -27,7 +27,7 @@ def outputs(res, n, want_map):
     return [bf.bf_result_copy_to_host(res, s, want_hist=True, want_map=want_map) for s in range(n)]
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "fft_fp32"])
 def test_plan_replays_equal_correlate(setup, prec):
     ctx, bank, spec = setup
     lens = [2048, 5000, 9000, 2049]
