@@ -5,7 +5,8 @@
 // reduced to [-1/2, 1/2) before the cosine, which then runs in FP32 (the
 // reduction is where FP64 is needed; after it FP32 holds the phase to ~1e-7
 // of a cycle).  The taper is sin^2(pi (j + 1/2) / M_D) in FP32; the unit norm is
-// an FP64 sum over the template.
+// an FP64 sum over the template, applied in FP32, where the hi/lo split of
+// the tensor-core layout is made too.
 //
 // GB300 runs FP64 at a small fraction of its FP32 rate, so the power-law phase
 // avoids a full FP64 pow: (1 - t/t_c)^(5/8) starts from the FP32 powf value and
@@ -103,7 +104,8 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
                 if (j < 0 || j >= p.MD) return 0.f;
                 const double c = d_cycles(p.track, k1, k2, (double)j * inv_fs);
                 const double fr = c - rint(c);             // [-1/2, 1/2]
-                const float cs = sine ? sinpif((float)(2.0 * fr)) : cospif((float)(2.0 * fr));
+                const float f2 = 2.f * (float)fr;          // exact doubling in FP32
+                const float cs = sine ? sinpif(f2) : cospif(f2);
                 const float sn = sinpif(((float)j + 0.5f) * inv_md);
                 return sn * sn * cs;
             };
@@ -121,14 +123,17 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
     __syncthreads();
     double tot = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-    const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
+    // the samples g are FP32, so scaling and splitting them in FP32 loses only
+    // the last ulp of h (the split's own error is 2^-17); GB300's FP64 rate is
+    // kept for the phase
+    const float inv = tot > 0.0 ? (float)(1.0 / sqrt(tot)) : 0.f;
 
     for (uint32_t m = threadIdx.x; m < M_pad; m += blockDim.x) {
-        double h = m < M_s ? (double)g[m] * inv : 0.0;
-        if (f32) f32[(size_t)k * M_pad + m] = (float)h;
+        const float h = m < M_s ? g[m] * inv : 0.f;
+        if (f32) f32[(size_t)k * M_pad + m] = h;
         if (hi) {
-            __nv_bfloat16 bh = __double2bfloat16(h);
-            __nv_bfloat16 bl = __double2bfloat16(h - (double)__bfloat162float(bh));
+            __nv_bfloat16 bh = __float2bfloat16_rn(h);
+            __nv_bfloat16 bl = __float2bfloat16_rn(h - __bfloat162float(bh));   // exact difference
             size_t off = tc_offset(k, m, n_kb);
             *reinterpret_cast<__nv_bfloat16*>(hi + off) = bh;
             *reinterpret_cast<__nv_bfloat16*>(lo + off) = bl;
