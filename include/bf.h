@@ -446,6 +446,18 @@ bf_status bf_serve_stats_get(bf_ctx* ctx, bf_serve_stats* out);
 const char* bf_last_error(void);
 const char* bf_status_string(bf_status s);
 int bf_abi_version(void);
+
+/* Self-test of the bounded waits that guard the tensor-core kernel's
+ * pipeline (every mbarrier wait gives up after a time limit, records a code
+ * in the context's device status word and lets the kernel drain and return,
+ * so that no wait can hang the GPU).  Runs the same wait on an mbarrier that
+ * receives its one arrival when `signal` is nonzero and never otherwise, with
+ * a limit of limit_us microseconds (at most 1,000,000), synchronously on the
+ * context stream.  Returns BF_OK when the arrival came, BF_EDEVICE when the
+ * wait ran out (the status word is then cleared and the context stays
+ * usable), BF_EINVAL for a limit out of range.  *waited_us (if not NULL) gets
+ * the time the wait took. */
+bf_status bf_selftest_wait(bf_ctx* ctx, int signal, uint32_t limit_us, double* waited_us);
 /* Number of kernels this library has launched in the process so far (all
  * contexts); a diagnostic for benchmarks.  The paper has no counterpart. */
 uint64_t bf_kernel_launches(void);

@@ -155,6 +155,7 @@ def load() -> C.CDLL:
             "bf_last_error": (C.c_char_p, []),
             "bf_status_string": (C.c_char_p, [i]),
             "bf_abi_version": (i, []),
+            "bf_selftest_wait": (i, [p, i, C.c_uint32, P(d)]),
             "bf_kernel_launches": (u64, []),
         }
         for name, (res, args) in sig.items():
@@ -493,6 +494,14 @@ def bf_last_error() -> str:
 
 def bf_status_string(st: int) -> str:
     return load().bf_status_string(st).decode()
+
+
+def bf_selftest_wait(ctx: int, signal: bool, limit_us: int) -> float:
+    """Runs the bounded-wait self-test; returns the microseconds waited and
+    raises BFError (BF_EDEVICE) when the wait ran out."""
+    w = C.c_double()
+    _check(load().bf_selftest_wait(ctx, int(bool(signal)), int(limit_us), C.byref(w)))
+    return w.value
 
 
 def bf_abi_version() -> int:

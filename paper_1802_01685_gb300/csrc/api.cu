@@ -769,6 +769,24 @@ extern "C" {
 
 const char* bf_last_error(void) { return g_err.c_str(); }
 int bf_abi_version(void) { return BF_ABI_VERSION; }
+
+bf_status bf_selftest_wait(bf_ctx* ctx, int signal, uint32_t limit_us, double* waited_us)
+{
+    if (!ctx) { set_error("NULL context"); return BF_EINVAL; }
+    if (limit_us == 0 || limit_us > 1000000u) { set_error("limit_us must be in [1, 1e6]"); return BF_EINVAL; }
+    cudaSetDevice(ctx->device);
+    std::lock_guard<std::mutex> g(ctx->launch_mu);
+    unsigned long long* w = static_cast<unsigned long long*>(ctx->mem->alloc(sizeof(unsigned long long)));
+    if (!w) { set_error("out of device memory"); return BF_ENOMEM; }
+    cudaError_t e = launch_wait_selftest(ctx->d_err, signal, (uint64_t)limit_us * 1000ull, w, ctx->stream);
+    unsigned long long ns = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, w, sizeof ns, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    ctx->mem->release(w);
+    if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+    if (waited_us) *waited_us = (double)ns / 1e3;
+    return check_device_status(ctx);
+}
 uint64_t bf_kernel_launches(void) { return g_launches.load(); }
 
 const char* bf_status_string(bf_status s)

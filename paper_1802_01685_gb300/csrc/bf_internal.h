@@ -143,6 +143,8 @@ bf_status cuda_fail(cudaError_t e, const char* what);
 inline void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 cudaError_t launch_corr_simt(const CorrParams& p, cudaStream_t s);
+cudaError_t launch_wait_selftest(int* err, int signal, uint64_t limit_ns, unsigned long long* waited,
+                                 cudaStream_t st);
 cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int lt, int n_sm, cudaStream_t s);
 // sets the tensor-core kernels' shared-memory attribute (outside graph capture)
 cudaError_t corr_tc_set_attributes();

@@ -114,7 +114,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 
 // Bounded wait.  Returns false on timeout or when another role aborted.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
-                                          volatile int* abort_flag, bool honour_abort = true)
+                                          volatile int* abort_flag, bool honour_abort = true,
+                                          uint64_t limit_ns = TIMEOUT_NS)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
@@ -122,7 +123,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63) == 0) {
             if (honour_abort && *abort_flag) return false;
-            if (globaltimer() - t0 > TIMEOUT_NS) return false;
+            if (globaltimer() - t0 > limit_ns) return false;
         }
     }
 }
@@ -624,6 +625,38 @@ cudaError_t corr_tc_set_attributes()
     if (e == cudaSuccess) e = set_attr<3, 256>();
     if (e == cudaSuccess) g_attr_done = true;
     return e;
+}
+
+// Self-test of the bounded wait above: one mbarrier expecting one arrival,
+// which thread 0 of warp 1 makes only when `signal` is set, and warp 0 waiting
+// on it with the given limit.  A timeout is recorded in the status word as in
+// the correlation kernel; waited[0] gets the nanoseconds spent waiting.
+__global__ void k_wait_selftest(int* err, int signal, uint64_t limit_ns, unsigned long long* waited)
+{
+    __shared__ __align__(8) uint64_t bar_storage;
+    __shared__ int abort_word;
+    const uint32_t bar = smem_u32(&bar_storage);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        abort_word = 0;
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 32 && signal) mbar_arrive(bar);
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = globaltimer();
+        const bool ok = mbar_wait(bar, 0, reinterpret_cast<volatile int*>(&abort_word), true, limit_ns);
+        *waited = globaltimer() - t0;
+        if (!ok) record_error(err, DEV_TIMEOUT_FULL);
+    }
+}
+
+cudaError_t launch_wait_selftest(int* err, int signal, uint64_t limit_ns, unsigned long long* waited,
+                                 cudaStream_t st)
+{
+    count_launches(1);
+    k_wait_selftest<<<1, 64, 0, st>>>(err, signal, limit_ns, waited);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int lt, int n_sm, cudaStream_t st)
