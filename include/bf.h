@@ -40,6 +40,12 @@
 extern "C" {
 #endif
 
+/* The library is built with hidden symbol visibility; the declarations below
+ * are its only exports. */
+#if defined(BF_BUILDING_LIBRARY) && defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
 #define BF_ABI_VERSION 1
 
 typedef enum {
@@ -461,6 +467,10 @@ bf_status bf_selftest_wait(bf_ctx* ctx, int signal, uint32_t limit_us, double* w
 /* Number of kernels this library has launched in the process so far (all
  * contexts); a diagnostic for benchmarks.  The paper has no counterpart. */
 uint64_t bf_kernel_launches(void);
+
+#if defined(BF_BUILDING_LIBRARY) && defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
 
 #ifdef __cplusplus
 }

@@ -23,8 +23,10 @@ SOURCES = ["api.cu", "serve.cu", "bank.cu", "prep.cu", "corr_simt.cu", "corr_tc.
 HEADERS = ["bf_internal.h", "runtime.h", "corr_common.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# hidden visibility: only the declarations of include/bf.h are exported
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                     "-Xcompiler", "-Wall", "-I", INCLUDE, "-I", CSRC]
+                     "-Xcompiler", "-Wall", "-Xcompiler", "-fvisibility=hidden",
+                     "-DBF_BUILDING_LIBRARY", "-I", INCLUDE, "-I", CSRC]
 
 
 def _nvcc() -> str:
