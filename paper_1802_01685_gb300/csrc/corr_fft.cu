@@ -638,7 +638,8 @@ cudaError_t fft_correlate_chunked(bf_ctx* ctx, const bf_bank* bank, std::vector<
     Allocator& mem = *ctx->mem;
     float2* slot[2] = {nullptr, nullptr};
     // the ring outlives this call's launches: the result releases it
-    float* scratch = static_cast<float*>(mem.alloc(FFT_SYNTH_ROWS * FN * sizeof(float)));
+    const size_t synth_rows = std::min(FFT_SYNTH_ROWS, chunk);           // both even
+    float* scratch = static_cast<float*>(mem.alloc(synth_rows * FN * sizeof(float)));
     keep.push_back(scratch);
     for (int i = 0; i < 2 && i < (int)n_chunks; ++i) {
         slot[i] = static_cast<float2*>(mem.alloc(chunk * FH * sizeof(float2)));
@@ -663,7 +664,7 @@ cudaError_t fft_correlate_chunked(bf_ctx* ctx, const bf_bank* bank, std::vector<
         const uint32_t c1 = (uint32_t)std::min<size_t>(c0 + chunk, row_end);
         if (c >= 2) e = cudaStreamWaitEvent(ctx->aux, used[sl], 0);
         if (e == cudaSuccess)
-            e = template_spectra(bank, c0, c1 - c0, scratch, FFT_SYNTH_ROWS, tw, slot[sl], ctx->n_sm, ctx->aux);
+            e = template_spectra(bank, c0, c1 - c0, scratch, synth_rows, tw, slot[sl], ctx->n_sm, ctx->aux);
         if (e == cudaSuccess) e = cudaEventRecord(made[sl], ctx->aux);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, made[sl], 0);
         for (FftParams& p : batches) {

@@ -183,3 +183,30 @@ def test_generated_bank_in_chunks(ctx):
     assert np.abs(s["sigma"].astype(np.float64) - g["sigma"]).max() <= 2 * TOL[PREC]
     bf.bf_bank_destroy(stored)
     bf.bf_bank_destroy(gen)
+
+
+def test_spectra_over_the_budget():
+    """Template spectra that do not fit the context's HBM budget give
+    BF_ENOMEM and leave the context usable; a generated bank needs only its
+    ring and goes through."""
+    import __graft_entry__
+    __graft_entry__.build()
+    cfg = bf.bf_config_default()
+    cfg.hbm_budget = 256 << 20                      # 256 MiB
+    ctx = bf.bf_init(cfg)
+    try:
+        fs, M = 2048.0, 2048
+        spec = synth.grid_spec([synth.LINEAR], [synth.ASC, synth.DESC], [1.0], 20.0, 1000.0, 64, 64)
+        x = np.random.default_rng(31).standard_normal(10000).astype(np.float32)
+        stored = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_FP32)   # 8192 x 2048 floats
+        with pytest.raises(bf.BFError) as e:                # 8192 x 32 KiB of spectra
+            run(ctx, stored, [x], fs, PREC)
+        assert e.value.status == bf.BF_ENOMEM
+        a = run(ctx, stored, [x], fs, "fp32", bank_end=512)[0][0]
+        bf.bf_bank_destroy(stored)
+        gen = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_GENERATED)
+        b = run(ctx, gen, [x], fs, PREC, bank_end=512)[0][0]
+        assert np.abs(a["max"].astype(np.float64) - b["max"]).max() <= 2 * TOL[PREC]
+        bf.bf_bank_destroy(gen)
+    finally:
+        bf.bf_destroy(ctx)
