@@ -179,19 +179,11 @@ __device__ __forceinline__ void dft16(float (&r)[16], float (&i)[16])
 // thread j reads in[j + 512 r], twiddles by e^{SIGN 2 pi i r (j mod NS) / (16 NS)},
 // takes the 16-point DFT and writes out[(j / NS) 16 NS + j mod NS + q NS].
 // Padded addresses (i + i/16) are a per-thread base plus constant offsets.
+// The second half of a pass, from the 16 inputs already in registers.
 template <int SIGN, int NS>
-__device__ __forceinline__ void pass16(const Smem& m)
+__device__ __forceinline__ void pass16_from(const Smem& m, float (&vr)[16], float (&vi)[16])
 {
     const int j = threadIdx.x;
-    const int rd = j + (j >> 4);
-    float vr[16], vi[16];
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const float2 v = m.z[rd + ROW * r];
-        vr[r] = v.x;
-        vi[r] = v.y;
-    }
-    __syncthreads();
     if (NS > 1) {
         const int k = j % NS;
         const float2* t = m.tw + (NS == 16 ? TW2 : TW3) + k;
@@ -210,6 +202,22 @@ __device__ __forceinline__ void pass16(const Smem& m)
         m.z[wb + off] = make_float2(vr[p], vi[p]);
     }
     __syncthreads();
+}
+
+template <int SIGN, int NS>
+__device__ __forceinline__ void pass16(const Smem& m)
+{
+    const int j = threadIdx.x;
+    const int rd = j + (j >> 4);
+    float vr[16], vi[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const float2 v = m.z[rd + ROW * r];
+        vr[r] = v.x;
+        vi[r] = v.y;
+    }
+    __syncthreads();
+    pass16_from<SIGN, NS>(m, vr, vi);
 }
 
 template <int SIGN>
@@ -402,12 +410,19 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
         }
         cp_async_wait<1>();                         // this segment's spectrum
         __syncthreads();
+        // Z = X conj(H_a) + i X conj(H_b).  The first pass of the FFT reads
+        // Z[tid + 512 r]: for r < 8 those are this thread's own bins, kept in
+        // registers; for r >= 8 they are Z[F - f] of the mirror thread 512 - tid
+        // (thread 0: its own bins and the Nyquist term), exchanged through
+        // shared memory.
+        float vr[16], vi[16];
 #pragma unroll
         for (int i = 0; i < FBINS; ++i) {
             const float2 x = m.x[tid + FT * i];
             if (tid == 0 && i == 0) {
                 // DC (x.x) and Nyquist (x.y): real products
-                m.z[0] = make_float2(x.x * ha[0].x, x.x * hb[0].x);
+                vr[0] = x.x * ha[0].x;
+                vi[0] = x.x * hb[0].x;
                 m.z[UPPER] = make_float2(x.y * ha[0].y, x.y * hb[0].y);
             } else {
                 // Y = X conj(H); Z[f] = Ya + i Yb, Z[F - f] = conj(Ya) + i conj(Yb)
@@ -415,14 +430,24 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
                 const float yai = x.y * ha[i].x - x.x * ha[i].y;
                 const float ybr = x.x * hb[i].x + x.y * hb[i].y;
                 const float ybi = x.y * hb[i].x - x.x * hb[i].y;
-                m.z[rd + ROW * i] = make_float2(yar - ybi, yai + ybr);
+                vr[i] = yar - ybi;
+                vi[i] = yai + ybr;
                 m.z[rv - ROW * i] = make_float2(yar + ybi, ybr - yai);
             }
         }
         __syncthreads();
+#pragma unroll
+        for (int r = FBINS; r < 16; ++r) {
+            const float2 v = m.z[rd + ROW * r];
+            vr[r] = v.x;
+            vi[r] = v.y;
+        }
         if (np < n_pairs) stage_spectrum(m, p.ser[ns].spec + (size_t)nj * FH);
         cp_async_commit();
-        fft_passes<1>(m);
+        __syncthreads();                            // every exchange read before pass 1 writes
+        pass16_from<1, 1>(m, vr, vi);
+        pass16<1, 16>(m);
+        pass16<1, 256>(m);
         cp_async_wait<1>();                         // this segment's window norms
         __syncthreads();
         float pa = 0.f, pb = 0.f;
