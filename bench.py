@@ -48,7 +48,7 @@ UNIT = "correlations/s"
 # Keyed by (hash of the kernel source the counters were taken on, lags per
 # tile); a changed kernel reports null until it is captured again.
 TRAFFIC_BYTES_PER_TEMPLATE_TILE = {
-    ("4269de39282eb06d", 256): (272.01e6 + 3.93e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
+    ("adad15c72ececdc6", 256): (272.56e6 + 4.09e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
 }
 
 
