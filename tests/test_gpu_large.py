@@ -131,3 +131,55 @@ def test_long_templates(ctx):
         err = np.abs(rho.cpu().numpy() - ref["rho"]).max()
         assert err <= TOL[prec], (prec, err)
     bf.bf_bank_destroy(bank)
+
+
+def test_full_bank_full_size_sampled(ctx):
+    """The 8,640,000-template bank at full size (32 s at 2048 Hz), generated on
+    the fly, on the tensor-core path and the FFT route (its spectra made in
+    chunks); 16 templates spread over the bank recomputed by the oracle; the
+    two routes against each other on every template."""
+    w = synth.full_bank()
+    fs, M = w["fs"], w["M"]
+    x = w["series"][0]
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_GENERATED)
+    K = bf.bf_bank_size(bank)
+    assert K == 8640000
+    a = run(ctx, bank, [x], fs, "split_bf16", want_hist=True)[0][0]
+    b = run(ctx, bank, [x], fs, "fft_fp32", want_hist=True)[0][0]
+    p = oracle_params(w["grid"])
+    idx = np.linspace(0, K - 1, 16).astype(np.int64)
+    ref = oracle.search(x, fs, subset(p, idx), M, want_rho=True)
+    for prec, g in (("split_bf16", a), ("fft_fp32", b)):
+        gs = {k: v[idx] for k, v in g.items() if k in ("max", "argmax", "sigma")}
+        check_maxima(gs, ref, ref["rho"], TOL[prec], f"full bank {prec}")
+        check_sigma(gs, ref, TOL[prec])
+        assert g["hist"].sum() == K
+    assert np.abs(a["max"].astype(np.float64) - b["max"]).max() <= 2 * TOL["split_bf16"]
+    bf.bf_bank_destroy(bank)
+
+
+def test_grb_batch_all_series_sampled(ctx):
+    """All 42 light curves at full length (9.3 M samples) in one batched
+    launch against a 2048-template slice of the full 2^20 bank; 16 templates
+    of the slice recomputed by the oracle on every series; the mean over
+    series."""
+    w = synth.grb_batch()
+    fs, M = w["fs"], w["M"]
+    xs = w["series"]
+    assert len(xs) == 42
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16)
+    assert bf.bf_bank_size(bank) == 2 ** 20
+    b0, b1 = 600000, 602048
+    outs, mean, info = run(ctx, bank, xs, fs, "split_bf16", bank_begin=b0, bank_end=b1)
+    assert info.correlations == sum(len(x) - M + 1 for x in xs) * (b1 - b0)
+    p = oracle_params(w["grid"])
+    idx = np.linspace(0, b1 - b0 - 1, 16).astype(np.int64)
+    sub = subset(p, idx + b0)
+    ref_max = []
+    for s, (g, x) in enumerate(zip(outs, xs)):
+        r = oracle.search(x, fs, sub, M, want_rho=True)      # one series at a time
+        gs = {k: v[idx] for k, v in g.items() if k in ("max", "argmax", "sigma")}
+        check_maxima(gs, r, r["rho"], TOL["split_bf16"], f"series {s}")
+        ref_max.append(r["max"])
+    np.testing.assert_allclose(mean[idx], np.mean(ref_max, axis=0), atol=TOL["split_bf16"])
+    bf.bf_bank_destroy(bank)
