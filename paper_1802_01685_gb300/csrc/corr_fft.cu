@@ -622,8 +622,8 @@ bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
 
 uint32_t fft_segments(uint32_t L, uint32_t M)
 {
-    const uint32_t V = FFT_POINTS - M + 1;
-    return (L + V - 1) / V;
+    const uint64_t V = FFT_POINTS - M + 1;
+    return (uint32_t)(((uint64_t)L + V - 1) / V);          // L may be close to 2^32
 }
 
 cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, int n_sm, cudaStream_t st)

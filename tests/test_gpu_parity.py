@@ -451,3 +451,34 @@ def test_coincidence_pseudo_spectra(ctx):
         bf.bf_result_coincidence(res, 0, 1)                          # no maps
     bf.bf_result_destroy(res)
     bf.bf_bank_destroy(bank)
+
+
+def test_concurrent_calls_from_threads(ctx, tiny):
+    """Several host threads search through one context at once (tensor-core,
+    SIMT and FFT routes, and a fit); every result equals the same call made
+    alone."""
+    import threading
+    w, bank, _, _ = tiny
+    x, fs = w["series"][0], w["fs"]
+    precs = ["split_bf16", "fp32", "fft_fp32", "split_bf16"]
+    alone = [run(ctx, bank, [x], fs, p)[0][0] for p in precs]
+    got = [None] * len(precs)
+    errors = []
+
+    def worker(i):
+        try:
+            for _ in range(3):
+                got[i] = run(ctx, bank, [x], fs, precs[i])[0][0]
+        except Exception as e:                     # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(len(precs))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for a, g in zip(alone, got):
+        np.testing.assert_array_equal(g["max"], a["max"])
+        np.testing.assert_array_equal(g["argmax"], a["argmax"])
+        np.testing.assert_array_equal(g["hist"], a["hist"])
