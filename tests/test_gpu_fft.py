@@ -210,3 +210,30 @@ def test_spectra_over_the_budget():
         bf.bf_bank_destroy(gen)
     finally:
         bf.bf_destroy(ctx)
+
+
+@pytest.mark.parametrize("fs,T", [(64.0, 1.0), (2.0, 1.0), (1000.0, 1.0), (4096.0, 1.0)])
+def test_template_lengths(ctx, fs, T):
+    """Template lengths from 2 to 4096 samples (up to 8191 lags per
+    segment), series of one segment, of several and of exactly one lag."""
+    M = int(round(T * fs))
+    ny = fs / 2
+    chirps = [(bf.BF_LINEAR, bf.BF_ASC, 0.1 * ny, 0.8 * ny, 1.0 * T),
+              (bf.BF_POWERLAW, bf.BF_DESC, 0.05 * ny, 0.6 * ny, 0.7 * T),
+              (bf.BF_LINEAR, bf.BF_BOTH, 0.2 * ny, 0.5 * ny, 0.9 * T)]
+    if M < 8:
+        chirps = chirps[:1]
+    bank = bf.bf_bank_create(ctx, chirps, fs, T)
+    p = dict(track=np.array([c[0] for c in chirps], np.int32), sense=np.array([c[1] for c in chirps], np.int32),
+             f_lo=np.array([c[2] for c in chirps]), f_hi=np.array([c[3] for c in chirps]),
+             D=np.array([c[4] for c in chirps]))
+    rng = np.random.default_rng(M)
+    for n in (M, M + 5, 3 * F + 17):
+        x = rng.standard_normal(n).astype(np.float32)
+        ref = oracle.search(x, fs, p, M, want_rho=True)
+        K, L = ref["rho"].shape
+        rho = torch.zeros((K, L), dtype=torch.float32, device="cuda")
+        outs, _, _ = run(ctx, bank, [x], fs, PREC, rho_out=rho)
+        assert np.abs(rho.cpu().numpy() - ref["rho"]).max() <= TOL[PREC], (M, n)
+        check_maxima(outs[0], ref, ref["rho"], TOL[PREC], f"M={M} n={n}")
+    bf.bf_bank_destroy(bank)
