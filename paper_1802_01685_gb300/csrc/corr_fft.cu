@@ -15,19 +15,23 @@
 // argmax, sum rho^2, tails).
 //
 // GB300 layout of the work:
-//  * template spectra are computed once per bank (two real templates per
-//    complex FFT) and kept in HBM as half spectra: 4096 complex values per
-//    template, bin 0 carrying the DC and Nyquist terms (both real);
+//  * template spectra (two real templates per complex FFT) are half spectra
+//    of 4096 complex values per template, bin 0 carrying the DC and Nyquist
+//    terms (both real).  A stored bank keeps them in HBM, made once; a
+//    generated bank makes them per call, 16,384 rows at a time, in a two-slot
+//    ring on the auxiliary stream;
 //  * each segment spectrum is computed once per call; all of them stay in L2
 //    and reach shared memory by asynchronous copies (cp.async) issued one
 //    segment ahead, together with the segment's window norms;
 //  * one CTA of 512 threads owns a pair of templates (a, b) at a time and
 //    holds their spectra in registers (8 bins per thread).  For every segment
 //    it forms Z = X conj(H_a) + i X conj(H_b) over all F bins (Hermitian
-//    symmetry fills the upper half), runs one inverse complex FFT in shared
-//    memory and reads c_a = Re z, c_b = Im z -- two real correlations per
-//    transform.  The last radix-2 stage of the FFT is fused into the
-//    epilogue, so the filter output never reaches HBM.
+//    symmetry fills the upper half; each thread keeps the half that its
+//    first FFT pass reads in registers), runs one inverse complex FFT in
+//    shared memory and reads c_a = Re z, c_b = Im z -- two real correlations
+//    per transform (or, for a quadrature pair, |z|).  The last radix-2 stage
+//    of the FFT is fused into the epilogue, so the filter output never
+//    reaches HBM.
 //  * The FFT is a Stockham autosort FFT with three radix-16 passes (each
 //    thread one 16-point DFT per pass, in registers) and a final radix-2
 //    stage; the work array holds complex values with index i stored at
