@@ -48,7 +48,7 @@ UNIT = "correlations/s"
 # Keyed by (hash of the kernel source the counters were taken on, lags per
 # tile); a changed kernel reports null until it is captured again.
 TRAFFIC_BYTES_PER_TEMPLATE_TILE = {
-    ("adad15c72ececdc6", 256): (272.56e6 + 4.09e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
+    ("e61fa4dee945568f", 256): (272.05e6 + 3.99e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
 }
 
 
@@ -271,6 +271,11 @@ def run_ours(args, rank, world, local):
     if not args.no_fft:
         fft = run_fft(ctx, bf, w, xs, ctrl, corr_per_step)
 
+    # the split-FP16 tensor-core route on the same step
+    f16 = None
+    if not args.no_fp16:
+        f16 = run_split_fp16(ctx, bf, w, xs, ctrl, corr_per_step)
+
     # oracle on a bounded sample, and accuracy of the timed path on that sample
     cpu = None
     accuracy = None
@@ -304,7 +309,7 @@ def run_ours(args, rank, world, local):
                                       "coincidence pseudo-spectra (delta f 50 Hz)"]},
         "stage_ms": {k: round(float(np.mean(v)), 2) for k, v in stage_ms.items()},
         "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
-        "fp32_path": fp32, "fft_path": fft, "accuracy_vs_oracle": accuracy, "cpu_baseline": cpu, "serve": serve,
+        "fp32_path": fp32, "fft_path": fft, "split_fp16_path": f16, "accuracy_vs_oracle": accuracy, "cpu_baseline": cpu, "serve": serve,
         "maxima_fit": fits,
         "coincidence_counts": coincidences,
     }
@@ -367,6 +372,33 @@ def run_fp32(ctx, bf, torch, w, xs, ctrl, corr_per_step):
             "note": "bank synthesis excluded; same series, bank and outputs, FP32 SIMT kernel"}
 
 
+def run_split_fp16(ctx, bf, w, xs, ctrl, corr_per_step, steps=3):
+    """The same step on the split-FP16 tensor-core route: bank synthesised in
+    the FP16 layout, series scaled by a power of two on the device, three
+    FP16 MMAs per operand pair, histogram and map."""
+    fs, M = w["fs"], w["M"]
+    opts = bf.make_opts(precision="split_fp16", want_map=True, want_hist=True)
+
+    def step():
+        t0 = time.perf_counter()
+        bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_FP16)
+        res = bf.bf_correlate(ctx, bank, xs + ctrl, fs, opts)
+        wall = time.perf_counter() - t0
+        info = bf.bf_result_info_get(res)
+        bf.bf_result_destroy(res)
+        bf.bf_bank_destroy(bank)
+        return wall, info.kernel_ms, info.tile_lags
+
+    step()
+    walls, kms, lts = zip(*[step() for _ in range(steps)])
+    wall, k_ms = float(np.mean(walls)), float(np.mean(kms))
+    return {"value": corr_per_step / wall, "unit": UNIT, "ms_per_step": round(1e3 * wall, 1),
+            "kernel_ms": round(k_ms, 1), "tile_lags": sorted(set(lts)),
+            "issued_tflops": round(3 * 2 * M * corr_per_step / (k_ms / 1e3) / 1e12, 1),
+            "note": "bank synthesis included (FP16 hi/lo of 2^8 h); three FP16 MMAs per "
+                    "operand pair into FP32, like split-BF16"}
+
+
 def run_fft(ctx, bf, w, xs, ctrl, corr_per_step, steps=3):
     """The same step through the FFT route (the paper's own route): bank from
     the chirp parameters, template spectra, segment spectra and the fused
@@ -427,9 +459,9 @@ def run_cpu_sample(ctx, bf, w, xs_host, n_templates):
            "sample": f"{n_templates} templates spread over the 65536-template bank x all "
                      f"{L} lags of series 0 (FP64 direct correlation, OpenMP over templates)"}
     # accuracy of the timed GPU path on the same sample
-    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16)
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_SPLIT_FP16)
     acc = {}
-    for prec in ("split_bf16", "bf16", "fft_fp32"):
+    for prec in ("split_bf16", "bf16", "fft_fp32", "split_fp16"):
         res = bf.bf_correlate(ctx, bank, [xs_host[0]], fs, bf.make_opts(precision=prec))
         got = bf.bf_result_copy_to_host(res, 0)
         bf.bf_result_destroy(res)
@@ -575,7 +607,8 @@ def run_kernel_case(tile_lags: int, precision: str = "split_bf16"):
     __graft_entry__.build()
     w = synth.gw_pair(n=65536, I=128, J=128)
     ctx = bf.bf_init()
-    bank = bf.bf_bank_create_grid(ctx, w["grid"], w["fs"], 1.0, bf.BF_BANK_SPLIT_BF16)
+    storage = bf.BF_BANK_SPLIT_FP16 if precision == "split_fp16" else bf.BF_BANK_SPLIT_BF16
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], w["fs"], 1.0, storage)
     for _ in range(2):
         res = bf.bf_correlate(ctx, bank, [w["series"][0]], w["fs"],
                               bf.make_opts(precision=precision, tile_lags=tile_lags))
@@ -764,7 +797,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-fft", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--fft", action="store_true", help="--kernel-case: the FFT route")
+    ap.add_argument("--fp16", action="store_true", help="--kernel-case: the split-FP16 route")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--cpu-templates", type=int, default=384)
@@ -773,7 +808,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=8.0)
     args = ap.parse_args()
     if args.kernel_case:
-        run_kernel_case(args.tile_lags, "fft_fp32" if args.fft else "split_bf16")
+        run_kernel_case(args.tile_lags, "fft_fp32" if args.fft else
+                        ("split_fp16" if args.fp16 else "split_bf16"))
         return
     if args.workload == "serving":
         run_serving_workload()

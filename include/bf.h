@@ -79,7 +79,7 @@ typedef enum {
     BF_BF16 = 1,        /* BF16 operands on tcgen05 tensor cores               */
     BF_SPLIT_BF16 = 2,  /* x = hi + lo, h = hi + lo in BF16; three tcgen05 MMAs
                            hi*hi + hi*lo + lo*hi into one FP32 accumulator     */
-    BF_FFT_FP32 = 3     /* the paper's route (Sect. 2.2, Fig. 5): FP32 FFTs,
+    BF_FFT_FP32 = 3,    /* the paper's route (Sect. 2.2, Fig. 5): FP32 FFTs,
                            overlap-save over segments of 8192 samples
                            (8193 - M lags each).  Template spectra are made
                            from the chirp parameters, whatever the bank
@@ -90,6 +90,14 @@ typedef enum {
                            works.  Templates of at most 4096 samples, else
                            BF_ENOTSUP.  Plans and the serving loop run it
                            with a stored bank.  tile_lags is ignored.        */
+    BF_SPLIT_FP16 = 4   /* as BF_SPLIT_BF16 with FP16 hi and lo parts: the
+                           split holds x and h to 2^-22 instead of 2^-17, at
+                           the same tensor-core rate.  FP16's range is kept
+                           by exact power-of-two scaling on the device (each
+                           series so that its largest |x| lies in
+                           [2^13, 2^14), templates by 2^8), undone in the
+                           epilogue.  Needs BF_BANK_SPLIT_FP16 or a
+                           generated bank.                                   */
 } bf_precision;
 
 /* which sample layouts a bank keeps in device memory (bit flags) */
@@ -102,6 +110,8 @@ enum {
                                   small ring that stays in L2 while the
                                   correlation consumes it.  Exclusive of the
                                   other layout flags; serves every precision. */
+    BF_BANK_SPLIT_FP16 = 16,   /* needed by BF_SPLIT_FP16: the tensor-core
+                                  layout with FP16 hi and lo parts of 2^8 h    */
     BF_BANK_QUADRATURE = 8     /* with any of the above: every chirp also gets
                                   its quadrature partner, the Hilbert
                                   transform of the template (sin(2 pi c(t))

@@ -23,11 +23,12 @@ BF_OK, BF_EINVAL, BF_ENOMEM, BF_ECUDA, BF_ETIMEDOUT, BF_EPENDING, BF_EAGAIN, \
     BF_ECANCELED, BF_EDEVICE, BF_ENOTSUP = range(10)
 BF_LINEAR, BF_POWERLAW = 0, 1
 BF_ASC, BF_DESC, BF_BOTH = 0, 1, 2
-BF_FP32, BF_BF16, BF_SPLIT_BF16, BF_FFT_FP32 = 0, 1, 2, 3
-BF_BANK_FP32, BF_BANK_SPLIT_BF16, BF_BANK_GENERATED, BF_BANK_QUADRATURE = 1, 2, 4, 8
+BF_FP32, BF_BF16, BF_SPLIT_BF16, BF_FFT_FP32, BF_SPLIT_FP16 = 0, 1, 2, 3, 4
+BF_BANK_FP32, BF_BANK_SPLIT_BF16, BF_BANK_GENERATED, BF_BANK_QUADRATURE, BF_BANK_SPLIT_FP16 = 1, 2, 4, 8, 16
 BF_SIGMA_WHITE, BF_SIGMA_PARSEVAL = 0, 1
 
-PRECISIONS = {"fp32": BF_FP32, "bf16": BF_BF16, "split_bf16": BF_SPLIT_BF16, "fft_fp32": BF_FFT_FP32}
+PRECISIONS = {"fp32": BF_FP32, "bf16": BF_BF16, "split_bf16": BF_SPLIT_BF16, "fft_fp32": BF_FFT_FP32,
+              "split_fp16": BF_SPLIT_FP16}
 
 
 class BFError(RuntimeError):

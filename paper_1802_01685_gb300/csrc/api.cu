@@ -188,6 +188,10 @@ bf_status prepare_series_alloc(bf_ctx* ctx, size_t N, uint32_t M, uint32_t M_pad
         ps.yhi = static_cast<uint4*>(grab(ps.rows * 16));
         ps.ylo = static_cast<uint4*>(grab(ps.rows * 16));
         ok = ps.yhi && ps.ylo;
+        if (ok && precision == BF_SPLIT_FP16) {
+            ps.xmax = static_cast<uint32_t*>(grab(sizeof(uint32_t)));
+            ok = ps.xmax != nullptr;
+        }
     }
     if (!ok) {
         ps.release(mem);
@@ -202,7 +206,9 @@ cudaError_t prepare_series_kernels(const PreparedSeries& ps, uint32_t M, int pre
 {
     cudaError_t e = cudaMemsetAsync(ps.x + ps.N, 0, (ps.xcap - ps.N) * sizeof(float), st);
     if (e == cudaSuccess) e = launch_inv_norm(ps.x, ps.N, M, ps.prefix, ps.bsum, ps.nb, ps.inv, st);
-    if (e == cudaSuccess && uses_split_rows(precision))
+    if (e == cudaSuccess && precision == BF_SPLIT_FP16)
+        e = launch_split_rows_f16(ps.x, ps.N, ps.rows, ps.yhi, ps.ylo, ps.xmax, st);
+    else if (e == cudaSuccess && uses_split_rows(precision))
         e = launch_split_rows(ps.x, ps.N, ps.rows, ps.yhi, ps.ylo, st);
     return e;
 }
@@ -228,6 +234,7 @@ size_t prepared_series_bytes(size_t N, uint32_t M, uint32_t M_pad, int precision
                inv_norm_scratch_blocks(N) * 8;
     if (uses_split_rows(precision)) b += 2 * (ceil_div(L, TC_TILE_L) * TC_TILE_L + M_pad + 64) * 16;
     if (precision == BF_FFT_FP32) b += (size_t)fft_segments((uint32_t)L, M) * (FFT_POINTS / 2) * 8;
+    if (precision == BF_SPLIT_FP16) b += 4096;                  // max |x|
     return b + 8 * 4096;
 }
 
@@ -250,6 +257,11 @@ Seg make_segment(const PreparedSeries& ps, uint32_t series_id, const bf_bank* ba
     g.n_lag_tiles = (uint32_t)ceil_div(ps.L, tile_lags(precision));
     g.tt0 = tt_first;
     g.n_tt = tt_count;
+    if (precision == BF_SPLIT_FP16) {
+        g.bank_hi = bank->hi16;
+        g.bank_lo = bank->lo16;
+        g.xmax = ps.xmax;
+    }
     g.k_begin = (uint32_t)bank_row(bank, k_begin);
     g.k_end = (uint32_t)bank_row(bank, k_end);
     g.quad = bank->quad ? 1u : 0u;
@@ -362,8 +374,9 @@ cudaError_t launch_segments(bf_ctx* ctx, const std::vector<Seg>& segs, int preci
         p.cand_count = cand_count;
         p.cand_cap = cand_cap;
         p.err = ctx->d_err;
+        p.idesc = tc_idesc(precision);
         cudaError_t e = precision == BF_FP32 ? launch_corr_simt(p, st)
-                                             : launch_corr_tc(p, precision == BF_SPLIT_BF16 ? 3 : 1,
+                                             : launch_corr_tc(p, precision == BF_BF16 ? 1 : 3,
                                                               lt, ctx->n_sm, st);
         if (e != cudaSuccess) return e;
         tiles += t;
@@ -410,7 +423,7 @@ bf_status resolve_opts(const bf_bank* bank, const bf_opts* in, bf_opts* o)
         return BF_EINVAL;
     }
     if (o->precision != BF_FP32 && o->precision != BF_BF16 && o->precision != BF_SPLIT_BF16 &&
-        o->precision != BF_FFT_FP32) {
+        o->precision != BF_FFT_FP32 && o->precision != BF_SPLIT_FP16) {
         set_error("unknown precision %d", o->precision);
         return BF_EINVAL;
     }
@@ -427,7 +440,11 @@ bf_status resolve_opts(const bf_bank* bank, const bf_opts* in, bf_opts* o)
         set_error("bank keeps no FP32 layout (create it with BF_BANK_FP32)");
         return BF_EINVAL;
     }
-    if (!bank->generated && uses_split_rows(o->precision) && !bank->hi) {
+    if (!bank->generated && o->precision == BF_SPLIT_FP16 && !bank->hi16) {
+        set_error("bank keeps no split-FP16 layout (create it with BF_BANK_SPLIT_FP16)");
+        return BF_EINVAL;
+    }
+    if (!bank->generated && (o->precision == BF_BF16 || o->precision == BF_SPLIT_BF16) && !bank->hi) {
         set_error("bank keeps no split-BF16 layout (create it with BF_BANK_SPLIT_BF16)");
         return BF_EINVAL;
     }
@@ -588,6 +605,7 @@ cudaError_t correlate_generated(bf_ctx* ctx, const bf_bank* bank, const bf_opts&
                                 const std::vector<Seg>& segs, bf_result* r, cudaStream_t strm, int lt)
 {
     const bool tc = o.precision != BF_FP32;
+    const bool f16 = o.precision == BF_SPLIT_FP16;
     const size_t tile_bytes = (size_t)TC_TILE_T * bank->M_pad * 4;     // hi+lo, or FP32
     const size_t chunk_tiles = std::max<size_t>(1, GEN_SLOT_BYTES / tile_bytes);
     const size_t t_begin = bank_row(bank, o.bank_begin) / TC_TILE_T;
@@ -626,8 +644,10 @@ cudaError_t correlate_generated(bf_ctx* ctx, const bf_bank* bank, const bf_opts&
                                   (uint32_t)((t1 - t0) * TC_TILE_T),
                                   bank->M, bank->M_pad, bank->fs,
                                   tc ? nullptr : static_cast<float*>(slot[sl][0]),
-                                  tc ? static_cast<uint8_t*>(slot[sl][0]) : nullptr,
-                                  tc ? static_cast<uint8_t*>(slot[sl][1]) : nullptr, ctx->aux);
+                                  tc && !f16 ? static_cast<uint8_t*>(slot[sl][0]) : nullptr,
+                                  tc && !f16 ? static_cast<uint8_t*>(slot[sl][1]) : nullptr, ctx->aux,
+                                  f16 ? static_cast<uint8_t*>(slot[sl][0]) : nullptr,
+                                  f16 ? static_cast<uint8_t*>(slot[sl][1]) : nullptr);
         if (e == cudaSuccess) e = cudaEventRecord(synth_done[sl], ctx->aux);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(strm, synth_done[sl], 0);
         if (e != cudaSuccess) break;
@@ -900,10 +920,11 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
     const bool quad = (storage & BF_BANK_QUADRATURE) != 0;
     const unsigned layout = storage & ~(unsigned)BF_BANK_QUADRATURE;
     const bool generated = layout == BF_BANK_GENERATED;
-    if (!generated && ((layout & (BF_BANK_FP32 | BF_BANK_SPLIT_BF16)) == 0 || (layout & ~3u))) {
-        set_error("storage mask %u must be BF_BANK_GENERATED alone, or select BF_BANK_FP32 "
-                  "and/or BF_BANK_SPLIT_BF16 (either way optionally with BF_BANK_QUADRATURE)",
-                  storage);
+    const unsigned stored = BF_BANK_FP32 | BF_BANK_SPLIT_BF16 | BF_BANK_SPLIT_FP16;
+    if (!generated && ((layout & stored) == 0 || (layout & ~stored))) {
+        set_error("storage mask %u must be BF_BANK_GENERATED alone, or select any of BF_BANK_FP32, "
+                  "BF_BANK_SPLIT_BF16 and BF_BANK_SPLIT_FP16 (either way optionally with "
+                  "BF_BANK_QUADRATURE)", storage);
         return BF_EINVAL;
     }
     const uint32_t M = template_len(T, fs);
@@ -941,8 +962,13 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
         b->hi = static_cast<uint8_t*>(mem.alloc(elems * 2));
         b->lo = static_cast<uint8_t*>(mem.alloc(elems * 2));
     }
+    if (storage & BF_BANK_SPLIT_FP16) {
+        b->hi16 = static_cast<uint8_t*>(mem.alloc(elems * 2));
+        b->lo16 = static_cast<uint8_t*>(mem.alloc(elems * 2));
+    }
     if (!b->d_params || ((storage & BF_BANK_FP32) && !b->f32) ||
-        ((storage & BF_BANK_SPLIT_BF16) && (!b->hi || !b->lo))) {
+        ((storage & BF_BANK_SPLIT_BF16) && (!b->hi || !b->lo)) ||
+        ((storage & BF_BANK_SPLIT_FP16) && (!b->hi16 || !b->lo16))) {
         bf_bank_destroy(b.release());
         set_error("bank of %zu x %u samples exceeds the device memory budget", K, M);
         return BF_ENOMEM;
@@ -953,7 +979,7 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !generated)
         e = launch_bank_synth(b->d_params, 0, quad, (uint32_t)b->rows, (uint32_t)b->K_pad, M, b->M_pad, fs,
-                              b->f32, b->hi, b->lo, st);
+                              b->f32, b->hi, b->lo, st, b->hi16, b->lo16);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         bf_bank_destroy(b.release());
@@ -1001,6 +1027,8 @@ void bf_bank_destroy(bf_bank* b)
     mem.release(b->f32);
     mem.release(b->hi);
     mem.release(b->lo);
+    mem.release(b->hi16);
+    mem.release(b->lo16);
     delete b;
 }
 
@@ -1041,13 +1069,28 @@ bf_status bf_bank_read(const bf_bank* b, size_t c0, size_t nc, float* out)
                                      cudaMemcpyDeviceToHost);
         return e == cudaSuccess ? BF_OK : cuda_fail(e, "bank read");
     }
-    // split layout: copy whole 128-template tiles and decode hi + lo
+    // split layout: copy whole 128-template tiles and decode hi + lo (BF16, or
+    // FP16 of 2^8 h)
+    const bool f16 = b->hi == nullptr;
+    const uint8_t* dhi = f16 ? b->hi16 : b->hi;
+    const uint8_t* dlo = f16 ? b->lo16 : b->lo;
+    auto decode = [f16](uint16_t v) -> float {
+        if (f16) {
+            __half_raw r;
+            r.x = v;
+            return __half2float(__half(r)) / TEMPLATE_F16_SCALE;
+        }
+        uint32_t u = (uint32_t)v << 16;
+        float f;
+        memcpy(&f, &u, 4);
+        return f;
+    };
     const uint32_t n_kb = b->M_pad / TC_BK;
     const size_t tile_bytes = (size_t)n_kb * TILE_BYTES_A;
     std::vector<uint16_t> hi(tile_bytes / 2), lo(tile_bytes / 2);
     for (size_t tt = k0 / TC_TILE_T; tt * TC_TILE_T < k0 + n; ++tt) {
-        cudaError_t e = cudaMemcpy(hi.data(), b->hi + tt * tile_bytes, tile_bytes, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) e = cudaMemcpy(lo.data(), b->lo + tt * tile_bytes, tile_bytes, cudaMemcpyDeviceToHost);
+        cudaError_t e = cudaMemcpy(hi.data(), dhi + tt * tile_bytes, tile_bytes, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(lo.data(), dlo + tt * tile_bytes, tile_bytes, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "bank read");
         for (uint32_t r = 0; r < TC_TILE_T; ++r) {
             const size_t k = tt * TC_TILE_T + r;
@@ -1056,11 +1099,7 @@ bf_status bf_bank_read(const bf_bank* b, size_t c0, size_t nc, float* out)
                 const uint32_t kb = m / TC_BK, c = m % TC_BK;
                 const size_t off = ((size_t)kb * TILE_BYTES_A + (r / 8) * 1024 + (c / 8) * 128 +
                                     (r % 8) * 16 + (c % 8) * 2) / 2;
-                uint32_t hb = (uint32_t)hi[off] << 16, lb = (uint32_t)lo[off] << 16;
-                float hf, lf;
-                memcpy(&hf, &hb, 4);
-                memcpy(&lf, &lb, 4);
-                out[(k - k0) * b->M + m] = hf + lf;
+                out[(k - k0) * b->M + m] = decode(hi[off]) + decode(lo[off]);
             }
         }
     }

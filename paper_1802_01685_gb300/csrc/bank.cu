@@ -68,7 +68,9 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
                                                     uint32_t M, uint32_t M_pad,
                                                     double fs, float* __restrict__ f32,
                                                     uint8_t* __restrict__ hi,
-                                                    uint8_t* __restrict__ lo)
+                                                    uint8_t* __restrict__ lo,
+                                                    uint8_t* __restrict__ hi16,
+                                                    uint8_t* __restrict__ lo16)
 {
     extern __shared__ float g[];        // the first M_s = round64(M) samples of the row
     __shared__ double red[8];
@@ -138,12 +140,21 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
             *reinterpret_cast<__nv_bfloat16*>(hi + off) = bh;
             *reinterpret_cast<__nv_bfloat16*>(lo + off) = bl;
         }
+        if (hi16) {
+            // FP16 split of 2^8 h: the scale keeps the lo parts normal
+            const float hs = h * TEMPLATE_F16_SCALE;
+            const __half fh = __float2half_rn(hs);
+            const __half fl = __float2half_rn(hs - __half2float(fh));       // exact difference
+            size_t off = tc_offset(k, m, n_kb);
+            *reinterpret_cast<__half*>(hi16 + off) = fh;
+            *reinterpret_cast<__half*>(lo16 + off) = fl;
+        }
     }
 }
 
 cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t row0, int quad, uint32_t K, uint32_t K_pad, uint32_t M,
                               uint32_t M_pad, double fs, float* f32, uint8_t* hi, uint8_t* lo,
-                              cudaStream_t s)
+                              cudaStream_t s, uint8_t* hi16, uint8_t* lo16)
 {
     size_t smem = (size_t)std::min(M_pad, (M + 63u) & ~63u) * sizeof(float);
     if (smem > 48 * 1024) {
@@ -153,7 +164,7 @@ cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t row0, int quad, u
         if (e != cudaSuccess) return e;
     }
     count_launches(1);
-    k_bank_synth<<<K_pad, 256, smem, s>>>(params, row0, quad, K, M, M_pad, fs, f32, hi, lo);
+    k_bank_synth<<<K_pad, 256, smem, s>>>(params, row0, quad, K, M, M_pad, fs, f32, hi, lo, hi16, lo16);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <atomic>
 #include <condition_variable>
@@ -67,6 +68,8 @@ struct Seg {
     const float* sigma_pred;        // optional predicted sigma per template
                                     // (index k - k_begin): tails are then
                                     // |rho| >= kappa * sigma_pred[k]
+    const uint32_t* xmax;           // split-FP16 only: float bits of max |x|, from
+                                    // which the operand scales are derived
     float kappa;
     float pad2;
     uint32_t bank_k0;               // template row held at the bank pointers
@@ -85,7 +88,7 @@ struct Seg {
 
 struct CorrParams {
     int n_seg;
-    int pad0;
+    uint32_t idesc;                 // tcgen05 instruction descriptor (operand type)
     uint64_t total_tiles;
     float thr;                      // candidate threshold on |rho|
     unsigned int cand_cap;
@@ -146,6 +149,8 @@ cudaError_t launch_corr_simt(const CorrParams& p, cudaStream_t s);
 cudaError_t launch_wait_selftest(int* err, int signal, uint64_t limit_ns, unsigned long long* waited,
                                  cudaStream_t st);
 cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int lt, int n_sm, cudaStream_t s);
+// the instruction descriptor of a tensor-core precision (BF16 or FP16 operands)
+uint32_t tc_idesc(int precision);
 // sets the tensor-core kernels' shared-memory attribute (outside graph capture)
 cudaError_t corr_tc_set_attributes();
 
@@ -162,11 +167,29 @@ struct ChirpDev {                   // device copy of a template's parameters
 // row0 + K - 1 are zero); quad: row r is chirp r / 2, sine phase when r is odd
 cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t row0, int quad, uint32_t K, uint32_t K_pad,
                               uint32_t M, uint32_t M_pad, double fs, float* f32,
-                              uint8_t* hi, uint8_t* lo, cudaStream_t s);
+                              uint8_t* hi, uint8_t* lo, cudaStream_t s,
+                              uint8_t* hi16 = nullptr, uint8_t* lo16 = nullptr);
+// templates in the split-FP16 layout are scaled by this power of two
+constexpr float TEMPLATE_F16_SCALE = 256.f;
 
 // series preparation: padded FP32 copy, split rows, FP64 prefix, inverse norms
 cudaError_t launch_split_rows(const float* x, uint64_t N, uint64_t rows, uint4* yhi,
                               uint4* ylo, cudaStream_t s);
+// split-FP16 rows of x 2^s, s from max |x| (written to *xmax as float bits)
+cudaError_t launch_split_rows_f16(const float* x, uint64_t N, uint64_t rows, uint4* yhi, uint4* ylo,
+                                  uint32_t* xmax, cudaStream_t s);
+
+// The power-of-two exponent s that puts the largest |x| (float bits, >= 0) of a
+// series in [2^13, 2^14) for its FP16 split; 0 for an all-zero series.  s is
+// held to at most 118 so that 2^s and the epilogue's 2^-(s+8) stay normal
+// floats (series whose largest |x| is below 2^-105 are scaled less).
+__host__ __device__ inline int f16_series_shift(uint32_t max_bits)
+{
+    if (max_bits == 0) return 0;
+    const int e = (int)(max_bits >> 23) - 127;         // floor(log2 max) for normal floats
+    const int s = 13 - e;                              // >= 13 - 127 = -114
+    return s > 118 ? 118 : s;
+}
 cudaError_t launch_inv_norm(const float* x, uint64_t N, uint32_t M, double* prefix,
                             double* block_scratch, uint64_t n_blocks_cap, float* inv,
                             cudaStream_t s);
@@ -269,6 +292,8 @@ struct bf_bank {
     float* f32 = nullptr;
     uint8_t* hi = nullptr;
     uint8_t* lo = nullptr;
+    uint8_t* hi16 = nullptr;            // split-FP16 layout (2^8 h)
+    uint8_t* lo16 = nullptr;
     float* ph = nullptr;                // template power spectra [K_pad][M+1] (lazy)
     float2* fspec = nullptr;            // template half spectra for the FFT route (lazy)
 };

@@ -66,10 +66,11 @@ static_assert(Geo<512>::SMEM <= 232448 && Geo<256>::SMEM <= 232448, "shared memo
 constexpr uint64_t TIMEOUT_NS = 10ull * 1000 * 1000 * 1000;
 constexpr uint32_t TMEM_COLS = 512;
 
-// instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major,
-// N = 256, M = 128
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
-                           ((128u >> 4) << 24);
+// instruction descriptors, kind::f16, D = F32, both operands K-major, N = 256,
+// M = 128: A = B = BF16 (formats 1), or A = B = FP16 (formats 0)
+constexpr uint32_t IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
+                                ((128u >> 4) << 24);
+constexpr uint32_t IDESC_F16 = (1u << 4) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -148,13 +149,14 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
     return d;                                   // base offset 0, no swizzle
 }
 
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum)
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accum)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(IDESC), "r"(accum)
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
         : "memory");
 }
 
@@ -465,10 +467,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
                             const uint64_t bhi = make_desc(sbase + G::OFF_BHI + boff, 128, 128);
                             const uint64_t blo = make_desc(sbase + G::OFF_BLO + boff, 128, 128);
                             const uint32_t d = tmem + buf * 256 + h * 256;
-                            mma_f16(d, ahi, bhi, (kb | kk) != 0);
+                            mma_f16(d, ahi, bhi, p.idesc, (kb | kk) != 0);
                             if (NPROD == 3) {
-                                mma_f16(d, ahi, blo, 1);
-                                mma_f16(d, alo, bhi, 1);
+                                mma_f16(d, ahi, blo, p.idesc, 1);
+                                mma_f16(d, alo, bhi, p.idesc, 1);
                             }
                         }
                     }
@@ -495,9 +497,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             const TileCoord c = tile_coord<LT>(p, t);
             const Seg& s = *c.s;
             const uint32_t nvalid = min((uint32_t)LT, s.L - c.lag0);
+            // split-FP16 operands were scaled by 2^s (series) and 2^8 (templates)
+            const float oscale = s.xmax ? ldexpf(1.f, -(f16_series_shift(*s.xmax) + 8)) : 1.f;
             epilogue_sync();
             for (uint32_t j = e; j < (uint32_t)LT; j += EPI_THREADS)
-                sh_inv[j] = j < nvalid ? s.inv_norm[c.lag0 + j] : 0.f;
+                sh_inv[j] = j < nvalid ? s.inv_norm[c.lag0 + j] * oscale : 0.f;
             epilogue_sync();
             const bool ok = mbar_wait(tfull_bar(buf), (tph >> buf) & 1, abort_flag);
             if (epilogue_any(!ok)) {       // all epilogue threads leave together
@@ -658,6 +662,8 @@ cudaError_t launch_wait_selftest(int* err, int signal, uint64_t limit_ns, unsign
     k_wait_selftest<<<1, 64, 0, st>>>(err, signal, limit_ns, waited);
     return cudaGetLastError();
 }
+
+uint32_t tc_idesc(int precision) { return precision == BF_SPLIT_FP16 ? IDESC_F16 : IDESC_BF16; }
 
 cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int lt, int n_sm, cudaStream_t st)
 {

@@ -14,6 +14,8 @@
 //     nonzero samples decides it, because the block-wise scan sums the energy
 //     prefix in different orders on either side of a block edge, so S may
 //     differ by rounding across an all-zero window.
+#include <algorithm>
+
 #include "bf_internal.h"
 
 namespace bfi {
@@ -37,6 +39,57 @@ __global__ void k_split_rows(const float* __restrict__ x, uint64_t N, uint64_t r
         yhi[w] = make_uint4(h[0], h[1], h[2], h[3]);
         ylo[w] = make_uint4(l[0], l[1], l[2], l[3]);
     }
+}
+
+// max |x| as float bits (non-negative floats order like unsigned integers)
+__global__ void k_absmax(const float* __restrict__ x, uint64_t N, uint32_t* __restrict__ xmax)
+{
+    uint32_t m = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        m = max(m, __float_as_uint(fabsf(x[i])));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(xmax, m);
+}
+
+// Split rows as k_split_rows, in FP16 of x 2^s: hi = fp16(x 2^s), lo =
+// fp16(x 2^s - hi) (exact difference in FP32), s from the series' max |x|.
+__global__ void k_split_rows_f16(const float* __restrict__ x, uint64_t N, uint64_t rows,
+                                 uint4* __restrict__ yhi, uint4* __restrict__ ylo,
+                                 const uint32_t* __restrict__ xmax)
+{
+    const float scale = ldexpf(1.f, f16_series_shift(*xmax));
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < rows;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int c = 0; c < 8; c += 2) {
+            const float v0 = ((w + c < N) ? x[w + c] : 0.f) * scale;
+            const float v1 = ((w + c + 1 < N) ? x[w + c + 1] : 0.f) * scale;
+            const __half h0 = __float2half_rn(v0), h1 = __float2half_rn(v1);
+            const __half l0 = __float2half_rn(v0 - __half2float(h0));
+            const __half l1 = __float2half_rn(v1 - __half2float(h1));
+            h[c / 2] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+            l[c / 2] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+        }
+        yhi[w] = make_uint4(h[0], h[1], h[2], h[3]);
+        ylo[w] = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+cudaError_t launch_split_rows_f16(const float* x, uint64_t N, uint64_t rows, uint4* yhi, uint4* ylo,
+                                  uint32_t* xmax, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(xmax, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    uint64_t b1 = std::min<uint64_t>((N + 255) / 256, 1024);
+    uint64_t blocks = (rows + 255) / 256;
+    if (blocks > 65535ull * 16) blocks = 65535ull * 16;
+    if (blocks == 0) blocks = 1;
+    count_launches(2);
+    k_absmax<<<(unsigned)std::max<uint64_t>(b1, 1), 256, 0, s>>>(x, N, xmax);
+    k_split_rows_f16<<<(unsigned)blocks, 256, 0, s>>>(x, N, rows, yhi, ylo, xmax);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_split_rows(const float* x, uint64_t N, uint64_t rows, uint4* yhi, uint4* ylo,

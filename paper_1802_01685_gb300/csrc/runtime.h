@@ -18,6 +18,7 @@ struct PreparedSeries {
     uint4* yhi = nullptr;           // split rows (tensor-core path)
     uint4* ylo = nullptr;
     double* prefix = nullptr;       // FP64 prefix of x^2, then the uint32 nonzero counts (scratch)
+    uint32_t* xmax = nullptr;       // split-FP16 rows: float bits of max |x|
     double* bsum = nullptr;         // scan block sums (scratch)
     uint64_t xcap = 0, nb = 0, rows = 0;
     std::vector<void*> owned;       // every buffer, prefix scratch included
@@ -46,7 +47,10 @@ inline uint32_t tile_lags(int precision) { return precision == BF_FP32 ? SIMT_TI
 // first template row of chirp k (quadrature banks hold two rows per chirp)
 inline size_t bank_row(const bf_bank* b, size_t k) { return b->quad ? 2 * k : k; }
 // the tensor-core precisions read the series as bf16 split rows
-inline bool uses_split_rows(int precision) { return precision == BF_BF16 || precision == BF_SPLIT_BF16; }
+inline bool uses_split_rows(int precision)
+{
+    return precision == BF_BF16 || precision == BF_SPLIT_BF16 || precision == BF_SPLIT_FP16;
+}
 
 // One segment: series `ps` (result slot series_id) against template tiles
 // [tt_first, tt_first + tt_count), keeping outputs of templates [k_begin, k_end).

@@ -249,7 +249,7 @@ static void scheduler(ServeState* S)
         }
 
         // one iteration: a chunk of template tiles of every admitted request
-        std::vector<std::pair<Request*, Seg>> segs[3];
+        std::vector<std::pair<Request*, Seg>> segs[5];          // by precision (the FFT route has none)
         std::vector<Request*> finishing;
         uint64_t n_work = 0;
         for (Request* r : act)
@@ -277,7 +277,7 @@ static void scheduler(ServeState* S)
         // candidate buffer its segment writes, so it gets a launch of its own
         // in the same iteration.
         bool any = false;
-        for (int prec = 0; prec < 3; ++prec) {
+        for (int prec = 0; prec < 5; ++prec) {
             if (segs[prec].empty()) continue;
             std::vector<Seg> shared;
             std::vector<Request*> shared_owner;

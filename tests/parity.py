@@ -7,7 +7,10 @@ from paper_1802_01685_gb300 import bf
 
 # per-result tolerances on normalised correlation (FP32, split-BF16 and the
 # FP32 FFT route vs plain BF16 operands)
-TOL = {"fp32": 2e-5, "split_bf16": 2e-5, "bf16": 1e-3, "fft_fp32": 2e-5}
+TOL = {"fp32": 2e-5, "split_bf16": 2e-5, "bf16": 1e-3, "fft_fp32": 2e-5, "split_fp16": 2e-5}
+
+# every stored layout, so that one bank serves every route
+STORE_ALL = bf.BF_BANK_FP32 | bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_SPLIT_FP16
 
 
 def oracle_params(spec):

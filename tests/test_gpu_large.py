@@ -55,22 +55,23 @@ def test_gw_pair_full_size_sampled(ctx):
     w = synth.gw_pair()
     fs, M = w["fs"], w["M"]
     xs = w["series"]
-    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16)
-    outs, mean, info = run(ctx, bank, xs, fs, "split_bf16")
-    assert info.correlations == 2 * (len(xs[0]) - M + 1) * 65536
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_SPLIT_FP16)
     p = oracle_params(w["grid"])
     idx = np.array([0, 1, 255, 4096, 20000, 32767, 32768, 40000, 50000, 60001, 65534, 65535])
     ref = oracle.search(xs[0], fs, subset(p, idx), M, want_rho=True)
-    g = {k: v[idx] for k, v in outs[0].items() if k in ("max", "argmax", "sigma")}
-    check_maxima(g, ref, ref["rho"], TOL["split_bf16"], "full size")
-    check_sigma(g, ref, TOL["split_bf16"])
-    # properties that hold at any size
-    for o in outs:
-        assert np.all(o["max"] <= 1.0 + 1e-5) and np.all(o["max"] > 0)
-        assert o["hist"].sum() == 65536
-        assert np.all(o["argmax"] >= 0) and np.all(o["argmax"] < len(xs[0]) - M + 1)
-    np.testing.assert_allclose(mean, (outs[0]["max"].astype(np.float64) + outs[1]["max"]) / 2,
-                               rtol=1e-6)
+    for prec in ("split_bf16", "split_fp16"):
+        outs, mean, info = run(ctx, bank, xs, fs, prec)
+        assert info.correlations == 2 * (len(xs[0]) - M + 1) * 65536
+        g = {k: v[idx] for k, v in outs[0].items() if k in ("max", "argmax", "sigma")}
+        check_maxima(g, ref, ref["rho"], TOL[prec], f"full size {prec}")
+        check_sigma(g, ref, TOL[prec])
+        # properties that hold at any size
+        for o in outs:
+            assert np.all(o["max"] <= 1.0 + 1e-5) and np.all(o["max"] > 0)
+            assert o["hist"].sum() == 65536
+            assert np.all(o["argmax"] >= 0) and np.all(o["argmax"] < len(xs[0]) - M + 1)
+        np.testing.assert_allclose(mean, (outs[0]["max"].astype(np.float64) + outs[1]["max"]) / 2,
+                                   rtol=1e-6)
     bf.bf_bank_destroy(bank)
 
 

@@ -6,8 +6,8 @@ import pytest
 import oracle
 from paper_1802_01685_gb300 import bf, synth
 
-from parity import (TOL, check_hist, check_map, check_maxima, check_sigma, oracle_params, run,
-                    subset)
+from parity import (STORE_ALL, TOL, check_hist, check_map, check_maxima, check_sigma, oracle_params,
+                    run, subset)
 
 pytestmark = pytest.mark.gpu
 
@@ -27,7 +27,7 @@ def ctx():
 def tiny(ctx):
     w = synth.tiny(seed=1)
     fs, M = w["fs"], w["M"]
-    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, M / fs)
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, M / fs, STORE_ALL)
     p = oracle_params(w["grid"])
     ref = oracle.search(w["series"][0], fs, p, M, want_rho=True)
     yield w, bank, p, ref
@@ -43,7 +43,7 @@ def test_bank_templates_match_oracle(ctx):
               (bf.BF_POWERLAW, bf.BF_ASC, 2.0, 1000.0, 1.0), (bf.BF_POWERLAW, bf.BF_DESC, 30.0, 1000.0, 0.3),
               (bf.BF_LINEAR, bf.BF_BOTH, 120.0, 800.0, 1.0), (bf.BF_POWERLAW, bf.BF_BOTH, 40.0, 400.0, 0.45)]
     fs, T = 2048.0, 1.0
-    for storage in (bf.BF_BANK_FP32, bf.BF_BANK_SPLIT_BF16):
+    for storage in (bf.BF_BANK_FP32, bf.BF_BANK_SPLIT_BF16, bf.BF_BANK_SPLIT_FP16):
         bank = bf.bf_bank_create(ctx, chirps, fs, T, storage)
         got = bf.bf_bank_read(bank, 0, len(chirps))
         for k, c in enumerate(chirps):
@@ -106,6 +106,7 @@ def test_control_seed_edge_values(ctx):
 # ------------------------------------------------------------------ tiny config, full parity
 
 @pytest.mark.parametrize("prec,lt", [("split_bf16", 512), ("split_bf16", 256), ("fp32", 0),
+                                     ("split_fp16", 512), ("split_fp16", 256),
                                      ("bf16", 512), ("bf16", 256), ("fft_fp32", 0)])
 def test_tiny_dense_rho(ctx, tiny, prec, lt):
     w, bank, p, ref = tiny
@@ -120,7 +121,7 @@ def test_tiny_dense_rho(ctx, tiny, prec, lt):
     assert info.correlations == K * L
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "fft_fp32"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "fft_fp32", "split_fp16"])
 def test_tiny_maxima_sigma_hist(ctx, tiny, prec):
     w, bank, p, ref = tiny
     x, fs = w["series"][0], w["fs"]
@@ -134,7 +135,7 @@ def test_tiny_maxima_sigma_hist(ctx, tiny, prec):
     np.testing.assert_array_equal(mean, g["max"])             # one series
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fft_fp32"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fft_fp32", "split_fp16"])
 def test_tiny_tf_map(ctx, tiny, prec):
     w, bank, p, ref = tiny
     x, fs, M = w["series"][0], w["fs"], w["M"]
@@ -145,7 +146,7 @@ def test_tiny_tf_map(ctx, tiny, prec):
     assert n_gpu > 0
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "fft_fp32"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "fft_fp32", "split_fp16"])
 def test_tiny_tails(ctx, tiny, prec):
     """The tail list holds every (k, tau) with |rho| >= thr + tol, nothing
     below thr - tol, each with its rho within tol."""
@@ -184,12 +185,12 @@ def test_parseval_predictor_matches_oracle(ctx):
                            20.0, 1000.0, 4, 5)                    # 160 templates
     p = oracle_params(spec)
     H = oracle.bank(p, fs, M)
-    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, STORE_ALL)
     xs = [synth.white(20000, rng).astype(np.float32),
           synth.gw_coloured(30000, fs, rng).astype(np.float32),
           synth.grb_lightcurve(25000, fs, rng).astype(np.float32),
           synth.white(3000, rng).astype(np.float32)]
-    for prec in ("split_bf16", "fp32"):
+    for prec in ("split_bf16", "fp32", "split_fp16"):
         res = bf.bf_correlate(ctx, bank, xs, fs, bf.make_opts(precision=prec, bank_begin=7,
                                                                bank_end=150,
                                                                tail_sigma=bf.BF_SIGMA_PARSEVAL))
@@ -205,7 +206,7 @@ def test_parseval_predictor_matches_oracle(ctx):
     bf.bf_bank_destroy(bank)
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fft_fp32"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fft_fp32", "split_fp16"])
 def test_parseval_tails_and_map(ctx, prec):
     """Tails |rho| >= kappa sigma_k with sigma_k predicted per template: the
     list and the map against the oracle with per-template thresholds."""
@@ -215,7 +216,7 @@ def test_parseval_tails_and_map(ctx, prec):
     p = oracle_params(w["grid"])
     H = oracle.bank(p, fs, M)
     kappa, tol = 3.0, TOL[prec]
-    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0)
+    bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, STORE_ALL)
     res = bf.bf_correlate(ctx, bank, [x], fs, bf.make_opts(
         precision=prec, kappa=kappa, want_tails=True, want_map=True,
         tail_sigma=bf.BF_SIGMA_PARSEVAL))
@@ -239,7 +240,7 @@ def test_parseval_tails_and_map(ctx, prec):
     bf.bf_bank_destroy(bank)
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fft_fp32"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fft_fp32", "split_fp16"])
 def test_butterfly_templates(ctx, prec):
     """Superposed templates (ascending + descending, both senses at once):
     dense rho, maxima and the map of their two tracks against the oracle."""
@@ -252,7 +253,7 @@ def test_butterfly_templates(ctx, prec):
     h = oracle.template(int(p["track"][5]), synth.BOTH, p["f_lo"][5], p["f_hi"][5], 1.0, fs, M)
     x[2000:2000 + M] += 20.0 * h
     x = x.astype(np.float32)
-    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, STORE_ALL)
     ref = oracle.search(x, fs, p, M, want_rho=True)
     K, L = ref["rho"].shape
     rho = torch.zeros((K, L), dtype=torch.float32, device="cuda")
@@ -275,8 +276,8 @@ def test_injection_recovered(ctx):
     x = np.random.default_rng(3).standard_normal(8192)
     x[n0:n0 + M] += 30.0 * h
     x = x.astype(np.float32)
-    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
-    for prec in ("split_bf16", "fp32", "bf16"):
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, STORE_ALL)
+    for prec in ("split_bf16", "fp32", "bf16", "split_fp16"):
         g = run(ctx, bank, [x], fs, prec)[0][0]
         assert g["argmax"][k] == n0 and g["max"][k] == g["max"].max()
     bf.bf_bank_destroy(bank)
@@ -296,9 +297,9 @@ def test_ragged_batch_and_bank_slice(ctx):
     lens = [M, M + 1, 1537, 2 * M + 700, 5000]
     xs = [rng.standard_normal(n).astype(np.float32) for n in lens]
     xs[3][100:1700] = 0.0                                        # windows of zeros
-    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, STORE_ALL)
     b0, b1 = 37, 181
-    for prec in ("split_bf16", "fp32", "bf16", "fft_fp32"):
+    for prec in ("split_bf16", "fp32", "bf16", "fft_fp32", "split_fp16"):
         outs, mean, info = run(ctx, bank, xs, fs, prec, bank_begin=b0, bank_end=b1)
         assert info.n_templates == b1 - b0
         ps = subset(p, np.arange(b0, b1))
@@ -315,9 +316,9 @@ def test_ragged_batch_and_bank_slice(ctx):
 def test_zero_series_gives_zero(ctx):
     fs, M = 1024.0, 1024
     spec = synth.grid_spec([synth.LINEAR], [synth.ASC], [1.0], 20.0, 500.0, 2, 2)
-    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0)
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, STORE_ALL)
     x = np.zeros(3000, np.float32)
-    for prec in ("split_bf16", "fp32", "fft_fp32"):
+    for prec in ("split_bf16", "fp32", "fft_fp32", "split_fp16"):
         g = run(ctx, bank, [x], fs, prec)[0][0]
         assert np.all(g["max"] == 0) and np.all(g["argmax"] == 0) and np.all(g["sigma"] == 0)
     bf.bf_bank_destroy(bank)
@@ -336,12 +337,25 @@ def test_invalid_calls(ctx, tiny):
     with pytest.raises(bf.BFError):
         bf.bf_correlate(ctx, bank, [], w["fs"])
     b32 = bf.bf_bank_create_grid(ctx, w["grid"], w["fs"], 1.0, bf.BF_BANK_FP32)
-    with pytest.raises(bf.BFError):                              # no split layout
-        bf.bf_correlate(ctx, b32, [x], w["fs"], bf.make_opts(precision="split_bf16"))
+    for prec in ("split_bf16", "split_fp16"):                    # no split layout
+        with pytest.raises(bf.BFError) as e:
+            bf.bf_correlate(ctx, b32, [x], w["fs"], bf.make_opts(precision=prec))
+        assert e.value.status == bf.BF_EINVAL
     bf.bf_bank_destroy(b32)
+    for storage, prec in ((bf.BF_BANK_SPLIT_BF16, "split_fp16"), (bf.BF_BANK_SPLIT_FP16, "split_bf16"),
+                          (bf.BF_BANK_SPLIT_FP16, "bf16"), (bf.BF_BANK_SPLIT_FP16, "fp32")):
+        b1 = bf.bf_bank_create_grid(ctx, w["grid"], w["fs"], 1.0, storage)
+        with pytest.raises(bf.BFError) as e:                     # the other split layout only
+            bf.bf_correlate(ctx, b1, [x], w["fs"], bf.make_opts(precision=prec))
+        assert e.value.status == bf.BF_EINVAL
+        bf.bf_bank_destroy(b1)
+    for storage in (32, bf.BF_BANK_GENERATED | bf.BF_BANK_SPLIT_FP16):
+        with pytest.raises(bf.BFError) as e:                     # unknown or mixed storage bits
+            bf.bf_bank_create_grid(ctx, w["grid"], w["fs"], 1.0, storage)
+        assert e.value.status == bf.BF_EINVAL
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "bf16"])
+@pytest.mark.parametrize("prec", ["split_bf16", "bf16", "split_fp16"])
 def test_tile_shapes_agree(ctx, prec):
     """Both tensor-core tile shapes compute every output by the same MMA
     sequence, so maxima and argmaxes agree bit for bit; ragged lag tiles of
@@ -349,7 +363,7 @@ def test_tile_shapes_agree(ctx, prec):
     fs = 2048.0
     spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0, 0.3],
                            20.0, 1000.0, 6, 7)                   # 336 templates
-    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_SPLIT_BF16)
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_SPLIT_FP16)
     rng = np.random.default_rng(12)
     xs = [rng.standard_normal(n).astype(np.float32) for n in (2048, 2048 + 255, 2048 + 700, 20000)]
     res = {}

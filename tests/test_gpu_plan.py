@@ -17,7 +17,8 @@ def setup():
     ctx = bf.bf_init()
     spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0, 0.5],
                            20.0, 1000.0, 8, 12)                  # 768 templates
-    bank = bf.bf_bank_create_grid(ctx, spec, 2048.0, 1.0)
+    bank = bf.bf_bank_create_grid(ctx, spec, 2048.0, 1.0,
+                                  bf.BF_BANK_FP32 | bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_SPLIT_FP16)
     yield ctx, bank, spec
     bf.bf_bank_destroy(bank)
     bf.bf_destroy(ctx)
@@ -27,7 +28,7 @@ def outputs(res, n, want_map):
     return [bf.bf_result_copy_to_host(res, s, want_hist=True, want_map=want_map) for s in range(n)]
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "fft_fp32"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "fft_fp32", "split_fp16"])
 def test_plan_replays_equal_correlate(setup, prec):
     ctx, bank, spec = setup
     lens = [2048, 5000, 9000, 2049]

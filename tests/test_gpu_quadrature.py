@@ -7,13 +7,13 @@ import pytest
 import oracle
 from paper_1802_01685_gb300 import bf, synth
 
-from parity import TOL, check_maxima, check_sigma, oracle_params, run, subset
+from parity import STORE_ALL, TOL, check_maxima, check_sigma, oracle_params, run, subset
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-PRECS = ["split_bf16", "fp32", "bf16", "fft_fp32"]
+PRECS = ["split_bf16", "fp32", "bf16", "fft_fp32", "split_fp16"]
 
 
 @pytest.fixture(scope="module")
@@ -57,7 +57,7 @@ def test_bank_rows_are_the_pairs(ctx, case):
     rows 2k, 2k + 1, equal to the oracle's within float rounding."""
     fs, M, chirps = case["fs"], case["M"], case["chirps"]
     idx = [0, 5, 77, 150, 223]
-    for storage in (bf.BF_BANK_FP32, bf.BF_BANK_SPLIT_BF16, bf.BF_BANK_GENERATED):
+    for storage in (bf.BF_BANK_FP32, bf.BF_BANK_SPLIT_BF16, bf.BF_BANK_SPLIT_FP16, bf.BF_BANK_GENERATED):
         bank = bf.bf_bank_create(ctx, chirps, fs, 1.0, storage | bf.BF_BANK_QUADRATURE)
         assert bf.bf_bank_size(bank) == len(chirps) and bf.bf_bank_rows(bank) == 2 * len(chirps)
         tol = 2e-5 if storage == bf.BF_BANK_SPLIT_BF16 else 1e-6
@@ -73,7 +73,7 @@ def test_bank_rows_are_the_pairs(ctx, case):
 @pytest.mark.parametrize("prec", PRECS)
 def test_dense_output_maxima_sigma(ctx, case, prec):
     fs, M, x, ref = case["fs"], case["M"], case["x"], case["ref"]
-    storage = bf.BF_BANK_FP32 | bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_QUADRATURE
+    storage = STORE_ALL | bf.BF_BANK_QUADRATURE
     bank = bf.bf_bank_create(ctx, case["chirps"], fs, 1.0, storage)
     K, L = ref["rho"].shape
     rho = torch.zeros((K, L), dtype=torch.float32, device="cuda")
@@ -92,7 +92,7 @@ def test_dense_output_maxima_sigma(ctx, case, prec):
     bf.bf_bank_destroy(bank)
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fft_fp32"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fft_fp32", "split_fp16"])
 def test_tails_map_and_slice(ctx, case, prec):
     """Tails |rho_q| >= kappa sqrt(2/M) and the map they paint, on an odd
     slice of the bank (a partial template tile at both ends)."""
@@ -102,8 +102,7 @@ def test_tails_map_and_slice(ctx, case, prec):
     kappa, tol = 4.0, TOL[prec]
     thr = kappa * np.sqrt(2.0 / M)
     ref = oracle.search(x, fs, ps, M, want_rho=True, quadrature=True, thr=thr)
-    bank = bf.bf_bank_create(ctx, case["chirps"], fs, 1.0,
-                             bf.BF_BANK_FP32 | bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_QUADRATURE)
+    bank = bf.bf_bank_create(ctx, case["chirps"], fs, 1.0, STORE_ALL | bf.BF_BANK_QUADRATURE)
     res = bf.bf_correlate(ctx, bank, [x], fs, bf.make_opts(precision=prec, bank_begin=b0, bank_end=b1,
                                                            kappa=kappa, want_tails=True, want_map=True))
     info = bf.bf_result_info_get(res)
@@ -129,10 +128,11 @@ def test_generated_bank_equals_stored(ctx, case):
     fs, x = case["fs"], case["x"]
     stored = bf.bf_bank_create(ctx, case["chirps"], fs, 1.0, bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_QUADRATURE)
     gen = bf.bf_bank_create(ctx, case["chirps"], fs, 1.0, bf.BF_BANK_GENERATED | bf.BF_BANK_QUADRATURE)
-    for prec in ("split_bf16", "fp32"):
-        if prec == "fp32":
+    for prec in ("split_bf16", "fp32", "split_fp16"):
+        if prec != "split_bf16":
             bf.bf_bank_destroy(stored)
-            stored = bf.bf_bank_create(ctx, case["chirps"], fs, 1.0, bf.BF_BANK_FP32 | bf.BF_BANK_QUADRATURE)
+            layout = bf.BF_BANK_FP32 if prec == "fp32" else bf.BF_BANK_SPLIT_FP16
+            stored = bf.bf_bank_create(ctx, case["chirps"], fs, 1.0, layout | bf.BF_BANK_QUADRATURE)
         a = run(ctx, stored, [x], fs, prec, bank_begin=9, bank_end=220)[0][0]
         b = run(ctx, gen, [x], fs, prec, bank_begin=9, bank_end=220)[0][0]
         np.testing.assert_array_equal(a["max"], b["max"])

@@ -22,7 +22,8 @@ def served():
     ctx = bf.bf_init(cfg)
     spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0, 0.5],
                            20.0, 1000.0, 16, 16)                 # 2048 templates
-    bank = bf.bf_bank_create_grid(ctx, spec, FS, T)
+    bank = bf.bf_bank_create_grid(ctx, spec, FS, T,
+                                  bf.BF_BANK_FP32 | bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_SPLIT_FP16)
     yield ctx, bank
     bf.bf_bank_destroy(bank)
     bf.bf_destroy(ctx)
@@ -36,7 +37,8 @@ def requests():
             (2.0, 0, 512, "bf16", False), (12.25, 640, 2048, "split_bf16", False),
             (4.0, 0, 1024, "fp32", True), (1.0 + 1 / 2048, 5, 133, "split_bf16", False),
             (5.0, 64, 1500, "split_bf16", True), (3.5, 0, 2048, "split_bf16", False),
-            (6.0, 17, 2000, "fft_fp32", True), (9.0, 0, 2048, "fft_fp32", False)]):
+            (6.0, 17, 2000, "fft_fp32", True), (9.0, 0, 2048, "fft_fp32", False),
+            (4.5, 30, 1800, "split_fp16", True), (2.5, 0, 2048, "split_fp16", False)]):
         n = int(secs * FS)
         x = synth.white(n, rng).astype(np.float32) if i % 2 == 0 else \
             synth.grb_lightcurve(n, FS, rng).astype(np.float32)
