@@ -8,8 +8,9 @@
 // an FP64 sum over the template, applied in FP32, where the hi/lo split of
 // the tensor-core layout is made too.
 //
-// GB300 runs FP64 at a small fraction of its FP32 rate, so the power-law phase
-// avoids a full FP64 pow: (1 - t/t_c)^(5/8) starts from the FP32 powf value and
+// GB300 runs FP64 at a small fraction of its FP32 rate, so FP64 is spent once
+// per group of 8 samples (synth_group below), and the power-law phase avoids
+// a full FP64 pow: (1 - t/t_c)^(5/8) starts from the FP32 powf value and
 // takes one Newton step on y^8 = u^5 in FP64 (relative error ~1e-7 squared),
 // whose reciprocal comes from an FP32 seed and one Newton-Raphson step.  Outputs, as requested:
 //   f32: row-major [K_pad][M_pad] float (SIMT path),
@@ -42,13 +43,54 @@ __device__ __forceinline__ double pow_5_8(double u)
     return y * fma(qv - 1.0, 0.125, 1.0);               // y - (y^8 - u^5) / (8 y^7)
 }
 
-// cycles elapsed at local time t of the ascending track; k1, k2 are
-// per-template constants (linear: f_lo and (f_hi - f_lo)/(2D); power law:
-// 1.6 f_lo t_c and 1/t_c)
-__device__ __forceinline__ double d_cycles(int track, double k1, double k2, double t)
+// Samples are made in groups of SYN_G consecutive template indices j0 + dir q.
+// The phase is evaluated in FP64 once per group, at an anchor sample j_a in
+// the group (clamped into the support), and carried to the others by the
+// exact phase difference over the short step d = (j - j_a) / fs, evaluated in
+// FP32 without cancellation:
+//   linear:    c(t_a + d) - c(t_a) = d (f(t_a) + k2 d);
+//   power law: c(t_a + d) - c(t_a) = k1 u_a^(5/8) (1 - (1 - d / (t_c - t_a))^(5/8))
+//              = -k1 u_a^(5/8) expm1(5/8 log1p(-d / (t_c - t_a))),
+// with u_a = 1 - t_a / t_c.  |d| <= SYN_G/2 samples keeps the difference
+// below ~2 cycles, where FP32 holds it to a few 1e-7 of a cycle.
+constexpr int SYN_G = 8;
+
+__device__ __forceinline__ void synth_group(float (&v)[SYN_G], int j0, int dir, float sign,
+                                            const ChirpDev& p, double k1, double k2, float k2f,
+                                            double inv_fs, float inv_fs_f, float inv_md, bool sine)
 {
-    if (track == BF_LINEAR) return t * fma(k2, t, k1);
-    return k1 * (1.0 - pow_5_8(fma(-t, k2, 1.0)));
+    const int j_lo = dir > 0 ? j0 : j0 - (SYN_G - 1);            // the group's index range
+    if (j_lo + SYN_G - 1 < 0 || j_lo >= p.MD) return;             // all outside the support
+    const int j_a = min(max(j0 + dir * (SYN_G / 2), 0), p.MD - 1);
+    const double t_a = (double)j_a * inv_fs;
+    double c_a;
+    float lin_f = 0.f, pw_amp = 0.f, pw_rate = 0.f;
+    if (p.track == BF_LINEAR) {
+        c_a = t_a * fma(k2, t_a, k1);
+        lin_f = (float)fma(2.0 * k2, t_a, k1);                    // f(t_a)
+    } else {
+        const double u_a = fma(-t_a, k2, 1.0);
+        const double pw = pow_5_8(u_a);
+        c_a = k1 * (1.0 - pw);
+        pw_amp = (float)(k1 * pw);
+        pw_rate = k2f / (float)u_a;                               // 1 / (t_c - t_a)
+    }
+    const float fr_a = (float)(c_a - rint(c_a));                  // [-1/2, 1/2]
+#pragma unroll
+    for (int q = 0; q < SYN_G; ++q) {
+        const int j = j0 + dir * q;
+        if (j < 0 || j >= p.MD) continue;
+        const float d = (float)(j - j_a) * inv_fs_f;
+        float dc = p.track == BF_LINEAR ? d * fmaf(k2f, d, lin_f)
+                                        : -pw_amp * expm1f(0.625f * log1pf(-d * pw_rate));
+        dc -= rintf(dc);                                          // exact
+        float fr = fr_a + dc;
+        fr -= rintf(fr);
+        const float f2 = 2.f * fr;                                // exact doubling
+        const float cs = sine ? sinpif(f2) : cospif(f2);
+        const float sn = sinpif(((float)j + 0.5f) * inv_md);
+        v[q] = fmaf(sign * sn * sn, cs, v[q]);
+    }
 }
 
 __device__ __forceinline__ size_t tc_offset(uint32_t k, uint32_t m, uint32_t n_kb)
@@ -95,29 +137,31 @@ __global__ void __launch_bounds__(256) k_bank_synth(const ChirpDev* __restrict__
         }
         inv_md = 1.0f / (float)p.MD;
     }
-    const uint32_t M_s = min(M_pad, (M + 63u) & ~63u);
+    const uint32_t M_s = min(M_pad, (M + 63u) & ~63u);      // a multiple of SYN_G
+    const float inv_fs_f = (float)inv_fs;
+    const float k2f = (float)k2;
     double part = 0.0;
-    for (uint32_t m = threadIdx.x; m < M_s; m += blockDim.x) {
-        float v = 0.f;
-        if (valid && m < M) {
-            // ascending-template sample index of m, and of its mirror M-1-m
-            const int ja = (int)m - p.first, jd = (int)(M - 1 - m) - p.first;
-            auto sample = [&](int j) -> float {
-                if (j < 0 || j >= p.MD) return 0.f;
-                const double c = d_cycles(p.track, k1, k2, (double)j * inv_fs);
-                const double fr = c - rint(c);             // [-1/2, 1/2]
-                const float f2 = 2.f * (float)fr;          // exact doubling in FP32
-                const float cs = sine ? sinpif(f2) : cospif(f2);
-                const float sn = sinpif(((float)j + 0.5f) * inv_md);
-                return sn * sn * cs;
-            };
+    for (uint32_t m0 = SYN_G * threadIdx.x; m0 < M_s; m0 += SYN_G * blockDim.x) {
+        float v[SYN_G];
+#pragma unroll
+        for (int q = 0; q < SYN_G; ++q) v[q] = 0.f;
+        if (valid && m0 < M) {
+            // ascending-template sample index of m0 (later samples count up),
+            // and of its mirror M-1-m0 (later samples count down)
             const float rev = sine ? -1.f : 1.f;       // the reversed part of a partner is negated
-            if (p.sense == BF_ASC) v = sample(ja);
-            else if (p.sense == BF_DESC) v = rev * sample(jd);
-            else v = sample(ja) + rev * sample(jd);    // superposition of both senses
+            if (p.sense != BF_DESC)
+                synth_group(v, (int)m0 - p.first, 1, 1.f, p, k1, k2, k2f, inv_fs, inv_fs_f, inv_md, sine);
+            if (p.sense != BF_ASC)
+                synth_group(v, (int)(M - 1 - m0) - p.first, -1, rev, p, k1, k2, k2f, inv_fs, inv_fs_f,
+                            inv_md, sine);
         }
-        g[m] = v;
-        part += (double)v * (double)v;
+        float gs = 0.f;                 // the group's sum of squares (8 terms, FP32)
+#pragma unroll
+        for (int q = 0; q < SYN_G; ++q) {
+            g[m0 + q] = v[q];
+            gs = fmaf(v[q], v[q], gs);
+        }
+        part += (double)gs;
     }
     // block sum of g^2 in FP64
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
