@@ -720,6 +720,24 @@ def run_serving_workload():
     print(json.dumps(out), flush=True)
 
 
+def k_block_fraction(p, fs, M):
+    """Fraction of the 64-sample K blocks the tensor-core kernel runs: a
+    128-template tile skips the blocks outside the union of its templates'
+    supports (centred sweeps of round(D fs) samples; a descending support is
+    the mirror of the ascending one)."""
+    MD = np.floor(p["D"] * fs + 0.5).astype(np.int64)
+    a0 = (M - MD) // 2
+    a1 = a0 + MD
+    lo = np.where(p["sense"] == 0, a0, np.where(p["sense"] == 1, M - a1, np.minimum(a0, M - a1)))
+    hi = np.where(p["sense"] == 0, a1, np.where(p["sense"] == 1, M - a0, np.maximum(a1, M - a0)))
+    K = len(MD)
+    pad = -K % 128
+    lo = np.concatenate([lo, np.full(pad, M)]).reshape(-1, 128).min(axis=1)
+    hi = np.concatenate([hi, np.zeros(pad, np.int64)]).reshape(-1, 128).max(axis=1)
+    blocks = -(-hi // 64) - lo // 64
+    return float(blocks.sum() / (len(blocks) * -(-M // 64)))
+
+
 def run_workload(name: str, n_check: int):
     """One timed search of a paper-sized workload other than the GW pair, with
     a sampled oracle check: 'grb_batch' (42 Poisson light curves of 20-200 s
@@ -777,7 +795,10 @@ def run_workload(name: str, n_check: int):
                                       "argmax_equal": int((got["argmax"][idx] == ref["argmax"]).sum()),
                                       "mean_of_maxima_finite": bool(np.all(np.isfinite(mean)))}}
         if prec != "fft_fp32":
-            out[mode]["issued_tflops"] = round(3 * 2 * M * info.correlations / (info.kernel_ms / 1e3) / 1e12, 1)
+            frac = k_block_fraction(p, fs, M)
+            out[mode]["k_blocks_run"] = round(frac, 4)
+            out[mode]["issued_tflops"] = round(3 * 2 * 64 * -(-M // 64) * frac * info.correlations
+                                               / (info.kernel_ms / 1e3) / 1e12, 1)
     bf.bf_destroy(ctx)
     print(json.dumps(out), flush=True)
 

@@ -143,6 +143,19 @@ static bool chirp_ok(const bf_chirp& c, double fs, uint32_t M, char* why, size_t
     return true;
 }
 
+// The samples [lo, hi) of the template row outside which it is zero: the
+// ascending support [m_s, m_s + M_D), its mirror [M - m_s - M_D, M - m_s) for a
+// descending chirp, and their union for both senses.  The quadrature partner
+// has the same support.
+static void row_support(const ChirpDev& d, uint32_t M, uint32_t& lo, uint32_t& hi)
+{
+    const uint32_t a0 = (uint32_t)d.first, a1 = a0 + (uint32_t)d.MD;
+    const uint32_t d0 = M - a1, d1 = M - a0;
+    if (d.sense == BF_ASC) { lo = a0; hi = a1; }
+    else if (d.sense == BF_DESC) { lo = d0; hi = d1; }
+    else { lo = std::min(a0, d0); hi = std::max(a1, d1); }
+}
+
 static ChirpDev to_dev(const bf_chirp& c, double fs, uint32_t M)
 {
     ChirpDev d{};
@@ -251,6 +264,7 @@ Seg make_segment(const PreparedSeries& ps, uint32_t series_id, const bf_bank* ba
     g.bank_f32 = bank->f32;
     g.bank_hi = bank->hi;
     g.bank_lo = bank->lo;
+    g.tile_kb = bank->tile_kb;
     g.vmax = packed_s;
     g.sumsq = sumsq_s;
     g.L = ps.L;
@@ -954,8 +968,24 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
     b->params.assign(params, params + K);
     std::vector<ChirpDev> dev(K);
     for (size_t k = 0; k < K; ++k) dev[k] = to_dev(params[k], fs, M);
+    // per 128-row tile, the 64-sample blocks that hold any nonzero sample
+    const size_t n_tiles = b->K_pad / TC_TILE_T;
+    std::vector<uint32_t> tkb(n_tiles);
+    for (size_t t = 0; t < n_tiles; ++t) {
+        uint32_t lo = UINT32_MAX, hi = 0;
+        for (size_t r = t * TC_TILE_T; r < std::min((t + 1) * TC_TILE_T, b->rows); ++r) {
+            uint32_t a, z;
+            row_support(dev[quad ? r / 2 : r], M, a, z);
+            lo = std::min(lo, a);
+            hi = std::max(hi, z);
+        }
+        const uint32_t kb_lo = lo < hi ? lo / TC_BK : 0;
+        const uint32_t kb_hi = lo < hi ? (uint32_t)ceil_div(hi, TC_BK) : 1;
+        tkb[t] = kb_lo | (kb_hi << 16);
+    }
     Allocator& mem = *ctx->mem;
     b->d_params = static_cast<ChirpDev*>(mem.alloc(K * sizeof(ChirpDev)));
+    b->tile_kb = static_cast<uint32_t*>(mem.alloc(n_tiles * sizeof(uint32_t)));
     const size_t elems = b->K_pad * (size_t)b->M_pad;
     if (storage & BF_BANK_FP32) b->f32 = static_cast<float*>(mem.alloc(elems * 4));
     if (storage & BF_BANK_SPLIT_BF16) {
@@ -966,7 +996,7 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
         b->hi16 = static_cast<uint8_t*>(mem.alloc(elems * 2));
         b->lo16 = static_cast<uint8_t*>(mem.alloc(elems * 2));
     }
-    if (!b->d_params || ((storage & BF_BANK_FP32) && !b->f32) ||
+    if (!b->d_params || !b->tile_kb || ((storage & BF_BANK_FP32) && !b->f32) ||
         ((storage & BF_BANK_SPLIT_BF16) && (!b->hi || !b->lo)) ||
         ((storage & BF_BANK_SPLIT_FP16) && (!b->hi16 || !b->lo16))) {
         bf_bank_destroy(b.release());
@@ -977,6 +1007,8 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
     cudaStream_t st = ctx->stream;
     cudaError_t e = cudaMemcpyAsync(b->d_params, dev.data(), K * sizeof(ChirpDev),
                                     cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->tile_kb, tkb.data(), n_tiles * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !generated)
         e = launch_bank_synth(b->d_params, 0, quad, (uint32_t)b->rows, (uint32_t)b->K_pad, M, b->M_pad, fs,
                               b->f32, b->hi, b->lo, st, b->hi16, b->lo16);
@@ -1029,6 +1061,7 @@ void bf_bank_destroy(bf_bank* b)
     mem.release(b->lo);
     mem.release(b->hi16);
     mem.release(b->lo16);
+    mem.release(b->tile_kb);
     delete b;
 }
 

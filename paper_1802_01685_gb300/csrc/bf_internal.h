@@ -70,6 +70,10 @@ struct Seg {
                                     // |rho| >= kappa * sigma_pred[k]
     const uint32_t* xmax;           // split-FP16 only: float bits of max |x|, from
                                     // which the operand scales are derived
+    const uint32_t* tile_kb;        // per 128-row template tile (absolute index):
+                                    // kb_lo | kb_hi << 16, the 64-sample blocks
+                                    // [kb_lo, kb_hi) outside which every row of
+                                    // the tile is zero; the K loops skip the rest
     float kappa;
     float pad2;
     uint32_t bank_k0;               // template row held at the bank pointers
@@ -294,6 +298,7 @@ struct bf_bank {
     uint8_t* lo = nullptr;
     uint8_t* hi16 = nullptr;            // split-FP16 layout (2^8 h)
     uint8_t* lo16 = nullptr;
+    uint32_t* tile_kb = nullptr;        // nonzero 64-sample block range per 128-row tile
     float* ph = nullptr;                // template power spectra [K_pad][M+1] (lazy)
     float2* fspec = nullptr;            // template half spectra for the FFT route (lazy)
 };

@@ -33,7 +33,15 @@ __global__ void __launch_bounds__(SIMT_THREADS, 2) k_corr_simt(const __grid_cons
 #pragma unroll
             for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
 
-        for (uint32_t m0 = 0; m0 < s.M_pad; m0 += SIMT_BK) {
+        // the 64-sample blocks of the 128-row tile holding this 64-row tile
+        // outside which all its rows are zero (SIMT_BK divides 64)
+        uint32_t m_lo = 0, m_hi = s.M_pad;
+        if (s.tile_kb) {
+            const uint32_t r = s.tile_kb[k0 / TC_TILE_T];
+            m_lo = (r & 0xffffu) * TC_BK;
+            m_hi = min((r >> 16) * TC_BK, s.M_pad);
+        }
+        for (uint32_t m0 = m_lo; m0 < m_hi; m0 += SIMT_BK) {
             __syncthreads();
             for (int i = tid; i < SIMT_TILE_T * SIMT_BK / 4; i += SIMT_THREADS) {
                 int row = i / (SIMT_BK / 4), c4 = i % (SIMT_BK / 4);

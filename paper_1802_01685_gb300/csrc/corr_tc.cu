@@ -333,6 +333,20 @@ struct TileCoord {
     uint32_t tt, lag0;
 };
 
+// The K blocks of template tile tt that hold nonzero samples (all of them
+// without a range table); the host guarantees lo < hi <= n_kb.  Skipped blocks
+// are zero in every row of the tile, so the outputs are the full loop's.
+struct KRange {
+    uint32_t lo, hi;
+};
+
+__device__ __forceinline__ KRange k_range(const Seg& s, uint32_t tt, uint32_t n_kb)
+{
+    if (!s.tile_kb) return {0u, n_kb};
+    const uint32_t r = s.tile_kb[tt];
+    return {r & 0xffffu, min(r >> 16, n_kb)};
+}
+
 template <int LT>
 __device__ __forceinline__ TileCoord tile_coord(const CorrParams& p, uint64_t t)
 {
@@ -402,10 +416,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             for (uint64_t t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
                 const TileCoord c = tile_coord<LT>(p, t);
                 const uint32_t n_kb = c.s->M_pad / TC_BK;
+                const KRange kr = k_range(*c.s, c.tt, n_kb);
                 const size_t tt_rel = c.tt - c.s->bank_k0 / TC_TILE_T;
                 const uint8_t* a_hi = c.s->bank_hi + tt_rel * n_kb * A_BYTES;
                 const uint8_t* a_lo = c.s->bank_lo + tt_rel * n_kb * A_BYTES;
-                for (uint32_t kb = 0; kb < n_kb; ++kb) {
+                for (uint32_t kb = kr.lo; kb < kr.hi; ++kb) {
                     if (!mbar_wait(empty_bar(st), ph ^ 1, abort_flag)) {
                         if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_EMPTY);
                         *abort_flag = 1;
@@ -441,14 +456,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             bool ok = true;
             for (uint64_t t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
                 const TileCoord c = tile_coord<LT>(p, t);
-                const uint32_t n_kb = c.s->M_pad / TC_BK;
+                const KRange kr = k_range(*c.s, c.tt, c.s->M_pad / TC_BK);
                 if (!mbar_wait(tempty_bar(buf), ((tph >> buf) & 1) ^ 1, abort_flag)) {
                     if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_TMEM);
                     *abort_flag = 1;
                     break;
                 }
                 fence_after();
-                for (uint32_t kb = 0; kb < n_kb; ++kb) {
+                for (uint32_t kb = kr.lo; kb < kr.hi; ++kb) {
                     if (!mbar_wait(full_bar(st), ph, abort_flag)) {
                         if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_FULL);
                         *abort_flag = 1;
@@ -467,7 +482,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
                             const uint64_t bhi = make_desc(sbase + G::OFF_BHI + boff, 128, 128);
                             const uint64_t blo = make_desc(sbase + G::OFF_BLO + boff, 128, 128);
                             const uint32_t d = tmem + buf * 256 + h * 256;
-                            mma_f16(d, ahi, bhi, p.idesc, (kb | kk) != 0);
+                            mma_f16(d, ahi, bhi, p.idesc, (kb != kr.lo) | (kk != 0));
                             if (NPROD == 3) {
                                 mma_f16(d, ahi, blo, p.idesc, 1);
                                 mma_f16(d, alo, bhi, p.idesc, 1);

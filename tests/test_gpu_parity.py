@@ -496,3 +496,45 @@ def test_concurrent_calls_from_threads(ctx, tiny):
         np.testing.assert_array_equal(g["max"], a["max"])
         np.testing.assert_array_equal(g["argmax"], a["argmax"])
         np.testing.assert_array_equal(g["hist"], a["hist"])
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "split_fp16"])
+def test_zero_blocks_skipped_exactly(ctx, prec):
+    """Templates sweeping 0.2-0.7 s of a 1 s window are zero outside their
+    support, and a tile of them skips those 64-sample blocks of the K loop.
+    The same templates in tiles that each also hold a full-length template
+    (so every block runs) give the same outputs bit for bit, and both match
+    the oracle."""
+    fs, M = 2048.0, 2048
+    rng = np.random.default_rng(33)
+
+    def chirps(n, D, sense):
+        f_lo = rng.uniform(20.0, 400.0, n)
+        f_hi = f_lo + rng.uniform(50.0, 500.0, n)
+        return [(int(rng.integers(2)), sense, float(a), float(b), D) for a, b in zip(f_lo, f_hi)]
+
+    short = chirps(128, 0.2, bf.BF_ASC) + chirps(128, 0.45, bf.BF_DESC) + chirps(50, 0.7, bf.BF_BOTH)
+    full = (bf.BF_LINEAR, bf.BF_ASC, 100.0, 900.0, 1.0)
+    mixed, where = [], []
+    for i, c in enumerate(short):
+        if len(mixed) % 128 == 0:
+            mixed.append(full)
+        where.append(len(mixed))
+        mixed.append(c)
+    x = rng.standard_normal(7000)
+    x[3000:3000 + M] += 25.0 * oracle.template(*short[140], fs, M)
+    x = x.astype(np.float32)
+    a_bank = bf.bf_bank_create(ctx, short, fs, 1.0, STORE_ALL)
+    b_bank = bf.bf_bank_create(ctx, mixed, fs, 1.0, STORE_ALL)
+    a = run(ctx, a_bank, [x], fs, prec, want_tails=True)[0][0]
+    b = run(ctx, b_bank, [x], fs, prec, want_tails=True)[0][0]
+    for key in ("max", "argmax", "sigma"):
+        np.testing.assert_array_equal(a[key], b[key][where])
+    p = {k: np.array([c[i] for c in short], dt)
+         for i, (k, dt) in enumerate((("track", np.int32), ("sense", np.int32), ("f_lo", np.float64),
+                                      ("f_hi", np.float64), ("D", np.float64)))}
+    ref = oracle.search(x, fs, p, M, want_rho=True)
+    check_maxima(a, ref, ref["rho"], TOL[prec], prec)
+    assert a["argmax"][140] == 3000
+    bf.bf_bank_destroy(a_bank)
+    bf.bf_bank_destroy(b_bank)
