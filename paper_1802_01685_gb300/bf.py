@@ -337,21 +337,33 @@ def bf_result_get_mean_max(res: int) -> int:
     return a.value
 
 
-def bf_result_copy_to_host(res: int, s: int, want_hist=True, want_map=False) -> dict:
+def bf_result_copy_to_host(res: int, s: int, want_hist=True, want_map=False, out: dict | None = None) -> dict:
+    """Per-template max, argmax and sigma of series s, and optionally its
+    histogram and map, copied into new numpy arrays, or into the caller's
+    arrays in ``out`` (keys max, argmax, sigma, hist, map: C-contiguous, of the
+    result's sizes and dtypes float32, int32, float32, uint32, float32), for
+    instance views of pinned host memory reused across calls."""
     info = bf_result_info_get(res)
     K = info.n_templates
-    vmax = np.zeros(K, np.float32)
-    arg = np.zeros(K, np.int32)
-    sig = np.zeros(K, np.float32)
-    hist = np.zeros(info.hist_bins, np.uint32) if want_hist else None
-    mp = None
+    shapes = {"max": ((K,), np.float32), "argmax": ((K,), np.int32), "sigma": ((K,), np.float32)}
+    if want_hist:
+        shapes["hist"] = ((info.hist_bins,), np.uint32)
     if want_map:
-        nt, nf = bf_result_map_shape(res, s)
-        mp = np.zeros((nt, nf), np.float32)
+        shapes["map"] = (tuple(bf_result_map_shape(res, s)), np.float32)
+    arrs = {}
+    for key, (shape, dt) in shapes.items():
+        a = out.get(key) if out is not None else None
+        if a is None:
+            a = np.zeros(shape, dt)
+        elif a.shape != shape or a.dtype != dt or not a.flags.c_contiguous or not a.flags.writeable:
+            raise ValueError(f"out[{key!r}] must be a writeable C-contiguous {np.dtype(dt).name} "
+                             f"array of shape {shape}")
+        arrs[key] = a
+    hist, mp = arrs.get("hist"), arrs.get("map")
     _check(load().bf_result_copy_to_host(
-        res, s, vmax.ctypes.data, arg.ctypes.data, sig.ctypes.data,
+        res, s, arrs["max"].ctypes.data, arrs["argmax"].ctypes.data, arrs["sigma"].ctypes.data,
         hist.ctypes.data if hist is not None else None, mp.ctypes.data if mp is not None else None))
-    return dict(max=vmax, argmax=arg, sigma=sig, hist=hist, map=mp)
+    return dict(max=arrs["max"], argmax=arrs["argmax"], sigma=arrs["sigma"], hist=hist, map=mp)
 
 
 def bf_result_copy_mean_max(res: int) -> np.ndarray:

@@ -538,3 +538,28 @@ def test_zero_blocks_skipped_exactly(ctx, prec):
     assert a["argmax"][140] == 3000
     bf.bf_bank_destroy(a_bank)
     bf.bf_bank_destroy(b_bank)
+
+
+def test_copy_into_caller_buffers(ctx, tiny):
+    """Results copied into caller-owned (pinned) host arrays equal the
+    default copy; arrays of the wrong shape or dtype are refused."""
+    w, bank, _, _ = tiny
+    x, fs = w["series"][0], w["fs"]
+    res = bf.bf_correlate(ctx, bank, [x], fs, bf.make_opts(want_map=True))
+    ref = bf.bf_result_copy_to_host(res, 0, want_hist=True, want_map=True)
+    K, nb = len(ref["max"]), len(ref["hist"])
+    out = {"max": torch.full((K,), -1.0, pin_memory=True).numpy(),
+           "argmax": torch.full((K,), -1, dtype=torch.int32, pin_memory=True).numpy(),
+           "sigma": torch.zeros(K, pin_memory=True).numpy(),
+           "hist": torch.zeros(nb, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32),
+           "map": torch.zeros(ref["map"].shape, pin_memory=True).numpy()}
+    for _ in range(2):                                           # reused across calls
+        got = bf.bf_result_copy_to_host(res, 0, want_hist=True, want_map=True, out=out)
+        for key in ref:
+            assert got[key] is out[key]
+            np.testing.assert_array_equal(got[key], ref[key])
+    with pytest.raises(ValueError):
+        bf.bf_result_copy_to_host(res, 0, out={"max": np.zeros(K + 1, np.float32)})
+    with pytest.raises(ValueError):
+        bf.bf_result_copy_to_host(res, 0, out={"argmax": np.zeros(K, np.int64)})
+    bf.bf_result_destroy(res)
