@@ -378,7 +378,7 @@ void bf_result_destroy(bf_result* r);
  * plan and launches the graph on `stream` (NULL: synchronously on the
  * context stream).  *out points at the plan's result: valid until the next run
  * or bf_plan_destroy, read with the bf_result_* calls, never destroyed by the
- * caller.  Stored banks only (BF_ENOTSUP for a generated bank).  Runs of one
+ * caller (bf_result_destroy on it does nothing but set bf_last_error).  Stored banks only (BF_ENOTSUP for a generated bank).  Runs of one
  * plan must not overlap on the GPU.
  */
 typedef struct bf_plan bf_plan;

@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libbf.so")
 
 SOURCES = ["api.cu", "serve.cu", "bank.cu", "prep.cu", "corr_simt.cu", "corr_tc.cu",
            "finalize.cu", "permute.cu", "noalloc.cu", "plan.cu", "predict.cu", "corr_fft.cu"]
-HEADERS = ["bf_internal.h", "runtime.h", "corr_common.cuh"]
+HEADERS = ["bf_internal.h", "runtime.h", "corr_common.cuh", "synth.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # hidden visibility: only the declarations of include/bf.h are exported

@@ -246,7 +246,8 @@ size_t prepared_series_bytes(size_t N, uint32_t M, uint32_t M_pad, int precision
     size_t b = (ceil_div(L, SIMT_TILE_L) * SIMT_TILE_L + M_pad + 1024) * 4 + L * 4 + prefix_bytes(N) +
                inv_norm_scratch_blocks(N) * 8;
     if (uses_split_rows(precision)) b += 2 * (ceil_div(L, TC_TILE_L) * TC_TILE_L + M_pad + 64) * 16;
-    if (precision == BF_FFT_FP32) b += (size_t)fft_segments((uint32_t)L, M) * (FFT_POINTS / 2) * 8;
+    if (precision == BF_FFT_FP32)                               // segment spectra, fixup list
+        b += (size_t)fft_segments((uint32_t)L, M) * (FFT_POINTS / 2) * 8 + (L + 1) * 4;
     if (precision == BF_SPLIT_FP16) b += 4096;                  // max |x|
     return b + 8 * 4096;
 }
@@ -303,6 +304,7 @@ void build_segments(const std::vector<PreparedSeries*>& ser, const std::vector<u
 // tiles, two waves of tiles each, and keeps the faster one per context.
 int choose_lag_tile(bf_ctx* ctx, const Seg& g, int precision, cudaStream_t st)
 {
+    if (precision != BF_BF16) return TC_TILE_L / 2;      // the split routes have one shape
     const std::pair<int, uint32_t> key(precision, g.M_pad);
     {
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
@@ -389,6 +391,8 @@ cudaError_t launch_segments(bf_ctx* ctx, const std::vector<Seg>& segs, int preci
         p.cand_cap = cand_cap;
         p.err = ctx->d_err;
         p.idesc = tc_idesc(precision);
+        // accumulator chunks of 2048 samples (split-BF16) or 1024 (split-FP16)
+        p.kchunk_log2 = precision == BF_SPLIT_FP16 ? 4u : 5u;
         cudaError_t e = precision == BF_FP32 ? launch_corr_simt(p, st)
                                              : launch_corr_tc(p, precision == BF_BF16 ? 1 : 3,
                                                               lt, ctx->n_sm, st);
@@ -464,6 +468,11 @@ bf_status resolve_opts(const bf_bank* bank, const bf_opts* in, bf_opts* o)
     }
     if (o->tail_sigma != BF_SIGMA_WHITE && o->tail_sigma != BF_SIGMA_PARSEVAL) {
         set_error("unknown tail_sigma %d", o->tail_sigma);
+        return BF_EINVAL;
+    }
+    if (o->tile_lags == TC_TILE_L && (o->precision == BF_SPLIT_BF16 || o->precision == BF_SPLIT_FP16)) {
+        set_error("tile_lags 512 holds one accumulator and serves BF_BF16 only; the split "
+                  "precisions accumulate K in chunks across two accumulators (use 0 or 256)");
         return BF_EINVAL;
     }
     if (o->tile_lags != 0 && o->tile_lags != TC_TILE_L && o->tile_lags != TC_TILE_L / 2) {
@@ -728,23 +737,38 @@ bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
         FftSeriesBatch b{};
         FftParams p{};
         uint32_t total = 0;
+        b.n_fix = static_cast<uint32_t*>(ctx->mem->alloc((size_t)n * sizeof(uint32_t)));
+        if (!b.n_fix) {
+            set_error("out of device memory for the fixup lists");
+            return BF_ENOMEM;
+        }
+        r->scratch.push_back(b.n_fix);
         for (int i = 0; i < n; ++i) {
             const size_t s = s0 + i;
             const uint32_t nseg = fft_segments(prep[s].L, bank->M);
             float2* spec = static_cast<float2*>(ctx->mem->alloc((size_t)nseg * (FFT_POINTS / 2) * sizeof(float2)));
-            if (!spec) {
+            uint32_t* fix = static_cast<uint32_t*>(ctx->mem->alloc((size_t)prep[s].L * sizeof(uint32_t)));
+            if (spec) r->scratch.push_back(spec);
+            if (fix) r->scratch.push_back(fix);
+            if (!spec || !fix) {
                 set_error("out of device memory for the segment spectra");
                 return BF_ENOMEM;
             }
-            r->scratch.push_back(spec);
             b.x[i] = prep[s].x;
             b.N[i] = prep[s].N;
             b.spec[i] = spec;
             b.seg_begin[i] = total;
+            b.S[i] = prep[s].prefix;
+            b.inv[i] = prep[s].inv;
+            b.L[i] = (uint32_t)prep[s].L;
+            b.fix[i] = fix;
             total += nseg;
             FftSeries& f = p.ser[i];
             f.spec = spec;
             f.inv = prep[s].inv;
+            f.x = prep[s].x;
+            f.fix = fix;
+            f.n_fix = b.n_fix + i;
             f.vmax = r->packed + s * K;
             f.sumsq = r->sumsq + s * K;
             f.rho = s == 0 ? o.rho_out : nullptr;
@@ -767,6 +791,9 @@ bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
         p.cand_cap = r->cand_cap;
         p.cand = r->cand;
         p.cand_count = r->cand_count;
+        p.chirps = bank->d_params;
+        p.M = bank->M;
+        p.fs = bank->fs;
         c->series.push_back(b);
         c->totals.push_back(total);
         c->batches.push_back(p);
@@ -1471,6 +1498,10 @@ bf_status bf_result_copy_tails(const bf_result* r, bf_tail* host, size_t cap, si
 void bf_result_destroy(bf_result* r)
 {
     if (!r) return;
+    if (r->plan_owned) {            // bf_plan_destroy frees it
+        set_error("bf_result_destroy: the result belongs to a plan (freed by bf_plan_destroy)");
+        return;
+    }
     free_result_buffers(r);
     delete r;
 }

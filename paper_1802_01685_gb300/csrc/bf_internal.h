@@ -99,20 +99,34 @@ struct CorrParams {
     Candidate* cand;
     unsigned int* cand_count;
     int* err;                       // device status word
+    uint32_t kchunk_log2;           // split routes: K blocks per accumulator chunk, log2
+    uint32_t pad3;
     Seg seg[MAX_SEG];
 };
 
 // The FFT route (corr_fft.cu): overlap-save over segments of FFT_POINTS samples.
 constexpr int FFT_POINTS = 8192;
 constexpr int MAX_FFT_SER = 64;           // series per FFT launch
+// A lag goes to the direct fixup when its window holds less than 1/16384 of
+// the energy of its FFT segment (|x_seg| / |x_window| > 128): the transform's
+// rounding error scales with the segment (measured: at most 3.5e-8 |x_seg| /
+// |x_window| in rho), so beyond that ratio it could exceed a quarter of the
+// bound on rho.
+constexpr double FFT_FIX_RATIO2 = 16384.0;
+
+struct ChirpDev;
 
 struct FftSeries {
     const float2* spec;             // [nseg][FFT_POINTS / 2] segment half spectra
-    const float* inv;               // [L] inverse window norms
+    const float* inv;               // [L] inverse window norms; negated at the
+                                    // lags left to the direct fixup
     unsigned long long* vmax;       // packed max per template, index k - k_begin
     double* sumsq;
     float* rho;                     // optional dense output [k - k_begin][tau]
     const float* sigma_pred;        // optional per-template predicted sigma
+    const float* x;                 // FP32 samples (for the direct fixup)
+    const uint32_t* fix;            // lags left to the direct fixup ...
+    const uint32_t* n_fix;          // ... and how many
     float kappa;
     uint32_t L, nseg, series_id;
 };
@@ -130,6 +144,9 @@ struct FftParams {
     unsigned int cand_cap;
     Candidate* cand;
     unsigned int* cand_count;
+    const ChirpDev* chirps;         // bank parameters (the fixup synthesises its rows)
+    uint32_t M;                     // template length (at most FFT_POINTS / 2)
+    double fs;
     FftSeries ser[MAX_FFT_SER];
 };
 
@@ -141,6 +158,13 @@ struct FftSeriesBatch {
     uint64_t N[MAX_FFT_SER];
     float2* spec[MAX_FFT_SER];
     uint32_t seg_begin[MAX_FFT_SER];
+    // lags for the direct fixup: found from the FP64 prefix of x^2 and the
+    // inverse norms (negated there), listed in fix[i], counted in n_fix[i]
+    const double* S[MAX_FFT_SER];
+    float* inv[MAX_FFT_SER];
+    uint32_t L[MAX_FFT_SER];
+    uint32_t* fix[MAX_FFT_SER];
+    uint32_t* n_fix;                // [n] counters, zeroed by launch_fft_series
 };
 
 // ---------------------------------------------------------------- launchers
@@ -305,6 +329,7 @@ struct bf_bank {
 
 struct bf_result {
     bf_ctx* ctx = nullptr;
+    bool plan_owned = false;            // a plan's result: bf_result_destroy leaves it alone
     size_t n_series = 0, K = 0, k_begin = 0;
     uint32_t M = 0, nbins = 0;
     double fs = 0, dt = 0, df = 0;

@@ -43,6 +43,7 @@
 //    rounded from FP64 once per context and copied into shared memory by
 //    every CTA.
 #include "corr_common.cuh"
+#include "synth.cuh"
 #include "runtime.h"
 
 namespace bfi {
@@ -462,17 +463,19 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t t = (uint32_t)(tid + FT * i + FH * h);
-                if (QUAD && t < nv) {
+                // a negated norm marks a lag left to the direct fixup
+                const float iv = t < nv ? m.inv[t] : -1.f;
+                if (QUAD && iv >= 0.f) {
                     // quadrature pair: |c_cos + i c_sin| / |window|
                     const uint32_t tau = t0 + t;
-                    const float r = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * (m.inv[t] * scale);
+                    const float r = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * (iv * scale);
                     track_max(r, tau, best_a, arg_a);
                     pa = fmaf(r, r, pa);
                     if (r >= thr_a) push_tail(p, S.series_id, ka >> 1, tau, r);
                     if (S.rho) S.rho[(size_t)la * S.L + tau] = r;
-                } else if (!QUAD && t < nv) {
+                } else if (!QUAD && iv >= 0.f) {
                     const uint32_t tau = t0 + t;
-                    const float inv = m.inv[t] * scale;
+                    const float inv = iv * scale;
                     const float ra = z[h].x * inv, rb = z[h].y * inv;
                     const float aa = fabsf(ra), ab = fabsf(rb);
                     track_max(aa, tau, best_a, arg_a);
@@ -524,6 +527,122 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
         j = nj;
     }
     cp_async_wait<0>();
+}
+
+// Lags whose window holds less than 1/FFT_FIX_RATIO2 of the energy of its
+// FFT segment (e.g. a quiet stretch or the tapered edge of a loud chirp next to
+// silence): the transform's rounding error scales with the segment, so there it
+// would swamp rho.  They are marked by negating the inverse norm, which the
+// correlation epilogue skips, and listed for k_fft_fixup.  The energies come
+// from the FP64 prefix of x^2.  One grid row per series.
+__global__ void __launch_bounds__(256) k_fft_flags(const __grid_constant__ FftSeriesBatch b)
+{
+    const int i = blockIdx.y;
+    if (i >= b.n) return;
+    const uint64_t L = b.L[i], N = b.N[i];
+    const double* S = b.S[i];
+    float* inv = b.inv[i];
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < L;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const float iv = inv[t];
+        if (!(iv > 0.f)) continue;                      // empty window: rho = 0 exactly
+        const uint64_t a = t / b.V * b.V;               // the segment's first sample
+        const uint64_t e = min(a + (uint64_t)FN, N);
+        const double E = S[e] - S[a];
+        if (E * (double)iv * (double)iv > FFT_FIX_RATIO2) {
+            inv[t] = -iv;
+            b.fix[i][atomicAdd(b.n_fix + i, 1u)] = (uint32_t)t;    // each lag once: < L entries
+        }
+    }
+}
+
+// The direct computation of the listed lags: each CTA takes outputs (a row, or
+// a quadrature pair of rows) of the launch's range, synthesises their
+// templates in shared memory as the bank does (FP32 rows at unit norm), and
+// for every listed lag of every series forms the FP32 dot product with the
+// window (one warp per lag), then feeds the same max keys, sums of rho^2,
+// tails and dense output as the correlation kernel.  Returns at once when no
+// series has a listed lag.
+constexpr int FIX_T = 256;
+
+template <bool QUAD>
+__global__ void __launch_bounds__(FIX_T) k_fft_fixup(const __grid_constant__ FftParams p)
+{
+    __shared__ float g[QUAD ? 2 : 1][FH];               // templates of at most FH samples
+    __shared__ double red[8];
+    __shared__ unsigned long long w_key[FIX_T / 32];
+    __shared__ double w_ss[FIX_T / 32];
+    uint32_t total = 0;
+    for (int i = 0; i < p.n_ser; ++i) total += *p.ser[i].n_fix;
+    if (total == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rows = QUAD ? 2u : 1u;
+    const uint32_t n_out = (p.k_hi - p.k_lo) / rows;
+    const uint32_t M = p.M, M_s = (M + 63u) & ~63u;
+    for (uint32_t u = blockIdx.x; u < n_out; u += gridDim.x) {
+        const uint32_t row = p.k_lo + rows * u;
+        const float n0 = synth_row(p.chirps, row, p.quad, true, M, M_s, p.fs, g[0], red);
+        const float n1 = QUAD ? synth_row(p.chirps, row + 1, p.quad, true, M, M_s, p.fs, g[QUAD ? 1 : 0], red)
+                              : 0.f;
+        for (uint32_t m = threadIdx.x; m < M_s; m += FIX_T) {
+            g[0][m] *= n0;
+            if (QUAD) g[QUAD ? 1 : 0][m] *= n1;
+        }
+        __syncthreads();
+        const uint32_t o = QUAD ? (row - p.k_begin) >> 1 : row - p.k_begin;    // output index
+        const uint32_t kt = QUAD ? row >> 1 : row;                             // tail index
+        for (int i = 0; i < p.n_ser; ++i) {
+            const FftSeries& S = p.ser[i];
+            const uint32_t n = min(*S.n_fix, S.L);
+            if (n == 0) continue;
+            const float thr = S.sigma_pred ? S.kappa * S.sigma_pred[o] : p.thr;
+            unsigned long long best = 0ull;
+            double ss = 0.0;
+            for (uint32_t f = warp; f < n; f += FIX_T / 32) {
+                const uint32_t tau = S.fix[f];
+                const float* xw = S.x + tau;
+                float c = 0.f, d = 0.f;
+                for (uint32_t m = lane; m < M; m += 32) {
+                    const float xv = xw[m];
+                    c = fmaf(xv, g[0][m], c);
+                    if (QUAD) d = fmaf(xv, g[QUAD ? 1 : 0][m], d);
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    c += __shfl_xor_sync(0xffffffffu, c, off);
+                    if (QUAD) d += __shfl_xor_sync(0xffffffffu, d, off);
+                }
+                const float iv = -S.inv[tau];                  // negated by k_fft_flags
+                const float r = QUAD ? sqrtf(c * c + d * d) * iv : c * iv;
+                const float a = fabsf(r);
+                if (lane == 0) {
+                    const unsigned long long key = pack_max(a, tau);
+                    best = key > best ? key : best;
+                    ss += (double)r * (double)r;
+                    if (a >= thr) push_tail(p, S.series_id, kt, tau, r);
+                    if (S.rho) S.rho[(size_t)o * S.L + tau] = r;
+                }
+            }
+            if (lane == 0) {
+                w_key[warp] = best;
+                w_ss[warp] = ss;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned long long kmax = 0ull;
+                double tot = 0.0;
+                for (int w = 0; w < FIX_T / 32; ++w) {
+                    kmax = w_key[w] > kmax ? w_key[w] : kmax;
+                    tot += w_ss[w];
+                }
+                if (kmax != 0ull) {
+                    atomicMax(S.vmax + o, kmax);
+                    atomicAdd(S.sumsq + o, tot);
+                }
+            }
+            __syncthreads();
+        }
+    }
 }
 
 cudaError_t fft_attributes()
@@ -635,6 +754,16 @@ cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, 
     if (total_segments == 0) return cudaSuccess;
     count_launches(1);
     k_fft_series<<<std::min<uint32_t>(total_segments, (uint32_t)n_sm), FT, FFT_SMEM, st>>>(b, total_segments);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !b.n_fix) return e;
+    // the lags for the direct fixup
+    e = cudaMemsetAsync(b.n_fix, 0, (size_t)b.n * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    uint32_t L_max = 0;
+    for (int i = 0; i < b.n; ++i) L_max = std::max(L_max, b.L[i]);
+    const unsigned bx = (unsigned)std::max<uint32_t>(1, std::min<uint32_t>((L_max + 255) / 256, 1024));
+    count_launches(1);
+    k_fft_flags<<<dim3(bx, (unsigned)b.n), 256, 0, st>>>(b);
     return cudaGetLastError();
 }
 
@@ -646,6 +775,15 @@ cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st)
     count_launches(1);
     if (p.quad) k_corr_fft<true><<<grid, FT, CORR_SMEM, st>>>(p);
     else k_corr_fft<false><<<grid, FT, CORR_SMEM, st>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !p.chirps) return e;
+    // the lags left to the direct computation (none: the CTAs return at once)
+    const uint32_t n_out = p.quad ? (p.k_hi - p.k_lo) / 2 : p.k_hi - p.k_lo;
+    if (n_out == 0) return e;
+    const unsigned fgrid = std::min<unsigned>(n_out, (unsigned)n_sm * 8);
+    count_launches(1);
+    if (p.quad) k_fft_fixup<true><<<fgrid, FIX_T, 0, st>>>(p);
+    else k_fft_fixup<false><<<fgrid, FIX_T, 0, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -202,6 +202,33 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32])
                  : "memory");
 }
 
+// TMEM stores complete after tmem_st_wait().
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// 64-column forms of the TMEM load and store, for the fold of a K chunk
+__device__ __forceinline__ void tmem_ld64_async(uint32_t taddr, uint32_t (&r)[64])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait64(uint32_t (&r)[64])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]), "+r"(r[36]), "+r"(r[37]), "+r"(r[38]), "+r"(r[39]), "+r"(r[40]), "+r"(r[41]), "+r"(r[42]), "+r"(r[43]), "+r"(r[44]), "+r"(r[45]), "+r"(r[46]), "+r"(r[47]), "+r"(r[48]), "+r"(r[49]), "+r"(r[50]), "+r"(r[51]), "+r"(r[52]), "+r"(r[53]), "+r"(r[54]), "+r"(r[55]), "+r"(r[56]), "+r"(r[57]), "+r"(r[58]), "+r"(r[59]), "+r"(r[60]), "+r"(r[61]), "+r"(r[62]), "+r"(r[63])
+                 :
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st64(uint32_t taddr, const uint32_t (&r)[64])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63,%64};"
+                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]), "r"(r[32]), "r"(r[33]), "r"(r[34]), "r"(r[35]), "r"(r[36]), "r"(r[37]), "r"(r[38]), "r"(r[39]), "r"(r[40]), "r"(r[41]), "r"(r[42]), "r"(r[43]), "r"(r[44]), "r"(r[45]), "r"(r[46]), "r"(r[47]), "r"(r[48]), "r"(r[49]), "r"(r[50]), "r"(r[51]), "r"(r[52]), "r"(r[53]), "r"(r[54]), "r"(r[55]), "r"(r[56]), "r"(r[57]), "r"(r[58]), "r"(r[59]), "r"(r[60]), "r"(r[61]), "r"(r[62]), "r"(r[63])
+                 : "memory");
+}
+
+
 constexpr uint32_t EPI_THREADS = TC_THREADS - 64;            // 256
 
 // OR of a predicate over the epilogue threads (named barrier 1)
@@ -347,6 +374,39 @@ __device__ __forceinline__ KRange k_range(const Seg& s, uint32_t tt, uint32_t n_
     return {r & 0xffffu, min(r >> 16, n_kb)};
 }
 
+// K blocks (64 samples each) accumulated in one TMEM accumulator before the
+// epilogue folds them into the tile's sum (2^p.kchunk_log2 blocks).  The
+// tensor core adds each MMA's product sum to its FP32 accumulator with
+// truncation, so each addition may lose part of an ulp of the running sum: on a
+// matched window (rho near 1) the loss grows with the number of additions into
+// one accumulator, about -5e-9 M at rho = 1 for M samples.  Chunks of C samples
+// hold it near the loss of a C-sample template whatever M is (C = 2048 for
+// split-BF16: about 1.1e-5; C = 1024 for split-FP16, whose loss per addition is
+// larger: about 8e-6); the fold of the partial sums is one FP32 addition
+// rounded to nearest.  Each fold stalls the MMAs for about 1.6K cycles: 0.6 %
+// of the kernel at M = 4096 with C = 2048, 3-6 % with C = 1024.
+//
+// Chunks of a tile's K range [lo, hi) are its intersections with the aligned
+// block ranges [c 2^k, (c + 1) 2^k), so that a tile whose range was narrowed to
+// its templates' support adds the same partial sums as one that runs every
+// block (the skipped blocks are zero).  The split routes only (a second
+// accumulator is needed); plain BF16, whose operand rounding is far larger
+// than the accumulation's, keeps one chunk, so its two tile shapes add in the
+// same order.
+template <int NPROD, uint32_t NBUF>
+__device__ __forceinline__ uint32_t n_chunks(KRange kr, uint32_t lg)
+{
+    return NPROD == 3 && NBUF == 2 ? ((kr.hi - 1) >> lg) - (kr.lo >> lg) + 1 : 1u;
+}
+
+template <int NPROD, uint32_t NBUF>
+__device__ __forceinline__ KRange chunk_range(KRange kr, uint32_t ch, uint32_t lg)
+{
+    if (!(NPROD == 3 && NBUF == 2)) return kr;
+    const uint32_t a = ((kr.lo >> lg) + ch) << lg;
+    return {max(kr.lo, a), min(kr.hi, a + (1u << lg))};
+}
+
 template <int LT>
 __device__ __forceinline__ TileCoord tile_coord(const CorrParams& p, uint64_t t)
 {
@@ -452,50 +512,61 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            uint32_t st = 0, ph = 0, buf = 0, tph = 0;     // tph bit b: phase of accumulator b
+            uint32_t st = 0, ph = 0;
+            uint32_t x = 0;             // the base accumulator of the next tile
+            uint32_t mph = 0;           // bit b: phase of the waits on tempty[b]
             bool ok = true;
             for (uint64_t t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
                 const TileCoord c = tile_coord<LT>(p, t);
                 const KRange kr = k_range(*c.s, c.tt, c.s->M_pad / TC_BK);
-                if (!mbar_wait(tempty_bar(buf), ((tph >> buf) & 1) ^ 1, abort_flag)) {
-                    if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_TMEM);
-                    *abort_flag = 1;
-                    break;
-                }
-                fence_after();
-                for (uint32_t kb = kr.lo; kb < kr.hi; ++kb) {
-                    if (!mbar_wait(full_bar(st), ph, abort_flag)) {
-                        if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_FULL);
+                const uint32_t n_ch = n_chunks<NPROD, G::NBUF>(kr, p.kchunk_log2);
+                for (uint32_t ch = 0; ok && ch < n_ch; ++ch) {
+                    // chunk 0 into the base accumulator, later chunks into the
+                    // other one, which the epilogue folds into the base
+                    const uint32_t b = ch == 0 ? x : x ^ 1u;
+                    if (!mbar_wait(tempty_bar(b), ((mph >> b) & 1) ^ 1, abort_flag)) {
+                        if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_TMEM);
                         *abort_flag = 1;
                         ok = false;
                         break;
                     }
+                    mph ^= 1u << b;
                     fence_after();
-                    const uint32_t sbase = base + st * G::STAGE_BYTES;
+                    const KRange cr = chunk_range<NPROD, G::NBUF>(kr, ch, p.kchunk_log2);
+                    const uint32_t kb0 = cr.lo, kb1 = cr.hi;
+                    for (uint32_t kb = kb0; kb < kb1; ++kb) {
+                        if (!mbar_wait(full_bar(st), ph, abort_flag)) {
+                            if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_FULL);
+                            *abort_flag = 1;
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint32_t sbase = base + st * G::STAGE_BYTES;
 #pragma unroll
-                    for (uint32_t kk = 0; kk < TC_BK / 16; ++kk) {
-                        const uint64_t ahi = make_desc(sbase + G::OFF_AHI + kk * 256, 128, 1024);
-                        const uint64_t alo = make_desc(sbase + G::OFF_ALO + kk * 256, 128, 1024);
+                        for (uint32_t kk = 0; kk < TC_BK / 16; ++kk) {
+                            const uint64_t ahi = make_desc(sbase + G::OFF_AHI + kk * 256, 128, 1024);
+                            const uint64_t alo = make_desc(sbase + G::OFF_ALO + kk * 256, 128, 1024);
 #pragma unroll
-                        for (uint32_t h = 0; h < G::NSUB; ++h) {
-                            const uint32_t boff = h * 256 * 16 + kk * 256;
-                            const uint64_t bhi = make_desc(sbase + G::OFF_BHI + boff, 128, 128);
-                            const uint64_t blo = make_desc(sbase + G::OFF_BLO + boff, 128, 128);
-                            const uint32_t d = tmem + buf * 256 + h * 256;
-                            mma_f16(d, ahi, bhi, p.idesc, (kb != kr.lo) | (kk != 0));
-                            if (NPROD == 3) {
-                                mma_f16(d, ahi, blo, p.idesc, 1);
-                                mma_f16(d, alo, bhi, p.idesc, 1);
+                            for (uint32_t h = 0; h < G::NSUB; ++h) {
+                                const uint32_t boff = h * 256 * 16 + kk * 256;
+                                const uint64_t bhi = make_desc(sbase + G::OFF_BHI + boff, 128, 128);
+                                const uint64_t blo = make_desc(sbase + G::OFF_BLO + boff, 128, 128);
+                                const uint32_t d = tmem + b * 256 + h * 256;
+                                mma_f16(d, ahi, bhi, p.idesc, (kb != kb0) | (kk != 0));
+                                if (NPROD == 3) {
+                                    mma_f16(d, ahi, blo, p.idesc, 1);
+                                    mma_f16(d, alo, bhi, p.idesc, 1);
+                                }
                             }
                         }
+                        mma_commit(empty_bar(st));
+                        if (++st == G::STAGES) { st = 0; ph ^= 1; }
                     }
-                    mma_commit(empty_bar(st));
-                    if (++st == G::STAGES) { st = 0; ph ^= 1; }
+                    if (!ok) break;
+                    mma_commit(tfull_bar(b));
                 }
-                if (!ok) break;
-                mma_commit(tfull_bar(buf));
-                tph ^= 1u << buf;
-                buf = buf + 1 == G::NBUF ? 0 : buf + 1;
+                if (G::NBUF == 2) x ^= 1u;      // the next tile's base is this tile's other one
             }
             // drain: every MMA issued by this thread completes before TMEM is freed
             mma_commit(drain_bar);
@@ -507,7 +578,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
         const uint32_t half = (warp - 2) >> 2;             // columns [half LT/2, (half+1) LT/2)
         const uint32_t row = q * 32 + lane;                // template row of the tile
         const uint32_t e = threadIdx.x - 64;               // 0 .. EPI_THREADS-1
-        uint32_t buf = 0, tph = 0;
+        uint32_t x = 0;                 // the base accumulator of this tile
+        uint32_t eph = 0;               // bit b: phase of the waits on tfull[b]
         for (uint64_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
             const TileCoord c = tile_coord<LT>(p, t);
             const Seg& s = *c.s;
@@ -518,13 +590,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             for (uint32_t j = e; j < (uint32_t)LT; j += EPI_THREADS)
                 sh_inv[j] = j < nvalid ? s.inv_norm[c.lag0 + j] * oscale : 0.f;
             epilogue_sync();
-            const bool ok = mbar_wait(tfull_bar(buf), (tph >> buf) & 1, abort_flag);
-            if (epilogue_any(!ok)) {       // all epilogue threads leave together
-                if (!ok && !*abort_flag) record_error(p.err, DEV_TIMEOUT_TMEM);
+            static_assert((LT / 2) % 64 == 0, "chunk pairs per warp");
+            const uint32_t cbeg = half * (LT / 2), cend = cbeg + LT / 2;
+            uint32_t ra[32], rb[32];
+            // chunk 0 of the K range is in the base accumulator x; each later
+            // chunk arrives in the other one and is added into x here (FP32,
+            // round to nearest), which frees it for the MMA warp
+            const uint32_t n_ch = n_chunks<NPROD, G::NBUF>(k_range(s, c.tt, s.M_pad / TC_BK), p.kchunk_log2);
+            bool ok = true;
+            for (uint32_t ch = 0; ch < n_ch; ++ch) {
+                const uint32_t b = ch == 0 ? x : x ^ 1u;
+                ok = mbar_wait(tfull_bar(b), (eph >> b) & 1, abort_flag);
+                eph ^= 1u << b;
+                if (epilogue_any(!ok)) {   // all epilogue threads leave together
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                if (ch == 0) continue;
+                const uint32_t tx = tmem + ((q * 32) << 16) + x * 256;
+                const uint32_t ty = tmem + ((q * 32) << 16) + b * 256;
+#pragma unroll 1
+                for (uint32_t c0 = cbeg; c0 < cend; c0 += 64) {
+                    uint32_t fx[64], fy[64];
+                    __syncwarp();
+                    tmem_ld64_async(tx + c0, fx);
+                    tmem_ld64_async(ty + c0, fy);
+                    tmem_wait64(fx);
+                    tmem_wait64(fy);
+#pragma unroll
+                    for (int i = 0; i < 64; ++i)
+                        fx[i] = __float_as_uint(__uint_as_float(fx[i]) + __uint_as_float(fy[i]));
+                    tmem_st64(tx + c0, fx);
+                }
+                tmem_st_wait();
+                fence_before();
+                mbar_arrive(tempty_bar(b));
+            }
+            if (!ok) {
+                if (!*abort_flag) record_error(p.err, DEV_TIMEOUT_TMEM);
                 *abort_flag = 1;
                 break;
             }
-            fence_after();
+            const uint32_t buf = x;
+            if (G::NBUF == 2) x ^= 1u;          // the next tile's base
             const uint32_t k = c.tt * TC_TILE_T + row;
             const bool keep = k >= s.k_begin && k < s.k_end;
             const bool full = nvalid == (uint32_t)LT;
@@ -546,9 +655,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
             // software pipeline over the chunks of 32 columns: the load of
             // chunk i+1 is in flight while chunk i is reduced; the accumulator
             // is handed back to the MMA warp as soon as the last load has landed
-            static_assert((LT / 2) % 64 == 0, "chunk pairs per warp");
-            const uint32_t cbeg = half * (LT / 2), cend = cbeg + LT / 2;
-            uint32_t ra[32], rb[32];
             auto reduce = [&](const uint32_t (&r)[32], uint32_t cc) {
                 if (cc >= nvalid) return;
                 float cmax;
@@ -586,8 +692,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
                 reduce(rb, c0 + 32);
                 if (more) tmem_wait(ra);
             }
-            tph ^= 1u << buf;
-            buf = buf + 1 == G::NBUF ? 0 : buf + 1;
             // merge the chains: largest |rho|, smallest column on ties
             float bv = st.bv[0];
             uint32_t bi = st.bi[0];
@@ -639,7 +743,6 @@ cudaError_t corr_tc_set_attributes()
 {
     if (g_attr_done) return cudaSuccess;
     cudaError_t e = set_attr<1, 512>();
-    if (e == cudaSuccess) e = set_attr<3, 512>();
     if (e == cudaSuccess) e = set_attr<1, 256>();
     if (e == cudaSuccess) e = set_attr<3, 256>();
     if (e == cudaSuccess) g_attr_done = true;
@@ -687,12 +790,14 @@ cudaError_t launch_corr_tc(const CorrParams& p, int nprod, int lt, int n_sm, cud
     if (ea != cudaSuccess) return ea;
     const unsigned grid = (unsigned)(p.total_tiles < (uint64_t)n_sm ? p.total_tiles : (uint64_t)n_sm);
     count_launches(1);
+    // the split routes need the second accumulator for their K chunks, so
+    // they run the 256-lag shape only
+    if (nprod == 3 && lt != 256) return cudaErrorInvalidValue;
     if (lt == 256) {
         if (nprod == 3) k_corr_tc<3, 256><<<grid, TC_THREADS, Geo<256>::SMEM, st>>>(p);
         else k_corr_tc<1, 256><<<grid, TC_THREADS, Geo<256>::SMEM, st>>>(p);
     } else {
-        if (nprod == 3) k_corr_tc<3, 512><<<grid, TC_THREADS, Geo<512>::SMEM, st>>>(p);
-        else k_corr_tc<1, 512><<<grid, TC_THREADS, Geo<512>::SMEM, st>>>(p);
+        k_corr_tc<1, 512><<<grid, TC_THREADS, Geo<512>::SMEM, st>>>(p);
     }
     return cudaGetLastError();
 }

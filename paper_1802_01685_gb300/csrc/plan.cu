@@ -35,7 +35,10 @@ void bf_plan_destroy(bf_plan* p)
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     for (auto& ps : p->prep) ps.release(*p->ctx->mem);
-    if (p->r) bf_result_destroy(p->r);
+    if (p->r) {
+        p->r->plan_owned = false;
+        bf_result_destroy(p->r);
+    }
     delete p;
 }
 
@@ -81,6 +84,7 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
     cudaStream_t strm = ctx->stream;
     st = alloc_result(ctx, bank, o, p->lengths, fs, strm, &p->r);
     if (st) return st;
+    p->r->plan_owned = true;
     p->prep.resize(n_series);
     std::vector<PreparedSeries*> pptr;
     std::vector<uint32_t> ids;

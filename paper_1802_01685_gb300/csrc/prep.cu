@@ -219,13 +219,27 @@ __global__ void __launch_bounds__(SCAN_T) k_prefix(const float* __restrict__ x, 
 // 1 / |window|, and exactly 0 for a window without a nonzero sample (rho := 0
 // there).  The count decides emptiness: a difference of FP64 prefix sums
 // formed in different orders need not vanish over an all-zero window.
-__global__ void k_inv_norm(const double* __restrict__ S, const uint32_t* __restrict__ C, uint64_t L,
-                           uint32_t M, float* __restrict__ inv)
+// The prefix difference S[t+M] - S[t] carries an absolute rounding error of a
+// few ulps of S[t+M]; where the window holds less than 2^-30 of the energy
+// before it (a quiet stretch after loud data) that would be a relative error
+// above ~5e-6, so such windows are summed directly (x^2 is exact in FP64).
+__global__ void k_inv_norm(const float* __restrict__ x, const double* __restrict__ S,
+                           const uint32_t* __restrict__ C, uint64_t L, uint32_t M,
+                           float* __restrict__ inv)
 {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < L;
          t += (uint64_t)gridDim.x * blockDim.x) {
         double nu = S[t + M] - S[t];
-        inv[t] = (C[t + M] != C[t] && nu > 0.0) ? (float)(1.0 / sqrt(nu)) : 0.f;
+        const bool any = C[t + M] != C[t];
+        if (any && nu < S[t + M] * 0x1p-30) {
+            double acc = 0.0;
+            for (uint32_t m = 0; m < M; ++m) {
+                const double v = (double)x[t + m];
+                acc = fma(v, v, acc);
+            }
+            nu = acc;
+        }
+        inv[t] = (any && nu > 0.0) ? (float)(1.0 / sqrt(nu)) : 0.f;
     }
 }
 
@@ -245,7 +259,7 @@ cudaError_t launch_inv_norm(const float* x, uint64_t N, uint32_t M, double* pref
     uint64_t L = N - M + 1;
     uint64_t blocks = (L + 255) / 256;
     if (blocks > 65535ull * 16) blocks = 65535ull * 16;
-    k_inv_norm<<<(unsigned)blocks, 256, 0, s>>>(prefix, counts, L, M, inv);
+    k_inv_norm<<<(unsigned)blocks, 256, 0, s>>>(x, prefix, counts, L, M, inv);
     return cudaGetLastError();
 }
 

@@ -57,6 +57,7 @@ struct Request {
     bool fft = false;
     FftParams fp{};                 // this request's series and outputs
     float2* seg_spec = nullptr;     // its segment spectra
+    uint32_t* fix = nullptr;        // lags for the direct fixup [L], then their count
     uint32_t k_next = 0, k_stop = 0;   // template-row cursor
 };
 
@@ -91,6 +92,10 @@ struct ServeState {
 static void release_request_device(bf_ctx* ctx, Request* r)
 {
     r->prep.release(*ctx->mem);
+    if (r->fix) {
+        ctx->mem->release(r->fix);
+        r->fix = nullptr;
+    }
     if (r->seg_spec) {
         ctx->mem->release(r->seg_spec);
         r->seg_spec = nullptr;
@@ -143,7 +148,8 @@ static bool admit(ServeState* S, Request* r)
         const uint32_t nseg = fft_segments(r->prep.L, bank->M);
         if (st == BF_OK) {
             r->seg_spec = static_cast<float2*>(ctx->mem->alloc((size_t)nseg * (FFT_POINTS / 2) * sizeof(float2)));
-            if (!r->seg_spec) {
+            r->fix = static_cast<uint32_t*>(ctx->mem->alloc(((size_t)r->prep.L + 1) * sizeof(uint32_t)));
+            if (!r->seg_spec || !r->fix) {
                 set_error("out of device memory for the segment spectra");
                 st = BF_ENOMEM;
             }
@@ -157,6 +163,11 @@ static bool admit(ServeState* S, Request* r)
             b.x[0] = r->prep.x;
             b.N[0] = r->prep.N;
             b.spec[0] = r->seg_spec;
+            b.S[0] = r->prep.prefix;
+            b.inv[0] = r->prep.inv;
+            b.L[0] = (uint32_t)r->prep.L;
+            b.fix[0] = r->fix;
+            b.n_fix = r->fix + r->prep.L;
             e = launch_fft_series(b, nseg, ctx->n_sm, S->stream);
             if (e != cudaSuccess) st = cuda_fail(e, "segment spectra");
             FftParams& p = r->fp;
@@ -172,9 +183,15 @@ static bool admit(ServeState* S, Request* r)
             p.cand_cap = res->cand_cap;
             p.cand = res->cand;
             p.cand_count = res->cand_count;
+            p.chirps = bank->d_params;
+            p.M = bank->M;
+            p.fs = bank->fs;
             FftSeries& f = p.ser[0];
             f.spec = r->seg_spec;
             f.inv = r->prep.inv;
+            f.x = r->prep.x;
+            f.fix = r->fix;
+            f.n_fix = r->fix + r->prep.L;
             f.vmax = res->packed;
             f.sumsq = res->sumsq;
             f.sigma_pred = res->parseval ? res->sigma_pred : nullptr;

@@ -237,3 +237,119 @@ def test_template_lengths(ctx, fs, T):
         assert np.abs(rho.cpu().numpy() - ref["rho"]).max() <= TOL[PREC], (M, n)
         check_maxima(outs[0], ref, ref["rho"], TOL[PREC], f"M={M} n={n}")
     bf.bf_bank_destroy(bank)
+
+
+def _quiet_loud_series(rng, n, quiet, scale):
+    """White noise with the stretches in `quiet` scaled by `scale`."""
+    x = rng.standard_normal(n)
+    for a, b in quiet:
+        x[a:b] *= scale
+    return x
+
+
+@pytest.mark.parametrize("quad", [False, True])
+def test_low_energy_windows_computed_directly(ctx, quad):
+    """Windows that hold almost none of their segment's energy: the tapered
+    edges of a chirp alone in silence, and a stretch of noise 10^5 times
+    quieter than its neighbours.  The transform's rounding error scales with
+    the segment, so these lags go to the direct fixup; dense rho, maxima,
+    sigma, tails and map all match the oracle, and rho never exceeds 1."""
+    fs, M = 2048.0, 2048
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC, synth.BOTH],
+                           [1.0, 0.5], 40.0, 900.0, 3, 5)        # 180 chirps
+    p = oracle_params(spec)
+    rng = np.random.default_rng(71)
+    storage = bf.BF_BANK_SPLIT_BF16 | (bf.BF_BANK_QUADRATURE if quad else 0)
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, storage)
+    # series 0: zeros with a bank template placed at 5000, 3 times its size
+    x0 = np.zeros(14000)
+    x0[5000:5000 + M] = 3.0 * oracle.template(int(p["track"][17]), int(p["sense"][17]), p["f_lo"][17],
+                                              p["f_hi"][17], p["D"][17], fs, M, 0)
+    # series 1: noise with a stretch 1e-5 as loud (windows inside it are
+    # normalised noise again, as loud in rho as the rest)
+    x1 = _quiet_loud_series(rng, 16000, [(6000, 11000)], 1e-5)
+    xs = [x0.astype(np.float32), x1.astype(np.float32)]
+    kappa = 2.5 if quad else 4.0       # phase-blind output: |rho|^2 M / 2 is chi^2 with 2 dof on noise
+    tol = TOL[PREC]
+    for s, x in enumerate(xs):
+        ref = oracle.search(x, fs, p, M, want_rho=True, quadrature=quad)
+        K, L = ref["rho"].shape
+        rho = torch.zeros((K, L), dtype=torch.float32, device="cuda")
+        outs, _, _ = run(ctx, bank, [x], fs, PREC, rho_out=rho)
+        got = rho.cpu().numpy().astype(np.float64)
+        assert np.abs(got).max() <= 1.0 + tol
+        err = np.abs(got - ref["rho"])
+        assert err.max() <= tol, (s, err.max(), np.unravel_index(err.argmax(), err.shape))
+        check_maxima(outs[0], ref, ref["rho"], tol, f"series {s}")
+        check_sigma(outs[0], ref, tol)
+        if s == 0:
+            assert abs(float(outs[0]["max"][17]) - 1.0) <= tol
+            if not quad:
+                assert outs[0]["argmax"][17] == 5000
+        # tails and map against the oracle at the same threshold
+        thr = kappa * np.sqrt((2.0 if quad else 1.0) / M)
+        res = bf.bf_correlate(ctx, bank, [x], fs, bf.make_opts(precision=PREC, kappa=kappa, want_tails=True,
+                                                               want_map=True))
+        tails = bf.bf_result_copy_tails(res)
+        mp = bf.bf_result_copy_to_host(res, 0, want_map=True)["map"]
+        bf.bf_result_destroy(res)
+        a = np.abs(ref["rho"])
+        got_t = {(int(t["k"]), int(t["tau"])) for t in tails}
+        must = set(zip(*[v.tolist() for v in np.nonzero(a >= thr + tol)]))
+        may = set(zip(*[v.tolist() for v in np.nonzero(a >= thr - tol)]))
+        assert len(must) > 0 and must <= got_t <= may
+        hi = oracle.search(x, fs, p, M, thr=thr + tol, want_map=True, quadrature=quad)["map"]
+        lo = oracle.search(x, fs, p, M, thr=thr - tol, want_map=True, quadrature=quad)["map"]
+        assert np.all(mp >= hi - tol) and np.all(mp <= lo + tol)
+    bf.bf_bank_destroy(bank)
+
+
+def test_low_energy_windows_in_plans_generated_banks_and_serving(ctx):
+    """The fixup runs inside a captured plan, with a generated bank (spectra
+    made chunk by chunk) and in the serving loop, giving what bf_correlate
+    gives with a stored bank."""
+    fs, M = 2048.0, 2048
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0], 40.0, 900.0, 4, 8)
+    rng = np.random.default_rng(72)
+    xs = [_quiet_loud_series(rng, n, [(3000, 7000)], 1e-6).astype(np.float32) for n in (12000, 9000)]
+    stored = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_SPLIT_BF16)
+    gen = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_GENERATED)
+    opts = bf.make_opts(precision=PREC, want_tails=True)
+
+    def outputs(res, owned=True):
+        o = [bf.bf_result_copy_to_host(res, s) for s in range(len(xs))]
+        t = np.sort(bf.bf_result_copy_tails(res), order=["series", "k", "tau"])
+        if owned:
+            bf.bf_result_destroy(res)
+        return o, t
+
+    ref, ref_t = outputs(bf.bf_correlate(ctx, stored, xs, fs, opts))
+    p = oracle_params(spec)
+    for s, x in enumerate(xs):
+        r = oracle.search(x, fs, p, M, want_rho=True)
+        check_maxima(ref[s], r, r["rho"], TOL[PREC], f"series {s}")
+    g, g_t = outputs(bf.bf_correlate(ctx, gen, xs, fs, opts))
+    plan = bf.bf_plan_create(ctx, stored, [len(x) for x in xs], fs, opts)
+    try:
+        for _ in range(2):
+            pl, pl_t = outputs(bf.bf_plan_run(plan, xs), owned=False)     # the plan's result
+            for a, b in zip(ref, pl):
+                np.testing.assert_array_equal(a["max"], b["max"])
+                np.testing.assert_array_equal(a["argmax"], b["argmax"])
+            np.testing.assert_array_equal(ref_t, pl_t)
+    finally:
+        bf.bf_plan_destroy(plan)
+    for a, b in zip(ref, g):
+        np.testing.assert_array_equal(a["max"], b["max"])
+        np.testing.assert_array_equal(a["argmax"], b["argmax"])
+    np.testing.assert_array_equal(ref_t, g_t)
+    for s, x in enumerate(xs):
+        t = bf.bf_serve_submit(ctx, stored, x, fs, opts)
+        st, res = bf.bf_serve_poll(ctx, t, 60_000_000)
+        assert st == bf.BF_OK
+        srv = bf.bf_result_copy_to_host(res, 0)
+        bf.bf_result_destroy(res)
+        np.testing.assert_array_equal(srv["max"], ref[s]["max"])
+        np.testing.assert_array_equal(srv["argmax"], ref[s]["argmax"])
+    bf.bf_bank_destroy(stored)
+    bf.bf_bank_destroy(gen)

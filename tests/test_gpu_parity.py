@@ -105,8 +105,8 @@ def test_control_seed_edge_values(ctx):
 
 # ------------------------------------------------------------------ tiny config, full parity
 
-@pytest.mark.parametrize("prec,lt", [("split_bf16", 512), ("split_bf16", 256), ("fp32", 0),
-                                     ("split_fp16", 512), ("split_fp16", 256),
+@pytest.mark.parametrize("prec,lt", [("split_bf16", 0), ("split_bf16", 256), ("fp32", 0),
+                                     ("split_fp16", 0), ("split_fp16", 256),
                                      ("bf16", 512), ("bf16", 256), ("fft_fp32", 0)])
 def test_tiny_dense_rho(ctx, tiny, prec, lt):
     w, bank, p, ref = tiny
@@ -116,6 +116,8 @@ def test_tiny_dense_rho(ctx, tiny, prec, lt):
     outs, _, info = run(ctx, bank, [x], fs, prec, rho_out=rho, tile_lags=lt)
     if lt:
         assert info.tile_lags == lt
+    elif prec.startswith("split"):
+        assert info.tile_lags == 256                      # the split routes' one shape
     err = np.abs(rho.cpu().numpy().astype(np.float64) - ref["rho"])
     assert err.max() <= TOL[prec], f"{prec}: max |rho - oracle| = {err.max():.3e}"
     assert info.correlations == K * L
@@ -357,29 +359,68 @@ def test_invalid_calls(ctx, tiny):
 
 @pytest.mark.parametrize("prec", ["split_bf16", "bf16", "split_fp16"])
 def test_tile_shapes_agree(ctx, prec):
-    """Both tensor-core tile shapes compute every output by the same MMA
-    sequence, so maxima and argmaxes agree bit for bit; ragged lag tiles of
-    either width and the autotuner's choice are covered."""
+    """Plain BF16 has two tensor-core tile shapes that compute every output by
+    the same MMA sequence, so maxima and argmaxes agree bit for bit; ragged
+    lag tiles of either width and the autotuner's choice are covered.  The
+    split routes run the 256-lag shape only (their K chunks need the second
+    accumulator) and refuse 512."""
     fs = 2048.0
     spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0, 0.3],
                            20.0, 1000.0, 6, 7)                   # 336 templates
     bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_SPLIT_FP16)
     rng = np.random.default_rng(12)
     xs = [rng.standard_normal(n).astype(np.float32) for n in (2048, 2048 + 255, 2048 + 700, 20000)]
+    shapes = (256, 512, 0) if prec == "bf16" else (256, 0)
     res = {}
-    for lt in (256, 512, 0):
+    for lt in shapes:
         outs, mean, info = run(ctx, bank, xs, fs, prec, tile_lags=lt, want_tails=True)
         assert info.tile_lags in (256, 512) and (lt == 0 or info.tile_lags == lt)
+        if prec != "bf16":
+            assert info.tile_lags == 256
         res[lt] = (outs, mean)
-    for lt in (512, 0):
+    for lt in shapes[1:]:
         for a, b in zip(res[256][0], res[lt][0]):
             np.testing.assert_array_equal(a["max"], b["max"])
             np.testing.assert_array_equal(a["argmax"], b["argmax"])
             np.testing.assert_allclose(a["sigma"], b["sigma"], rtol=1e-6)
             np.testing.assert_array_equal(a["hist"], b["hist"])
         np.testing.assert_array_equal(res[256][1], res[lt][1])
-    with pytest.raises(bf.BFError):
-        run(ctx, bank, xs, fs, prec, tile_lags=128)
+    bad = (128,) if prec == "bf16" else (128, 512)
+    for lt in bad:
+        with pytest.raises(bf.BFError) as e:
+            run(ctx, bank, xs, fs, prec, tile_lags=lt)
+        assert e.value.status == bf.BF_EINVAL
+    bf.bf_bank_destroy(bank)
+
+
+@pytest.mark.parametrize("M", [1024, 2048, 4096, 8192, 16384, 32768])
+def test_matched_window_at_rho_one(ctx, M):
+    """A bank template placed, scaled, into an otherwise zero series gives
+    rho = 1 at its offset (Cauchy-Schwarz equality).
+    This is the hardest case for FP32 accumulation: every partial sum of the
+    window grows towards |x| |h|.  The tensor core truncates each MMA's
+    addition to its accumulator, so the split routes add K in chunks of 2048
+    samples and fold the chunks in the epilogue; the error stays inside the
+    bound at every template length (about 1.1e-5 split-BF16, 1.5e-5
+    split-FP16, where one accumulator reached 1e-4 at M = 16384)."""
+    fs = float(M)
+    chirps = [(bf.BF_LINEAR, bf.BF_ASC, 0.02 * fs, 0.4 * fs, 1.0),
+              (bf.BF_POWERLAW, bf.BF_ASC, 0.01 * fs, 0.2 * fs, 1.0),
+              (bf.BF_LINEAR, bf.BF_DESC, 0.1 * fs, 0.3 * fs, 0.8),
+              (bf.BF_POWERLAW, bf.BF_BOTH, 0.02 * fs, 0.3 * fs, 1.0)]
+    bank = bf.bf_bank_create(ctx, chirps, fs, 1.0, STORE_ALL)
+    H = bf.bf_bank_read(bank, 0, len(chirps))
+    worst = {}
+    for k in range(len(chirps)):
+        x = np.zeros(3 * M, np.float32)
+        x[M:2 * M] = 3.0 * H[k]
+        for prec in ("split_bf16", "split_fp16", "fp32"):
+            g = run(ctx, bank, [x], fs, prec)[0][0]
+            assert g["argmax"][k] == M, (prec, k)
+            worst[prec] = max(worst.get(prec, 0.0), abs(float(g["max"][k]) - 1.0))
+    print(f"M={M}: |max rho - 1| per route: {worst}")
+    for prec, err in worst.items():
+        assert err <= TOL[prec], (prec, err)
     bf.bf_bank_destroy(bank)
 
 
@@ -563,3 +604,66 @@ def test_copy_into_caller_buffers(ctx, tiny):
     with pytest.raises(ValueError):
         bf.bf_result_copy_to_host(res, 0, out={"argmax": np.zeros(K, np.int64)})
     bf.bf_result_destroy(res)
+
+
+def test_zero_blocks_skipped_quadrature_generated_ragged_m(ctx):
+    """Skipping with quadrature pairs, a generated bank and M = 2000 (padded to
+    2048): short-sweep templates in a generated quadrature bank give, bit for
+    bit, what the same templates give in a stored bank whose tiles each hold a
+    full-length chirp, and match the oracle's phase-blind output."""
+    fs, M = 2000.0, 2000
+    rng = np.random.default_rng(34)
+    f_lo = rng.uniform(20.0, 300.0, 150)
+    short = [(int(i % 2), int(i % 3), float(a), float(a + rng.uniform(60.0, 600.0)), [0.25, 0.6][i >= 64])
+             for i, a in enumerate(f_lo)]
+    full = (bf.BF_POWERLAW, bf.BF_ASC, 40.0, 500.0, 1.0)
+    mixed, where = [], []
+    for c in short:
+        if len(mixed) % 64 == 0:                      # 64 chirps = 128 rows per tile
+            mixed.append(full)
+        where.append(len(mixed))
+        mixed.append(c)
+    x = rng.standard_normal(6100)
+    x[2500:2500 + M] += 20.0 * oracle.template(*short[100], fs, M, 1)
+    x = x.astype(np.float32)
+    gen = bf.bf_bank_create(ctx, short, fs, 1.0, bf.BF_BANK_GENERATED | bf.BF_BANK_QUADRATURE)
+    ref_bank = bf.bf_bank_create(ctx, mixed, fs, 1.0, bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_QUADRATURE)
+    a = run(ctx, gen, [x], fs, "split_bf16")[0][0]
+    b = run(ctx, ref_bank, [x], fs, "split_bf16")[0][0]
+    for key in ("max", "argmax", "sigma"):
+        np.testing.assert_array_equal(a[key], b[key][where])
+    p = {k: np.array([c[i] for c in short], dt)
+         for i, (k, dt) in enumerate((("track", np.int32), ("sense", np.int32), ("f_lo", np.float64),
+                                      ("f_hi", np.float64), ("D", np.float64)))}
+    ref = oracle.search(x, fs, p, M, want_rho=True, quadrature=True)
+    check_maxima(a, ref, ref["rho"], TOL["split_bf16"], "quadrature skip")
+    assert abs(int(a["argmax"][100]) - 2500) <= 2
+    bf.bf_bank_destroy(gen)
+    bf.bf_bank_destroy(ref_bank)
+
+
+@pytest.mark.parametrize("scale", [1e-3, 1e-6])
+def test_quiet_stretch_after_loud_data(ctx, scale):
+    """Noise with a long stretch `scale` times quieter than what precedes it.
+    Inside the stretch rho is normalised noise again, but the window energy is
+    a tiny difference of the FP64 prefix of x^2, which those windows sum
+    directly; every route matches the oracle's dense rho there."""
+    fs, M = 2048.0, 2048
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0, 0.4],
+                           40.0, 900.0, 4, 4)                    # 128 templates
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, STORE_ALL)
+    p = oracle_params(spec)
+    rng = np.random.default_rng(81)
+    x = rng.standard_normal(13000)
+    x[4000:9500] *= scale
+    x = x.astype(np.float32)
+    ref = oracle.search(x, fs, p, M, want_rho=True)
+    K, L = ref["rho"].shape
+    for prec in ("split_bf16", "fp32", "split_fp16", "fft_fp32", "bf16"):
+        rho = torch.zeros((K, L), dtype=torch.float32, device="cuda")
+        outs, _, _ = run(ctx, bank, [x], fs, prec, rho_out=rho)
+        err = np.abs(rho.cpu().numpy().astype(np.float64) - ref["rho"])
+        assert err.max() <= TOL[prec], (prec, err.max(), np.unravel_index(err.argmax(), err.shape))
+        check_maxima(outs[0], ref, ref["rho"], TOL[prec], prec)
+        check_sigma(outs[0], ref, TOL[prec])
+    bf.bf_bank_destroy(bank)

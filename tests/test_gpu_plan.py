@@ -78,6 +78,11 @@ def test_plan_on_a_stream_and_launch_count(setup):
     for g, r in zip(got, ref):
         np.testing.assert_array_equal(g["max"], r["max"])
         np.testing.assert_array_equal(g["argmax"], r["argmax"])
+    # the plan owns its result: destroying it is refused, and it stays readable
+    bf.bf_result_destroy(res)
+    assert "belongs to a plan" in bf.load().bf_last_error().decode()
+    for g, r in zip(outputs(res, 2, False), ref):
+        np.testing.assert_array_equal(g["max"], r["max"])
     bf.bf_plan_destroy(plan)
 
 
