@@ -352,6 +352,8 @@ def run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step):
     step()
     n = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record()
@@ -359,12 +361,14 @@ def run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step):
         d2h = step()
     ev1.record()
     torch.cuda.synchronize()
+    clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / n
     h2d = 2 * N * 4 + 4 * N * 4                     # control inputs + the four searched series
     out = {"value": corr_per_step / (ms / 1e3), "unit": UNIT, "ms_per_step": round(ms, 2),
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h + 2 * N * 4,
            "steps": n, "inputs": "pinned host float32; results copied each step into pinned host "
-                                       "buffers allocated once"}
+                                       "buffers allocated once",
+           "clocks": clocks}
     return out
 
 

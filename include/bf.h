@@ -78,7 +78,10 @@ typedef enum {
     BF_FP32 = 0,        /* FP32 operands, FP32 FMA (SIMT)                      */
     BF_BF16 = 1,        /* BF16 operands on tcgen05 tensor cores               */
     BF_SPLIT_BF16 = 2,  /* x = hi + lo, h = hi + lo in BF16; three tcgen05 MMAs
-                           hi*hi + hi*lo + lo*hi into one FP32 accumulator     */
+                           hi*hi + hi*lo + lo*hi into FP32 accumulators, K in
+                           chunks of 2048 samples added with rounding to
+                           nearest (the tensor core's own accumulation
+                           truncates)                                        */
     BF_FFT_FP32 = 3,    /* the paper's route (Sect. 2.2, Fig. 5): FP32 FFTs,
                            overlap-save over segments of 8192 samples
                            (8193 - M lags each).  Template spectra are made
@@ -89,7 +92,11 @@ typedef enum {
                            overlapped with the correlation, so any bank size
                            works.  Templates of at most 4096 samples, else
                            BF_ENOTSUP.  Plans and the serving loop run it
-                           with a stored bank.  tile_lags is ignored.        */
+                           with a stored bank.  tile_lags is ignored.  Lags
+                           whose window holds less than 1/16384 of its
+                           segment's energy (quiet or gated stretches next
+                           to loud data), where the transform's rounding
+                           would swamp rho, are computed directly.          */
     BF_SPLIT_FP16 = 4   /* as BF_SPLIT_BF16 with FP16 hi and lo parts: the
                            split holds x and h to 2^-22 instead of 2^-17, at
                            the same tensor-core rate.  FP16's range is kept
