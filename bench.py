@@ -830,7 +830,7 @@ def main():
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the moderate profiling case of the tensor-core kernel")
     ap.add_argument("--tile-lags", type=int, default=256,
-                    help="tile shape of --kernel-case (the autotuner's choice on GB300)")
+                    help="tile shape of --kernel-case (256, the split routes' shape)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

@@ -247,7 +247,7 @@ size_t prepared_series_bytes(size_t N, uint32_t M, uint32_t M_pad, int precision
                inv_norm_scratch_blocks(N) * 8;
     if (uses_split_rows(precision)) b += 2 * (ceil_div(L, TC_TILE_L) * TC_TILE_L + M_pad + 64) * 16;
     if (precision == BF_FFT_FP32)                               // segment spectra, fixup list
-        b += (size_t)fft_segments((uint32_t)L, M) * (FFT_POINTS / 2) * 8 + (L + 1) * 4;
+        b += (size_t)fft_segments((uint32_t)L, M) * (FFT_POINTS / 2) * 8 + (2 * L + 1) * 4;
     if (precision == BF_SPLIT_FP16) b += 4096;                  // max |x|
     return b + 8 * 4096;
 }
@@ -747,7 +747,7 @@ bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
             const size_t s = s0 + i;
             const uint32_t nseg = fft_segments(prep[s].L, bank->M);
             float2* spec = static_cast<float2*>(ctx->mem->alloc((size_t)nseg * (FFT_POINTS / 2) * sizeof(float2)));
-            uint32_t* fix = static_cast<uint32_t*>(ctx->mem->alloc((size_t)prep[s].L * sizeof(uint32_t)));
+            uint32_t* fix = static_cast<uint32_t*>(ctx->mem->alloc((size_t)prep[s].L * 2 * sizeof(uint32_t)));
             if (spec) r->scratch.push_back(spec);
             if (fix) r->scratch.push_back(fix);
             if (!spec || !fix) {

@@ -118,14 +118,15 @@ struct ChirpDev;
 
 struct FftSeries {
     const float2* spec;             // [nseg][FFT_POINTS / 2] segment half spectra
-    const float* inv;               // [L] inverse window norms; negated at the
-                                    // lags left to the direct fixup
+    const float* inv;               // [L] inverse window norms; 0 at the lags
+                                    // left to the direct fixup
     unsigned long long* vmax;       // packed max per template, index k - k_begin
     double* sumsq;
     float* rho;                     // optional dense output [k - k_begin][tau]
     const float* sigma_pred;        // optional per-template predicted sigma
     const float* x;                 // FP32 samples (for the direct fixup)
-    const uint32_t* fix;            // lags left to the direct fixup ...
+    const uint32_t* fix;            // lags left to the direct fixup, as pairs
+                                    // (lag, float bits of its inverse norm) ...
     const uint32_t* n_fix;          // ... and how many
     float kappa;
     uint32_t L, nseg, series_id;
@@ -159,7 +160,8 @@ struct FftSeriesBatch {
     float2* spec[MAX_FFT_SER];
     uint32_t seg_begin[MAX_FFT_SER];
     // lags for the direct fixup: found from the FP64 prefix of x^2 and the
-    // inverse norms (negated there), listed in fix[i], counted in n_fix[i]
+    // inverse norms (zeroed there), listed in fix[i] as (lag, norm) pairs
+    // (2 L words), counted in n_fix[i]
     const double* S[MAX_FFT_SER];
     float* inv[MAX_FFT_SER];
     uint32_t L[MAX_FFT_SER];

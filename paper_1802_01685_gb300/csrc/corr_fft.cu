@@ -463,19 +463,17 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t t = (uint32_t)(tid + FT * i + FH * h);
-                // a negated norm marks a lag left to the direct fixup
-                const float iv = t < nv ? m.inv[t] : -1.f;
-                if (QUAD && iv >= 0.f) {
+                if (QUAD && t < nv) {
                     // quadrature pair: |c_cos + i c_sin| / |window|
                     const uint32_t tau = t0 + t;
-                    const float r = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * (iv * scale);
+                    const float r = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * (m.inv[t] * scale);
                     track_max(r, tau, best_a, arg_a);
                     pa = fmaf(r, r, pa);
                     if (r >= thr_a) push_tail(p, S.series_id, ka >> 1, tau, r);
                     if (S.rho) S.rho[(size_t)la * S.L + tau] = r;
-                } else if (!QUAD && iv >= 0.f) {
+                } else if (!QUAD && t < nv) {
                     const uint32_t tau = t0 + t;
-                    const float inv = iv * scale;
+                    const float inv = m.inv[t] * scale;
                     const float ra = z[h].x * inv, rb = z[h].y * inv;
                     const float aa = fabsf(ra), ab = fabsf(rb);
                     track_max(aa, tau, best_a, arg_a);
@@ -532,9 +530,10 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
 // Lags whose window holds less than 1/FFT_FIX_RATIO2 of the energy of its
 // FFT segment (e.g. a quiet stretch or the tapered edge of a loud chirp next to
 // silence): the transform's rounding error scales with the segment, so there it
-// would swamp rho.  They are marked by negating the inverse norm, which the
-// correlation epilogue skips, and listed for k_fft_fixup.  The energies come
-// from the FP64 prefix of x^2.  One grid row per series.
+// would swamp rho.  Their inverse norm is set to 0, so the correlation kernel
+// gives them rho = 0 (no tail, nothing to the sum of squares, never above the
+// true maximum), and they are listed, with the norm, for k_fft_fixup.  The
+// energies come from the FP64 prefix of x^2.  One grid row per series.
 __global__ void __launch_bounds__(256) k_fft_flags(const __grid_constant__ FftSeriesBatch b)
 {
     const int i = blockIdx.y;
@@ -550,8 +549,10 @@ __global__ void __launch_bounds__(256) k_fft_flags(const __grid_constant__ FftSe
         const uint64_t e = min(a + (uint64_t)FN, N);
         const double E = S[e] - S[a];
         if (E * (double)iv * (double)iv > FFT_FIX_RATIO2) {
-            inv[t] = -iv;
-            b.fix[i][atomicAdd(b.n_fix + i, 1u)] = (uint32_t)t;    // each lag once: < L entries
+            inv[t] = 0.f;
+            const uint32_t slot = atomicAdd(b.n_fix + i, 1u);     // each lag once: < L entries
+            b.fix[i][2 * slot] = (uint32_t)t;
+            b.fix[i][2 * slot + 1] = __float_as_uint(iv);
         }
     }
 }
@@ -561,8 +562,8 @@ __global__ void __launch_bounds__(256) k_fft_flags(const __grid_constant__ FftSe
 // templates in shared memory as the bank does (FP32 rows at unit norm), and
 // for every listed lag of every series forms the FP32 dot product with the
 // window (one warp per lag), then feeds the same max keys, sums of rho^2,
-// tails and dense output as the correlation kernel.  Returns at once when no
-// series has a listed lag.
+// tails and dense output (written after the correlation kernel's 0 there) as
+// the correlation kernel.  Returns at once when no series has a listed lag.
 constexpr int FIX_T = 256;
 
 template <bool QUAD>
@@ -599,7 +600,7 @@ __global__ void __launch_bounds__(FIX_T) k_fft_fixup(const __grid_constant__ Fft
             unsigned long long best = 0ull;
             double ss = 0.0;
             for (uint32_t f = warp; f < n; f += FIX_T / 32) {
-                const uint32_t tau = S.fix[f];
+                const uint32_t tau = S.fix[2 * f];
                 const float* xw = S.x + tau;
                 float c = 0.f, d = 0.f;
                 for (uint32_t m = lane; m < M; m += 32) {
@@ -612,7 +613,7 @@ __global__ void __launch_bounds__(FIX_T) k_fft_fixup(const __grid_constant__ Fft
                     c += __shfl_xor_sync(0xffffffffu, c, off);
                     if (QUAD) d += __shfl_xor_sync(0xffffffffu, d, off);
                 }
-                const float iv = -S.inv[tau];                  // negated by k_fft_flags
+                const float iv = __uint_as_float(S.fix[2 * f + 1]);     // the window's norm
                 const float r = QUAD ? sqrtf(c * c + d * d) * iv : c * iv;
                 const float a = fabsf(r);
                 if (lane == 0) {

@@ -57,7 +57,7 @@ struct Request {
     bool fft = false;
     FftParams fp{};                 // this request's series and outputs
     float2* seg_spec = nullptr;     // its segment spectra
-    uint32_t* fix = nullptr;        // lags for the direct fixup [L], then their count
+    uint32_t* fix = nullptr;        // lags for the direct fixup [2 L], then their count
     uint32_t k_next = 0, k_stop = 0;   // template-row cursor
 };
 
@@ -148,7 +148,7 @@ static bool admit(ServeState* S, Request* r)
         const uint32_t nseg = fft_segments(r->prep.L, bank->M);
         if (st == BF_OK) {
             r->seg_spec = static_cast<float2*>(ctx->mem->alloc((size_t)nseg * (FFT_POINTS / 2) * sizeof(float2)));
-            r->fix = static_cast<uint32_t*>(ctx->mem->alloc(((size_t)r->prep.L + 1) * sizeof(uint32_t)));
+            r->fix = static_cast<uint32_t*>(ctx->mem->alloc((2 * (size_t)r->prep.L + 1) * sizeof(uint32_t)));
             if (!r->seg_spec || !r->fix) {
                 set_error("out of device memory for the segment spectra");
                 st = BF_ENOMEM;
@@ -167,7 +167,7 @@ static bool admit(ServeState* S, Request* r)
             b.inv[0] = r->prep.inv;
             b.L[0] = (uint32_t)r->prep.L;
             b.fix[0] = r->fix;
-            b.n_fix = r->fix + r->prep.L;
+            b.n_fix = r->fix + 2 * r->prep.L;
             e = launch_fft_series(b, nseg, ctx->n_sm, S->stream);
             if (e != cudaSuccess) st = cuda_fail(e, "segment spectra");
             FftParams& p = r->fp;
@@ -191,7 +191,7 @@ static bool admit(ServeState* S, Request* r)
             f.inv = r->prep.inv;
             f.x = r->prep.x;
             f.fix = r->fix;
-            f.n_fix = r->fix + r->prep.L;
+            f.n_fix = r->fix + 2 * r->prep.L;
             f.vmax = res->packed;
             f.sumsq = res->sumsq;
             f.sigma_pred = res->parseval ? res->sigma_pred : nullptr;
