@@ -667,3 +667,32 @@ def test_quiet_stretch_after_loud_data(ctx, scale):
         check_maxima(outs[0], ref, ref["rho"], TOL[prec], prec)
         check_sigma(outs[0], ref, TOL[prec])
     bf.bf_bank_destroy(bank)
+
+
+@pytest.mark.parametrize("case", ["dc_offset", "spike"])
+def test_offset_and_spike(ctx, case):
+    """A large DC offset (partial sums of the offset times the template's
+    running sum) and a single sample 1e5 times the noise (its FFT segments
+    send nearly every other lag to the direct fixup; the prefix of x^2 jumps
+    by 1e10): dense rho on every route matches the oracle."""
+    fs, M = 2048.0, 2048
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC, synth.BOTH], [1.0],
+                           40.0, 900.0, 3, 4)                    # 72 templates
+    bank = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, STORE_ALL)
+    p = oracle_params(spec)
+    rng = np.random.default_rng(91)
+    x = rng.standard_normal(12500)
+    if case == "dc_offset":
+        x += 50.0
+    else:
+        x[6001] = 1e5
+    x = x.astype(np.float32)
+    ref = oracle.search(x, fs, p, M, want_rho=True)
+    K, L = ref["rho"].shape
+    for prec in ("split_bf16", "fp32", "split_fp16", "fft_fp32", "bf16"):
+        rho = torch.zeros((K, L), dtype=torch.float32, device="cuda")
+        outs, _, _ = run(ctx, bank, [x], fs, prec, rho_out=rho)
+        err = np.abs(rho.cpu().numpy().astype(np.float64) - ref["rho"])
+        assert err.max() <= TOL[prec], (prec, err.max(), np.unravel_index(err.argmax(), err.shape))
+        check_maxima(outs[0], ref, ref["rho"], TOL[prec], prec)
+    bf.bf_bank_destroy(bank)
