@@ -13,20 +13,22 @@
 // are 128 B.  One bulk copy of 568 rows stages a whole 512-lag x 64-sample
 // block; the core matrices overlap in shared memory, which the MMA only reads.
 //
-// Precision: BF_BF16 issues one MMA (x_hi * h_hi); BF_SPLIT_BF16 issues three
-// into the same FP32 accumulator (x_hi h_hi + x_hi h_lo + x_lo h_hi), dropping
-// only x_lo h_lo (relative size 2^-16 or less).
+// Precision: BF_BF16 issues one MMA (x_hi * h_hi); BF_SPLIT_BF16 and
+// BF_SPLIT_FP16 issue three (x_hi h_hi + x_hi h_lo + x_lo h_hi), dropping only
+// x_lo h_lo (relative size 2^-16 or less), into FP32 accumulators that take
+// the K range in chunks (KRange / n_chunks below): the tensor core's own
+// accumulation truncates, and the chunks are added with rounding to nearest.
 //
 // Warp roles (320 threads, one CTA per SM, persistent over tiles):
 //   warp 0  producer: bulk copies of template and series blocks per stage
 //   warp 1  allocates TMEM, one lane issues tcgen05.mma and commits
-//   warps 2-9 epilogue: tcgen05.ld of the 128 x 512 FP32 accumulator; two
-//            warps per TMEM lane quadrant, each thread owning one template
-//            row and half of the lags: rho = C * inv_norm, running max/argmax
-//            (ties to the smallest lag), sum of rho^2, tails.  Four
-//            independent accumulator chains per thread keep the ALU busy:
-//            the accumulator fills TMEM, so the next tile's MMAs wait for the
-//            epilogue and its speed is tensor-pipe time.
+//   warps 2-9 epilogue: folds the K chunks of a tile, then tcgen05.ld of its
+//            FP32 accumulator; two warps per TMEM lane quadrant, each thread
+//            owning one template row and half of the lags: rho = C *
+//            inv_norm, running max/argmax (ties to the smallest lag), sum of
+//            rho^2, tails.  Four independent accumulator chains per thread
+//            keep the ALU busy.  With 256-lag tiles the two TMEM buffers
+//            alternate, so a tile's epilogue runs under the next tile's MMAs.
 // Every mbarrier wait is bounded in time; on expiry the kernel records an
 // error code in the status word, drains its own copies and MMAs, frees TMEM
 // and returns.
