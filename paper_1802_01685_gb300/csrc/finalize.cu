@@ -206,10 +206,24 @@ cudaError_t launch_skewnorm_fit(const float* v, uint64_t n, double* acc, double*
     return cudaGetLastError();
 }
 
+// v^(-3/8) for v in (0, 1]: the FP32 powf value, then one Newton step on
+// y^8 v^3 = 1 in FP64 (relative error ~1e-7 squared), as GB300 runs a full
+// FP64 pow at a small fraction of its FP32 rate; very small v (a sweep over
+// more than ~30x in frequency near its end) takes the FP64 pow
+__device__ __forceinline__ double pow_m3_8(double v)
+{
+    if (v < 1e-4) return pow(v, -0.375);
+    const double y = (double)powf((float)v, -0.375f);
+    const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
+    const double e = fma(y8, v * v * v, -1.0);          // y^8 v^3 - 1, near 0
+    return y * fma(-e, 0.125, 1.0);                     // y - (y^8 v^3 - 1) / (8 y^7 v^3)
+}
+
+// frequency of the ascending track at local time u (the map paints f(t))
 __device__ __forceinline__ double track_freq(const ChirpDev& p, double u)
 {
     if (p.track == BF_LINEAR) return p.f_lo + (p.f_hi - p.f_lo) * u / p.D;
-    return p.f_lo * pow(1.0 - u / p.tc, -0.375);
+    return p.f_lo * pow_m3_8(1.0 - u / p.tc);
 }
 
 // one warp per candidate, lanes over time cells
