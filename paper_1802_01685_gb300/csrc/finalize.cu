@@ -219,11 +219,17 @@ __device__ __forceinline__ double pow_m3_8(double v)
     return y * fma(-e, 0.125, 1.0);                     // y - (y^8 v^3 - 1) / (8 y^7 v^3)
 }
 
-// frequency of the ascending track at local time u (the map paints f(t))
-__device__ __forceinline__ double track_freq(const ChirpDev& p, double u)
+// Frequency cell of the ascending track at local time u (the map paints f(t)).
+// The fast power-law value is within ~1e-13 of the FP64 pow; where f / df lies
+// that close to a cell edge (the sweep's clamped end, f = f_hi, often does) the
+// cell is decided by the FP64 pow, the same formula the reference evaluates.
+__device__ __forceinline__ int64_t track_cell(const ChirpDev& p, double u, double df)
 {
-    if (p.track == BF_LINEAR) return p.f_lo + (p.f_hi - p.f_lo) * u / p.D;
-    return p.f_lo * pow_m3_8(1.0 - u / p.tc);
+    if (p.track == BF_LINEAR) return (int64_t)floor((p.f_lo + (p.f_hi - p.f_lo) * u / p.D) / df);
+    const double v = 1.0 - u / p.tc;
+    double q = p.f_lo * pow_m3_8(v) / df;
+    if (fabs(q - rint(q)) <= 1e-9 * fabs(q)) q = p.f_lo * pow(v, -0.375) / df;
+    return (int64_t)floor(q);
 }
 
 // one warp per candidate, lanes over time cells
@@ -257,7 +263,7 @@ __global__ void k_paint(const Candidate* __restrict__ cand, const unsigned int* 
             double u = sense == BF_ASC ? t : p.D - t;
             if (u < 0.0) u = 0.0;
             if (u > p.D) u = p.D;
-            const int64_t fb = (int64_t)floor(track_freq(p, u) / df);
+            const int64_t fb = track_cell(p, u, df);
             if (fb < 0 || fb >= (int64_t)nf) continue;
             atomicMax(reinterpret_cast<int*>(f.map + (size_t)b * nf + fb), __float_as_int(a));
         }
