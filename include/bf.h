@@ -97,9 +97,10 @@ typedef enum {
                            segment's energy (quiet or gated stretches next
                            to loud data), where the transform's rounding
                            would swamp rho, are computed directly.          */
-    BF_SPLIT_FP16 = 4   /* as BF_SPLIT_BF16 with FP16 hi and lo parts: the
-                           split holds x and h to 2^-22 instead of 2^-17, at
-                           the same tensor-core rate.  FP16's range is kept
+    BF_SPLIT_FP16 = 4   /* as BF_SPLIT_BF16 with FP16 hi and lo parts (K
+                           chunks of 1024 samples): the split holds x and h
+                           to 2^-22 instead of 2^-17, at the same tensor-core
+                           rate; the accumulation bounds both splits alike.  FP16's range is kept
                            by exact power-of-two scaling on the device (each
                            series so that its largest |x| lies in
                            [2^13, 2^14), templates by 2^8), undone in the
