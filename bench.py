@@ -257,7 +257,7 @@ def run_ours(args, rank, world, local):
     roofline = {"bound": "tensor", "achieved": round(achieved, 1),
                 "peak": peaks["bf16_sustained"], "unit": "TFLOP/s",
                 "frac": round(achieved / peaks["bf16_sustained"], 4), "traffic": traffic,
-                "kernel": f"k_corr_tc<3,{lt}> (split-BF16, {lt} lags per tile, autotuned)",
+                "kernel": f"k_corr_tc<3,{lt}> (split-BF16, {lt} lags per tile, K in 2048-sample chunks)",
                 "kernel_ms": round(k_ms, 2),
                 "peak_source": f"{peaks['source']} bf16_tflops_sustained",
                 "algorithmic_flops_per_launch": issued_flops,
@@ -340,12 +340,18 @@ def run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step):
     def pinned(shape, dtype):
         return torch.empty(shape, dtype=dtype, pin_memory=True).numpy()
 
-    def step():
+    phases = {}
+
+    def step(record=False):
         nonlocal res_host
+        t = [time.perf_counter()]
         bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16)
+        t.append(time.perf_counter())
         for x, c, sd in zip(xs_host, ctrl_host, seeds):
             bf.bf_control_randomize(ctx, x, sd, c)
+        t.append(time.perf_counter())
         res = bf.bf_correlate(ctx, bank, xs_host + ctrl_host, fs, opts)
+        t.append(time.perf_counter())
         if res_host is None:
             K = bf.bf_result_info_get(res).n_templates
             nbins = bf.bf_result_info_get(res).hist_bins
@@ -358,6 +364,11 @@ def run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step):
         for s in range(4):
             r = bf.bf_result_copy_to_host(res, s, want_hist=True, want_map=True, out=res_host[s])
             d2h += sum(a.nbytes for a in r.values() if a is not None)
+        t.append(time.perf_counter())
+        if record:
+            for name, a, b in (("bank_synthesis", 0, 1), ("controls", 1, 2), ("correlate", 2, 3),
+                               ("copy_out", 3, 4)):
+                phases.setdefault(name, []).append(1e3 * (t[b] - t[a]))
         bf.bf_result_destroy(res)
         bf.bf_bank_destroy(bank)
         return d2h
@@ -371,7 +382,7 @@ def run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record()
     for _ in range(n):
-        d2h = step()
+        d2h = step(record=True)
     ev1.record()
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -381,6 +392,7 @@ def run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h + 2 * N * 4,
            "steps": n, "inputs": "pinned host float32; results copied each step into pinned host "
                                        "buffers allocated once",
+           "phase_ms": {k: round(float(np.mean(v)), 2) for k, v in phases.items()},
            "clocks": clocks}
     return out
 
