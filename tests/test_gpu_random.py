@@ -1,0 +1,92 @@
+"""Randomised parity: seeded draws of template length (odd lengths and
+lengths off the 64-sample grid included), sample rate, chirp mix (tracks,
+senses, sweep times), quadrature or not, series lengths down to N = M, bank
+slices and route, each compared with the oracle on the dense output and the
+maxima.  Each case is small enough for the oracle to finish in a second."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_01685_gb300 import bf
+
+from parity import STORE_ALL, TOL, check_maxima
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+ROUTES = ["split_bf16", "fp32", "bf16", "fft_fp32", "split_fp16"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    h = bf.bf_init()
+    yield h
+    bf.bf_destroy(h)
+
+
+def draw_case(seed):
+    r = np.random.default_rng(seed)
+    M = int(r.choice([97, 250, 512, 777, 1000, 1024, 1500, 2000, 2048, 3001, 4096]))
+    T = 1.0
+    fs = float(M) / T
+    K = int(r.integers(3, 40))
+    chirps = []
+    for _ in range(K):
+        track = int(r.integers(2))
+        sense = int(r.integers(3))
+        f_lo = float(r.uniform(0.01, 0.2) * fs)
+        f_hi = float(min(f_lo * r.uniform(1.2, 6.0), 0.45 * fs))
+        D = float(r.uniform(max(2.0 / fs, 0.15), 1.0))
+        chirps.append((track, sense, f_lo, f_hi, D))
+    quad = bool(r.integers(4) == 0)
+    n_series = int(r.integers(1, 4))
+    lens = [M + int(r.choice([0, 1, int(r.integers(2, 2 * M))])) for _ in range(n_series)]
+    b0 = int(r.integers(0, K // 3 + 1))
+    b1 = int(r.integers(max(b0 + 1, 2 * K // 3), K + 1))
+    route = ROUTES[seed % len(ROUTES)]
+    return dict(M=M, fs=fs, chirps=chirps, quad=quad, lens=lens, b0=b0, b1=b1, route=route, rng=r)
+
+
+@pytest.mark.parametrize("seed", range(200))
+def test_random_case(ctx, seed):
+    c = draw_case(seed)
+    fs, M, route = c["fs"], c["M"], c["route"]
+    if route == "fft_fp32" and M > 4096:
+        pytest.skip("FFT route: templates of at most 4096 samples")
+    r = c["rng"]
+    xs = []
+    for n in c["lens"]:
+        x = r.standard_normal(n)
+        if r.integers(2):                               # a bank template placed in the noise
+            k = int(r.integers(len(c["chirps"])))
+            h = oracle.template(*c["chirps"][k], fs, M, 0)
+            o = int(r.integers(0, n - M + 1))
+            x[o:o + M] += float(r.uniform(2.0, 20.0)) * h
+        xs.append(x.astype(np.float32))
+    storage = STORE_ALL | (bf.BF_BANK_QUADRATURE if c["quad"] else 0)
+    bank = bf.bf_bank_create(ctx, c["chirps"], fs, 1.0, storage)
+    p = {k: np.array([ch[i] for ch in c["chirps"][c["b0"]:c["b1"]]], dt)
+         for i, (k, dt) in enumerate((("track", np.int32), ("sense", np.int32), ("f_lo", np.float64),
+                                      ("f_hi", np.float64), ("D", np.float64)))}
+    tol = TOL[route]
+    if route == "bf16" and M < 1024:
+        # plain BF16 rounds each operand to 2^-9: by Cauchy-Schwarz |drho| <= 2^-8 at
+        # any M; the stated 1e-3 relies on the averaging of long templates
+        tol = 2.0 ** -8
+    res = bf.bf_correlate(ctx, bank, xs, fs, bf.make_opts(precision=route, bank_begin=c["b0"], bank_end=c["b1"]))
+    outs = [bf.bf_result_copy_to_host(res, s) for s in range(len(xs))]
+    bf.bf_result_destroy(res)
+    for s, x in enumerate(xs):
+        ref = oracle.search(x, fs, p, M, want_rho=True, quadrature=c["quad"])
+        check_maxima(outs[s], ref, ref["rho"], tol, f"seed {seed} series {s} ({route}, M={M})")
+        if s == 0:
+            K, L = ref["rho"].shape
+            rho = torch.zeros((K, L), dtype=torch.float32, device="cuda")
+            bf.bf_result_destroy(bf.bf_correlate(ctx, bank, [x], fs, bf.make_opts(
+                precision=route, bank_begin=c["b0"], bank_end=c["b1"], rho_out=rho)))
+            err = np.abs(rho.cpu().numpy().astype(np.float64) - ref["rho"]).max()
+            assert err <= tol, (seed, route, M, err)
+    bf.bf_bank_destroy(bank)
