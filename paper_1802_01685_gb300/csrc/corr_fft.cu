@@ -810,7 +810,7 @@ cudaError_t fft_correlate_chunked(bf_ctx* ctx, const bf_bank* bank, std::vector<
     float* scratch = static_cast<float*>(mem.alloc(synth_rows * FN * sizeof(float)));
     keep.push_back(scratch);
     for (int i = 0; i < 2 && i < (int)n_chunks; ++i) {
-        slot[i] = static_cast<float2*>(mem.alloc(chunk * FH * sizeof(float2)));
+        slot[i] = static_cast<float2*>(mem.alloc((chunk + 2) * FH * sizeof(float2)));
         keep.push_back(slot[i]);
     }
     if (!scratch || !slot[0] || (n_chunks > 1 && !slot[1])) {
@@ -830,15 +830,20 @@ cudaError_t fft_correlate_chunked(bf_ctx* ctx, const bf_bank* bank, std::vector<
         const int sl = (int)(c & 1);
         const uint32_t c0 = row_begin + (uint32_t)(c * chunk);
         const uint32_t c1 = (uint32_t)std::min<size_t>(c0 + chunk, row_end);
+        // the spectra are made for the even-aligned row pairs that a stored bank
+        // uses, partner rows outside the slice included: each spectrum carries
+        // its partner's rounding, so the outputs equal the stored bank's
+        const uint32_t s0 = c0 & ~1u;
+        const uint32_t s1 = (uint32_t)std::min<size_t>((c1 + 1) & ~1u, bank->rows);
         if (c >= 2) e = cudaStreamWaitEvent(ctx->aux, used[sl], 0);
         if (e == cudaSuccess)
-            e = template_spectra(bank, c0, c1 - c0, scratch, synth_rows, tw, slot[sl], ctx->n_sm, ctx->aux);
+            e = template_spectra(bank, s0, s1 - s0, scratch, synth_rows, tw, slot[sl], ctx->n_sm, ctx->aux);
         if (e == cudaSuccess) e = cudaEventRecord(made[sl], ctx->aux);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, made[sl], 0);
         for (FftParams& p : batches) {
             if (e != cudaSuccess) break;
             p.hspec = slot[sl];
-            p.hrow0 = c0;
+            p.hrow0 = s0;
             p.k_lo = c0;
             p.k_hi = c1;
             e = launch_corr_fft(p, ctx->n_sm, st);

@@ -90,3 +90,40 @@ def test_random_case(ctx, seed):
             err = np.abs(rho.cpu().numpy().astype(np.float64) - ref["rho"]).max()
             assert err <= tol, (seed, route, M, err)
     bf.bf_bank_destroy(bank)
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_case_generated_bank_and_plan(ctx, seed):
+    """The same draws through a generated bank and through a captured plan:
+    maxima, argmaxes and sigma bit for bit equal to bf_correlate with the
+    stored bank (the plan with white tails; sigma to rounding, its sums are
+    atomics)."""
+    c = draw_case(seed)
+    fs, M, route = c["fs"], c["M"], c["route"]
+    if route == "fft_fp32" and M > 4096:
+        pytest.skip("FFT route: templates of at most 4096 samples")
+    r = c["rng"]
+    xs = [r.standard_normal(n).astype(np.float32) for n in c["lens"]]
+    q = bf.BF_BANK_QUADRATURE if c["quad"] else 0
+    stored = bf.bf_bank_create(ctx, c["chirps"], fs, 1.0, STORE_ALL | q)
+    gen = bf.bf_bank_create(ctx, c["chirps"], fs, 1.0, bf.BF_BANK_GENERATED | q)
+    opts = bf.make_opts(precision=route, bank_begin=c["b0"], bank_end=c["b1"])
+
+    def outs(res, owned=True):
+        o = [bf.bf_result_copy_to_host(res, s) for s in range(len(xs))]
+        if owned:
+            bf.bf_result_destroy(res)
+        return o
+
+    ref = outs(bf.bf_correlate(ctx, stored, xs, fs, opts))
+    g = outs(bf.bf_correlate(ctx, gen, xs, fs, opts))
+    plan = bf.bf_plan_create(ctx, stored, c["lens"], fs, opts)
+    pl = outs(bf.bf_plan_run(plan, xs), owned=False)          # the plan owns its result
+    for s in range(len(xs)):
+        for other in (g[s], pl[s]):
+            np.testing.assert_array_equal(other["max"], ref[s]["max"])
+            np.testing.assert_array_equal(other["argmax"], ref[s]["argmax"])
+            np.testing.assert_allclose(other["sigma"], ref[s]["sigma"], rtol=1e-6, atol=1e-12)
+    bf.bf_plan_destroy(plan)
+    bf.bf_bank_destroy(stored)
+    bf.bf_bank_destroy(gen)
