@@ -127,3 +127,96 @@ def test_random_case_generated_bank_and_plan(ctx, seed):
     bf.bf_plan_destroy(plan)
     bf.bf_bank_destroy(stored)
     bf.bf_bank_destroy(gen)
+
+
+@pytest.mark.parametrize("seed", range(300, 340))
+def test_random_case_tails_and_map(ctx, seed):
+    """Tails |rho| >= kappa sigma_white and the time-frequency map they paint,
+    for random draws, against the oracle at the same threshold: every tail
+    the oracle finds above thr + tol is listed, none below thr - tol, and
+    every map cell lies between the oracle maps painted at thr -/+ tol."""
+    c = draw_case(seed)
+    fs, M, route = c["fs"], c["M"], c["route"]
+    if route == "fft_fp32" and M > 4096:
+        pytest.skip("FFT route: templates of at most 4096 samples")
+    r = c["rng"]
+    x = r.standard_normal(c["lens"][0] + M)
+    k = int(r.integers(c["b0"], c["b1"]))
+    x[M // 2:M // 2 + M] += 6.0 * oracle.template(*c["chirps"][k], fs, M, 0)
+    x = x.astype(np.float32)
+    q = bf.BF_BANK_QUADRATURE if c["quad"] else 0
+    bank = bf.bf_bank_create(ctx, c["chirps"], fs, 1.0, STORE_ALL | q)
+    p = {kk: np.array([ch[i] for ch in c["chirps"][c["b0"]:c["b1"]]], dt)
+         for i, (kk, dt) in enumerate((("track", np.int32), ("sense", np.int32), ("f_lo", np.float64),
+                                       ("f_hi", np.float64), ("D", np.float64)))}
+    tol = TOL[route] if not (route == "bf16" and M < 1024) else 2.0 ** -8
+    kappa = 3.0
+    thr = kappa * np.sqrt((2.0 if c["quad"] else 1.0) / M)
+    res = bf.bf_correlate(ctx, bank, [x], fs, bf.make_opts(precision=route, bank_begin=c["b0"],
+                                                           bank_end=c["b1"], kappa=kappa,
+                                                           want_tails=True, want_map=True))
+    tails = bf.bf_result_copy_tails(res)
+    mp = bf.bf_result_copy_to_host(res, 0, want_map=True)["map"]
+    bf.bf_result_destroy(res)
+    ref = oracle.search(x, fs, p, M, want_rho=True, quadrature=c["quad"])
+    a = np.abs(ref["rho"])
+    koff = c["b0"]
+    got = {(int(t["k"]) - koff, int(t["tau"])) for t in tails}
+    must = set(zip(*[v.tolist() for v in np.nonzero(a >= thr + tol)]))
+    may = set(zip(*[v.tolist() for v in np.nonzero(a >= thr - tol)]))
+    assert must <= got <= may, (seed, route, len(must - got), len(got - may))
+    hi = oracle.search(x, fs, p, M, thr=thr + tol, want_map=True, quadrature=c["quad"])["map"]
+    lo = oracle.search(x, fs, p, M, thr=thr - tol, want_map=True, quadrature=c["quad"])["map"]
+    assert mp.shape == hi.shape
+    assert np.all(mp >= hi - tol) and np.all(mp <= lo + tol), (seed, route)
+    bf.bf_bank_destroy(bank)
+
+
+def test_random_serving_mix(ctx):
+    """Thirty random requests (lengths, bank slices, routes, map and tails on or
+    off) against a plain and a quadrature bank, all submitted at once: each
+    result equals, bit for bit, the same search run alone."""
+    import time
+    rng = np.random.default_rng(500)
+    fs = 2048.0
+    chirps = []
+    for _ in range(300):
+        f_lo = float(rng.uniform(20.0, 300.0))
+        chirps.append((int(rng.integers(2)), int(rng.integers(3)), f_lo,
+                       float(min(f_lo * rng.uniform(1.3, 5.0), 950.0)), float(rng.uniform(0.3, 1.0))))
+    banks = [bf.bf_bank_create(ctx, chirps, fs, 1.0, STORE_ALL),
+             bf.bf_bank_create(ctx, chirps, fs, 1.0, STORE_ALL | bf.BF_BANK_QUADRATURE)]
+    reqs = []
+    for i in range(30):
+        n = int(rng.integers(2048, 40000))
+        b0 = int(rng.integers(0, 150))
+        b1 = int(rng.integers(b0 + 1, 301))
+        route = ROUTES[int(rng.integers(len(ROUTES)))]
+        x = rng.standard_normal(n).astype(np.float32)
+        opts = bf.make_opts(precision=route, bank_begin=b0, bank_end=b1, want_map=bool(rng.integers(2)),
+                            want_tails=bool(rng.integers(2)), kappa=4.0)
+        reqs.append((banks[int(rng.integers(2))], x, opts))
+
+    def fetch(res, opts):
+        o = bf.bf_result_copy_to_host(res, 0, want_hist=True, want_map=bool(opts.want_map))
+        if opts.want_tails:
+            o["tails"] = np.sort(bf.bf_result_copy_tails(res), order=["k", "tau"])
+        bf.bf_result_destroy(res)
+        return o
+
+    alone = [fetch(bf.bf_correlate(ctx, b, [x], fs, o), o) for b, x, o in reqs]
+    tickets = [bf.bf_serve_submit(ctx, b, x, fs, o) for b, x, o in reqs]
+    for t, (b, x, o), a in zip(tickets, reqs, alone):
+        st, res = bf.bf_serve_poll(ctx, t, 120_000_000)
+        assert st == bf.BF_OK
+        m = fetch(res, o)
+        np.testing.assert_array_equal(m["max"], a["max"])
+        np.testing.assert_array_equal(m["argmax"], a["argmax"])
+        np.testing.assert_allclose(m["sigma"], a["sigma"], rtol=1e-6, atol=1e-12)
+        np.testing.assert_array_equal(m["hist"], a["hist"])
+        if o.want_map:
+            np.testing.assert_array_equal(m["map"], a["map"])
+        if o.want_tails:
+            np.testing.assert_array_equal(m["tails"], a["tails"])
+    for b in banks:
+        bf.bf_bank_destroy(b)
