@@ -220,3 +220,59 @@ def test_random_serving_mix(ctx):
             np.testing.assert_array_equal(m["tails"], a["tails"])
     for b in banks:
         bf.bf_bank_destroy(b)
+
+
+@pytest.mark.parametrize("route", ROUTES)
+def test_more_series_than_one_launch_holds(ctx, route):
+    """130 series of random lengths in one call: more than a launch holds (64
+    segments or 64 FFT series), so the call splits into several launches.
+    Every series' maxima and the mean over series match the oracle."""
+    rng = np.random.default_rng(600 + ROUTES.index(route))
+    fs, M = 256.0, 256
+    chirps = [(int(rng.integers(2)), int(rng.integers(3)), float(f), float(f * rng.uniform(1.5, 3.0)),
+               float(rng.uniform(0.4, 1.0))) for f in rng.uniform(5.0, 40.0, 20)]
+    bank = bf.bf_bank_create(ctx, chirps, fs, 1.0, STORE_ALL)
+    p = {k: np.array([ch[i] for ch in chirps], dt)
+         for i, (k, dt) in enumerate((("track", np.int32), ("sense", np.int32), ("f_lo", np.float64),
+                                      ("f_hi", np.float64), ("D", np.float64)))}
+    xs = [rng.standard_normal(int(rng.integers(M, 4 * M))).astype(np.float32) for _ in range(130)]
+    outs, mean, info = [None], None, None
+    res = bf.bf_correlate(ctx, bank, xs, fs, bf.make_opts(precision=route))
+    outs = [bf.bf_result_copy_to_host(res, s) for s in range(len(xs))]
+    mean = bf.bf_result_copy_mean_max(res)
+    bf.bf_result_destroy(res)
+    tol = TOL[route] if route != "bf16" else 2.0 ** -8
+    acc = np.zeros(len(chirps))
+    for s, x in enumerate(xs):
+        ref = oracle.search(x, fs, p, M, want_rho=True)
+        check_maxima(outs[s], ref, ref["rho"], tol, f"{route} series {s}")
+        acc += ref["max"]
+    np.testing.assert_allclose(mean, acc / len(xs), atol=tol)
+
+
+@pytest.mark.parametrize("seed", range(700, 712))
+def test_random_parseval_predictor(ctx, seed):
+    """The Parseval-predicted sigma of random banks and series (white, red and
+    Poisson-like) against the oracle's."""
+    c = draw_case(seed)
+    fs, M = c["fs"], c["M"]
+    r = c["rng"]
+    n = c["lens"][0] + 2 * M
+    kind = seed % 3
+    x = r.standard_normal(n)
+    if kind == 1:
+        x = np.cumsum(x) * 0.05 + x                    # red
+    elif kind == 2:
+        x = r.poisson(3.0, n) - 3.0                     # counts, mean removed
+    x = x.astype(np.float32)
+    bank = bf.bf_bank_create(ctx, c["chirps"], fs, 1.0, STORE_ALL)
+    res = bf.bf_correlate(ctx, bank, [x], fs, bf.make_opts(precision="split_bf16", bank_begin=c["b0"],
+                                                           bank_end=c["b1"], tail_sigma=bf.BF_SIGMA_PARSEVAL))
+    got = bf.bf_result_copy_sigma_pred(res, 0).astype(np.float64)
+    bf.bf_result_destroy(res)
+    p = {k: np.array([ch[i] for ch in c["chirps"][c["b0"]:c["b1"]]], dt)
+         for i, (k, dt) in enumerate((("track", np.int32), ("sense", np.int32), ("f_lo", np.float64),
+                                      ("f_hi", np.float64), ("D", np.float64)))}
+    ref = oracle.parseval_sigma(x, oracle.bank(p, fs, M))
+    np.testing.assert_allclose(got, ref, rtol=2e-5, atol=1e-9)
+    bf.bf_bank_destroy(bank)
