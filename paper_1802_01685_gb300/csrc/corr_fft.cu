@@ -541,104 +541,155 @@ __global__ void __launch_bounds__(256) k_fft_flags(const __grid_constant__ FftSe
     const uint64_t L = b.L[i], N = b.N[i];
     const double* S = b.S[i];
     float* inv = b.inv[i];
-    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < L;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-        const float iv = inv[t];
-        if (!(iv > 0.f)) continue;                      // empty window: rho = 0 exactly
-        const uint64_t a = t / b.V * b.V;               // the segment's first sample
-        const uint64_t e = min(a + (uint64_t)FN, N);
-        const double E = S[e] - S[a];
-        if (E * (double)iv * (double)iv > FFT_FIX_RATIO2) {
+    const uint32_t lane = threadIdx.x & 31;
+    // the loop bound is uniform over a warp, so each warp appends its lanes'
+    // lags together, in lag order (the fixup reads them as coalesced runs)
+    for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < L; base += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t t = base + threadIdx.x;
+        bool flag = false;
+        float iv = 0.f;
+        if (t < L) {
+            iv = inv[t];
+            if (iv > 0.f) {                             // empty window: rho = 0 exactly
+                const uint64_t a = t / b.V * b.V;       // the segment's first sample
+                const uint64_t e = min(a + (uint64_t)FN, N);
+                const double E = S[e] - S[a];
+                flag = E * (double)iv * (double)iv > FFT_FIX_RATIO2;
+            }
+        }
+        const uint32_t mask = __ballot_sync(0xffffffffu, flag);
+        if (mask == 0u) continue;
+        uint32_t slot0 = 0;
+        if (lane == 0) slot0 = atomicAdd(b.n_fix + i, (uint32_t)__popc(mask));   // each lag once: < L entries
+        slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+        if (flag) {
             inv[t] = 0.f;
-            const uint32_t slot = atomicAdd(b.n_fix + i, 1u);     // each lag once: < L entries
+            const uint32_t slot = slot0 + __popc(mask & ((1u << lane) - 1u));
             b.fix[i][2 * slot] = (uint32_t)t;
             b.fix[i][2 * slot + 1] = __float_as_uint(iv);
         }
     }
 }
 
-// The direct computation of the listed lags: each CTA takes outputs (a row, or
-// a quadrature pair of rows) of the launch's range, synthesises their
-// templates in shared memory as the bank does (FP32 rows at unit norm), and
-// for every listed lag of every series forms the FP32 dot product with the
-// window (one warp per lag), then feeds the same max keys, sums of rho^2,
-// tails and dense output (written after the correlation kernel's 0 there) as
-// the correlation kernel.  Returns at once when no series has a listed lag.
+// The direct computation of the listed lags.  Each CTA takes FIX_ROWS template
+// rows of the launch's range (FIX_ROWS / 2 quadrature pairs), synthesises them
+// in shared memory as the bank does (FP32 rows at unit norm), and gives each
+// lane one listed lag: the lane runs the FP32 dot products of its window with
+// every row, four samples at a time (four window loads, one 16-byte broadcast
+// per row), so one shared-memory wavefront feeds 32 FMAs of the warp rather
+// than one.  The products then feed the same max keys, sums of rho^2, tails and
+// dense output (written after the correlation kernel's 0 there) as the
+// correlation kernel.  Returns at once when no series has a listed lag.
 constexpr int FIX_T = 256;
+constexpr int FIX_ROWS = 4;
+constexpr size_t FIX_SMEM = (size_t)FIX_ROWS * FH * sizeof(float);      // rows of at most FH samples
 
 template <bool QUAD>
 __global__ void __launch_bounds__(FIX_T) k_fft_fixup(const __grid_constant__ FftParams p)
 {
-    __shared__ float g[QUAD ? 2 : 1][FH];               // templates of at most FH samples
+    constexpr int NOUT = QUAD ? FIX_ROWS / 2 : FIX_ROWS;
+    extern __shared__ __align__(16) float fx_rows[];                     // [FIX_ROWS][M_s]
     __shared__ double red[8];
-    __shared__ unsigned long long w_key[FIX_T / 32];
-    __shared__ double w_ss[FIX_T / 32];
+    __shared__ unsigned long long w_key[FIX_T / 32][NOUT];
+    __shared__ double w_ss[FIX_T / 32][NOUT];
     uint32_t total = 0;
     for (int i = 0; i < p.n_ser; ++i) total += *p.ser[i].n_fix;
     if (total == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rows = QUAD ? 2u : 1u;
-    const uint32_t n_out = (p.k_hi - p.k_lo) / rows;
     const uint32_t M = p.M, M_s = (M + 63u) & ~63u;
-    for (uint32_t u = blockIdx.x; u < n_out; u += gridDim.x) {
-        const uint32_t row = p.k_lo + rows * u;
-        const float n0 = synth_row(p.chirps, row, p.quad, true, M, M_s, p.fs, g[0], red);
-        const float n1 = QUAD ? synth_row(p.chirps, row + 1, p.quad, true, M, M_s, p.fs, g[QUAD ? 1 : 0], red)
-                              : 0.f;
-        for (uint32_t m = threadIdx.x; m < M_s; m += FIX_T) {
-            g[0][m] *= n0;
-            if (QUAD) g[QUAD ? 1 : 0][m] *= n1;
+    const uint32_t n_groups = (p.k_hi - p.k_lo + FIX_ROWS - 1) / FIX_ROWS;   // a pair never splits
+    for (uint32_t grp = blockIdx.x; grp < n_groups; grp += gridDim.x) {
+        const uint32_t row0 = p.k_lo + grp * FIX_ROWS;
+        const uint32_t nr = min((uint32_t)FIX_ROWS, p.k_hi - row0);
+        for (uint32_t r = 0; r < (uint32_t)FIX_ROWS; ++r) {
+            float* g = fx_rows + (size_t)r * M_s;
+            const float nrm = synth_row(p.chirps, row0 + r, p.quad, r < nr, M, M_s, p.fs, g, red);
+            for (uint32_t m = threadIdx.x; m < M_s; m += FIX_T) g[m] *= nrm;
         }
         __syncthreads();
-        const uint32_t o = QUAD ? (row - p.k_begin) >> 1 : row - p.k_begin;    // output index
-        const uint32_t kt = QUAD ? row >> 1 : row;                             // tail index
+        uint32_t o[NOUT], kt[NOUT];
+        bool live[NOUT];
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) {
+            const uint32_t row = row0 + (QUAD ? 2 * j : j);
+            live[j] = row < p.k_hi;
+            o[j] = QUAD ? (row - p.k_begin) >> 1 : row - p.k_begin;      // output index
+            kt[j] = QUAD ? row >> 1 : row;                               // tail index
+        }
         for (int i = 0; i < p.n_ser; ++i) {
             const FftSeries& S = p.ser[i];
             const uint32_t n = min(*S.n_fix, S.L);
-            if (n == 0) continue;
-            const float thr = S.sigma_pred ? S.kappa * S.sigma_pred[o] : p.thr;
-            unsigned long long best = 0ull;
-            double ss = 0.0;
-            for (uint32_t f = warp; f < n; f += FIX_T / 32) {
-                const uint32_t tau = S.fix[2 * f];
-                const float* xw = S.x + tau;
-                float c = 0.f, d = 0.f;
-                for (uint32_t m = lane; m < M; m += 32) {
-                    const float xv = xw[m];
-                    c = fmaf(xv, g[0][m], c);
-                    if (QUAD) d = fmaf(xv, g[QUAD ? 1 : 0][m], d);
+            if (n == 0) continue;                                        // uniform over the CTA
+            float thr[NOUT];
+#pragma unroll
+            for (int j = 0; j < NOUT; ++j)
+                thr[j] = !live[j] ? INFINITY : (S.sigma_pred ? S.kappa * S.sigma_pred[o[j]] : p.thr);
+            unsigned long long best[NOUT];
+            double ss[NOUT];
+#pragma unroll
+            for (int j = 0; j < NOUT; ++j) {
+                best[j] = 0ull;
+                ss[j] = 0.0;
+            }
+            for (uint32_t f0 = warp * 32u; f0 < n; f0 += FIX_T) {
+                const uint32_t f = f0 + lane;
+                const bool act = f < n;
+                const uint32_t tau = act ? S.fix[2 * f] : 0u;
+                const float iv = act ? __uint_as_float(S.fix[2 * f + 1]) : 0.f;   // the window's norm
+                const float* xw = S.x + tau;    // padded: reads up to tau + M + 2 stay inside
+                float c[FIX_ROWS];
+#pragma unroll
+                for (int r = 0; r < FIX_ROWS; ++r) c[r] = 0.f;
+                for (uint32_t m = 0; m < M; m += 4) {           // rows are zero past M
+                    const float x0 = xw[m], x1 = xw[m + 1], x2 = xw[m + 2], x3 = xw[m + 3];
+#pragma unroll
+                    for (int r = 0; r < FIX_ROWS; ++r) {
+                        const float4 gv = *reinterpret_cast<const float4*>(fx_rows + (size_t)r * M_s + m);
+                        c[r] = fmaf(x0, gv.x, c[r]);
+                        c[r] = fmaf(x1, gv.y, c[r]);
+                        c[r] = fmaf(x2, gv.z, c[r]);
+                        c[r] = fmaf(x3, gv.w, c[r]);
+                    }
                 }
+                if (!act) continue;
+#pragma unroll
+                for (int j = 0; j < NOUT; ++j) {
+                    if (!live[j]) continue;
+                    const float rho = QUAD ? sqrtf(c[2 * j] * c[2 * j] + c[2 * j + 1] * c[2 * j + 1]) * iv
+                                           : c[j] * iv;
+                    const float a = fabsf(rho);
+                    const unsigned long long key = pack_max(a, tau);
+                    best[j] = key > best[j] ? key : best[j];
+                    ss[j] += (double)rho * (double)rho;
+                    if (a >= thr[j]) push_tail(p, S.series_id, kt[j], tau, rho);
+                    if (S.rho) S.rho[(size_t)o[j] * S.L + tau] = rho;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NOUT; ++j) {
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
-                    c += __shfl_xor_sync(0xffffffffu, c, off);
-                    if (QUAD) d += __shfl_xor_sync(0xffffffffu, d, off);
+                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best[j], off);
+                    best[j] = ok > best[j] ? ok : best[j];
+                    ss[j] += __shfl_xor_sync(0xffffffffu, ss[j], off);
                 }
-                const float iv = __uint_as_float(S.fix[2 * f + 1]);     // the window's norm
-                const float r = QUAD ? sqrtf(c * c + d * d) * iv : c * iv;
-                const float a = fabsf(r);
                 if (lane == 0) {
-                    const unsigned long long key = pack_max(a, tau);
-                    best = key > best ? key : best;
-                    ss += (double)r * (double)r;
-                    if (a >= thr) push_tail(p, S.series_id, kt, tau, r);
-                    if (S.rho) S.rho[(size_t)o * S.L + tau] = r;
+                    w_key[warp][j] = best[j];
+                    w_ss[warp][j] = ss[j];
                 }
-            }
-            if (lane == 0) {
-                w_key[warp] = best;
-                w_ss[warp] = ss;
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
+            if (threadIdx.x < NOUT && live[threadIdx.x]) {
+                const int j = threadIdx.x;
                 unsigned long long kmax = 0ull;
                 double tot = 0.0;
                 for (int w = 0; w < FIX_T / 32; ++w) {
-                    kmax = w_key[w] > kmax ? w_key[w] : kmax;
-                    tot += w_ss[w];
+                    kmax = w_key[w][j] > kmax ? w_key[w][j] : kmax;
+                    tot += w_ss[w][j];
                 }
                 if (kmax != 0ull) {
-                    atomicMax(S.vmax + o, kmax);
-                    atomicAdd(S.sumsq + o, tot);
+                    atomicMax(S.vmax + o[j], kmax);
+                    atomicAdd(S.sumsq + o[j], tot);
                 }
             }
             __syncthreads();
@@ -657,6 +708,10 @@ cudaError_t fft_attributes()
         e = cudaFuncSetAttribute(k_fft_series, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fft_bank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_fixup<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FIX_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_fixup<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FIX_SMEM);
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -779,12 +834,13 @@ cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !p.chirps) return e;
     // the lags left to the direct computation (none: the CTAs return at once)
-    const uint32_t n_out = p.quad ? (p.k_hi - p.k_lo) / 2 : p.k_hi - p.k_lo;
-    if (n_out == 0) return e;
-    const unsigned fgrid = std::min<unsigned>(n_out, (unsigned)n_sm * 8);
+    const uint32_t n_groups = (p.k_hi - p.k_lo + FIX_ROWS - 1) / FIX_ROWS;
+    if (n_groups == 0) return e;
+    const unsigned fgrid = std::min<unsigned>(n_groups, (unsigned)n_sm * 3);
+    const size_t smem = (size_t)FIX_ROWS * ((p.M + 63u) & ~63u) * sizeof(float);
     count_launches(1);
-    if (p.quad) k_fft_fixup<true><<<fgrid, FIX_T, 0, st>>>(p);
-    else k_fft_fixup<false><<<fgrid, FIX_T, 0, st>>>(p);
+    if (p.quad) k_fft_fixup<true><<<fgrid, FIX_T, smem, st>>>(p);
+    else k_fft_fixup<false><<<fgrid, FIX_T, smem, st>>>(p);
     return cudaGetLastError();
 }
 
