@@ -299,6 +299,15 @@ bf_status bf_result_get_mean_max(const bf_result* r, const float** mean_max);
 bf_status bf_result_copy_to_host(const bf_result* r, size_t s, float* vmax,
                                  int32_t* argmax, float* sigma, uint32_t* hist,
                                  float* map);
+/* The same copies, enqueued on `stream` (a cudaStream_t; NULL: the legacy
+ * default stream) without waiting for them.  They are done when the stream is; until
+ * then `r` must not be destroyed and the host arrays must stay allocated.
+ * Host arrays should be page-locked (cudaHostAlloc or cudaHostRegister), else
+ * the copies may run synchronously.  Errors: as bf_result_copy_to_host, for
+ * the enqueueing only; a failed copy shows on the stream. */
+bf_status bf_result_copy_to_host_async(const bf_result* r, size_t s, float* vmax,
+                                       int32_t* argmax, float* sigma, uint32_t* hist,
+                                       float* map, void* stream);
 bf_status bf_result_copy_mean_max(const bf_result* r, float* host_mean_max);
 
 /* Skew-normal fit of the per-template maxima (Sect. 1, Fig. 2: the

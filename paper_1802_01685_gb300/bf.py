@@ -136,6 +136,7 @@ def load() -> C.CDLL:
             "bf_result_get_map": (i, [p, s, P(p)]),
             "bf_result_get_mean_max": (i, [p, P(p)]),
             "bf_result_copy_to_host": (i, [p, s, p, p, p, p, p]),
+            "bf_result_copy_to_host_async": (i, [p, s, p, p, p, p, p, p]),
             "bf_result_copy_mean_max": (i, [p, p]),
             "bf_result_fit_max": (i, [p, s, p, P(bf_skewnorm)]),
             "bf_result_coincidence": (i, [p, s, s, d, C.c_uint32, p, p, p, p, p]),
@@ -337,12 +338,9 @@ def bf_result_get_mean_max(res: int) -> int:
     return a.value
 
 
-def bf_result_copy_to_host(res: int, s: int, want_hist=True, want_map=False, out: dict | None = None) -> dict:
-    """Per-template max, argmax and sigma of series s, and optionally its
-    histogram and map, copied into new numpy arrays, or into the caller's
-    arrays in ``out`` (keys max, argmax, sigma, hist, map: C-contiguous, of the
-    result's sizes and dtypes float32, int32, float32, uint32, float32), for
-    instance views of pinned host memory reused across calls."""
+def _copy_arrays(res: int, s: int, want_hist: bool, want_map: bool, out: dict | None) -> dict:
+    """The host arrays a copy of series s writes: the caller's in ``out``,
+    checked against the result's sizes and dtypes, else new ones."""
     info = bf_result_info_get(res)
     K = info.n_templates
     shapes = {"max": ((K,), np.float32), "argmax": ((K,), np.int32), "sigma": ((K,), np.float32)}
@@ -359,11 +357,38 @@ def bf_result_copy_to_host(res: int, s: int, want_hist=True, want_map=False, out
             raise ValueError(f"out[{key!r}] must be a writeable C-contiguous {np.dtype(dt).name} "
                              f"array of shape {shape}")
         arrs[key] = a
-    hist, mp = arrs.get("hist"), arrs.get("map")
-    _check(load().bf_result_copy_to_host(
-        res, s, arrs["max"].ctypes.data, arrs["argmax"].ctypes.data, arrs["sigma"].ctypes.data,
-        hist.ctypes.data if hist is not None else None, mp.ctypes.data if mp is not None else None))
-    return dict(max=arrs["max"], argmax=arrs["argmax"], sigma=arrs["sigma"], hist=hist, map=mp)
+    return dict(max=arrs["max"], argmax=arrs["argmax"], sigma=arrs["sigma"], hist=arrs.get("hist"),
+                map=arrs.get("map"))
+
+
+def _ptrs(a: dict):
+    return [a[k].ctypes.data if a[k] is not None else None for k in ("max", "argmax", "sigma", "hist", "map")]
+
+
+def bf_result_copy_to_host(res: int, s: int, want_hist=True, want_map=False, out: dict | None = None) -> dict:
+    """Per-template max, argmax and sigma of series s, and optionally its
+    histogram and map, copied into new numpy arrays, or into the caller's
+    arrays in ``out`` (keys max, argmax, sigma, hist, map: C-contiguous, of the
+    result's sizes and dtypes float32, int32, float32, uint32, float32), for
+    instance views of pinned host memory reused across calls."""
+    arrs = _copy_arrays(res, s, want_hist, want_map, out)
+    _check(load().bf_result_copy_to_host(res, s, *_ptrs(arrs)))
+    return arrs
+
+
+def bf_result_copy_to_host_async(res: int, s: int, out: dict, stream=None, want_hist=True,
+                                 want_map=False) -> dict:
+    """Enqueues the copies of bf_result_copy_to_host into the caller's arrays
+    ``out`` (page-locked host memory, e.g. numpy views of pinned torch
+    tensors) on ``stream`` (a cudaStream_t handle such as
+    ``torch.cuda.Stream().cuda_stream``; None: the legacy default stream) and
+    returns at once. The arrays hold the outputs once the stream has been
+    synchronised; ``res`` must not be destroyed before then."""
+    arrs = _copy_arrays(res, s, want_hist, want_map, out)
+    if any(out.get(k) is None for k, v in arrs.items() if v is not None):
+        raise ValueError("an asynchronous copy needs every array it writes in `out`")
+    _check(load().bf_result_copy_to_host_async(res, s, *_ptrs(arrs), stream))
+    return arrs
 
 
 def bf_result_copy_mean_max(res: int) -> np.ndarray:

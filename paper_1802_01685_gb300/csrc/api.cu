@@ -1356,26 +1356,42 @@ bf_status bf_result_get_mean_max(const bf_result* r, const float** mean_max)
     return BF_OK;
 }
 
+// The copies of bf_result_copy_to_host(_async): all enqueued on one stream,
+// then waited for unless `async`.
+static bf_status copy_series(const bf_result* r, size_t s, float* vmax, int32_t* argmax,
+                             float* sigma, uint32_t* hist, float* map, cudaStream_t st, bool async)
+{
+    if (!r || s >= r->n_series) { set_error("bad series index"); return BF_EINVAL; }
+    if (hist && !r->hist) { set_error("no histogram was requested"); return BF_EINVAL; }
+    if (map && !r->map) { set_error("no map was requested"); return BF_EINVAL; }
+    cudaSetDevice(r->ctx->device);
+    const size_t K = r->K;
+    const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaSuccess;
+    if (vmax) e = cudaMemcpyAsync(vmax, r->vmax + s * K, K * 4, d2h, st);
+    if (e == cudaSuccess && argmax) e = cudaMemcpyAsync(argmax, r->argmax + s * K, K * 4, d2h, st);
+    if (e == cudaSuccess && sigma) e = cudaMemcpyAsync(sigma, r->sigma + s * K, K * 4, d2h, st);
+    if (e == cudaSuccess && hist) e = cudaMemcpyAsync(hist, r->hist + s * r->nbins, r->nbins * 4, d2h, st);
+    if (e == cudaSuccess && map)
+        e = cudaMemcpyAsync(map, r->map + r->map_off[s], (size_t)r->map_nt[s] * r->map_nf * 4, d2h, st);
+    if (e == cudaSuccess && !async) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? BF_OK : cuda_fail(e, "result copy");
+}
+
 bf_status bf_result_copy_to_host(const bf_result* r, size_t s, float* vmax, int32_t* argmax,
                                  float* sigma, uint32_t* hist, float* map)
 {
-    if (!r || s >= r->n_series) { set_error("bad series index"); return BF_EINVAL; }
-    cudaSetDevice(r->ctx->device);
-    const size_t K = r->K;
-    cudaError_t e = cudaSuccess;
-    if (vmax) e = cudaMemcpy(vmax, r->vmax + s * K, K * 4, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && argmax) e = cudaMemcpy(argmax, r->argmax + s * K, K * 4, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && sigma) e = cudaMemcpy(sigma, r->sigma + s * K, K * 4, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && hist) {
-        if (!r->hist) { set_error("no histogram was requested"); return BF_EINVAL; }
-        e = cudaMemcpy(hist, r->hist + s * r->nbins, r->nbins * 4, cudaMemcpyDeviceToHost);
-    }
-    if (e == cudaSuccess && map) {
-        if (!r->map) { set_error("no map was requested"); return BF_EINVAL; }
-        e = cudaMemcpy(map, r->map + r->map_off[s], (size_t)r->map_nt[s] * r->map_nf * 4,
-                       cudaMemcpyDeviceToHost);
-    }
-    return e == cudaSuccess ? BF_OK : cuda_fail(e, "result copy");
+    if (!r) { set_error("NULL result"); return BF_EINVAL; }
+    // the legacy default stream, as cudaMemcpy: ordered after work on blocking streams
+    return copy_series(r, s, vmax, argmax, sigma, hist, map, cudaStreamLegacy, false);
+}
+
+bf_status bf_result_copy_to_host_async(const bf_result* r, size_t s, float* vmax, int32_t* argmax,
+                                       float* sigma, uint32_t* hist, float* map, void* stream)
+{
+    if (!r) { set_error("NULL result"); return BF_EINVAL; }
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : cudaStreamLegacy;
+    return copy_series(r, s, vmax, argmax, sigma, hist, map, st, true);
 }
 
 bf_status bf_result_copy_mean_max(const bf_result* r, float* out)

@@ -606,6 +606,55 @@ def test_copy_into_caller_buffers(ctx, tiny):
     bf.bf_result_destroy(res)
 
 
+def test_async_copy_into_pinned_buffers(ctx, tiny):
+    """bf_result_copy_to_host_async gives, once its stream is synchronised,
+    what the synchronous copy gives, for every series of a batch, on a caller
+    stream busy with other work first, and on the default stream. Without every array in `out`, or with a histogram that
+    was not requested, it is refused before anything is enqueued."""
+    w, bank, _, _ = tiny
+    fs = w["fs"]
+    xs = [w["series"][0], w["series"][0][:5000].copy(), w["series"][0][1000:].copy()]
+    res = bf.bf_correlate(ctx, bank, xs, fs, bf.make_opts(want_map=True))
+    stream = torch.cuda.Stream()
+    big = torch.zeros(1 << 26, device="cuda")
+    for st in (stream, None):
+        refs, outs = [], []
+        for s in range(len(xs)):
+            ref = bf.bf_result_copy_to_host(res, s, want_hist=True, want_map=True)
+            K, nb = len(ref["max"]), len(ref["hist"])
+            outs.append({"max": torch.full((K,), -1.0, pin_memory=True).numpy(),
+                         "argmax": torch.full((K,), -1, dtype=torch.int32, pin_memory=True).numpy(),
+                         "sigma": torch.zeros(K, pin_memory=True).numpy(),
+                         "hist": torch.zeros(nb, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32),
+                         "map": torch.zeros(ref["map"].shape, pin_memory=True).numpy()})
+            refs.append(ref)
+        if st is not None:
+            with torch.cuda.stream(st):
+                big.mul_(2.0).add_(1.0)                      # the stream is busy first
+        for s in range(len(xs)):
+            got = bf.bf_result_copy_to_host_async(res, s, outs[s], st.cuda_stream if st else None,
+                                                  want_hist=True, want_map=True)
+            assert all(got[k] is outs[s][k] for k in got)
+        if st is not None:
+            st.synchronize()
+        else:
+            torch.cuda.default_stream().synchronize()
+        for ref, out in zip(refs, outs):
+            for key in ref:
+                np.testing.assert_array_equal(out[key], ref[key])
+    K = len(refs[0]["max"])
+    with pytest.raises(ValueError):
+        bf.bf_result_copy_to_host_async(res, 0, {"max": np.zeros(K, np.float32)}, want_hist=False)
+    res2 = bf.bf_correlate(ctx, bank, xs[:1], fs, bf.make_opts(want_hist=False))
+    o = {"max": np.zeros(K, np.float32), "argmax": np.zeros(K, np.int32), "sigma": np.zeros(K, np.float32),
+         "hist": np.zeros(1024, np.uint32)}
+    with pytest.raises(bf.BFError) as e:
+        bf.bf_result_copy_to_host_async(res2, 0, o, want_hist=True)
+    assert e.value.status == bf.BF_EINVAL
+    bf.bf_result_destroy(res2)
+    bf.bf_result_destroy(res)
+
+
 def test_zero_blocks_skipped_quadrature_generated_ragged_m(ctx):
     """Skipping with quadrature pairs, a generated bank and M = 2000 (padded to
     2048): short-sweep templates in a generated quadrature bank give, bit for
