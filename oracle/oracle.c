@@ -59,6 +59,10 @@ double oracle_cycles(int track, double f_lo, double f_hi, double D, double t)
 /* instantaneous frequency of the ascending track at local time t */
 double oracle_freq(int track, double f_lo, double f_hi, double D, double t)
 {
+    /* the end of the sweep: f(D) = f_hi by the definition of both tracks.
+     * Evaluated through the formula it lands within an ulp of f_hi, and
+     * where f_hi / df is a whole number the map cell would hang on that ulp. */
+    if (t >= D) return f_hi;
     if (track == O_LINEAR)
         return f_lo + (f_hi - f_lo) * t / D;
     double tc = oracle_powerlaw_tc(f_lo, f_hi, D);

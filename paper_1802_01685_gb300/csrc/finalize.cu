@@ -220,11 +220,14 @@ __device__ __forceinline__ double pow_m3_8(double v)
 }
 
 // Frequency cell of the ascending track at local time u (the map paints f(t)).
-// The fast power-law value is within ~1e-13 of the FP64 pow; where f / df lies
-// that close to a cell edge (the sweep's clamped end, f = f_hi, often does) the
-// cell is decided by the FP64 pow, the same formula the reference evaluates.
+// The end of the sweep (u clamped to D) takes its defined value f(D) = f_hi
+// exactly: through the formula it lands within an ulp of f_hi, and where
+// f_hi / df is a whole number the cell would hang on that ulp.  Elsewhere the
+// fast power-law value is within ~1e-13 of the FP64 pow; where f / df lies
+// that close to a cell edge the cell is decided by the FP64 pow.
 __device__ __forceinline__ int64_t track_cell(const ChirpDev& p, double u, double df)
 {
+    if (u >= p.D) return (int64_t)floor(p.f_hi / df);
     if (p.track == BF_LINEAR) return (int64_t)floor((p.f_lo + (p.f_hi - p.f_lo) * u / p.D) / df);
     const double v = 1.0 - u / p.tc;
     double q = p.f_lo * pow_m3_8(v) / df;

@@ -280,6 +280,11 @@ def test_powerlaw_instantaneous_frequency_follows_minus_three_eighths_law():
     # end points of the track and t_c
     assert abs(oracle.freq(oracle.POWERLAW, f0, f1, D, 0.0) - f0) < 1e-12
     assert abs(oracle.freq(oracle.POWERLAW, f0, f1, D, D) - f1) < 1e-9
+    # the end of the sweep is f_hi exactly, on both tracks (the map's cell edge
+    # at f_hi / df must not depend on the last bit of a pow)
+    for track in (oracle.LINEAR, oracle.POWERLAW):
+        assert oracle.freq(track, 364.7022859372599, 900.0, 0.9033323293453285, 0.9033323293453285) == 900.0
+        assert oracle.freq(track, f0, f1, D, D) == f1
     assert abs(oracle.powerlaw_tc(f0, f1, D) - tc) < 1e-12
 
 
