@@ -183,12 +183,12 @@ def test_random_case_tails_and_map(ctx, seed):
     bf.bf_bank_destroy(bank)
 
 
-def test_random_serving_mix(ctx):
+@pytest.mark.parametrize("seed", seeds(500, 1))
+def test_random_serving_mix(ctx, seed):
     """Thirty random requests (lengths, bank slices, routes, map and tails on or
     off) against a plain and a quadrature bank, all submitted at once: each
     result equals, bit for bit, the same search run alone."""
-    import time
-    rng = np.random.default_rng(500)
+    rng = np.random.default_rng(seed)
     fs = 2048.0
     chirps = []
     for _ in range(300):
