@@ -62,6 +62,8 @@ def test_null_arguments_are_rejected(lib):
     assert lib.bf_control_randomize(None, None, 10, 1, None) == bf.BF_EINVAL
     assert lib.bf_serve_submit(None, None, None) == bf.BF_EINVAL
     assert lib.bf_result_info_get(None, None) == bf.BF_EINVAL
+    assert lib.bf_result_copy_to_host(None, 0, None, None, None, None, None) == bf.BF_EINVAL
+    assert lib.bf_result_copy_to_host_async(None, 0, None, None, None, None, None, None) == bf.BF_EINVAL
     assert "NULL" in bf.bf_last_error() or bf.bf_last_error()
     lib.bf_destroy(None)
     lib.bf_result_destroy(None)
