@@ -5,6 +5,7 @@
  *   - a bank template placed, scaled, into an otherwise zero series gives
  *     normalised correlation 1 at its offset (Cauchy-Schwarz equality);
  *   - the time-randomised control is a permutation of the series;
+ *   - the asynchronous result copy gives what the synchronous one gives;
  *   - a served request gives what bf_correlate gives.
  * Exit status: 0 all checks passed, 1 a check failed, 2 a call failed,
  * 77 no GPU (bf_init failed).  Test infrastructure.
@@ -74,6 +75,18 @@ int main(void)
     if (fabsf(vmax[k_inj] - 1.0f) > 2e-5f || argmax[k_inj] != (int32_t)n0) fail = 1;
     for (size_t k = 0; k < K; ++k)
         if (!(vmax[k] <= 1.0f + 2e-5f) || !(vmax[k] >= 0.0f)) fail = 1;
+
+    /* the asynchronous copy on the legacy default stream; the synchronous copy
+     * after it runs on that stream too and waits for it */
+    float amax[6], asig[6], tmp[6];
+    int32_t aarg[6];
+    CALL(bf_result_copy_to_host_async(res, 0, amax, aarg, asig, NULL, NULL, NULL));
+    CALL(bf_result_copy_to_host(res, 0, tmp, NULL, NULL, NULL, NULL));
+    const int async_same = memcmp(amax, vmax, sizeof vmax) == 0 &&
+                           memcmp(aarg, argmax, sizeof argmax) == 0 &&
+                           memcmp(asig, sigma, sizeof sigma) == 0;
+    printf("asynchronous copy equals the synchronous one: %s\n", async_same ? "yes" : "no");
+    if (!async_same) fail = 1;
 
     /* time-randomised control: a permutation of the series */
     float* y = malloc(N * sizeof(float));
