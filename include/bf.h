@@ -262,6 +262,10 @@ void bf_opts_default(bf_opts* opts);
  * holds, per series, per template: max |rho| (float), its first argmax
  * (int32, smallest lag on ties), sigma; the histogram and map when asked;
  * and over all series the per-template mean of the maxima.
+ * Samples must be finite.  The window energies come from a running sum of
+ * x^2, so one NaN or infinity leaves rho undefined at every later lag of its
+ * series, not only in the windows that hold it; mark gaps with zeros (an
+ * all-zero window gives rho = 0).  Nothing checks this.
  * BF_EINVAL on a bad length, rate, range or a precision whose layout the bank
  * lacks; BF_EDEVICE if a kernel reported an internal timeout.
  */
