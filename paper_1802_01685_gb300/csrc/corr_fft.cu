@@ -42,6 +42,9 @@
 //    entries for the second and third passes and 4096 for the last stage,
 //    rounded from FP64 once per context and copied into shared memory by
 //    every CTA.
+//  * The transform's rounding error scales with its whole segment, so lags
+//    whose window holds almost none of the segment's energy are taken out of
+//    the FFT route (k_fft_flags) and computed directly (k_fft_fixup).
 #include "corr_common.cuh"
 #include "synth.cuh"
 #include "runtime.h"
