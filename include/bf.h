@@ -305,7 +305,8 @@ bf_status bf_result_copy_to_host(const bf_result* r, size_t s, float* vmax,
                                  float* map);
 /* The same copies, enqueued on `stream` (a cudaStream_t; NULL: the legacy
  * default stream) without waiting for them.  They are done when the stream is; until
- * then `r` must not be destroyed and the host arrays must stay allocated.
+ * then `r` must not be destroyed (a plan's result: the plan must not run
+ * again) and the host arrays must stay allocated.
  * Host arrays should be page-locked (cudaHostAlloc or cudaHostRegister), else
  * the copies may run synchronously.  Errors: as bf_result_copy_to_host, for
  * the enqueueing only; a failed copy shows on the stream. */
@@ -399,8 +400,10 @@ void bf_result_destroy(bf_result* r);
  * plan and launches the graph on `stream` (NULL: synchronously on the
  * context stream).  *out points at the plan's result: valid until the next run
  * or bf_plan_destroy, read with the bf_result_* calls, never destroyed by the
- * caller (bf_result_destroy on it does nothing but set bf_last_error).  Stored banks only (BF_ENOTSUP for a generated bank).  Runs of one
- * plan must not overlap on the GPU.
+ * caller (bf_result_destroy on it does nothing but set bf_last_error).
+ * Stored banks only (BF_ENOTSUP for a generated bank).  Runs of one plan must
+ * not overlap on the GPU, nor a run with asynchronous copies of the previous
+ * run's result.
  */
 typedef struct bf_plan bf_plan;
 bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths,
