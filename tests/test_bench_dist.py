@@ -51,3 +51,22 @@ def test_single_rank_needs_no_process_group():
     barrier()
     assert max_over_ranks(3.5) == 3.5
     assert bench.whole_job_value(10.0, 2, 1, 1000.0) == 20.0
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the oracle on a bounded sample of the
+    same workload and reports the same metric and unit, with a cpu_baseline
+    describing the run and an e2e entry that moves no bytes; ranks other than
+    0 do no work."""
+    import argparse
+    args = argparse.Namespace(ref_templates=1, steps=1, warmup=0)
+    assert bench.run_reference(args, 1, 2, 1) is None
+    line = bench.run_reference(args, 0, 1, 0)
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["n_gpus"] == 1
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
+    assert "1 of 65536 templates" in cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
