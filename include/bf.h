@@ -265,9 +265,12 @@ void bf_opts_default(bf_opts* opts);
  * Samples must be finite.  The window energies come from a running sum of
  * x^2, so one NaN or infinity leaves rho undefined at every later lag of its
  * series, not only in the windows that hold it; mark gaps with zeros (an
- * all-zero window gives rho = 0).  Nothing checks this.
- * BF_EINVAL on a bad length, rate, range or a precision whose layout the bank
- * lacks; BF_EDEVICE if a kernel reported an internal timeout.
+ * all-zero window gives rho = 0).  A synchronous call (opts->stream NULL)
+ * checks this after the search and then returns BF_EINVAL with no result;
+ * calls on a stream, plans and served requests do not check.
+ * BF_EINVAL on a bad length, rate, range, a precision whose layout the bank
+ * lacks, or a non-finite sample; BF_EDEVICE if a kernel reported an internal
+ * timeout.
  */
 bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* series,
                        const size_t* lengths, size_t n_series, double fs,

@@ -1284,6 +1284,18 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
         if (e != cudaSuccess) return cuda_fail(e, "correlation");
         st = check_device_status(ctx);
         if (st) return st;
+        // every sample must be finite: the FP64 total of x^2 (the prefix's last
+        // entry; at most 2^32 squares of floats, far below the FP64 range) is
+        // finite exactly then
+        for (size_t s = 0; s < n_series; ++s) {
+            double total = 0.0;
+            e = cudaMemcpy(&total, prep[s].prefix + prep[s].N, sizeof total, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e, "series check");
+            if (!std::isfinite(total)) {
+                set_error("series %zu holds a non-finite sample (NaN or infinity)", s);
+                return BF_EINVAL;
+            }
+        }
         unsigned int cnt = 0;
         cudaMemcpy(&cnt, r->cand_count, sizeof cnt, cudaMemcpyDeviceToHost);
         r->n_candidates = cnt;

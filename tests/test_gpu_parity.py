@@ -606,6 +606,31 @@ def test_copy_into_caller_buffers(ctx, tiny):
     bf.bf_result_destroy(res)
 
 
+@pytest.mark.parametrize("prec", ["split_bf16", "fft_fp32", "fp32"])
+def test_non_finite_samples_are_refused(ctx, tiny, prec):
+    """A NaN or an infinity anywhere in a series makes a synchronous search
+    return BF_EINVAL naming the series (host and device inputs), with no
+    result; the context then runs a finite search as before."""
+    w, bank, _, _ = tiny
+    x, fs = w["series"][0], w["fs"]
+    opts = bf.make_opts(precision=prec)
+    ref = bf.bf_correlate(ctx, bank, [x], fs, opts)
+    want = bf.bf_result_copy_to_host(res=ref, s=0)
+    bf.bf_result_destroy(ref)
+    for bad, at in ((np.nan, 3000), (np.inf, 0), (-np.inf, len(x) - 1)):
+        y = x.copy()
+        y[at] = bad
+        for arg in (y, torch.from_numpy(y).cuda()):
+            with pytest.raises(bf.BFError) as e:
+                bf.bf_correlate(ctx, bank, [x, arg], fs, opts)
+            assert e.value.status == bf.BF_EINVAL and "series 1" in str(e.value), str(e.value)
+    res = bf.bf_correlate(ctx, bank, [x], fs, opts)
+    got = bf.bf_result_copy_to_host(res, 0)
+    bf.bf_result_destroy(res)
+    for key in ("max", "argmax", "sigma", "hist"):
+        np.testing.assert_array_equal(got[key], want[key])
+
+
 def test_async_copy_into_pinned_buffers(ctx, tiny):
     """bf_result_copy_to_host_async gives, once its stream is synchronised,
     what the synchronous copy gives, for every series of a batch, on a caller
