@@ -12,6 +12,56 @@ TOL = {"fp32": 2e-5, "split_bf16": 2e-5, "bf16": 1e-3, "fft_fp32": 2e-5, "split_
 # every stored layout, so that one bank serves every route
 STORE_ALL = bf.BF_BANK_FP32 | bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_SPLIT_FP16
 
+# Bound on the L2 distance of a synthesised FP32 template row from the
+# oracle's FP64 row.  By Cauchy-Schwarz a template off by dh moves rho by at
+# most ||dh||_2 at any window, so this keeps the synthesis within a tenth of
+# the 2e-5 budget on rho (the rows are unit-norm, Sect. 2.1 templates).
+TEMPLATE_L2 = 2e-6
+
+
+def bf16_rn(a):
+    """FP32 values rounded to the nearest bfloat16 (ties to even), as FP32."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return r.astype(np.uint32).view(np.float32)
+
+
+def split_decoded(h32, layout):
+    """hi + lo of the tensor-core operand split of FP32 rows, as the bank read
+    decodes it: BF16 hi = rn(h), lo = rn(h - hi); FP16 the same on 2^8 h."""
+    h32 = np.asarray(h32, np.float32)
+    if layout == "bf16":
+        hi = bf16_rn(h32)
+        return hi + bf16_rn(h32 - hi)
+    hs = h32 * np.float32(256.0)
+    hi = hs.astype(np.float16)
+    lo = (hs - hi.astype(np.float32)).astype(np.float16)
+    return hi.astype(np.float32) / np.float32(256.0) + lo.astype(np.float32) / np.float32(256.0)
+
+
+def check_template_rows(h32, split, ref, label=""):
+    """FP32 rows h32 within TEMPLATE_L2 (L2 norm) of the oracle rows ref;
+    every split layout in `split` ({"bf16": rows, "fp16": rows}, hi + lo as
+    read back) equal to the round-to-nearest split of h32 bit for bit, and
+    within its own representation error (2^-16 relative for BF16 pairs,
+    2^-22 for FP16 pairs) plus TEMPLATE_L2 of ref.  Returns the largest L2
+    distance of the FP32 rows."""
+    h32 = np.atleast_2d(np.asarray(h32, np.float32))
+    ref = np.atleast_2d(np.asarray(ref, np.float64))
+    d = np.sqrt(((h32.astype(np.float64) - ref) ** 2).sum(axis=1))
+    assert d.max() <= TEMPLATE_L2, f"{label} template L2 error {d.max():.3e} > {TEMPLATE_L2}"
+    for layout, rows in split.items():
+        rows = np.atleast_2d(np.asarray(rows, np.float32))
+        want = split_decoded(h32, layout)
+        assert np.array_equal(rows, want), f"{label} {layout} split differs from rn split of the FP32 row"
+        rel = 2.0 ** -16 if layout == "bf16" else 2.0 ** -22
+        rep = np.sqrt(((rows.astype(np.float64) - h32) ** 2).sum(axis=1))
+        n32 = np.sqrt((h32.astype(np.float64) ** 2).sum(axis=1))
+        assert np.all(rep <= rel * n32), f"{label} {layout} split error above {rel:.1e} relative"
+        dd = np.sqrt(((rows.astype(np.float64) - ref) ** 2).sum(axis=1))
+        assert np.all(dd <= rep + TEMPLATE_L2), f"{label} {layout} rows off the oracle"
+    return float(d.max())
+
 
 def oracle_params(spec):
     return oracle.grid(spec["tracks"], spec["senses"], spec["durations"], spec["f_min"],

@@ -8,7 +8,7 @@ import pytest
 import oracle
 from paper_1802_01685_gb300 import bf, synth
 
-from parity import TOL, check_maxima, oracle_params, run, subset
+from parity import TOL, check_maxima, check_template_rows, oracle_params, run, subset
 
 pytestmark = pytest.mark.gpu
 
@@ -43,11 +43,9 @@ def test_generated_read_back_matches_oracle(ctx, banks):
     for k0, n in ((0, 3), (3070, 5), (8190, 2)):
         got = bf.bf_bank_read(gen, k0, n)
         np.testing.assert_array_equal(got, bf.bf_bank_read(stored, k0, n))
-        for i in range(n):
-            k = k0 + i
-            ref = oracle.template(int(p["track"][k]), int(p["sense"][k]), p["f_lo"][k], p["f_hi"][k],
-                                  p["D"][k], 2048.0, 2048)
-            assert np.abs(got[i] - ref).max() < 1e-6
+        ref = np.stack([oracle.template(int(p["track"][k]), int(p["sense"][k]), p["f_lo"][k], p["f_hi"][k],
+                                        p["D"][k], 2048.0, 2048) for k in range(k0, k0 + n)])
+        check_template_rows(got, {}, ref, f"rows {k0}..{k0 + n}")
 
 
 @pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16"])

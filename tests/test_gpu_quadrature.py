@@ -7,7 +7,8 @@ import pytest
 import oracle
 from paper_1802_01685_gb300 import bf, synth
 
-from parity import STORE_ALL, TOL, check_maxima, check_sigma, oracle_params, run, subset
+from parity import (STORE_ALL, TOL, check_maxima, check_sigma, check_template_rows, oracle_params, run,
+                    subset)
 
 pytestmark = pytest.mark.gpu
 
@@ -54,20 +55,22 @@ def case(ctx):
 
 def test_bank_rows_are_the_pairs(ctx, case):
     """Stored and generated quadrature banks hold template and partner as
-    rows 2k, 2k + 1, equal to the oracle's within float rounding."""
+    rows 2k, 2k + 1: the FP32 rows within 2e-6 (L2) of the oracle's pairs,
+    the split layouts the exact splits of those rows, and the generated bank
+    the stored one bit for bit."""
     fs, M, chirps = case["fs"], case["M"], case["chirps"]
     idx = [0, 5, 77, 150, 223]
-    for storage in (bf.BF_BANK_FP32, bf.BF_BANK_SPLIT_BF16, bf.BF_BANK_SPLIT_FP16, bf.BF_BANK_GENERATED):
+    ref = np.stack([oracle.template(*chirps[k], fs, M, ph) for k in idx for ph in (0, 1)])
+    rows = {}
+    for name, storage in (("f32", bf.BF_BANK_FP32), ("bf16", bf.BF_BANK_SPLIT_BF16),
+                          ("fp16", bf.BF_BANK_SPLIT_FP16), ("gen", bf.BF_BANK_GENERATED)):
         bank = bf.bf_bank_create(ctx, chirps, fs, 1.0, storage | bf.BF_BANK_QUADRATURE)
         assert bf.bf_bank_size(bank) == len(chirps) and bf.bf_bank_rows(bank) == 2 * len(chirps)
-        tol = 2e-5 if storage == bf.BF_BANK_SPLIT_BF16 else 1e-6
-        for k in idx:
-            rows = bf.bf_bank_read(bank, k, 1)
-            assert rows.shape == (2, M)
-            for ph in (0, 1):
-                ref = oracle.template(*chirps[k], fs, M, ph)
-                assert np.abs(rows[ph] - ref).max() <= tol, (storage, k, ph)
+        rows[name] = np.concatenate([bf.bf_bank_read(bank, k, 1) for k in idx])
+        assert rows[name].shape == (2 * len(idx), M)
         bf.bf_bank_destroy(bank)
+    np.testing.assert_array_equal(rows["gen"], rows["f32"])
+    check_template_rows(rows["f32"], {"bf16": rows["bf16"], "fp16": rows["fp16"]}, ref)
 
 
 @pytest.mark.parametrize("prec", PRECS)
