@@ -3,7 +3,10 @@ series must give what bf_correlate gives for the same inputs."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1802_01685_gb300 import bf, synth
+
+from parity import TOL, check_hist, check_map, check_maxima, check_sigma, oracle_params, subset
 
 pytestmark = pytest.mark.gpu
 
@@ -30,10 +33,15 @@ def outputs(res, n, want_map):
 
 @pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "fft_fp32", "split_fp16"])
 def test_plan_replays_equal_correlate(setup, prec):
+    """Three replays on new series: each replayed result equals the oracle
+    within the route's tolerance, and bf_correlate on the same inputs bit for
+    bit."""
     ctx, bank, spec = setup
     lens = [2048, 5000, 9000, 2049]
     opts = bf.make_opts(precision=prec, bank_begin=10, bank_end=700, want_map=True, kappa=4.0,
                         want_tails=True)
+    p = subset(oracle_params(spec), np.arange(10, 700))
+    tol = TOL[prec]
     plan = bf.bf_plan_create(ctx, bank, lens, 2048.0, opts)
     try:
         for run in range(3):
@@ -43,6 +51,12 @@ def test_plan_replays_equal_correlate(setup, prec):
             got = outputs(res, len(lens), True)
             got_mean = bf.bf_result_copy_mean_max(res)
             got_tails = np.sort(bf.bf_result_copy_tails(res), order=["series", "k", "tau"])
+            for x, g in zip(xs, got):                # the replay itself against the oracle
+                ref = oracle.search(x, 2048.0, p, 2048, want_rho=True)
+                check_maxima(g, ref, ref["rho"], tol, f"plan {prec} run {run}")
+                check_sigma(g, ref, tol, f"plan {prec}")
+                check_hist(g["hist"], ref["max"], tol)
+                check_map(g["map"], x, 2048.0, p, 2048, 4.0, tol)
             ref_h = bf.bf_correlate(ctx, bank, xs, 2048.0, opts)
             ref = outputs(ref_h, len(lens), True)
             ref_mean = bf.bf_result_copy_mean_max(ref_h)

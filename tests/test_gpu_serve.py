@@ -4,7 +4,10 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 from paper_1802_01685_gb300 import bf, synth
+
+from parity import TOL, check_hist, check_map, check_maxima, check_sigma, oracle_params, subset
 
 pytestmark = pytest.mark.gpu
 
@@ -24,9 +27,13 @@ def served():
                            20.0, 1000.0, 16, 16)                 # 2048 templates
     bank = bf.bf_bank_create_grid(ctx, spec, FS, T,
                                   bf.BF_BANK_FP32 | bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_SPLIT_FP16)
-    yield ctx, bank
+    yield ctx, bank, spec
     bf.bf_bank_destroy(bank)
     bf.bf_destroy(ctx)
+
+
+PREC = {bf.BF_SPLIT_BF16: "split_bf16", bf.BF_BF16: "bf16", bf.BF_FP32: "fp32",
+        bf.BF_FFT_FP32: "fft_fp32", bf.BF_SPLIT_FP16: "split_fp16"}
 
 
 def requests():
@@ -59,7 +66,11 @@ def fetch(res, want_map, parseval=False, tails=False):
 
 
 def test_each_result_is_the_same_alone_and_in_the_mix(served):
-    ctx, bank = served
+    """Twelve requests of every route, bank slice, length and series kind
+    submitted together: each served result equals the oracle within its
+    route's tolerance, and the same search run alone bit for bit."""
+    ctx, bank, spec = served
+    params = oracle_params(spec)
     reqs = requests()
     alone = [fetch(bf.bf_correlate(ctx, bank, [x], FS, o), o.want_map, o.tail_sigma == 1,
                    o.want_tails == 1) for x, o in reqs]
@@ -69,6 +80,17 @@ def test_each_result_is_the_same_alone_and_in_the_mix(served):
         st, res = bf.bf_serve_poll(ctx, t, 60_000_000)
         assert st == bf.BF_OK
         mixed.append(fetch(res, o.want_map, o.tail_sigma == 1, o.want_tails == 1))
+    for (x, o), m in zip(reqs, mixed):
+        # the served result itself against the oracle on the same inputs
+        tol = TOL[PREC[o.precision]]
+        k0, k1 = o.bank_begin, o.bank_end
+        p = subset(params, np.arange(k0, k1))
+        ref = oracle.search(x, FS, p, int(FS), want_rho=True)
+        check_maxima(m, ref, ref["rho"], tol, f"served {PREC[o.precision]} [{k0}, {k1})")
+        check_sigma(m, ref, tol, "served")
+        check_hist(m["hist"], ref["max"], tol)
+        if o.want_map and o.tail_sigma != bf.BF_SIGMA_PARSEVAL:       # maps painted at kappa / sqrt(M)
+            check_map(m["map"], x, FS, p, int(FS), o.kappa, tol)
     for a, m in zip(alone, mixed):
         np.testing.assert_array_equal(m["max"], a["max"])
         np.testing.assert_array_equal(m["argmax"], a["argmax"])
@@ -86,7 +108,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix(served):
 
 
 def test_late_small_request_joins_and_finishes_first(served):
-    ctx, bank = served
+    ctx, bank, _ = served
     rng = np.random.default_rng(5)
     big = synth.white(int(600 * FS), rng).astype(np.float32)     # 10 minutes x 2048 templates, FP32
     small = synth.white(int(2 * FS), rng).astype(np.float32)
@@ -110,7 +132,7 @@ def test_late_small_request_joins_and_finishes_first(served):
 
 
 def test_cancel_and_unknown_ticket(served):
-    ctx, bank = served
+    ctx, bank, _ = served
     x = synth.white(int(200 * FS), np.random.default_rng(1)).astype(np.float32)
     t = bf.bf_serve_submit(ctx, bank, x, FS, bf.make_opts(precision="fp32"))
     bf.bf_serve_cancel(ctx, t)
