@@ -171,6 +171,9 @@ typedef struct {
     size_t I, J;
 } bf_chirp_grid;
 
+/* Context configuration.  The paper has no counterpart: its platform
+ * (Sect. 2.2, twelve GPUs under OpenCL) managed devices in its own runtime;
+ * these are this library's per-GPU resource limits. */
 typedef struct {
     int32_t device;          /* CUDA device ordinal                             */
     size_t hbm_budget;       /* bytes the context may hold; 0 = 90 % of free    */
@@ -188,10 +191,17 @@ typedef struct bf_result bf_result;
 void bf_config_default(bf_config* cfg);
 
 /* Creates a context on cfg->device (cfg may be NULL for defaults).  The
- * context owns a stream, a caching device allocator bounded by hbm_budget and,
- * once serving is used, a scheduler thread.  BF_ENOTSUP if the device is not
- * compute capability 10.3. */
+ * paper has no counterpart: a context is this library's handle on one GPU.
+ * It owns two streams, a caching device allocator bounded by hbm_budget, a
+ * device status word through which kernels report timed-out waits and, once
+ * serving is used, a scheduler thread.  It also does the set-up of
+ * bf_control_randomize_static on its device.  *out receives the context.
+ * BF_EINVAL for a device ordinal out of range; BF_ENOTSUP if the device is not
+ * compute capability 10.3; BF_ECUDA if CUDA fails. */
 bf_status bf_init(const bf_config* cfg, bf_ctx** out);
+/* Waits for the context's work, stops its serving thread (pending requests
+ * are dropped) and frees everything it owns.  Banks, results and plans made
+ * in the context must be destroyed first.  NULL is ignored. */
 void bf_destroy(bf_ctx* ctx);
 
 /*
@@ -206,7 +216,10 @@ bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double f
                          double T, unsigned storage, bf_bank** out);
 bf_status bf_bank_create_grid(bf_ctx* ctx, const bf_chirp_grid* grid, double fs,
                               double T, unsigned storage, bf_bank** out);
+/* Frees the bank's device memory (after the context's pending work on it);
+ * NULL is ignored.  Requests and plans that use the bank must be done. */
 void bf_bank_destroy(bf_bank* bank);
+/* Shape of the bank (Sect. 2.1: a bank of templates of ~1 s); 0 for NULL. */
 size_t bf_bank_size(const bf_bank* bank);           /* K */
 size_t bf_bank_template_len(const bf_bank* bank);   /* M */
 size_t bf_bank_rows(const bf_bank* bank);   /* template rows: K, or 2K with BF_BANK_QUADRATURE */
@@ -253,6 +266,9 @@ typedef struct {
                                 per context.  Ignored by BF_FP32.            */
 } bf_opts;
 
+/* Fills *opts with the defaults: BF_SPLIT_BF16, the whole bank, kappa 5,
+ * 1 ms x 4 Hz map cells, 1024 histogram bins, histogram on, no map, no
+ * tails, synchronous, white-noise sigma, autotuned tiles. */
 void bf_opts_default(bf_opts* opts);
 
 /*
@@ -276,6 +292,9 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
                        const size_t* lengths, size_t n_series, double fs,
                        const bf_opts* opts, bf_result** out);
 
+/* Summary of one search.  correlations counts one template at one lag, the
+ * unit of the paper's throughput figure (Sect. 2.2: correlations per second);
+ * the rest has no counterpart in the paper. */
 typedef struct {
     size_t n_series;
     size_t n_templates;            /* bank_end - bank_begin                     */
@@ -290,19 +309,36 @@ typedef struct {
     int32_t tile_lags;             /* lags per tile of the kernel that ran      */
 } bf_result_info;
 
+/* Copies the summary to *info.  BF_EINVAL for NULL arguments. */
 bf_status bf_result_info_get(const bf_result* r, bf_result_info* info);
-/* Map of series s: nt = ceil(N_s / (fs dt)) time cells (rows) by
- * nf = ceil((fs / 2) / df) frequency cells, row-major; cell (b, c) covers
- * times [b dt, (b+1) dt) and frequencies [c df, (c+1) df). */
+/* Time-frequency map of series s (Sect. 2.1: chirp-based spectrograms that
+ * show trajectories f(t) of finite slope): nt = ceil(N_s / (fs dt)) time
+ * cells (rows) by nf = ceil((fs / 2) / df) frequency cells, row-major; cell
+ * (b, c) covers times [b dt, (b+1) dt) and frequencies [c df, (c+1) df).
+ * BF_EINVAL for a bad series index. */
 bf_status bf_result_map_shape(const bf_result* r, size_t s, size_t* nt, size_t* nf);
-/* Device pointers into the result for series s (valid until destroy). */
+/* Device pointers into the result for series s, valid until the result is
+ * destroyed (a plan's result: until the plan runs again); BF_EINVAL for a bad
+ * index or an output the call did not make.
+ *   get_max:  per template, max |rho| (float), its first argmax (int32) and
+ *             sigma (float) -- the maxima of the butterfly output whose
+ *             distributions Fig. 2 compares for data and control;
+ *   get_hist: histogram of those maxima (hist_bins uint32 counts on [0, 1],
+ *             Fig. 2);
+ *   get_map:  the time-frequency map (bf_result_map_shape);
+ *   get_mean_max: per template, the mean over the call's series of max |rho|
+ *             (Fig. 1: a spectrum averaged over 42 light curves). */
 bf_status bf_result_get_max(const bf_result* r, size_t s, const float** vmax,
                             const int32_t** argmax, const float** sigma);
 bf_status bf_result_get_hist(const bf_result* r, size_t s, const uint32_t** hist);
 bf_status bf_result_get_map(const bf_result* r, size_t s, const float** map);
 bf_status bf_result_get_mean_max(const bf_result* r, const float** mean_max);
-/* Copies series s's outputs to host arrays; NULL arrays are skipped.
- * Sizes: n_templates for vmax/argmax/sigma, hist_bins, map_nt * map_nf. */
+/* Copies series s's outputs (those of bf_result_get_max, _hist and _map) to
+ * host arrays, synchronously; NULL arrays are skipped.  Sizes: n_templates
+ * for vmax/argmax/sigma, hist_bins, map_nt * map_nf.  The paper ships only
+ * reduced output from the GPU (Sect. 2.2); these are this library's reduced
+ * outputs.  BF_EINVAL for a bad index or an array asked for an output the
+ * call did not make. */
 bf_status bf_result_copy_to_host(const bf_result* r, size_t s, float* vmax,
                                  int32_t* argmax, float* sigma, uint32_t* hist,
                                  float* map);
@@ -316,6 +352,8 @@ bf_status bf_result_copy_to_host(const bf_result* r, size_t s, float* vmax,
 bf_status bf_result_copy_to_host_async(const bf_result* r, size_t s, float* vmax,
                                        int32_t* argmax, float* sigma, uint32_t* hist,
                                        float* map, void* stream);
+/* Copies the per-template mean of the maxima (n_templates floats, Fig. 1)
+ * to host memory, synchronously. */
 bf_status bf_result_copy_mean_max(const bf_result* r, float* host_mean_max);
 
 /* Skew-normal fit of the per-template maxima (Sect. 1, Fig. 2: the
@@ -390,10 +428,15 @@ typedef struct {
 } bf_tail;
 bf_status bf_result_tails(const bf_result* r, const bf_tail** tails, size_t* count);
 bf_status bf_result_copy_tails(const bf_result* r, bf_tail* host, size_t cap, size_t* count);
+/* Frees a result; NULL is ignored; a plan's result is refused (it belongs to
+ * the plan; bf_last_error says so). */
 void bf_result_destroy(bf_result* r);
 
 /*
- * Search plans: a fixed search shape replayed as one CUDA graph.
+ * Search plans: a fixed search shape replayed as one CUDA graph.  The paper
+ * has no counterpart; plans serve its workloads of many series searched
+ * against one bank (Sect. 2.1: 42 light curves; Fig. 6: 288 blocks of data),
+ * where per-call set-up would otherwise repeat for every block.
  * bf_plan_create fixes the bank, the template range, the number and lengths of
  * the series, the rate and the options (opts.stream and opts.rho_out are
  * ignored), allocates every buffer once and captures the device work of one
@@ -441,18 +484,26 @@ bf_status bf_control_randomize(bf_ctx* ctx, const float* in, size_t n, uint64_t 
  *            reaches it.
  * Output equals bf_control_randomize(ctx, in, n, seed, out).  The sort scratch
  * is a fixed array in the library's device code (6 MiB, held on every GPU
- * that loads the library until the process exits); it is shared by every
- * call and keeps the last call's contents (nothing in it needs clearing), so
- * calls whose work overlaps on the GPU, e.g. on two streams, race.  The first
- * call on a device looks the array's address up (cudaGetSymbolAddress); make
- * that first call outside any stream capture.
+ * that loads it until the process exits); it is shared by every call and
+ * keeps the last call's contents (nothing in it needs clearing), so calls
+ * whose work overlaps on the GPU, e.g. on two streams, race.
+ * Set-up: CUDA loads a library's device code lazily by default, so the first
+ * call on a device -- or bf_init on that device, which does the same set-up --
+ * loads the array and the permutation kernels into device memory and looks up
+ * the array's device address (cudaGetSymbolAddress).  That first call may
+ * allocate through the CUDA driver: make it (n = 1 is enough), or create a
+ * context on the device, before the point where nothing may be allocated, and
+ * outside any stream capture.  Later calls allocate nothing.  After a
+ * cudaDeviceReset the next call on that device is a first call again.
  */
 #define BF_STATIC_CONTROL_MAX 524288
 bf_status bf_control_randomize_static(const float* in, size_t n, uint64_t seed, float* out,
                                       void* stream);
 
 /*
- * Serving with continuous batching.  submit copies the series and returns a
+ * Serving with continuous batching.  The paper has no counterpart: it runs
+ * one campaign at a time (Sect. 2.2); serving lets searches of different
+ * lengths and bank slices share one GPU.  submit copies the series and returns a
  * ticket without waiting for GPU work; a scheduler thread admits requests
  * while slots and HBM budget allow, and each launch of the batched kernel
  * mixes template tiles of every admitted request, so a request that arrives
@@ -473,8 +524,12 @@ bf_status bf_serve_submit(bf_ctx* ctx, const bf_request* req, uint64_t* ticket);
  * BF_ECANCELED if cancelled; BF_EINVAL for an unknown ticket. */
 bf_status bf_serve_poll(bf_ctx* ctx, uint64_t ticket, int64_t timeout_us,
                         bf_result** out);
+/* Asks for the request to stop; its next poll returns BF_ECANCELED (or its
+ * result, if it finished first).  BF_EINVAL for an unknown ticket. */
 bf_status bf_serve_cancel(bf_ctx* ctx, uint64_t ticket);
 
+/* Counters of the serving loop since the context was made (no counterpart in
+ * the paper). */
 typedef struct {
     uint64_t submitted, completed, cancelled, rejected;
     uint64_t queued, active;
@@ -486,6 +541,8 @@ typedef struct {
 
 bf_status bf_serve_stats_get(bf_ctx* ctx, bf_serve_stats* out);
 
+/* Diagnostics (no counterpart in the paper): the calling thread's last error
+ * message, the text of a status, and BF_ABI_VERSION of the built library. */
 const char* bf_last_error(void);
 const char* bf_status_string(bf_status s);
 int bf_abi_version(void);
@@ -504,6 +561,15 @@ bf_status bf_selftest_wait(bf_ctx* ctx, int signal, uint32_t limit_us, double* w
 /* Number of kernels this library has launched in the process so far (all
  * contexts); a diagnostic for benchmarks.  The paper has no counterpart. */
 uint64_t bf_kernel_launches(void);
+
+/* Measured FMA rates of device `device` (a diagnostic for the rooflines of
+ * the ALU-bound kernels; the paper has no counterpart): FP32 and FP64 FMA
+ * loops of independent chains filling every SM, timed with CUDA events, best
+ * of three launches of about 40 ms each.  Writes TFLOP/s (two flops per FMA)
+ * to the non-NULL outputs.  Allocates a small output buffer and a stream for
+ * the duration of the call and restores the current device.  BF_EINVAL if
+ * both outputs are NULL; BF_ECUDA on a CUDA error. */
+bf_status bf_probe_alu_peaks(int device, double* fp32_tflops, double* fp64_tflops);
 
 #if defined(BF_BUILDING_LIBRARY) && defined(__GNUC__)
 #pragma GCC visibility pop
