@@ -48,7 +48,7 @@ UNIT = "correlations/s"
 # Keyed by (hash of the kernel source the counters were taken on, lags per
 # tile); a changed kernel reports null until it is captured again.
 TRAFFIC_BYTES_PER_TEMPLATE_TILE = {
-    ("4a9ed8bef4bc3dc1", 256): (272.14e6 + 4.31e6) / 128,   # profiles/k_corr_tc_split_bf16_gw_pair_16s_16384.md
+    ("4a9ed8bef4bc3dc1", 256): (272.14e6 + 4.31e6) / 128,   # the 16 s x 16,384-template capture
 }
 
 
@@ -244,11 +244,16 @@ def run_ours(args, rank, world, local):
     ms_per_step = elapsed_ms / args.steps
     value = whole_job_value(corr_per_step, args.steps, world, elapsed_ms)
 
-    # roofline of the dominant kernel (the split-BF16 tcgen05 correlation)
+    # roofline of the dominant kernel (the split-BF16 tcgen05 correlation), on
+    # the method's work: 2M flops per lag-correlation (one length-M inner
+    # product).  The split issues three BF16 MMAs per operand pair, 6M tensor
+    # flops per lag-correlation, reported beside it.
     peaks = measured_peaks()
     k_ms = float(np.mean(kernel_ms))
-    issued_flops = 3 * 2 * M * corr_per_step          # three BF16 MMAs per sample pair
-    achieved = issued_flops / (k_ms / 1e3) / 1e12
+    useful_flops = 2 * M * corr_per_step
+    issued_flops = 3 * useful_flops
+    achieved = useful_flops / (k_ms / 1e3) / 1e12
+    issued = issued_flops / (k_ms / 1e3) / 1e12
     th = kernel_source_hash()
     lt = sorted(shapes)[0] if len(shapes) == 1 else None
     traffic = None
@@ -259,9 +264,18 @@ def run_ours(args, rank, world, local):
                 "frac": round(achieved / peaks["bf16_sustained"], 4), "traffic": traffic,
                 "kernel": f"k_corr_tc<3,{lt}> (split-BF16, {lt} lags per tile, K in 2048-sample chunks)",
                 "kernel_ms": round(k_ms, 2),
-                "peak_source": f"{peaks['source']} bf16_tflops_sustained",
-                "algorithmic_flops_per_launch": issued_flops,
-                "useful_tflops": round(2 * M * corr_per_step / (k_ms / 1e3) / 1e12, 1)}
+                "peak_source": f"{peaks['source']} bf16_tflops_sustained (the kernel runs ~0.8 s "
+                               "inside a step)",
+                "algorithmic_flops_per_launch": useful_flops,
+                "work": "2M flops per lag-correlation, M = 4096; one launch = 4 series x 258049 "
+                        "lags x 65536 templates",
+                "issued_tflops": round(issued, 1),
+                "issued_frac": round(issued / peaks["bf16_sustained"], 4),
+                "issued_note": "split-BF16 issues three BF16 MMAs per operand pair (6M tensor "
+                               "flops per lag-correlation); issued_frac is the tensor pipe's "
+                               "load against the cuBLAS-measured rate"}
+    # measured FP32 / FP64 FMA rates, the peaks of the ALU-bound paths
+    alu = probe_alu(bf)
 
     # end to end through the public API with pinned host buffers
     e2e = run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step)
@@ -269,12 +283,12 @@ def run_ours(args, rank, world, local):
     # plain FP32 SIMT path on the same workload (one step)
     fp32 = None
     if not args.no_fp32:
-        fp32 = run_fp32(ctx, bf, torch, w, xs, ctrl, corr_per_step)
+        fp32 = run_fp32(ctx, bf, torch, w, xs, ctrl, corr_per_step, alu)
 
     # the paper's FFT route on the same step
     fft = None
     if not args.no_fft:
-        fft = run_fft(ctx, bf, w, xs, ctrl, corr_per_step)
+        fft = run_fft(ctx, bf, w, xs, ctrl, corr_per_step, alu)
 
     # the split-FP16 tensor-core route on the same step
     f16 = None
@@ -313,7 +327,7 @@ def run_ours(args, rank, world, local):
                                       "skew-normal fit of maxima",
                                       "coincidence pseudo-spectra (delta f 50 Hz)"]},
         "stage_ms": {k: round(float(np.mean(v)), 2) for k, v in stage_ms.items()},
-        "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "alu_peaks": alu, "e2e": e2e,
         "fp32_path": fp32, "fft_path": fft, "split_fp16_path": f16, "accuracy_vs_oracle": accuracy, "cpu_baseline": cpu, "serve": serve,
         "maxima_fit": fits,
         "coincidence_counts": coincidences,
@@ -432,7 +446,16 @@ def run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step):
     return out
 
 
-def run_fp32(ctx, bf, torch, w, xs, ctrl, corr_per_step):
+def probe_alu(bf) -> dict:
+    """FP32 and FP64 FMA rates measured on this device (bf_probe_alu_peaks)."""
+    import torch
+    f32, f64 = bf.bf_probe_alu_peaks(torch.cuda.current_device())
+    return {"fp32_tflops": round(f32, 2), "fp64_tflops": round(f64, 3),
+            "how": "independent FMA chains filling every SM, best of three ~40 ms launches, "
+                   "CUDA events; two flops per FMA"}
+
+
+def run_fp32(ctx, bf, torch, w, xs, ctrl, corr_per_step, alu):
     fs = w["fs"]
     bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_FP32)
     warm = bf.make_opts(precision="fp32", bank_end=1024, want_map=True)
@@ -445,9 +468,14 @@ def run_fp32(ctx, bf, torch, w, xs, ctrl, corr_per_step):
     info = bf.bf_result_info_get(res)
     bf.bf_result_destroy(res)
     bf.bf_bank_destroy(bank)
+    tflops = 2 * w["M"] * corr_per_step / (info.kernel_ms / 1e3) / 1e12
     return {"value": corr_per_step / wall, "unit": UNIT, "ms_per_step": round(1e3 * wall, 1),
             "kernel_ms": round(info.kernel_ms, 1),
-            "kernel_tflops": round(2 * w["M"] * corr_per_step / (info.kernel_ms / 1e3) / 1e12, 1),
+            "kernel_tflops": round(tflops, 1),
+            "roofline": {"bound": "alu", "achieved": round(tflops, 1), "peak": alu["fp32_tflops"],
+                         "unit": "TFLOP/s", "frac": round(tflops / alu["fp32_tflops"], 4),
+                         "peak_source": "measured FP32 FMA rate (alu_peaks)",
+                         "work": "2M flops per lag-correlation, one FMA per sample pair"},
             "note": "bank synthesis excluded; same series, bank and outputs, FP32 SIMT kernel"}
 
 
@@ -478,7 +506,7 @@ def run_split_fp16(ctx, bf, w, xs, ctrl, corr_per_step, steps=3):
                     "operand pair into FP32, like split-BF16"}
 
 
-def run_fft(ctx, bf, w, xs, ctrl, corr_per_step, steps=3):
+def run_fft(ctx, bf, w, xs, ctrl, corr_per_step, alu, steps=3):
     """The same step through the FFT route (the paper's own route): bank from
     the chirp parameters, template spectra, segment spectra and the fused
     inverse-FFT correlation, with histogram and map."""
@@ -508,6 +536,13 @@ def run_fft(ctx, bf, w, xs, ctrl, corr_per_step, steps=3):
             "kernel_value": corr_per_step / (k_ms / 1e3),
             "transforms": int(n_transforms),
             "fft_tflops_nominal": round(fft_flops / (k_ms / 1e3) / 1e12, 1),
+            "roofline": {"bound": "alu", "achieved": round(fft_flops / (k_ms / 1e3) / 1e12, 1),
+                         "peak": alu["fp32_tflops"], "unit": "TFLOP/s",
+                         "frac": round(fft_flops / (k_ms / 1e3) / 1e12 / alu["fp32_tflops"], 4),
+                         "peak_source": "measured FP32 FMA rate (alu_peaks)",
+                         "work": "5 F log2 F nominal flops per F-point transform",
+                         "note": "on-chip bound: the profile puts shared-memory wavefronts and "
+                                 "issue at about half their peaks each; no DRAM bound"},
             "note": "FP32 FFTs of 8192 points, overlap-save (8193 - M lags per segment), two "
                     "templates per complex transform; ms_per_step includes the template spectra "
                     "(computed from the chirp parameters every step); kernel_ms is the segment "

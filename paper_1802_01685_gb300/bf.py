@@ -159,6 +159,7 @@ def load() -> C.CDLL:
             "bf_abi_version": (i, []),
             "bf_selftest_wait": (i, [p, i, C.c_uint32, P(d)]),
             "bf_kernel_launches": (u64, []),
+            "bf_probe_alu_peaks": (i, [i, P(d), P(d)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -548,3 +549,10 @@ def bf_abi_version() -> int:
 
 def bf_kernel_launches() -> int:
     return int(load().bf_kernel_launches())
+
+
+def bf_probe_alu_peaks(device: int = 0) -> tuple:
+    """Measured FP32 and FP64 FMA rates of the device, TFLOP/s."""
+    f32, f64 = C.c_double(), C.c_double()
+    _check(load().bf_probe_alu_peaks(int(device), C.byref(f32), C.byref(f64)))
+    return f32.value, f64.value

@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbf.so")
 
 SOURCES = ["api.cu", "serve.cu", "bank.cu", "prep.cu", "corr_simt.cu", "corr_tc.cu",
-           "finalize.cu", "permute.cu", "noalloc.cu", "plan.cu", "predict.cu", "corr_fft.cu"]
+           "finalize.cu", "permute.cu", "noalloc.cu", "plan.cu", "predict.cu", "corr_fft.cu", "probe.cu"]
 HEADERS = ["bf_internal.h", "runtime.h", "corr_common.cuh", "synth.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
