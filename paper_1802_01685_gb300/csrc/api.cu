@@ -933,6 +933,15 @@ bf_status bf_init(const bf_config* cfg, bf_ctx** out)
         cudaStreamDestroy(ctx->stream);
         return cuda_fail(e, "status word");
     }
+    // the allocation-free control's set-up on this device, so that a caller
+    // holding a context never has it happen at its first control
+    bf_status st = static_control_setup(c.device);
+    if (st) {
+        cudaFree(ctx->d_err);
+        cudaStreamDestroy(ctx->stream);
+        cudaStreamDestroy(ctx->aux);
+        return st;
+    }
     *out = ctx.release();
     return BF_OK;
 }

@@ -266,6 +266,12 @@ cudaError_t launch_paint(const Candidate* cand, const unsigned int* count,
 size_t permute_scratch_bytes(uint64_t n);
 cudaError_t launch_permute(const float* in, uint64_t n, uint64_t seed, float* out,
                            void* scratch, cudaStream_t s);
+// loads the permutation kernels' code on the current device (permute.cu)
+cudaError_t preload_permute();
+// set-up of the allocation-free control on `device` (noalloc.cu): loads the
+// array of its scratch and the permutation kernels, and caches the array's
+// device address (to *addr, if not NULL); called by bf_init for its device
+bf_status static_control_setup(int device, void** addr = nullptr);
 
 // ---------------------------------------------------------------- host side
 void set_error(const char* fmt, ...);

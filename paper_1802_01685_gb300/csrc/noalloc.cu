@@ -11,13 +11,17 @@
 // permutation kernels with the scratch held in the fixed array below, so it
 // calls no cudaMalloc, cudaFree or other allocating routine.
 //
-// The array is allocated when the library's device code is loaded on a GPU
-// and stays there until the process exits, on every GPU that loads the
-// library: BF_STATIC_CONTROL_MAX samples of scratch, 12 bytes per padded
-// sample (6 MiB).  Every call shares it and finds the previous call's
-// contents; the key kernel rewrites every entry it later reads, so nothing
-// has to start at zero.  Two calls whose work overlaps on the GPU (for
-// example on two streams) race on the array.
+// The array lives in the library's device code.  CUDA loads that code lazily
+// by default, so the array (BF_STATIC_CONTROL_MAX samples of scratch, 12
+// bytes per padded sample: 6 MiB) and the permutation kernels are placed in
+// device memory by a set-up step: the first call on a device, or bf_init on
+// that device, loads them and looks up the array's device address.  That
+// first call may allocate through the driver; every later call allocates
+// nothing.  The array then stays until the process exits, on every GPU that
+// loaded it.  Every call shares it and finds the previous call's contents;
+// the key kernel rewrites every entry it later reads, so nothing has to start
+// at zero.  Two calls whose work overlaps on the GPU (for example on two
+// streams) race on the array.
 #include <mutex>
 
 #include "bf_internal.h"
@@ -32,28 +36,40 @@ constexpr size_t STATIC_SCRATCH_BYTES = STATIC_CONTROL_PAD * (sizeof(uint64_t) +
 
 static __device__ __align__(256) unsigned char g_control_scratch[STATIC_SCRATCH_BYTES];
 
-// Device address of the array, looked up once per device.  In host code the
-// name g_control_scratch is only a host-side stand-in, so kernels must be
-// given this address, never the name.
+// Device address of the array per device.  In host code the name
+// g_control_scratch is only a host-side stand-in, so kernels must be given
+// this address, never the name.
 static void* g_scratch_addr[64];
 static std::mutex g_scratch_mu;
 
-static bf_status scratch_address(int device, void** out)
+}  // namespace bfi
+
+// With `device` current: looks the array's device address up (loading the
+// module that holds it, on the first call) and, the first time that address
+// is seen on the device, loads the permutation kernels too, so that no later
+// call loads code.  The lookup runs on every call -- once the module is
+// loaded it is a host-side table lookup -- so that after a cudaDeviceReset,
+// which unloads the module, the address is taken afresh rather than reused.
+bf_status bfi::static_control_setup(int device, void** addr)
 {
     if (device < 0 || device >= 64) {
         set_error("device ordinal %d out of range", device);
         return BF_EINVAL;
     }
     std::lock_guard<std::mutex> g(g_scratch_mu);
-    if (!g_scratch_addr[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_control_scratch);
-        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress of the control scratch");
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_control_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress of the control scratch");
+    if (p != g_scratch_addr[device]) {
+        e = preload_permute();
+        if (e != cudaSuccess) return cuda_fail(e, "loading the permutation kernels");
         g_scratch_addr[device] = p;
     }
-    *out = g_scratch_addr[device];
+    if (addr) *addr = p;
     return BF_OK;
 }
+
+namespace bfi {
 
 static bool on_device(const void* p, int device)
 {
@@ -90,7 +106,7 @@ extern "C" bf_status bf_control_randomize_static(const float* in, size_t n, uint
     const char* b = reinterpret_cast<const char*>(out);
     if (a < b + n * 4 && b < a + n * 4) { set_error("in and out overlap"); return BF_EINVAL; }
     void* scratch = nullptr;
-    bf_status st = scratch_address(dev, &scratch);
+    bf_status st = static_control_setup(dev, &scratch);
     if (st) return st;
     e = launch_permute(in, n, seed, out, scratch, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? BF_OK : cuda_fail(e, "control randomisation (static scratch)");

@@ -117,6 +117,20 @@ static unsigned grid_for(uint64_t work)
     return (unsigned)(b ? b : 1);
 }
 
+// Loads the code of the permutation kernels on the current device.  Under
+// CUDA's lazy module loading a kernel's module (and the device memory it
+// takes) is otherwise loaded at the kernel's first launch; asking for the
+// kernels' attributes loads it now.
+cudaError_t preload_permute()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_perm_keys);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_bitonic_shared);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_bitonic_global);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_gather);
+    return e;
+}
+
 cudaError_t launch_permute(const float* in, uint64_t n, uint64_t seed, float* out, void* scratch,
                            cudaStream_t s)
 {
