@@ -15,6 +15,7 @@
 // chunk of template pairs per iteration, in a launch of its own (the FFT
 // kernel walks one template range for all the series it is given).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -43,7 +44,9 @@ struct Request {
     RState state = R_QUEUED;
     bf_status status = BF_OK;
     std::string error;
-    bool cancel = false;
+    // set by bf_serve_cancel (under the serving mutex) and by the scheduler on
+    // a failed launch; read by the scheduler without the mutex
+    std::atomic<bool> cancel{false};
     bf_result* result = nullptr;
     PreparedSeries prep;
     uint32_t tt_next = 0, tt_end = 0;   // template-tile cursor
