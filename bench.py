@@ -526,11 +526,11 @@ def run_fft(ctx, bf, w, xs, ctrl, corr_per_step, alu, steps=3):
     step()
     walls, kms = zip(*[step() for _ in range(steps)])
     wall, k_ms = float(np.mean(walls)), float(np.mean(kms))
-    F = 8192
-    V = F - M + 1
+    N = 8192                      # complex points per transform
+    V = 2 * N - M + 1             # lags per transform: one template, 16384-sample segments
     K = synth_grid_size(w)
-    n_transforms = (K + 1) // 2 * sum(-(-(x.numel() - M + 1) // V) for x in xs + ctrl)
-    fft_flops = n_transforms * 5 * F * np.log2(F)
+    n_transforms = K * sum(-(-(x.numel() - M + 1) // V) for x in xs + ctrl)
+    fft_flops = n_transforms * 5 * N * np.log2(N)
     return {"value": corr_per_step / wall, "unit": UNIT, "ms_per_step": round(1e3 * wall, 1),
             "kernel_ms": round(k_ms, 1),
             "kernel_value": corr_per_step / (k_ms / 1e3),
@@ -540,14 +540,15 @@ def run_fft(ctx, bf, w, xs, ctrl, corr_per_step, alu, steps=3):
                          "peak": alu["fp32_tflops"], "unit": "TFLOP/s",
                          "frac": round(fft_flops / (k_ms / 1e3) / 1e12 / alu["fp32_tflops"], 4),
                          "peak_source": "measured FP32 FMA rate (alu_peaks)",
-                         "work": "5 F log2 F nominal flops per F-point transform",
+                         "work": "5 N log2 N nominal flops per N-point complex transform",
                          "note": "on-chip bound: the profile puts shared-memory wavefronts and "
                                  "issue at about half their peaks each; no DRAM bound"},
-            "note": "FP32 FFTs of 8192 points, overlap-save (8193 - M lags per segment), two "
-                    "templates per complex transform; ms_per_step includes the template spectra "
+            "note": "FP32 complex FFTs of 8192 points carrying real segments of 16384 samples "
+                    "(even/odd packing), overlap-save with 16385 - M lags per segment, one "
+                    "template per transform; ms_per_step includes the template spectra "
                     "(computed from the chirp parameters every step); kernel_ms is the segment "
-                    "spectra plus the correlation kernel; fft_tflops_nominal counts 5 F log2 F "
-                    "per transform"}
+                    "spectra plus the correlation kernel; fft_tflops_nominal counts 5 N log2 N "
+                    "per N-point complex transform"}
 
 
 def synth_grid_size(w):

@@ -246,8 +246,10 @@ size_t prepared_series_bytes(size_t N, uint32_t M, uint32_t M_pad, int precision
     size_t b = (ceil_div(L, SIMT_TILE_L) * SIMT_TILE_L + M_pad + 1024) * 4 + L * 4 + prefix_bytes(N) +
                inv_norm_scratch_blocks(N) * 8;
     if (uses_split_rows(precision)) b += 2 * (ceil_div(L, TC_TILE_L) * TC_TILE_L + M_pad + 64) * 16;
-    if (precision == BF_FFT_FP32)                               // segment spectra, fixup list
-        b += (size_t)fft_segments((uint32_t)L, M) * (FFT_POINTS / 2) * 8 + (2 * L + 1) * 4;
+    if (precision == BF_FFT_FP32) {                             // segment spectra (either route), fixup list
+        b += std::max(fft_series_bytes((uint32_t)L, M, true), fft_series_bytes((uint32_t)L, M, false)) +
+             (2 * L + 1) * 4;
+    }
     if (precision == BF_SPLIT_FP16) b += 4096;                  // max |x|
     return b + 8 * 4096;
 }
@@ -728,7 +730,8 @@ bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
                       const std::vector<PreparedSeries>& prep, bf_result* r, cudaStream_t st, FftCall* c)
 {
     const size_t S = prep.size(), K = r->K;
-    const uint32_t V = FFT_POINTS - bank->M + 1;
+    const bool quad = bank->quad;
+    const uint32_t V = fft_lags_per_seg(bank->M, quad);
     const float2* tw = nullptr;
     cudaError_t e = fft_tables(ctx, st, &tw);
     if (e != cudaSuccess) return cuda_fail(e, "FFT tables");
@@ -745,8 +748,8 @@ bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
         r->scratch.push_back(b.n_fix);
         for (int i = 0; i < n; ++i) {
             const size_t s = s0 + i;
-            const uint32_t nseg = fft_segments(prep[s].L, bank->M);
-            float2* spec = static_cast<float2*>(ctx->mem->alloc((size_t)nseg * (FFT_POINTS / 2) * sizeof(float2)));
+            const uint32_t nseg = fft_segments(prep[s].L, bank->M, quad);
+            float2* spec = static_cast<float2*>(ctx->mem->alloc(fft_series_bytes(prep[s].L, bank->M, quad)));
             uint32_t* fix = static_cast<uint32_t*>(ctx->mem->alloc((size_t)prep[s].L * 2 * sizeof(uint32_t)));
             if (spec) r->scratch.push_back(spec);
             if (fix) r->scratch.push_back(fix);
@@ -760,12 +763,13 @@ bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
             b.seg_begin[i] = total;
             b.S[i] = prep[s].prefix;
             b.inv[i] = prep[s].inv;
+            b.inv_seg[i] = fft_seg_norms(spec, nseg, quad);
             b.L[i] = (uint32_t)prep[s].L;
             b.fix[i] = fix;
             total += nseg;
             FftSeries& f = p.ser[i];
             f.spec = spec;
-            f.inv = prep[s].inv;
+            f.inv = b.inv_seg[i];
             f.x = prep[s].x;
             f.fix = fix;
             f.n_fix = b.n_fix + i;
@@ -779,13 +783,18 @@ bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
             f.series_id = (uint32_t)s;
         }
         b.n = n;
+        b.quad = quad ? 1 : 0;
+        b.F = fft_seg_len(quad);
         b.V = V;
+        b.Vp = fft_norm_stride(bank->M, quad);
+        b.scale = fft_inverse_scale(quad);
         b.tw = tw;
         p.tw = tw;
         p.k_begin = (uint32_t)bank_row(bank, o.bank_begin);
         p.k_end = (uint32_t)bank_row(bank, o.bank_end);
         p.quad = bank->quad ? 1 : 0;
         p.V = V;
+        p.Vp = b.Vp;
         p.n_ser = n;
         p.thr = r->thr;
         p.cand_cap = r->cand_cap;

@@ -104,7 +104,10 @@ struct CorrParams {
     Seg seg[MAX_SEG];
 };
 
-// The FFT route (corr_fft.cu): overlap-save over segments of FFT_POINTS samples.
+// The FFT route (corr_fft.cu): complex transforms of FFT_POINTS points;
+// overlap-save over segments of 2 FFT_POINTS samples (real route, plain banks:
+// one template per transform) or FFT_POINTS samples (pair route, quadrature
+// banks: a template and its partner per transform).
 constexpr int FFT_POINTS = 8192;
 constexpr int MAX_FFT_SER = 64;           // series per FFT launch
 // A lag goes to the direct fixup when its window holds less than 1/16384 of
@@ -117,9 +120,11 @@ constexpr double FFT_FIX_RATIO2 = 16384.0;
 struct ChirpDev;
 
 struct FftSeries {
-    const float2* spec;             // [nseg][FFT_POINTS / 2] segment half spectra
-    const float* inv;               // [L] inverse window norms; 0 at the lags
-                                    // left to the direct fixup
+    const float2* spec;             // [nseg][fft_spec_bins] segment half spectra
+    const float* inv;               // inverse window norms times the inverse
+                                    // transform's scale, per segment
+                                    // [nseg][Vp]; 0 at the lags left to the
+                                    // direct fixup
     unsigned long long* vmax;       // packed max per template, index k - k_begin
     double* sumsq;
     float* rho;                     // optional dense output [k - k_begin][tau]
@@ -133,13 +138,14 @@ struct FftSeries {
 };
 
 struct FftParams {
-    const float2* hspec;            // template half spectra [.][FFT_POINTS / 2]; row hrow0 first
+    const float2* hspec;            // template half spectra [.][fft_spec_bins]; row hrow0 first
     const float2* tw;               // twiddle tables (corr_fft.cu)
     uint32_t k_begin, k_end;        // template rows of the call (outputs count from k_begin)
     uint32_t k_lo, k_hi;            // template rows of this launch, within [k_begin, k_end)
     uint32_t hrow0;                 // template row held at hspec[0]
-    int quad;                       // rows (2c, 2c+1) are a quadrature pair
-    uint32_t V;                     // valid lags per segment, FFT_POINTS - M + 1
+    int quad;                       // rows (2c, 2c+1) are a quadrature pair (pair route)
+    uint32_t V;                     // valid lags per segment, fft_lags_per_seg
+    uint32_t Vp;                    // row stride of the per-segment norms
     int n_ser;
     float thr;
     unsigned int cand_cap;
@@ -153,6 +159,8 @@ struct FftParams {
 
 struct FftSeriesBatch {
     int n;
+    int quad;                       // pair route (quadrature bank), else real route
+    uint32_t F;                     // samples per segment, fft_seg_len(quad)
     uint32_t V;
     const float2* tw;
     const float* x[MAX_FFT_SER];
@@ -164,6 +172,9 @@ struct FftSeriesBatch {
     // (2 L words), counted in n_fix[i]
     const double* S[MAX_FFT_SER];
     float* inv[MAX_FFT_SER];
+    float* inv_seg[MAX_FFT_SER];    // per-segment norms [nseg][Vp], times scale
+    uint32_t Vp;
+    float scale;
     uint32_t L[MAX_FFT_SER];
     uint32_t* fix[MAX_FFT_SER];
     uint32_t* n_fix;                // [n] counters, zeroed by launch_fft_series
@@ -244,7 +255,19 @@ struct FinalizeParams {
     FinalizeSeries ser[MAX_FIN];
 };
 cudaError_t launch_finalize(const FinalizeParams& p, uint32_t K, uint32_t nbins, cudaStream_t s);
-uint32_t fft_segments(uint32_t L, uint32_t M);
+uint32_t fft_seg_len(bool quad);            // samples per segment
+uint32_t fft_spec_bins(bool quad);          // complex bins per segment or template spectrum
+uint32_t fft_lags_per_seg(uint32_t M, bool quad);          // V = fft_seg_len - M + 1
+uint32_t fft_norm_stride(uint32_t M, bool quad);           // Vp: V rounded up to a multiple of 4
+float fft_inverse_scale(bool quad);
+// a series' FFT-route scratch: its segment spectra [nseg][fft_spec_bins],
+// then its window norms per segment [nseg][fft_norm_stride] (fft_seg_norms)
+size_t fft_series_bytes(uint32_t L, uint32_t M, bool quad);
+inline float* fft_seg_norms(float2* spec, uint32_t nseg, bool quad)
+{
+    return reinterpret_cast<float*>(spec + (size_t)nseg * fft_spec_bins(quad));
+}
+uint32_t fft_segments(uint32_t L, uint32_t M, bool quad);
 cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, int n_sm, cudaStream_t st);
 cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st);
 // FFT route: template spectra in chunks, for banks whose spectra are not kept (corr_fft.cu)

@@ -1,7 +1,7 @@
 // Correlation by FFT: the paper's own route to the filter output (Sect. 2.2
 // and Fig. 5: the output of every template against data segments through
 // single-precision FFTs on the GPU, with only the tails rho > kappa sigma
-// leaving the device).  Overlap-save with transforms of F = 8192 points:
+// leaving the device).  Overlap-save: with segments of F samples,
 //
 //   segment j of a series covers lags tau0 = j V .. tau0 + V - 1, V = F - M + 1,
 //   X_j = DFT_F(x[tau0 .. tau0 + F))             (zero past the series end)
@@ -14,34 +14,46 @@
 // and reduced exactly like the direct kernels (max |rho| with its first
 // argmax, sum rho^2, tails).
 //
+// Every transform here is a complex FFT of N = 8192 points in one CTA.  Two
+// ways of using it:
+//  * the real route (plain banks): segments of F = 2N = 16384 samples.  The
+//    real input of length F is packed as N complex values (even samples in
+//    the real part, odd in the imaginary) and the half spectra of N + 1 bins
+//    are separated from the complex transform by the usual even/odd split; the
+//    inverse runs the same way backwards: the N complex outputs of one inverse
+//    transform are the correlation at 2N consecutive lags of ONE template.
+//    At M = 4096 that is 12289 useful lags per transform.
+//  * the pair route (quadrature banks): segments of F = N = 8192 samples and
+//    a template with its quadrature partner in one complex transform, output
+//    |c_cos + i c_sin| at the V = 8193 - M lags of the segment.
+//
 // GB300 layout of the work:
-//  * template spectra (two real templates per complex FFT) are half spectra
-//    of 4096 complex values per template, bin 0 carrying the DC and Nyquist
-//    terms (both real).  A stored bank keeps them in HBM, made once; a
-//    generated bank makes them per call, 16,384 rows at a time, in a two-slot
-//    ring on the auxiliary stream;
+//  * template spectra are kept by a stored bank in HBM (made once) and made
+//    per call for a generated bank, chunk by chunk, in a two-slot ring on the
+//    auxiliary stream;
 //  * each segment spectrum is computed once per call; all of them stay in L2
 //    and reach shared memory by asynchronous copies (cp.async) issued one
 //    segment ahead, together with the segment's window norms;
-//  * one CTA of 512 threads owns a pair of templates (a, b) at a time and
-//    holds their spectra in registers (8 bins per thread).  For every segment
-//    it forms Z = X conj(H_a) + i X conj(H_b) over all F bins (Hermitian
-//    symmetry fills the upper half; each thread keeps the half that its
-//    first FFT pass reads in registers), runs one inverse complex FFT in
-//    shared memory and reads c_a = Re z, c_b = Im z -- two real correlations
-//    per transform (or, for a quadrature pair, |z|).  The last radix-2 stage
-//    of the FFT is fused into the epilogue, so the filter output never
-//    reaches HBM.
+//  * one CTA of 512 threads owns a template (real route) or a pair (pair
+//    route) at a time and holds its spectra in registers (16 bins per
+//    thread).  For every segment it forms the product spectrum; the first FFT
+//    pass reads, per thread, 8 bins it formed itself and 8 that the mirror
+//    thread formed (Hermitian symmetry), exchanged through shared memory; it
+//    runs one inverse transform in shared memory and reduces the output in
+//    registers.  The last radix-2 stage of the FFT is fused into the
+//    epilogue, so the filter output never reaches HBM.
 //  * The FFT is a Stockham autosort FFT with three radix-16 passes (each
 //    thread one 16-point DFT per pass, in registers) and a final radix-2
 //    stage; the work array holds complex values with index i stored at
 //    i + i/16, so that every pass moves a warp's 64-bit values in the
 //    minimum two wavefronts, and every thread addresses it at fixed offsets
-//    from one base.  The twiddles of each pass sit in their own table, laid out
-//    [r][k] so that a warp reads consecutive entries: 15 x 16 and 15 x 256
-//    entries for the second and third passes and 4096 for the last stage,
-//    rounded from FP64 once per context and copied into shared memory by
-//    every CTA.
+//    from one base.  Twiddles: the second pass reads a [15][16] table, the
+//    third reads e^{2 pi i r k / 4096} for r = 1, 2, 3, 4, 8, 12 and forms the
+//    others as one product of two; the last stage and the real route's
+//    even/odd split use per-thread constants e^{i pi tid / 4096} and
+//    e^{i pi tid / 8192} (rounded from FP64 once per thread) times exact-
+//    to-rounding roots of unity.  The tables are rounded from FP64 once per
+//    context and copied into shared memory by every CTA.
 //  * The transform's rounding error scales with its whole segment, so lags
 //    whose window holds almost none of the segment's energy are taken out of
 //    the FFT route (k_fft_flags) and computed directly (k_fft_fixup).
@@ -53,28 +65,37 @@ namespace bfi {
 
 namespace {
 
-constexpr int FN = FFT_POINTS;            // 8192
-constexpr int FH = FN / 2;                // 4096 half-spectrum bins (+ Nyquist packed in bin 0)
+constexpr int FN = FFT_POINTS;            // 8192 complex points per transform
+constexpr int FH = FN / 2;                // 4096
+constexpr int FR = 2 * FN;                // 16384 samples per segment of the real route
 constexpr int FT = 512;                   // threads per FFT block
-constexpr int FBINS = FH / FT;            // 8 bins per thread
+constexpr int FBINS = FH / FT;            // 8 bins per thread (and their 8 mirrors)
 constexpr int ZPAD = FN + FN / 16;        // padded complex values of the work array
 constexpr int ROW = FT + FT / 16;         // padded distance of elements 512 apart (544)
 constexpr int UPPER = FH + FH / 16;       // padded distance of elements 4096 apart (4352)
-// twiddle tables e^{+2 pi i n / 8192}: pass 2 [15][16], pass 3 [15][256], last stage [4096]
-constexpr int TW2 = 0, TW3 = 15 * 16, TWF = TW3 + 15 * 256, TW_N = TWF + FH;   // 8176 entries
-constexpr int INV_MAX = FN;               // window norms staged per segment (V <= 8192)
+// twiddle tables e^{+2 pi i n / 8192}: pass 2 [15][16] (r (j mod 16) units of
+// 32), pass 3 [6][256] (r (j mod 256) units of 2 for r = 1, 2, 3, 4, 8, 12)
+constexpr int TW2 = 0, TW3 = 15 * 16, TW_N = TW3 + 6 * 256;     // 1776 entries
+constexpr int INV_PAIR = FN;              // window norms staged per segment (V <= 8192)
+constexpr int INV_REAL = FR;              // real route (V <= 16384)
 // shared memory: work array, twiddles, then (correlation only) the staged
 // segment spectrum and window norms
 constexpr size_t FFT_SMEM = (ZPAD + TW_N) * sizeof(float2);
-constexpr size_t CORR_SMEM = FFT_SMEM + FH * sizeof(float2) + INV_MAX * sizeof(float);
+constexpr size_t CORR_SMEM = FFT_SMEM + FH * sizeof(float2) + INV_PAIR * sizeof(float);
+constexpr size_t RCORR_SMEM = FFT_SMEM + FN * sizeof(float2) + INV_REAL * sizeof(float);
+static_assert(RCORR_SMEM <= 227 * 1024, "real-route correlation fits one SM's shared memory");
 
 __global__ void k_fft_tables(float2* __restrict__ tw)
 {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < TW_N; e += gridDim.x * blockDim.x) {
         int n;                                    // exponent in units of 2 pi / 8192
-        if (e < TW3) n = ((e - TW2) / 16 + 1) * ((e - TW2) % 16) * 32;
-        else if (e < TWF) n = ((e - TW3) / 256 + 1) * ((e - TW3) % 256) * 2;
-        else n = e - TWF;
+        if (e < TW3) {
+            n = ((e - TW2) / 16 + 1) * ((e - TW2) % 16) * 32;
+        } else {
+            const int q = (e - TW3) / 256, k = (e - TW3) % 256;
+            const int r = q < 4 ? q + 1 : 4 * (q - 2);           // 1, 2, 3, 4, 8, 12
+            n = r * k * 2;
+        }
         double sn, cs;
         sincospi((double)n / 4096.0, &sn, &cs);
         tw[e] = make_float2((float)cs, (float)sn);
@@ -82,7 +103,7 @@ __global__ void k_fft_tables(float2* __restrict__ tw)
 }
 
 // Work array z (complex, index i stored at i + i/16), twiddle tables, and the
-// staging buffers of the correlation kernel.
+// staging buffers of the correlation kernels (x: NX spectrum bins).
 struct Smem {
     float2* z;
     const float2* tw;
@@ -90,10 +111,11 @@ struct Smem {
     float* inv;
 };
 
+template <int NX>
 __device__ __forceinline__ Smem smem_setup(const float2* __restrict__ tw_global)
 {
     extern __shared__ __align__(16) float2 fsm[];
-    Smem m{fsm, fsm + ZPAD, fsm + ZPAD + TW_N, reinterpret_cast<float*>(fsm + ZPAD + TW_N + FH)};
+    Smem m{fsm, fsm + ZPAD, fsm + ZPAD + TW_N, reinterpret_cast<float*>(fsm + ZPAD + TW_N + NX)};
     float4* dst = reinterpret_cast<float4*>(fsm + ZPAD);
     const float4* src = reinterpret_cast<const float4*>(tw_global);
     for (int i = threadIdx.x; i < TW_N / 2; i += blockDim.x) dst[i] = __ldg(src + i);
@@ -105,12 +127,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -126,11 +142,35 @@ __device__ __forceinline__ float2 tw_get(const float2* t, int e)
     return make_float2(w.x, SIGN > 0 ? w.y : -w.y);
 }
 
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
 __device__ __forceinline__ void rotate(float& r, float& i, float2 w)
 {
     const float a = r * w.x - i * w.y;
     i = r * w.y + i * w.x;
     r = a;
+}
+
+// e^{i pi a / 16} for a compile-time a in [0, 16): cos(pi a/16) for a <= 8 is
+// C[a], past 8 it is -C[16 - a]; sin(pi a/16) is C[8 - a], past 8 C[a - 8]
+__device__ __forceinline__ float2 root32(int a)
+{
+    const float C[9] = {1.0f, 0.9807852804032304491262f, 0.9238795325112867561282f,
+                        0.8314696123025452370788f, 0.7071067811865475244008f,
+                        0.5555702330196022247428f, 0.3826834323650897717285f,
+                        0.1950903220161282678483f, 0.0f};
+    return a <= 8 ? make_float2(C[a], C[8 - a]) : make_float2(-C[16 - a], C[a - 8]);
+}
+
+// e^{i pi tid / den}, rounded from FP64 (a per-thread constant)
+__device__ __forceinline__ float2 thread_root(double den)
+{
+    double sn, cs;
+    sincospi((double)threadIdx.x / den, &sn, &cs);
+    return make_float2((float)cs, (float)sn);
 }
 
 // 4-point DFT with kernel e^{SIGN 2 pi i n k / 4}, in place
@@ -187,16 +227,37 @@ __device__ __forceinline__ void dft16(float (&r)[16], float (&i)[16])
 // thread j reads in[j + 512 r], twiddles by e^{SIGN 2 pi i r (j mod NS) / (16 NS)},
 // takes the 16-point DFT and writes out[(j / NS) 16 NS + j mod NS + q NS].
 // Padded addresses (i + i/16) are a per-thread base plus constant offsets.
-// The second half of a pass, from the 16 inputs already in registers.
-template <int SIGN, int NS>
+// The second half of a pass, from the 16 inputs already in registers; it
+// ends with a barrier, before which the calling thread's pending cp.async
+// groups but WAIT_CP are waited for (WAIT_CP < 0: no wait).
+template <int SIGN, int NS, int WAIT_CP = -1>
 __device__ __forceinline__ void pass16_from(const Smem& m, float (&vr)[16], float (&vi)[16])
 {
     const int j = threadIdx.x;
-    if (NS > 1) {
-        const int k = j % NS;
-        const float2* t = m.tw + (NS == 16 ? TW2 : TW3) + k;
+    if (NS == 16) {
+        const float2* t = m.tw + TW2 + (j % 16);
 #pragma unroll
-        for (int r = 1; r < 16; ++r) rotate(vr[r], vi[r], tw_get<SIGN>(t, (r - 1) * NS));
+        for (int r = 1; r < 16; ++r) rotate(vr[r], vi[r], tw_get<SIGN>(t, (r - 1) * 16));
+    } else if (NS == 256) {
+        // e^{2 pi i r k / 4096}, k = j mod 256, from r = 1, 2, 3, 4, 8, 12
+        const float2* t = m.tw + TW3 + (j % 256);
+        const float2 w1 = tw_get<SIGN>(t, 0), w2 = tw_get<SIGN>(t, 256), w3 = tw_get<SIGN>(t, 512);
+        const float2 w4 = tw_get<SIGN>(t, 768), w8 = tw_get<SIGN>(t, 1024), w12 = tw_get<SIGN>(t, 1280);
+        rotate(vr[1], vi[1], w1);
+        rotate(vr[2], vi[2], w2);
+        rotate(vr[3], vi[3], w3);
+        rotate(vr[4], vi[4], w4);
+        rotate(vr[5], vi[5], cmul(w4, w1));
+        rotate(vr[6], vi[6], cmul(w4, w2));
+        rotate(vr[7], vi[7], cmul(w4, w3));
+        rotate(vr[8], vi[8], w8);
+        rotate(vr[9], vi[9], cmul(w8, w1));
+        rotate(vr[10], vi[10], cmul(w8, w2));
+        rotate(vr[11], vi[11], cmul(w8, w3));
+        rotate(vr[12], vi[12], w12);
+        rotate(vr[13], vi[13], cmul(w12, w1));
+        rotate(vr[14], vi[14], cmul(w12, w2));
+        rotate(vr[15], vi[15], cmul(w12, w3));
     }
     dft16<SIGN>(vr, vi);
     int wb;                                       // padded address of output q = 0
@@ -209,10 +270,11 @@ __device__ __forceinline__ void pass16_from(const Smem& m, float (&vr)[16], floa
         const int off = NS == 1 ? q : NS == 16 ? 17 * q : 272 * q;
         m.z[wb + off] = make_float2(vr[p], vi[p]);
     }
+    if (WAIT_CP >= 0) cp_async_wait<(WAIT_CP >= 0 ? WAIT_CP : 0)>();
     __syncthreads();
 }
 
-template <int SIGN, int NS>
+template <int SIGN, int NS, int WAIT_CP = -1>
 __device__ __forceinline__ void pass16(const Smem& m)
 {
     const int j = threadIdx.x;
@@ -225,7 +287,7 @@ __device__ __forceinline__ void pass16(const Smem& m)
         vi[r] = v.y;
     }
     __syncthreads();
-    pass16_from<SIGN, NS>(m, vr, vi);
+    pass16_from<SIGN, NS, WAIT_CP>(m, vr, vi);
 }
 
 template <int SIGN>
@@ -236,68 +298,140 @@ __device__ __forceinline__ void fft_passes(const Smem& m)
     pass16<SIGN, 256>(m);
 }
 
-// The final radix-2 stage for output pair (k, k + 4096), k = tid + 512 i.
+// twiddle e^{SIGN i pi k / 4096} of the final radix-2 stage for k = tid + 512 i
+// (base_f = e^{i pi tid / 4096})
 template <int SIGN>
-__device__ __forceinline__ void fft_final(const Smem& m, int i, float2& lo, float2& hi)
+__device__ __forceinline__ float2 final_tw(float2 base_f, int i)
 {
-    const int k = threadIdx.x + FT * i;
+    const float2 w = cmul(base_f, root32(2 * i));
+    return make_float2(w.x, SIGN > 0 ? w.y : -w.y);
+}
+
+// The final radix-2 stage for output pair (k, k + 4096), k = tid + 512 i, with
+// its twiddle w = final_tw<SIGN>(base_f, i).
+__device__ __forceinline__ void fft_final(const Smem& m, int i, float2 w, float2& lo, float2& hi)
+{
     const int a = threadIdx.x + (threadIdx.x >> 4) + ROW * i;
     const float2 v = m.z[a + UPPER];
     float vr = v.x, vi = v.y;
-    rotate(vr, vi, tw_get<SIGN>(m.tw + TWF, k));
+    rotate(vr, vi, w);
     const float2 u = m.z[a];
     lo = make_float2(u.x + vr, u.y + vi);
     hi = make_float2(u.x - vr, u.y - vi);
 }
 
-// Z[F - k] = the upper output of the final stage at 4096 - k, 1 <= k < 4096
-template <int SIGN>
-__device__ __forceinline__ float2 fft_final_mirror(const Smem& m, int k)
+// Z[8192 - k] = the upper output of the final stage at 4096 - k, 1 <= k < 4096,
+// whose twiddle e^{SIGN i pi (4096 - k) / 4096} is -conj(w), w that of k
+__device__ __forceinline__ float2 fft_final_mirror(const Smem& m, int k, float2 w)
 {
     const int kk = FH - k;
     const int a = kk + (kk >> 4);
     const float2 v = m.z[a + UPPER];
     float vr = v.x, vi = v.y;
-    rotate(vr, vi, tw_get<SIGN>(m.tw + TWF, kk));
+    rotate(vr, vi, make_float2(-w.x, w.y));
     const float2 u = m.z[a];
     return make_float2(u.x - vr, u.y - vi);
 }
 
-// Spectra of segments of a batch of series: real input, half spectrum out.
+// Half spectrum of a real signal s of F = 16384 samples from the complex
+// transform U of u[n] = s[2n] + i s[2n+1] (in the work array after
+// fft_passes<-1>): with E = (U[k] + conj U[N-k]) / 2 and
+// O = (U[k] - conj U[N-k]) / 2i the transforms of the even and odd samples,
+//   S[k] = E + e^{-i pi k / N} O,   S[N - k] = conj(E - e^{-i pi k / N} O),
+//   S[N/2] = conj(U[N/2]),  S[0] = E_0 + O_0,  S[N] = E_0 - O_0 (real),
+// written as out[0 .. N) with out[0] = (S[0], S[N]).
+__device__ __forceinline__ void real_spectrum_out(const Smem& m, float2 base_f, float2 base_r,
+                                                  float2* __restrict__ out)
+{
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < FBINS; ++i) {
+        const int k = tid + FT * i;
+        const float2 w = final_tw<-1>(base_f, i);
+        float2 zk, zh;
+        fft_final(m, i, w, zk, zh);                               // U[k], U[k + 4096]
+        if (k == 0) {
+            out[0] = make_float2(zk.x + zk.y, zk.x - zk.y);
+            out[FH] = make_float2(zh.x, -zh.y);
+        } else {
+            const float2 zm = fft_final_mirror(m, k, w);         // U[N - k]
+            const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+            const float2 wr = cmul(base_r, root32(i));            // e^{i pi k / N}
+            const float2 wo = cmul(make_float2(wr.x, -wr.y), o);
+            out[k] = make_float2(e.x + wo.x, e.y + wo.y);
+            out[FN - k] = make_float2(e.x - wo.x, wo.y - e.y);
+        }
+    }
+}
+
+// Spectra of segments of a batch of series.  Pair route (F = 8192): the real
+// segment through one complex transform, half spectrum of 4096 bins with bin
+// 0 = (DC, Nyquist).  Real route (F = 16384): even/odd packed, 8192 bins with
+// bin 0 = (DC, Nyquist).
+template <bool REAL>
 __global__ void __launch_bounds__(FT, 1) k_fft_series(const __grid_constant__ FftSeriesBatch p,
                                                       uint32_t total)
 {
-    const Smem m = smem_setup(p.tw);
+    const Smem m = smem_setup<0>(p.tw);
     const int tid = threadIdx.x;
+    const float2 base_f = thread_root(4096.0);
+    const float2 base_r = thread_root(8192.0);
     for (uint32_t g = blockIdx.x; g < total; g += gridDim.x) {
         int s = 0;
         while (s + 1 < p.n && g >= p.seg_begin[s + 1]) ++s;
         const uint32_t j = g - p.seg_begin[s];
         const float* x = p.x[s];
         const uint64_t N = p.N[s], t0 = (uint64_t)j * p.V;
-        for (int n = tid; n < FN; n += FT) m.z[n + (n >> 4)] = make_float2(t0 + n < N ? x[t0 + n] : 0.f, 0.f);
+        if (REAL) {
+            for (int n = tid; n < FN; n += FT) {
+                const uint64_t a = t0 + 2 * (uint64_t)n;
+                m.z[n + (n >> 4)] = make_float2(a < N ? x[a] : 0.f, a + 1 < N ? x[a + 1] : 0.f);
+            }
+        } else {
+            for (int n = tid; n < FN; n += FT) m.z[n + (n >> 4)] = make_float2(t0 + n < N ? x[t0 + n] : 0.f, 0.f);
+        }
         __syncthreads();
         fft_passes<-1>(m);
-        float2* out = p.spec[s] + (size_t)j * FH;
+        if (REAL) {
+            real_spectrum_out(m, base_f, base_r, p.spec[s] + (size_t)j * FN);
+        } else {
+            float2* out = p.spec[s] + (size_t)j * FH;
 #pragma unroll
-        for (int i = 0; i < FBINS; ++i) {
-            float2 lo, hi;
-            fft_final<-1>(m, i, lo, hi);
-            out[tid + FT * i] = (tid == 0 && i == 0) ? make_float2(lo.x, hi.x) : lo;
+            for (int i = 0; i < FBINS; ++i) {
+                float2 lo, hi;
+                fft_final(m, i, final_tw<-1>(base_f, i), lo, hi);
+                out[tid + FT * i] = (tid == 0 && i == 0) ? make_float2(lo.x, hi.x) : lo;
+            }
         }
         __syncthreads();
     }
 }
 
-// Spectra of templates (2q, 2q + 1) of a chunk of synthesised rows: one
-// complex transform of h_a + i h_b, separated by Hermitian symmetry.
+// Template spectra of a chunk of synthesised rows (rows of 8192 samples, zero
+// past M).  Pair route: rows (2q, 2q + 1) through one complex transform of
+// h_a + i h_b, separated by Hermitian symmetry into two half spectra of 4096
+// bins.  Real route: one row per transform, even/odd packed, zero past 8192
+// samples, 8192 bins.
+template <bool REAL>
 __global__ void __launch_bounds__(FT, 1) k_fft_bank(const float* __restrict__ rows, uint32_t n_rows,
-                                                    uint32_t n_pairs, const float2* __restrict__ tw,
+                                                    uint32_t n_items, const float2* __restrict__ tw,
                                                     float2* __restrict__ spec)
 {
-    const Smem m = smem_setup(tw);
+    const Smem m = smem_setup<0>(tw);
     const int tid = threadIdx.x;
-    for (uint32_t q = blockIdx.x; q < n_pairs; q += gridDim.x) {
+    const float2 base_f = thread_root(4096.0);
+    const float2 base_r = thread_root(8192.0);
+    for (uint32_t q = blockIdx.x; q < n_items; q += gridDim.x) {
+        if (REAL) {
+            const float2* r2 = reinterpret_cast<const float2*>(rows + (size_t)q * FN);
+            for (int n = tid; n < FN; n += FT) m.z[n + (n >> 4)] = n < FH ? r2[n] : make_float2(0.f, 0.f);
+            __syncthreads();
+            fft_passes<-1>(m);
+            real_spectrum_out(m, base_f, base_r, spec + (size_t)q * FN);
+            __syncthreads();
+            continue;
+        }
         const uint32_t a = 2 * q, b = a + 1;
         const float* ra = rows + (size_t)a * FN;
         const float* rb = rows + (size_t)b * FN;
@@ -309,14 +443,15 @@ __global__ void __launch_bounds__(FT, 1) k_fft_bank(const float* __restrict__ ro
 #pragma unroll
         for (int i = 0; i < FBINS; ++i) {
             const int k = tid + FT * i;
+            const float2 w = final_tw<-1>(base_f, i);
             float2 zk, zn;
-            fft_final<-1>(m, i, zk, zn);           // Z[k], Z[k + 4096]
+            fft_final(m, i, w, zk, zn);            // Z[k], Z[k + 4096]
             if (k == 0) {
                 // DC and Nyquist of both real templates: real parts of Z[0], Z[4096]
                 sa[0] = make_float2(zk.x, zn.x);
                 if (b < n_rows) sb[0] = make_float2(zk.y, zn.y);
             } else {
-                const float2 zm = fft_final_mirror<-1>(m, k);      // Z[F - k]
+                const float2 zm = fft_final_mirror(m, k, w);      // Z[F - k]
                 // H_a = (Z[k] + conj Z[F-k]) / 2,  H_b = (Z[k] - conj Z[F-k]) / 2i
                 sa[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
                 if (b < n_rows) sb[k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
@@ -342,71 +477,244 @@ __device__ __forceinline__ void track_max(float a, uint32_t tau, float& best, ui
     }
 }
 
-// segment spectrum j of a series into shared memory (16-byte asynchronous copies)
+// segment spectrum of NX bins into shared memory (16-byte asynchronous copies)
+template <int NX>
 __device__ __forceinline__ void stage_spectrum(const Smem& m, const float2* src)
 {
-    for (int c = threadIdx.x; c < FH / 2; c += FT) cp_async16(m.x + 2 * c, src + 2 * c);
+    for (int c = threadIdx.x; c < NX / 2; c += FT) cp_async16(m.x + 2 * c, src + 2 * c);
 }
 
-// The correlation.  Each CTA walks its items (template pair, series, segment)
-// in order; while the FFT of one segment runs, the spectrum of the next one
-// and the window norms of this one arrive in shared memory.
-// QUAD (a compile-time copy of p.quad, so that each epilogue gets its own
-// register allocation): the pair is a template and its quadrature partner.
-template <bool QUAD>
-__global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftParams p)
+// window norms of a segment (a row of the per-segment copy, which starts
+// 16-byte aligned and has room for whole 16-byte copies) into shared memory
+__device__ __forceinline__ void stage_norms(const Smem& m, const float* src, uint32_t nv)
 {
-    const Smem m = smem_setup(p.tw);
-    const int tid = threadIdx.x, lane = tid & 31;
+    for (uint32_t c = threadIdx.x; 4 * c < nv; c += FT) cp_async16(m.inv + 4 * c, src + 4 * c);
+}
+
+// warp reduction of a packed max key and a sum, then one atomic each per warp
+__device__ __forceinline__ void publish(unsigned long long key, double d, unsigned long long* vmax,
+                                       double* sumsq)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+        key = ok > key ? ok : key;
+        d += __shfl_xor_sync(0xffffffffu, d, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(vmax, key);
+        atomicAdd(sumsq, d);
+    }
+}
+
+// The correlation of the real route (plain banks).  Each CTA walks its items
+// (template row, series, segment) in order; while the FFT of one segment
+// runs, the spectrum of the next one and the window norms of this one arrive
+// in shared memory.
+__global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ FftParams p)
+{
+    const Smem m = smem_setup<FN>(p.tw);
+    const int tid = threadIdx.x;
+    const int rd = tid + (tid >> 4);
+    const int rv = (FN - tid) + ((FN - tid) >> 4);        // padded address of Z[N - tid]
+    const float2 base_f = thread_root(4096.0);
+    const float2 base_r = thread_root(8192.0);
+    const uint32_t n_rows = p.k_hi - p.k_lo;
+    uint32_t row = blockIdx.x;
+    if (row >= n_rows || p.n_ser == 0) return;
+    int s = 0;
+    uint32_t j = 0;
+    stage_spectrum<FN>(m, p.ser[0].spec);
+    cp_async_commit();
+
+    float2 hk[FBINS], hp[FBINS], hm = make_float2(0.f, 0.f);
+    uint32_t k = 0;
+    float thr = 0.f, best = -1.f;
+    uint32_t arg = 0xFFFFFFFFu;
+    // per-thread sum of rho^2 over a series (a few thousand terms of similar
+    // size: FP32 is ample); the sum over threads is FP64
+    float ss = 0.f;
+    bool new_row = true, new_series = true;
+
+    for (;;) {
+        const FftSeries& S = p.ser[s];
+        if (new_row) {
+            k = p.k_lo + row;
+            const float2* H = p.hspec + (size_t)(k - p.hrow0) * FN;
+#pragma unroll
+            for (int i = 0; i < FBINS; ++i) {
+                const int f = tid + FT * i;
+                hk[i] = H[f];
+                hp[i] = H[(FN - f) & (FN - 1)];
+            }
+            if (tid == 0) hm = H[FH];
+        }
+        const uint32_t o = k - p.k_begin;
+        if (new_series) {
+            thr = S.sigma_pred ? S.kappa * S.sigma_pred[o] : p.thr;
+            best = -1.f;
+            arg = 0xFFFFFFFFu;
+            ss = 0.f;
+        }
+        const uint32_t t0 = j * p.V;
+        const uint32_t nv = min(p.V, S.L - t0);
+        stage_norms(m, S.inv + (size_t)j * p.Vp, nv);
+        cp_async_commit();
+        // the item after this one
+        uint32_t np = row, nj = j + 1;
+        int ns = s;
+        if (nj >= S.nseg) {
+            nj = 0;
+            if (++ns >= p.n_ser) {
+                ns = 0;
+                np = row + gridDim.x;
+            }
+        }
+        cp_async_wait<1>();                         // this segment's spectrum
+        __syncthreads();
+        // Y = X conj(H) over all F bins, and the packed spectrum
+        // Z'[f] = A + i w B, Z'[N - f] = conj(A - i w B), with A = Y[f] +
+        // conj Y[N-f], B = Y[f] - conj Y[N-f], w = e^{i pi f / N}: twice the
+        // transform of c[2n] + i c[2n+1].  The first pass of the FFT reads
+        // Z'[tid + 512 r]: for r < 8 this thread's own, kept in registers; for
+        // r >= 8 those of the mirror thread 512 - tid (thread 0: its own
+        // mirrors and the middle bin), exchanged through shared memory.
+        float vr[16], vi[16];
+#pragma unroll
+        for (int r = 0; r < FBINS; ++r) {
+            const int f = tid + FT * r;
+            if (tid == 0 && r == 0) {
+                // DC and Nyquist (real): Z'[0] = (Y0 + YN) + i (Y0 - YN);
+                // middle bin: Z'[N/2] = 2 conj(Y[N/2]) = 2 conj(X) H
+                const float2 x0 = m.x[0];
+                const float y0 = x0.x * hk[0].x, yn = x0.y * hk[0].y;
+                vr[0] = y0 + yn;
+                vi[0] = y0 - yn;
+                const float2 xm = m.x[FH];
+                m.z[UPPER] = make_float2(2.f * (xm.x * hm.x + xm.y * hm.y), 2.f * (xm.x * hm.y - xm.y * hm.x));
+            } else {
+                const float2 xk = m.x[f], xq = m.x[FN - f];
+                const float ykr = xk.x * hk[r].x + xk.y * hk[r].y, yki = xk.y * hk[r].x - xk.x * hk[r].y;
+                const float yqr = xq.x * hp[r].x + xq.y * hp[r].y, yqi = xq.y * hp[r].x - xq.x * hp[r].y;
+                const float ar = ykr + yqr, ai = yki - yqi;
+                const float br = ykr - yqr, bi = yki + yqi;
+                const float2 w = cmul(base_r, root32(r));
+                const float wbr = w.x * br - w.y * bi, wbi = w.x * bi + w.y * br;
+                vr[r] = ar - wbi;
+                vi[r] = ai + wbr;
+                m.z[rv - ROW * r] = make_float2(ar + wbi, wbr - ai);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = FBINS; r < 16; ++r) {
+            const float2 v = m.z[rd + ROW * r];
+            vr[r] = v.x;
+            vi[r] = v.y;
+        }
+        if (np < n_rows) stage_spectrum<FN>(m, p.ser[ns].spec + (size_t)nj * FN);
+        cp_async_commit();
+        __syncthreads();                            // every exchange read before pass 1 writes
+        pass16_from<1, 1>(m, vr, vi);
+        pass16<1, 16>(m);
+        pass16<1, 256, 1>(m);                       // and this segment's window norms
+        float pa = 0.f;
+#pragma unroll 1
+        for (int i0 = 0; i0 < FBINS; i0 += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u;
+            float2 w = final_tw<1>(base_f, u);     // e^{i pi (tid + 512 u) / 4096} ...
+            if (i0) w = make_float2(-w.y, w.x);    // ... times e^{i pi / 2} for i = 4 + u
+            float2 z[2];
+            fft_final(m, i, w, z[0], z[1]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                // z = c[2n] + i c[2n + 1]: two consecutive lags
+                const uint32_t t = 2u * (uint32_t)(tid + FT * i + FH * h);
+                if (t < nv) {
+                    const float2 iv = *reinterpret_cast<const float2*>(m.inv + t);   // t + 1 < INV_REAL
+                    const uint32_t tau = t0 + t;
+                    const float ra = z[h].x * iv.x;    // norms carry 1/F (k_fft_flags)
+                    const float aa = fabsf(ra);
+                    track_max(aa, tau, best, arg);
+                    pa = fmaf(ra, ra, pa);
+                    if (aa >= thr) push_tail(p, S.series_id, k, tau, ra);
+                    if (S.rho) S.rho[(size_t)o * S.L + tau] = ra;
+                    if (t + 1 < nv) {
+                        const float rb = z[h].y * iv.y;
+                        const float ab = fabsf(rb);
+                        track_max(ab, tau + 1, best, arg);
+                        pa = fmaf(rb, rb, pa);
+                        if (ab >= thr) push_tail(p, S.series_id, k, tau + 1, rb);
+                        if (S.rho) S.rho[(size_t)o * S.L + tau + 1] = rb;
+                    }
+                }
+            }
+        }
+        }
+        ss += pa;
+        if (nj == 0)                                // last segment of this series: publish
+            publish(best >= 0.f ? pack_max(best, arg) : 0ull, (double)ss, S.vmax + o, S.sumsq + o);
+        __syncthreads();
+        if (np >= n_rows) break;
+        new_row = np != row;
+        new_series = nj == 0;
+        row = np;
+        s = ns;
+        j = nj;
+    }
+    cp_async_wait<0>();
+}
+
+// The correlation of the pair route (quadrature banks): a template and its
+// quadrature partner in one complex transform, |rho| = |c_cos + i c_sin| /
+// |window|.  Each CTA walks its items (pair, series, segment) in order, with
+// the next segment's spectrum and this segment's norms staged as above.
+__global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__ FftParams p)
+{
+    const Smem m = smem_setup<FH>(p.tw);
+    const int tid = threadIdx.x;
     const int rd = tid + (tid >> 4);
     const int rv = (FN - tid) + ((FN - tid) >> 4);        // padded address of Z[F - tid]
+    const float2 base_f = thread_root(4096.0);
     const uint32_t n_pairs = (p.k_hi - p.k_lo + 1) / 2;
-    const float scale = 1.f / (float)FN;
     uint32_t pair = blockIdx.x;
     if (pair >= n_pairs || p.n_ser == 0) return;
     int s = 0;
     uint32_t j = 0;
-    stage_spectrum(m, p.ser[0].spec);
+    stage_spectrum<FH>(m, p.ser[0].spec);
     cp_async_commit();
 
     float2 ha[FBINS], hb[FBINS];
-    uint32_t ka = 0, kb = 0;
-    bool has_b = false;
-    float thr_a = 0.f, thr_b = 0.f;
-    float best_a = -1.f, best_b = -1.f;
-    uint32_t arg_a = 0xFFFFFFFFu, arg_b = 0xFFFFFFFFu;
-    // per-thread sums of rho^2 over a series (a few thousand terms of similar
-    // size: FP32 is ample); the sums over threads are FP64
-    float ss_a = 0.f, ss_b = 0.f;
+    uint32_t ka = 0;
+    float thr = 0.f, best = -1.f;
+    uint32_t arg = 0xFFFFFFFFu;
+    float ss = 0.f;
     bool new_pair = true, new_series = true;
 
     for (;;) {
         const FftSeries& S = p.ser[s];
         if (new_pair) {
             ka = p.k_lo + 2 * pair;
-            kb = ka + 1;
-            has_b = kb < p.k_hi;
 #pragma unroll
             for (int i = 0; i < FBINS; ++i) {
                 const int f = tid + FT * i;
                 ha[i] = p.hspec[(size_t)(ka - p.hrow0) * FH + f];
-                hb[i] = has_b ? p.hspec[(size_t)(kb - p.hrow0) * FH + f] : make_float2(0.f, 0.f);
+                hb[i] = p.hspec[(size_t)(ka + 1 - p.hrow0) * FH + f];
             }
         }
-        // output indices: one per row, or one per quadrature pair (rows ka, kb)
-        const uint32_t la = QUAD ? (ka - p.k_begin) >> 1 : ka - p.k_begin, lb = kb - p.k_begin;
+        const uint32_t la = (ka - p.k_begin) >> 1;           // output index of the pair
         if (new_series) {
-            thr_a = S.sigma_pred ? S.kappa * S.sigma_pred[la] : p.thr;
-            thr_b = (!has_b || QUAD) ? INFINITY : (S.sigma_pred ? S.kappa * S.sigma_pred[lb] : p.thr);
-            best_a = best_b = -1.f;
-            arg_a = arg_b = 0xFFFFFFFFu;
-            ss_a = ss_b = 0.f;
+            thr = S.sigma_pred ? S.kappa * S.sigma_pred[la] : p.thr;
+            best = -1.f;
+            arg = 0xFFFFFFFFu;
+            ss = 0.f;
         }
         const uint32_t t0 = j * p.V;
         const uint32_t nv = min(p.V, S.L - t0);
-        for (uint32_t e = tid; e < nv; e += FT) cp_async4(m.inv + e, S.inv + t0 + e);
+        stage_norms(m, S.inv + (size_t)j * p.Vp, nv);
         cp_async_commit();
-        // the item after this one
         uint32_t np = pair, nj = j + 1;
         int ns = s;
         if (nj >= S.nseg) {
@@ -418,11 +726,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
         }
         cp_async_wait<1>();                         // this segment's spectrum
         __syncthreads();
-        // Z = X conj(H_a) + i X conj(H_b).  The first pass of the FFT reads
-        // Z[tid + 512 r]: for r < 8 those are this thread's own bins, kept in
-        // registers; for r >= 8 they are Z[F - f] of the mirror thread 512 - tid
-        // (thread 0: its own bins and the Nyquist term), exchanged through
-        // shared memory.
+        // Z = X conj(H_a) + i X conj(H_b); Z[F - f] = conj(Ya) + i conj(Yb)
         float vr[16], vi[16];
 #pragma unroll
         for (int i = 0; i < FBINS; ++i) {
@@ -433,7 +737,6 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
                 vi[0] = x.x * hb[0].x;
                 m.z[UPPER] = make_float2(x.y * ha[0].y, x.y * hb[0].y);
             } else {
-                // Y = X conj(H); Z[f] = Ya + i Yb, Z[F - f] = conj(Ya) + i conj(Yb)
                 const float yar = x.x * ha[i].x + x.y * ha[i].y;
                 const float yai = x.y * ha[i].x - x.x * ha[i].y;
                 const float ybr = x.x * hb[i].x + x.y * hb[i].y;
@@ -450,75 +753,39 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
             vr[r] = v.x;
             vi[r] = v.y;
         }
-        if (np < n_pairs) stage_spectrum(m, p.ser[ns].spec + (size_t)nj * FH);
+        if (np < n_pairs) stage_spectrum<FH>(m, p.ser[ns].spec + (size_t)nj * FH);
         cp_async_commit();
         __syncthreads();                            // every exchange read before pass 1 writes
         pass16_from<1, 1>(m, vr, vi);
         pass16<1, 16>(m);
-        pass16<1, 256>(m);
-        cp_async_wait<1>();                         // this segment's window norms
-        __syncthreads();
-        float pa = 0.f, pb = 0.f;
-#pragma unroll 4          // a full unroll pushes the non-quadrature copy past 128 registers
-        for (int i = 0; i < FBINS; ++i) {
+        pass16<1, 256, 1>(m);                       // and this segment's window norms
+        float pa = 0.f;
+#pragma unroll 1
+        for (int i0 = 0; i0 < FBINS; i0 += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u;
+            float2 w = final_tw<1>(base_f, u);
+            if (i0) w = make_float2(-w.y, w.x);
             float2 z[2];
-            fft_final<1>(m, i, z[0], z[1]);
+            fft_final(m, i, w, z[0], z[1]);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t t = (uint32_t)(tid + FT * i + FH * h);
-                if (QUAD && t < nv) {
-                    // quadrature pair: |c_cos + i c_sin| / |window|
+                if (t < nv) {
                     const uint32_t tau = t0 + t;
-                    const float r = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * (m.inv[t] * scale);
-                    track_max(r, tau, best_a, arg_a);
+                    const float r = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * m.inv[t];   // norms carry 1/F
+                    track_max(r, tau, best, arg);
                     pa = fmaf(r, r, pa);
-                    if (r >= thr_a) push_tail(p, S.series_id, ka >> 1, tau, r);
+                    if (r >= thr) push_tail(p, S.series_id, ka >> 1, tau, r);
                     if (S.rho) S.rho[(size_t)la * S.L + tau] = r;
-                } else if (!QUAD && t < nv) {
-                    const uint32_t tau = t0 + t;
-                    const float inv = m.inv[t] * scale;
-                    const float ra = z[h].x * inv, rb = z[h].y * inv;
-                    const float aa = fabsf(ra), ab = fabsf(rb);
-                    track_max(aa, tau, best_a, arg_a);
-                    track_max(ab, tau, best_b, arg_b);
-                    pa = fmaf(ra, ra, pa);
-                    pb = fmaf(rb, rb, pb);
-                    if (aa >= thr_a || ab >= thr_b) {
-                        if (aa >= thr_a) push_tail(p, S.series_id, ka, tau, ra);
-                        if (ab >= thr_b) push_tail(p, S.series_id, kb, tau, rb);
-                    }
-                    if (S.rho) {
-                        S.rho[(size_t)la * S.L + tau] = ra;
-                        if (has_b) S.rho[(size_t)lb * S.L + tau] = rb;
-                    }
                 }
             }
         }
-        ss_a += pa;
-        ss_b += pb;
-        if (nj == 0) {
-            // last segment of this series: reduce and publish
-            unsigned long long key_a = best_a >= 0.f ? pack_max(best_a, arg_a) : 0ull;
-            unsigned long long key_b = best_b >= 0.f ? pack_max(best_b, arg_b) : 0ull;
-            double da = (double)ss_a, db = (double)ss_b;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long oa = __shfl_xor_sync(0xffffffffu, key_a, o);
-                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, key_b, o);
-                key_a = oa > key_a ? oa : key_a;
-                key_b = ob > key_b ? ob : key_b;
-                da += __shfl_xor_sync(0xffffffffu, da, o);
-                db += __shfl_xor_sync(0xffffffffu, db, o);
-            }
-            if (lane == 0) {
-                atomicMax(S.vmax + la, key_a);
-                atomicAdd(S.sumsq + la, da);
-                if (has_b && !QUAD) {
-                    atomicMax(S.vmax + lb, key_b);
-                    atomicAdd(S.sumsq + lb, db);
-                }
-            }
         }
+        ss += pa;
+        if (nj == 0)
+            publish(best >= 0.f ? pack_max(best, arg) : 0ull, (double)ss, S.vmax + la, S.sumsq + la);
         __syncthreads();
         if (np >= n_pairs) break;
         new_pair = np != pair;
@@ -537,6 +804,10 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft(const __grid_constant__ FftP
 // gives them rho = 0 (no tail, nothing to the sum of squares, never above the
 // true maximum), and they are listed, with the norm, for k_fft_fixup.  The
 // energies come from the FP64 prefix of x^2.  One grid row per series.
+// Every norm is also written, times the inverse transform's scale (a power of
+// two, so exactly), to the per-segment copy the correlation kernel stages:
+// segment j's lags at inv_seg[j Vp ..), Vp = V rounded up to a multiple of 4,
+// so every segment starts 16-byte aligned.
 __global__ void __launch_bounds__(256) k_fft_flags(const __grid_constant__ FftSeriesBatch b)
 {
     const int i = blockIdx.y;
@@ -553,12 +824,14 @@ __global__ void __launch_bounds__(256) k_fft_flags(const __grid_constant__ FftSe
         float iv = 0.f;
         if (t < L) {
             iv = inv[t];
+            const uint64_t j = t / b.V;                 // the segment
+            const uint64_t a = j * b.V;                 // its first sample
             if (iv > 0.f) {                             // empty window: rho = 0 exactly
-                const uint64_t a = t / b.V * b.V;       // the segment's first sample
-                const uint64_t e = min(a + (uint64_t)FN, N);
+                const uint64_t e = min(a + (uint64_t)b.F, N);
                 const double E = S[e] - S[a];
                 flag = E * (double)iv * (double)iv > FFT_FIX_RATIO2;
             }
+            b.inv_seg[i][j * b.Vp + (t - a)] = flag ? 0.f : iv * b.scale;
         }
         const uint32_t mask = __ballot_sync(0xffffffffu, flag);
         if (mask == 0u) continue;
@@ -704,13 +977,17 @@ cudaError_t fft_attributes()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_corr_fft<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CORR_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_corr_rfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RCORR_SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_corr_fft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CORR_SMEM);
+        e = cudaFuncSetAttribute(k_corr_fft_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CORR_SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fft_series, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+        e = cudaFuncSetAttribute(k_fft_series<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fft_bank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+        e = cudaFuncSetAttribute(k_fft_series<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_bank<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_bank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fft_fixup<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FIX_SMEM);
     if (e == cudaSuccess)
@@ -742,33 +1019,38 @@ cudaError_t fft_tables(bf_ctx* ctx, cudaStream_t st, const float2** out)
     return fft_attributes();
 }
 
-// Half spectra of template rows [row0, row0 + nrows) into out[0 ..] (nrows
-// rounded up to even; an odd tail pairs with a zero row whose spectrum is not
-// written), through `scratch`, room for `scratch_rows` synthesised rows of F
-// samples.  Asynchronous on st.
+uint32_t fft_seg_len(bool quad) { return quad ? FN : FR; }
+uint32_t fft_spec_bins(bool quad) { return quad ? FH : FN; }
+
+// Spectra of template rows [row0, row0 + nrows) into out[0 ..] (fft_spec_bins
+// complex values per row), through `scratch`, room for `scratch_rows`
+// synthesised rows of 8192 samples.  The pair route rounds nrows up to even:
+// an odd tail pairs with a zero row whose spectrum is not written.
+// Asynchronous on st.
 static cudaError_t template_spectra(const bf_bank* bank, size_t row0, size_t nrows, float* scratch,
                                     size_t scratch_rows, const float2* tw, float2* out, int n_sm,
                                     cudaStream_t st)
 {
+    const size_t bins = fft_spec_bins(bank->quad);
     cudaError_t e = cudaSuccess;
     for (size_t k = 0; k < nrows && e == cudaSuccess; k += scratch_rows) {
         const size_t kc = std::min(scratch_rows, nrows - k);     // rows of this sub-chunk
-        const size_t nr = kc + (kc & 1);                          // scratch_rows is even
+        const size_t nr = bank->quad ? kc + (kc & 1) : kc;        // scratch_rows is even
         e = launch_bank_synth(bank->d_params, (uint32_t)(row0 + k), bank->quad, (uint32_t)kc, (uint32_t)nr,
                               bank->M, FN, bank->fs, scratch, nullptr, nullptr, st);
-        if (e == cudaSuccess) {
-            const uint32_t pairs = (uint32_t)(nr / 2);
-            count_launches(1);
-            k_fft_bank<<<std::min<uint32_t>(pairs, (uint32_t)n_sm), FT, FFT_SMEM, st>>>(
-                scratch, (uint32_t)kc, pairs, tw, out + k * FH);
-            e = cudaGetLastError();
-        }
+        if (e != cudaSuccess) break;
+        const uint32_t items = (uint32_t)(bank->quad ? nr / 2 : nr);
+        const unsigned grid = std::min<uint32_t>(items, (uint32_t)n_sm);
+        count_launches(1);
+        if (bank->quad) k_fft_bank<false><<<grid, FT, FFT_SMEM, st>>>(scratch, (uint32_t)kc, items, tw, out + k * bins);
+        else k_fft_bank<true><<<grid, FT, FFT_SMEM, st>>>(scratch, (uint32_t)kc, items, tw, out + k * bins);
+        e = cudaGetLastError();
     }
     return e;
 }
 
-// Half spectra of every template of the bank, [K rounded up to even][4096]
-// complex, computed once and kept with the bank.
+// Spectra of every template of the bank, [rows (rounded up to even for the
+// pair route)][fft_spec_bins] complex, computed once and kept with the bank.
 bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
 {
     if (bank->fspec) return BF_OK;
@@ -780,15 +1062,16 @@ bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
     const float2* tw = nullptr;
     cudaError_t e = fft_tables(ctx, st, &tw);
     if (e != cudaSuccess) return cuda_fail(e, "FFT tables");
-    const size_t K2 = bank->rows + (bank->rows & 1);
+    const size_t K2 = bank->quad ? bank->rows + (bank->rows & 1) : bank->rows;
+    const size_t bins = fft_spec_bins(bank->quad);
     Allocator& mem = *ctx->mem;
-    float2* spec = static_cast<float2*>(mem.alloc(K2 * FH * sizeof(float2)));
-    const size_t chunk = std::min<size_t>(4096, K2);
+    float2* spec = static_cast<float2*>(mem.alloc(K2 * bins * sizeof(float2)));
+    const size_t chunk = std::min<size_t>(4096, K2 + (K2 & 1));
     float* rows = static_cast<float*>(mem.alloc(chunk * FN * sizeof(float)));
     if (!spec || !rows) {
         mem.release(spec);
         mem.release(rows);
-        set_error("out of device memory for the template spectra (%zu MB)", (K2 * FH * 8) >> 20);
+        set_error("out of device memory for the template spectra (%zu MB)", (K2 * bins * 8) >> 20);
         return BF_ENOMEM;
     }
     e = template_spectra(bank, 0, bank->rows, rows, chunk, tw, spec, ctx->n_sm, st);
@@ -802,17 +1085,31 @@ bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
     return BF_OK;
 }
 
-uint32_t fft_segments(uint32_t L, uint32_t M)
+uint32_t fft_lags_per_seg(uint32_t M, bool quad) { return fft_seg_len(quad) - M + 1; }
+uint32_t fft_norm_stride(uint32_t M, bool quad) { return (fft_lags_per_seg(M, quad) + 3) & ~3u; }
+// 1/F for the real route: the inverse transform is unnormalised and the
+// even/odd split forms twice the packed spectrum; 1/N for the pair route
+float fft_inverse_scale(bool quad) { return 1.f / (float)fft_seg_len(quad); }
+
+size_t fft_series_bytes(uint32_t L, uint32_t M, bool quad)
 {
-    const uint64_t V = FFT_POINTS - M + 1;
+    const size_t nseg = fft_segments(L, M, quad);
+    return nseg * fft_spec_bins(quad) * sizeof(float2) + nseg * fft_norm_stride(M, quad) * sizeof(float);
+}
+
+uint32_t fft_segments(uint32_t L, uint32_t M, bool quad)
+{
+    const uint64_t V = fft_lags_per_seg(M, quad);
     return (uint32_t)(((uint64_t)L + V - 1) / V);          // L may be close to 2^32
 }
 
 cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, int n_sm, cudaStream_t st)
 {
     if (total_segments == 0) return cudaSuccess;
+    const unsigned grid = std::min<uint32_t>(total_segments, (uint32_t)n_sm);
     count_launches(1);
-    k_fft_series<<<std::min<uint32_t>(total_segments, (uint32_t)n_sm), FT, FFT_SMEM, st>>>(b, total_segments);
+    if (b.quad) k_fft_series<false><<<grid, FT, FFT_SMEM, st>>>(b, total_segments);
+    else k_fft_series<true><<<grid, FT, FFT_SMEM, st>>>(b, total_segments);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !b.n_fix) return e;
     // the lags for the direct fixup
@@ -828,12 +1125,12 @@ cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, 
 
 cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st)
 {
-    const uint32_t n_pairs = (p.k_hi - p.k_lo + 1) / 2;
-    if (n_pairs == 0 || p.n_ser == 0) return cudaSuccess;
-    const unsigned grid = std::min<unsigned>(n_pairs, (unsigned)n_sm);
+    const uint32_t items = p.quad ? (p.k_hi - p.k_lo + 1) / 2 : p.k_hi - p.k_lo;
+    if (items == 0 || p.n_ser == 0) return cudaSuccess;
+    const unsigned grid = std::min<unsigned>(items, (unsigned)n_sm);
     count_launches(1);
-    if (p.quad) k_corr_fft<true><<<grid, FT, CORR_SMEM, st>>>(p);
-    else k_corr_fft<false><<<grid, FT, CORR_SMEM, st>>>(p);
+    if (p.quad) k_corr_fft_quad<<<grid, FT, CORR_SMEM, st>>>(p);
+    else k_corr_rfft<<<grid, FT, RCORR_SMEM, st>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !p.chirps) return e;
     // the lags left to the direct computation (none: the CTAs return at once)
@@ -848,28 +1145,30 @@ cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st)
 }
 
 // A bank that keeps only its chirp parameters: the template spectra are made
-// chunk by chunk (FFT_CHUNK_ROWS rows, 512 MiB of spectra) into a two-slot
-// ring on the auxiliary stream, and chunk c is correlated against every
-// series batch on the main stream while chunk c+1 is made.  Events order the
-// reuse of a slot after the launches that read it.
-constexpr size_t FFT_CHUNK_ROWS = 16384;
+// chunk by chunk (512 MiB of spectra: 8192 rows of the real route, 16384 of
+// the pair route) into a two-slot ring on the auxiliary stream, and chunk c is
+// correlated against every series batch on the main stream while chunk c+1 is
+// made.  Events order the reuse of a slot after the launches that read it.
+constexpr size_t FFT_CHUNK_BYTES = size_t(512) << 20;
 constexpr size_t FFT_SYNTH_ROWS = 4096;
 
 cudaError_t fft_correlate_chunked(bf_ctx* ctx, const bf_bank* bank, std::vector<FftParams>& batches,
                                   uint32_t row_begin, uint32_t row_end, std::vector<void*>& keep,
                                   cudaStream_t st)
 {
+    const bool quad = bank->quad;
+    const size_t bins = fft_spec_bins(quad);
     const size_t n_rows = row_end - row_begin;
-    const size_t chunk = std::min(FFT_CHUNK_ROWS, n_rows + (n_rows & 1));
+    const size_t chunk = std::min(FFT_CHUNK_BYTES / (bins * sizeof(float2)), n_rows + (n_rows & 1));
     const size_t n_chunks = (n_rows + chunk - 1) / chunk;
     Allocator& mem = *ctx->mem;
     float2* slot[2] = {nullptr, nullptr};
     // the ring outlives this call's launches: the result releases it
-    const size_t synth_rows = std::min(FFT_SYNTH_ROWS, chunk);           // both even
+    const size_t synth_rows = std::min(FFT_SYNTH_ROWS, chunk + (chunk & 1));   // even
     float* scratch = static_cast<float*>(mem.alloc(synth_rows * FN * sizeof(float)));
     keep.push_back(scratch);
     for (int i = 0; i < 2 && i < (int)n_chunks; ++i) {
-        slot[i] = static_cast<float2*>(mem.alloc((chunk + 2) * FH * sizeof(float2)));
+        slot[i] = static_cast<float2*>(mem.alloc((chunk + 2) * bins * sizeof(float2)));
         keep.push_back(slot[i]);
     }
     if (!scratch || !slot[0] || (n_chunks > 1 && !slot[1])) {
@@ -889,11 +1188,12 @@ cudaError_t fft_correlate_chunked(bf_ctx* ctx, const bf_bank* bank, std::vector<
         const int sl = (int)(c & 1);
         const uint32_t c0 = row_begin + (uint32_t)(c * chunk);
         const uint32_t c1 = (uint32_t)std::min<size_t>(c0 + chunk, row_end);
-        // the spectra are made for the even-aligned row pairs that a stored bank
-        // uses, partner rows outside the slice included: each spectrum carries
-        // its partner's rounding, so the outputs equal the stored bank's
-        const uint32_t s0 = c0 & ~1u;
-        const uint32_t s1 = (uint32_t)std::min<size_t>((c1 + 1) & ~1u, bank->rows);
+        // the pair route makes the spectra of the even-aligned row pairs that a
+        // stored bank uses, partner rows outside the slice included (each
+        // spectrum carries its partner's rounding), so the outputs equal the
+        // stored bank's; the real route makes one row per transform
+        const uint32_t s0 = quad ? c0 & ~1u : c0;
+        const uint32_t s1 = quad ? (uint32_t)std::min<size_t>((c1 + 1) & ~1u, bank->rows) : c1;
         if (c >= 2) e = cudaStreamWaitEvent(ctx->aux, used[sl], 0);
         if (e == cudaSuccess)
             e = template_spectra(bank, s0, s1 - s0, scratch, synth_rows, tw, slot[sl], ctx->n_sm, ctx->aux);

@@ -148,9 +148,10 @@ static bool admit(ServeState* S, Request* r)
         cudaError_t e = fft_tables(ctx, S->stream, &tw);
         st = e == cudaSuccess ? bank_fft_spectra(ctx, const_cast<bf_bank*>(bank), S->stream)
                               : cuda_fail(e, "FFT tables");
-        const uint32_t nseg = fft_segments(r->prep.L, bank->M);
+        const bool quad = bank->quad;
+        const uint32_t nseg = fft_segments(r->prep.L, bank->M, quad);
         if (st == BF_OK) {
-            r->seg_spec = static_cast<float2*>(ctx->mem->alloc((size_t)nseg * (FFT_POINTS / 2) * sizeof(float2)));
+            r->seg_spec = static_cast<float2*>(ctx->mem->alloc(fft_series_bytes(r->prep.L, bank->M, quad)));
             r->fix = static_cast<uint32_t*>(ctx->mem->alloc((2 * (size_t)r->prep.L + 1) * sizeof(uint32_t)));
             if (!r->seg_spec || !r->fix) {
                 set_error("out of device memory for the segment spectra");
@@ -158,16 +159,21 @@ static bool admit(ServeState* S, Request* r)
             }
         }
         if (st == BF_OK) {
-            const uint32_t V = FFT_POINTS - bank->M + 1;
+            const uint32_t V = fft_lags_per_seg(bank->M, quad);
             FftSeriesBatch b{};
             b.n = 1;
+            b.quad = quad ? 1 : 0;
+            b.F = fft_seg_len(quad);
             b.V = V;
+            b.Vp = fft_norm_stride(bank->M, quad);
+            b.scale = fft_inverse_scale(quad);
             b.tw = tw;
             b.x[0] = r->prep.x;
             b.N[0] = r->prep.N;
             b.spec[0] = r->seg_spec;
             b.S[0] = r->prep.prefix;
             b.inv[0] = r->prep.inv;
+            b.inv_seg[0] = fft_seg_norms(r->seg_spec, nseg, quad);
             b.L[0] = (uint32_t)r->prep.L;
             b.fix[0] = r->fix;
             b.n_fix = r->fix + 2 * r->prep.L;
@@ -181,6 +187,7 @@ static bool admit(ServeState* S, Request* r)
             p.hrow0 = 0;
             p.quad = bank->quad ? 1 : 0;
             p.V = V;
+            p.Vp = b.Vp;
             p.n_ser = 1;
             p.thr = res->thr;
             p.cand_cap = res->cand_cap;
@@ -191,7 +198,7 @@ static bool admit(ServeState* S, Request* r)
             p.fs = bank->fs;
             FftSeries& f = p.ser[0];
             f.spec = r->seg_spec;
-            f.inv = r->prep.inv;
+            f.inv = b.inv_seg[0];
             f.x = r->prep.x;
             f.fix = r->fix;
             f.n_fix = r->fix + 2 * r->prep.L;
@@ -325,13 +332,15 @@ static void scheduler(ServeState* S)
             }
             any = true;
         }
-        // FFT-route requests: a chunk of template pairs each
+        // FFT-route requests: a chunk of templates (real route) or template
+        // pairs (pair route) each, one transform per item and segment
         for (Request* r : act) {
             if (!r->fft || r->cancel || r->k_next >= r->k_stop) continue;
             const uint64_t per = std::max<uint64_t>(1, (uint64_t)ctx->n_sm * TRANSFORMS_PER_SM /
                                                            std::max<uint64_t>(1, n_work));
-            const uint64_t pairs = std::max<uint64_t>((uint64_t)ctx->n_sm, per / std::max<uint32_t>(1, r->fp.ser[0].nseg));
-            const uint32_t rows = (uint32_t)std::min<uint64_t>(2 * pairs, r->k_stop - r->k_next);
+            const uint64_t items = std::max<uint64_t>((uint64_t)ctx->n_sm, per / std::max<uint32_t>(1, r->fp.ser[0].nseg));
+            const uint64_t want = r->fp.quad ? 2 * items : items;
+            const uint32_t rows = (uint32_t)std::min<uint64_t>(want, r->k_stop - r->k_next);
             FftParams p = r->fp;
             p.k_lo = r->k_next;
             p.k_hi = r->k_next + rows;

@@ -1,7 +1,7 @@
 """GPU parity of the FFT route (BF_FFT_FP32: overlap-save over segments of
-8192 samples, template spectra kept with the bank) against the oracle, at
-sizes that span several segments with a ragged last one, and at the full GW
-size on sampled templates."""
+16384 samples with plain banks, 8192 with quadrature banks; template spectra
+kept with the bank) against the oracle, at sizes that span several segments
+with a ragged last one, and at the full GW size on sampled templates."""
 import numpy as np
 import pytest
 
@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 PREC = "fft_fp32"
-F = 8192
+F = 16384                    # samples per segment with a plain bank
 
 
 @pytest.fixture(scope="module")
@@ -28,10 +28,10 @@ def ctx():
 
 
 def test_gw_cut_down_several_segments(ctx):
-    """M = 4096: 4097 lags per segment, 12,289 lags = three segments, the
-    last two lags short.  Dense rho across the seams, maxima, sigma and
+    """M = 4096: 12,289 lags per segment, 28,673 lags = three segments, the
+    last one 4,095 lags.  Dense rho across the seams, maxima, sigma and
     histogram of the data and both controls."""
-    w = synth.gw_pair(n=16384, I=16, J=16)
+    w = synth.gw_pair(n=32768, I=16, J=16)
     fs, M = w["fs"], w["M"]
     xs = w["series"]
     ctrl = [bf.bf_control_randomize(ctx, x, sd) for x, sd in zip(xs, w["control_seeds"])]
@@ -39,13 +39,13 @@ def test_gw_cut_down_several_segments(ctx):
     refs = [oracle.search(x, fs, p, M, want_rho=True) for x in xs + ctrl]
     bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_SPLIT_BF16)
     K, L = refs[0]["rho"].shape
-    assert L == 12289 and -(-L // (F - M + 1)) == 3
+    assert L == 28673 and -(-L // (F - M + 1)) == 3
     rho = torch.zeros((K, L), dtype=torch.float32, device="cuda")
     run(ctx, bank, xs[:1], fs, PREC, rho_out=rho)
     err = np.abs(rho.cpu().numpy().astype(np.float64) - refs[0]["rho"])
     assert err.max() <= TOL[PREC], err.max()
     # the lags on either side of each seam
-    for t in (4095, 4096, 4097, 8193, 8194, L - 1):
+    for t in (12287, 12288, 12289, 24577, 24578, L - 1):
         assert err[:, t].max() <= TOL[PREC]
     outs, mean, info = run(ctx, bank, xs + ctrl, fs, PREC)
     assert info.correlations == 4 * K * L and info.tile_lags == 0
@@ -112,7 +112,7 @@ def test_agrees_with_the_direct_path(ctx):
 
 
 def test_full_size_gw_pair_sampled(ctx):
-    """Both 64 s series against all 65,536 templates (63 segments each);
+    """Both 64 s series against all 65,536 templates (21 segments each);
     twelve templates spread over the bank recomputed by the oracle over every
     lag of series 0; the whole output against the split-BF16 path."""
     w = synth.gw_pair()
@@ -157,9 +157,9 @@ def test_rejections(ctx):
 
 
 def test_generated_bank_in_chunks(ctx):
-    """A bank that keeps only chirp parameters makes its spectra 16,384 rows
+    """A bank that keeps only chirp parameters makes its spectra 8,192 rows
     at a time in a two-slot ring: a 20,000-template bank from an odd offset
-    spans two chunks.  Templates around the chunk edge against the oracle;
+    spans three chunks.  Templates around the chunk edges against the oracle;
     every template against the bank that keeps its spectra."""
     fs, M = 2048.0, 2048
     spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0], 20.0,
@@ -171,7 +171,7 @@ def test_generated_bank_in_chunks(ctx):
     g = outs[0]
     assert info.n_templates == 20000 - b0
     p = oracle_params(spec)
-    idx = np.array([0, 1, 16382, 16383, 16384, 16385, 16386, 19991, 19992]) + 0
+    idx = np.array([0, 1, 8190, 8191, 8192, 8193, 16382, 16383, 16384, 16385, 19991, 19992])
     idx = idx[idx < 20000 - b0]
     ref = oracle.search(x, fs, subset(p, idx + b0), M, want_rho=True)
     gs = {k: v[idx] for k, v in g.items() if k in ("max", "argmax", "sigma")}
@@ -199,7 +199,7 @@ def test_spectra_over_the_budget():
         spec = synth.grid_spec([synth.LINEAR], [synth.ASC, synth.DESC], [1.0], 20.0, 1000.0, 64, 64)
         x = np.random.default_rng(31).standard_normal(10000).astype(np.float32)
         stored = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_FP32)   # 8192 x 2048 floats
-        with pytest.raises(bf.BFError) as e:                # 8192 x 32 KiB of spectra
+        with pytest.raises(bf.BFError) as e:                # 8192 x 64 KiB of spectra
             run(ctx, stored, [x], fs, PREC)
         assert e.value.status == bf.BF_ENOMEM
         a = run(ctx, stored, [x], fs, "fp32", bank_end=512)[0][0]
@@ -214,7 +214,7 @@ def test_spectra_over_the_budget():
 
 @pytest.mark.parametrize("fs,T", [(64.0, 1.0), (2.0, 1.0), (1000.0, 1.0), (4096.0, 1.0)])
 def test_template_lengths(ctx, fs, T):
-    """Template lengths from 2 to 4096 samples (up to 8191 lags per
+    """Template lengths from 2 to 4096 samples (up to 16383 lags per
     segment), series of one segment, of several and of exactly one lag."""
     M = int(round(T * fs))
     ny = fs / 2
