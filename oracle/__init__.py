@@ -224,16 +224,26 @@ def welch_power(x: np.ndarray, F: int) -> np.ndarray:
     return np.abs(np.fft.fft(x, F)) ** 2 * (F / N)
 
 
+# DFT length and Welch segment length of the Parseval predictor: 16384
+# samples, the real segment of the FFT route (the paper's predictor works on
+# the segment transforms of its FFT route; it gives no length)
+PARSEVAL_F = 16384
+
+
 def parseval_sigma(x: np.ndarray, H: np.ndarray) -> np.ndarray:
     """Predicted standard deviation of rho for each template row of H ([K, M]),
     before the search, from Parseval's theorem (Sect. 2.2, Fig. 5 caption):
-      E[C_k(tau)^2] = sum_f S_x(f) |H_k(f)|^2 / F   (S_x = P / F, F = 2M),
+      E[C_k(tau)^2] = sum_f S_x(f) |H_k(f)|^2 / F   (S_x = P / F, F = PARSEVAL_F),
       rho = C / |window|,  |window|^2 ~ M sigma_x^2,
-    so sigma_k^2 = sum_f P(f) |H_k(f)|^2 / (F^2 M sigma_x^2), sigma_x^2 the
-    mean of x^2; 0 for an all-zero series."""
+    so sigma_k^2 = sum_f P(f) |H_k(f)|^2 / (F^2 M sigma_x^2), the sum over all
+    F bins, sigma_x^2 the mean of x^2; 0 for an all-zero series.  F >= 2M
+    keeps the template's circular autocorrelation free of wrap-around, so
+    templates of at most F/2 samples."""
     H = np.atleast_2d(np.asarray(H, np.float64))
     K, M = H.shape
-    F = 2 * M
+    F = PARSEVAL_F
+    if 2 * M > F:
+        raise ValueError("parseval_sigma: templates longer than F/2")
     x = np.asarray(x, np.float64)
     sx2 = np.mean(x * x)
     if sx2 == 0.0:

@@ -462,6 +462,27 @@ def test_parseval_sigma_white_noise_is_one_over_sqrt_m():
     assert oracle.parseval_sigma(np.zeros(4 * Mw), h[None, :])[0] == 0.0
 
 
+def test_parseval_sigma_is_exact_for_one_segment_of_circular_correlations():
+    """For a series of exactly F = PARSEVAL_F samples (one Welch segment),
+    sigma^2 F M sigma_x^2 equals the sum of the squared circular correlations
+    of the series with the zero-padded template over all F lags (Parseval),
+    computed here by plain loops over lags; templates longer than F/2 are
+    refused."""
+    F = oracle.PARSEVAL_F
+    r = rng(24)
+    x = r.standard_normal(F)
+    Mp = 300
+    h = r.standard_normal(Mp)
+    h /= np.linalg.norm(h)
+    s = oracle.parseval_sigma(x, h[None, :])[0]
+    xx = np.concatenate([x, x[:Mp]])                # circular: the series wraps around
+    circ = np.array([np.dot(xx[t:t + Mp], h) for t in range(F)])
+    lhs = s * s * F * Mp * np.mean(x * x)
+    assert abs(lhs - np.sum(circ ** 2)) < 1e-9 * np.sum(circ ** 2)
+    with pytest.raises(ValueError):
+        oracle.parseval_sigma(x, np.ones((1, F // 2 + 1)))
+
+
 def test_parseval_sigma_predicts_measured_sigma_of_coloured_noise():
     """On stationary coloured noise the prediction agrees with the rms of rho
     measured by the search, template by template, to within the bias of a
