@@ -402,11 +402,14 @@ bf_status bf_result_coincidence(const bf_result* r, size_t a, size_t b, double d
  * Predicted noise level of rho (Sect. 2.2 and Fig. 5 caption: sigma from
  * Parseval's theorem in a predictor step, before the search), kept when
  * opts.tail_sigma == BF_SIGMA_PARSEVAL:
- *   sigma_k^2 = sum_f P_x(f) |H_k(f)|^2 / (F^2 M sigma_x^2),   F = 2M,
- * P_x the periodogram of the series averaged over rectangular F-sample
- * segments at hop F/2 (a series shorter than F: one zero-padded segment scaled
- * by F/N), H_k the F-point DFT of template k, sigma_x^2 the mean of x^2.
- * Exactly 1/sqrt(M) on white noise.  n_templates floats per series.
+ *   sigma_k^2 = sum_f P_x(f) |H_k(f)|^2 / (F^2 M sigma_x^2),   F = 16384,
+ * the sum over all F bins, P_x the periodogram of the series averaged over
+ * rectangular F-sample segments at hop F/2 (a series shorter than F: one
+ * zero-padded segment scaled by F/N), H_k the F-point DFT of template k,
+ * sigma_x^2 the mean of x^2.  Its expectation on white noise is 1/M.  F is
+ * the FFT route's real segment length: the predictor runs on the library's
+ * own transforms, in plans and serving too, and takes templates of at most
+ * 8192 samples (BF_ENOTSUP otherwise).  n_templates floats per series.
  */
 bf_status bf_result_get_sigma_pred(const bf_result* r, size_t s, const float** sigma_pred);
 bf_status bf_result_copy_sigma_pred(const bf_result* r, size_t s, float* host);

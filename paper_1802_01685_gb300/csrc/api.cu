@@ -1098,7 +1098,6 @@ void bf_bank_destroy(bf_bank* b)
     if (!b) return;
     Allocator& mem = *b->ctx->mem;
     cudaStreamSynchronize(b->ctx->stream);
-    mem.release(b->ph);
     mem.release(b->fspec);
     mem.release(b->d_params);
     mem.release(b->f32);
@@ -1245,11 +1244,14 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
     }
     if (r->parseval) {
         // the predictor step: sigma_k per series before the search
-        st = bank_power_spectra(ctx, const_cast<bf_bank*>(bank), strm);
-        for (size_t s = 0; s < n_series && st == BF_OK; ++s)
-            st = predict_sigma(ctx, bank, prep[s], o.bank_begin, o.bank_end, r->sigma_pred + s * r->K,
-                               r->scratch, strm);
+        std::vector<const PreparedSeries*> pp;
+        for (const PreparedSeries& p : prep) pp.push_back(&p);
+        PredictCall pc;
+        st = predict_prepare(ctx, bank, pp, o.bank_begin, o.bank_end, r->sigma_pred, r->K, r->scratch, strm,
+                             &pc);
         if (st) return st;
+        cudaError_t ep = predict_launch(ctx, bank, pc, strm);
+        if (ep != cudaSuccess) return cuda_fail(ep, "predictor");
         for (size_t s = 0; s < segs.size(); ++s) {
             segs[s].sigma_pred = r->sigma_pred + s * r->K;
             segs[s].kappa = r->kappa;

@@ -180,6 +180,21 @@ struct FftSeriesBatch {
     uint32_t* n_fix;                // [n] counters, zeroed by launch_fft_series
 };
 
+// The Parseval predictor (predict.cu, kernels in corr_fft.cu): periodograms
+// averaged over Welch segments of PRED_F samples at hop PRED_F / 2, and
+// template power spectra, both on the FFT route's real 16384-point transform.
+constexpr int PRED_F = 2 * FFT_POINTS;
+constexpr int PRED_BINS = FFT_POINTS + 1;     // one-sided bins 0 .. PRED_F / 2
+struct WelchBatch {
+    int n;
+    const float2* tw;
+    const float* x[MAX_FFT_SER];
+    uint64_t N[MAX_FFT_SER];
+    uint32_t seg_begin[MAX_FFT_SER + 1];      // series s: rows [seg_begin[s], seg_begin[s+1])
+    float* pseg;                              // [total segments][PRED_BINS]
+    float* P;                                 // [n][PRED_BINS] averaged periodograms
+};
+
 // ---------------------------------------------------------------- launchers
 // Process-wide count of kernel launches made by this library.
 extern std::atomic<uint64_t> g_launches;
@@ -255,6 +270,11 @@ struct FinalizeParams {
     FinalizeSeries ser[MAX_FIN];
 };
 cudaError_t launch_finalize(const FinalizeParams& p, uint32_t K, uint32_t nbins, cudaStream_t s);
+uint32_t welch_segments(uint64_t N);         // Welch segments of a series of N samples
+cudaError_t launch_welch(const WelchBatch& b, int n_sm, cudaStream_t st);
+cudaError_t launch_template_power_dot(const float* rows, uint32_t n_rows, const float2* tw, const float* P,
+                                      uint32_t n_ser, float* D, uint32_t d_stride, uint32_t row0, int n_sm,
+                                      cudaStream_t st);
 uint32_t fft_seg_len(bool quad);            // samples per segment
 uint32_t fft_spec_bins(bool quad);          // complex bins per segment or template spectrum
 uint32_t fft_lags_per_seg(uint32_t M, bool quad);          // V = fft_seg_len - M + 1
@@ -354,7 +374,6 @@ struct bf_bank {
     uint8_t* hi16 = nullptr;            // split-FP16 layout (2^8 h)
     uint8_t* lo16 = nullptr;
     uint32_t* tile_kb = nullptr;        // nonzero 64-sample block range per 128-row tile
-    float* ph = nullptr;                // template power spectra [K_pad][M+1] (lazy)
     float2* fspec = nullptr;            // template half spectra for the FFT route (lazy)
 };
 

@@ -338,10 +338,13 @@ __device__ __forceinline__ float2 fft_final_mirror(const Smem& m, int k, float2 
 // fft_passes<-1>): with E = (U[k] + conj U[N-k]) / 2 and
 // O = (U[k] - conj U[N-k]) / 2i the transforms of the even and odd samples,
 //   S[k] = E + e^{-i pi k / N} O,   S[N - k] = conj(E - e^{-i pi k / N} O),
-//   S[N/2] = conj(U[N/2]),  S[0] = E_0 + O_0,  S[N] = E_0 - O_0 (real),
-// written as out[0 .. N) with out[0] = (S[0], S[N]).
-__device__ __forceinline__ void real_spectrum_out(const Smem& m, float2 base_f, float2 base_r,
-                                                  float2* __restrict__ out)
+//   S[N/2] = conj(U[N/2]),  S[0] = E_0 + O_0,  S[N] = E_0 - O_0 (real).
+// Calls emit(i, slot, k, S[k]) for this thread's bins: slot 0 for
+// k = tid + 512 i, slot 1 for N - k (i < 8); thread 0, i = 0 emits slot 0
+// with k = 0 and (S[0], S[N]) packed, and slot 2 with k = N/2.  i is a
+// compile-time constant in each call.
+template <typename Emit>
+__device__ __forceinline__ void real_spectrum(const Smem& m, float2 base_f, float2 base_r, Emit emit)
 {
     const int tid = threadIdx.x;
 #pragma unroll
@@ -351,18 +354,25 @@ __device__ __forceinline__ void real_spectrum_out(const Smem& m, float2 base_f, 
         float2 zk, zh;
         fft_final(m, i, w, zk, zh);                               // U[k], U[k + 4096]
         if (k == 0) {
-            out[0] = make_float2(zk.x + zk.y, zk.x - zk.y);
-            out[FH] = make_float2(zh.x, -zh.y);
+            emit(i, 0, 0, make_float2(zk.x + zk.y, zk.x - zk.y));
+            emit(i, 2, FH, make_float2(zh.x, -zh.y));
         } else {
             const float2 zm = fft_final_mirror(m, k, w);         // U[N - k]
             const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
             const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
             const float2 wr = cmul(base_r, root32(i));            // e^{i pi k / N}
             const float2 wo = cmul(make_float2(wr.x, -wr.y), o);
-            out[k] = make_float2(e.x + wo.x, e.y + wo.y);
-            out[FN - k] = make_float2(e.x - wo.x, wo.y - e.y);
+            emit(i, 0, k, make_float2(e.x + wo.x, e.y + wo.y));
+            emit(i, 1, FN - k, make_float2(e.x - wo.x, wo.y - e.y));
         }
     }
+}
+
+// the spectrum as out[0 .. N), out[0] = (S[0], S[N])
+__device__ __forceinline__ void real_spectrum_out(const Smem& m, float2 base_f, float2 base_r,
+                                                  float2* __restrict__ out)
+{
+    real_spectrum(m, base_f, base_r, [&](int, int, int k, float2 v) { out[k] = v; });
 }
 
 // Spectra of segments of a batch of series.  Pair route (F = 8192): the real
@@ -458,6 +468,126 @@ __global__ void __launch_bounds__(FT, 1) k_fft_bank(const float* __restrict__ ro
             }
         }
         __syncthreads();
+    }
+}
+
+// ---- Parseval predictor of sigma (Sect. 2.2, Fig. 5 caption): periodograms
+// and template power spectra on the real route's 16384-point transform.
+
+// |S[k]|^2, k = 0 .. N, of this thread's bins into out (N + 1 floats)
+__device__ __forceinline__ void real_power_out(const Smem& m, float2 base_f, float2 base_r,
+                                               float* __restrict__ out)
+{
+    real_spectrum(m, base_f, base_r, [&](int, int, int k, float2 v) {
+        if (k == 0) {
+            out[0] = v.x * v.x;
+            out[FN] = v.y * v.y;
+        } else {
+            out[k] = v.x * v.x + v.y * v.y;
+        }
+    });
+}
+
+// Periodograms of the Welch segments of a batch of series: segment g of
+// series s covers samples [g F/2, g F/2 + F), zero past the end; row
+// seg_begin[s] + g of pseg gets |S[k]|^2 for k = 0 .. N.
+__global__ void __launch_bounds__(FT, 1) k_welch_segments(const __grid_constant__ WelchBatch p, uint32_t total)
+{
+    const Smem m = smem_setup<0>(p.tw);
+    const int tid = threadIdx.x;
+    const float2 base_f = thread_root(4096.0);
+    const float2 base_r = thread_root(8192.0);
+    for (uint32_t g = blockIdx.x; g < total; g += gridDim.x) {
+        int s = 0;
+        while (s + 1 < p.n && g >= p.seg_begin[s + 1]) ++s;
+        const uint64_t N = p.N[s], a0 = (uint64_t)(g - p.seg_begin[s]) * FN;      // hop F/2 = N
+        const float* x = p.x[s];
+        for (int n = tid; n < FN; n += FT) {
+            const uint64_t a = a0 + 2 * (uint64_t)n;
+            m.z[n + (n >> 4)] = make_float2(a < N ? x[a] : 0.f, a + 1 < N ? x[a + 1] : 0.f);
+        }
+        __syncthreads();
+        fft_passes<-1>(m);
+        real_power_out(m, base_f, base_r, p.pseg + (size_t)g * PRED_BINS);
+        __syncthreads();
+    }
+}
+
+// P_s(k) = c_s / S_s sum_g pseg[g](k) over the S_s segments of series s, the
+// sum in FP64 in segment order; c_s = 1, or F / N_s for a series shorter than
+// F (one zero-padded segment).  Grid: (bins, series).
+__global__ void k_welch_mean(const __grid_constant__ WelchBatch p)
+{
+    const int s = blockIdx.y;
+    if (s >= p.n) return;
+    const uint32_t g0 = p.seg_begin[s], S = p.seg_begin[s + 1] - g0;
+    const double c = p.N[s] < (uint64_t)PRED_F ? (double)PRED_F / (double)p.N[s] : 1.0;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < (uint32_t)PRED_BINS; k += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (uint32_t g = 0; g < S; ++g) acc += (double)p.pseg[(size_t)(g0 + g) * PRED_BINS + k];
+        p.P[(size_t)s * PRED_BINS + k] = (float)(acc * c / (double)S);
+    }
+}
+
+// For template rows q < n_rows of a chunk (8192 samples each, zero past M):
+// D[s][row0 + q] = sum over all F bins of P_s(f) |H_q(f)|^2, i.e. the bins
+// 0 and N once and the others twice, for each series s < n_ser; the partial
+// sums per thread in FP32 (16 terms), across the CTA in FP64.
+__global__ void __launch_bounds__(FT, 1) k_template_power_dot(const float* __restrict__ rows, uint32_t n_rows,
+                                                              const float2* __restrict__ tw,
+                                                              const float* __restrict__ P, uint32_t n_ser,
+                                                              float* __restrict__ D, uint32_t d_stride,
+                                                              uint32_t row0)
+{
+    const Smem m = smem_setup<0>(tw);
+    __shared__ double red[FT / 32];
+    const int tid = threadIdx.x;
+    const float2 base_f = thread_root(4096.0);
+    const float2 base_r = thread_root(8192.0);
+    for (uint32_t q = blockIdx.x; q < n_rows; q += gridDim.x) {
+        const float2* r2 = reinterpret_cast<const float2*>(rows + (size_t)q * FN);
+        for (int n = tid; n < FN; n += FT) m.z[n + (n >> 4)] = n < FH ? r2[n] : make_float2(0.f, 0.f);
+        __syncthreads();
+        fft_passes<-1>(m);
+        // this thread's weighted powers: pw[i] at k = tid + 512 i, pm[i] at
+        // N - k (thread 0, i = 0: S[0] and S[N], each once); thread 0 also
+        // holds the middle bin N/2 in mid
+        float pw[FBINS], pm[FBINS], mid = 0.f;
+        real_spectrum(m, base_f, base_r, [&](int i, int slot, int k, float2 v) {
+            const float a = 2.f * (v.x * v.x + v.y * v.y);
+            if (slot == 0 && k == 0) {                      // S[0] and S[N], each once
+                pw[i] = v.x * v.x;
+                pm[i] = v.y * v.y;
+            } else if (slot == 0) {
+                pw[i] = a;
+            } else if (slot == 1) {
+                pm[i] = a;
+            } else {
+                mid = a;
+            }
+        });
+        __syncthreads();                        // work array read: the next row may load
+        for (uint32_t s = 0; s < n_ser; ++s) {
+            const float* Ps = P + (size_t)s * PRED_BINS;
+            float acc = tid == 0 ? mid * Ps[FH] : 0.f;
+#pragma unroll
+            for (int i = 0; i < FBINS; ++i) {
+                const int k = tid + FT * i;
+                acc = fmaf(pw[i], Ps[k], acc);
+                acc = fmaf(pm[i], Ps[k == 0 ? FN : FN - k], acc);
+            }
+            double d = (double)acc;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if ((tid & 31) == 0) red[tid >> 5] = d;
+            __syncthreads();
+            if (tid == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < FT / 32; ++w) tot += red[w];
+                D[(size_t)s * d_stride + row0 + q] = (float)tot;
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -989,6 +1119,10 @@ cudaError_t fft_attributes()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fft_bank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_welch_segments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_template_power_dot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fft_fixup<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FIX_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fft_fixup<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FIX_SMEM);
@@ -1101,6 +1235,34 @@ uint32_t fft_segments(uint32_t L, uint32_t M, bool quad)
 {
     const uint64_t V = fft_lags_per_seg(M, quad);
     return (uint32_t)(((uint64_t)L + V - 1) / V);          // L may be close to 2^32
+}
+
+uint32_t welch_segments(uint64_t N)
+{
+    return N >= (uint64_t)PRED_F ? (uint32_t)((N - PRED_F) / (PRED_F / 2) + 1) : 1u;
+}
+
+cudaError_t launch_welch(const WelchBatch& b, int n_sm, cudaStream_t st)
+{
+    const uint32_t total = b.seg_begin[b.n];
+    if (b.n == 0 || total == 0) return cudaSuccess;
+    count_launches(2);
+    k_welch_segments<<<std::min<uint32_t>(total, (uint32_t)n_sm), FT, FFT_SMEM, st>>>(b, total);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_welch_mean<<<dim3((PRED_BINS + 255) / 256, (unsigned)b.n), 256, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_template_power_dot(const float* rows, uint32_t n_rows, const float2* tw, const float* P,
+                                      uint32_t n_ser, float* D, uint32_t d_stride, uint32_t row0, int n_sm,
+                                      cudaStream_t st)
+{
+    if (n_rows == 0 || n_ser == 0) return cudaSuccess;
+    count_launches(1);
+    k_template_power_dot<<<std::min<uint32_t>(n_rows, (uint32_t)n_sm), FT, FFT_SMEM, st>>>(
+        rows, n_rows, tw, P, n_ser, D, d_stride, row0);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, int n_sm, cudaStream_t st)

@@ -62,10 +62,6 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
     bf_opts o;
     bf_status st = resolve_opts(bank, opts, &o);
     if (st) return st;
-    if (o.tail_sigma == BF_SIGMA_PARSEVAL) {
-        set_error("plans take BF_SIGMA_WHITE tails (the Parseval predictor runs cuFFT outside the graph)");
-        return BF_ENOTSUP;
-    }
     o.stream = nullptr;
     o.rho_out = nullptr;
     for (size_t s = 0; s < n_series; ++s)
@@ -98,7 +94,15 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
     const bool fft = o.precision == BF_FFT_FP32;
     std::vector<Seg> segs;
     FftCall fc;
+    PredictCall pc;
     int lt = 0;
+    if (p->r->parseval) {
+        // the predictor's buffers and the twiddle tables before the capture
+        std::vector<const PreparedSeries*> pp(pptr.begin(), pptr.end());
+        st = predict_prepare(ctx, bank, pp, o.bank_begin, o.bank_end, p->r->sigma_pred, p->r->K,
+                             p->r->scratch, strm, &pc);
+        if (st) return st;
+    }
     if (fft) {
         // everything that allocates or synchronises happens before the capture:
         // the bank's spectra, the twiddle tables, the segment-spectra buffers
@@ -110,6 +114,11 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
     } else {
         build_segments(pptr, ids, bank, o.bank_begin, o.bank_end, o.precision, p->r->packed,
                        p->r->sumsq, p->r->K, segs);
+        if (p->r->parseval)
+            for (size_t s = 0; s < segs.size(); ++s) {
+                segs[s].sigma_pred = p->r->sigma_pred + s * p->r->K;
+                segs[s].kappa = p->r->kappa;
+            }
         cudaError_t es = cudaStreamSynchronize(strm);
         if (es == cudaSuccess) es = corr_tc_set_attributes();
         if (es != cudaSuccess) return cuda_fail(es, "plan set-up");
@@ -126,6 +135,7 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
     cudaError_t ec = clear_result(p->r, strm);
     for (size_t s = 0; s < n_series && ec == cudaSuccess; ++s)
         ec = prepare_series_kernels(p->prep[s], bank->M, o.precision, strm);
+    if (ec == cudaSuccess && p->r->parseval) ec = predict_launch(ctx, bank, pc, strm);
     if (ec == cudaSuccess)
         ec = fft ? fft_launch(ctx, bank, fc, p->r, strm)
                  : launch_segments(ctx, segs, o.precision, p->r->thr, p->r->cand, p->r->cand_count,

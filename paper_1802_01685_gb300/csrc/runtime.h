@@ -76,8 +76,6 @@ bf_status check_device_status(bf_ctx* ctx);
 
 void serve_shutdown(bf_ctx* ctx);
 
-// Parseval predictor of the noise level of rho (predict.cu)
-bf_status bank_power_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st);
 // template half spectra of the FFT route, computed once per bank
 bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st);
 // one call of the FFT route: per batch of series, the segment-spectra job and
@@ -92,7 +90,27 @@ bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
 cudaError_t fft_launch(bf_ctx* ctx, const bf_bank* bank, FftCall& c, bf_result* r, cudaStream_t st);
 // the context's twiddle tables of the FFT route (built on first use)
 cudaError_t fft_tables(bf_ctx* ctx, cudaStream_t st, const float2** out);
-bf_status predict_sigma(bf_ctx* ctx, const bf_bank* bank, const PreparedSeries& ps, size_t k_begin,
-                        size_t k_end, float* out, std::vector<void*>& scratch, cudaStream_t st);
+// Parseval predictor of the noise level of rho (predict.cu): predict_prepare
+// allocates (into `scratch`, owned by the result) and makes the twiddle
+// tables; predict_launch enqueues kernels only, so a plan can capture it.
+// sigma of series s, output j goes to out[s * out_stride + j].
+struct SigmaBatch;
+struct PredictCall {
+    const float2* tw = nullptr;
+    uint32_t row_begin = 0, row_end = 0, n_out = 0, n_series = 0, chunk = 0;
+    float* rows = nullptr;                  // synthesised template rows [chunk][FFT_POINTS]
+    float* D = nullptr;                     // power dot products [n_series][rows]
+    float* P = nullptr;                     // averaged periodograms [n_series][PRED_BINS]
+    std::vector<WelchBatch> welch;
+    std::vector<SigmaBatch*> sigma;
+    PredictCall() = default;
+    PredictCall(const PredictCall&) = delete;
+    PredictCall& operator=(const PredictCall&) = delete;
+    ~PredictCall();
+};
+bf_status predict_prepare(bf_ctx* ctx, const bf_bank* bank, const std::vector<const PreparedSeries*>& ps,
+                          size_t k_begin, size_t k_end, float* out, size_t out_stride,
+                          std::vector<void*>& scratch, cudaStream_t st, PredictCall* c);
+cudaError_t predict_launch(bf_ctx* ctx, const bf_bank* bank, const PredictCall& c, cudaStream_t st);
 
 }  // namespace bfi

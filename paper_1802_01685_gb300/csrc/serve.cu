@@ -128,11 +128,14 @@ static bool admit(ServeState* S, Request* r)
         return false;
     }
     if (res->parseval) {
-        std::lock_guard<std::mutex> g(ctx->launch_mu);    // the bank's spectra cache
-        st = bank_power_spectra(ctx, const_cast<bf_bank*>(bank), S->stream);
-        if (st == BF_OK)
-            st = predict_sigma(ctx, bank, r->prep, r->opts.bank_begin, r->opts.bank_end,
-                               res->sigma_pred, res->scratch, S->stream);
+        std::lock_guard<std::mutex> g(ctx->launch_mu);    // the context's twiddle tables
+        PredictCall pc;
+        st = predict_prepare(ctx, bank, {&r->prep}, r->opts.bank_begin, r->opts.bank_end, res->sigma_pred,
+                             res->K, res->scratch, S->stream, &pc);
+        if (st == BF_OK) {
+            cudaError_t ep = predict_launch(ctx, bank, pc, S->stream);
+            if (ep != cudaSuccess) st = cuda_fail(ep, "predictor");
+        }
         if (st != BF_OK) {
             r->status = st;
             r->error = bf_last_error();

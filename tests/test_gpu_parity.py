@@ -182,7 +182,7 @@ def test_tiny_tails(ctx, tiny, prec):
 def test_parseval_predictor_matches_oracle(ctx):
     """sigma_k predicted before the search (Parseval) against the FP64
     oracle: white noise, coloured GW-like noise, a Poisson light curve, and a
-    series shorter than the 2M-sample FFT (one zero-padded segment)."""
+    series shorter than the 16384-sample FFT (one zero-padded segment)."""
     rng = np.random.default_rng(41)
     fs, M = 2048.0, 2048
     spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0, 0.35],
@@ -208,6 +208,32 @@ def test_parseval_predictor_matches_oracle(ctx):
         bf.bf_result_copy_sigma_pred(res, 0)                      # not requested
     bf.bf_result_destroy(res)
     bf.bf_bank_destroy(bank)
+
+
+def test_parseval_predictor_long_templates_and_several_segments(ctx):
+    """A 15 s series at 8192 Hz (14 Welch segments of 16384 samples at hop
+    8192) and templates of 8192 samples, the longest the predictor's
+    16384-point transform takes; longer templates answer BF_ENOTSUP."""
+    rng = np.random.default_rng(43)
+    fs = 8192.0
+    chirps = [(bf.BF_LINEAR, bf.BF_ASC, 100.0, 3000.0, 1.0), (bf.BF_POWERLAW, bf.BF_DESC, 50.0, 2000.0, 0.6),
+              (bf.BF_LINEAR, bf.BF_BOTH, 300.0, 900.0, 0.8)]
+    bank = bf.bf_bank_create(ctx, chirps, fs, 1.0, STORE_ALL)
+    p = {k: np.array([c[i] for c in chirps], dt) for i, (k, dt) in enumerate(
+        (("track", np.int32), ("sense", np.int32), ("f_lo", np.float64), ("f_hi", np.float64), ("D", np.float64)))}
+    x = synth.gw_coloured(int(15 * fs), fs, rng).astype(np.float32)
+    res = bf.bf_correlate(ctx, bank, [x], fs, bf.make_opts(precision="split_bf16",
+                                                           tail_sigma=bf.BF_SIGMA_PARSEVAL))
+    got = bf.bf_result_copy_sigma_pred(res, 0)
+    bf.bf_result_destroy(res)
+    np.testing.assert_allclose(got, oracle.parseval_sigma(x, oracle.bank(p, fs, 8192)), rtol=2e-5, atol=1e-9)
+    bf.bf_bank_destroy(bank)
+    long_bank = bf.bf_bank_create(ctx, [(bf.BF_LINEAR, bf.BF_ASC, 100.0, 3000.0, 1.0)], 16384.0, 1.0, STORE_ALL)
+    with pytest.raises(bf.BFError) as e:
+        bf.bf_correlate(ctx, long_bank, [np.zeros(20000, np.float32)], 16384.0,
+                        bf.make_opts(tail_sigma=bf.BF_SIGMA_PARSEVAL))
+    assert e.value.status == bf.BF_ENOTSUP
+    bf.bf_bank_destroy(long_bank)
 
 
 @pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fft_fp32", "split_fp16"])

@@ -74,6 +74,47 @@ def test_plan_replays_equal_correlate(setup, prec):
         bf.bf_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("prec", ["split_bf16", "fft_fp32"])
+def test_plan_with_parseval_tails(setup, prec):
+    """The Parseval predictor runs inside the plan's graph: each replay's
+    predicted sigma matches the oracle's, and the replay equals bf_correlate
+    on the same series (maxima, predicted sigma, tails at kappa sigma_k, map)
+    bit for bit."""
+    ctx, bank, spec = setup
+    lens = [20000, 5000, 2049]
+    opts = bf.make_opts(precision=prec, bank_begin=3, bank_end=500, kappa=3.5, want_tails=True,
+                        want_map=True, tail_sigma=bf.BF_SIGMA_PARSEVAL)
+    p = subset(oracle_params(spec), np.arange(3, 500))
+    H = oracle.bank(p, 2048.0, 2048)
+    plan = bf.bf_plan_create(ctx, bank, lens, 2048.0, opts)
+    try:
+        for run in range(2):
+            rng = np.random.default_rng(300 + run)
+            xs = [synth.gw_coloured(lens[0], 2048.0, rng).astype(np.float32),
+                  synth.grb_lightcurve(lens[1], 2048.0, rng).astype(np.float32),
+                  rng.standard_normal(lens[2]).astype(np.float32)]
+            res = bf.bf_plan_run(plan, xs)
+            got = outputs(res, len(lens), True)
+            got_sig = [bf.bf_result_copy_sigma_pred(res, s) for s in range(len(lens))]
+            got_tails = np.sort(bf.bf_result_copy_tails(res), order=["series", "k", "tau"])
+            for x, sg in zip(xs, got_sig):
+                np.testing.assert_allclose(sg, oracle.parseval_sigma(x, H), rtol=2e-5, atol=1e-9)
+            ref_h = bf.bf_correlate(ctx, bank, xs, 2048.0, opts)
+            ref = outputs(ref_h, len(lens), True)
+            ref_sig = [bf.bf_result_copy_sigma_pred(ref_h, s) for s in range(len(lens))]
+            ref_tails = np.sort(bf.bf_result_copy_tails(ref_h), order=["series", "k", "tau"])
+            bf.bf_result_destroy(ref_h)
+            assert len(ref_tails) > 0
+            for g, r, gs, rs in zip(got, ref, got_sig, ref_sig):
+                np.testing.assert_array_equal(gs, rs)
+                np.testing.assert_array_equal(g["max"], r["max"])
+                np.testing.assert_array_equal(g["argmax"], r["argmax"])
+                np.testing.assert_array_equal(g["map"], r["map"])
+            np.testing.assert_array_equal(got_tails, ref_tails)
+    finally:
+        bf.bf_plan_destroy(plan)
+
+
 def test_plan_on_a_stream_and_launch_count(setup):
     ctx, bank, spec = setup
     lens = [4096, 3000]
