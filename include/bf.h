@@ -83,16 +83,19 @@ typedef enum {
                            nearest (the tensor core's own accumulation
                            truncates)                                        */
     BF_FFT_FP32 = 3,    /* the paper's route (Sect. 2.2, Fig. 5): FP32 FFTs,
-                           overlap-save over segments of 8192 samples
-                           (8193 - M lags each).  Template spectra are made
-                           from the chirp parameters, whatever the bank
-                           stores: a stored bank keeps them (32 KiB per
-                           template, made on first use); a generated bank
-                           makes them per call, 16,384 rows at a time,
+                           overlap-save.  Plain banks: real segments of
+                           16384 samples (16385 - M lags each), one template
+                           per 8192-point complex transform; quadrature
+                           banks: segments of 8192 samples (8193 - M lags),
+                           template and partner in one transform.  Template
+                           spectra are made from the chirp parameters,
+                           whatever the bank stores: a stored bank keeps
+                           them (64 KiB per template, 32 KiB per
+                           quadrature row; made on first use); a generated
+                           bank makes them per call, 512 MiB at a time,
                            overlapped with the correlation, so any bank size
                            works.  Templates of at most 4096 samples, else
-                           BF_ENOTSUP.  Plans and the serving loop run it
-                           with a stored bank.  tile_lags is ignored.  Lags
+                           BF_ENOTSUP.  tile_lags is ignored.  Lags
                            whose window holds less than 1/16384 of its
                            segment's energy (quiet or gated stretches next
                            to loud data), where the transform's rounding
@@ -450,7 +453,9 @@ void bf_result_destroy(bf_result* r);
  * context stream).  *out points at the plan's result: valid until the next run
  * or bf_plan_destroy, read with the bf_result_* calls, never destroyed by the
  * caller (bf_result_destroy on it does nothing but set bf_last_error).
- * Stored banks only (BF_ENOTSUP for a generated bank).  Runs of one plan must
+ * A generated bank's synthesis ring (template chunks, or their spectra,
+ * made on the context's second stream) is captured in the graph too.  Runs
+ * of one plan must
  * not overlap on the GPU, nor a run with asynchronous copies of the previous
  * run's result.
  */
@@ -510,8 +515,12 @@ bf_status bf_control_randomize_static(const float* in, size_t n, uint64_t seed, 
  * ticket without waiting for GPU work; a scheduler thread admits requests
  * while slots and HBM budget allow, and each launch of the batched kernel
  * mixes template tiles of every admitted request, so a request that arrives
- * while others run joins the next launch.  BF_EAGAIN: queue full.
- * BF_ENOMEM: the request alone exceeds the budget.  BF_EINVAL: bad request.
+ * while others run joins the next launch.  A request on a generated bank
+ * gets a synthesis slot of its own (about 50 MB of template tiles, or 128 MiB
+ * of template spectra on the FFT route, counted against the budget), refilled
+ * every iteration with what that iteration correlates.  BF_EAGAIN: queue
+ * full.  BF_ENOMEM: the request alone exceeds the budget.  BF_EINVAL: bad
+ * request.
  */
 typedef struct {
     const float* series;     /* host or device, n samples                        */

@@ -626,82 +626,136 @@ bf_status finalize_result(bf_ctx* ctx, const bf_bank* bank, bf_result* r, cudaSt
 // `segs` describe the whole call; each chunk restricts them to its tiles.
 constexpr size_t GEN_SLOT_BYTES = 24u << 20;
 
-cudaError_t correlate_generated(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
-                                const std::vector<Seg>& segs, bf_result* r, cudaStream_t strm, int lt)
+cudaError_t RingEvents::create()
+{
+    cudaError_t e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&made[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&used[i], cudaEventDisableTiming);
+    }
+    return e;
+}
+
+// events may be destroyed while pending work still references them
+RingEvents::~RingEvents()
+{
+    if (start) cudaEventDestroy(start);
+    for (int i = 0; i < 2; ++i) {
+        if (made[i]) cudaEventDestroy(made[i]);
+        if (used[i]) cudaEventDestroy(used[i]);
+    }
+}
+
+bf_status gen_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o, bf_result* r, GenRing* g)
 {
     const bool tc = o.precision != BF_FP32;
-    const bool f16 = o.precision == BF_SPLIT_FP16;
     const size_t tile_bytes = (size_t)TC_TILE_T * bank->M_pad * 4;     // hi+lo, or FP32
-    const size_t chunk_tiles = std::max<size_t>(1, GEN_SLOT_BYTES / tile_bytes);
-    const size_t t_begin = bank_row(bank, o.bank_begin) / TC_TILE_T;
-    const size_t t_end = ceil_div(bank_row(bank, o.bank_end), TC_TILE_T);
-    const size_t n_chunks = ceil_div(t_end - t_begin, chunk_tiles);
-    const size_t slot_elems = std::min(chunk_tiles, t_end - t_begin) * TC_TILE_T * bank->M_pad;
+    g->chunk_tiles = std::max<size_t>(1, GEN_SLOT_BYTES / tile_bytes);
+    g->t_begin = bank_row(bank, o.bank_begin) / TC_TILE_T;
+    g->t_end = ceil_div(bank_row(bank, o.bank_end), TC_TILE_T);
+    g->n_chunks = ceil_div(g->t_end - g->t_begin, g->chunk_tiles);
+    const size_t slot_bytes = gen_slot_bytes(bank, o.precision,
+                                             std::min(g->chunk_tiles, g->t_end - g->t_begin) * TC_TILE_T);
     Allocator& mem = *ctx->mem;
-    void* slot[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    for (int i = 0; i < 2 && i < (int)n_chunks; ++i)
+    for (int i = 0; i < 2 && i < (int)g->n_chunks; ++i)
         for (int j = 0; j < (tc ? 2 : 1); ++j) {
-            slot[i][j] = mem.alloc(slot_elems * (tc ? 2 : 4));
-            if (!slot[i][j]) {
+            g->slot[i][j] = mem.alloc(slot_bytes);
+            if (!g->slot[i][j]) {
                 set_error("out of device memory for the synthesis ring");
-                return cudaErrorMemoryAllocation;
+                return BF_ENOMEM;
             }
-            r->scratch.push_back(slot[i][j]);
+            r->scratch.push_back(g->slot[i][j]);
         }
-    cudaEvent_t ev_start, synth_done[2], corr_done[2];
-    cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
-    for (int i = 0; i < 2; ++i) {
-        cudaEventCreateWithFlags(&synth_done[i], cudaEventDisableTiming);
-        cudaEventCreateWithFlags(&corr_done[i], cudaEventDisableTiming);
+    cudaError_t e = g->ev.create();
+    return e == cudaSuccess ? BF_OK : cuda_fail(e, "ring events");
+}
+
+cudaError_t gen_synth_rows(const bf_bank* bank, int precision, size_t k0, size_t k1, void* slot0, void* slot1,
+                           cudaStream_t s)
+{
+    const bool tc = precision != BF_FP32;
+    const bool f16 = precision == BF_SPLIT_FP16;
+    const size_t kc = std::min(k1, bank->rows) - k0;
+    return launch_bank_synth(bank->d_params, (uint32_t)k0, bank->quad, (uint32_t)kc, (uint32_t)(k1 - k0),
+                             bank->M, bank->M_pad, bank->fs,
+                             tc ? nullptr : static_cast<float*>(slot0),
+                             tc && !f16 ? static_cast<uint8_t*>(slot0) : nullptr,
+                             tc && !f16 ? static_cast<uint8_t*>(slot1) : nullptr, s,
+                             f16 ? static_cast<uint8_t*>(slot0) : nullptr,
+                             f16 ? static_cast<uint8_t*>(slot1) : nullptr);
+}
+
+void gen_point_segment(Seg& g, int precision, size_t k0, const void* slot0, const void* slot1)
+{
+    const bool tc = precision != BF_FP32;
+    g.bank_k0 = (uint32_t)k0;
+    g.bank_f32 = tc ? nullptr : static_cast<const float*>(slot0);
+    g.bank_hi = tc ? static_cast<const uint8_t*>(slot0) : nullptr;
+    g.bank_lo = tc ? static_cast<const uint8_t*>(slot1) : nullptr;
+}
+
+size_t gen_slot_bytes(const bf_bank* bank, int precision, size_t rows)
+{
+    return rows * bank->M_pad * (precision != BF_FP32 ? 2 : 4);    // per plane (hi, lo) or FP32
+}
+
+// synthesis of chunk c of a generated bank into slot sl, on stream s
+static cudaError_t gen_synth(const bf_bank* bank, const bf_opts& o, const GenRing& g, size_t c, int sl,
+                             cudaStream_t s)
+{
+    const size_t t0 = g.t_begin + c * g.chunk_tiles;
+    const size_t t1 = std::min(t0 + g.chunk_tiles, g.t_end);
+    return gen_synth_rows(bank, o.precision, t0 * TC_TILE_T, t1 * TC_TILE_T, g.slot[sl][0], g.slot[sl][1], s);
+}
+
+// the call's segments restricted to chunk c's template tiles, reading slot sl
+static std::vector<Seg> gen_chunk_segments(const bf_bank* bank, const bf_opts& o, const std::vector<Seg>& segs,
+                                           const GenRing& g, size_t c, int sl)
+{
+    const size_t t0 = g.t_begin + c * g.chunk_tiles;
+    const size_t t1 = std::min(t0 + g.chunk_tiles, g.t_end);
+    const size_t k0 = t0 * TC_TILE_T;
+    const uint32_t tile_t = tile_templates(o.precision);
+    const size_t q0 = std::max(k0, bank_row(bank, o.bank_begin)) / tile_t;
+    const size_t q1 = ceil_div(std::min(t1 * TC_TILE_T, bank_row(bank, o.bank_end)), tile_t);
+    std::vector<Seg> cs = segs;
+    for (Seg& s : cs) {
+        s.tt0 = (uint32_t)q0;
+        s.n_tt = (uint32_t)(q1 - q0);
+        gen_point_segment(s, o.precision, k0, g.slot[sl][0], g.slot[sl][1]);
     }
+    return cs;
+}
+
+int gen_autotune(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o, const std::vector<Seg>& segs,
+                 cudaStream_t strm, GenRing& g)
+{
+    if (gen_synth(bank, o, g, 0, 0, strm) != cudaSuccess) return TC_TILE_L / 2;
+    return choose_lag_tile(ctx, gen_chunk_segments(bank, o, segs, g, 0, 0)[0], o.precision, strm);
+}
+
+cudaError_t gen_launch(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o, const std::vector<Seg>& segs,
+                       bf_result* r, cudaStream_t strm, int lt, GenRing& g)
+{
+    const RingEvents& ev = g.ev;
     // the synthesis stream starts after everything already queued on the main one
-    cudaError_t e = cudaEventRecord(ev_start, strm);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, ev_start, 0);
-    for (size_t c = 0; c < n_chunks && e == cudaSuccess; ++c) {
+    cudaError_t e = cudaEventRecord(ev.start, strm);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, ev.start, 0);
+    for (size_t c = 0; c < g.n_chunks && e == cudaSuccess; ++c) {
         const int sl = (int)(c & 1);
-        const size_t t0 = t_begin + c * chunk_tiles;
-        const size_t t1 = std::min(t0 + chunk_tiles, t_end);
-        const size_t k0 = t0 * TC_TILE_T;
-        const size_t kc = std::min(t1 * TC_TILE_T, bank->rows) - k0;
-        if (c >= 2) e = cudaStreamWaitEvent(ctx->aux, corr_done[sl], 0);
-        if (e == cudaSuccess)
-            e = launch_bank_synth(bank->d_params, (uint32_t)k0, bank->quad, (uint32_t)kc,
-                                  (uint32_t)((t1 - t0) * TC_TILE_T),
-                                  bank->M, bank->M_pad, bank->fs,
-                                  tc ? nullptr : static_cast<float*>(slot[sl][0]),
-                                  tc && !f16 ? static_cast<uint8_t*>(slot[sl][0]) : nullptr,
-                                  tc && !f16 ? static_cast<uint8_t*>(slot[sl][1]) : nullptr, ctx->aux,
-                                  f16 ? static_cast<uint8_t*>(slot[sl][0]) : nullptr,
-                                  f16 ? static_cast<uint8_t*>(slot[sl][1]) : nullptr);
-        if (e == cudaSuccess) e = cudaEventRecord(synth_done[sl], ctx->aux);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(strm, synth_done[sl], 0);
+        if (c >= 2) e = cudaStreamWaitEvent(ctx->aux, ev.used[sl], 0);
+        if (e == cudaSuccess) e = gen_synth(bank, o, g, c, sl, ctx->aux);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.made[sl], ctx->aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(strm, ev.made[sl], 0);
         if (e != cudaSuccess) break;
-        // the call's segments restricted to this chunk's template tiles
-        const uint32_t tile_t = tile_templates(o.precision);
-        const size_t q0 = std::max(k0, bank_row(bank, o.bank_begin)) / tile_t;
-        const size_t q1 = ceil_div(std::min(t1 * TC_TILE_T, bank_row(bank, o.bank_end)), tile_t);
-        std::vector<Seg> cs = segs;
-        for (Seg& g : cs) {
-            g.tt0 = (uint32_t)q0;
-            g.n_tt = (uint32_t)(q1 - q0);
-            g.bank_k0 = (uint32_t)k0;
-            g.bank_f32 = tc ? nullptr : static_cast<const float*>(slot[sl][0]);
-            g.bank_hi = tc ? static_cast<const uint8_t*>(slot[sl][0]) : nullptr;
-            g.bank_lo = tc ? static_cast<const uint8_t*>(slot[sl][1]) : nullptr;
-        }
+        std::vector<Seg> cs = gen_chunk_segments(bank, o, segs, g, c, sl);
         if (lt == 0) {
             lt = choose_lag_tile(ctx, cs[0], o.precision, strm);
             r->tile_lags = lt;
         }
         e = launch_segments(ctx, cs, o.precision, r->thr, r->cand, r->cand_count, r->cand_cap, strm,
                             nullptr, lt);
-        if (e == cudaSuccess) e = cudaEventRecord(corr_done[sl], strm);
-    }
-    // events may be destroyed while pending work still references them
-    cudaEventDestroy(ev_start);
-    for (int i = 0; i < 2; ++i) {
-        cudaEventDestroy(synth_done[i]);
-        cudaEventDestroy(corr_done[i]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.used[sl], strm);
     }
     return e;
 }
@@ -807,6 +861,8 @@ bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
         c->totals.push_back(total);
         c->batches.push_back(p);
     }
+    if (bank->generated && !c->batches.empty())
+        return fft_ring_prepare(ctx, bank, c->batches[0].k_begin, c->batches[0].k_end, r->scratch, &c->ring);
     return BF_OK;
 }
 
@@ -817,7 +873,7 @@ cudaError_t fft_launch(bf_ctx* ctx, const bf_bank* bank, FftCall& c, bf_result* 
         e = launch_fft_series(c.series[i], c.totals[i], ctx->n_sm, st);
     if (e != cudaSuccess || c.batches.empty()) return e;
     const uint32_t r0 = c.batches[0].k_begin, r1 = c.batches[0].k_end;
-    if (bank->generated) return fft_correlate_chunked(ctx, bank, c.batches, r0, r1, r->scratch, st);
+    if (bank->generated) return fft_correlate_chunked(ctx, bank, c.batches, r0, r1, c.ring, st);
     // spectra kept with the bank
     for (FftParams& p : c.batches) {
         p.hspec = bank->fspec;
@@ -1267,6 +1323,11 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
         st = fft_prepare(ctx, bank, o, prep, r, strm, &fc);
         if (st) return st;
     }
+    GenRing ring;
+    if (!fft && bank->generated) {
+        st = gen_prepare(ctx, bank, o, r, &ring);
+        if (st) return st;
+    }
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (sync) {
@@ -1281,7 +1342,7 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
     r->tile_lags = lt;
     cudaError_t e = fft ? fft_launch(ctx, bank, fc, r, strm)
                     : bank->generated
-                        ? correlate_generated(ctx, bank, o, segs, r, strm, lt)
+                        ? gen_launch(ctx, bank, o, segs, r, strm, lt, ring)
                         : launch_segments(ctx, segs, o.precision, r->thr, r->cand, r->cand_count,
                                           r->cand_cap, strm, nullptr, lt);
     if (sync) cudaEventRecord(e1, strm);

@@ -291,8 +291,9 @@ uint32_t fft_segments(uint32_t L, uint32_t M, bool quad);
 cudaError_t launch_fft_series(const FftSeriesBatch& b, uint32_t total_segments, int n_sm, cudaStream_t st);
 cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st);
 // FFT route: template spectra in chunks, for banks whose spectra are not kept (corr_fft.cu)
+struct FftRing;
 cudaError_t fft_correlate_chunked(bf_ctx* ctx, const bf_bank* bank, std::vector<FftParams>& batches,
-                                  uint32_t row_begin, uint32_t row_end, std::vector<void*>& keep,
+                                  uint32_t row_begin, uint32_t row_end, const FftRing& ring,
                                   cudaStream_t st);
 cudaError_t launch_coincidence(const float* A, const float* B, uint32_t nt, uint32_t nf, uint32_t w,
                                uint32_t dt, unsigned int* out, int n_sm, cudaStream_t s);

@@ -1183,6 +1183,12 @@ static cudaError_t template_spectra(const bf_bank* bank, size_t row0, size_t nro
     return e;
 }
 
+cudaError_t fft_template_spectra(const bf_bank* bank, size_t row0, size_t nrows, float* scratch,
+                                 size_t scratch_rows, const float2* tw, float2* out, int n_sm, cudaStream_t st)
+{
+    return template_spectra(bank, row0, nrows, scratch, scratch_rows, tw, out, n_sm, st);
+}
+
 // Spectra of every template of the bank, [rows (rounded up to even for the
 // pair route)][fft_spec_bins] complex, computed once and kept with the bank.
 bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st)
@@ -1314,68 +1320,63 @@ cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st)
 constexpr size_t FFT_CHUNK_BYTES = size_t(512) << 20;
 constexpr size_t FFT_SYNTH_ROWS = 4096;
 
+bf_status fft_ring_prepare(bf_ctx* ctx, const bf_bank* bank, uint32_t row_begin, uint32_t row_end,
+                           std::vector<void*>& keep, FftRing* ring)
+{
+    const size_t bins = fft_spec_bins(bank->quad);
+    const size_t n_rows = row_end - row_begin;
+    ring->chunk = std::min(FFT_CHUNK_BYTES / (bins * sizeof(float2)), n_rows + (n_rows & 1));
+    ring->n_chunks = (n_rows + ring->chunk - 1) / ring->chunk;
+    ring->synth_rows = std::min(FFT_SYNTH_ROWS, ring->chunk + (ring->chunk & 1));    // even
+    Allocator& mem = *ctx->mem;
+    ring->scratch = static_cast<float*>(mem.alloc(ring->synth_rows * FN * sizeof(float)));
+    if (ring->scratch) keep.push_back(ring->scratch);
+    for (int i = 0; i < 2 && i < (int)ring->n_chunks; ++i) {
+        ring->slot[i] = static_cast<float2*>(mem.alloc((ring->chunk + 2) * bins * sizeof(float2)));
+        if (ring->slot[i]) keep.push_back(ring->slot[i]);
+    }
+    if (!ring->scratch || !ring->slot[0] || (ring->n_chunks > 1 && !ring->slot[1])) {
+        set_error("out of device memory for the template-spectra ring");
+        return BF_ENOMEM;
+    }
+    cudaError_t e = ring->ev.create();
+    return e == cudaSuccess ? BF_OK : cuda_fail(e, "ring events");
+}
+
 cudaError_t fft_correlate_chunked(bf_ctx* ctx, const bf_bank* bank, std::vector<FftParams>& batches,
-                                  uint32_t row_begin, uint32_t row_end, std::vector<void*>& keep,
+                                  uint32_t row_begin, uint32_t row_end, const FftRing& ring,
                                   cudaStream_t st)
 {
     const bool quad = bank->quad;
-    const size_t bins = fft_spec_bins(quad);
-    const size_t n_rows = row_end - row_begin;
-    const size_t chunk = std::min(FFT_CHUNK_BYTES / (bins * sizeof(float2)), n_rows + (n_rows & 1));
-    const size_t n_chunks = (n_rows + chunk - 1) / chunk;
-    Allocator& mem = *ctx->mem;
-    float2* slot[2] = {nullptr, nullptr};
-    // the ring outlives this call's launches: the result releases it
-    const size_t synth_rows = std::min(FFT_SYNTH_ROWS, chunk + (chunk & 1));   // even
-    float* scratch = static_cast<float*>(mem.alloc(synth_rows * FN * sizeof(float)));
-    keep.push_back(scratch);
-    for (int i = 0; i < 2 && i < (int)n_chunks; ++i) {
-        slot[i] = static_cast<float2*>(mem.alloc((chunk + 2) * bins * sizeof(float2)));
-        keep.push_back(slot[i]);
-    }
-    if (!scratch || !slot[0] || (n_chunks > 1 && !slot[1])) {
-        set_error("out of device memory for the template-spectra ring");
-        return cudaErrorMemoryAllocation;
-    }
     const float2* tw = batches.empty() ? nullptr : batches[0].tw;
-    cudaEvent_t ev_start, made[2], used[2];
-    cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
-    for (int i = 0; i < 2; ++i) {
-        cudaEventCreateWithFlags(&made[i], cudaEventDisableTiming);
-        cudaEventCreateWithFlags(&used[i], cudaEventDisableTiming);
-    }
-    cudaError_t e = cudaEventRecord(ev_start, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, ev_start, 0);
-    for (size_t c = 0; c < n_chunks && e == cudaSuccess; ++c) {
+    const RingEvents& ev = ring.ev;
+    cudaError_t e = cudaEventRecord(ev.start, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, ev.start, 0);
+    for (size_t c = 0; c < ring.n_chunks && e == cudaSuccess; ++c) {
         const int sl = (int)(c & 1);
-        const uint32_t c0 = row_begin + (uint32_t)(c * chunk);
-        const uint32_t c1 = (uint32_t)std::min<size_t>(c0 + chunk, row_end);
+        const uint32_t c0 = row_begin + (uint32_t)(c * ring.chunk);
+        const uint32_t c1 = (uint32_t)std::min<size_t>(c0 + ring.chunk, row_end);
         // the pair route makes the spectra of the even-aligned row pairs that a
         // stored bank uses, partner rows outside the slice included (each
         // spectrum carries its partner's rounding), so the outputs equal the
         // stored bank's; the real route makes one row per transform
         const uint32_t s0 = quad ? c0 & ~1u : c0;
         const uint32_t s1 = quad ? (uint32_t)std::min<size_t>((c1 + 1) & ~1u, bank->rows) : c1;
-        if (c >= 2) e = cudaStreamWaitEvent(ctx->aux, used[sl], 0);
+        if (c >= 2) e = cudaStreamWaitEvent(ctx->aux, ev.used[sl], 0);
         if (e == cudaSuccess)
-            e = template_spectra(bank, s0, s1 - s0, scratch, synth_rows, tw, slot[sl], ctx->n_sm, ctx->aux);
-        if (e == cudaSuccess) e = cudaEventRecord(made[sl], ctx->aux);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, made[sl], 0);
+            e = template_spectra(bank, s0, s1 - s0, ring.scratch, ring.synth_rows, tw, ring.slot[sl], ctx->n_sm,
+                                 ctx->aux);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.made[sl], ctx->aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev.made[sl], 0);
         for (FftParams& p : batches) {
             if (e != cudaSuccess) break;
-            p.hspec = slot[sl];
+            p.hspec = ring.slot[sl];
             p.hrow0 = s0;
             p.k_lo = c0;
             p.k_hi = c1;
             e = launch_corr_fft(p, ctx->n_sm, st);
         }
-        if (e == cudaSuccess) e = cudaEventRecord(used[sl], st);
-    }
-    // events may be destroyed while pending work still references them
-    cudaEventDestroy(ev_start);
-    for (int i = 0; i < 2; ++i) {
-        cudaEventDestroy(made[i]);
-        cudaEventDestroy(used[i]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.used[sl], st);
     }
     return e;
 }

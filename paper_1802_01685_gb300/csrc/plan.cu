@@ -51,10 +51,6 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
     }
     *out = nullptr;
     if (bank->ctx != ctx) { set_error("bank belongs to another context"); return BF_EINVAL; }
-    if (bank->generated) {
-        set_error("plans need a stored bank (BF_BANK_FP32 and/or BF_BANK_SPLIT_BF16)");
-        return BF_ENOTSUP;
-    }
     if (std::fabs(fs - bank->fs) > 1e-9 * bank->fs) {
         set_error("series rate %g differs from the bank's %g", fs, bank->fs);
         return BF_EINVAL;
@@ -94,6 +90,7 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
     const bool fft = o.precision == BF_FFT_FP32;
     std::vector<Seg> segs;
     FftCall fc;
+    GenRing ring;
     PredictCall pc;
     int lt = 0;
     if (p->r->parseval) {
@@ -105,8 +102,9 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
     }
     if (fft) {
         // everything that allocates or synchronises happens before the capture:
-        // the bank's spectra, the twiddle tables, the segment-spectra buffers
-        st = bank_fft_spectra(ctx, const_cast<bf_bank*>(bank), strm);
+        // the bank's spectra (a generated bank: the spectra ring), the twiddle
+        // tables, the segment-spectra buffers
+        if (!bank->generated) st = bank_fft_spectra(ctx, const_cast<bf_bank*>(bank), strm);
         if (st == BF_OK) st = fft_prepare(ctx, bank, o, p->prep, p->r, strm, &fc);
         if (st) return st;
         cudaError_t es = cudaStreamSynchronize(strm);
@@ -119,12 +117,22 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
                 segs[s].sigma_pred = p->r->sigma_pred + s * p->r->K;
                 segs[s].kappa = p->r->kappa;
             }
+        if (bank->generated) {
+            // the synthesis ring, before the capture
+            st = gen_prepare(ctx, bank, o, p->r, &ring);
+            if (st) return st;
+        }
         cudaError_t es = cudaStreamSynchronize(strm);
         if (es == cudaSuccess) es = corr_tc_set_attributes();
         if (es != cudaSuccess) return cuda_fail(es, "plan set-up");
-        // the tile shape is fixed before capture (the autotuner times launches)
+        // the tile shape is fixed before capture (the autotuner times launches;
+        // for a generated bank on its first synthesised chunk)
         lt = o.precision == BF_FP32 ? SIMT_TILE_L
-                                    : (o.tile_lags ? o.tile_lags : choose_lag_tile(ctx, segs[0], o.precision, strm));
+             : o.tile_lags          ? o.tile_lags
+             : bank->generated      ? gen_autotune(ctx, bank, o, segs, strm, ring)
+                                    : choose_lag_tile(ctx, segs[0], o.precision, strm);
+        es = cudaStreamSynchronize(strm);
+        if (es != cudaSuccess) return cuda_fail(es, "plan set-up");
     }
     p->r->tile_lags = lt;
 
@@ -137,9 +145,10 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
         ec = prepare_series_kernels(p->prep[s], bank->M, o.precision, strm);
     if (ec == cudaSuccess && p->r->parseval) ec = predict_launch(ctx, bank, pc, strm);
     if (ec == cudaSuccess)
-        ec = fft ? fft_launch(ctx, bank, fc, p->r, strm)
-                 : launch_segments(ctx, segs, o.precision, p->r->thr, p->r->cand, p->r->cand_count,
-                                   p->r->cand_cap, strm, nullptr, lt);
+        ec = fft              ? fft_launch(ctx, bank, fc, p->r, strm)
+             : bank->generated ? gen_launch(ctx, bank, o, segs, p->r, strm, lt, ring)
+                               : launch_segments(ctx, segs, o.precision, p->r->thr, p->r->cand,
+                                                 p->r->cand_count, p->r->cand_cap, strm, nullptr, lt);
     bf_status fst = BF_OK;
     if (ec == cudaSuccess) fst = finalize_result(ctx, bank, p->r, strm);
     cudaGraph_t graph = nullptr;

@@ -78,12 +78,61 @@ void serve_shutdown(bf_ctx* ctx);
 
 // template half spectra of the FFT route, computed once per bank
 bf_status bank_fft_spectra(bf_ctx* ctx, bf_bank* bank, cudaStream_t st);
+// Two-slot rings in which a generated bank is synthesised chunk by chunk on
+// the context's auxiliary stream while the main stream correlates the chunk
+// before; events order the reuse of a slot after the launches that read it.
+// The *_prepare calls allocate (into the result's scratch, which outlives the
+// launches) and create the events, the launch calls only enqueue work, so a
+// plan can capture them.  The events go with the ring.
+struct RingEvents {
+    cudaEvent_t start = nullptr, made[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
+    cudaError_t create();
+    RingEvents() = default;
+    RingEvents(const RingEvents&) = delete;
+    RingEvents& operator=(const RingEvents&) = delete;
+    ~RingEvents();
+};
+// direct routes: template tiles in the correlation kernels' layout (api.cu)
+struct GenRing {
+    void* slot[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    size_t chunk_tiles = 0, n_chunks = 0, t_begin = 0, t_end = 0;
+    RingEvents ev;
+};
+// FFT route: template spectra (corr_fft.cu)
+struct FftRing {
+    float* scratch = nullptr;               // synthesised rows
+    float2* slot[2] = {nullptr, nullptr};   // spectra
+    size_t chunk = 0, synth_rows = 0, n_chunks = 0;
+    RingEvents ev;
+};
+// bank rows [k0, k1) of a generated bank (k0 a multiple of 128) synthesised
+// into the layout `precision` reads: FP32 rows at slot0, or the tensor-core
+// tiles of the hi and lo parts at slot0 and slot1 (gen_slot_bytes each)
+cudaError_t gen_synth_rows(const bf_bank* bank, int precision, size_t k0, size_t k1, void* slot0, void* slot1,
+                           cudaStream_t s);
+size_t gen_slot_bytes(const bf_bank* bank, int precision, size_t rows);
+// a segment reading the rows synthesised from k0 into slot0 / slot1
+void gen_point_segment(Seg& g, int precision, size_t k0, const void* slot0, const void* slot1);
+// template spectra of the FFT route for bank rows [row0, row0 + nrows) (corr_fft.cu)
+cudaError_t fft_template_spectra(const bf_bank* bank, size_t row0, size_t nrows, float* scratch,
+                                 size_t scratch_rows, const float2* tw, float2* out, int n_sm, cudaStream_t st);
+bf_status gen_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o, bf_result* r, GenRing* g);
+cudaError_t gen_launch(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o, const std::vector<Seg>& segs,
+                       bf_result* r, cudaStream_t strm, int lt, GenRing& g);
+// the tile shape for a generated bank: the first chunk synthesised (on strm,
+// synchronously) and the autotuner run on it; call before any capture
+int gen_autotune(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o, const std::vector<Seg>& segs,
+                 cudaStream_t strm, GenRing& g);
+bf_status fft_ring_prepare(bf_ctx* ctx, const bf_bank* bank, uint32_t row_begin, uint32_t row_end,
+                           std::vector<void*>& keep, FftRing* ring);
+
 // one call of the FFT route: per batch of series, the segment-spectra job and
-// the correlation record (api.cu)
+// the correlation record, and for a generated bank the spectra ring (api.cu)
 struct FftCall {
     std::vector<FftSeriesBatch> series;
     std::vector<uint32_t> totals;
     std::vector<FftParams> batches;
+    FftRing ring;
 };
 bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
                       const std::vector<PreparedSeries>& prep, bf_result* r, cudaStream_t st, FftCall* c);

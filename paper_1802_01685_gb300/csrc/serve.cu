@@ -62,6 +62,13 @@ struct Request {
     float2* seg_spec = nullptr;     // its segment spectra
     uint32_t* fix = nullptr;        // lags for the direct fixup [2 L], then their count
     uint32_t k_next = 0, k_stop = 0;   // template-row cursor
+    // a generated bank: this request's synthesis slot, refilled every
+    // iteration (before that iteration's launch, on the same stream) with the
+    // template tiles it correlates -- or, on the FFT route, their spectra
+    // (gslot[0]) made through the synthesised rows in gscratch
+    void* gslot[2] = {nullptr, nullptr};
+    float* gscratch = nullptr;
+    uint32_t gcap_rows = 0, gscratch_rows = 0;
 };
 
 // tiles per SM per iteration: large enough to amortise the launch, small
@@ -69,6 +76,28 @@ struct Request {
 constexpr uint64_t TILES_PER_SM = 8;
 // FFT-route transforms per SM per iteration (about as long as the tiles above)
 constexpr uint64_t TRANSFORMS_PER_SM = 100;
+// a generated bank's slot per request: template rows of one iteration on the
+// direct routes, and 128 MiB of template spectra on the FFT route
+constexpr uint32_t GEN_SERVE_ROWS = 3072;
+constexpr size_t GEN_SERVE_SPEC_BYTES = size_t(128) << 20;
+constexpr uint32_t GEN_SERVE_SYNTH_ROWS = 2048;
+
+uint32_t gen_fft_rows(const bf_bank* bank)
+{
+    return (uint32_t)(GEN_SERVE_SPEC_BYTES / (fft_spec_bins(bank->quad) * sizeof(float2))) & ~1u;
+}
+
+// device bytes of a request's synthesis slot (0 for a stored bank)
+size_t gen_serve_bytes(const bf_bank* bank, int precision)
+{
+    if (!bank->generated) return 0;
+    if (precision == BF_FFT_FP32) {
+        const size_t rows = gen_fft_rows(bank);
+        return (rows + 2) * fft_spec_bins(bank->quad) * sizeof(float2) +
+               (size_t)std::min(GEN_SERVE_SYNTH_ROWS, (uint32_t)rows) * FFT_POINTS * sizeof(float);
+    }
+    return (precision != BF_FP32 ? 2 : 1) * gen_slot_bytes(bank, precision, GEN_SERVE_ROWS);
+}
 
 }  // namespace
 
@@ -103,6 +132,12 @@ static void release_request_device(bf_ctx* ctx, Request* r)
         ctx->mem->release(r->seg_spec);
         r->seg_spec = nullptr;
     }
+    for (void*& p : r->gslot) {
+        ctx->mem->release(p);
+        p = nullptr;
+    }
+    ctx->mem->release(r->gscratch);
+    r->gscratch = nullptr;
     if (r->done) {
         cudaEventDestroy(r->done);
         r->done = nullptr;
@@ -149,8 +184,20 @@ static bool admit(ServeState* S, Request* r)
         std::lock_guard<std::mutex> g(ctx->launch_mu);
         const float2* tw = nullptr;
         cudaError_t e = fft_tables(ctx, S->stream, &tw);
-        st = e == cudaSuccess ? bank_fft_spectra(ctx, const_cast<bf_bank*>(bank), S->stream)
-                              : cuda_fail(e, "FFT tables");
+        st = e != cudaSuccess     ? cuda_fail(e, "FFT tables")
+             : bank->generated ? BF_OK
+                               : bank_fft_spectra(ctx, const_cast<bf_bank*>(bank), S->stream);
+        if (st == BF_OK && bank->generated) {
+            // the spectra slot and the rows it is made through
+            r->gcap_rows = gen_fft_rows(bank);
+            r->gscratch_rows = std::min(GEN_SERVE_SYNTH_ROWS, r->gcap_rows);
+            r->gslot[0] = ctx->mem->alloc((size_t)(r->gcap_rows + 2) * fft_spec_bins(bank->quad) * sizeof(float2));
+            r->gscratch = static_cast<float*>(ctx->mem->alloc((size_t)r->gscratch_rows * FFT_POINTS * sizeof(float)));
+            if (!r->gslot[0] || !r->gscratch) {
+                set_error("out of device memory for the request's template spectra");
+                st = BF_ENOMEM;
+            }
+        }
         const bool quad = bank->quad;
         const uint32_t nseg = fft_segments(r->prep.L, bank->M, quad);
         if (st == BF_OK) {
@@ -223,6 +270,22 @@ static bool admit(ServeState* S, Request* r)
             return false;
         }
     }
+    if (bank->generated && !r->fft) {
+        // the template-tile slot of the direct routes
+        const int planes = r->opts.precision != BF_FP32 ? 2 : 1;
+        r->gcap_rows = GEN_SERVE_ROWS;
+        for (int i = 0; i < planes; ++i) {
+            r->gslot[i] = ctx->mem->alloc(gen_slot_bytes(bank, r->opts.precision, GEN_SERVE_ROWS));
+            if (!r->gslot[i]) {
+                set_error("out of device memory for the request's synthesis slot");
+                r->status = BF_ENOMEM;
+                r->error = bf_last_error();
+                release_request_device(ctx, r);
+                bf_result_destroy(res);
+                return false;
+            }
+        }
+    }
     r->result = res;
     const uint32_t tile_t = tile_templates(r->opts.precision);
     r->tt_next = (uint32_t)(bank_row(r->bank, r->opts.bank_begin) / tile_t);
@@ -290,10 +353,21 @@ static void scheduler(ServeState* S)
             uint64_t per = std::max<uint64_t>(1, budget / std::max<uint64_t>(1, n_work));
             uint64_t ntt = std::max<uint64_t>(1, per / std::max<uint32_t>(1, r->n_lag_tiles));
             ntt = std::min<uint64_t>(ntt, r->tt_end - r->tt_next);
+            const uint32_t tile_t = tile_templates(r->opts.precision);
+            if (r->bank->generated)     // the rows synthesised (from a multiple of 128) fit the slot
+                ntt = std::min<uint64_t>(ntt, (r->gcap_rows - (tile_t < TC_TILE_T ? TC_TILE_T : 0)) / tile_t);
             bf_result* res = r->result;
             Seg g = make_segment(r->prep, 0, r->bank, r->opts.bank_begin, r->opts.bank_end,
                                  r->tt_next, (uint32_t)ntt, r->opts.precision, res->packed,
                                  res->sumsq);
+            if (r->bank->generated) {
+                const size_t k0 = (size_t)r->tt_next * tile_t / TC_TILE_T * TC_TILE_T;
+                const size_t k1 = ceil_div((size_t)(r->tt_next + ntt) * tile_t, (size_t)TC_TILE_T) * TC_TILE_T;
+                cudaError_t e = gen_synth_rows(r->bank, r->opts.precision, k0, k1, r->gslot[0], r->gslot[1],
+                                               S->stream);
+                if (e != cudaSuccess) { r->status = cuda_fail(e, "serve synthesis"); r->cancel = true; }
+                gen_point_segment(g, r->opts.precision, k0, r->gslot[0], r->gslot[1]);
+            }
             if (res->parseval) {
                 g.sigma_pred = res->sigma_pred;
                 g.kappa = res->kappa;
@@ -343,11 +417,20 @@ static void scheduler(ServeState* S)
                                                            std::max<uint64_t>(1, n_work));
             const uint64_t items = std::max<uint64_t>((uint64_t)ctx->n_sm, per / std::max<uint32_t>(1, r->fp.ser[0].nseg));
             const uint64_t want = r->fp.quad ? 2 * items : items;
-            const uint32_t rows = (uint32_t)std::min<uint64_t>(want, r->k_stop - r->k_next);
+            uint32_t rows = (uint32_t)std::min<uint64_t>(want, r->k_stop - r->k_next);
+            if (r->bank->generated) rows = std::min(rows, r->gcap_rows);         // even, as k_next
             FftParams p = r->fp;
             p.k_lo = r->k_next;
             p.k_hi = r->k_next + rows;
-            cudaError_t e = launch_corr_fft(p, ctx->n_sm, S->stream);
+            cudaError_t e = cudaSuccess;
+            if (r->bank->generated) {
+                // this iteration's template spectra (a pair route's rows start even)
+                e = fft_template_spectra(r->bank, r->k_next, rows, r->gscratch, r->gscratch_rows, p.tw,
+                                         static_cast<float2*>(r->gslot[0]), ctx->n_sm, S->stream);
+                p.hspec = static_cast<const float2*>(r->gslot[0]);
+                p.hrow0 = r->k_next;
+            }
+            if (e == cudaSuccess) e = launch_corr_fft(p, ctx->n_sm, S->stream);
             if (e != cudaSuccess) { r->status = cuda_fail(e, "serve launch"); r->cancel = true; }
             r->k_next += rows;
             if (r->k_next >= r->k_stop) finishing.push_back(r);
@@ -478,10 +561,6 @@ bf_status bf_serve_submit(bf_ctx* ctx, const bf_request* req, uint64_t* ticket)
     }
     const bf_bank* bank = req->bank;
     if (bank->ctx != ctx) { set_error("bank belongs to another context"); return BF_EINVAL; }
-    if (bank->generated) {
-        set_error("serving needs a stored bank (BF_BANK_FP32 and/or BF_BANK_SPLIT_BF16)");
-        return BF_ENOTSUP;
-    }
     if (std::fabs(req->fs - bank->fs) > 1e-9 * bank->fs) {
         set_error("request rate %g differs from the bank's %g", req->fs, bank->fs);
         return BF_EINVAL;
@@ -503,7 +582,8 @@ bf_status bf_serve_submit(bf_ctx* ctx, const bf_request* req, uint64_t* ticket)
     r->bank = bank;
     r->opts = o;
     r->bytes = prepared_series_bytes(req->n, bank->M, bank->M_pad, o.precision) +
-               result_bytes(bank, o, req->n, req->fs, ctx->cfg.max_candidates);
+               result_bytes(bank, o, req->n, req->fs, ctx->cfg.max_candidates) +
+               gen_serve_bytes(bank, o.precision);
     if (r->bytes > ctx->mem->budget()) {
         set_error("request needs %zu bytes, over the budget of %zu", r->bytes, ctx->mem->budget());
         return BF_ENOMEM;

@@ -135,9 +135,7 @@ def test_full_size_gw_pair_sampled(ctx):
 
 
 def test_rejections(ctx):
-    """Templates longer than half a transform answer BF_ENOTSUP; plans and
-    the serving loop take the FFT route only with a bank that keeps its
-    spectra."""
+    """Templates longer than half a transform answer BF_ENOTSUP."""
     fs = 8192.0
     bank = bf.bf_bank_create(ctx, [(bf.BF_LINEAR, bf.BF_ASC, 100.0, 2000.0, 1.0)], fs, 1.0)
     x = np.random.default_rng(1).standard_normal(20000).astype(np.float32)
@@ -145,15 +143,6 @@ def test_rejections(ctx):
         run(ctx, bank, [x], fs, PREC)
     assert e.value.status == bf.BF_ENOTSUP
     bf.bf_bank_destroy(bank)
-    w = synth.tiny()
-    gen = bf.bf_bank_create_grid(ctx, w["grid"], w["fs"], 1.0, bf.BF_BANK_GENERATED)
-    with pytest.raises(bf.BFError) as e:
-        bf.bf_plan_create(ctx, gen, [8192], w["fs"], bf.make_opts(precision=PREC))
-    assert e.value.status == bf.BF_ENOTSUP
-    with pytest.raises(bf.BFError) as e:
-        bf.bf_serve_submit(ctx, gen, w["series"][0], w["fs"], bf.make_opts(precision=PREC))
-    assert e.value.status == bf.BF_ENOTSUP
-    bf.bf_bank_destroy(gen)
 
 
 def test_generated_bank_in_chunks(ctx):
@@ -182,6 +171,45 @@ def test_generated_bank_in_chunks(ctx):
     assert np.abs(s["max"].astype(np.float64) - g["max"]).max() <= 2 * TOL[PREC]
     assert np.abs(s["sigma"].astype(np.float64) - g["sigma"]).max() <= 2 * TOL[PREC]
     bf.bf_bank_destroy(stored)
+    bf.bf_bank_destroy(gen)
+
+
+def test_plan_on_generated_bank_in_chunks(ctx):
+    """A plan on a 20,000-template generated bank captures the spectra ring
+    (three chunks of 8,192 rows made on the auxiliary stream) in its graph:
+    replays equal bf_correlate on the same bank bit for bit, and the oracle
+    around the chunk edges."""
+    fs, M = 2048.0, 2048
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0], 20.0,
+                           1000.0, 50, 100)                      # 20,000 templates
+    gen = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_GENERATED)
+    p = oracle_params(spec)
+    b0 = 7
+    idx = np.array([0, 8191, 8192, 16383, 16384, 19992])
+    opts = bf.make_opts(precision=PREC, bank_begin=b0, want_tails=True, kappa=4.0)
+    lens = [12000, 3000]
+    plan = bf.bf_plan_create(ctx, gen, lens, fs, opts)
+    try:
+        for run_i in range(2):
+            rng = np.random.default_rng(230 + run_i)
+            xs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+            res = bf.bf_plan_run(plan, xs)
+            got = [bf.bf_result_copy_to_host(res, s) for s in range(len(lens))]
+            got_t = np.sort(bf.bf_result_copy_tails(res), order=["series", "k", "tau"])
+            ref_h = bf.bf_correlate(ctx, gen, xs, fs, opts)
+            ref = [bf.bf_result_copy_to_host(ref_h, s) for s in range(len(lens))]
+            ref_t = np.sort(bf.bf_result_copy_tails(ref_h), order=["series", "k", "tau"])
+            bf.bf_result_destroy(ref_h)
+            for g, r in zip(got, ref):
+                np.testing.assert_array_equal(g["max"], r["max"])
+                np.testing.assert_array_equal(g["argmax"], r["argmax"])
+                np.testing.assert_array_equal(g["hist"], r["hist"])
+            np.testing.assert_array_equal(got_t, ref_t)
+            o = oracle.search(xs[0], fs, subset(p, idx + b0), M, want_rho=True)
+            gs = {k: v[idx] for k, v in got[0].items() if k in ("max", "argmax", "sigma")}
+            check_maxima(gs, o, o["rho"], TOL[PREC], "plan, chunk edges")
+    finally:
+        bf.bf_plan_destroy(plan)
     bf.bf_bank_destroy(gen)
 
 

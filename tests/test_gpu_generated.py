@@ -75,8 +75,85 @@ def test_generated_against_oracle(ctx, banks):
     check_maxima(g, ref, ref["rho"], TOL["split_bf16"], "generated")
 
 
-def test_serving_rejects_generated_bank(ctx, banks):
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "split_fp16", "fft_fp32"])
+def test_plan_on_generated_bank(ctx, banks, prec):
+    """A plan on a generated bank captures its synthesis ring in the graph
+    (template chunks, or their spectra, made on the auxiliary stream; three
+    chunks for the direct routes here): each replay equals bf_correlate on
+    the stored bank bit for bit (on the generated bank for the routes whose
+    layout the stored bank lacks), and the oracle on templates around the
+    chunk edges."""
     spec, stored, gen = banks
-    with pytest.raises(bf.BFError) as e:
-        bf.bf_serve_submit(ctx, gen, np.zeros(4096, np.float32), 2048.0)
-    assert e.value.status == bf.BF_ENOTSUP
+    p = oracle_params(spec)
+    lens = [5000, 2049]
+    b0, b1 = 7, 8000
+    opts = bf.make_opts(precision=prec, bank_begin=b0, bank_end=b1, want_map=True, kappa=4.0,
+                        want_tails=True)
+    ref_bank = stored if prec in ("split_bf16", "fp32", "bf16") else gen
+    idx = np.array([0, 1, 3064, 3065, 3066, 6136, 6137, 7992])    # chunk edges at 3065, 6137
+    plan = bf.bf_plan_create(ctx, gen, lens, 2048.0, opts)
+    try:
+        for run_i in range(2):
+            rng = np.random.default_rng(900 + run_i)
+            xs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+            res = bf.bf_plan_run(plan, xs)
+            got = [bf.bf_result_copy_to_host(res, s, want_hist=True, want_map=True) for s in range(2)]
+            got_t = np.sort(bf.bf_result_copy_tails(res), order=["series", "k", "tau"])
+            ref_h = bf.bf_correlate(ctx, ref_bank, xs, 2048.0, opts)
+            ref = [bf.bf_result_copy_to_host(ref_h, s, want_hist=True, want_map=True) for s in range(2)]
+            ref_t = np.sort(bf.bf_result_copy_tails(ref_h), order=["series", "k", "tau"])
+            bf.bf_result_destroy(ref_h)
+            for g, r in zip(got, ref):
+                np.testing.assert_array_equal(g["max"], r["max"])
+                np.testing.assert_array_equal(g["argmax"], r["argmax"])
+                np.testing.assert_allclose(g["sigma"], r["sigma"], rtol=1e-6)
+                np.testing.assert_array_equal(g["hist"], r["hist"])
+                np.testing.assert_array_equal(g["map"], r["map"])
+            np.testing.assert_array_equal(got_t, ref_t)
+            for x, g in zip(xs, got):
+                o = oracle.search(x, 2048.0, subset(p, idx + b0), 2048, want_rho=True)
+                gs = {k: g[k][idx] for k in ("max", "argmax", "sigma")}
+                check_maxima(gs, o, o["rho"], TOL[prec], f"plan {prec}")
+    finally:
+        bf.bf_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "bf16", "split_fp16", "fft_fp32"])
+def test_serving_generated_bank(ctx, banks, prec):
+    """Requests on a generated bank are served with a synthesis slot of their
+    own, refilled every iteration with the template tiles (or, on the FFT
+    route, their spectra) that iteration correlates.  Three requests served
+    together, over bank slices that take several iterations each: every
+    result equals bf_correlate on the stored bank bit for bit (on the
+    generated bank for the routes whose layout the stored bank lacks), and
+    the oracle on sampled templates."""
+    spec, stored, gen = banks
+    p = oracle_params(spec)
+    ref_bank = stored if prec in ("split_bf16", "fp32", "bf16") else gen
+    rng = np.random.default_rng(55)
+    reqs = [(rng.standard_normal(n).astype(np.float32), b0, b1)
+            for n, b0, b1 in ((6000, 0, 8192), (3000, 101, 5000), (9000, 3000, 8000))]
+    opts = [bf.make_opts(precision=prec, bank_begin=b0, bank_end=b1, want_map=True, kappa=4.0,
+                         want_tails=True) for _, b0, b1 in reqs]
+    tickets = [bf.bf_serve_submit(ctx, gen, x, 2048.0, o) for (x, _, _), o in zip(reqs, opts)]
+    for t, (x, b0, b1), o in zip(tickets, reqs, opts):
+        st, res = bf.bf_serve_poll(ctx, t, 120_000_000)
+        assert st == bf.BF_OK
+        got = bf.bf_result_copy_to_host(res, 0, want_hist=True, want_map=True)
+        got_t = np.sort(bf.bf_result_copy_tails(res), order=["k", "tau"])
+        bf.bf_result_destroy(res)
+        ref_h = bf.bf_correlate(ctx, ref_bank, [x], 2048.0, o)
+        ref = bf.bf_result_copy_to_host(ref_h, 0, want_hist=True, want_map=True)
+        ref_t = np.sort(bf.bf_result_copy_tails(ref_h), order=["k", "tau"])
+        bf.bf_result_destroy(ref_h)
+        np.testing.assert_array_equal(got["max"], ref["max"])
+        np.testing.assert_array_equal(got["argmax"], ref["argmax"])
+        np.testing.assert_allclose(got["sigma"], ref["sigma"], rtol=1e-6)
+        np.testing.assert_array_equal(got["hist"], ref["hist"])
+        np.testing.assert_array_equal(got["map"], ref["map"])
+        np.testing.assert_array_equal(got_t, ref_t)
+        n = b1 - b0
+        idx = np.unique(np.clip(np.array([0, 1, 3071 - b0, 3072 - b0, 6143 - b0, 6144 - b0, n - 1]), 0, n - 1))
+        o_ref = oracle.search(x, 2048.0, subset(p, idx + b0), 2048, want_rho=True)
+        gs = {k: got[k][idx] for k in ("max", "argmax", "sigma")}
+        check_maxima(gs, o_ref, o_ref["rho"], TOL[prec], f"served {prec}")

@@ -141,13 +141,8 @@ def test_plan_on_a_stream_and_launch_count(setup):
     bf.bf_plan_destroy(plan)
 
 
-def test_plan_rejects_generated_bank_and_bad_lengths(setup):
+def test_plan_rejects_bad_lengths(setup):
     ctx, bank, spec = setup
-    gen = bf.bf_bank_create_grid(ctx, spec, 2048.0, 1.0, bf.BF_BANK_GENERATED)
-    with pytest.raises(bf.BFError) as e:
-        bf.bf_plan_create(ctx, gen, [4096], 2048.0)
-    assert e.value.status == bf.BF_ENOTSUP
-    bf.bf_bank_destroy(gen)
     with pytest.raises(bf.BFError) as e:
         bf.bf_plan_create(ctx, bank, [100], 2048.0)
     assert e.value.status == bf.BF_EINVAL
