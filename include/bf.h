@@ -284,9 +284,12 @@ void bf_opts_default(bf_opts* opts);
  * Samples must be finite.  The window energies come from a running sum of
  * x^2, so one NaN or infinity leaves rho undefined at every later lag of its
  * series, not only in the windows that hold it; mark gaps with zeros (an
- * all-zero window gives rho = 0).  A synchronous call (opts->stream NULL)
- * checks this after the search and then returns BF_EINVAL with no result;
- * calls on a stream, plans and served requests do not check.
+ * all-zero window gives rho = 0).  The series preparation flags a series
+ * whose FP64 total of x^2 is not finite in the result's status word: a
+ * synchronous call (opts->stream NULL) reads it after the search and then
+ * returns BF_EINVAL with no result; after a call on a stream, or a plan run
+ * on a stream, bf_result_check reads it once the stream has synchronised; a
+ * served request fails with BF_EINVAL.
  * BF_EINVAL on a bad length, rate, range, a precision whose layout the bank
  * lacks, or a non-finite sample; BF_EDEVICE if a kernel reported an internal
  * timeout.
@@ -312,6 +315,13 @@ typedef struct {
     int32_t tile_lags;             /* lags per tile of the kernel that ran      */
 } bf_result_info;
 
+/* Status of a result whose work has completed (for calls and plan runs on a
+ * caller's stream, after that stream has synchronised; the paper has no
+ * counterpart): BF_EINVAL if a series held a NaN or infinite sample (its
+ * outputs are then undefined), BF_EDEVICE if a kernel of the context reported
+ * a timed-out wait (the context's status word is then cleared), BF_OK
+ * otherwise.  Reads device memory synchronously. */
+bf_status bf_result_check(const bf_result* r);
 /* Copies the summary to *info.  BF_EINVAL for NULL arguments. */
 bf_status bf_result_info_get(const bf_result* r, bf_result_info* info);
 /* Time-frequency map of series s (Sect. 2.1: chirp-based spectrograms that

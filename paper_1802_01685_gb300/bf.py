@@ -130,6 +130,7 @@ def load() -> C.CDLL:
             "bf_opts_default": (None, [P(bf_opts)]),
             "bf_correlate": (i, [p, p, P(p), P(s), s, d, P(bf_opts), P(p)]),
             "bf_result_info_get": (i, [p, P(bf_result_info)]),
+            "bf_result_check": (i, [p]),
             "bf_result_map_shape": (i, [p, s, P(s), P(s)]),
             "bf_result_get_max": (i, [p, s, P(p), P(p), P(p)]),
             "bf_result_get_hist": (i, [p, s, P(p)]),
@@ -301,6 +302,12 @@ def bf_correlate(ctx: int, bank: int, series, fs: float, opts: bf_opts | None = 
     _check(load().bf_correlate(ctx, bank, ptrs, lens, n, fs,
                                C.byref(opts) if opts is not None else None, C.byref(h)))
     return h.value
+
+
+def bf_result_check(res: int) -> None:
+    """Raises BFError (BF_EINVAL) if a series of the finished result held a
+    non-finite sample, (BF_EDEVICE) if a kernel reported a timed-out wait."""
+    _check(load().bf_result_check(res))
 
 
 def bf_result_info_get(res: int) -> bf_result_info:

@@ -218,7 +218,7 @@ cudaError_t prepare_series_kernels(const PreparedSeries& ps, uint32_t M, int pre
                                    cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(ps.x + ps.N, 0, (ps.xcap - ps.N) * sizeof(float), st);
-    if (e == cudaSuccess) e = launch_inv_norm(ps.x, ps.N, M, ps.prefix, ps.bsum, ps.nb, ps.inv, st);
+    if (e == cudaSuccess) e = launch_inv_norm(ps.x, ps.N, M, ps.prefix, ps.bsum, ps.nb, ps.inv, st, ps.status);
     if (e == cudaSuccess && precision == BF_SPLIT_FP16)
         e = launch_split_rows_f16(ps.x, ps.N, ps.rows, ps.yhi, ps.ylo, ps.xmax, st);
     else if (e == cudaSuccess && uses_split_rows(precision))
@@ -227,10 +227,11 @@ cudaError_t prepare_series_kernels(const PreparedSeries& ps, uint32_t M, int pre
 }
 
 bf_status prepare_series(bf_ctx* ctx, const float* src, size_t N, uint32_t M, uint32_t M_pad,
-                         int precision, cudaStream_t st, PreparedSeries* out)
+                         int precision, cudaStream_t st, PreparedSeries* out, unsigned int* status)
 {
     bf_status s = prepare_series_alloc(ctx, N, M, M_pad, precision, out);
     if (s) return s;
+    out->status = status;
     cudaError_t e = cudaMemcpyAsync(out->x, src, N * sizeof(float), cudaMemcpyDefault, st);
     if (e == cudaSuccess) e = prepare_series_kernels(*out, M, precision, st);
     if (e != cudaSuccess) {
@@ -425,6 +426,7 @@ static void free_result_buffers(bf_result* r)
     r->mean_max = nullptr;
     r->cand = nullptr;
     r->cand_count = nullptr;
+    r->status = nullptr;
 }
 
 void map_shape(size_t N, double fs, double dt, double df, uint32_t* nt, uint32_t* nf)
@@ -523,7 +525,8 @@ bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
     if (!r->want_map && !r->want_tails) r->cand_cap = 0;
     r->cand = static_cast<Candidate*>(mem.alloc(std::max<size_t>(r->cand_cap, 1) * sizeof(Candidate)));
     if (r->parseval) r->sigma_pred = static_cast<float*>(mem.alloc(S * K * 4));
-    r->cand_count = static_cast<unsigned int*>(mem.alloc(sizeof(unsigned int)));
+    r->cand_count = static_cast<unsigned int*>(mem.alloc(2 * sizeof(unsigned int)));
+    r->status = r->cand_count ? r->cand_count + 1 : nullptr;
     bool ok = r->packed && r->sumsq && r->vmax && r->argmax && r->sigma && r->mean_max && r->cand &&
               r->cand_count && (!r->parseval || r->sigma_pred);
     if (ok && r->want_hist) {
@@ -580,7 +583,7 @@ cudaError_t clear_result(bf_result* r, cudaStream_t st)
     const size_t S = r->n_series, K = r->K;
     cudaError_t e = cudaMemsetAsync(r->packed, 0, S * K * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->sumsq, 0, S * K * 8, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(r->cand_count, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->cand_count, 0, 2 * sizeof(unsigned int), st);
     if (e == cudaSuccess && r->hist) e = cudaMemsetAsync(r->hist, 0, S * r->nbins * 4, st);
     if (e == cudaSuccess && r->map) e = cudaMemsetAsync(r->map, 0, r->map_total * 4, st);
     return e;
@@ -758,6 +761,18 @@ cudaError_t gen_launch(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o, const
         if (e == cudaSuccess) e = cudaEventRecord(ev.used[sl], strm);
     }
     return e;
+}
+
+bf_status result_status(const bf_result* r)
+{
+    unsigned int w = 0;
+    cudaError_t e = cudaMemcpy(&w, r->status, sizeof w, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the result status");
+    if (w & 1u) {
+        set_error("a series holds a non-finite sample (NaN or infinity)");
+        return BF_EINVAL;
+    }
+    return BF_OK;
 }
 
 bf_status check_device_status(bf_ctx* ctx)
@@ -1280,7 +1295,8 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
     std::vector<PreparedSeries*> pptr;
     std::vector<uint32_t> ids;
     for (size_t s = 0; s < n_series; ++s) {
-        st = prepare_series(ctx, series[s], lengths[s], bank->M, bank->M_pad, o.precision, strm, &prep[s]);
+        st = prepare_series(ctx, series[s], lengths[s], bank->M, bank->M_pad, o.precision, strm, &prep[s],
+                            r->status);
         if (st) {
             for (auto& p : prep) p.release(*ctx->mem);
             return st;
@@ -1365,18 +1381,18 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
         if (e != cudaSuccess) return cuda_fail(e, "correlation");
         st = check_device_status(ctx);
         if (st) return st;
-        // every sample must be finite: the FP64 total of x^2 (the prefix's last
-        // entry; at most 2^32 squares of floats, far below the FP64 range) is
-        // finite exactly then
-        for (size_t s = 0; s < n_series; ++s) {
+        // every sample must be finite (the series preparation flags it)
+        st = result_status(r);
+        for (size_t s = 0; st == BF_EINVAL && s < n_series; ++s) {
+            // name the series: the one whose FP64 total of x^2 is not finite
             double total = 0.0;
-            e = cudaMemcpy(&total, prep[s].prefix + prep[s].N, sizeof total, cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) return cuda_fail(e, "series check");
-            if (!std::isfinite(total)) {
+            if (cudaMemcpy(&total, prep[s].prefix + prep[s].N, sizeof total, cudaMemcpyDeviceToHost) ==
+                    cudaSuccess && !std::isfinite(total)) {
                 set_error("series %zu holds a non-finite sample (NaN or infinity)", s);
-                return BF_EINVAL;
+                break;
             }
         }
+        if (st) return st;
         unsigned int cnt = 0;
         cudaMemcpy(&cnt, r->cand_count, sizeof cnt, cudaMemcpyDeviceToHost);
         r->n_candidates = cnt;
@@ -1385,6 +1401,14 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
     }
     *out = guard.release();
     return BF_OK;
+}
+
+bf_status bf_result_check(const bf_result* r)
+{
+    if (!r) { set_error("NULL argument"); return BF_EINVAL; }
+    cudaSetDevice(r->ctx->device);
+    bf_status st = check_device_status(r->ctx);
+    return st ? st : result_status(r);
 }
 
 bf_status bf_result_info_get(const bf_result* r, bf_result_info* info)

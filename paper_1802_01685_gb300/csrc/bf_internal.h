@@ -246,9 +246,11 @@ __host__ __device__ inline int f16_series_shift(uint32_t max_bits)
     const int s = 13 - e;                              // >= 13 - 127 = -114
     return s > 118 ? 118 : s;
 }
+// status (if not NULL): bit 0 set when the FP64 total of x^2 is not finite,
+// i.e. when a sample is NaN or infinite
 cudaError_t launch_inv_norm(const float* x, uint64_t N, uint32_t M, double* prefix,
                             double* block_scratch, uint64_t n_blocks_cap, float* inv,
-                            cudaStream_t s);
+                            cudaStream_t s, unsigned int* status = nullptr);
 uint64_t inv_norm_scratch_blocks(uint64_t N);
 // bytes of the prefix scratch: FP64 energies S[0..N], then uint32 counts C[0..N]
 size_t prefix_bytes(uint64_t N);
@@ -403,6 +405,9 @@ struct bf_result {
     float* mean_max = nullptr;              // [K]
     bfi::Candidate* cand = nullptr;
     unsigned int* cand_count = nullptr;
+    // device word after cand_count, zeroed with it: bit 0 is set by the series
+    // preparation when a series holds a non-finite sample
+    unsigned int* status = nullptr;
     unsigned int cand_cap = 0;
     uint64_t n_candidates = 0;
     float thr = 0;

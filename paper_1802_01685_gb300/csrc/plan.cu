@@ -83,6 +83,7 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
     for (size_t s = 0; s < n_series; ++s) {
         st = prepare_series_alloc(ctx, lengths[s], bank->M, bank->M_pad, o.precision, &p->prep[s]);
         if (st) return st;
+        p->prep[s].status = p->r->status;           // non-finite samples, per run
         pptr.push_back(&p->prep[s]);
         ids.push_back((uint32_t)s);
         p->r->correlations += (double)p->prep[s].L * (double)p->r->K * (bank->quad ? 2.0 : 1.0);
@@ -208,6 +209,8 @@ bf_status bf_plan_run(bf_plan* p, const float* const* series, void* stream, cons
         unsigned int c = 0;
         cudaMemcpy(&c, p->r->cand_count, sizeof c, cudaMemcpyDeviceToHost);
         p->r->n_candidates = c;
+        st = result_status(p->r);               // non-finite samples
+        if (st) return st;
     }
     *out = p->r;
     return BF_OK;

@@ -223,10 +223,14 @@ __global__ void __launch_bounds__(SCAN_T) k_prefix(const float* __restrict__ x, 
 // few ulps of S[t+M]; where the window holds less than 2^-30 of the energy
 // before it (a quiet stretch after loud data) that would be a relative error
 // above ~5e-6, so such windows are summed directly (x^2 is exact in FP64).
+// The first thread also reports a non-finite series: the FP64 total of x^2
+// (at most 2^32 squares of floats, far below the FP64 range) is finite
+// exactly when every sample is.
 __global__ void k_inv_norm(const float* __restrict__ x, const double* __restrict__ S,
                            const uint32_t* __restrict__ C, uint64_t L, uint32_t M,
-                           float* __restrict__ inv)
+                           float* __restrict__ inv, unsigned int* __restrict__ status)
 {
+    if (status && blockIdx.x == 0 && threadIdx.x == 0 && !isfinite(S[L + M - 1])) atomicOr(status, 1u);
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < L;
          t += (uint64_t)gridDim.x * blockDim.x) {
         double nu = S[t + M] - S[t];
@@ -247,7 +251,7 @@ size_t prefix_bytes(uint64_t N) { return (N + 1) * (sizeof(double) + sizeof(uint
 
 cudaError_t launch_inv_norm(const float* x, uint64_t N, uint32_t M, double* prefix,
                             double* block_scratch, uint64_t n_blocks_cap, float* inv,
-                            cudaStream_t s)
+                            cudaStream_t s, unsigned int* status)
 {
     uint64_t nb = (N + SCAN_B - 1) / SCAN_B;
     if (nb == 0 || 2 * nb > n_blocks_cap || N < M) return cudaErrorInvalidValue;
@@ -259,7 +263,7 @@ cudaError_t launch_inv_norm(const float* x, uint64_t N, uint32_t M, double* pref
     uint64_t L = N - M + 1;
     uint64_t blocks = (L + 255) / 256;
     if (blocks > 65535ull * 16) blocks = 65535ull * 16;
-    k_inv_norm<<<(unsigned)blocks, 256, 0, s>>>(x, prefix, counts, L, M, inv);
+    k_inv_norm<<<(unsigned)blocks, 256, 0, s>>>(x, prefix, counts, L, M, inv, status);
     return cudaGetLastError();
 }
 

@@ -21,12 +21,13 @@ struct PreparedSeries {
     uint32_t* xmax = nullptr;       // split-FP16 rows: float bits of max |x|
     double* bsum = nullptr;         // scan block sums (scratch)
     uint64_t xcap = 0, nb = 0, rows = 0;
+    unsigned int* status = nullptr; // the result's status word (non-finite samples)
     std::vector<void*> owned;       // every buffer, prefix scratch included
     void release(Allocator& mem);
 };
 
 bf_status prepare_series(bf_ctx* ctx, const float* src, size_t N, uint32_t M, uint32_t M_pad,
-                         int precision, cudaStream_t st, PreparedSeries* out);
+                         int precision, cudaStream_t st, PreparedSeries* out, unsigned int* status);
 // the two halves of prepare_series: buffers, then the kernels that fill them
 // from ps.x[0..N)
 bf_status prepare_series_alloc(bf_ctx* ctx, size_t N, uint32_t M, uint32_t M_pad, int precision,
@@ -73,6 +74,9 @@ bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
 size_t result_bytes(const bf_bank* bank, const bf_opts& o, size_t N, double fs, size_t max_cand);
 bf_status finalize_result(bf_ctx* ctx, const bf_bank* bank, bf_result* r, cudaStream_t st);
 bf_status check_device_status(bf_ctx* ctx);
+// BF_EINVAL if the result's status word says a series held a non-finite
+// sample (reads it synchronously: call after the result's work is done)
+bf_status result_status(const bf_result* r);
 
 void serve_shutdown(bf_ctx* ctx);
 

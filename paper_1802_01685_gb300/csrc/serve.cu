@@ -154,7 +154,7 @@ static bool admit(ServeState* S, Request* r)
     bf_status st = alloc_result(ctx, bank, r->opts, len, r->fs, S->stream, &res);
     if (st == BF_OK) {
         st = prepare_series(ctx, r->host.data(), r->host.size(), bank->M, bank->M_pad,
-                            r->opts.precision, S->stream, &r->prep);
+                            r->opts.precision, S->stream, &r->prep, res->status);
         if (st != BF_OK) bf_result_destroy(res);
     }
     if (st != BF_OK) {
@@ -480,14 +480,23 @@ static void scheduler(ServeState* S)
                         r->result = nullptr;
                         r->state = R_CANCELED;
                         ++S->cancelled;
-                    } else if (r->status != BF_OK || dev != BF_OK) {
+                        continue;
+                    }
+                    // the candidate count, then the status word (non-finite samples)
+                    unsigned int w[2] = {0, 0};
+                    if (r->status == BF_OK && dev == BF_OK &&
+                        cudaMemcpy(w, r->result->cand_count, sizeof w, cudaMemcpyDeviceToHost) != cudaSuccess)
+                        r->status = BF_ECUDA;
+                    if (r->status == BF_OK && dev == BF_OK && (w[1] & 1u)) {
+                        r->status = BF_EINVAL;
+                        r->error = "the request's series holds a non-finite sample (NaN or infinity)";
+                    }
+                    if (r->status != BF_OK || dev != BF_OK) {
                         bf_result_destroy(r->result);
                         r->result = nullptr;
                         r->state = R_FAILED;
                     } else {
-                        unsigned int c = 0;
-                        cudaMemcpy(&c, r->result->cand_count, sizeof c, cudaMemcpyDeviceToHost);
-                        r->result->n_candidates = c;
+                        r->result->n_candidates = w[0];
                         r->state = R_DONE;
                         r->t_done = t;
                         ++S->completed;

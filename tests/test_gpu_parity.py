@@ -659,6 +659,57 @@ def test_non_finite_samples_are_refused(ctx, tiny, prec):
         np.testing.assert_array_equal(got[key], want[key])
 
 
+@pytest.mark.parametrize("prec", ["split_bf16", "fft_fp32"])
+def test_non_finite_samples_on_asynchronous_paths(ctx, tiny, prec):
+    """A series holding a NaN through a call on a stream, a plan (run
+    synchronously and on a stream) and a served request: the calls on a
+    stream report BF_EINVAL through bf_result_check once the stream has
+    synchronised, the synchronous plan run returns it, and the served request
+    fails with it.  Finite series before and after check clean, on the same
+    plan and context."""
+    w, bank, _, _ = tiny
+    x, fs = w["series"][0], w["fs"]
+    y = x.copy()
+    y[3000] = np.nan
+    s = torch.cuda.Stream()
+    for series, bad in (([x, y], True), ([x, x], False)):
+        res = bf.bf_correlate(ctx, bank, series, fs, bf.make_opts(precision=prec, stream=s.cuda_stream))
+        s.synchronize()
+        if bad:
+            with pytest.raises(bf.BFError) as e:
+                bf.bf_result_check(res)
+            assert e.value.status == bf.BF_EINVAL and "non-finite" in str(e.value)
+        else:
+            bf.bf_result_check(res)
+        bf.bf_result_destroy(res)
+    plan = bf.bf_plan_create(ctx, bank, [len(x), len(x)], fs, bf.make_opts(precision=prec))
+    try:
+        with pytest.raises(bf.BFError) as e:
+            bf.bf_plan_run(plan, [x, y])
+        assert e.value.status == bf.BF_EINVAL
+        bf.bf_result_check(bf.bf_plan_run(plan, [x, x]))
+        for series, bad in (([y, x], True), ([x, x], False)):
+            res = bf.bf_plan_run(plan, series, s.cuda_stream)
+            s.synchronize()
+            if bad:
+                with pytest.raises(bf.BFError) as e:
+                    bf.bf_result_check(res)
+                assert e.value.status == bf.BF_EINVAL
+            else:
+                bf.bf_result_check(res)
+    finally:
+        bf.bf_plan_destroy(plan)
+    t_bad = bf.bf_serve_submit(ctx, bank, y, fs, bf.make_opts(precision=prec))
+    t_good = bf.bf_serve_submit(ctx, bank, x, fs, bf.make_opts(precision=prec))
+    with pytest.raises(bf.BFError) as e:
+        bf.bf_serve_poll(ctx, t_bad, 60_000_000)
+    assert e.value.status == bf.BF_EINVAL and "non-finite" in str(e.value)
+    st, res = bf.bf_serve_poll(ctx, t_good, 60_000_000)
+    assert st == bf.BF_OK
+    bf.bf_result_check(res)
+    bf.bf_result_destroy(res)
+
+
 def test_async_copy_into_pinned_buffers(ctx, tiny):
     """bf_result_copy_to_host_async gives, once its stream is synchronised,
     what the synchronous copy gives, for every series of a batch, on a caller
