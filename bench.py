@@ -306,6 +306,8 @@ def run_ours(args, rank, world, local):
         serve = run_serve(ctx, bf, synth, args)
 
     bf.bf_destroy(ctx)
+    if serve is not None and not args.no_config5:
+        serve["config5"] = run_config5(bf, synth)
     if rank != 0:
         return None
     return {
@@ -782,57 +784,77 @@ def serve_stream(ctx, bf, banks, reqs, series, precision, time_scale=1.0):
     return bf.bf_serve_stats_get(ctx), time.perf_counter() - t0
 
 
-def run_serving_workload():
+def run_config5(bf, synth, n_sustained=100):
     """The serving workload at its stated size: 200 requests arriving as a
     Poisson process at 50 per second, series of 4-256 s at 2048 or 4096 Hz,
     bank slices of 2^12..2^20 templates, an HBM budget of 150 GB.  That
-    offered load is far above one GPU's capacity, so the same requests are
-    also replayed with the arrivals stretched to about 70 % of the capacity
-    measured in the first run.  Both routes (split-BF16 tensor cores, FFT),
-    each in a fresh context."""
-    import __graft_entry__
-    from paper_1802_01685_gb300 import bf, synth
-    __graft_entry__.build()
+    offered load is far above one GPU's capacity, so the first n_sustained
+    requests are also replayed with the arrivals stretched to 70 % of the
+    capacity measured in the offered run.  Split-BF16 (stored banks) with the
+    shortest-first policy; the FFT route (generated banks: the stored spectra
+    of two 2^20-template banks would not fit the budget) with both policies
+    offered, shortest-first replayed.  Each run in a fresh context."""
     reqs = synth.serving_stream(seed=8, n_requests=200, rate_hz=50.0, t_min=4.0, t_max=256.0,
                                 k_min_log2=12, k_max_log2=20)
     series = [synth.request_series(r) for r in reqs]
-    corr = float(sum((len(x) - int(r["fs"]) + 1) * r["n_templates"] for r, x in zip(reqs, series)))
-    span = reqs[-1]["arrival_s"]
-    out = {"workload": "serving", "requests": len(reqs), "rate_hz": 50.0,
-           "series_s": [4, 256], "templates": [2 ** 12, 2 ** 20], "hbm_budget_gb": 150,
-           "correlations": corr}
-    for precision in ("split_bf16", "fft_fp32"):
-        res = {}
-        for label in ("offered", "sustainable"):
-            cfg = bf.bf_config_default()
-            cfg.hbm_budget = 150 << 30
-            ctx = bf.bf_init(cfg)
-            try:
-                banks = {}
-                for fs in (2048.0, 4096.0):
-                    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0],
-                                           20.0, min(1000.0, fs / 2 - 24), 512, 512)
-                    banks[fs] = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, bf.BF_BANK_SPLIT_BF16)
-                    # untimed: the autotuner's choice, and the FFT route's template spectra
-                    warm = np.zeros(int(2 * fs), np.float32)
-                    bf.bf_result_destroy(bf.bf_correlate(ctx, banks[fs], [warm], fs,
-                                                         bf.make_opts(precision=precision)))
-                scale = 1.0
-                if label == "sustainable":
-                    # arrivals stretched so the offered rate is ~70 % of the capacity just measured
-                    scale = max(1.0, corr / (0.7 * res["offered"]["busy_correlations_per_s"]) / span)
-                s, wall = serve_stream(ctx, bf, banks, reqs, series, precision, scale)
-                res[label] = {"rate_hz": round(50.0 / scale, 3), "p50_ms": round(s.p50_ms, 1),
-                              "p99_ms": round(s.p99_ms, 1), "wall_s": round(wall, 1),
-                              "sustained_correlations_per_s": corr / wall,
-                              "busy_correlations_per_s": s.correlations_per_s,
-                              "completed": int(s.completed), "rejected": int(s.rejected)}
-                for b in banks.values():
-                    bf.bf_bank_destroy(b)
-            finally:
-                bf.bf_destroy(ctx)
-        out[precision] = res
-    print(json.dumps(out), flush=True)
+
+    def work(rs, xs):
+        return float(sum((len(x) - int(r["fs"]) + 1) * r["n_templates"] for r, x in zip(rs, xs)))
+
+    corr = work(reqs, series)
+    out = {"workload": "serving: 200 requests, Poisson arrivals at 50/s, 4-256 s at 2048/4096 Hz, "
+                       "2^12..2^20 templates, HBM budget 150 GB",
+           "requests": len(reqs), "rate_hz": 50.0, "correlations": corr,
+           "sustainable_requests": n_sustained}
+    policies = {"shortest": bf.BF_SERVE_SHORTEST, "fair": bf.BF_SERVE_FAIR}
+    runs = [("split_bf16", bf.BF_BANK_SPLIT_BF16, "shortest", "offered"),
+            ("split_bf16", bf.BF_BANK_SPLIT_BF16, "shortest", "sustainable"),
+            ("fft_fp32", bf.BF_BANK_GENERATED, "shortest", "offered"),
+            ("fft_fp32", bf.BF_BANK_GENERATED, "fair", "offered"),
+            ("fft_fp32", bf.BF_BANK_GENERATED, "shortest", "sustainable")]
+    for precision, storage, policy, label in runs:
+        res = out.setdefault(precision, {"banks": "stored split-BF16" if storage != bf.BF_BANK_GENERATED
+                                         else "generated (spectra made per iteration per request)"})
+        rs, xs = (reqs, series) if label == "offered" else (reqs[:n_sustained], series[:n_sustained])
+        c = work(rs, xs)
+        scale = 1.0
+        if label == "sustainable":
+            # arrivals stretched so the offered rate is ~70 % of the capacity just measured
+            cap = res[f"offered_{policy}"]["busy_correlations_per_s"]
+            scale = max(1.0, c / (0.7 * cap) / max(rs[-1]["arrival_s"], 1e-9))
+        cfg = bf.bf_config_default()
+        cfg.hbm_budget = 150 << 30
+        cfg.serve_policy = policies[policy]
+        ctx = bf.bf_init(cfg)
+        try:
+            banks = {}
+            for fs in (2048.0, 4096.0):
+                spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0],
+                                       20.0, min(1000.0, fs / 2 - 24), 512, 512)
+                banks[fs] = bf.bf_bank_create_grid(ctx, spec, fs, 1.0, storage)
+                # untimed: the autotuner's choice, the twiddle tables
+                warm = np.zeros(int(2 * fs), np.float32)
+                bf.bf_result_destroy(bf.bf_correlate(ctx, banks[fs], [warm], fs,
+                                                     bf.make_opts(precision=precision, bank_end=4096)))
+            st, wall = serve_stream(ctx, bf, banks, rs, xs, precision, scale)
+            res[f"{label}_{policy}"] = {
+                "rate_hz": round(50.0 / scale, 3), "requests": len(rs), "p50_ms": round(st.p50_ms, 1),
+                "p99_ms": round(st.p99_ms, 1), "wall_s": round(wall, 1),
+                "sustained_correlations_per_s": c / wall,
+                "busy_correlations_per_s": st.correlations_per_s,
+                "completed": int(st.completed), "rejected": int(st.rejected)}
+            for b in banks.values():
+                bf.bf_bank_destroy(b)
+        finally:
+            bf.bf_destroy(ctx)
+    return out
+
+
+def run_serving_workload():
+    import __graft_entry__
+    from paper_1802_01685_gb300 import bf, synth
+    __graft_entry__.build()
+    print(json.dumps(run_config5(bf, synth)), flush=True)
 
 
 def k_block_fraction(p, fs, M):
@@ -938,6 +960,8 @@ def main():
     ap.add_argument("--fp16", action="store_true", help="--kernel-case: the split-FP16 route")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-config5", action="store_true",
+                    help="skip the stated serving stream (200 requests at 50/s, about 10 minutes)")
     ap.add_argument("--cpu-templates", type=int, default=384)
     ap.add_argument("--ref-templates", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=32)

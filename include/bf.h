@@ -46,7 +46,7 @@ extern "C" {
 #pragma GCC visibility push(default)
 #endif
 
-#define BF_ABI_VERSION 1
+#define BF_ABI_VERSION 2
 
 typedef enum {
     BF_OK = 0,
@@ -184,7 +184,18 @@ typedef struct {
     int32_t serve_slots;     /* requests served concurrently; 0 = 8             */
     int32_t serve_queue;     /* requests waiting for a slot; 0 = 1024           */
     int32_t log_level;       /* 0 silent .. 3 verbose                           */
+    int32_t serve_policy;    /* bf_serve_policy; 0 = BF_SERVE_FAIR              */
 } bf_config;
+
+/* How the serving loop shares the GPU (no counterpart in the paper).
+ * BF_SERVE_FAIR: requests are admitted in arrival order and every iteration
+ * splits its work budget evenly over the active requests (processor
+ * sharing).  BF_SERVE_SHORTEST: the queued request with the least work
+ * (lags x templates) is admitted first, and every iteration gives its budget
+ * to the active requests with the least remaining work first, each active
+ * request still getting at least one template tile (FFT route: one template
+ * per SM) so that none stalls.  Results do not depend on the policy. */
+typedef enum { BF_SERVE_FAIR = 0, BF_SERVE_SHORTEST = 1 } bf_serve_policy;
 
 typedef struct bf_ctx bf_ctx;
 typedef struct bf_bank bf_bank;

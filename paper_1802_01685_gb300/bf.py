@@ -16,7 +16,8 @@ import threading
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libbf.so")
+# the library; BF_LIBRARY selects another build of it (libbf_debug.so)
+LIB_PATH = os.environ.get("BF_LIBRARY") or os.path.join(_PKG, "libbf.so")
 
 # ---------------------------------------------------------------- constants
 BF_OK, BF_EINVAL, BF_ENOMEM, BF_ECUDA, BF_ETIMEDOUT, BF_EPENDING, BF_EAGAIN, \
@@ -25,6 +26,7 @@ BF_LINEAR, BF_POWERLAW = 0, 1
 BF_ASC, BF_DESC, BF_BOTH = 0, 1, 2
 BF_FP32, BF_BF16, BF_SPLIT_BF16, BF_FFT_FP32, BF_SPLIT_FP16 = 0, 1, 2, 3, 4
 BF_BANK_FP32, BF_BANK_SPLIT_BF16, BF_BANK_GENERATED, BF_BANK_QUADRATURE, BF_BANK_SPLIT_FP16 = 1, 2, 4, 8, 16
+BF_SERVE_FAIR, BF_SERVE_SHORTEST = 0, 1
 BF_SIGMA_WHITE, BF_SIGMA_PARSEVAL = 0, 1
 
 PRECISIONS = {"fp32": BF_FP32, "bf16": BF_BF16, "split_bf16": BF_SPLIT_BF16, "fft_fp32": BF_FFT_FP32,
@@ -41,7 +43,7 @@ class BFError(RuntimeError):
 class bf_config(C.Structure):
     _fields_ = [("device", C.c_int32), ("hbm_budget", C.c_size_t),
                 ("max_candidates", C.c_size_t), ("serve_slots", C.c_int32),
-                ("serve_queue", C.c_int32), ("log_level", C.c_int32)]
+                ("serve_queue", C.c_int32), ("log_level", C.c_int32), ("serve_policy", C.c_int32)]
 
 
 class bf_chirp(C.Structure):

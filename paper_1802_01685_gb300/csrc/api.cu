@@ -414,6 +414,7 @@ static void free_result_buffers(bf_result* r)
                     (void*)r->cand, (void*)r->cand_count, (void*)r->sigma_pred})
         mem.release(p);
     r->sigma_pred = nullptr;
+    r->canaries.clear();
     for (void* p : r->scratch) mem.release(p);
     r->scratch.clear();
     r->packed = nullptr;
@@ -515,22 +516,35 @@ bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
     r->thr = (float)(o.kappa * std::sqrt((bank->quad ? 2.0 : 1.0) / (double)bank->M));
     Allocator& mem = *ctx->mem;
     const size_t S = r->n_series, K = r->K;
-    r->packed = static_cast<unsigned long long*>(mem.alloc(S * K * 8));
-    r->sumsq = static_cast<double*>(mem.alloc(S * K * 8));
-    r->vmax = static_cast<float*>(mem.alloc(S * K * 4));
-    r->argmax = static_cast<int32_t*>(mem.alloc(S * K * 4));
-    r->sigma = static_cast<float*>(mem.alloc(S * K * 4));
-    r->mean_max = static_cast<float*>(mem.alloc(K * 4));
+    bf_result* rr = r.get();
+    // an output buffer; debug builds pad it with a canary (checked after the
+    // search by check_canaries)
+    auto out_alloc = [&mem, rr](size_t bytes) -> void* {
+#ifdef BF_DEBUG_BOUNDS
+        unsigned char* p = static_cast<unsigned char*>(mem.alloc(bytes + CANARY_BYTES));
+        if (p) rr->canaries.push_back(p + bytes);
+        return p;
+#else
+        (void)rr;
+        return mem.alloc(bytes);
+#endif
+    };
+    r->packed = static_cast<unsigned long long*>(out_alloc(S * K * 8));
+    r->sumsq = static_cast<double*>(out_alloc(S * K * 8));
+    r->vmax = static_cast<float*>(out_alloc(S * K * 4));
+    r->argmax = static_cast<int32_t*>(out_alloc(S * K * 4));
+    r->sigma = static_cast<float*>(out_alloc(S * K * 4));
+    r->mean_max = static_cast<float*>(out_alloc(K * 4));
     r->cand_cap = (unsigned int)std::min<size_t>(ctx->cfg.max_candidates, 0xFFFFFFF0u);
     if (!r->want_map && !r->want_tails) r->cand_cap = 0;
-    r->cand = static_cast<Candidate*>(mem.alloc(std::max<size_t>(r->cand_cap, 1) * sizeof(Candidate)));
-    if (r->parseval) r->sigma_pred = static_cast<float*>(mem.alloc(S * K * 4));
+    r->cand = static_cast<Candidate*>(out_alloc(std::max<size_t>(r->cand_cap, 1) * sizeof(Candidate)));
+    if (r->parseval) r->sigma_pred = static_cast<float*>(out_alloc(S * K * 4));
     r->cand_count = static_cast<unsigned int*>(mem.alloc(2 * sizeof(unsigned int)));
     r->status = r->cand_count ? r->cand_count + 1 : nullptr;
     bool ok = r->packed && r->sumsq && r->vmax && r->argmax && r->sigma && r->mean_max && r->cand &&
               r->cand_count && (!r->parseval || r->sigma_pred);
     if (ok && r->want_hist) {
-        r->hist = static_cast<uint32_t*>(mem.alloc(S * r->nbins * 4));
+        r->hist = static_cast<uint32_t*>(out_alloc(S * r->nbins * 4));
         ok = r->hist != nullptr;
     }
     size_t map_total = 0;
@@ -544,7 +558,7 @@ bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
         map_total += (size_t)nt * nf;
     }
     if (ok && r->want_map) {
-        r->map = static_cast<float*>(mem.alloc(map_total * 4));
+        r->map = static_cast<float*>(out_alloc(map_total * 4));
         ok = r->map != nullptr;
     }
     if (!ok) {
@@ -553,7 +567,10 @@ bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
         return BF_ENOMEM;
     }
     r->map_total = map_total;
-    cudaError_t e = clear_result(r.get(), st);
+    cudaError_t e = cudaSuccess;
+    for (unsigned char* c : r->canaries)
+        if (e == cudaSuccess) e = cudaMemsetAsync(c, CANARY_FILL, CANARY_BYTES, st);
+    if (e == cudaSuccess) e = clear_result(r.get(), st);
     if (e != cudaSuccess) {
         free_result_buffers(r.get());
         return cuda_fail(e, "clearing result buffers");
@@ -597,6 +614,8 @@ bf_status finalize_result(bf_ctx* ctx, const bf_bank* bank, bf_result* r, cudaSt
     for (size_t s0 = 0; s0 < S && e == cudaSuccess; s0 += MAX_FIN) {
         FinalizeParams fp{};
         fp.s0 = (uint32_t)s0;
+        fp.n_chirps = (uint32_t)bank->K;
+        fp.err = ctx->d_err;
         fp.n = (uint32_t)std::min(S - s0, (size_t)MAX_FIN);
         for (uint32_t i = 0; i < fp.n; ++i) {
             const size_t s = s0 + i;
@@ -763,6 +782,21 @@ cudaError_t gen_launch(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o, const
     return e;
 }
 
+bf_status check_canaries(const bf_result* r)
+{
+    for (size_t i = 0; i < r->canaries.size(); ++i) {
+        unsigned char h[CANARY_BYTES];
+        cudaError_t e = cudaMemcpy(h, r->canaries[i], CANARY_BYTES, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "reading an output canary");
+        for (size_t b = 0; b < CANARY_BYTES; ++b)
+            if (h[b] != CANARY_FILL) {
+                set_error("output buffer %zu was written past its end (canary byte %zu)", i, b);
+                return BF_EDEVICE;
+            }
+    }
+    return BF_OK;
+}
+
 bf_status result_status(const bf_result* r)
 {
     unsigned int w = 0;
@@ -782,7 +816,8 @@ bf_status check_device_status(bf_ctx* ctx)
     if (e != cudaSuccess) return cuda_fail(e, "reading kernel status");
     if (h != DEV_OK) {
         cudaMemset(ctx->d_err, 0, sizeof(int));
-        set_error("kernel reported internal timeout (code %d)", h);
+        if (h == DEV_BOUNDS) set_error("a kernel's bounds check failed (debug build)");
+        else set_error("kernel reported internal timeout (code %d)", h);
         return BF_EDEVICE;
     }
     return BF_OK;
@@ -852,6 +887,8 @@ bf_status fft_prepare(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
             f.series_id = (uint32_t)s;
         }
         b.n = n;
+        b.err = ctx->d_err;
+        p.err = ctx->d_err;
         b.quad = quad ? 1 : 0;
         b.F = fft_seg_len(quad);
         b.V = V;
@@ -957,6 +994,7 @@ void bf_config_default(bf_config* c)
     c->serve_slots = 8;
     c->serve_queue = 1024;
     c->log_level = 0;
+    c->serve_policy = BF_SERVE_FAIR;
 }
 
 void bf_opts_default(bf_opts* o)
@@ -981,6 +1019,10 @@ bf_status bf_init(const bf_config* cfg, bf_ctx** out)
     if (c.max_candidates == 0) c.max_candidates = 1u << 22;
     if (c.serve_slots <= 0) c.serve_slots = 8;
     if (c.serve_queue <= 0) c.serve_queue = 1024;
+    if (c.serve_policy != BF_SERVE_FAIR && c.serve_policy != BF_SERVE_SHORTEST) {
+        set_error("serve_policy %d is not a bf_serve_policy", c.serve_policy);
+        return BF_EINVAL;
+    }
     int n = 0;
     cudaError_t e = cudaGetDeviceCount(&n);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -1043,6 +1085,7 @@ void bf_destroy(bf_ctx* ctx)
 bf_status bf_bank_create(bf_ctx* ctx, const bf_chirp* params, size_t K, double fs, double T,
                          unsigned storage, bf_bank** out)
 {
+    NvtxRange range("bf_bank_create");
     if (!ctx || !params || !out) { set_error("NULL argument"); return BF_EINVAL; }
     *out = nullptr;
     if (K == 0 || K > 0x7FFFFF00u) { set_error("bank size %zu outside [1, 2^31)", K); return BF_EINVAL; }
@@ -1258,6 +1301,7 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
                        const size_t* lengths, size_t n_series, double fs, const bf_opts* opts,
                        bf_result** out)
 {
+    NvtxRange range("bf_correlate");
     if (!ctx || !bank || !series || !lengths || !out || n_series == 0) {
         set_error("NULL argument or no series");
         return BF_EINVAL;
@@ -1315,6 +1359,7 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
         if (o.rho_out) segs[0].rho = o.rho_out;
     }
     if (r->parseval) {
+        NvtxRange pr("predictor");
         // the predictor step: sigma_k per series before the search
         std::vector<const PreparedSeries*> pp;
         for (const PreparedSeries& p : prep) pp.push_back(&p);
@@ -1366,7 +1411,10 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
         if (e0) { cudaEventDestroy(e0); cudaEventDestroy(e1); }
         return cuda_fail(e, "correlation launch");
     }
-    st = finalize_result(ctx, bank, r, strm);
+    {
+        NvtxRange fr("finalize");
+        st = finalize_result(ctx, bank, r, strm);
+    }
     if (st) {
         if (e0) { cudaEventDestroy(e0); cudaEventDestroy(e1); }
         return st;
@@ -1380,6 +1428,9 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
         cudaEventDestroy(e1);
         if (e != cudaSuccess) return cuda_fail(e, "correlation");
         st = check_device_status(ctx);
+        if (st) return st;
+        // debug builds: no output written past its end
+        st = check_canaries(r);
         if (st) return st;
         // every sample must be finite (the series preparation flags it)
         st = result_status(r);
@@ -1408,6 +1459,7 @@ bf_status bf_result_check(const bf_result* r)
     if (!r) { set_error("NULL argument"); return BF_EINVAL; }
     cudaSetDevice(r->ctx->device);
     bf_status st = check_device_status(r->ctx);
+    if (st == BF_OK) st = check_canaries(r);
     return st ? st : result_status(r);
 }
 
@@ -1641,6 +1693,7 @@ void bf_result_destroy(bf_result* r)
 
 bf_status bf_control_randomize(bf_ctx* ctx, const float* in, size_t n, uint64_t seed, float* out)
 {
+    NvtxRange range("bf_control_randomize");
     if (!ctx || !in || !out) { set_error("NULL argument"); return BF_EINVAL; }
     if (n == 0) return BF_OK;
     if (n >= 0xFFFFFFFFull) { set_error("series of %zu samples too long", n); return BF_EINVAL; }

@@ -19,6 +19,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bf.h"
 
 namespace bfi {
@@ -44,7 +46,24 @@ constexpr uint32_t TILE_BYTES_A = TC_TILE_T * TC_BK * 2;   // 16 KiB per k-block
 
 // device error codes written to the context's status word
 enum : int { DEV_OK = 0, DEV_TIMEOUT_FULL = 1, DEV_TIMEOUT_EMPTY = 2,
-             DEV_TIMEOUT_TMEM = 3, DEV_TMEM_ALLOC = 4 };
+             DEV_TIMEOUT_TMEM = 3, DEV_TMEM_ALLOC = 4, DEV_BOUNDS = 5 };
+
+// Debug builds (-DBF_DEBUG_BOUNDS, built as libbf_debug.so): the kernels
+// check the indices their outputs, staging buffers and tables rely on --
+// invariants that the launch set-up guarantees, so a release build does not
+// test them.  A failed check records DEV_BOUNDS in the context's status word
+// (the first code recorded stays) and skips the access; the call then
+// returns BF_EDEVICE.  Nothing traps.  In release builds BF_BOUNDS is `true`.
+#ifdef BF_DEBUG_BOUNDS
+__device__ __forceinline__ bool bounds_ok(int* err, bool ok)
+{
+    if (!ok && err) atomicCAS(err, DEV_OK, DEV_BOUNDS);
+    return ok;
+}
+#define BF_BOUNDS(err, cond) (::bfi::bounds_ok((err), (cond)))
+#else
+#define BF_BOUNDS(err, cond) true
+#endif
 
 struct Candidate {
     uint32_t series;
@@ -154,6 +173,7 @@ struct FftParams {
     const ChirpDev* chirps;         // bank parameters (the fixup synthesises its rows)
     uint32_t M;                     // template length (at most FFT_POINTS / 2)
     double fs;
+    int* err;                       // device status word (debug-build bounds checks)
     FftSeries ser[MAX_FFT_SER];
 };
 
@@ -178,6 +198,7 @@ struct FftSeriesBatch {
     uint32_t L[MAX_FFT_SER];
     uint32_t* fix[MAX_FFT_SER];
     uint32_t* n_fix;                // [n] counters, zeroed by launch_fft_series
+    int* err;                       // device status word (debug-build bounds checks)
 };
 
 // The Parseval predictor (predict.cu, kernels in corr_fft.cu): periodograms
@@ -193,6 +214,15 @@ struct WelchBatch {
     uint32_t seg_begin[MAX_FFT_SER + 1];      // series s: rows [seg_begin[s], seg_begin[s+1])
     float* pseg;                              // [total segments][PRED_BINS]
     float* P;                                 // [n][PRED_BINS] averaged periodograms
+};
+
+// A named range on the calling thread for profilers (NVTX: the ranges cost a
+// few instructions when no profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -269,6 +299,8 @@ struct FinalizeSeries {
 constexpr int MAX_FIN = 128;        // series per finalize / paint launch
 struct FinalizeParams {
     uint32_t s0, n;                 // series [s0, s0 + n) of the result
+    uint32_t n_chirps;              // chirps of the bank (painted templates index them)
+    int* err;                       // device status word (debug-build bounds checks)
     FinalizeSeries ser[MAX_FIN];
 };
 cudaError_t launch_finalize(const FinalizeParams& p, uint32_t K, uint32_t nbins, cudaStream_t s);
@@ -415,4 +447,6 @@ struct bf_result {
     double correlations = 0;
     double kernel_ms = 0;
     std::vector<void*> scratch;             // released at destroy
+    // debug builds: the canary past the end of each output buffer
+    std::vector<unsigned char*> canaries;
 };

@@ -616,9 +616,11 @@ __device__ __forceinline__ void stage_spectrum(const Smem& m, const float2* src)
 
 // window norms of a segment (a row of the per-segment copy, which starts
 // 16-byte aligned and has room for whole 16-byte copies) into shared memory
-__device__ __forceinline__ void stage_norms(const Smem& m, const float* src, uint32_t nv)
+template <int CAP>
+__device__ __forceinline__ void stage_norms(const Smem& m, const float* src, uint32_t nv, int* err)
 {
-    for (uint32_t c = threadIdx.x; 4 * c < nv; c += FT) cp_async16(m.inv + 4 * c, src + 4 * c);
+    for (uint32_t c = threadIdx.x; 4 * c < nv; c += FT)
+        if (BF_BOUNDS(err, 4 * c + 4 <= (uint32_t)CAP)) cp_async16(m.inv + 4 * c, src + 4 * c);
 }
 
 // warp reduction of a packed max key and a sum, then one atomic each per warp
@@ -680,6 +682,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
             if (tid == 0) hm = H[FH];
         }
         const uint32_t o = k - p.k_begin;
+        (void)BF_BOUNDS(p.err, o < p.k_end - p.k_begin && k >= p.hrow0 && j < S.nseg);
         if (new_series) {
             thr = S.sigma_pred ? S.kappa * S.sigma_pred[o] : p.thr;
             best = -1.f;
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
         }
         const uint32_t t0 = j * p.V;
         const uint32_t nv = min(p.V, S.L - t0);
-        stage_norms(m, S.inv + (size_t)j * p.Vp, nv);
+        stage_norms<INV_REAL>(m, S.inv + (size_t)j * p.Vp, nv, p.err);
         cp_async_commit();
         // the item after this one
         uint32_t np = row, nj = j + 1;
@@ -770,14 +773,14 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
                     track_max(aa, tau, best, arg);
                     pa = fmaf(ra, ra, pa);
                     if (aa >= thr) push_tail(p, S.series_id, k, tau, ra);
-                    if (S.rho) S.rho[(size_t)o * S.L + tau] = ra;
+                    if (S.rho && BF_BOUNDS(p.err, tau < S.L)) S.rho[(size_t)o * S.L + tau] = ra;
                     if (t + 1 < nv) {
                         const float rb = z[h].y * iv.y;
                         const float ab = fabsf(rb);
                         track_max(ab, tau + 1, best, arg);
                         pa = fmaf(rb, rb, pa);
                         if (ab >= thr) push_tail(p, S.series_id, k, tau + 1, rb);
-                        if (S.rho) S.rho[(size_t)o * S.L + tau + 1] = rb;
+                        if (S.rho && BF_BOUNDS(p.err, tau + 1 < S.L)) S.rho[(size_t)o * S.L + tau + 1] = rb;
                     }
                 }
             }
@@ -835,6 +838,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
             }
         }
         const uint32_t la = (ka - p.k_begin) >> 1;           // output index of the pair
+        (void)BF_BOUNDS(p.err, ka + 1 < p.k_end && ka >= p.hrow0 && j < S.nseg);
         if (new_series) {
             thr = S.sigma_pred ? S.kappa * S.sigma_pred[la] : p.thr;
             best = -1.f;
@@ -843,7 +847,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
         }
         const uint32_t t0 = j * p.V;
         const uint32_t nv = min(p.V, S.L - t0);
-        stage_norms(m, S.inv + (size_t)j * p.Vp, nv);
+        stage_norms<INV_PAIR>(m, S.inv + (size_t)j * p.Vp, nv, p.err);
         cp_async_commit();
         uint32_t np = pair, nj = j + 1;
         int ns = s;
@@ -908,7 +912,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
                     track_max(r, tau, best, arg);
                     pa = fmaf(r, r, pa);
                     if (r >= thr) push_tail(p, S.series_id, ka >> 1, tau, r);
-                    if (S.rho) S.rho[(size_t)la * S.L + tau] = r;
+                    if (S.rho && BF_BOUNDS(p.err, tau < S.L)) S.rho[(size_t)la * S.L + tau] = r;
                 }
             }
         }
@@ -968,9 +972,9 @@ __global__ void __launch_bounds__(256) k_fft_flags(const __grid_constant__ FftSe
         uint32_t slot0 = 0;
         if (lane == 0) slot0 = atomicAdd(b.n_fix + i, (uint32_t)__popc(mask));   // each lag once: < L entries
         slot0 = __shfl_sync(0xffffffffu, slot0, 0);
-        if (flag) {
+        const uint32_t slot = slot0 + __popc(mask & ((1u << lane) - 1u));
+        if (flag && BF_BOUNDS(b.err, slot < L)) {
             inv[t] = 0.f;
-            const uint32_t slot = slot0 + __popc(mask & ((1u << lane) - 1u));
             b.fix[i][2 * slot] = (uint32_t)t;
             b.fix[i][2 * slot + 1] = __float_as_uint(iv);
         }

@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(SIMT_THREADS, 2) k_corr_simt(const __grid_cons
         const uint32_t tt = s.tt0 + (uint32_t)(local / s.n_lag_tiles);
         const uint32_t lag0 = (uint32_t)(local % s.n_lag_tiles) * SIMT_TILE_L;
         const uint32_t k0 = tt * SIMT_TILE_T;
+        if (!BF_BOUNDS(p.err, k0 >= s.bank_k0 && lag0 < s.L)) continue;      // the same for the whole CTA
         const float* __restrict__ bank = s.bank_f32 + (size_t)(k0 - s.bank_k0) * s.M_pad;
         const float* __restrict__ xs = s.x + lag0;
 

@@ -714,7 +714,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_corr_tc(const __grid_constant
                     bi = obi;
                 }
             }
-            if (keep && bv >= 0.f && !(quad && odd)) {
+            if (keep && bv >= 0.f && !(quad && odd) &&
+                BF_BOUNDS(p.err, c.lag0 + bi < s.L && (size_t)c.tt * TC_TILE_T >= s.bank_k0)) {
                 atomicMax(s.vmax + o, pack_max(bv, c.lag0 + bi));
                 atomicAdd(s.sumsq + o, (double)ssum);
             }

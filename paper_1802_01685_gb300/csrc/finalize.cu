@@ -247,6 +247,7 @@ __global__ void k_paint(const Candidate* __restrict__ cand, const unsigned int* 
     for (unsigned int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n; c += warps) {
         const Candidate cd = cand[c];
         if (cd.series < fp.s0 || cd.series >= fp.s0 + fp.n) continue;
+        if (!BF_BOUNDS(fp.err, cd.k < fp.n_chirps)) continue;
         const ChirpDev p = params[cd.k];
         const FinalizeSeries& f = fp.ser[cd.series - fp.s0];
         const float a = fabsf(cd.rho);

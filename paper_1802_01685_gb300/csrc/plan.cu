@@ -45,6 +45,7 @@ void bf_plan_destroy(bf_plan* p)
 bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths, size_t n_series,
                          double fs, const bf_opts* opts, bf_plan** out)
 {
+    NvtxRange range("bf_plan_create");
     if (!ctx || !bank || !lengths || !out || n_series == 0) {
         set_error("NULL argument or no series");
         return BF_EINVAL;
@@ -171,6 +172,7 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
 
 bf_status bf_plan_run(bf_plan* p, const float* const* series, void* stream, const bf_result** out)
 {
+    NvtxRange range("bf_plan_run");
     if (!p || !series || !out) { set_error("NULL argument"); return BF_EINVAL; }
     *out = nullptr;
     for (size_t s = 0; s < p->lengths.size(); ++s)
@@ -209,7 +211,8 @@ bf_status bf_plan_run(bf_plan* p, const float* const* series, void* stream, cons
         unsigned int c = 0;
         cudaMemcpy(&c, p->r->cand_count, sizeof c, cudaMemcpyDeviceToHost);
         p->r->n_candidates = c;
-        st = result_status(p->r);               // non-finite samples
+        st = check_canaries(p->r);              // debug builds
+        if (st == BF_OK) st = result_status(p->r);      // non-finite samples
         if (st) return st;
     }
     *out = p->r;

@@ -77,6 +77,10 @@ bf_status check_device_status(bf_ctx* ctx);
 // BF_EINVAL if the result's status word says a series held a non-finite
 // sample (reads it synchronously: call after the result's work is done)
 bf_status result_status(const bf_result* r);
+// debug builds: BF_EDEVICE if an output buffer was written past its end
+constexpr size_t CANARY_BYTES = 256;
+constexpr int CANARY_FILL = 0xA5;
+bf_status check_canaries(const bf_result* r);
 
 void serve_shutdown(bf_ctx* ctx);
 

@@ -69,6 +69,10 @@ struct Request {
     void* gslot[2] = {nullptr, nullptr};
     float* gscratch = nullptr;
     uint32_t gcap_rows = 0, gscratch_rows = 0;
+    // BF_SERVE_SHORTEST: the request's size (lags x template rows) and its
+    // share of the current iteration (work units: tile pairs or transforms)
+    double work = 0;
+    uint64_t share = 0;
 };
 
 // tiles per SM per iteration: large enough to amortise the launch, small
@@ -212,6 +216,7 @@ static bool admit(ServeState* S, Request* r)
             const uint32_t V = fft_lags_per_seg(bank->M, quad);
             FftSeriesBatch b{};
             b.n = 1;
+            b.err = ctx->d_err;
             b.quad = quad ? 1 : 0;
             b.F = fft_seg_len(quad);
             b.V = V;
@@ -239,6 +244,7 @@ static bool admit(ServeState* S, Request* r)
             p.V = V;
             p.Vp = b.Vp;
             p.n_ser = 1;
+            p.err = ctx->d_err;
             p.thr = res->thr;
             p.cand_cap = res->cand_cap;
             p.cand = res->cand;
@@ -315,17 +321,24 @@ static void scheduler(ServeState* S)
             S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->active.empty(); });
             if (S->stop) break;
             // admission, in arrival order, while a slot and the budget allow
+            const bool shortest = ctx->cfg.serve_policy == BF_SERVE_SHORTEST;
             while (!S->queue.empty() && (int)S->active.size() < ctx->cfg.serve_slots) {
-                Request* r = S->queue.front();
+                // arrival order, or the least work first (the earliest among equals)
+                auto pick = !shortest ? S->queue.begin()
+                                      : std::min_element(S->queue.begin(), S->queue.end(),
+                                                         [](const Request* a, const Request* b) {
+                                                             return a->work < b->work;
+                                                         });
+                Request* r = *pick;
                 if (r->cancel) {
-                    S->queue.pop_front();
+                    S->queue.erase(pick);
                     r->state = R_CANCELED;
                     ++S->cancelled;
                     S->cv_done.notify_all();
                     continue;
                 }
                 if (!ctx->mem->fits(r->bytes) && !S->active.empty()) break;
-                S->queue.pop_front();
+                S->queue.erase(pick);
                 lk.unlock();
                 const bool ok = admit(S, r);
                 lk.lock();
@@ -342,15 +355,49 @@ static void scheduler(ServeState* S)
         }
 
         // one iteration: a chunk of template tiles of every admitted request
+        NvtxRange iter_range("serve iteration");
         std::vector<std::pair<Request*, Seg>> segs[5];          // by precision (the FFT route has none)
         std::vector<Request*> finishing;
         uint64_t n_work = 0;
         for (Request* r : act)
             if (!r->cancel && (r->tt_next < r->tt_end || r->k_next < r->k_stop)) ++n_work;
         const uint64_t budget = (uint64_t)ctx->n_sm * TILES_PER_SM;
+        const uint64_t t_budget = (uint64_t)ctx->n_sm * TRANSFORMS_PER_SM;
+        const bool shortest = ctx->cfg.serve_policy == BF_SERVE_SHORTEST;
+        if (shortest) {
+            // each budget to the requests with the least remaining work first,
+            // every request still getting one template tile / template per SM
+            std::vector<std::pair<uint64_t, Request*>> tiles, ffts;
+            for (Request* r : act) {
+                if (r->cancel) continue;
+                if (r->fft && r->k_next < r->k_stop)
+                    ffts.emplace_back((uint64_t)(r->k_stop - r->k_next) / (r->fp.quad ? 2 : 1) *
+                                          std::max<uint32_t>(1, r->fp.ser[0].nseg), r);
+                else if (!r->fft && r->tt_next < r->tt_end)
+                    tiles.emplace_back((uint64_t)(r->tt_end - r->tt_next) * std::max<uint32_t>(1, r->n_lag_tiles), r);
+            }
+            auto by_rest = [](const std::pair<uint64_t, Request*>& a, const std::pair<uint64_t, Request*>& b) {
+                return a.first < b.first;
+            };
+            std::stable_sort(tiles.begin(), tiles.end(), by_rest);
+            std::stable_sort(ffts.begin(), ffts.end(), by_rest);
+            uint64_t left = budget;
+            for (auto& w : tiles) {
+                const uint64_t g = std::max<uint64_t>(std::min(w.first, left), w.second->n_lag_tiles);
+                left -= std::min(left, g);
+                w.second->share = g;
+            }
+            left = t_budget;
+            for (auto& w : ffts) {
+                const uint64_t nseg = std::max<uint32_t>(1, w.second->fp.ser[0].nseg);
+                const uint64_t g = std::max<uint64_t>(std::min(w.first, left), (uint64_t)ctx->n_sm * nseg);
+                left -= std::min(left, g);
+                w.second->share = g;
+            }
+        }
         for (Request* r : act) {
             if (r->cancel || r->tt_next >= r->tt_end) continue;
-            uint64_t per = std::max<uint64_t>(1, budget / std::max<uint64_t>(1, n_work));
+            uint64_t per = shortest ? r->share : std::max<uint64_t>(1, budget / std::max<uint64_t>(1, n_work));
             uint64_t ntt = std::max<uint64_t>(1, per / std::max<uint32_t>(1, r->n_lag_tiles));
             ntt = std::min<uint64_t>(ntt, r->tt_end - r->tt_next);
             const uint32_t tile_t = tile_templates(r->opts.precision);
@@ -413,8 +460,8 @@ static void scheduler(ServeState* S)
         // pairs (pair route) each, one transform per item and segment
         for (Request* r : act) {
             if (!r->fft || r->cancel || r->k_next >= r->k_stop) continue;
-            const uint64_t per = std::max<uint64_t>(1, (uint64_t)ctx->n_sm * TRANSFORMS_PER_SM /
-                                                           std::max<uint64_t>(1, n_work));
+            const uint64_t per = shortest ? r->share
+                                          : std::max<uint64_t>(1, t_budget / std::max<uint64_t>(1, n_work));
             const uint64_t items = std::max<uint64_t>((uint64_t)ctx->n_sm, per / std::max<uint32_t>(1, r->fp.ser[0].nseg));
             const uint64_t want = r->fp.quad ? 2 * items : items;
             uint32_t rows = (uint32_t)std::min<uint64_t>(want, r->k_stop - r->k_next);
@@ -590,6 +637,7 @@ bf_status bf_serve_submit(bf_ctx* ctx, const bf_request* req, uint64_t* ticket)
     r->fs = req->fs;
     r->bank = bank;
     r->opts = o;
+    r->work = (double)(req->n - bank->M + 1) * (double)(bank_row(bank, o.bank_end) - bank_row(bank, o.bank_begin));
     r->bytes = prepared_series_bytes(req->n, bank->M, bank->M_pad, o.precision) +
                result_bytes(bank, o, req->n, req->fs, ctx->cfg.max_candidates) +
                gen_serve_bytes(bank, o.precision);

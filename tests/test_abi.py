@@ -40,7 +40,7 @@ def test_binding_covers_the_header(lib):
 
 
 def test_status_strings_and_version(lib):
-    assert bf.bf_abi_version() == 1
+    assert bf.bf_abi_version() == 2
     assert bf.bf_status_string(bf.BF_OK) == "ok"
     assert bf.bf_status_string(bf.BF_EINVAL) == "invalid argument"
     assert bf.bf_status_string(99) == "unknown status"
@@ -49,6 +49,7 @@ def test_status_strings_and_version(lib):
 def test_defaults(lib):
     c = bf.bf_config_default()
     assert c.max_candidates == 1 << 22 and c.serve_slots == 8 and c.serve_queue == 1024
+    assert c.serve_policy == bf.BF_SERVE_FAIR
     o = bf.bf_opts_default()
     assert o.precision == bf.BF_SPLIT_BF16 and o.kappa == 5.0 and o.hist_bins == 1024
     assert abs(o.map_dt_s - 1e-3) < 1e-15 and o.map_df_hz == 4.0 and o.rho_out is None

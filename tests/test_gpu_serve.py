@@ -182,3 +182,66 @@ def test_queue_full_and_budget():
     assert e.value.status == bf.BF_ENOMEM
     bf.bf_bank_destroy(bank)
     bf.bf_destroy(ctx)
+
+
+def test_shortest_policy_same_results_and_small_requests_first():
+    """BF_SERVE_SHORTEST changes only the order of the work: the twelve-request
+    mix gives, request by request, what the same searches alone give, bit for
+    bit; and with one slot, a small request queued behind a large one is
+    admitted first (the large one is still pending when the small one is
+    done)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    cfg = bf.bf_config_default()
+    cfg.serve_slots = 4
+    cfg.serve_policy = bf.BF_SERVE_SHORTEST
+    ctx = bf.bf_init(cfg)
+    spec = synth.grid_spec([synth.LINEAR, synth.POWERLAW], [synth.ASC, synth.DESC], [1.0, 0.5],
+                           20.0, 1000.0, 16, 16)                 # 2048 templates
+    bank = bf.bf_bank_create_grid(ctx, spec, FS, T,
+                                  bf.BF_BANK_FP32 | bf.BF_BANK_SPLIT_BF16 | bf.BF_BANK_SPLIT_FP16)
+    try:
+        reqs = requests()
+        alone = [fetch(bf.bf_correlate(ctx, bank, [x], FS, o), o.want_map) for x, o in reqs]
+        tickets = [bf.bf_serve_submit(ctx, bank, x, FS, o) for x, o in reqs]
+        for t, (x, o), a in zip(tickets, reqs, alone):
+            st, res = bf.bf_serve_poll(ctx, t, 60_000_000)
+            assert st == bf.BF_OK
+            m = fetch(res, o.want_map)
+            np.testing.assert_array_equal(m["max"], a["max"])
+            np.testing.assert_array_equal(m["argmax"], a["argmax"])
+            np.testing.assert_array_equal(m["hist"], a["hist"])
+            if a["map"] is not None:
+                np.testing.assert_array_equal(m["map"], a["map"])
+    finally:
+        bf.bf_bank_destroy(bank)
+        bf.bf_destroy(ctx)
+
+    cfg.serve_slots = 1
+    ctx = bf.bf_init(cfg)
+    bank = bf.bf_bank_create_grid(ctx, spec, FS, T)
+    try:
+        rng = np.random.default_rng(9)
+        big = [synth.white(int(600 * FS), rng).astype(np.float32) for _ in range(2)]
+        small = synth.white(int(2 * FS), rng).astype(np.float32)
+        o_big = bf.make_opts(precision="fp32")
+        o_small = bf.make_opts(precision="split_bf16", bank_end=256)
+        t1 = bf.bf_serve_submit(ctx, bank, big[0], FS, o_big)
+        for _ in range(2000):                                    # the first one runs
+            if bf.bf_serve_stats_get(ctx).active >= 1:
+                break
+            time.sleep(0.001)
+        t2 = bf.bf_serve_submit(ctx, bank, big[1], FS, o_big)
+        ts = bf.bf_serve_submit(ctx, bank, small, FS, o_small)
+        st, rs = bf.bf_serve_poll(ctx, ts, 120_000_000)
+        assert st == bf.BF_OK
+        assert bf.bf_serve_poll(ctx, t2, 0)[0] == bf.BF_EPENDING, "the large request was admitted first"
+        ref = fetch(bf.bf_correlate(ctx, bank, [small], FS, o_small), False)
+        np.testing.assert_array_equal(fetch(rs, False)["max"], ref["max"])
+        for t in (t1, t2):
+            st, r = bf.bf_serve_poll(ctx, t, 240_000_000)
+            assert st == bf.BF_OK
+            bf.bf_result_destroy(r)
+    finally:
+        bf.bf_bank_destroy(bank)
+        bf.bf_destroy(ctx)
