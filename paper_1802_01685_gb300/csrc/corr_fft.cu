@@ -643,6 +643,9 @@ __device__ __forceinline__ void publish(unsigned long long key, double d, unsign
 // (template row, series, segment) in order; while the FFT of one segment
 // runs, the spectrum of the next one and the window norms of this one arrive
 // in shared memory.
+// DENSE: a series of the launch keeps the dense output rho (a compile-time
+// copy, so that the common case carries no per-lag test for it)
+template <bool DENSE>
 __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ FftParams p)
 {
     const Smem m = smem_setup<FN>(p.tw);
@@ -768,19 +771,22 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
                 if (t < nv) {
                     const float2 iv = *reinterpret_cast<const float2*>(m.inv + t);   // t + 1 < INV_REAL
                     const uint32_t tau = t0 + t;
-                    const float ra = z[h].x * iv.x;    // norms carry 1/F (k_fft_flags)
-                    const float aa = fabsf(ra);
-                    track_max(aa, tau, best, arg);
+                    const bool two = t + 1 < nv;          // the second lag is valid (its norm is staged)
+                    const float ra = z[h].x * iv.x;       // norms carry 1/F (k_fft_flags)
+                    const float rb = two ? z[h].y * iv.y : 0.f;
+                    const float aa = fabsf(ra), ab = fabsf(rb);
+                    // the pair's larger |rho|, the earlier lag on ties, into the running max
+                    const bool second = ab > aa;
+                    track_max(second ? ab : aa, second ? tau + 1 : tau, best, arg);
                     pa = fmaf(ra, ra, pa);
-                    if (aa >= thr) push_tail(p, S.series_id, k, tau, ra);
-                    if (S.rho && BF_BOUNDS(p.err, tau < S.L)) S.rho[(size_t)o * S.L + tau] = ra;
-                    if (t + 1 < nv) {
-                        const float rb = z[h].y * iv.y;
-                        const float ab = fabsf(rb);
-                        track_max(ab, tau + 1, best, arg);
-                        pa = fmaf(rb, rb, pa);
-                        if (ab >= thr) push_tail(p, S.series_id, k, tau + 1, rb);
-                        if (S.rho && BF_BOUNDS(p.err, tau + 1 < S.L)) S.rho[(size_t)o * S.L + tau + 1] = rb;
+                    pa = fmaf(rb, rb, pa);
+                    if (fmaxf(aa, ab) >= thr) {
+                        if (aa >= thr) push_tail(p, S.series_id, k, tau, ra);
+                        if (two && ab >= thr) push_tail(p, S.series_id, k, tau + 1, rb);
+                    }
+                    if (DENSE && S.rho && BF_BOUNDS(p.err, tau + (two ? 1u : 0u) < S.L)) {
+                        S.rho[(size_t)o * S.L + tau] = ra;
+                        if (two) S.rho[(size_t)o * S.L + tau + 1] = rb;
                     }
                 }
             }
@@ -1111,7 +1117,9 @@ cudaError_t fft_attributes()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_corr_rfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RCORR_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_corr_rfft<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RCORR_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_corr_rfft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RCORR_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_corr_fft_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CORR_SMEM);
     if (e == cudaSuccess)
@@ -1302,7 +1310,12 @@ cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st)
     const unsigned grid = std::min<unsigned>(items, (unsigned)n_sm);
     count_launches(1);
     if (p.quad) k_corr_fft_quad<<<grid, FT, CORR_SMEM, st>>>(p);
-    else k_corr_rfft<<<grid, FT, RCORR_SMEM, st>>>(p);
+    else {
+        bool dense = false;
+        for (int i = 0; i < p.n_ser; ++i) dense = dense || p.ser[i].rho != nullptr;
+        if (dense) k_corr_rfft<true><<<grid, FT, RCORR_SMEM, st>>>(p);
+        else k_corr_rfft<false><<<grid, FT, RCORR_SMEM, st>>>(p);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !p.chirps) return e;
     // the lags left to the direct computation (none: the CTAs return at once)
