@@ -694,8 +694,6 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
         }
         const uint32_t t0 = j * p.V;
         const uint32_t nv = min(p.V, S.L - t0);
-        stage_norms<INV_REAL>(m, S.inv + (size_t)j * p.Vp, nv, p.err);
-        cp_async_commit();
         // the item after this one
         uint32_t np = row, nj = j + 1;
         int ns = s;
@@ -706,8 +704,12 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
                 np = row + gridDim.x;
             }
         }
-        cp_async_wait<1>();                         // this segment's spectrum
+        cp_async_wait<0>();                         // this segment's spectrum
         __syncthreads();
+        // this segment's window norms (the previous item's epilogue read its own
+        // before the barrier above)
+        stage_norms<INV_REAL>(m, S.inv + (size_t)j * p.Vp, nv, p.err);
+        cp_async_commit();
         // Y = X conj(H) over all F bins, and the packed spectrum
         // Z'[f] = A + i w B, Z'[N - f] = conj(A - i w B), with A = Y[f] +
         // conj Y[N-f], B = Y[f] - conj Y[N-f], w = e^{i pi f / N}: twice the
@@ -795,7 +797,9 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
         ss += pa;
         if (nj == 0)                                // last segment of this series: publish
             publish(best >= 0.f ? pack_max(best, arg) : 0ull, (double)ss, S.vmax + o, S.sumsq + o);
-        __syncthreads();
+        // no barrier here: the next item writes shared memory (its exchange and
+        // norms) only after its first barrier, which every thread reaches after
+        // this epilogue's reads
         if (np >= n_rows) break;
         new_row = np != row;
         new_series = nj == 0;
@@ -853,8 +857,6 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
         }
         const uint32_t t0 = j * p.V;
         const uint32_t nv = min(p.V, S.L - t0);
-        stage_norms<INV_PAIR>(m, S.inv + (size_t)j * p.Vp, nv, p.err);
-        cp_async_commit();
         uint32_t np = pair, nj = j + 1;
         int ns = s;
         if (nj >= S.nseg) {
@@ -864,8 +866,10 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
                 np = pair + gridDim.x;
             }
         }
-        cp_async_wait<1>();                         // this segment's spectrum
+        cp_async_wait<0>();                         // this segment's spectrum
         __syncthreads();
+        stage_norms<INV_PAIR>(m, S.inv + (size_t)j * p.Vp, nv, p.err);
+        cp_async_commit();
         // Z = X conj(H_a) + i X conj(H_b); Z[F - f] = conj(Ya) + i conj(Yb)
         float vr[16], vi[16];
 #pragma unroll
@@ -926,8 +930,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
         ss += pa;
         if (nj == 0)
             publish(best >= 0.f ? pack_max(best, arg) : 0ull, (double)ss, S.vmax + la, S.sumsq + la);
-        __syncthreads();
-        if (np >= n_pairs) break;
+        if (np >= n_pairs) break;               // (no barrier: see k_corr_rfft)
         new_pair = np != pair;
         new_series = nj == 0;
         pair = np;
