@@ -76,14 +76,14 @@ constexpr int UPPER = FH + FH / 16;       // padded distance of elements 4096 ap
 // twiddle tables e^{+2 pi i n / 8192}: pass 2 [15][16] (r (j mod 16) units of
 // 32), pass 3 [6][256] (r (j mod 256) units of 2 for r = 1, 2, 3, 4, 8, 12)
 constexpr int TW2 = 0, TW3 = 15 * 16, TW_N = TW3 + 6 * 256;     // 1776 entries
-constexpr int INV_PAIR = FN;              // window norms staged per segment (V <= 8192)
-constexpr int INV_REAL = FR;              // real route (V <= 16384)
-// shared memory: work array, twiddles, then (correlation only) the staged
-// segment spectrum and window norms
+// shared memory: work array, twiddles, then (correlation only) a second work
+// array, so that the passes alternate between the two, and the staged segment
+// spectrum (FH bins on the pair route, FN on the real route)
 constexpr size_t FFT_SMEM = (ZPAD + TW_N) * sizeof(float2);
-constexpr size_t CORR_SMEM = FFT_SMEM + FH * sizeof(float2) + INV_PAIR * sizeof(float);
-constexpr size_t RCORR_SMEM = FFT_SMEM + FN * sizeof(float2) + INV_REAL * sizeof(float);
+constexpr size_t CORR_SMEM = FFT_SMEM + ZPAD * sizeof(float2) + FH * sizeof(float2);
+constexpr size_t RCORR_SMEM = FFT_SMEM + ZPAD * sizeof(float2) + FN * sizeof(float2);
 static_assert(RCORR_SMEM <= 227 * 1024, "real-route correlation fits one SM's shared memory");
+static_assert(FFT_SMEM % 16 == 0 && (FFT_SMEM + ZPAD * sizeof(float2)) % 16 == 0, "16-byte staging");
 
 __global__ void k_fft_tables(float2* __restrict__ tw)
 {
@@ -102,20 +102,20 @@ __global__ void k_fft_tables(float2* __restrict__ tw)
     }
 }
 
-// Work array z (complex, index i stored at i + i/16), twiddle tables, and the
-// staging buffers of the correlation kernels (x: NX spectrum bins).
+// Work array z (complex, index i stored at i + i/16), twiddle tables, and, in
+// the correlation kernels, a second work array z2 and the staged spectrum x.
 struct Smem {
     float2* z;
     const float2* tw;
+    float2* z2;
     float2* x;
-    float* inv;
 };
 
-template <int NX>
+template <bool CORR>
 __device__ __forceinline__ Smem smem_setup(const float2* __restrict__ tw_global)
 {
     extern __shared__ __align__(16) float2 fsm[];
-    Smem m{fsm, fsm + ZPAD, fsm + ZPAD + TW_N, reinterpret_cast<float*>(fsm + ZPAD + TW_N + NX)};
+    Smem m{fsm, fsm + ZPAD, CORR ? fsm + ZPAD + TW_N : nullptr, CORR ? fsm + 2 * ZPAD + TW_N : nullptr};
     float4* dst = reinterpret_cast<float4*>(fsm + ZPAD);
     const float4* src = reinterpret_cast<const float4*>(tw_global);
     for (int i = threadIdx.x; i < TW_N / 2; i += blockDim.x) dst[i] = __ldg(src + i);
@@ -227,11 +227,12 @@ __device__ __forceinline__ void dft16(float (&r)[16], float (&i)[16])
 // thread j reads in[j + 512 r], twiddles by e^{SIGN 2 pi i r (j mod NS) / (16 NS)},
 // takes the 16-point DFT and writes out[(j / NS) 16 NS + j mod NS + q NS].
 // Padded addresses (i + i/16) are a per-thread base plus constant offsets.
-// The second half of a pass, from the 16 inputs already in registers; it
-// ends with a barrier, before which the calling thread's pending cp.async
-// groups but WAIT_CP are waited for (WAIT_CP < 0: no wait).
+// The second half of a pass, from the 16 inputs already in registers, into
+// the work array dst; it ends with a barrier, before which the calling
+// thread's pending cp.async groups but WAIT_CP are waited for (WAIT_CP < 0:
+// no wait).
 template <int SIGN, int NS, int WAIT_CP = -1>
-__device__ __forceinline__ void pass16_from(const Smem& m, float (&vr)[16], float (&vi)[16])
+__device__ __forceinline__ void pass16_from(const Smem& m, float2* dst, float (&vr)[16], float (&vi)[16])
 {
     const int j = threadIdx.x;
     if (NS == 16) {
@@ -268,34 +269,36 @@ __device__ __forceinline__ void pass16_from(const Smem& m, float (&vr)[16], floa
     for (int p = 0; p < 16; ++p) {
         const int q = 4 * (p % 4) + p / 4;
         const int off = NS == 1 ? q : NS == 16 ? 17 * q : 272 * q;
-        m.z[wb + off] = make_float2(vr[p], vi[p]);
+        dst[wb + off] = make_float2(vr[p], vi[p]);
     }
     if (WAIT_CP >= 0) cp_async_wait<(WAIT_CP >= 0 ? WAIT_CP : 0)>();
     __syncthreads();
 }
 
-template <int SIGN, int NS, int WAIT_CP = -1>
-__device__ __forceinline__ void pass16(const Smem& m)
+// A pass from work array src to dst; in place (src == dst) every thread's
+// reads complete at a barrier before the first write.
+template <int SIGN, int NS, int WAIT_CP = -1, bool IN_PLACE = true>
+__device__ __forceinline__ void pass16(const Smem& m, const float2* src, float2* dst)
 {
     const int j = threadIdx.x;
     const int rd = j + (j >> 4);
     float vr[16], vi[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-        const float2 v = m.z[rd + ROW * r];
+        const float2 v = src[rd + ROW * r];
         vr[r] = v.x;
         vi[r] = v.y;
     }
-    __syncthreads();
-    pass16_from<SIGN, NS, WAIT_CP>(m, vr, vi);
+    if (IN_PLACE) __syncthreads();
+    pass16_from<SIGN, NS, WAIT_CP>(m, dst, vr, vi);
 }
 
 template <int SIGN>
 __device__ __forceinline__ void fft_passes(const Smem& m)
 {
-    pass16<SIGN, 1>(m);
-    pass16<SIGN, 16>(m);
-    pass16<SIGN, 256>(m);
+    pass16<SIGN, 1>(m, m.z, m.z);
+    pass16<SIGN, 16>(m, m.z, m.z);
+    pass16<SIGN, 256>(m, m.z, m.z);
 }
 
 // twiddle e^{SIGN i pi k / 4096} of the final radix-2 stage for k = tid + 512 i
@@ -308,28 +311,28 @@ __device__ __forceinline__ float2 final_tw(float2 base_f, int i)
 }
 
 // The final radix-2 stage for output pair (k, k + 4096), k = tid + 512 i, with
-// its twiddle w = final_tw<SIGN>(base_f, i).
-__device__ __forceinline__ void fft_final(const Smem& m, int i, float2 w, float2& lo, float2& hi)
+// its twiddle w = final_tw<SIGN>(base_f, i), from the work array z.
+__device__ __forceinline__ void fft_final(const float2* z, int i, float2 w, float2& lo, float2& hi)
 {
     const int a = threadIdx.x + (threadIdx.x >> 4) + ROW * i;
-    const float2 v = m.z[a + UPPER];
+    const float2 v = z[a + UPPER];
     float vr = v.x, vi = v.y;
     rotate(vr, vi, w);
-    const float2 u = m.z[a];
+    const float2 u = z[a];
     lo = make_float2(u.x + vr, u.y + vi);
     hi = make_float2(u.x - vr, u.y - vi);
 }
 
 // Z[8192 - k] = the upper output of the final stage at 4096 - k, 1 <= k < 4096,
 // whose twiddle e^{SIGN i pi (4096 - k) / 4096} is -conj(w), w that of k
-__device__ __forceinline__ float2 fft_final_mirror(const Smem& m, int k, float2 w)
+__device__ __forceinline__ float2 fft_final_mirror(const float2* z, int k, float2 w)
 {
     const int kk = FH - k;
     const int a = kk + (kk >> 4);
-    const float2 v = m.z[a + UPPER];
+    const float2 v = z[a + UPPER];
     float vr = v.x, vi = v.y;
     rotate(vr, vi, make_float2(-w.x, w.y));
-    const float2 u = m.z[a];
+    const float2 u = z[a];
     return make_float2(u.x - vr, u.y - vi);
 }
 
@@ -352,12 +355,12 @@ __device__ __forceinline__ void real_spectrum(const Smem& m, float2 base_f, floa
         const int k = tid + FT * i;
         const float2 w = final_tw<-1>(base_f, i);
         float2 zk, zh;
-        fft_final(m, i, w, zk, zh);                               // U[k], U[k + 4096]
+        fft_final(m.z, i, w, zk, zh);                               // U[k], U[k + 4096]
         if (k == 0) {
             emit(i, 0, 0, make_float2(zk.x + zk.y, zk.x - zk.y));
             emit(i, 2, FH, make_float2(zh.x, -zh.y));
         } else {
-            const float2 zm = fft_final_mirror(m, k, w);         // U[N - k]
+            const float2 zm = fft_final_mirror(m.z, k, w);         // U[N - k]
             const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
             const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
             const float2 wr = cmul(base_r, root32(i));            // e^{i pi k / N}
@@ -383,7 +386,7 @@ template <bool REAL>
 __global__ void __launch_bounds__(FT, 1) k_fft_series(const __grid_constant__ FftSeriesBatch p,
                                                       uint32_t total)
 {
-    const Smem m = smem_setup<0>(p.tw);
+    const Smem m = smem_setup<false>(p.tw);
     const int tid = threadIdx.x;
     const float2 base_f = thread_root(4096.0);
     const float2 base_r = thread_root(8192.0);
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(FT, 1) k_fft_series(const __grid_constant__ Ff
 #pragma unroll
             for (int i = 0; i < FBINS; ++i) {
                 float2 lo, hi;
-                fft_final(m, i, final_tw<-1>(base_f, i), lo, hi);
+                fft_final(m.z, i, final_tw<-1>(base_f, i), lo, hi);
                 out[tid + FT * i] = (tid == 0 && i == 0) ? make_float2(lo.x, hi.x) : lo;
             }
         }
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(FT, 1) k_fft_bank(const float* __restrict__ ro
                                                     uint32_t n_items, const float2* __restrict__ tw,
                                                     float2* __restrict__ spec)
 {
-    const Smem m = smem_setup<0>(tw);
+    const Smem m = smem_setup<false>(tw);
     const int tid = threadIdx.x;
     const float2 base_f = thread_root(4096.0);
     const float2 base_r = thread_root(8192.0);
@@ -455,13 +458,13 @@ __global__ void __launch_bounds__(FT, 1) k_fft_bank(const float* __restrict__ ro
             const int k = tid + FT * i;
             const float2 w = final_tw<-1>(base_f, i);
             float2 zk, zn;
-            fft_final(m, i, w, zk, zn);            // Z[k], Z[k + 4096]
+            fft_final(m.z, i, w, zk, zn);          // Z[k], Z[k + 4096]
             if (k == 0) {
                 // DC and Nyquist of both real templates: real parts of Z[0], Z[4096]
                 sa[0] = make_float2(zk.x, zn.x);
                 if (b < n_rows) sb[0] = make_float2(zk.y, zn.y);
             } else {
-                const float2 zm = fft_final_mirror(m, k, w);      // Z[F - k]
+                const float2 zm = fft_final_mirror(m.z, k, w);    // Z[F - k]
                 // H_a = (Z[k] + conj Z[F-k]) / 2,  H_b = (Z[k] - conj Z[F-k]) / 2i
                 sa[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
                 if (b < n_rows) sb[k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
@@ -493,7 +496,7 @@ __device__ __forceinline__ void real_power_out(const Smem& m, float2 base_f, flo
 // seg_begin[s] + g of pseg gets |S[k]|^2 for k = 0 .. N.
 __global__ void __launch_bounds__(FT, 1) k_welch_segments(const __grid_constant__ WelchBatch p, uint32_t total)
 {
-    const Smem m = smem_setup<0>(p.tw);
+    const Smem m = smem_setup<false>(p.tw);
     const int tid = threadIdx.x;
     const float2 base_f = thread_root(4096.0);
     const float2 base_r = thread_root(8192.0);
@@ -539,7 +542,7 @@ __global__ void __launch_bounds__(FT, 1) k_template_power_dot(const float* __res
                                                               float* __restrict__ D, uint32_t d_stride,
                                                               uint32_t row0)
 {
-    const Smem m = smem_setup<0>(tw);
+    const Smem m = smem_setup<false>(tw);
     __shared__ double red[FT / 32];
     const int tid = threadIdx.x;
     const float2 base_f = thread_root(4096.0);
@@ -614,15 +617,6 @@ __device__ __forceinline__ void stage_spectrum(const Smem& m, const float2* src)
     for (int c = threadIdx.x; c < NX / 2; c += FT) cp_async16(m.x + 2 * c, src + 2 * c);
 }
 
-// window norms of a segment (a row of the per-segment copy, which starts
-// 16-byte aligned and has room for whole 16-byte copies) into shared memory
-template <int CAP>
-__device__ __forceinline__ void stage_norms(const Smem& m, const float* src, uint32_t nv, int* err)
-{
-    for (uint32_t c = threadIdx.x; 4 * c < nv; c += FT)
-        if (BF_BOUNDS(err, 4 * c + 4 <= (uint32_t)CAP)) cp_async16(m.inv + 4 * c, src + 4 * c);
-}
-
 // warp reduction of a packed max key and a sum, then one atomic each per warp
 __device__ __forceinline__ void publish(unsigned long long key, double d, unsigned long long* vmax,
                                        double* sumsq)
@@ -639,16 +633,58 @@ __device__ __forceinline__ void publish(unsigned long long key, double d, unsign
     }
 }
 
+// The transform of an item in both correlation kernels alternates between the
+// two work arrays, so that no pass waits for the reads of the one before:
+//   product spectrum from x: own bins in registers, mirrors into z   barrier 1
+//   (the next segment's spectrum starts to arrive in x)
+//   pass 1: registers and the mirrors read from z, into z2           barrier 2
+//   pass 2: z2 into z                                                 barrier 3
+//   pass 3: z into z2 (and the next spectrum has arrived)             barrier 4
+//   final radix-2 stage and epilogue read z2.
+// Each array's last reads come before the barrier that precedes its next
+// write: z is read by pass 3 (before barrier 4) and written by the next item's
+// product spectrum; z2 is read by the epilogue and written only after the next
+// item's barrier 1; x is read by the product spectrum and refilled after
+// barrier 1.  Four barriers per item.  The window norms (the per-segment copy,
+// 16-byte aligned rows, carrying 1/F) are read from L2 into registers, half of
+// them while pass 3 runs and half while the first half of the epilogue runs.
+
+// this thread's norms for the lag pairs t = 2 (tid + 512 (I0 + u) + 4096 h),
+// u < 4, of the real route (zero past the segment's nv lags)
+template <int I0>
+__device__ __forceinline__ void load_norm_pairs(const float* __restrict__ nrm, uint32_t nv, float2 (&iv)[8])
+{
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t t = 2u * (uint32_t)(threadIdx.x + FT * (I0 + u) + FH * h);
+            iv[2 * u + h] = t < nv ? __ldg(reinterpret_cast<const float2*>(nrm + t)) : make_float2(0.f, 0.f);
+        }
+}
+
+// the same for the lags t = tid + 512 (I0 + u) + 4096 h of the pair route
+template <int I0>
+__device__ __forceinline__ void load_norms(const float* __restrict__ nrm, uint32_t nv, float (&iv)[8])
+{
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t t = (uint32_t)(threadIdx.x + FT * (I0 + u) + FH * h);
+            iv[2 * u + h] = t < nv ? __ldg(nrm + t) : 0.f;
+        }
+}
+
 // The correlation of the real route (plain banks).  Each CTA walks its items
 // (template row, series, segment) in order; while the FFT of one segment
-// runs, the spectrum of the next one and the window norms of this one arrive
-// in shared memory.
+// runs, the spectrum of the next one arrives in shared memory.
 // DENSE: a series of the launch keeps the dense output rho (a compile-time
 // copy, so that the common case carries no per-lag test for it)
 template <bool DENSE>
 __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ FftParams p)
 {
-    const Smem m = smem_setup<FN>(p.tw);
+    const Smem m = smem_setup<true>(p.tw);
     const int tid = threadIdx.x;
     const int rd = tid + (tid >> 4);
     const int rv = (FN - tid) + ((FN - tid) >> 4);        // padded address of Z[N - tid]
@@ -661,6 +697,8 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
     uint32_t j = 0;
     stage_spectrum<FN>(m, p.ser[0].spec);
     cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
 
     float2 hk[FBINS], hp[FBINS], hm = make_float2(0.f, 0.f);
     uint32_t k = 0;
@@ -694,6 +732,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
         }
         const uint32_t t0 = j * p.V;
         const uint32_t nv = min(p.V, S.L - t0);
+        const float* nrm = S.inv + (size_t)j * p.Vp;     // (BF_BOUNDS above: j < nseg)
         // the item after this one
         uint32_t np = row, nj = j + 1;
         int ns = s;
@@ -704,12 +743,6 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
                 np = row + gridDim.x;
             }
         }
-        cp_async_wait<0>();                         // this segment's spectrum
-        __syncthreads();
-        // this segment's window norms (the previous item's epilogue read its own
-        // before the barrier above)
-        stage_norms<INV_REAL>(m, S.inv + (size_t)j * p.Vp, nv, p.err);
-        cp_async_commit();
         // Y = X conj(H) over all F bins, and the packed spectrum
         // Z'[f] = A + i w B, Z'[N - f] = conj(A - i w B), with A = Y[f] +
         // conj Y[N-f], B = Y[f] - conj Y[N-f], w = e^{i pi f / N}: twice the
@@ -743,63 +776,63 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
                 m.z[rv - ROW * r] = make_float2(ar + wbi, wbr - ai);
             }
         }
-        __syncthreads();
+        __syncthreads();                            // 1
+        if (np < n_rows) stage_spectrum<FN>(m, p.ser[ns].spec + (size_t)nj * FN);
+        cp_async_commit();
 #pragma unroll
         for (int r = FBINS; r < 16; ++r) {
             const float2 v = m.z[rd + ROW * r];
             vr[r] = v.x;
             vi[r] = v.y;
         }
-        if (np < n_rows) stage_spectrum<FN>(m, p.ser[ns].spec + (size_t)nj * FN);
-        cp_async_commit();
-        __syncthreads();                            // every exchange read before pass 1 writes
-        pass16_from<1, 1>(m, vr, vi);
-        pass16<1, 16>(m);
-        pass16<1, 256, 1>(m);                       // and this segment's window norms
+        pass16_from<1, 1>(m, m.z2, vr, vi);               // 2
+        pass16<1, 16, -1, false>(m, m.z2, m.z);           // 3
+        float2 iv0[8], iv1[8];
+        load_norm_pairs<0>(nrm, nv, iv0);
+        pass16<1, 256, 0, false>(m, m.z, m.z2);           // 4, and the next segment's spectrum
+        load_norm_pairs<4>(nrm, nv, iv1);
         float pa = 0.f;
-#pragma unroll 1
-        for (int i0 = 0; i0 < FBINS; i0 += 4) {
+        // lag pairs t = 2 (tid + 512 i + 4096 h) for i = i0 + u, with norms iv
+        auto lags = [&](const int i0, const float2 (&iv)[8]) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u;
-            float2 w = final_tw<1>(base_f, u);     // e^{i pi (tid + 512 u) / 4096} ...
-            if (i0) w = make_float2(-w.y, w.x);    // ... times e^{i pi / 2} for i = 4 + u
-            float2 z[2];
-            fft_final(m, i, w, z[0], z[1]);
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u;
+                float2 w = final_tw<1>(base_f, u);     // e^{i pi (tid + 512 u) / 4096} ...
+                if (i0) w = make_float2(-w.y, w.x);    // ... times e^{i pi / 2} for i = 4 + u
+                float2 z[2];
+                fft_final(m.z2, i, w, z[0], z[1]);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                // z = c[2n] + i c[2n + 1]: two consecutive lags
-                const uint32_t t = 2u * (uint32_t)(tid + FT * i + FH * h);
-                if (t < nv) {
-                    const float2 iv = *reinterpret_cast<const float2*>(m.inv + t);   // t + 1 < INV_REAL
-                    const uint32_t tau = t0 + t;
-                    const bool two = t + 1 < nv;          // the second lag is valid (its norm is staged)
-                    const float ra = z[h].x * iv.x;       // norms carry 1/F (k_fft_flags)
-                    const float rb = two ? z[h].y * iv.y : 0.f;
-                    const float aa = fabsf(ra), ab = fabsf(rb);
-                    // the pair's larger |rho|, the earlier lag on ties, into the running max
-                    const bool second = ab > aa;
-                    track_max(second ? ab : aa, second ? tau + 1 : tau, best, arg);
-                    pa = fmaf(ra, ra, pa);
-                    pa = fmaf(rb, rb, pa);
-                    if (fmaxf(aa, ab) >= thr) {
-                        if (aa >= thr) push_tail(p, S.series_id, k, tau, ra);
-                        if (two && ab >= thr) push_tail(p, S.series_id, k, tau + 1, rb);
-                    }
-                    if (DENSE && S.rho && BF_BOUNDS(p.err, tau + (two ? 1u : 0u) < S.L)) {
-                        S.rho[(size_t)o * S.L + tau] = ra;
-                        if (two) S.rho[(size_t)o * S.L + tau + 1] = rb;
+                for (int h = 0; h < 2; ++h) {
+                    // z = c[2n] + i c[2n + 1]: two consecutive lags
+                    const uint32_t t = 2u * (uint32_t)(tid + FT * i + FH * h);
+                    if (t < nv) {
+                        const uint32_t tau = t0 + t;
+                        const bool two = t + 1 < nv;          // the second lag is valid
+                        const float ra = z[h].x * iv[2 * u + h].x;    // norms carry 1/F (k_fft_flags)
+                        const float rb = two ? z[h].y * iv[2 * u + h].y : 0.f;
+                        const float aa = fabsf(ra), ab = fabsf(rb);
+                        // the pair's larger |rho|, the earlier lag on ties, into the running max
+                        const bool second = ab > aa;
+                        track_max(second ? ab : aa, second ? tau + 1 : tau, best, arg);
+                        pa = fmaf(ra, ra, pa);
+                        pa = fmaf(rb, rb, pa);
+                        if (fmaxf(aa, ab) >= thr) {
+                            if (aa >= thr) push_tail(p, S.series_id, k, tau, ra);
+                            if (two && ab >= thr) push_tail(p, S.series_id, k, tau + 1, rb);
+                        }
+                        if (DENSE && S.rho && BF_BOUNDS(p.err, tau + (two ? 1u : 0u) < S.L)) {
+                            S.rho[(size_t)o * S.L + tau] = ra;
+                            if (two) S.rho[(size_t)o * S.L + tau + 1] = rb;
+                        }
                     }
                 }
             }
-        }
-        }
+        };
+        lags(0, iv0);
+        lags(4, iv1);
         ss += pa;
         if (nj == 0)                                // last segment of this series: publish
             publish(best >= 0.f ? pack_max(best, arg) : 0ull, (double)ss, S.vmax + o, S.sumsq + o);
-        // no barrier here: the next item writes shared memory (its exchange and
-        // norms) only after its first barrier, which every thread reaches after
-        // this epilogue's reads
         if (np >= n_rows) break;
         new_row = np != row;
         new_series = nj == 0;
@@ -807,16 +840,15 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
         s = ns;
         j = nj;
     }
-    cp_async_wait<0>();
 }
 
 // The correlation of the pair route (quadrature banks): a template and its
 // quadrature partner in one complex transform, |rho| = |c_cos + i c_sin| /
 // |window|.  Each CTA walks its items (pair, series, segment) in order, with
-// the next segment's spectrum and this segment's norms staged as above.
+// the next segment's spectrum staged and the norms read as above.
 __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__ FftParams p)
 {
-    const Smem m = smem_setup<FH>(p.tw);
+    const Smem m = smem_setup<true>(p.tw);
     const int tid = threadIdx.x;
     const int rd = tid + (tid >> 4);
     const int rv = (FN - tid) + ((FN - tid) >> 4);        // padded address of Z[F - tid]
@@ -828,6 +860,8 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
     uint32_t j = 0;
     stage_spectrum<FH>(m, p.ser[0].spec);
     cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
 
     float2 ha[FBINS], hb[FBINS];
     uint32_t ka = 0;
@@ -857,6 +891,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
         }
         const uint32_t t0 = j * p.V;
         const uint32_t nv = min(p.V, S.L - t0);
+        const float* nrm = S.inv + (size_t)j * p.Vp;
         uint32_t np = pair, nj = j + 1;
         int ns = s;
         if (nj >= S.nseg) {
@@ -866,10 +901,6 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
                 np = pair + gridDim.x;
             }
         }
-        cp_async_wait<0>();                         // this segment's spectrum
-        __syncthreads();
-        stage_norms<INV_PAIR>(m, S.inv + (size_t)j * p.Vp, nv, p.err);
-        cp_async_commit();
         // Z = X conj(H_a) + i X conj(H_b); Z[F - f] = conj(Ya) + i conj(Yb)
         float vr[16], vi[16];
 #pragma unroll
@@ -890,54 +921,56 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
                 m.z[rv - ROW * i] = make_float2(yar + ybi, ybr - yai);
             }
         }
-        __syncthreads();
+        __syncthreads();                            // 1
+        if (np < n_pairs) stage_spectrum<FH>(m, p.ser[ns].spec + (size_t)nj * FH);
+        cp_async_commit();
 #pragma unroll
         for (int r = FBINS; r < 16; ++r) {
             const float2 v = m.z[rd + ROW * r];
             vr[r] = v.x;
             vi[r] = v.y;
         }
-        if (np < n_pairs) stage_spectrum<FH>(m, p.ser[ns].spec + (size_t)nj * FH);
-        cp_async_commit();
-        __syncthreads();                            // every exchange read before pass 1 writes
-        pass16_from<1, 1>(m, vr, vi);
-        pass16<1, 16>(m);
-        pass16<1, 256, 1>(m);                       // and this segment's window norms
+        pass16_from<1, 1>(m, m.z2, vr, vi);               // 2
+        pass16<1, 16, -1, false>(m, m.z2, m.z);           // 3
+        float iv0[8], iv1[8];
+        load_norms<0>(nrm, nv, iv0);
+        pass16<1, 256, 0, false>(m, m.z, m.z2);           // 4, and the next segment's spectrum
+        load_norms<4>(nrm, nv, iv1);
         float pa = 0.f;
-#pragma unroll 1
-        for (int i0 = 0; i0 < FBINS; i0 += 4) {
+        auto lags = [&](const int i0, const float (&iv)[8]) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u;
-            float2 w = final_tw<1>(base_f, u);
-            if (i0) w = make_float2(-w.y, w.x);
-            float2 z[2];
-            fft_final(m, i, w, z[0], z[1]);
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u;
+                float2 w = final_tw<1>(base_f, u);
+                if (i0) w = make_float2(-w.y, w.x);
+                float2 z[2];
+                fft_final(m.z2, i, w, z[0], z[1]);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t t = (uint32_t)(tid + FT * i + FH * h);
-                if (t < nv) {
-                    const uint32_t tau = t0 + t;
-                    const float r = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * m.inv[t];   // norms carry 1/F
-                    track_max(r, tau, best, arg);
-                    pa = fmaf(r, r, pa);
-                    if (r >= thr) push_tail(p, S.series_id, ka >> 1, tau, r);
-                    if (S.rho && BF_BOUNDS(p.err, tau < S.L)) S.rho[(size_t)la * S.L + tau] = r;
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t t = (uint32_t)(tid + FT * i + FH * h);
+                    if (t < nv) {
+                        const uint32_t tau = t0 + t;
+                        const float r = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * iv[2 * u + h];  // norms carry 1/F
+                        track_max(r, tau, best, arg);
+                        pa = fmaf(r, r, pa);
+                        if (r >= thr) push_tail(p, S.series_id, ka >> 1, tau, r);
+                        if (S.rho && BF_BOUNDS(p.err, tau < S.L)) S.rho[(size_t)la * S.L + tau] = r;
+                    }
                 }
             }
-        }
-        }
+        };
+        lags(0, iv0);
+        lags(4, iv1);
         ss += pa;
         if (nj == 0)
             publish(best >= 0.f ? pack_max(best, arg) : 0ull, (double)ss, S.vmax + la, S.sumsq + la);
-        if (np >= n_pairs) break;               // (no barrier: see k_corr_rfft)
+        if (np >= n_pairs) break;
         new_pair = np != pair;
         new_series = nj == 0;
         pair = np;
         s = ns;
         j = nj;
     }
-    cp_async_wait<0>();
 }
 
 // Lags whose window holds less than 1/FFT_FIX_RATIO2 of the energy of its
