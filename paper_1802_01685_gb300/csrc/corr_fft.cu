@@ -422,29 +422,17 @@ __global__ void __launch_bounds__(FT, 1) k_fft_series(const __grid_constant__ Ff
 }
 
 // Template spectra of a chunk of synthesised rows (rows of 8192 samples, zero
-// past M).  Pair route: rows (2q, 2q + 1) through one complex transform of
+// past M), pair route: rows (2q, 2q + 1) through one complex transform of
 // h_a + i h_b, separated by Hermitian symmetry into two half spectra of 4096
-// bins.  Real route: one row per transform, even/odd packed, zero past 8192
-// samples, 8192 bins.
-template <bool REAL>
-__global__ void __launch_bounds__(FT, 1) k_fft_bank(const float* __restrict__ rows, uint32_t n_rows,
-                                                    uint32_t n_items, const float2* __restrict__ tw,
-                                                    float2* __restrict__ spec)
+// bins.
+__global__ void __launch_bounds__(FT, 1) k_fft_bank_pair(const float* __restrict__ rows, uint32_t n_rows,
+                                                         uint32_t n_items, const float2* __restrict__ tw,
+                                                         float2* __restrict__ spec)
 {
     const Smem m = smem_setup<false>(tw);
     const int tid = threadIdx.x;
     const float2 base_f = thread_root(4096.0);
-    const float2 base_r = thread_root(8192.0);
     for (uint32_t q = blockIdx.x; q < n_items; q += gridDim.x) {
-        if (REAL) {
-            const float2* r2 = reinterpret_cast<const float2*>(rows + (size_t)q * FN);
-            for (int n = tid; n < FN; n += FT) m.z[n + (n >> 4)] = n < FH ? r2[n] : make_float2(0.f, 0.f);
-            __syncthreads();
-            fft_passes<-1>(m);
-            real_spectrum_out(m, base_f, base_r, spec + (size_t)q * FN);
-            __syncthreads();
-            continue;
-        }
         const uint32_t a = 2 * q, b = a + 1;
         const float* ra = rows + (size_t)a * FN;
         const float* rb = rows + (size_t)b * FN;
@@ -471,6 +459,54 @@ __global__ void __launch_bounds__(FT, 1) k_fft_bank(const float* __restrict__ ro
             }
         }
         __syncthreads();
+    }
+}
+
+// Template spectra of the real route from synthesised rows (8192 samples each,
+// zero past M): one row per transform, even/odd packed into 4096 complex
+// values and zero past them (the 16384-sample segment), 8192 bins per row.
+// While one row is transformed the next one's first M samples arrive by
+// cp.async, and the passes alternate between the two work arrays: four
+// barriers per row.  The upper half of the first pass's input is zero at
+// compile time.
+__global__ void __launch_bounds__(FT, 1) k_fft_bank_real(const float* __restrict__ rows, uint32_t n_rows,
+                                                         uint32_t M, const float2* __restrict__ tw,
+                                                         float2* __restrict__ spec)
+{
+    const Smem m = smem_setup<true>(tw);
+    const int tid = threadIdx.x;
+    const float2 base_f = thread_root(4096.0);
+    const float2 base_r = thread_root(8192.0);
+    const uint32_t n16 = (M + 3) / 4;             // 16-byte pieces holding a row's first M samples
+    const uint32_t mh = 2 * n16;                  // complex values staged (M <= FN: mh <= FH)
+    uint32_t q = blockIdx.x;
+    if (q >= n_rows) return;
+    auto stage = [&](uint32_t r) {
+        const float* src = rows + (size_t)r * FN;
+        for (uint32_t c = tid; c < n16; c += FT) cp_async16(m.x + 2 * c, src + 4 * c);
+    };
+    stage(q);
+    cp_async_commit();
+    for (;;) {
+        cp_async_wait<0>();
+        __syncthreads();                          // the row staged; the previous spectrum read
+        float vr[16], vi[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const uint32_t n = (uint32_t)(tid + FT * r);
+            const float2 v = r < FBINS && n < mh ? m.x[n] : make_float2(0.f, 0.f);
+            vr[r] = v.x;
+            vi[r] = v.y;
+        }
+        pass16_from<-1, 1>(m, m.z, vr, vi);       // every thread has read its staged values
+        const uint32_t qn = q + gridDim.x;
+        if (qn < n_rows) stage(qn);
+        cp_async_commit();
+        pass16<-1, 16, -1, false>(m, m.z, m.z2);
+        pass16<-1, 256, -1, false>(m, m.z2, m.z);
+        real_spectrum_out(m, base_f, base_r, spec + (size_t)q * FN);
+        if (qn >= n_rows) break;
+        q = qn;
     }
 }
 
@@ -615,6 +651,12 @@ template <int NX>
 __device__ __forceinline__ void stage_spectrum(const Smem& m, const float2* src)
 {
     for (int c = threadIdx.x; c < NX / 2; c += FT) cp_async16(m.x + 2 * c, src + 2 * c);
+}
+
+// a 128-byte line from DRAM into L2 (no register, no wait)
+__device__ __forceinline__ void prefetch_l2(const void* g)
+{
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(g));
 }
 
 // warp reduction of a packed max key and a sum, then one atomic each per warp
@@ -779,6 +821,8 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
         __syncthreads();                            // 1
         if (np < n_rows) stage_spectrum<FN>(m, p.ser[ns].spec + (size_t)nj * FN);
         cp_async_commit();
+        if (np != row && np < n_rows)               // the next row's template spectrum into L2 (64 KiB)
+            prefetch_l2(p.hspec + (size_t)(p.k_lo + np - p.hrow0) * FN + 16 * tid);
 #pragma unroll
         for (int r = FBINS; r < 16; ++r) {
             const float2 v = m.z[rd + ROW * r];
@@ -807,9 +851,10 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
                     const uint32_t t = 2u * (uint32_t)(tid + FT * i + FH * h);
                     if (t < nv) {
                         const uint32_t tau = t0 + t;
-                        const bool two = t + 1 < nv;          // the second lag is valid
-                        const float ra = z[h].x * iv[2 * u + h].x;    // norms carry 1/F (k_fft_flags)
-                        const float rb = two ? z[h].y * iv[2 * u + h].y : 0.f;
+                        // norms carry 1/F (k_fft_flags); the norm of t + 1 is 0
+                        // when t is the segment's last lag, and so is rb
+                        const float ra = z[h].x * iv[2 * u + h].x;
+                        const float rb = z[h].y * iv[2 * u + h].y;
                         const float aa = fabsf(ra), ab = fabsf(rb);
                         // the pair's larger |rho|, the earlier lag on ties, into the running max
                         const bool second = ab > aa;
@@ -818,11 +863,14 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
                         pa = fmaf(rb, rb, pa);
                         if (fmaxf(aa, ab) >= thr) {
                             if (aa >= thr) push_tail(p, S.series_id, k, tau, ra);
-                            if (two && ab >= thr) push_tail(p, S.series_id, k, tau + 1, rb);
+                            if (t + 1 < nv && ab >= thr) push_tail(p, S.series_id, k, tau + 1, rb);
                         }
-                        if (DENSE && S.rho && BF_BOUNDS(p.err, tau + (two ? 1u : 0u) < S.L)) {
-                            S.rho[(size_t)o * S.L + tau] = ra;
-                            if (two) S.rho[(size_t)o * S.L + tau + 1] = rb;
+                        if (DENSE && S.rho) {
+                            const bool two = t + 1 < nv;
+                            if (BF_BOUNDS(p.err, tau + (two ? 1u : 0u) < S.L)) {
+                                S.rho[(size_t)o * S.L + tau] = ra;
+                                if (two) S.rho[(size_t)o * S.L + tau + 1] = rb;
+                            }
                         }
                     }
                 }
@@ -924,6 +972,8 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
         __syncthreads();                            // 1
         if (np < n_pairs) stage_spectrum<FH>(m, p.ser[ns].spec + (size_t)nj * FH);
         cp_async_commit();
+        if (np != pair && np < n_pairs)             // the next pair's two spectra into L2 (64 KiB)
+            prefetch_l2(p.hspec + (size_t)(p.k_lo + 2 * np - p.hrow0) * FH + 16 * tid);
 #pragma unroll
         for (int r = FBINS; r < 16; ++r) {
             const float2 v = m.z[rd + ROW * r];
@@ -983,7 +1033,8 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
 // Every norm is also written, times the inverse transform's scale (a power of
 // two, so exactly), to the per-segment copy the correlation kernel stages:
 // segment j's lags at inv_seg[j Vp ..), Vp = V rounded up to a multiple of 4,
-// so every segment starts 16-byte aligned.
+// so every segment starts 16-byte aligned; past a segment's last lag its row
+// holds zeros, so that the real route reads whole pairs (t, t + 1) of norms.
 __global__ void __launch_bounds__(256) k_fft_flags(const __grid_constant__ FftSeriesBatch b)
 {
     const int i = blockIdx.y;
@@ -992,6 +1043,19 @@ __global__ void __launch_bounds__(256) k_fft_flags(const __grid_constant__ FftSe
     const double* S = b.S[i];
     float* inv = b.inv[i];
     const uint32_t lane = threadIdx.x & 31;
+    {
+        // the zeros: Vp - V per full segment, Vp - (its lags) in the last one
+        const uint64_t nseg = (L + b.V - 1) / b.V;
+        const uint64_t last = L - (nseg - 1) * b.V;
+        const uint64_t padv = b.Vp - b.V, n_full = (nseg - 1) * padv;
+        const uint64_t n_pad = n_full + (b.Vp - last);
+        for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n_pad;
+             q += (uint64_t)gridDim.x * blockDim.x) {
+            const uint64_t pos = q < n_full ? (q / padv) * b.Vp + b.V + q % padv
+                                            : (nseg - 1) * b.Vp + last + (q - n_full);
+            if (BF_BOUNDS(b.err, pos < nseg * b.Vp)) b.inv_seg[i][pos] = 0.f;
+        }
+    }
     // the loop bound is uniform over a warp, so each warp appends its lanes'
     // lags together, in lag order (the fixup reads them as coalesced runs)
     for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < L; base += (uint64_t)gridDim.x * blockDim.x) {
@@ -1163,9 +1227,9 @@ cudaError_t fft_attributes()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fft_series<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fft_bank<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+        e = cudaFuncSetAttribute(k_fft_bank_real, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CORR_SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fft_bank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
+        e = cudaFuncSetAttribute(k_fft_bank_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_welch_segments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
     if (e == cudaSuccess)
@@ -1224,8 +1288,8 @@ static cudaError_t template_spectra(const bf_bank* bank, size_t row0, size_t nro
         const uint32_t items = (uint32_t)(bank->quad ? nr / 2 : nr);
         const unsigned grid = std::min<uint32_t>(items, (uint32_t)n_sm);
         count_launches(1);
-        if (bank->quad) k_fft_bank<false><<<grid, FT, FFT_SMEM, st>>>(scratch, (uint32_t)kc, items, tw, out + k * bins);
-        else k_fft_bank<true><<<grid, FT, FFT_SMEM, st>>>(scratch, (uint32_t)kc, items, tw, out + k * bins);
+        if (bank->quad) k_fft_bank_pair<<<grid, FT, FFT_SMEM, st>>>(scratch, (uint32_t)kc, items, tw, out + k * bins);
+        else k_fft_bank_real<<<grid, FT, CORR_SMEM, st>>>(scratch, (uint32_t)kc, bank->M, tw, out + k * bins);
         e = cudaGetLastError();
     }
     return e;
