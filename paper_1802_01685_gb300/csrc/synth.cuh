@@ -85,28 +85,37 @@ __device__ __forceinline__ void synth_group(float (&v)[SYN_G], int j0, int dir, 
 // M_s is a multiple of SYN_G), returning the factor 1 / |g| that gives it unit
 // norm (0 for an all-zero row).  valid = false makes a zero row.  Called by all
 // 256 threads of the CTA; red holds 8 doubles of shared scratch.  Ends with a
-// CTA barrier, after which g is complete and red may be reused.
+// CTA barrier, after which g is complete and red may be reused.  The row's
+// FP64 constants (two divisions) and its norm (a square root and a division)
+// are computed once, by thread 0, and shared: the FP64 pipe is the bound.
 __device__ __forceinline__ float synth_row(const ChirpDev* __restrict__ params, uint32_t row, int quad,
                                            bool valid, uint32_t M, uint32_t M_s, double fs, float* g,
                                            double* red)
 {
+    __shared__ double s_c[3];           // k1, k2, 1/fs of this row
+    __shared__ float s_inv;             // 1/|g|
     const bool sine = quad && (row & 1u);
     ChirpDev p{};
     if (valid) p = params[quad ? row >> 1 : row];
 
-    const double inv_fs = 1.0 / fs;
-    double k1 = 0.0, k2 = 0.0;
-    float inv_md = 0.f;
-    if (valid) {
-        if (p.track == BF_LINEAR) {
-            k1 = p.f_lo;
-            k2 = (p.f_hi - p.f_lo) / (2.0 * p.D);
-        } else {
-            k1 = 1.6 * p.f_lo * p.tc;
-            k2 = 1.0 / p.tc;
+    if (threadIdx.x == 0) {
+        double c1 = 0.0, c2 = 0.0;
+        if (valid) {
+            if (p.track == BF_LINEAR) {
+                c1 = p.f_lo;
+                c2 = (p.f_hi - p.f_lo) / (2.0 * p.D);
+            } else {
+                c1 = 1.6 * p.f_lo * p.tc;
+                c2 = 1.0 / p.tc;
+            }
         }
-        inv_md = 1.0f / (float)p.MD;
+        s_c[0] = c1;
+        s_c[1] = c2;
+        s_c[2] = 1.0 / fs;
     }
+    __syncthreads();
+    const double k1 = s_c[0], k2 = s_c[1], inv_fs = s_c[2];
+    const float inv_md = valid ? 1.0f / (float)p.MD : 0.f;
     const float inv_fs_f = (float)inv_fs;
     const float k2f = (float)k2;
     double part = 0.0;
@@ -136,11 +145,13 @@ __device__ __forceinline__ float synth_row(const ChirpDev* __restrict__ params, 
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
     __syncthreads();
-    double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-    const float inv = tot > 0.0 ? (float)(1.0 / sqrt(tot)) : 0.f;
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        s_inv = tot > 0.0 ? (float)(1.0 / sqrt(tot)) : 0.f;
+    }
     __syncthreads();
-    return inv;
+    return s_inv;
 }
 
 }  // namespace bfi
