@@ -467,8 +467,9 @@ __global__ void __launch_bounds__(FT, 1) k_fft_bank_pair(const float* __restrict
 // values and zero past them (the 16384-sample segment), 8192 bins per row.
 // While one row is transformed the next one's first M samples arrive by
 // cp.async, and the passes alternate between the two work arrays: four
-// barriers per row.  The upper half of the first pass's input is zero at
-// compile time.
+// barriers per row.  The route takes M <= 4096, so the inputs past the first
+// quarter of the transform are zero, and the first pass knows it at compile
+// time.
 __global__ void __launch_bounds__(FT, 1) k_fft_bank_real(const float* __restrict__ rows, uint32_t n_rows,
                                                          uint32_t M, const float2* __restrict__ tw,
                                                          float2* __restrict__ spec)
@@ -478,7 +479,7 @@ __global__ void __launch_bounds__(FT, 1) k_fft_bank_real(const float* __restrict
     const float2 base_f = thread_root(4096.0);
     const float2 base_r = thread_root(8192.0);
     const uint32_t n16 = (M + 3) / 4;             // 16-byte pieces holding a row's first M samples
-    const uint32_t mh = 2 * n16;                  // complex values staged (M <= FN: mh <= FH)
+    const uint32_t mh = 2 * n16;                  // complex values staged (M <= FH: mh <= FH / 2)
     uint32_t q = blockIdx.x;
     if (q >= n_rows) return;
     auto stage = [&](uint32_t r) {
@@ -494,7 +495,7 @@ __global__ void __launch_bounds__(FT, 1) k_fft_bank_real(const float* __restrict
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const uint32_t n = (uint32_t)(tid + FT * r);
-            const float2 v = r < FBINS && n < mh ? m.x[n] : make_float2(0.f, 0.f);
+            const float2 v = r < FBINS / 2 && n < mh ? m.x[n] : make_float2(0.f, 0.f);
             vr[r] = v.x;
             vi[r] = v.y;
         }
@@ -637,13 +638,13 @@ __device__ __forceinline__ void push_tail(const FftParams& p, uint32_t series, u
     if (i < p.cand_cap) p.cand[i] = Candidate{series, k, tau, rho};
 }
 
-// running max |rho| with its first lag (lags arrive out of order within a thread)
-__device__ __forceinline__ void track_max(float a, uint32_t tau, float& best, uint32_t& arg)
+// running max |rho| with its first lag, as the packed key of pack_max (|rho|
+// >= 0, so its bits order as its values; then the lower lag): one unsigned
+// 64-bit max per update, whatever order the lags arrive in
+__device__ __forceinline__ void track_max(float a, uint32_t tau, unsigned long long& best)
 {
-    if (a > best || (a == best && tau < arg)) {
-        best = a;
-        arg = tau;
-    }
+    const unsigned long long key = pack_max(a, tau);
+    best = key > best ? key : best;
 }
 
 // segment spectrum of NX bins into shared memory (16-byte asynchronous copies)
@@ -744,8 +745,8 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
 
     float2 hk[FBINS], hp[FBINS], hm = make_float2(0.f, 0.f);
     uint32_t k = 0;
-    float thr = 0.f, best = -1.f;
-    uint32_t arg = 0xFFFFFFFFu;
+    float thr = 0.f;
+    unsigned long long best = 0ull;             // packed max key, 0: none yet
     // per-thread sum of rho^2 over a series (a few thousand terms of similar
     // size: FP32 is ample); the sum over threads is FP64
     float ss = 0.f;
@@ -768,8 +769,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
         (void)BF_BOUNDS(p.err, o < p.k_end - p.k_begin && k >= p.hrow0 && j < S.nseg);
         if (new_series) {
             thr = S.sigma_pred ? S.kappa * S.sigma_pred[o] : p.thr;
-            best = -1.f;
-            arg = 0xFFFFFFFFu;
+            best = 0ull;
             ss = 0.f;
         }
         const uint32_t t0 = j * p.V;
@@ -858,7 +858,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
                         const float aa = fabsf(ra), ab = fabsf(rb);
                         // the pair's larger |rho|, the earlier lag on ties, into the running max
                         const bool second = ab > aa;
-                        track_max(second ? ab : aa, second ? tau + 1 : tau, best, arg);
+                        track_max(second ? ab : aa, second ? tau + 1 : tau, best);
                         pa = fmaf(ra, ra, pa);
                         pa = fmaf(rb, rb, pa);
                         if (fmaxf(aa, ab) >= thr) {
@@ -880,7 +880,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
         lags(4, iv1);
         ss += pa;
         if (nj == 0)                                // last segment of this series: publish
-            publish(best >= 0.f ? pack_max(best, arg) : 0ull, (double)ss, S.vmax + o, S.sumsq + o);
+            publish(best, (double)ss, S.vmax + o, S.sumsq + o);
         if (np >= n_rows) break;
         new_row = np != row;
         new_series = nj == 0;
@@ -913,8 +913,8 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
 
     float2 ha[FBINS], hb[FBINS];
     uint32_t ka = 0;
-    float thr = 0.f, best = -1.f;
-    uint32_t arg = 0xFFFFFFFFu;
+    float thr = 0.f;
+    unsigned long long best = 0ull;
     float ss = 0.f;
     bool new_pair = true, new_series = true;
 
@@ -933,8 +933,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
         (void)BF_BOUNDS(p.err, ka + 1 < p.k_end && ka >= p.hrow0 && j < S.nseg);
         if (new_series) {
             thr = S.sigma_pred ? S.kappa * S.sigma_pred[la] : p.thr;
-            best = -1.f;
-            arg = 0xFFFFFFFFu;
+            best = 0ull;
             ss = 0.f;
         }
         const uint32_t t0 = j * p.V;
@@ -1001,7 +1000,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
                     if (t < nv) {
                         const uint32_t tau = t0 + t;
                         const float r = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * iv[2 * u + h];  // norms carry 1/F
-                        track_max(r, tau, best, arg);
+                        track_max(r, tau, best);
                         pa = fmaf(r, r, pa);
                         if (r >= thr) push_tail(p, S.series_id, ka >> 1, tau, r);
                         if (S.rho && BF_BOUNDS(p.err, tau < S.L)) S.rho[(size_t)la * S.L + tau] = r;
@@ -1013,7 +1012,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
         lags(4, iv1);
         ss += pa;
         if (nj == 0)
-            publish(best >= 0.f ? pack_max(best, arg) : 0ull, (double)ss, S.vmax + la, S.sumsq + la);
+            publish(best, (double)ss, S.vmax + la, S.sumsq + la);
         if (np >= n_pairs) break;
         new_pair = np != pair;
         new_series = nj == 0;
@@ -1278,6 +1277,7 @@ static cudaError_t template_spectra(const bf_bank* bank, size_t row0, size_t nro
                                     cudaStream_t st)
 {
     const size_t bins = fft_spec_bins(bank->quad);
+    if (bank->M > (uint32_t)FH) return cudaErrorInvalidValue;     // the route's limit (checked by the callers)
     cudaError_t e = cudaSuccess;
     for (size_t k = 0; k < nrows && e == cudaSuccess; k += scratch_rows) {
         const size_t kc = std::min(scratch_rows, nrows - k);     // rows of this sub-chunk
