@@ -738,6 +738,36 @@ def run_kernel_case(tile_lags: int, precision: str = "split_bf16"):
     bf.bf_destroy(ctx)
 
 
+def run_fft_step(steps: int, warmup: int):
+    """The GW-pair step on the FFT route alone, for launch lists: the two
+    series and their time-reversed copies (standing in for the controls,
+    same lengths) against the 65,536-template bank made from its parameters
+    (template spectra synthesised chunk by chunk), warm-up steps first; prints
+    each timed step's wall and CUDA-event kernel times."""
+    import torch
+    from paper_1802_01685_gb300 import bf, synth
+    import __graft_entry__
+    __graft_entry__.build()
+    w = synth.gw_pair()
+    fs = w["fs"]
+    ctx = bf.bf_init()
+    xs = [torch.from_numpy(x).cuda() for x in w["series"]]
+    xs = xs + [x.flip(0).contiguous() for x in xs]
+    opts = bf.make_opts(precision="fft_fp32", want_map=True, want_hist=True)
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        bank = bf.bf_bank_create_grid(ctx, w["grid"], fs, 1.0, bf.BF_BANK_GENERATED)
+        res = bf.bf_correlate(ctx, bank, xs, fs, opts)
+        wall = time.perf_counter() - t0
+        info = bf.bf_result_info_get(res)
+        if i >= warmup:
+            print(json.dumps({"fft_step": i - warmup, "wall_ms": round(1e3 * wall, 2),
+                              "kernel_ms": round(info.kernel_ms, 2)}), flush=True)
+        bf.bf_result_destroy(res)
+        bf.bf_bank_destroy(bank)
+    bf.bf_destroy(ctx)
+
+
 def run_workload_plan(ctx, bf, w, idx, ref):
     """The GRB batch as a plan: the 42-series search captured once as a CUDA
     graph (autotuned tile shape, one persistent correlation launch) and
@@ -958,6 +988,8 @@ def main():
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--fft", action="store_true", help="--kernel-case: the FFT route")
     ap.add_argument("--fp16", action="store_true", help="--kernel-case: the split-FP16 route")
+    ap.add_argument("--fft-step", action="store_true",
+                    help="run only the GW-pair step on the FFT route (--steps timed after --warmup)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-config5", action="store_true",
@@ -970,6 +1002,9 @@ def main():
     if args.kernel_case:
         run_kernel_case(args.tile_lags, "fft_fp32" if args.fft else
                         ("split_fp16" if args.fp16 else "split_bf16"))
+        return
+    if args.fft_step:
+        run_fft_step(args.steps, args.warmup)
         return
     if args.workload == "serving":
         run_serving_workload()
