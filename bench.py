@@ -347,10 +347,12 @@ def run_ours(args, rank, world, local):
 def run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step):
     """The step end to end through the public API: inputs from pinned host
     memory, results back into pinned host memory. A step's results are copied
-    by bf_result_copy_to_host_async on a second stream, into one of two sets
-    of host buffers, while the next step's correlation runs (after its
-    controls, whose device-to-host copies would otherwise queue behind them);
-    the result and its bank are destroyed once the copies are done. The last
+    on a second stream, into one of two sets of host buffers, while the next
+    step's correlation runs (after its controls, whose device-to-host copies
+    would otherwise queue behind them): maxima, argmaxes, sigmas and
+    histograms by bf_result_copy_to_host_async, and each map's painted cells
+    by bf_result_copy_map_cells_async (the map itself, cell by cell). The
+    result and its bank are destroyed once the copies are done. The last
     step's copies run and end inside the timed region."""
     fs = w["fs"]
     seeds = w["control_seeds"]
@@ -359,9 +361,11 @@ def run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step):
     copy_stream = torch.cuda.Stream()
     res_host = None                     # two sets of pinned host buffers, allocated once
     done = []                           # (result, bank) not yet copied
-    inflight = []                       # (result, bank) whose copies are enqueued
+    inflight = []                       # (result, bank, buffer set) whose copies are enqueued
     n_copied = 0
     d2h = [0]
+    cells_max = [0]
+    CELL_CAP = 1 << 20                  # painted cells per map that fit the buffers
 
     def pinned(shape, dtype):
         return torch.empty(shape, dtype=dtype, pin_memory=True).numpy()
@@ -375,20 +379,30 @@ def run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step):
                 res_host = [[{"max": pinned((K,), torch.float32), "argmax": pinned((K,), torch.int32),
                               "sigma": pinned((K,), torch.float32),
                               "hist": pinned((nbins,), torch.int32).view(np.uint32),
-                              "map": pinned(tuple(bf.bf_result_map_shape(res, s)), torch.float32)}
+                              "cell": pinned((CELL_CAP,), torch.int32).view(np.uint32),
+                              "value": pinned((CELL_CAP,), torch.float32),
+                              "count": pinned((1,), torch.int32).view(np.uint32)}
                              for s in range(4)] for _ in range(2)]
             d2h[0] = 0
+            hs = res_host[n_copied % 2]
             for s in range(4):
-                r = bf.bf_result_copy_to_host_async(res, s, res_host[n_copied % 2][s], copy_stream.cuda_stream,
-                                                    want_hist=True, want_map=True)
+                r = bf.bf_result_copy_to_host_async(res, s, hs[s], copy_stream.cuda_stream, want_hist=True)
                 d2h[0] += sum(a.nbytes for a in r.values() if a is not None)
+                bf.bf_result_copy_map_cells_async(res, s, hs[s]["cell"], hs[s]["value"], hs[s]["count"],
+                                                  copy_stream.cuda_stream)
             n_copied += 1
-            inflight.append((res, bank))
+            inflight.append((res, bank, hs))
         done.clear()
 
     def retire():
         copy_stream.synchronize()
-        for res, bank in inflight:
+        for res, bank, hs in inflight:
+            for s in range(4):
+                n = int(hs[s]["count"][0])
+                if n > CELL_CAP:
+                    raise RuntimeError(f"{n} painted cells: more than the {CELL_CAP} the buffers hold")
+                cells_max[0] = max(cells_max[0], n)
+                d2h[0] += 4 + 8 * n             # the count, then (cell, value) per painted cell
             bf.bf_result_destroy(res)
             bf.bf_bank_destroy(bank)
         inflight.clear()
@@ -438,10 +452,14 @@ def run_e2e(args, ctx, bf, torch, w, xs_host, opts, corr_per_step):
     h2d = 2 * N * 4 + 4 * N * 4                     # control inputs + the four searched series
     out = {"value": corr_per_step / (ms / 1e3), "unit": UNIT, "ms_per_step": round(ms, 2),
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h[0] + 2 * N * 4,
-           "steps": n, "inputs": "pinned host float32; each step's results copied by "
-                                 "bf_result_copy_to_host_async on a second stream into pinned host "
-                                 "buffers (two sets, allocated once) while the next step correlates; "
-                                 "the last step's copies run and end inside the timed region",
+           "steps": n, "inputs": "pinned host float32; each step's results copied on a second stream "
+                                 "into pinned host buffers (two sets, allocated once) while the next "
+                                 "step correlates: maxima, argmaxes, sigmas and histograms by "
+                                 "bf_result_copy_to_host_async, each map's painted cells by "
+                                 "bf_result_copy_map_cells_async (written by the kernels into mapped "
+                                 "pinned memory); the last step's copies run and end inside the "
+                                 "timed region",
+           "map_cells_max": cells_max[0],
            "phase_ms": {k: round(float(np.mean(v)), 2) for k, v in phases.items()},
            "last_step_copies_ms": round(last_ms, 2),
            "clocks": clocks}

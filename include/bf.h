@@ -376,6 +376,25 @@ bf_status bf_result_copy_to_host(const bf_result* r, size_t s, float* vmax,
 bf_status bf_result_copy_to_host_async(const bf_result* r, size_t s, float* vmax,
                                        int32_t* argmax, float* sigma, uint32_t* hist,
                                        float* map, void* stream);
+/* The painted (nonzero) cells of series s's time-frequency map (see
+ * bf_result_map_shape), in increasing cell index b nf + c, enqueued on
+ * `stream` (NULL: the legacy default stream) without waiting: cell[i] and
+ * value[i] for i < min(*count, cap), and *count = the number of painted
+ * cells, which may exceed cap (then call again with a larger cap).  The map
+ * of a search is sparse (Sect. 2.1: the tails rho > kappa sigma painted along
+ * the chirps' tracks), so this moves a few kilobytes where the dense map is
+ * map_nt * map_nf floats.  cell, value and count must be device memory or
+ * page-locked host memory mapped into the device's address space
+ * (cudaHostAlloc / cudaMallocHost under unified addressing, or
+ * cudaHostRegister with cudaHostRegisterMapped): the kernels write them
+ * directly.  The outputs are done when the stream is; until then `r` must not
+ * be destroyed (a plan's result: the plan must not run again), and only one
+ * such call per series of a result may be in flight.  Errors: BF_EINVAL for
+ * NULL arguments (cell and value may be NULL when cap = 0), a bad index, a
+ * result without maps, or arrays the device cannot address; BF_ENOTSUP for a
+ * map of more than 2^32 cells. */
+bf_status bf_result_copy_map_cells_async(const bf_result* r, size_t s, uint32_t* cell, float* value,
+                                         size_t cap, uint32_t* count, void* stream);
 /* Copies the per-template mean of the maxima (n_templates floats, Fig. 1)
  * to host memory, synchronously. */
 bf_status bf_result_copy_mean_max(const bf_result* r, float* host_mean_max);

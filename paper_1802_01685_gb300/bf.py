@@ -140,6 +140,7 @@ def load() -> C.CDLL:
             "bf_result_get_mean_max": (i, [p, P(p)]),
             "bf_result_copy_to_host": (i, [p, s, p, p, p, p, p]),
             "bf_result_copy_to_host_async": (i, [p, s, p, p, p, p, p, p]),
+            "bf_result_copy_map_cells_async": (i, [p, s, p, p, s, p, p]),
             "bf_result_copy_mean_max": (i, [p, p]),
             "bf_result_fit_max": (i, [p, s, p, P(bf_skewnorm)]),
             "bf_result_coincidence": (i, [p, s, s, d, C.c_uint32, p, p, p, p, p]),
@@ -399,6 +400,28 @@ def bf_result_copy_to_host_async(res: int, s: int, out: dict, stream=None, want_
         raise ValueError("an asynchronous copy needs every array it writes in `out`")
     _check(load().bf_result_copy_to_host_async(res, s, *_ptrs(arrs), stream))
     return arrs
+
+
+def _addr(a) -> int:
+    """Address of a torch tensor or a numpy array (no copy)."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def bf_result_copy_map_cells_async(res: int, s: int, cell, value, count, stream=None) -> None:
+    """Enqueues the compaction of series s's painted map cells into ``cell``
+    (uint32), ``value`` (float32), both of length cap, and ``count`` (one
+    uint32): device tensors or page-locked host memory mapped into the
+    device's address space (e.g. pinned torch tensors, or numpy views of
+    them). After the stream is synchronised, count[0] is the number of
+    painted cells and the first min(count[0], cap) entries hold them in
+    increasing cell index."""
+    cap = len(cell)
+    if len(value) != cap or len(count) < 1:
+        raise ValueError("cell and value must have the same length; count needs one element")
+    _check(load().bf_result_copy_map_cells_async(res, s, _addr(cell) if cap else None,
+                                                 _addr(value) if cap else None, cap, _addr(count), stream))
 
 
 def bf_result_copy_mean_max(res: int) -> np.ndarray:

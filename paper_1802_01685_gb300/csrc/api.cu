@@ -214,26 +214,63 @@ bf_status prepare_series_alloc(bf_ctx* ctx, size_t N, uint32_t M, uint32_t M_pad
     return BF_OK;
 }
 
+cudaError_t prepare_series_batch(const std::vector<const PreparedSeries*>& ps, uint32_t M, int precision,
+                                 cudaStream_t st)
+{
+    const int mode = precision == BF_SPLIT_FP16 ? 2 : uses_split_rows(precision) ? 1 : 0;
+    for (size_t i0 = 0; i0 < ps.size(); i0 += MAX_PREP) {
+        PrepBatch b{};
+        b.n = (int)std::min<size_t>(MAX_PREP, ps.size() - i0);
+        b.mode = mode;
+        b.M = M;
+        for (int i = 0; i < b.n; ++i) {
+            const PreparedSeries& p = *ps[i0 + i];
+            b.x[i] = p.x;
+            b.N[i] = p.N;
+            b.xcap[i] = p.xcap;
+            b.nb[i] = prep_scan_blocks(p.N);
+            if (2 * b.nb[i] > p.nb) return cudaErrorInvalidValue;      // the block-sum scratch
+            b.bsum[i] = p.bsum;
+            b.S[i] = p.prefix;
+            b.inv[i] = p.inv;
+            b.status[i] = p.status;
+            b.rows[i] = p.rows;
+            b.yhi[i] = p.yhi;
+            b.ylo[i] = p.ylo;
+            b.xmax[i] = p.xmax;
+        }
+        const cudaError_t e = launch_prep(b, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t prepare_series_kernels(const PreparedSeries& ps, uint32_t M, int precision,
                                    cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(ps.x + ps.N, 0, (ps.xcap - ps.N) * sizeof(float), st);
-    if (e == cudaSuccess) e = launch_inv_norm(ps.x, ps.N, M, ps.prefix, ps.bsum, ps.nb, ps.inv, st, ps.status);
-    if (e == cudaSuccess && precision == BF_SPLIT_FP16)
-        e = launch_split_rows_f16(ps.x, ps.N, ps.rows, ps.yhi, ps.ylo, ps.xmax, st);
-    else if (e == cudaSuccess && uses_split_rows(precision))
-        e = launch_split_rows(ps.x, ps.N, ps.rows, ps.yhi, ps.ylo, st);
-    return e;
+    return prepare_series_batch({&ps}, M, precision, st);
+}
+
+bf_status prepare_series_copy(bf_ctx* ctx, const float* src, size_t N, uint32_t M, uint32_t M_pad,
+                              int precision, cudaStream_t st, PreparedSeries* out, unsigned int* status)
+{
+    bf_status s = prepare_series_alloc(ctx, N, M, M_pad, precision, out);
+    if (s) return s;
+    out->status = status;
+    const cudaError_t e = cudaMemcpyAsync(out->x, src, N * sizeof(float), cudaMemcpyDefault, st);
+    if (e != cudaSuccess) {
+        out->release(*ctx->mem);
+        return cuda_fail(e, "series copy");
+    }
+    return BF_OK;
 }
 
 bf_status prepare_series(bf_ctx* ctx, const float* src, size_t N, uint32_t M, uint32_t M_pad,
                          int precision, cudaStream_t st, PreparedSeries* out, unsigned int* status)
 {
-    bf_status s = prepare_series_alloc(ctx, N, M, M_pad, precision, out);
+    bf_status s = prepare_series_copy(ctx, src, N, M, M_pad, precision, st, out, status);
     if (s) return s;
-    out->status = status;
-    cudaError_t e = cudaMemcpyAsync(out->x, src, N * sizeof(float), cudaMemcpyDefault, st);
-    if (e == cudaSuccess) e = prepare_series_kernels(*out, M, precision, st);
+    const cudaError_t e = prepare_series_kernels(*out, M, precision, st);
     if (e != cudaSuccess) {
         out->release(*ctx->mem);
         return cuda_fail(e, "series preparation");
@@ -559,7 +596,14 @@ bf_status alloc_result(bf_ctx* ctx, const bf_bank* bank, const bf_opts& o,
     }
     if (ok && r->want_map) {
         r->map = static_cast<float*>(out_alloc(map_total * 4));
-        ok = r->map != nullptr;
+        size_t blocks = 0;
+        for (size_t s = 0; s < S; ++s) {
+            r->cell_off.push_back(blocks);
+            blocks += map_cell_blocks((uint64_t)r->map_nt[s] * r->map_nf);
+        }
+        r->cell_counts = static_cast<uint32_t*>(mem.alloc(std::max<size_t>(blocks, 1) * sizeof(uint32_t)));
+        if (r->cell_counts) r->scratch.push_back(r->cell_counts);
+        ok = r->map != nullptr && r->cell_counts != nullptr;
     }
     if (!ok) {
         free_result_buffers(r.get());
@@ -587,7 +631,7 @@ size_t result_bytes(const bf_bank* bank, const bf_opts& o, size_t N, double fs, 
     if (o.want_map) {
         uint32_t nt, nf;
         map_shape(N, fs, o.map_dt_s, o.map_df_hz, &nt, &nf);
-        b += (size_t)nt * nf * 4;
+        b += (size_t)nt * nf * 4 + map_cell_blocks((uint64_t)nt * nf) * sizeof(uint32_t);
     }
     if (o.want_map || o.want_tails) b += max_cand * sizeof(Candidate);
     (void)bank;
@@ -1339,8 +1383,8 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
     std::vector<PreparedSeries*> pptr;
     std::vector<uint32_t> ids;
     for (size_t s = 0; s < n_series; ++s) {
-        st = prepare_series(ctx, series[s], lengths[s], bank->M, bank->M_pad, o.precision, strm, &prep[s],
-                            r->status);
+        st = prepare_series_copy(ctx, series[s], lengths[s], bank->M, bank->M_pad, o.precision, strm,
+                                 &prep[s], r->status);
         if (st) {
             for (auto& p : prep) p.release(*ctx->mem);
             return st;
@@ -1350,6 +1394,12 @@ bf_status bf_correlate(bf_ctx* ctx, const bf_bank* bank, const float* const* ser
         pptr.push_back(&prep[s]);
         ids.push_back((uint32_t)s);
         r->correlations += (double)prep[s].L * (double)r->K * (bank->quad ? 2.0 : 1.0);
+    }
+    {
+        // every series' padding, prefix, norms and split rows: one launch per kernel
+        const std::vector<const PreparedSeries*> pp(pptr.begin(), pptr.end());
+        const cudaError_t ep = prepare_series_batch(pp, bank->M, o.precision, strm);
+        if (ep != cudaSuccess) return cuda_fail(ep, "series preparation");
     }
     const bool fft = o.precision == BF_FFT_FP32;
     std::vector<Seg> segs;
@@ -1561,6 +1611,42 @@ bf_status bf_result_copy_to_host_async(const bf_result* r, size_t s, float* vmax
     if (!r) { set_error("NULL result"); return BF_EINVAL; }
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : cudaStreamLegacy;
     return copy_series(r, s, vmax, argmax, sigma, hist, map, st, true);
+}
+
+// a device address of p (device or managed memory, or page-locked host memory
+// mapped into the device's address space), else nullptr
+static void* device_view(void* p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return nullptr;
+}
+
+bf_status bf_result_copy_map_cells_async(const bf_result* r, size_t s, uint32_t* cell, float* value,
+                                         size_t cap, uint32_t* count, void* stream)
+{
+    if (!r || !count || (cap && (!cell || !value))) { set_error("NULL argument"); return BF_EINVAL; }
+    if (s >= r->n_series) { set_error("bad series index"); return BF_EINVAL; }
+    if (!r->map) { set_error("no map was requested"); return BF_EINVAL; }
+    const uint64_t n = (uint64_t)r->map_nt[s] * r->map_nf;
+    if (n > 0xFFFFFFFFull) { set_error("map of %llu cells: more than 32-bit indices", (unsigned long long)n); return BF_ENOTSUP; }
+    cudaSetDevice(r->ctx->device);
+    uint32_t* dcount = static_cast<uint32_t*>(device_view(count));
+    uint32_t* dcell = cap ? static_cast<uint32_t*>(device_view(cell)) : nullptr;
+    float* dvalue = cap ? static_cast<float*>(device_view(value)) : nullptr;
+    if (!dcount || (cap && (!dcell || !dvalue))) {
+        set_error("the cell arrays and the count must be device memory or mapped page-locked host memory");
+        return BF_EINVAL;
+    }
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : cudaStreamLegacy;
+    const cudaError_t e = launch_map_cells(r->map + r->map_off[s], n, r->cell_counts + r->cell_off[s], dcell,
+                                           dvalue, cap, dcount, st);
+    return e == cudaSuccess ? BF_OK : cuda_fail(e, "map cells");
 }
 
 bf_status bf_result_copy_mean_max(const bf_result* r, float* out)

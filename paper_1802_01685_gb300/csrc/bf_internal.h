@@ -258,12 +258,34 @@ cudaError_t launch_bank_synth(const ChirpDev* params, uint32_t row0, int quad, u
 // templates in the split-FP16 layout are scaled by this power of two
 constexpr float TEMPLATE_F16_SCALE = 256.f;
 
-// series preparation: padded FP32 copy, split rows, FP64 prefix, inverse norms
-cudaError_t launch_split_rows(const float* x, uint64_t N, uint64_t rows, uint4* yhi,
-                              uint4* ylo, cudaStream_t s);
-// split-FP16 rows of x 2^s, s from max |x| (written to *xmax as float bits)
-cudaError_t launch_split_rows_f16(const float* x, uint64_t N, uint64_t rows, uint4* yhi, uint4* ylo,
-                                  uint32_t* xmax, cudaStream_t s);
+// Series preparation, batched: one launch per kernel for up to MAX_PREP series
+// (blockIdx.y is the series).  For each series: zero its padding x[N, xcap),
+// the FP64 prefix of x^2 and of the nonzero count, the inverse window norms,
+// and (mode 1) split-BF16 rows or (mode 2) split-FP16 rows of x 2^s, s from
+// max |x| (written to *xmax as float bits).  status[i] (may be NULL): bit 0 set
+// when the FP64 total of x^2 is not finite, i.e. when a sample is NaN or
+// infinite.
+constexpr int MAX_PREP = 64;
+struct PrepBatch {
+    int n;
+    int mode;                       // 0: norms only, 1: + split-BF16 rows, 2: + split-FP16 rows
+    uint32_t M;
+    float* x[MAX_PREP];             // samples [0, N), padding [N, xcap)
+    uint64_t N[MAX_PREP];
+    uint64_t xcap[MAX_PREP];
+    uint64_t nb[MAX_PREP];          // FP64 scan blocks of the series
+    double* bsum[MAX_PREP];         // their sums: 2 nb doubles (energies, counts)
+    double* S[MAX_PREP];            // prefix of x^2 [N + 1], then the uint32 counts [N + 1]
+    float* inv[MAX_PREP];           // [N - M + 1]
+    unsigned int* status[MAX_PREP];
+    uint64_t rows[MAX_PREP];        // split rows
+    uint4* yhi[MAX_PREP];
+    uint4* ylo[MAX_PREP];
+    uint32_t* xmax[MAX_PREP];
+};
+cudaError_t launch_prep(const PrepBatch& b, cudaStream_t s);
+// scan blocks of a series of N samples, and the capacity of its block-sum scratch
+uint64_t prep_scan_blocks(uint64_t N);
 
 // The power-of-two exponent s that puts the largest |x| (float bits, >= 0) of a
 // series in [2^13, 2^14) for its FP16 split; 0 for an all-zero series.  s is
@@ -276,11 +298,6 @@ __host__ __device__ inline int f16_series_shift(uint32_t max_bits)
     const int s = 13 - e;                              // >= 13 - 127 = -114
     return s > 118 ? 118 : s;
 }
-// status (if not NULL): bit 0 set when the FP64 total of x^2 is not finite,
-// i.e. when a sample is NaN or infinite
-cudaError_t launch_inv_norm(const float* x, uint64_t N, uint32_t M, double* prefix,
-                            double* block_scratch, uint64_t n_blocks_cap, float* inv,
-                            cudaStream_t s, unsigned int* status = nullptr);
 uint64_t inv_norm_scratch_blocks(uint64_t N);
 // bytes of the prefix scratch: FP64 energies S[0..N], then uint32 counts C[0..N]
 size_t prefix_bytes(uint64_t N);
@@ -329,6 +346,12 @@ struct FftRing;
 cudaError_t fft_correlate_chunked(bf_ctx* ctx, const bf_bank* bank, std::vector<FftParams>& batches,
                                   uint32_t row_begin, uint32_t row_end, const FftRing& ring,
                                   cudaStream_t st);
+// the nonzero cells of a map of n_cells floats, in increasing index: cell[i],
+// value[i] for i < min(*total, cap), *total = their number; counts: scratch of
+// map_cell_blocks(n_cells) words
+uint64_t map_cell_blocks(uint64_t n_cells);
+cudaError_t launch_map_cells(const float* map, uint64_t n_cells, uint32_t* counts, uint32_t* cell, float* value,
+                             uint64_t cap, uint32_t* total, cudaStream_t s);
 cudaError_t launch_coincidence(const float* A, const float* B, uint32_t nt, uint32_t nf, uint32_t w,
                                uint32_t dt, unsigned int* out, int n_sm, cudaStream_t s);
 cudaError_t launch_skewnorm_fit(const float* v, uint64_t n, double* acc, double* out, int n_sm,
@@ -434,6 +457,8 @@ struct bf_result {
     float* map = nullptr;                   // concatenated per-series maps
     std::vector<size_t> map_off;            // element offsets into map
     size_t map_total = 0;
+    uint32_t* cell_counts = nullptr;        // per-block scratch of bf_result_copy_map_cells_async
+    std::vector<size_t> cell_off;           // each series' first block in it
     float* mean_max = nullptr;              // [K]
     bfi::Candidate* cand = nullptr;
     unsigned int* cand_count = nullptr;

@@ -284,4 +284,117 @@ cudaError_t launch_paint(const Candidate* cand, const unsigned int* count, unsig
     return cudaGetLastError();
 }
 
+// ---- Painted cells of a time-frequency map, in increasing cell index.
+// Three launches over the map's CELL_BLK-cell blocks: the nonzero count of
+// each block, an exclusive scan of those counts (one CTA; it also writes the
+// total), then each block writes its nonzero cells at its offset, in cell
+// order.  The outputs may be mapped page-locked host memory: only the painted
+// cells cross to the host.
+constexpr int CELL_T = 256;
+constexpr int CELL_IT = 32;                         // cells per thread per block
+constexpr uint32_t CELL_BLK = CELL_T * CELL_IT;     // 8192 cells per block
+
+uint64_t map_cell_blocks(uint64_t n_cells) { return (n_cells + CELL_BLK - 1) / CELL_BLK; }
+
+__global__ void __launch_bounds__(CELL_T) k_cells_count(const float* __restrict__ map, uint64_t n,
+                                                        uint32_t* __restrict__ counts)
+{
+    __shared__ uint32_t red[CELL_T / 32];
+    const uint64_t base = (uint64_t)blockIdx.x * CELL_BLK;
+    uint32_t c = 0;
+#pragma unroll 4
+    for (int it = 0; it < CELL_IT; ++it) {
+        const uint64_t i = base + (uint64_t)it * CELL_T + threadIdx.x;
+        if (i < n && map[i] != 0.f) ++c;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < CELL_T / 32; ++w) t += red[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+// exclusive scan of counts[0, nb) in place, and the total into *total
+__global__ void __launch_bounds__(1024) k_cells_scan(uint32_t* __restrict__ counts, uint64_t nb,
+                                                     uint32_t* __restrict__ total)
+{
+    __shared__ uint32_t sh[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (uint64_t c0 = 0; c0 < nb; c0 += blockDim.x) {
+        const uint64_t i = c0 + threadIdx.x;
+        const uint32_t v = i < nb ? counts[i] : 0u;
+        uint32_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) sh[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            sh[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t before = (wid > 0 ? sh[wid - 1] : 0u) + inc - v;
+        if (i < nb) counts[i] = carry + before;
+        carry += sh[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(CELL_T) k_cells_write(const float* __restrict__ map, uint64_t n,
+                                                        const uint32_t* __restrict__ offsets,
+                                                        uint32_t* __restrict__ cell, float* __restrict__ value,
+                                                        uint64_t cap)
+{
+    __shared__ uint32_t wsum[CELL_T / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint64_t base = (uint64_t)blockIdx.x * CELL_BLK;
+    uint64_t at = offsets[blockIdx.x];
+    for (int it = 0; it < CELL_IT; ++it) {
+        const uint64_t i = base + (uint64_t)it * CELL_T + threadIdx.x;
+        const float v = i < n ? map[i] : 0.f;
+        const bool hit = v != 0.f;
+        const uint32_t m = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) wsum[wid] = __popc(m);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < CELL_T / 32; ++w) {
+            before += w < wid ? wsum[w] : 0u;
+            total += wsum[w];
+        }
+        const uint64_t slot = at + before + __popc(m & ((1u << lane) - 1u));
+        if (hit && slot < cap) {
+            cell[slot] = (uint32_t)i;
+            value[slot] = v;
+        }
+        at += total;
+        __syncthreads();                            // wsum read before the next iteration writes it
+    }
+}
+
+cudaError_t launch_map_cells(const float* map, uint64_t n_cells, uint32_t* counts, uint32_t* cell, float* value,
+                             uint64_t cap, uint32_t* total, cudaStream_t s)
+{
+    const uint64_t nb = map_cell_blocks(n_cells);
+    if (nb == 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
+    if (nb > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    count_launches(3);
+    k_cells_count<<<(unsigned)nb, CELL_T, 0, s>>>(map, n_cells, counts);
+    k_cells_scan<<<1, 1024, 0, s>>>(counts, nb, total);
+    k_cells_write<<<(unsigned)nb, CELL_T, 0, s>>>(map, n_cells, counts, cell, value, cap);
+    return cudaGetLastError();
+}
+
 }  // namespace bfi

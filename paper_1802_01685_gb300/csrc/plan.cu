@@ -143,8 +143,10 @@ bf_status bf_plan_create(bf_ctx* ctx, const bf_bank* bank, const size_t* lengths
     cudaError_t e = cudaStreamBeginCapture(strm, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     cudaError_t ec = clear_result(p->r, strm);
-    for (size_t s = 0; s < n_series && ec == cudaSuccess; ++s)
-        ec = prepare_series_kernels(p->prep[s], bank->M, o.precision, strm);
+    if (ec == cudaSuccess) {
+        const std::vector<const PreparedSeries*> pp(pptr.begin(), pptr.end());
+        ec = prepare_series_batch(pp, bank->M, o.precision, strm);
+    }
     if (ec == cudaSuccess && p->r->parseval) ec = predict_launch(ctx, bank, pc, strm);
     if (ec == cudaSuccess)
         ec = fft              ? fft_launch(ctx, bank, fc, p->r, strm)

@@ -20,9 +20,15 @@
 
 namespace bfi {
 
-__global__ void k_split_rows(const float* __restrict__ x, uint64_t N, uint64_t rows,
-                             uint4* __restrict__ yhi, uint4* __restrict__ ylo)
+// split rows of series s = blockIdx.y: row w holds x[w .. w+7] (zero past N)
+__global__ void k_split_rows(const __grid_constant__ PrepBatch b)
 {
+    const int s = blockIdx.y;
+    if (s >= b.n) return;
+    const float* x = b.x[s];
+    const uint64_t N = b.N[s], rows = b.rows[s];
+    uint4* yhi = b.yhi[s];
+    uint4* ylo = b.ylo[s];
     for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < rows;
          w += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t h[4], l[4];
@@ -41,24 +47,33 @@ __global__ void k_split_rows(const float* __restrict__ x, uint64_t N, uint64_t r
     }
 }
 
-// max |x| as float bits (non-negative floats order like unsigned integers)
-__global__ void k_absmax(const float* __restrict__ x, uint64_t N, uint32_t* __restrict__ xmax)
+// max |x| of series blockIdx.y as float bits (non-negative floats order like
+// unsigned integers), into *xmax (zeroed by k_block_sq)
+__global__ void k_absmax(const __grid_constant__ PrepBatch b)
 {
+    const int s = blockIdx.y;
+    if (s >= b.n) return;
+    const float* x = b.x[s];
+    const uint64_t N = b.N[s];
     uint32_t m = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N;
          i += (uint64_t)gridDim.x * blockDim.x)
         m = max(m, __float_as_uint(fabsf(x[i])));
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(xmax, m);
+    if ((threadIdx.x & 31) == 0) atomicMax(b.xmax[s], m);
 }
 
 // Split rows as k_split_rows, in FP16 of x 2^s: hi = fp16(x 2^s), lo =
 // fp16(x 2^s - hi) (exact difference in FP32), s from the series' max |x|.
-__global__ void k_split_rows_f16(const float* __restrict__ x, uint64_t N, uint64_t rows,
-                                 uint4* __restrict__ yhi, uint4* __restrict__ ylo,
-                                 const uint32_t* __restrict__ xmax)
+__global__ void k_split_rows_f16(const __grid_constant__ PrepBatch b)
 {
-    const float scale = ldexpf(1.f, f16_series_shift(*xmax));
+    const int s = blockIdx.y;
+    if (s >= b.n) return;
+    const float* x = b.x[s];
+    const uint64_t N = b.N[s], rows = b.rows[s];
+    uint4* yhi = b.yhi[s];
+    uint4* ylo = b.ylo[s];
+    const float scale = ldexpf(1.f, f16_series_shift(*b.xmax[s]));
     for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < rows;
          w += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t h[4], l[4];
@@ -75,32 +90,6 @@ __global__ void k_split_rows_f16(const float* __restrict__ x, uint64_t N, uint64
         yhi[w] = make_uint4(h[0], h[1], h[2], h[3]);
         ylo[w] = make_uint4(l[0], l[1], l[2], l[3]);
     }
-}
-
-cudaError_t launch_split_rows_f16(const float* x, uint64_t N, uint64_t rows, uint4* yhi, uint4* ylo,
-                                  uint32_t* xmax, cudaStream_t s)
-{
-    cudaError_t e = cudaMemsetAsync(xmax, 0, sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
-    uint64_t b1 = std::min<uint64_t>((N + 255) / 256, 1024);
-    uint64_t blocks = (rows + 255) / 256;
-    if (blocks > 65535ull * 16) blocks = 65535ull * 16;
-    if (blocks == 0) blocks = 1;
-    count_launches(2);
-    k_absmax<<<(unsigned)std::max<uint64_t>(b1, 1), 256, 0, s>>>(x, N, xmax);
-    k_split_rows_f16<<<(unsigned)blocks, 256, 0, s>>>(x, N, rows, yhi, ylo, xmax);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_split_rows(const float* x, uint64_t N, uint64_t rows, uint4* yhi, uint4* ylo,
-                              cudaStream_t s)
-{
-    uint64_t blocks = (rows + 255) / 256;
-    if (blocks > 65535ull * 16) blocks = 65535ull * 16;
-    if (blocks == 0) blocks = 1;
-    count_launches(1);
-    k_split_rows<<<(unsigned)blocks, 256, 0, s>>>(x, N, rows, yhi, ylo);
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- FP64 scan
@@ -138,11 +127,21 @@ __device__ __forceinline__ double block_excl_scan(double v, double* sh, double* 
 }
 
 // Per-block sums of x^2 (FP64) and of the count of nonzero samples (an exact
-// integer in FP64): bsum[0, nb) and bsum[nb, 2 nb).
-__global__ void __launch_bounds__(SCAN_T) k_block_sq(const float* __restrict__ x, uint64_t N, uint64_t nb,
-                                                     double* __restrict__ bsum)
+// integer in FP64) of series s = blockIdx.y: bsum[0, nb) and bsum[nb, 2 nb).
+// The same launch zeroes the series' padding x[N, xcap) and its max |x| word.
+__global__ void __launch_bounds__(SCAN_T) k_block_sq(const __grid_constant__ PrepBatch b)
 {
     __shared__ double sh[SCAN_T / 32];
+    const int s = blockIdx.y;
+    if (s >= b.n) return;
+    const float* x = b.x[s];
+    const uint64_t N = b.N[s], nb = b.nb[s];
+    for (uint64_t i = N + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < b.xcap[s];
+         i += (uint64_t)gridDim.x * blockDim.x)
+        b.x[s][i] = 0.f;
+    if (b.mode == 2 && blockIdx.x == 0 && threadIdx.x == 0) *b.xmax[s] = 0u;
+    if (blockIdx.x >= nb) return;
+    double* bsum = b.bsum[s];
     uint64_t base = (uint64_t)blockIdx.x * SCAN_B + (uint64_t)threadIdx.x * SCAN_E;
     double v = 0.0, c = 0.0;
 #pragma unroll
@@ -162,11 +161,15 @@ __global__ void __launch_bounds__(SCAN_T) k_block_sq(const float* __restrict__ x
     }
 }
 
-// exclusive scan of the n block sums of one lane, in place (one block)
-__global__ void __launch_bounds__(SCAN_T) k_scan_sums(double* __restrict__ bsum, uint64_t n)
+// exclusive scan of the nb block sums of one lane of series blockIdx.y, in
+// place (block x = 0: energies, 1: counts)
+__global__ void __launch_bounds__(SCAN_T) k_scan_sums(const __grid_constant__ PrepBatch b)
 {
     __shared__ double sh[SCAN_T / 32];
-    double* lane_sums = bsum + blockIdx.x * n;        // block 0: energies, block 1: counts
+    const int s = blockIdx.y;
+    if (s >= b.n) return;
+    const uint64_t n = b.nb[s];
+    double* lane_sums = b.bsum[s] + blockIdx.x * n;
     double carry = 0.0;
     for (uint64_t c = 0; c < n; c += SCAN_T) {
         uint64_t i = c + threadIdx.x;
@@ -180,12 +183,18 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_sums(double* __restrict__ bsum,
     }
 }
 
-// S[t] = sum_{i < t} x_i^2 and C[t] = #{i < t : x_i != 0}, t = 0..N
-__global__ void __launch_bounds__(SCAN_T) k_prefix(const float* __restrict__ x, uint64_t N, uint64_t nb,
-                                                   const double* __restrict__ boff,
-                                                   double* __restrict__ S, uint32_t* __restrict__ C)
+// S[t] = sum_{i < t} x_i^2 and C[t] = #{i < t : x_i != 0}, t = 0..N, of
+// series blockIdx.y
+__global__ void __launch_bounds__(SCAN_T) k_prefix(const __grid_constant__ PrepBatch b)
 {
     __shared__ double sh[SCAN_T / 32];
+    const int s = blockIdx.y;
+    if (s >= b.n || blockIdx.x >= b.nb[s]) return;
+    const float* x = b.x[s];
+    const uint64_t N = b.N[s], nb = b.nb[s];
+    const double* boff = b.bsum[s];
+    double* S = b.S[s];
+    uint32_t* C = reinterpret_cast<uint32_t*>(S + N + 1);
     uint64_t base = (uint64_t)blockIdx.x * SCAN_B + (uint64_t)threadIdx.x * SCAN_E;
     double v[SCAN_E];
     uint32_t nz[SCAN_E];
@@ -223,14 +232,20 @@ __global__ void __launch_bounds__(SCAN_T) k_prefix(const float* __restrict__ x, 
 // few ulps of S[t+M]; where the window holds less than 2^-30 of the energy
 // before it (a quiet stretch after loud data) that would be a relative error
 // above ~5e-6, so such windows are summed directly (x^2 is exact in FP64).
-// The first thread also reports a non-finite series: the FP64 total of x^2
-// (at most 2^32 squares of floats, far below the FP64 range) is finite
-// exactly when every sample is.
-__global__ void k_inv_norm(const float* __restrict__ x, const double* __restrict__ S,
-                           const uint32_t* __restrict__ C, uint64_t L, uint32_t M,
-                           float* __restrict__ inv, unsigned int* __restrict__ status)
+// The first thread of a series also reports a non-finite series: the FP64
+// total of x^2 (at most 2^32 squares of floats, far below the FP64 range) is
+// finite exactly when every sample is.
+__global__ void k_inv_norm(const __grid_constant__ PrepBatch b)
 {
-    if (status && blockIdx.x == 0 && threadIdx.x == 0 && !isfinite(S[L + M - 1])) atomicOr(status, 1u);
+    const int s = blockIdx.y;
+    if (s >= b.n) return;
+    const float* x = b.x[s];
+    const uint32_t M = b.M;
+    const uint64_t N = b.N[s], L = N - M + 1;
+    const double* S = b.S[s];
+    const uint32_t* C = reinterpret_cast<const uint32_t*>(S + N + 1);
+    float* inv = b.inv[s];
+    if (b.status[s] && blockIdx.x == 0 && threadIdx.x == 0 && !isfinite(S[N])) atomicOr(b.status[s], 1u);
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < L;
          t += (uint64_t)gridDim.x * blockDim.x) {
         double nu = S[t + M] - S[t];
@@ -249,21 +264,36 @@ __global__ void k_inv_norm(const float* __restrict__ x, const double* __restrict
 
 size_t prefix_bytes(uint64_t N) { return (N + 1) * (sizeof(double) + sizeof(uint32_t)); }
 
-cudaError_t launch_inv_norm(const float* x, uint64_t N, uint32_t M, double* prefix,
-                            double* block_scratch, uint64_t n_blocks_cap, float* inv,
-                            cudaStream_t s, unsigned int* status)
+uint64_t prep_scan_blocks(uint64_t N) { return (N + SCAN_B - 1) / SCAN_B; }
+
+cudaError_t launch_prep(const PrepBatch& b, cudaStream_t st)
 {
-    uint64_t nb = (N + SCAN_B - 1) / SCAN_B;
-    if (nb == 0 || 2 * nb > n_blocks_cap || N < M) return cudaErrorInvalidValue;
-    uint32_t* counts = reinterpret_cast<uint32_t*>(prefix + N + 1);
+    if (b.n <= 0 || b.n > MAX_PREP) return cudaErrorInvalidValue;
+    uint64_t nb = 0, lmax = 0, rmax = 0, nmax = 0;
+    for (int i = 0; i < b.n; ++i) {
+        if (b.N[i] < b.M || b.nb[i] != prep_scan_blocks(b.N[i]) || b.nb[i] == 0) return cudaErrorInvalidValue;
+        nb = std::max(nb, b.nb[i]);
+        lmax = std::max(lmax, b.N[i] - b.M + 1);
+        rmax = std::max(rmax, b.rows[i]);
+        nmax = std::max(nmax, b.N[i]);
+    }
+    auto grid_x = [](uint64_t work) {
+        return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, 65535ull * 16));
+    };
+    const unsigned ny = (unsigned)b.n;
     count_launches(4);
-    k_block_sq<<<(unsigned)nb, SCAN_T, 0, s>>>(x, N, nb, block_scratch);
-    k_scan_sums<<<2, SCAN_T, 0, s>>>(block_scratch, nb);
-    k_prefix<<<(unsigned)nb, SCAN_T, 0, s>>>(x, N, nb, block_scratch, prefix, counts);
-    uint64_t L = N - M + 1;
-    uint64_t blocks = (L + 255) / 256;
-    if (blocks > 65535ull * 16) blocks = 65535ull * 16;
-    k_inv_norm<<<(unsigned)blocks, 256, 0, s>>>(x, prefix, counts, L, M, inv, status);
+    k_block_sq<<<dim3((unsigned)nb, ny), SCAN_T, 0, st>>>(b);
+    k_scan_sums<<<dim3(2, ny), SCAN_T, 0, st>>>(b);
+    k_prefix<<<dim3((unsigned)nb, ny), SCAN_T, 0, st>>>(b);
+    k_inv_norm<<<dim3(grid_x(lmax), ny), 256, 0, st>>>(b);
+    if (b.mode == 1) {
+        count_launches(1);
+        k_split_rows<<<dim3(grid_x(rmax), ny), 256, 0, st>>>(b);
+    } else if (b.mode == 2) {
+        count_launches(2);
+        k_absmax<<<dim3((unsigned)std::min<uint64_t>((nmax + 255) / 256, 1024), ny), 256, 0, st>>>(b);
+        k_split_rows_f16<<<dim3(grid_x(rmax), ny), 256, 0, st>>>(b);
+    }
     return cudaGetLastError();
 }
 

@@ -34,6 +34,12 @@ bf_status prepare_series_alloc(bf_ctx* ctx, size_t N, uint32_t M, uint32_t M_pad
                                PreparedSeries* out);
 cudaError_t prepare_series_kernels(const PreparedSeries& ps, uint32_t M, int precision,
                                    cudaStream_t st);
+// the same kernels for many series, one launch per kernel for MAX_PREP series
+cudaError_t prepare_series_batch(const std::vector<const PreparedSeries*>& ps, uint32_t M, int precision,
+                                 cudaStream_t st);
+// prepare_series_alloc, then the copy of src into ps.x (no kernels)
+bf_status prepare_series_copy(bf_ctx* ctx, const float* src, size_t N, uint32_t M, uint32_t M_pad,
+                              int precision, cudaStream_t st, PreparedSeries* out, unsigned int* status);
 void build_segments(const std::vector<PreparedSeries*>& ser, const std::vector<uint32_t>& ids,
                     const bf_bank* bank, size_t k_begin, size_t k_end, int precision,
                     unsigned long long* packed, double* sumsq, size_t K, std::vector<Seg>& segs);
