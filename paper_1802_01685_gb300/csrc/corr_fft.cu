@@ -647,6 +647,21 @@ __device__ __forceinline__ void track_max(float a, uint32_t tau, unsigned long l
     best = key > best ? key : best;
 }
 
+// the largest of the warp's packed keys: the largest value bits, then among
+// the lanes that hold them the largest low word (the earliest lag)
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k)
+{
+    const uint32_t hi = __reduce_max_sync(0xffffffffu, (uint32_t)(k >> 32));
+    const uint32_t lo = __reduce_max_sync(0xffffffffu, (uint32_t)(k >> 32) == hi ? (uint32_t)k : 0u);
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// the warp's largest of the non-negative g (float bits order as values)
+__device__ __forceinline__ float warp_max_abs(float g)
+{
+    return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(g)));
+}
+
 // segment spectrum of NX bins into shared memory (16-byte asynchronous copies)
 template <int NX>
 __device__ __forceinline__ void stage_spectrum(const Smem& m, const float2* src)
@@ -746,7 +761,10 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
     float2 hk[FBINS], hp[FBINS], hm = make_float2(0.f, 0.f);
     uint32_t k = 0;
     float thr = 0.f;
-    unsigned long long best = 0ull;             // packed max key, 0: none yet
+    // the warp's packed max key over the series so far (0: none yet) and its
+    // value: a lag below both it and the tail threshold changes nothing
+    unsigned long long best = 0ull;
+    float best_v = 0.f;
     // per-thread sum of rho^2 over a series (a few thousand terms of similar
     // size: FP32 is ample); the sum over threads is FP64
     float ss = 0.f;
@@ -770,6 +788,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
         if (new_series) {
             thr = S.sigma_pred ? S.kappa * S.sigma_pred[o] : p.thr;
             best = 0ull;
+            best_v = 0.f;
             ss = 0.f;
         }
         const uint32_t t0 = j * p.V;
@@ -845,34 +864,52 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
                 if (i0) w = make_float2(-w.y, w.x);    // ... times e^{i pi / 2} for i = 4 + u
                 float2 z[2];
                 fft_final(m.z2, i, w, z[0], z[1]);
+                // z = c[2n] + i c[2n + 1]: the lag pairs t = 2 (tid + 512 i + 4096 h);
+                // norms carry 1/F (k_fft_flags), and the norm of t + 1 is 0 when t
+                // is the segment's last lag, so rb is 0 there
+                float ra[2], rb[2], g = 0.f;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    // z = c[2n] + i c[2n + 1]: two consecutive lags
                     const uint32_t t = 2u * (uint32_t)(tid + FT * i + FH * h);
+                    ra[h] = rb[h] = 0.f;
                     if (t < nv) {
-                        const uint32_t tau = t0 + t;
-                        // norms carry 1/F (k_fft_flags); the norm of t + 1 is 0
-                        // when t is the segment's last lag, and so is rb
-                        const float ra = z[h].x * iv[2 * u + h].x;
-                        const float rb = z[h].y * iv[2 * u + h].y;
-                        const float aa = fabsf(ra), ab = fabsf(rb);
-                        // the pair's larger |rho|, the earlier lag on ties, into the running max
-                        const bool second = ab > aa;
-                        track_max(second ? ab : aa, second ? tau + 1 : tau, best);
-                        pa = fmaf(ra, ra, pa);
-                        pa = fmaf(rb, rb, pa);
-                        if (fmaxf(aa, ab) >= thr) {
-                            if (aa >= thr) push_tail(p, S.series_id, k, tau, ra);
-                            if (t + 1 < nv && ab >= thr) push_tail(p, S.series_id, k, tau + 1, rb);
-                        }
+                        ra[h] = z[h].x * iv[2 * u + h].x;
+                        rb[h] = z[h].y * iv[2 * u + h].y;
                         if (DENSE && S.rho) {
+                            const uint32_t tau = t0 + t;
                             const bool two = t + 1 < nv;
                             if (BF_BOUNDS(p.err, tau + (two ? 1u : 0u) < S.L)) {
-                                S.rho[(size_t)o * S.L + tau] = ra;
-                                if (two) S.rho[(size_t)o * S.L + tau + 1] = rb;
+                                S.rho[(size_t)o * S.L + tau] = ra[h];
+                                if (two) S.rho[(size_t)o * S.L + tau + 1] = rb[h];
                             }
                         }
                     }
+                    pa = fmaf(ra[h], ra[h], pa);
+                    pa = fmaf(rb[h], rb[h], pa);
+                    g = fmaxf(g, fmaxf(fabsf(ra[h]), fabsf(rb[h])));
+                }
+                // only lags reaching the warp's running max (ties included: an
+                // earlier lag wins them) or the tail threshold need their keys
+                if (warp_max_abs(g) >= fminf(thr, best_v)) {
+                    unsigned long long lk = 0ull;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t t = 2u * (uint32_t)(tid + FT * i + FH * h);
+                        if (t < nv) {
+                            const uint32_t tau = t0 + t;
+                            const float aa = fabsf(ra[h]), ab = fabsf(rb[h]);
+                            // the pair's larger |rho|, the earlier lag on ties
+                            const bool second = ab > aa;
+                            track_max(second ? ab : aa, second ? tau + 1 : tau, lk);
+                            if (fmaxf(aa, ab) >= thr) {
+                                if (aa >= thr) push_tail(p, S.series_id, k, tau, ra[h]);
+                                if (t + 1 < nv && ab >= thr) push_tail(p, S.series_id, k, tau + 1, rb[h]);
+                            }
+                        }
+                    }
+                    lk = warp_max_key(lk);
+                    best = lk > best ? lk : best;
+                    best_v = __uint_as_float((uint32_t)(best >> 32));
                 }
             }
         };
@@ -914,7 +951,8 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
     float2 ha[FBINS], hb[FBINS];
     uint32_t ka = 0;
     float thr = 0.f;
-    unsigned long long best = 0ull;
+    unsigned long long best = 0ull;             // the warp's packed max key, as above
+    float best_v = 0.f;
     float ss = 0.f;
     bool new_pair = true, new_series = true;
 
@@ -934,6 +972,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
         if (new_series) {
             thr = S.sigma_pred ? S.kappa * S.sigma_pred[la] : p.thr;
             best = 0ull;
+            best_v = 0.f;
             ss = 0.f;
         }
         const uint32_t t0 = j * p.V;
@@ -994,17 +1033,31 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
                 if (i0) w = make_float2(-w.y, w.x);
                 float2 z[2];
                 fft_final(m.z2, i, w, z[0], z[1]);
+                float r[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const uint32_t t = (uint32_t)(tid + FT * i + FH * h);
+                    r[h] = 0.f;
                     if (t < nv) {
                         const uint32_t tau = t0 + t;
-                        const float r = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * iv[2 * u + h];  // norms carry 1/F
-                        track_max(r, tau, best);
-                        pa = fmaf(r, r, pa);
-                        if (r >= thr) push_tail(p, S.series_id, ka >> 1, tau, r);
-                        if (S.rho && BF_BOUNDS(p.err, tau < S.L)) S.rho[(size_t)la * S.L + tau] = r;
+                        r[h] = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * iv[2 * u + h];   // norms carry 1/F
+                        pa = fmaf(r[h], r[h], pa);
+                        if (S.rho && BF_BOUNDS(p.err, tau < S.L)) S.rho[(size_t)la * S.L + tau] = r[h];
                     }
+                }
+                if (warp_max_abs(fmaxf(r[0], r[1])) >= fminf(thr, best_v)) {
+                    unsigned long long lk = 0ull;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t t = (uint32_t)(tid + FT * i + FH * h);
+                        if (t < nv) {
+                            track_max(r[h], t0 + t, lk);
+                            if (r[h] >= thr) push_tail(p, S.series_id, ka >> 1, t0 + t, r[h]);
+                        }
+                    }
+                    lk = warp_max_key(lk);
+                    best = lk > best ? lk : best;
+                    best_v = __uint_as_float((uint32_t)(best >> 32));
                 }
             }
         };
