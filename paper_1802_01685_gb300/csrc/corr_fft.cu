@@ -744,8 +744,6 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
 {
     const Smem m = smem_setup<true>(p.tw);
     const int tid = threadIdx.x;
-    const int rd = tid + (tid >> 4);
-    const int rv = (FN - tid) + ((FN - tid) >> 4);        // padded address of Z[N - tid]
     const float2 base_f = thread_root(4096.0);
     const float2 base_r = thread_root(8192.0);
     const uint32_t n_rows = p.k_hi - p.k_lo;
@@ -810,7 +808,11 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
         // transform of c[2n] + i c[2n+1].  The first pass of the FFT reads
         // Z'[tid + 512 r]: for r < 8 this thread's own, kept in registers; for
         // r >= 8 those of the mirror thread 512 - tid (thread 0: its own
-        // mirrors and the middle bin), exchanged through shared memory.
+        // mirrors and the middle bin), exchanged through shared memory in an
+        // unpadded [8][512] layout of its own: reader j finds Z'[j + 512 r] at
+        // (r - 8) 512 + j, which writer tid fills for its bin r' at
+        // (8 - r') 512 - tid (the middle bin at 0).  A half-warp then writes,
+        // and reads, 16 consecutive values: no bank conflict either way.
         float vr[16], vi[16];
 #pragma unroll
         for (int r = 0; r < FBINS; ++r) {
@@ -823,7 +825,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
                 vr[0] = y0 + yn;
                 vi[0] = y0 - yn;
                 const float2 xm = m.x[FH];
-                m.z[UPPER] = make_float2(2.f * (xm.x * hm.x + xm.y * hm.y), 2.f * (xm.x * hm.y - xm.y * hm.x));
+                m.z[0] = make_float2(2.f * (xm.x * hm.x + xm.y * hm.y), 2.f * (xm.x * hm.y - xm.y * hm.x));
             } else {
                 const float2 xk = m.x[f], xq = m.x[FN - f];
                 const float ykr = xk.x * hk[r].x + xk.y * hk[r].y, yki = xk.y * hk[r].x - xk.x * hk[r].y;
@@ -834,7 +836,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
                 const float wbr = w.x * br - w.y * bi, wbi = w.x * bi + w.y * br;
                 vr[r] = ar - wbi;
                 vi[r] = ai + wbr;
-                m.z[rv - ROW * r] = make_float2(ar + wbi, wbr - ai);
+                m.z[(FBINS - r) * FT - tid] = make_float2(ar + wbi, wbr - ai);
             }
         }
         __syncthreads();                            // 1
@@ -844,7 +846,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
             prefetch_l2(p.hspec + (size_t)(p.k_lo + np - p.hrow0) * FN + 16 * tid);
 #pragma unroll
         for (int r = FBINS; r < 16; ++r) {
-            const float2 v = m.z[rd + ROW * r];
+            const float2 v = m.z[(r - FBINS) * FT + tid];
             vr[r] = v.x;
             vi[r] = v.y;
         }
@@ -935,8 +937,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
 {
     const Smem m = smem_setup<true>(p.tw);
     const int tid = threadIdx.x;
-    const int rd = tid + (tid >> 4);
-    const int rv = (FN - tid) + ((FN - tid) >> 4);        // padded address of Z[F - tid]
+
     const float2 base_f = thread_root(4096.0);
     const uint32_t n_pairs = (p.k_hi - p.k_lo + 1) / 2;
     uint32_t pair = blockIdx.x;
@@ -987,7 +988,8 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
                 np = pair + gridDim.x;
             }
         }
-        // Z = X conj(H_a) + i X conj(H_b); Z[F - f] = conj(Ya) + i conj(Yb)
+        // Z = X conj(H_a) + i X conj(H_b); Z[F - f] = conj(Ya) + i conj(Yb),
+        // exchanged with the mirror thread as in k_corr_rfft
         float vr[16], vi[16];
 #pragma unroll
         for (int i = 0; i < FBINS; ++i) {
@@ -996,7 +998,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
                 // DC (x.x) and Nyquist (x.y): real products
                 vr[0] = x.x * ha[0].x;
                 vi[0] = x.x * hb[0].x;
-                m.z[UPPER] = make_float2(x.y * ha[0].y, x.y * hb[0].y);
+                m.z[0] = make_float2(x.y * ha[0].y, x.y * hb[0].y);
             } else {
                 const float yar = x.x * ha[i].x + x.y * ha[i].y;
                 const float yai = x.y * ha[i].x - x.x * ha[i].y;
@@ -1004,7 +1006,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
                 const float ybi = x.y * hb[i].x - x.x * hb[i].y;
                 vr[i] = yar - ybi;
                 vi[i] = yai + ybr;
-                m.z[rv - ROW * i] = make_float2(yar + ybi, ybr - yai);
+                m.z[(FBINS - i) * FT - tid] = make_float2(yar + ybi, ybr - yai);
             }
         }
         __syncthreads();                            // 1
@@ -1014,7 +1016,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
             prefetch_l2(p.hspec + (size_t)(p.k_lo + 2 * np - p.hrow0) * FH + 16 * tid);
 #pragma unroll
         for (int r = FBINS; r < 16; ++r) {
-            const float2 v = m.z[rd + ROW * r];
+            const float2 v = m.z[(r - FBINS) * FT + tid];
             vr[r] = v.x;
             vi[r] = v.y;
         }
