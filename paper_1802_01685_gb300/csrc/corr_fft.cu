@@ -33,15 +33,17 @@
 //    auxiliary stream;
 //  * each segment spectrum is computed once per call; all of them stay in L2
 //    and reach shared memory by asynchronous copies (cp.async) issued one
-//    segment ahead, together with the segment's window norms;
+//    segment ahead; the segment's window norms are read from L2 straight
+//    into registers;
 //  * one CTA of 512 threads owns a template (real route) or a pair (pair
 //    route) at a time and holds its spectra in registers (16 bins per
 //    thread).  For every segment it forms the product spectrum; the first FFT
 //    pass reads, per thread, 8 bins it formed itself and 8 that the mirror
 //    thread formed (Hermitian symmetry), exchanged through shared memory; it
-//    runs one inverse transform in shared memory and reduces the output in
-//    registers.  The last radix-2 stage of the FFT is fused into the
-//    epilogue, so the filter output never reaches HBM.
+//    runs one inverse transform in shared memory, alternating between two
+//    work arrays, and reduces the output in registers, with a warp-level
+//    test before the max/argmax and tail work.  The last radix-2 stage of the
+//    FFT is fused into the epilogue, so the filter output never reaches HBM.
 //  * The FFT is a Stockham autosort FFT with three radix-16 passes (each
 //    thread one 16-point DFT per pass, in registers) and a final radix-2
 //    stage; the work array holds complex values with index i stored at
@@ -1085,7 +1087,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
 // true maximum), and they are listed, with the norm, for k_fft_fixup.  The
 // energies come from the FP64 prefix of x^2.  One grid row per series.
 // Every norm is also written, times the inverse transform's scale (a power of
-// two, so exactly), to the per-segment copy the correlation kernel stages:
+// two, so exactly), to the per-segment copy the correlation kernel reads:
 // segment j's lags at inv_seg[j Vp ..), Vp = V rounded up to a multiple of 4,
 // so every segment starts 16-byte aligned; past a segment's last lag its row
 // holds zeros, so that the real route reads whole pairs (t, t + 1) of norms.
