@@ -934,7 +934,9 @@ __global__ void __launch_bounds__(FT, 1) k_corr_rfft(const __grid_constant__ Fft
 // The correlation of the pair route (quadrature banks): a template and its
 // quadrature partner in one complex transform, |rho| = |c_cos + i c_sin| /
 // |window|.  Each CTA walks its items (pair, series, segment) in order, with
-// the next segment's spectrum staged and the norms read as above.
+// the next segment's spectrum staged and the norms read as above.  DENSE as
+// in k_corr_rfft.
+template <bool DENSE>
 __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__ FftParams p)
 {
     const Smem m = smem_setup<true>(p.tw);
@@ -1046,7 +1048,7 @@ __global__ void __launch_bounds__(FT, 1) k_corr_fft_quad(const __grid_constant__
                         const uint32_t tau = t0 + t;
                         r[h] = sqrtf(z[h].x * z[h].x + z[h].y * z[h].y) * iv[2 * u + h];   // norms carry 1/F
                         pa = fmaf(r[h], r[h], pa);
-                        if (S.rho && BF_BOUNDS(p.err, tau < S.L)) S.rho[(size_t)la * S.L + tau] = r[h];
+                        if (DENSE && S.rho && BF_BOUNDS(p.err, tau < S.L)) S.rho[(size_t)la * S.L + tau] = r[h];
                     }
                 }
                 if (warp_max_abs(fmaxf(r[0], r[1])) >= fminf(thr, best_v)) {
@@ -1277,7 +1279,9 @@ cudaError_t fft_attributes()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_corr_rfft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RCORR_SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_corr_fft_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CORR_SMEM);
+        e = cudaFuncSetAttribute(k_corr_fft_quad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CORR_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_corr_fft_quad<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CORR_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fft_series<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM);
     if (e == cudaSuccess)
@@ -1466,10 +1470,12 @@ cudaError_t launch_corr_fft(const FftParams& p, int n_sm, cudaStream_t st)
     if (items == 0 || p.n_ser == 0) return cudaSuccess;
     const unsigned grid = std::min<unsigned>(items, (unsigned)n_sm);
     count_launches(1);
-    if (p.quad) k_corr_fft_quad<<<grid, FT, CORR_SMEM, st>>>(p);
-    else {
-        bool dense = false;
-        for (int i = 0; i < p.n_ser; ++i) dense = dense || p.ser[i].rho != nullptr;
+    bool dense = false;
+    for (int i = 0; i < p.n_ser; ++i) dense = dense || p.ser[i].rho != nullptr;
+    if (p.quad) {
+        if (dense) k_corr_fft_quad<true><<<grid, FT, CORR_SMEM, st>>>(p);
+        else k_corr_fft_quad<false><<<grid, FT, CORR_SMEM, st>>>(p);
+    } else {
         if (dense) k_corr_rfft<true><<<grid, FT, RCORR_SMEM, st>>>(p);
         else k_corr_rfft<false><<<grid, FT, RCORR_SMEM, st>>>(p);
     }
