@@ -219,20 +219,35 @@ __device__ __forceinline__ double pow_m3_8(double v)
     return y * fma(-e, 0.125, 1.0);                     // y - (y^8 v^3 - 1) / (8 y^7 v^3)
 }
 
+// A template's track in cell units, per candidate: q(u) = a + b u (linear) or
+// a (1 - b u)^(-3/8) (power law), i.e. f(u) / df with the divisions by D, t_c
+// and df taken once, not per cell (GB300 divides in FP64 at a small fraction
+// of its FP32 rate).
+struct TrackCells {
+    double a, b;
+};
+
+__device__ __forceinline__ TrackCells track_cells(const ChirpDev& p, double df)
+{
+    if (p.track == BF_LINEAR) return {p.f_lo / df, (p.f_hi - p.f_lo) / (p.D * df)};
+    return {p.f_lo / df, 1.0 / p.tc};
+}
+
 // Frequency cell of the ascending track at local time u (the map paints f(t)).
 // The end of the sweep (u clamped to D) takes its defined value f(D) = f_hi
 // exactly: through the formula it lands within an ulp of f_hi, and where
 // f_hi / df is a whole number the cell would hang on that ulp.  Elsewhere the
-// fast power-law value is within ~1e-13 of the FP64 pow; where f / df lies
-// that close to a cell edge the cell is decided by the FP64 pow.
-__device__ __forceinline__ int64_t track_cell(const ChirpDev& p, double u, double df)
+// fast value is within ~1e-13 of f / df; where f / df lies that close to a
+// cell edge the cell is decided by the defining formula in FP64, with its
+// divisions, as the oracle evaluates it.
+__device__ __forceinline__ int64_t track_cell(const ChirpDev& p, const TrackCells& c, double u, double df)
 {
     if (u >= p.D) return (int64_t)floor(p.f_hi / df);
-    if (p.track == BF_LINEAR) return (int64_t)floor((p.f_lo + (p.f_hi - p.f_lo) * u / p.D) / df);
-    const double v = 1.0 - u / p.tc;
-    double q = p.f_lo * pow_m3_8(v) / df;
-    if (fabs(q - rint(q)) <= 1e-9 * fabs(q)) q = p.f_lo * pow(v, -0.375) / df;
-    return (int64_t)floor(q);
+    const bool lin = p.track == BF_LINEAR;
+    const double q = lin ? fma(c.b, u, c.a) : c.a * pow_m3_8(fma(-u, c.b, 1.0));
+    if (fabs(q - rint(q)) > 1e-9 * fabs(q)) return (int64_t)floor(q);
+    const double f = lin ? p.f_lo + (p.f_hi - p.f_lo) * u / p.D : p.f_lo * pow(1.0 - u / p.tc, -0.375);
+    return (int64_t)floor(f / df);
 }
 
 // one warp per candidate, lanes over time cells
@@ -249,6 +264,7 @@ __global__ void k_paint(const Candidate* __restrict__ cand, const unsigned int* 
         if (cd.series < fp.s0 || cd.series >= fp.s0 + fp.n) continue;
         if (!BF_BOUNDS(fp.err, cd.k < fp.n_chirps)) continue;
         const ChirpDev p = params[cd.k];
+        const TrackCells tcells = track_cells(p, df);
         const FinalizeSeries& f = fp.ser[cd.series - fp.s0];
         const float a = fabsf(cd.rho);
         // a superposed template paints both of its tracks
@@ -267,7 +283,7 @@ __global__ void k_paint(const Candidate* __restrict__ cand, const unsigned int* 
             double u = sense == BF_ASC ? t : p.D - t;
             if (u < 0.0) u = 0.0;
             if (u > p.D) u = p.D;
-            const int64_t fb = track_cell(p, u, df);
+            const int64_t fb = track_cell(p, tcells, u, df);
             if (fb < 0 || fb >= (int64_t)nf) continue;
             atomicMax(reinterpret_cast<int*>(f.map + (size_t)b * nf + fb), __float_as_int(a));
         }
