@@ -544,7 +544,10 @@ def run_fft(ctx, bf, w, xs, ctrl, corr_per_step, alu, steps=3):
         return wall, info.kernel_ms
 
     step()
+    sampler = ClockSampler(torch_device_index())
+    sampler.start()
     walls, kms = zip(*[step() for _ in range(steps)])
+    clocks = sampler.stop()
     wall, k_ms = float(np.mean(walls)), float(np.mean(kms))
     N = 8192                      # complex points per transform
     V = 2 * N - M + 1             # lags per transform: one template, 16384-sample segments
@@ -563,12 +566,44 @@ def run_fft(ctx, bf, w, xs, ctrl, corr_per_step, alu, steps=3):
                          "work": "5 N log2 N nominal flops per N-point complex transform",
                          "note": "on-chip bound: the profile puts shared-memory wavefronts and "
                                  "issue at about half their peaks each; no DRAM bound"},
+            "roofline_smem": smem_roofline(n_transforms, k_ms, clocks),
+            "clocks": clocks,
             "note": "FP32 complex FFTs of 8192 points carrying real segments of 16384 samples "
                     "(even/odd packing), overlap-save with 16385 - M lags per segment, one "
                     "template per transform; ms_per_step includes the template spectra "
                     "(computed from the chirp parameters every step); kernel_ms is the segment "
                     "spectra plus the correlation kernel; fft_tflops_nominal counts 5 N log2 N "
                     "per N-point complex transform"}
+
+
+# shared-memory wavefronts per 8192-point transform of the real-route
+# correlation kernel (ncu l1tex__data_pipe_lsu_wavefronts_mem_shared.sum over
+# the transforms of the 16 s x 16,384-template case): the passes' loads and
+# stores, twiddles, the mirror exchange, the staged segment spectrum and the
+# final stage's loads
+FFT_SMEM_WAVEFRONTS = 4170
+
+
+def torch_device_index() -> int:
+    import torch
+    return torch.cuda.current_device()
+
+
+def smem_roofline(n_transforms, k_ms, clocks):
+    """The FFT route's shared-memory roofline: wavefronts per second over the
+    SMs' peak of one wavefront per SM per cycle at the sampled SM clock."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = clocks.get("sm_mhz") or None
+    achieved = n_transforms * FFT_SMEM_WAVEFRONTS / (k_ms / 1e3)
+    peak = n_sm * mhz * 1e6 if mhz else None
+    return {"bound": "shared-memory wavefronts", "achieved": round(achieved / 1e9, 1),
+            "peak": round(peak / 1e9, 1) if peak else None, "unit": "G wavefronts/s",
+            "frac": round(achieved / peak, 4) if peak else None,
+            "per_transform": FFT_SMEM_WAVEFRONTS,
+            "note": "wavefronts per transform from ncu on the 16 s x 16,384-template case; peak = "
+                    "one wavefront per SM per cycle at the median SM clock sampled during the "
+                    "FFT steps; the kernel time includes the template and segment spectra"}
 
 
 def synth_grid_size(w):
