@@ -8,26 +8,63 @@
 // GB300 runs FP64 at a small fraction of its FP32 rate, so FP64 is spent once
 // per group of 8 samples (synth_group), and the power-law phase avoids a full
 // FP64 pow: (1 - t/t_c)^(5/8) starts from the FP32 powf value and takes one
-// Newton step on y^8 = u^5 in FP64 (relative error ~1e-7 squared), whose
-// reciprocal comes from an FP32 seed and one Newton-Raphson step.
+// Newton step on y^8 = u^5 in float-float arithmetic (relative error ~1e-7
+// squared).
 #pragma once
 
 #include "bf_internal.h"
 
 namespace bfi {
 
-// u^(5/8) for u in (0, 1]; very small u (a sweep over more than ~30x in
-// frequency) would underflow y^8 in FP32 and takes the FP64 pow instead
+// Float-float (double-single) helpers: error-free FP32 products and sums
+// (Dekker; the product's error from one FMA).  The _rn intrinsics keep the
+// compiler from contracting a rounded product into a later addition, which
+// would break the error terms.
+__device__ __forceinline__ float2 ff_two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return make_float2(p, __fmaf_rn(a, b, -p));
+}
+
+// a + b as (sum, error) for |a| >= |b|
+__device__ __forceinline__ float2 ff_fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b)
+{
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    return ff_fast_two_sum(p, e);
+}
+
+// u^(5/8) for u in (0, 1]: the FP32 powf value y, then one Newton step on
+// y^8 = u^5, y <- y (1 + (u^5 / y^8 - 1) / 8), with u^5 and y^8 in float-float
+// (about 46 bits: the difference u^5 - y^8 needs them to well below FP32's
+// resolution, not to FP64's); the result's error is ~1e-14, far inside what
+// the phase anchor needs, at a third of an FP64 Newton step's FP64
+// operations.  Very small u (a sweep over more than ~30x in frequency) would
+// underflow y^8 in FP32 and takes the FP64 pow instead.
 __device__ __forceinline__ double pow_5_8(double u)
 {
     if (u < 1e-4) return pow(u, 0.625);
-    const double y = (double)powf((float)u, 0.625f);
-    const double u2 = u * u, u5 = u2 * u2 * u;
-    const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
-    double r = (double)(1.0f / (float)y8);              // 1/y^8, then one refinement
-    r = r * fma(-y8, r, 2.0);
-    const double qv = u5 * r;                           // u^5 / y^8, close to 1
-    return y * fma(qv - 1.0, 0.125, 1.0);               // y - (y^8 - u^5) / (8 y^7)
+    const float uh = (float)u;
+    const float2 uu = make_float2(uh, (float)(u - (double)uh));
+    const float y0 = powf(uh, 0.625f);
+    const float2 y2 = ff_two_prod(y0, y0);
+    const float2 y4 = ff_mul(y2, y2);
+    const float2 y8 = ff_mul(y4, y4);
+    const float2 u2 = ff_mul(uu, uu);
+    const float2 u4 = ff_mul(u2, u2);
+    const float2 u5 = ff_mul(u4, uu);
+    // the heads agree to within a factor of 2, so their difference is exact
+    const float d = __fadd_rn(__fsub_rn(u5.x, y8.x), __fsub_rn(u5.y, y8.y));
+    const float e = __fdividef(d, y8.x);                    // u^5 / y^8 - 1, near 0
+    return (double)y0 + (double)__fmul_rn(y0, 0.125f * e);
 }
 
 // Samples are made in groups of SYN_G consecutive template indices j0 + dir q.
